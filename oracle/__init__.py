@@ -1,0 +1,273 @@
+"""FP64 CPU oracle of the chunk-coding path -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import this
+package.  It wraps ``ufvc_oracle.c`` (plain C, FP64, OpenMP) through ctypes and shares no code with the
+CUDA library.  See the C file's header for the paper passages and readings each function follows.
+
+Parity status: every function is pinned by ``tests/test_oracle_*.py`` (brute force on tiny tensors,
+closed forms, library cross-checks, exact bit counts).  The rate-distortion behaviour of the
+random-weight codec is "parity unpinned" (random weights have no published R-D to compare with).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ufvc_oracle.c")
+_LIB = os.path.join(_HERE, "libufvc_oracle.so")
+
+NBINS, NSYM, RMAX = 64, 511, 255
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, -O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.orc_gelu.restype = C.c_double
+        _lib.orc_gelu.argtypes = [C.c_double]
+        _lib.orc_scale.restype = C.c_double
+        _lib.orc_scale.argtypes = [C.c_int]
+        _lib.orc_log_threshold.restype = C.c_double
+        _lib.orc_log_threshold.argtypes = [C.c_int]
+        _lib.orc_qstep.restype = C.c_double
+        _lib.orc_qstep.argtypes = [C.c_int]
+        _lib.orc_weight_count.restype = C.c_size_t
+        _lib.orc_weight_count.argtypes = [C.c_int, C.c_int]
+        _lib.orc_rans_encode.restype = C.c_size_t
+    return _lib
+
+
+def _p(a: np.ndarray) -> C.c_void_p:
+    assert a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+# ---------------------------------------------------------------- primitives
+def conv2d(x: np.ndarray, w: np.ndarray, b: np.ndarray, stride: int) -> np.ndarray:
+    """x [H][W][Cin] float64, w [Cout][k][k][Cin] float32, b [Cout] float32 -> [Ho][Wo][Cout]."""
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    H, W, Cin = x.shape
+    Cout, k, _, _ = w.shape
+    p = k // 2
+    Ho, Wo = (H + 2 * p - k) // stride + 1, (W + 2 * p - k) // stride + 1
+    out = np.empty((Ho, Wo, Cout), np.float64)
+    lib().orc_conv2d(_p(x), H, W, Cin, _p(w), _p(b), Cout, k, stride, _p(out))
+    return out
+
+
+def gelu(x: float) -> float:
+    return lib().orc_gelu(float(x))
+
+
+def pixel_shuffle(x: np.ndarray) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64)
+    H, W, C4 = x.shape
+    out = np.empty((2 * H, 2 * W, C4 // 4), np.float64)
+    lib().orc_pixel_shuffle(_p(x), H, W, C4 // 4, _p(out))
+    return out
+
+
+def scale(k: int) -> float:
+    return lib().orc_scale(k)
+
+
+def log_threshold(k: int) -> float:
+    return lib().orc_log_threshold(k)
+
+
+def qstep(qp: int) -> float:
+    return lib().orc_qstep(qp)
+
+
+def thresholds(qp: int) -> np.ndarray:
+    thr = np.empty(NBINS - 1, np.float32)
+    lib().orc_thresholds(qp, _p(thr))
+    return thr
+
+
+def build_tables() -> tuple[np.ndarray, np.ndarray]:
+    """(freq [64][511] uint32, cum [64][512] uint32)."""
+    freq = np.empty((NBINS, NSYM), np.uint32)
+    cum = np.empty((NBINS, NSYM + 1), np.uint32)
+    lib().orc_build_tables(_p(freq), _p(cum))
+    return freq, cum
+
+
+def weight_count(arch: int, n_frames: int) -> int:
+    return int(lib().orc_weight_count(arch, n_frames))
+
+
+def latent_dims(arch: int, H: int, W: int) -> dict:
+    v = [C.c_int() for _ in range(6)]
+    _check(lib().orc_latent_dims(arch, H, W, *[C.byref(t) for t in v]), "latent_dims")
+    return dict(zip(["Hy", "Wy", "Hz", "Wz", "Cy", "Cz"], [t.value for t in v]))
+
+
+# ---------------------------------------------------------------- rANS
+def rans_encode(sym: np.ndarray, tab: np.ndarray, K: int, freq: np.ndarray | None = None,
+                cum: np.ndarray | None = None, offset: int = RMAX) -> bytes:
+    if freq is None:
+        freq, cum = build_tables()
+    sym = np.ascontiguousarray(sym, np.int16)
+    tab = np.ascontiguousarray(tab, np.uint8)
+    freq = np.ascontiguousarray(freq, np.uint32)
+    cum = np.ascontiguousarray(cum, np.uint32)
+    nsym = freq.shape[1]
+    n = sym.size
+    cap = 4 * K + 2 * (n + 2 * K) + 4
+    out = np.empty(cap, np.uint8)
+    size = lib().orc_rans_encode(_p(sym), _p(tab), C.c_size_t(n), K, _p(freq), _p(cum), nsym, offset,
+                                 _p(out), C.c_size_t(cap))
+    if size == 0:
+        raise RuntimeError("oracle rans_encode: capacity")
+    return out[:size].tobytes()
+
+
+def rans_decode(buf: bytes, tab: np.ndarray, n: int, K: int, freq: np.ndarray | None = None,
+                cum: np.ndarray | None = None, offset: int = RMAX) -> tuple[np.ndarray, int]:
+    if freq is None:
+        freq, cum = build_tables()
+    tab = np.ascontiguousarray(tab, np.uint8)
+    freq = np.ascontiguousarray(freq, np.uint32)
+    cum = np.ascontiguousarray(cum, np.uint32)
+    a = np.frombuffer(buf, np.uint8).copy() if len(buf) else np.zeros(1, np.uint8)
+    sym = np.empty(max(n, 1), np.int16)
+    used = C.c_size_t()
+    rc = lib().orc_rans_decode(_p(a), C.c_size_t(len(buf)), _p(tab), C.c_size_t(n), K, _p(freq), _p(cum),
+                               freq.shape[1], offset, _p(sym), C.byref(used))
+    _check(rc, "rans_decode")
+    return sym[:n], used.value
+
+
+# ---------------------------------------------------------------- network stages
+def analysis(arch: int, frames: np.ndarray, weights: np.ndarray) -> np.ndarray:
+    frames = np.ascontiguousarray(frames, np.uint8)
+    N, H, W, _ = frames.shape
+    d = latent_dims(arch, H, W)
+    y = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
+    _check(lib().orc_analysis(arch, N, _p(frames), H, W, _p(weights), _p(y)), "analysis")
+    return y
+
+
+def hyper_analysis(arch: int, N: int, y: np.ndarray, weights: np.ndarray) -> np.ndarray:
+    y = np.ascontiguousarray(y, np.float64)
+    Hy, Wy, _ = y.shape
+    cz = {0: 64, 1: 128}[arch]
+    z = np.empty(((Hy + 3) // 4, (Wy + 3) // 4, cz), np.float64)
+    _check(lib().orc_hyper_analysis(arch, N, _p(y), Hy, Wy, _p(weights), _p(z)), "hyper_analysis")
+    return z
+
+
+def quantize_z(z: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    z = np.ascontiguousarray(z, np.float64)
+    Hz, Wz, Cz = z.shape
+    zhat = np.empty(z.shape, np.int16)
+    iz = np.empty(Cz, np.uint8)
+    _check(lib().orc_quantize_z(_p(z), Hz * Wz, Cz, _p(zhat), _p(iz)), "quantize_z")
+    return zhat, iz
+
+
+def hyper_synthesis(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, weights: np.ndarray):
+    zhat = np.ascontiguousarray(zhat, np.int16)
+    Hz, Wz, _ = zhat.shape
+    cy = {0: 128, 1: 256}[arch]
+    mu = np.empty((Hy, Wy, cy), np.float64)
+    ls = np.empty((Hy, Wy, cy), np.float64)
+    _check(lib().orc_hyper_synthesis(arch, N, _p(zhat), Hz, Wz, Hy, Wy, _p(weights), _p(mu), _p(ls)),
+           "hyper_synthesis")
+    return mu, ls
+
+
+def quantize_y(y: np.ndarray, mu: np.ndarray, logsig: np.ndarray, qp: int):
+    y, mu, logsig = (np.ascontiguousarray(a, np.float64) for a in (y, mu, logsig))
+    rhat = np.empty(y.shape, np.int16)
+    idx = np.empty(y.shape, np.uint8)
+    _check(lib().orc_quantize_y(_p(y), _p(mu), _p(logsig), C.c_size_t(y.size), qp, _p(rhat), _p(idx)),
+           "quantize_y")
+    return rhat, idx
+
+
+def scale_index(logsig: np.ndarray, qp: int) -> np.ndarray:
+    logsig = np.ascontiguousarray(logsig, np.float64)
+    idx = np.empty(logsig.shape, np.uint8)
+    _check(lib().orc_scale_index(_p(logsig), C.c_size_t(logsig.size), qp, _p(idx)), "scale_index")
+    return idx
+
+
+def synthesis(arch: int, N: int, yhat: np.ndarray, H: int, W: int, weights: np.ndarray) -> np.ndarray:
+    yhat = np.ascontiguousarray(yhat, np.float64)
+    Hy, Wy, _ = yhat.shape
+    out = np.empty((N, H, W, 3), np.float64)
+    _check(lib().orc_synthesis(arch, N, _p(yhat), Hy, Wy, H, W, _p(weights), _p(out)), "synthesis")
+    return out
+
+
+class _Debug(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("y", "z", "zhat", "iz", "mu", "logsig", "rhat", "idx")]
+
+
+def encode_chunk(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.ndarray, debug: bool = False):
+    """-> bit-stream bytes (and, with debug, a dict of every intermediate)."""
+    frames = np.ascontiguousarray(frames, np.uint8)
+    N, H, W, _ = frames.shape
+    d = latent_dims(arch, H, W)
+    ny = d["Hy"] * d["Wy"] * d["Cy"]
+    nz = d["Hz"] * d["Wz"] * d["Cz"]
+    cap = 64 + d["Cz"] + 4 * (K + min(K, nz)) + 2 * (ny + nz + 4 * K) + 16
+    out = np.empty(cap, np.uint8)
+    nbytes = C.c_size_t()
+    dbg = None
+    arrs = {}
+    if debug:
+        arrs = dict(y=np.empty((d["Hy"], d["Wy"], d["Cy"])), z=np.empty((d["Hz"], d["Wz"], d["Cz"])),
+                    zhat=np.empty((d["Hz"], d["Wz"], d["Cz"]), np.int16), iz=np.empty(d["Cz"], np.uint8),
+                    mu=np.empty((d["Hy"], d["Wy"], d["Cy"])), logsig=np.empty((d["Hy"], d["Wy"], d["Cy"])),
+                    rhat=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.int16),
+                    idx=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.uint8))
+        dbg = _Debug(**{k: v.ctypes.data for k, v in arrs.items()})
+    rc = lib().orc_encode_chunk(arch, N, _p(frames), H, W, qp, K, _p(weights), _p(out), C.c_size_t(cap),
+                                C.byref(nbytes), C.byref(dbg) if dbg is not None else None)
+    _check(rc, "encode_chunk")
+    bits = out[:nbytes.value].tobytes()
+    return (bits, arrs) if debug else bits
+
+
+def decode_chunk(arch: int, N: int, bits: bytes, H: int, W: int, weights: np.ndarray,
+                 want_frames: bool = True):
+    """-> (frames [N][H][W][3] float64 in [0,1] or None, yhat [Hy][Wy][Cy])."""
+    d = latent_dims(arch, H, W)
+    a = np.frombuffer(bits, np.uint8).copy()
+    yhat = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
+    frames = np.empty((N, H, W, 3), np.float64) if want_frames else None
+    rc = lib().orc_decode_chunk(arch, N, _p(a), C.c_size_t(len(bits)), H, W, _p(weights),
+                                _p(frames) if want_frames else None, _p(yhat))
+    _check(rc, "decode_chunk")
+    return frames, yhat
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())

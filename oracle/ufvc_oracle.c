@@ -1,0 +1,703 @@
+/*
+ * ufvc_oracle.c -- plain, slow, FP64 CPU oracle of the chunk-coding path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load this library.  It shares no code, header, table or constant generator with the CUDA library:
+ * everything here is written out again from the paper and from the readings listed below.
+ *
+ * What it follows (paper "Ultra-Fast Neural Video Compression"):
+ *   Sec. 3.1 (Overview, Fig. 3): a chunk X_i of N frames is patch-embedded, encoded into ONE latent y_i,
+ *     quantised to y^_i, converted into a bit-stream, parsed back and decoded; qp_i sets the rate.
+ *   Sec. 3.2: N frame-specific decoders, one per temporal position, reconstruct all frames in parallel.
+ *   Sec. 3.4 (Fig. 4c): r^ = round(y - mu), coded with the scale sigma only; y^ = r^ + mu; the scales of
+ *     ALL latent elements come from one parameter-estimation pass, so the whole latent is entropy
+ *     coded in a single step.
+ * The paper shows the module internals only in figures.  The plain architecture used here (strided
+ * 3x3 convs + GELU, one residual cross-frame interaction block, a 2-layer hyper-analysis, a 3-layer
+ * hyper-synthesis emitting (mu, log sigma), and conv/residual/pixel-shuffle decoders) and every
+ * numeric convention (scale bins, CDF construction, rANS parameters, bit-stream layout) are the
+ * readings stated beside each function.
+ *
+ * Precision: all convolutions, GELU and hyper-synthesis in FP64 with the float32 weights promoted to
+ * double; CDF tables built in FP64 with libm erf/erfc; rANS in exact integers.
+ *
+ * Parity status of each function: pinned by tests under tests/ (brute force, closed forms, library
+ * cross-checks, exact bit counts), except the rate-distortion behaviour of the random-weight codec,
+ * which no published value can pin ("parity unpinned": random weights have no meaningful R-D).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_CAPACITY 2
+#define ORC_ERR_CORRUPT 3
+#define ORC_ERR_OOM 4
+
+#define NBINS 64          /* scale bins */
+#define RMAX 255          /* |r^| <= 255 */
+#define NSYM 511          /* symbols -255..255 */
+#define PROB_BITS 16
+#define PROB_M (1u << PROB_BITS)
+#define RANS_L (1u << 16) /* lower bound of the 32-bit rANS state */
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Architecture (plain reading of Fig. 3; widths per workload)                                      */
+/* ------------------------------------------------------------------------------------------------ */
+typedef struct { int e0, e1, e2, cy, cz, cd1, cd2; } arch_t;
+
+static int get_arch(int arch, arch_t* a) {
+    if (arch == 0) { arch_t t = {64, 96, 128, 128, 64, 128, 64}; *a = t; return ORC_OK; }
+    if (arch == 1) { arch_t t = {64, 128, 192, 256, 128, 128, 64}; *a = t; return ORC_OK; }
+    return ORC_ERR_ARG;
+}
+
+/* Layer l of the blob: (cout, k, cin).  Encoder/hyper layers 0..10, then 8 per frame. */
+int orc_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
+    arch_t a;
+    if (get_arch(arch, &a) || N < 1 || l < 0 || l >= 11 + 8 * N) return ORC_ERR_ARG;
+    int t[11][3] = {{a.e0, 3, 3 * N}, {a.e1, 3, a.e0}, {a.e2, 3, a.e1}, {a.e2, 3, a.e2}, {a.e2, 1, a.e2},
+                    {a.cy, 3, a.e2},  {a.cz, 3, a.cy}, {a.cz, 3, a.cz}, {4 * a.cz, 3, a.cz},
+                    {4 * a.cz, 3, a.cz}, {2 * a.cy, 1, a.cz}};
+    int d[8][3] = {{4 * a.cd1, 3, a.cy}, {a.cd1, 3, a.cd1}, {a.cd1, 3, a.cd1}, {4 * a.cd2, 3, a.cd1},
+                   {a.cd2, 3, a.cd2},    {a.cd2, 3, a.cd2}, {4 * a.cd2, 3, a.cd2}, {12, 3, a.cd2}};
+    const int* r = (l < 11) ? t[l] : d[(l - 11) % 8];
+    *cout = r[0]; *k = r[1]; *cin = r[2];
+    return ORC_OK;
+}
+
+size_t orc_weight_count(int arch, int N) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < 11 + 8 * N; l++) {
+        if (orc_layer_shape(arch, N, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
+/* Pointers to layer l's kernel [Cout][k][k][Cin] and bias [Cout] inside the blob. */
+static void layer_ptr(int arch, int N, const float* blob, int l, const float** w, const float** b) {
+    size_t off = 0;
+    int co, k, ci;
+    for (int i = 0; i < l; i++) {
+        orc_layer_shape(arch, N, i, &co, &k, &ci);
+        off += (size_t)co * k * k * ci + co;
+    }
+    orc_layer_shape(arch, N, l, &co, &k, &ci);
+    *w = blob + off;
+    *b = blob + off + (size_t)co * k * k * ci;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Network primitives                                                                               */
+/* ------------------------------------------------------------------------------------------------ */
+
+/* 2-D convolution, NHWC, zero padding k/2, stride s:
+ *   out[oh][ow][co] = b[co] + sum_{ky,kx,ci} w[co][ky][kx][ci] * in[oh*s+ky-k/2][ow*s+kx-k/2][ci]
+ * (terms outside the input are zero).  Ho = (H + 2*(k/2) - k)/s + 1. */
+void orc_conv2d(const double* in, int H, int W, int Cin, const float* w, const float* b, int Cout, int k,
+                int s, double* out) {
+    int p = k / 2;
+    int Ho = (H + 2 * p - k) / s + 1, Wo = (W + 2 * p - k) / s + 1;
+    double* wd = (double*)malloc(sizeof(double) * (size_t)Cout * k * k * Cin);
+    for (size_t i = 0; i < (size_t)Cout * k * k * Cin; i++) wd[i] = (double)w[i];
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int oh = 0; oh < Ho; oh++)
+        for (int ow = 0; ow < Wo; ow++) {
+            double* o = out + ((size_t)oh * Wo + ow) * Cout;
+            for (int co = 0; co < Cout; co++) {
+                double acc = (double)b[co];
+                for (int ky = 0; ky < k; ky++) {
+                    int ih = oh * s + ky - p;
+                    if (ih < 0 || ih >= H) continue;
+                    for (int kx = 0; kx < k; kx++) {
+                        int iw = ow * s + kx - p;
+                        if (iw < 0 || iw >= W) continue;
+                        const double* x = in + ((size_t)ih * W + iw) * Cin;
+                        const double* wk = wd + (((size_t)co * k + ky) * k + kx) * Cin;
+                        for (int ci = 0; ci < Cin; ci++) acc += wk[ci] * x[ci];
+                    }
+                }
+                o[co] = acc;
+            }
+        }
+    free(wd);
+}
+
+/* GELU, exact erf form: x * Phi(x) = 0.5 x (1 + erf(x / sqrt 2)). */
+double orc_gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
+
+static void gelu_inplace(double* x, size_t n) {
+    for (size_t i = 0; i < n; i++) x[i] = orc_gelu(x[i]);
+}
+
+/* Pixel shuffle x2 (NHWC): out[2h+dy][2w+dx][c] = in[h][w][4c + 2dy + dx]; in has 4C channels. */
+void orc_pixel_shuffle(const double* in, int H, int W, int C, double* out) {
+    for (int h = 0; h < H; h++)
+        for (int w = 0; w < W; w++)
+            for (int c = 0; c < C; c++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++)
+                        out[(((size_t)(2 * h + dy)) * (2 * W) + (2 * w + dx)) * C + c] =
+                            in[((size_t)h * W + w) * 4 * C + 4 * c + 2 * dy + dx];
+}
+
+static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+
+static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1; }
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Analysis (patchify + chunk encoder + cross-frame interaction), Sec. 3.1, Fig. 3                 */
+/* ------------------------------------------------------------------------------------------------ */
+
+/* Chunk -> latent y [Hy][Wy][Cy].  The N frames' RGB are stacked into 3N input channels (frame n ->
+ * channels 3n..3n+2), scaled by 1/255 and replicate-padded to multiples of 16.  Then
+ * A1..A3 (3x3 stride 2 + GELU), the interaction block h + Xb(GELU(Xa(h))), A4 (3x3 stride 2). */
+int orc_analysis(int arch, int N, const uint8_t* frames, int H, int W, const float* wts, double* y) {
+    arch_t a;
+    if (get_arch(arch, &a) || N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
+    int Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16, C0 = 3 * N;
+    double* x = dalloc((size_t)Hp * Wp * C0);
+    for (int h = 0; h < Hp; h++)
+        for (int w = 0; w < Wp; w++)
+            for (int n = 0; n < N; n++)
+                for (int c = 0; c < 3; c++) {
+                    int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
+                    x[((size_t)h * Wp + w) * C0 + 3 * n + c] =
+                        frames[(((size_t)n * H + sh) * W + sw) * 3 + c] / 255.0;
+                }
+    const float *wk, *bk;
+    int h1 = conv_out(Hp, 3, 2), w1 = conv_out(Wp, 3, 2);
+    double* t1 = dalloc((size_t)h1 * w1 * a.e0);
+    layer_ptr(arch, N, wts, 0, &wk, &bk);
+    orc_conv2d(x, Hp, Wp, C0, wk, bk, a.e0, 3, 2, t1);
+    gelu_inplace(t1, (size_t)h1 * w1 * a.e0);
+    int h2 = conv_out(h1, 3, 2), w2 = conv_out(w1, 3, 2);
+    double* t2 = dalloc((size_t)h2 * w2 * a.e1);
+    layer_ptr(arch, N, wts, 1, &wk, &bk);
+    orc_conv2d(t1, h1, w1, a.e0, wk, bk, a.e1, 3, 2, t2);
+    gelu_inplace(t2, (size_t)h2 * w2 * a.e1);
+    int h3 = conv_out(h2, 3, 2), w3 = conv_out(w2, 3, 2);
+    size_t n3 = (size_t)h3 * w3 * a.e2;
+    double* t3 = dalloc(n3);
+    layer_ptr(arch, N, wts, 2, &wk, &bk);
+    orc_conv2d(t2, h2, w2, a.e1, wk, bk, a.e2, 3, 2, t3);
+    gelu_inplace(t3, n3);
+    /* cross-frame interaction: h + Xb(GELU(Xa(h))) */
+    double* u = dalloc(n3);
+    double* v = dalloc(n3);
+    layer_ptr(arch, N, wts, 3, &wk, &bk);
+    orc_conv2d(t3, h3, w3, a.e2, wk, bk, a.e2, 3, 1, u);
+    gelu_inplace(u, n3);
+    layer_ptr(arch, N, wts, 4, &wk, &bk);
+    orc_conv2d(u, h3, w3, a.e2, wk, bk, a.e2, 1, 1, v);
+    for (size_t i = 0; i < n3; i++) t3[i] += v[i];
+    layer_ptr(arch, N, wts, 5, &wk, &bk);
+    orc_conv2d(t3, h3, w3, a.e2, wk, bk, a.cy, 3, 2, y);
+    free(x); free(t1); free(t2); free(t3); free(u); free(v);
+    return ORC_OK;
+}
+
+/* Hyper-analysis: z = H2(GELU(H1(y))), both 3x3 stride 2.  z: [ceil(Hy/4)][ceil(Wy/4)][Cz]. */
+int orc_hyper_analysis(int arch, int N, const double* y, int Hy, int Wy, const float* wts, double* z) {
+    arch_t a;
+    if (get_arch(arch, &a)) return ORC_ERR_ARG;
+    const float *wk, *bk;
+    int h1 = conv_out(Hy, 3, 2), w1 = conv_out(Wy, 3, 2);
+    double* t = dalloc((size_t)h1 * w1 * a.cz);
+    layer_ptr(arch, N, wts, 6, &wk, &bk);
+    orc_conv2d(y, Hy, Wy, a.cy, wk, bk, a.cz, 3, 2, t);
+    gelu_inplace(t, (size_t)h1 * w1 * a.cz);
+    layer_ptr(arch, N, wts, 7, &wk, &bk);
+    orc_conv2d(t, h1, w1, a.cz, wk, bk, a.cz, 3, 2, z);
+    free(t);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Scale bins, thresholds and CDF tables                                                            */
+/* ------------------------------------------------------------------------------------------------ */
+
+/* Scale bin k = 0..63: s_k = exp(ln 0.11 + k (ln 64 - ln 0.11) / 63) (64 log-spaced bins on [0.11, 64]). */
+double orc_scale(int k) { return exp(log(0.11) + k * (log(64.0) - log(0.11)) / 63.0); }
+
+/* Log-domain decision threshold between bins k-1 and k (k = 1..63): the midpoint of their logs. */
+double orc_log_threshold(int k) { return 0.5 * (log(orc_scale(k - 1)) + log(orc_scale(k))); }
+
+/* Quantisation step for qp in [0, 63]: q = 2^((qp - 32) / 8); qp = 32 gives q = 1. */
+double orc_qstep(int qp) { return pow(2.0, (qp - 32) / 8.0); }
+
+/* FP32 thresholds used to index log sigma at rate qp: thr[k-1] = float(t_k + ln q), k = 1..63.
+ * The element's scale relative to the quantisation step is sigma/q, so ln(sigma/q) > t_k  <=>
+ * ln sigma > t_k + ln q. */
+void orc_thresholds(int qp, float* thr) {
+    double lq = log(orc_qstep(qp));
+    for (int k = 1; k < NBINS; k++) thr[k - 1] = (float)(orc_log_threshold(k) + lq);
+}
+
+/* Integer CDF table for bin k: a zero-mean Gaussian of std s = s_k discretised on the integers,
+ * |r| <= 255, tails beyond +-254.5 folded into the end symbols:
+ *   p_0 = erf(0.5 / (s sqrt2)),  p_r = (erfc((|r|-0.5)/(s sqrt2)) - erfc((|r|+0.5)/(s sqrt2))) / 2
+ *   for 0 < |r| < 255, p_{+-255} = erfc(254.5 / (s sqrt2)) / 2;
+ *   f_r = 1 + floor(p_r (2^16 - 511)), then f_0 += 2^16 - sum f (the mode takes the rounding deficit).
+ * freq[k*511 + (r+255)] = f_r; cum[k*512 + j] = sum_{i<j} f.  Built in FP64. */
+void orc_build_tables(uint32_t* freq, uint32_t* cum) {
+    const double budget = (double)(PROB_M - NSYM);
+    for (int k = 0; k < NBINS; k++) {
+        double s = orc_scale(k), d = s * sqrt(2.0);
+        uint32_t* f = freq + (size_t)k * NSYM;
+        for (int r = 0; r <= RMAX; r++) {
+            double p;
+            if (r == 0) p = erf(0.5 / d);
+            else if (r < RMAX) p = 0.5 * (erfc((r - 0.5) / d) - erfc((r + 0.5) / d));
+            else p = 0.5 * erfc((RMAX - 0.5) / d);
+            uint32_t fr = 1u + (uint32_t)floor(p * budget);
+            f[RMAX + r] = fr;
+            f[RMAX - r] = fr;
+        }
+        uint32_t sum = 0;
+        for (int i = 0; i < NSYM; i++) sum += f[i];
+        f[RMAX] += PROB_M - sum;
+        uint32_t* c = cum + (size_t)k * (NSYM + 1);
+        c[0] = 0;
+        for (int i = 0; i < NSYM; i++) c[i + 1] = c[i] + f[i];
+    }
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Quantisation (Sec. 3.4: r^ = round(y - mu), y^ = r^ + mu) and scale indexing                      */
+/* ------------------------------------------------------------------------------------------------ */
+
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* Hyper-latent: z^ = clamp(rint(z), -255, 255).  Per channel c, the scale index used to code z^ is the
+ * nearest log bin of the channel's RMS: iz[c] = #{k : t_k < ln sqrt(S_c / n)}, S_c = sum z^^2 over the
+ * n = Hz*Wz positions (S_c = 0 gives bin 0). */
+int orc_quantize_z(const double* z, int npos, int cz, int16_t* zhat, uint8_t* iz) {
+    for (size_t i = 0; i < (size_t)npos * cz; i++) zhat[i] = (int16_t)clampd(rint(z[i]), -RMAX, RMAX);
+    for (int c = 0; c < cz; c++) {
+        double S = 0.0;
+        for (int p = 0; p < npos; p++) {
+            double v = zhat[(size_t)p * cz + c];
+            S += v * v;
+        }
+        int idx = 0;
+        if (S > 0.0) {
+            double lr = 0.5 * log(S / npos);
+            for (int k = 1; k < NBINS; k++) idx += orc_log_threshold(k) < lr;
+        }
+        iz[c] = (uint8_t)idx;
+    }
+    return ORC_OK;
+}
+
+/* Hyper-synthesis (single-step parameter estimation, Sec. 3.4): from z^ alone, one pass gives mu and
+ * log sigma for every latent element.  S1, S2: 3x3 conv Cz -> 4Cz, pixel shuffle x2, GELU; crop to
+ * (Hy, Wy); S3: 1x1 conv Cz -> 2Cy; channels [0, Cy) are mu, [Cy, 2Cy) are log sigma. */
+int orc_hyper_synthesis(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
+                        const float* wts, double* mu, double* logsig) {
+    arch_t a;
+    if (get_arch(arch, &a) || 4 * Hz < Hy || 4 * Wz < Wy) return ORC_ERR_ARG;
+    const float *wk, *bk;
+    int cz = a.cz;
+    double* zd = dalloc((size_t)Hz * Wz * cz);
+    for (size_t i = 0; i < (size_t)Hz * Wz * cz; i++) zd[i] = zhat[i];
+    double* t = dalloc((size_t)Hz * Wz * 4 * cz);
+    double* s1 = dalloc((size_t)4 * Hz * Wz * cz);
+    layer_ptr(arch, N, wts, 8, &wk, &bk);
+    orc_conv2d(zd, Hz, Wz, cz, wk, bk, 4 * cz, 3, 1, t);
+    orc_pixel_shuffle(t, Hz, Wz, cz, s1);
+    gelu_inplace(s1, (size_t)4 * Hz * Wz * cz);
+    int H1 = 2 * Hz, W1 = 2 * Wz;
+    double* t2 = dalloc((size_t)H1 * W1 * 4 * cz);
+    double* s2 = dalloc((size_t)4 * H1 * W1 * cz);
+    layer_ptr(arch, N, wts, 9, &wk, &bk);
+    orc_conv2d(s1, H1, W1, cz, wk, bk, 4 * cz, 3, 1, t2);
+    orc_pixel_shuffle(t2, H1, W1, cz, s2);
+    gelu_inplace(s2, (size_t)4 * H1 * W1 * cz);
+    /* crop (2H1 x 2W1) -> (Hy x Wy) */
+    double* s2c = dalloc((size_t)Hy * Wy * cz);
+    for (int h = 0; h < Hy; h++)
+        memcpy(s2c + (size_t)h * Wy * cz, s2 + (size_t)h * (2 * W1) * cz, sizeof(double) * Wy * cz);
+    double* p = dalloc((size_t)Hy * Wy * 2 * a.cy);
+    layer_ptr(arch, N, wts, 10, &wk, &bk);
+    orc_conv2d(s2c, Hy, Wy, cz, wk, bk, 2 * a.cy, 1, 1, p);
+    for (size_t i = 0; i < (size_t)Hy * Wy; i++) {
+        memcpy(mu + i * a.cy, p + i * 2 * a.cy, sizeof(double) * a.cy);
+        memcpy(logsig + i * a.cy, p + i * 2 * a.cy + a.cy, sizeof(double) * a.cy);
+    }
+    free(zd); free(t); free(s1); free(t2); free(s2); free(s2c); free(p);
+    return ORC_OK;
+}
+
+/* Latent quantisation at rate qp: r^ = clamp(rint((y - mu) / q), -255, 255) and the scale index
+ * idx = #{k : thr_qp[k] < log sigma} with the FP32 thresholds of orc_thresholds (the comparison is
+ * strict, so a value equal to a threshold goes to the lower bin). */
+int orc_quantize_y(const double* y, const double* mu, const double* logsig, size_t n, int qp,
+                   int16_t* rhat, uint8_t* idx) {
+    if (qp < 0 || qp > 63) return ORC_ERR_ARG;
+    double q = orc_qstep(qp);
+    float thr[NBINS - 1];
+    orc_thresholds(qp, thr);
+    for (size_t i = 0; i < n; i++) {
+        rhat[i] = (int16_t)clampd(rint((y[i] - mu[i]) / q), -RMAX, RMAX);
+        int k = 0;
+        for (int j = 0; j < NBINS - 1; j++) k += (double)thr[j] < logsig[i];
+        idx[i] = (uint8_t)k;
+    }
+    return ORC_OK;
+}
+
+/* Index only (used by the decoder, which has log sigma but no y). */
+int orc_scale_index(const double* logsig, size_t n, int qp, uint8_t* idx) {
+    if (qp < 0 || qp > 63) return ORC_ERR_ARG;
+    float thr[NBINS - 1];
+    orc_thresholds(qp, thr);
+    for (size_t i = 0; i < n; i++) {
+        int k = 0;
+        for (int j = 0; j < NBINS - 1; j++) k += (double)thr[j] < logsig[i];
+        idx[i] = (uint8_t)k;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Interleaved rANS (single consolidated coding step over the whole latent, Sec. 3.4)               */
+/* ------------------------------------------------------------------------------------------------ */
+/* Reading: 32-bit state x in [2^16, 2^32), probabilities with 16-bit precision (M = 2^16), 16-bit
+ * output words (Duda's rANS with Giesen's interleaving).  K lanes: element i goes to lane i mod K; lane
+ * j codes its elements i = j, j+K, j+2K, ... .  Encoding runs each lane backwards (last element first)
+ * starting from x = 2^16:
+ *     if x >= f * 2^16: emit x & 0xFFFF, x >>= 16           (at most one word per symbol)
+ *     x = floor(x / f) * 2^16 + (x mod f) + c
+ * then flushes x as two words.  A lane's stream is stored in decoding order: the final state's high
+ * half, its low half, then the renormalisation words newest first.  Decoding runs forwards:
+ *     x = (w0 << 16) | w1;  per symbol: slot = x & 0xFFFF, s = the symbol with c_s <= slot < c_s + f_s,
+ *     x = f_s (x >> 16) + slot - c_s;  if x < 2^16: x = (x << 16) | next word
+ * and a valid lane ends with x == 2^16 having consumed exactly its words.
+ *
+ * Tables are generic for testing: symbol value v uses slot v + offset of table t (freq[t*nsym + slot],
+ * cum[t*(nsym+1) + slot]); the codec uses nsym = 511, offset = 255.
+ *
+ * Section layout: K little-endian u32 word counts, then the K lane streams back to back (u16 words),
+ * zero-padded to a multiple of 4 bytes.  Returns the section size in bytes (0 on capacity error). */
+size_t orc_rans_encode(const int16_t* sym, const uint8_t* tab, size_t n, int K, const uint32_t* freq,
+                       const uint32_t* cum, int nsym, int offset, uint8_t* out, size_t cap) {
+    if (K < 1) return 0;
+    size_t per_lane = n / K + 1 + 2;
+    uint16_t* buf = (uint16_t*)malloc(sizeof(uint16_t) * per_lane);
+    size_t head = (size_t)K * 4, pos = head;
+    if (cap < head) { free(buf); return 0; }
+    for (int j = 0; j < K; j++) {
+        size_t cnt = (j < (long long)n) ? (n - j + K - 1) / K : 0; /* elements of lane j */
+        size_t wp = per_lane;                                     /* fill buf from the back */
+        uint32_t x = RANS_L;
+        for (size_t m = cnt; m-- > 0;) {
+            size_t i = (size_t)j + m * K;
+            int slot = sym[i] + offset;
+            uint32_t f = freq[(size_t)tab[i] * nsym + slot];
+            uint32_t c = cum[(size_t)tab[i] * (nsym + 1) + slot];
+            if ((uint64_t)x >= (uint64_t)f << 16) {
+                buf[--wp] = (uint16_t)(x & 0xFFFF);
+                x >>= 16;
+            }
+            x = (x / f) * PROB_M + (x % f) + c;
+        }
+        buf[--wp] = (uint16_t)(x & 0xFFFF);
+        buf[--wp] = (uint16_t)(x >> 16);
+        uint32_t words = (uint32_t)(per_lane - wp);
+        if (pos + 2 * (size_t)words > cap) { free(buf); return 0; }
+        out[4 * j + 0] = (uint8_t)(words & 0xFF);
+        out[4 * j + 1] = (uint8_t)((words >> 8) & 0xFF);
+        out[4 * j + 2] = (uint8_t)((words >> 16) & 0xFF);
+        out[4 * j + 3] = (uint8_t)(words >> 24);
+        for (uint32_t w = 0; w < words; w++) {
+            uint16_t v = buf[wp + w];
+            out[pos++] = (uint8_t)(v & 0xFF);
+            out[pos++] = (uint8_t)(v >> 8);
+        }
+    }
+    while (pos % 4) {
+        if (pos >= cap) { free(buf); return 0; }
+        out[pos++] = 0;
+    }
+    free(buf);
+    return pos;
+}
+
+/* Decode a section produced by orc_rans_encode.  avail = bytes available from `in`.  Writes the n
+ * symbols and *used = section size in bytes.  Returns ORC_ERR_CORRUPT if a lane's counts, words or
+ * final state are inconsistent. */
+int orc_rans_decode(const uint8_t* in, size_t avail, const uint8_t* tab, size_t n, int K, const uint32_t* freq,
+                    const uint32_t* cum, int nsym, int offset, int16_t* sym, size_t* used) {
+    if (K < 1 || avail < (size_t)K * 4) return ORC_ERR_CORRUPT;
+    size_t pos = (size_t)K * 4;
+    for (int j = 0; j < K; j++) {
+        uint32_t words = (uint32_t)in[4 * j] | ((uint32_t)in[4 * j + 1] << 8) | ((uint32_t)in[4 * j + 2] << 16) |
+                         ((uint32_t)in[4 * j + 3] << 24);
+        size_t cnt = (j < (long long)n) ? (n - j + K - 1) / K : 0;
+        if (words < 2 || words > cnt + 2 || pos + 2 * (size_t)words > avail) return ORC_ERR_CORRUPT;
+        const uint8_t* p = in + pos;
+        uint32_t r = 0;
+#define NEXTW() ((uint32_t)p[2 * r] | ((uint32_t)p[2 * r + 1] << 8))
+        uint32_t x = NEXTW() << 16;
+        r++;
+        x |= NEXTW();
+        r++;
+        for (size_t m = 0; m < cnt; m++) {
+            size_t i = (size_t)j + m * K;
+            const uint32_t* c = cum + (size_t)tab[i] * (nsym + 1);
+            uint32_t slot = x & 0xFFFF;
+            int s = 0;
+            while (s + 1 < nsym && c[s + 1] <= slot) s++; /* linear search: plain, slow, obvious */
+            uint32_t f = c[s + 1] - c[s];
+            x = f * (x >> 16) + slot - c[s];
+            if (x < RANS_L) {
+                if (r >= words) return ORC_ERR_CORRUPT;
+                x = (x << 16) | NEXTW();
+                r++;
+            }
+            sym[i] = (int16_t)(s - offset);
+        }
+#undef NEXTW
+        if (x != RANS_L || r != words) return ORC_ERR_CORRUPT;
+        pos += 2 * (size_t)words;
+    }
+    while (pos % 4) pos++;
+    if (pos > avail) return ORC_ERR_CORRUPT;
+    *used = pos;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Frame-specific synthesis (Sec. 3.2): N decoders, decoder f reconstructs frame f from y^            */
+/* ------------------------------------------------------------------------------------------------ */
+
+/* Decoder f: D0 3x3 Cy->4Cd1, PS, GELU; R1: h + R1b(GELU(R1a(h))); U1 3x3 Cd1->4Cd2, PS, GELU;
+ * R2: h + R2b(GELU(R2a(h))); U2 3x3 Cd2->4Cd2, PS, GELU; U3 3x3 Cd2->12, PS -> o (3 channels);
+ * x^ = clamp(0.5 + o, 0, 1), cropped to H x W.  frames: [N][H][W][3] doubles in [0, 1]. */
+int orc_synthesis(int arch, int N, const double* yhat, int Hy, int Wy, int H, int W, const float* wts,
+                  double* frames) {
+    arch_t a;
+    if (get_arch(arch, &a) || 16 * Hy < H || 16 * Wy < W) return ORC_ERR_ARG;
+    for (int f = 0; f < N; f++) {
+        const float *wk, *bk;
+        int base = 11 + 8 * f;
+        int h = Hy, w = Wy;
+        /* D0 */
+        double* t = dalloc((size_t)h * w * 4 * a.cd1);
+        layer_ptr(arch, N, wts, base + 0, &wk, &bk);
+        orc_conv2d(yhat, h, w, a.cy, wk, bk, 4 * a.cd1, 3, 1, t);
+        double* h1 = dalloc((size_t)4 * h * w * a.cd1);
+        orc_pixel_shuffle(t, h, w, a.cd1, h1);
+        free(t);
+        h *= 2; w *= 2;
+        size_t n1 = (size_t)h * w * a.cd1;
+        gelu_inplace(h1, n1);
+        /* R1 */
+        double* u = dalloc(n1);
+        double* v = dalloc(n1);
+        layer_ptr(arch, N, wts, base + 1, &wk, &bk);
+        orc_conv2d(h1, h, w, a.cd1, wk, bk, a.cd1, 3, 1, u);
+        gelu_inplace(u, n1);
+        layer_ptr(arch, N, wts, base + 2, &wk, &bk);
+        orc_conv2d(u, h, w, a.cd1, wk, bk, a.cd1, 3, 1, v);
+        for (size_t i = 0; i < n1; i++) h1[i] += v[i];
+        free(u); free(v);
+        /* U1 */
+        t = dalloc((size_t)h * w * 4 * a.cd2);
+        layer_ptr(arch, N, wts, base + 3, &wk, &bk);
+        orc_conv2d(h1, h, w, a.cd1, wk, bk, 4 * a.cd2, 3, 1, t);
+        double* h2 = dalloc((size_t)4 * h * w * a.cd2);
+        orc_pixel_shuffle(t, h, w, a.cd2, h2);
+        free(t); free(h1);
+        h *= 2; w *= 2;
+        size_t n2 = (size_t)h * w * a.cd2;
+        gelu_inplace(h2, n2);
+        /* R2 */
+        u = dalloc(n2);
+        v = dalloc(n2);
+        layer_ptr(arch, N, wts, base + 4, &wk, &bk);
+        orc_conv2d(h2, h, w, a.cd2, wk, bk, a.cd2, 3, 1, u);
+        gelu_inplace(u, n2);
+        layer_ptr(arch, N, wts, base + 5, &wk, &bk);
+        orc_conv2d(u, h, w, a.cd2, wk, bk, a.cd2, 3, 1, v);
+        for (size_t i = 0; i < n2; i++) h2[i] += v[i];
+        free(u); free(v);
+        /* U2 */
+        t = dalloc((size_t)h * w * 4 * a.cd2);
+        layer_ptr(arch, N, wts, base + 6, &wk, &bk);
+        orc_conv2d(h2, h, w, a.cd2, wk, bk, 4 * a.cd2, 3, 1, t);
+        double* h3 = dalloc((size_t)4 * h * w * a.cd2);
+        orc_pixel_shuffle(t, h, w, a.cd2, h3);
+        free(t); free(h2);
+        h *= 2; w *= 2;
+        gelu_inplace(h3, (size_t)h * w * a.cd2);
+        /* U3 */
+        t = dalloc((size_t)h * w * 12);
+        layer_ptr(arch, N, wts, base + 7, &wk, &bk);
+        orc_conv2d(h3, h, w, a.cd2, wk, bk, 12, 3, 1, t);
+        double* o = dalloc((size_t)4 * h * w * 3);
+        orc_pixel_shuffle(t, h, w, 3, o);
+        free(t); free(h3);
+        h *= 2; w *= 2;
+        for (int yy = 0; yy < H; yy++)
+            for (int xx = 0; xx < W; xx++)
+                for (int c = 0; c < 3; c++)
+                    frames[(((size_t)f * H + yy) * W + xx) * 3 + c] =
+                        clampd(0.5 + o[((size_t)yy * w + xx) * 3 + c], 0.0, 1.0);
+        free(o);
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Whole chunk: encode and decode with the bit-stream container                                     */
+/* ------------------------------------------------------------------------------------------------ */
+/* Container (little-endian): "UFVC", u8 version = 1, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K,
+ * u32 Kz, Cz bytes iz[c]; zero-padded to a multiple of 4; then the z^ section (Kz lanes, Kz = min(K,
+ * n_z)), then the y^ section (K lanes).  Both sections as in orc_rans_encode. */
+
+static void put16(uint8_t* p, uint32_t v) { p[0] = v & 0xFF; p[1] = (v >> 8) & 0xFF; }
+static void put32(uint8_t* p, uint32_t v) { put16(p, v & 0xFFFF); put16(p + 2, v >> 16); }
+static uint32_t get16(const uint8_t* p) { return (uint32_t)p[0] | ((uint32_t)p[1] << 8); }
+static uint32_t get32(const uint8_t* p) { return get16(p) | (get16(p + 2) << 16); }
+
+typedef struct {
+    double* y;        /* [Hy][Wy][Cy] */
+    double* z;        /* [Hz][Wz][Cz] */
+    int16_t* zhat;
+    uint8_t* iz;      /* [Cz] */
+    double* mu;
+    double* logsig;
+    int16_t* rhat;
+    uint8_t* idx;
+} orc_debug;
+
+int orc_latent_dims(int arch, int H, int W, int* Hy, int* Wy, int* Hz, int* Wz, int* Cy, int* Cz) {
+    arch_t a;
+    if (get_arch(arch, &a) || H < 1 || W < 1) return ORC_ERR_ARG;
+    int hp = (H + 15) / 16 * 16, wp = (W + 15) / 16 * 16;
+    *Hy = hp / 16; *Wy = wp / 16;
+    *Hz = (*Hy + 3) / 4; *Wz = (*Wy + 3) / 4;
+    /* two stride-2 convs with padding 1 give ceil(ceil(x/2)/2) = ceil(x/4) */
+    *Cy = a.cy; *Cz = a.cz;
+    return ORC_OK;
+}
+
+int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int qp, int K, const float* wts,
+                     uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg) {
+    int Hy, Wy, Hz, Wz, Cy, Cz;
+    if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz) || N < 1 || N > 255 || qp < 0 || qp > 63 ||
+        K < 1 || W > 65535 || H > 65535)
+        return ORC_ERR_ARG;
+    size_t ny = (size_t)Hy * Wy * Cy, nz = (size_t)Hz * Wz * Cz;
+    double* y = dalloc(ny);
+    double* z = dalloc(nz);
+    int16_t* zhat = (int16_t*)malloc(2 * nz);
+    uint8_t iz[256];
+    double* mu = dalloc(ny);
+    double* ls = dalloc(ny);
+    int16_t* rhat = (int16_t*)malloc(2 * ny);
+    uint8_t* idx = (uint8_t*)malloc(ny);
+    uint8_t* zidx = (uint8_t*)malloc(nz);
+    uint32_t* freq = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * NSYM);
+    uint32_t* cum = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * (NSYM + 1));
+    int rc = ORC_OK;
+    orc_build_tables(freq, cum);
+    orc_analysis(arch, N, frames, H, W, wts, y);
+    orc_hyper_analysis(arch, N, y, Hy, Wy, wts, z);
+    orc_quantize_z(z, Hz * Wz, Cz, zhat, iz);
+    orc_hyper_synthesis(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls);
+    orc_quantize_y(y, mu, ls, ny, qp, rhat, idx);
+    for (size_t i = 0; i < nz; i++) zidx[i] = iz[i % Cz];
+    size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
+    int Kz = (size_t)K < nz ? K : (int)nz;
+    if (cap < hdr) { rc = ORC_ERR_CAPACITY; goto done; }
+    memset(out, 0, hdr);
+    memcpy(out, "UFVC", 4);
+    out[4] = 1; out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
+    put16(out + 8, (uint32_t)W); put16(out + 10, (uint32_t)H);
+    put32(out + 12, (uint32_t)K); put32(out + 16, (uint32_t)Kz);
+    memcpy(out + 20, iz, Cz);
+    size_t s1 = orc_rans_encode(zhat, zidx, nz, Kz, freq, cum, NSYM, RMAX, out + hdr, cap - hdr);
+    if (!s1) { rc = ORC_ERR_CAPACITY; goto done; }
+    size_t s2 = orc_rans_encode(rhat, idx, ny, K, freq, cum, NSYM, RMAX, out + hdr + s1, cap - hdr - s1);
+    if (!s2) { rc = ORC_ERR_CAPACITY; goto done; }
+    *nbytes = hdr + s1 + s2;
+    if (dbg) {
+        if (dbg->y) memcpy(dbg->y, y, sizeof(double) * ny);
+        if (dbg->z) memcpy(dbg->z, z, sizeof(double) * nz);
+        if (dbg->zhat) memcpy(dbg->zhat, zhat, 2 * nz);
+        if (dbg->iz) memcpy(dbg->iz, iz, Cz);
+        if (dbg->mu) memcpy(dbg->mu, mu, sizeof(double) * ny);
+        if (dbg->logsig) memcpy(dbg->logsig, ls, sizeof(double) * ny);
+        if (dbg->rhat) memcpy(dbg->rhat, rhat, 2 * ny);
+        if (dbg->idx) memcpy(dbg->idx, idx, ny);
+    }
+done:
+    free(y); free(z); free(zhat); free(mu); free(ls); free(rhat); free(idx); free(zidx); free(freq); free(cum);
+    return rc;
+}
+
+/* Decode: parse the container, decode z^ (single step), hyper-synthesis -> mu, log sigma -> indices,
+ * decode r^ for the whole latent in one step, y^ = r^ q + mu, then the N frame-specific decoders.
+ * frames_out: [N][H][W][3] doubles in [0, 1]; yhat_out (optional): [Hy][Wy][Cy]. */
+int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H, int W, const float* wts,
+                     double* frames_out, double* yhat_out) {
+    int Hy, Wy, Hz, Wz, Cy, Cz;
+    if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz)) return ORC_ERR_ARG;
+    size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
+    if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] != 1) return ORC_ERR_CORRUPT;
+    if (bits[5] != arch || bits[6] != N || get16(bits + 8) != (uint32_t)W || get16(bits + 10) != (uint32_t)H)
+        return ORC_ERR_ARG;
+    int qp = bits[7];
+    int K = (int)get32(bits + 12), Kz = (int)get32(bits + 16);
+    size_t ny = (size_t)Hy * Wy * Cy, nz = (size_t)Hz * Wz * Cz;
+    if (qp > 63 || K < 1 || Kz != ((size_t)K < nz ? K : (int)nz)) return ORC_ERR_CORRUPT;
+    for (int c = 0; c < Cz; c++)
+        if (bits[20 + c] >= NBINS) return ORC_ERR_CORRUPT;
+    uint32_t* freq = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * NSYM);
+    uint32_t* cum = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * (NSYM + 1));
+    orc_build_tables(freq, cum);
+    int16_t* zhat = (int16_t*)malloc(2 * nz);
+    uint8_t* zidx = (uint8_t*)malloc(nz);
+    for (size_t i = 0; i < nz; i++) zidx[i] = bits[20 + i % Cz];
+    double* mu = dalloc(ny);
+    double* ls = dalloc(ny);
+    uint8_t* idx = (uint8_t*)malloc(ny);
+    int16_t* rhat = (int16_t*)malloc(2 * ny);
+    double* yhat = dalloc(ny);
+    size_t used1 = 0, used2 = 0;
+    int rc = orc_rans_decode(bits + hdr, nbytes - hdr, zidx, nz, Kz, freq, cum, NSYM, RMAX, zhat, &used1);
+    if (rc) goto done;
+    orc_hyper_synthesis(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls);
+    orc_scale_index(ls, ny, qp, idx);
+    rc = orc_rans_decode(bits + hdr + used1, nbytes - hdr - used1, idx, ny, K, freq, cum, NSYM, RMAX, rhat, &used2);
+    if (rc) goto done;
+    if (hdr + used1 + used2 != nbytes) { rc = ORC_ERR_CORRUPT; goto done; }
+    {
+        double q = orc_qstep(qp);
+        for (size_t i = 0; i < ny; i++) yhat[i] = rhat[i] * q + mu[i];
+    }
+    if (yhat_out) memcpy(yhat_out, yhat, sizeof(double) * ny);
+    if (frames_out) orc_synthesis(arch, N, yhat, Hy, Wy, H, W, wts, frames_out);
+done:
+    free(freq); free(cum); free(zhat); free(zidx); free(mu); free(ls); free(idx); free(rhat); free(yhat);
+    return rc;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

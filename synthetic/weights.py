@@ -1,0 +1,67 @@
+"""Random-init weights for the plain chunk codec, as one flat float32 blob.
+
+Blob layout (what ``ufvc_create`` and the oracle both read): the layers below in order; for each layer
+its kernel as float32 [Cout][k][k][Cin] (NHWC-friendly, input channel fastest), then its bias
+float32 [Cout].  Kernels are drawn N(0, 2/fan_in) with fan_in = k*k*Cin; biases N(0, bias_std^2).
+
+Layer list for chunk length N (widths per architecture in ``ARCHS``; e0..e2 = analysis widths,
+Cy = latent channels, Cz = hyper-latent channels, Cd1/Cd2 = decoder widths):
+
+    A1 (e0, 3, 3N)   A2 (e1, 3, e0)   A3 (e2, 3, e1)   Xa (e2, 3, e2)   Xb (e2, 1, e2)   A4 (Cy, 3, e2)
+    H1 (Cz, 3, Cy)   H2 (Cz, 3, Cz)
+    S1 (4Cz, 3, Cz)  S2 (4Cz, 3, Cz)  S3 (2Cy, 1, Cz)
+    then for each frame position f = 0..N-1:
+    D0 (4Cd1, 3, Cy) R1a (Cd1, 3, Cd1) R1b (Cd1, 3, Cd1) U1 (4Cd2, 3, Cd1)
+    R2a (Cd2, 3, Cd2) R2b (Cd2, 3, Cd2) U2 (4Cd2, 3, Cd2) U3 (12, 3, Cd2)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# arch 0: the tiny 64x64 workload; arch 1: the 1080p-family workload (720p, 480p and 4K use it too).
+ARCHS = {
+    0: dict(enc=(64, 96, 128), cy=128, cz=64, cd1=128, cd2=64),
+    1: dict(enc=(64, 128, 192), cy=256, cz=128, cd1=128, cd2=64),
+}
+
+
+def layer_table(arch: int, n_frames: int) -> list[tuple[str, int, int, int]]:
+    """[(name, Cout, k, Cin)] in blob order."""
+    a = ARCHS[arch]
+    e0, e1, e2 = a["enc"]
+    cy, cz, cd1, cd2 = a["cy"], a["cz"], a["cd1"], a["cd2"]
+    t = [("A1", e0, 3, 3 * n_frames), ("A2", e1, 3, e0), ("A3", e2, 3, e1),
+         ("Xa", e2, 3, e2), ("Xb", e2, 1, e2), ("A4", cy, 3, e2),
+         ("H1", cz, 3, cy), ("H2", cz, 3, cz),
+         ("S1", 4 * cz, 3, cz), ("S2", 4 * cz, 3, cz), ("S3", 2 * cy, 1, cz)]
+    for f in range(n_frames):
+        t += [(f"D0.{f}", 4 * cd1, 3, cy), (f"R1a.{f}", cd1, 3, cd1), (f"R1b.{f}", cd1, 3, cd1),
+              (f"U1.{f}", 4 * cd2, 3, cd1), (f"R2a.{f}", cd2, 3, cd2), (f"R2b.{f}", cd2, 3, cd2),
+              (f"U2.{f}", 4 * cd2, 3, cd2), (f"U3.{f}", 12, 3, cd2)]
+    return t
+
+
+def weight_count(arch: int, n_frames: int) -> int:
+    return sum(co * k * k * ci + co for _, co, k, ci in layer_table(arch, n_frames))
+
+
+def draw_weights(arch: int, n_frames: int, seed: int = 0, bias_std: float = 0.01) -> np.ndarray:
+    """Flat float32 blob (see module docstring)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, co, k, ci in layer_table(arch, n_frames):
+        fan_in = k * k * ci
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
+        parts.append(rng.normal(0.0, bias_std, size=co).astype(np.float32))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def split_weights(blob: np.ndarray, arch: int, n_frames: int) -> dict[str, tuple[np.ndarray, np.ndarray]]:
+    """name -> (kernel [Cout][k][k][Cin], bias [Cout]) views into the blob (for tests)."""
+    out, off = {}, 0
+    for name, co, k, ci in layer_table(arch, n_frames):
+        n = co * k * k * ci
+        out[name] = (blob[off:off + n].reshape(co, k, k, ci), blob[off + n:off + n + co])
+        off += n + co
+    assert off == blob.size
+    return out
