@@ -1,0 +1,185 @@
+/*
+ * ufvc.h -- C ABI of the B300 (sm_103a) chunk-coding library libufvc.so.
+ *
+ * The library codes one chunk of N video frames through ONE shared latent, following the paper
+ * "Ultra-Fast Neural Video Compression" (DCVC-UF):
+ *   Sec. 3.1, Fig. 3  -- chunk X_i = {x_i,0..x_i,N-1} -> patch embedding -> chunk encoder with
+ *                        cross-frame interaction -> latent y_i -> quantised y^_i -> bit-stream; qp_i
+ *                        is the rate input;
+ *   Sec. 3.2          -- N frame-specific decoders reconstruct all frames of the chunk in parallel;
+ *   Sec. 3.4, Fig. 4c -- r^ = round(y - mu) is entropy coded with the scale sigma only, y^ = r^ + mu,
+ *                        and the scales of ALL latent elements come from one parameter-estimation
+ *                        pass, so the whole latent is entropy coded in a single step.
+ * The module internals are figure-only in the paper; this library implements the plain reading
+ * (strided 3x3 convolutions + GELU, one residual cross-frame interaction block, a hyperprior whose
+ * synthesis outputs (mu, log sigma), and conv / residual / pixel-shuffle decoders), a 64-bin scale
+ * index into fixed 16-bit integer Gaussian CDF tables, and K interleaved rANS lanes.
+ *
+ * Conventions (all entry points):
+ *   - Every buffer is owned by the caller.  "d_" pointers are CUDA device pointers on the context's
+ *     device; "h_" pointers are host pointers.  The library keeps no pointer after a call returns,
+ *     except that asynchronous work on the given stream reads / writes the buffers until it completes.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  Calls are
+ *     stream-ordered and asynchronous unless documented otherwise.
+ *   - Argument errors are detected on the host and returned before any launch (UFVC_ERR_ARG).
+ *     Errors found on the device (corrupt bit-stream, too-small capacity) set a status word in the
+ *     context; ufvc_sync_status() synchronises the stream and returns (and clears) it.
+ *   - A context is not thread-safe: use one per host thread, or lock around calls.
+ *   - Layouts are NHWC with the channel fastest.  Frames are uint8 RGB [N][H][W][3].
+ */
+#ifndef UFVC_H
+#define UFVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ufvc_ctx ufvc_ctx;
+typedef struct ufvc_server ufvc_server;
+
+typedef enum {
+    UFVC_OK = 0,
+    UFVC_ERR_ARG = 1,          /* invalid argument (checked on the host, nothing launched) */
+    UFVC_ERR_CAPACITY = 2,     /* output buffer too small for the bit-stream */
+    UFVC_ERR_CORRUPT = 3,      /* bit-stream header / lane counts / lane final state inconsistent */
+    UFVC_ERR_OOM = 4,          /* device allocation failed */
+    UFVC_ERR_CUDA = 5,         /* a CUDA call failed (see ufvc_last_error) */
+    UFVC_ERR_TIMEOUT = 6,      /* a bounded device or host wait gave up */
+    UFVC_ERR_UNSUPPORTED = 7,  /* configuration not supported on this device */
+    UFVC_PENDING = 8           /* serving: request not finished yet */
+} ufvc_status;
+
+typedef enum {
+    UFVC_FP32 = 0,  /* every convolution in FP32 on CUDA cores (deterministic) */
+    UFVC_BF16 = 1,  /* analysis / hyper-analysis / decoder convolutions: BF16 operands on tcgen05
+                       tensor cores, FP32 accumulation in TMEM; entropy-parameter path stays FP32 */
+    UFVC_FP8 = 2    /* as BF16 but E4M3 operands with per-output-channel weight scales and one
+                       per-layer activation scale */
+} ufvc_precision;
+
+typedef struct {
+    int arch;        /* 0: tiny widths (analysis 64/96/128, Cy=128, Cz=64);
+                        1: 1080p-family widths (analysis 64/128/192, Cy=256, Cz=128) */
+    int chunk_len;   /* N, frames per chunk (1..16); N frame-specific decoders */
+    int lanes;       /* K, interleaved rANS lanes of the latent section (1..65536) */
+    int precision;   /* ufvc_precision */
+    int device;      /* CUDA device ordinal */
+} ufvc_config;
+
+/* Number of float32 weights the architecture needs (the blob layout is documented at
+ * ufvc_create). */
+size_t ufvc_weight_count(int arch, int chunk_len);
+
+/* Create a context: copies the weights to the device, builds the CDF and threshold tables on the
+ * host in FP64 and uploads them.  `weights` is a host float32 blob: for each layer in the order
+ *   A1 A2 A3 Xa Xb A4 H1 H2 S1 S2 S3, then for f = 0..N-1: D0 R1a R1b U1 R2a R2b U2 U3,
+ * the kernel [Cout][k][k][Cin] followed by the bias [Cout] (shapes: see ufvc_layer_shape).
+ * Returns UFVC_ERR_ARG if n_weights != ufvc_weight_count(arch, chunk_len). */
+ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights, size_t n_weights, ufvc_ctx** out);
+void ufvc_destroy(ufvc_ctx* ctx);
+
+/* Shape (Cout, k, Cin) of blob layer l (0-based, order above). */
+ufvc_status ufvc_layer_shape(int arch, int chunk_len, int layer, int* cout, int* k, int* cin);
+
+/* Latent geometry of a W x H chunk: frames are replicate-padded to multiples of 16; the latent is
+ * [Hy][Wy][Cy] with Hy = ceil(H/16), Wy = ceil(W/16); the hyper-latent [Hz][Wz][Cz] with
+ * Hz = ceil(Hy/4), Wz = ceil(Wy/4). */
+ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy, int* Wy, int* Hz, int* Wz, int* Cy,
+                             int* Cz);
+
+/* Upper bound of the bit-stream size of one W x H chunk (header + two sections, at most one 16-bit
+ * word per symbol plus two flush words and one 32-bit count per lane). */
+size_t ufvc_max_bitstream_bytes(const ufvc_ctx* ctx, int width, int height);
+
+/* Encode one chunk (Sec. 3.1 / 3.4).  d_frames: device uint8 [N][H][W][3], N = chunk_len.
+ * qp in [0, 63] sets the quantisation step q = 2^((qp-32)/8).  The bit-stream is written to d_bits
+ * (capacity bytes) and its size to *d_nbytes (device uint64).  If the stream would not fit,
+ * nothing past `capacity` is written and the status word becomes UFVC_ERR_CAPACITY.
+ * Bit-stream layout: "UFVC", u8 version=1, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K, u32 Kz,
+ * Cz bytes of per-channel hyper-latent scale indices, zero padding to 4 bytes; then the z^ section
+ * (Kz = min(K, #z^) lanes) and the y^ section (K lanes), each = K u32 lane word counts followed by
+ * the lane streams (u16 words in decoding order), zero-padded to 4 bytes.  Little-endian. */
+ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height,
+                              int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, void* stream);
+
+/* Decode one chunk: one entropy-decoding step for z^, the hyper-synthesis (mu, log sigma for every
+ * latent element in one pass), one entropy-decoding step for the whole latent, y^ = r^ q + mu, then
+ * the N frame-specific decoders (Sec. 3.2) in parallel.  nbytes = the stream size (the number the
+ * encoder wrote); n_frames / width / height must match the header (else status UFVC_ERR_ARG on the
+ * device).  d_frames: device uint8 [N][H][W][3], x^ = clamp(0.5 + o, 0, 1) scaled by 255 and rounded
+ * half-to-even.  The _f32 variant writes x^ in [0, 1] as float32 instead. */
+ufvc_status ufvc_decode_chunk(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, uint8_t* d_frames,
+                              int n_frames, int width, int height, void* stream);
+ufvc_status ufvc_decode_chunk_f32(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, float* d_frames,
+                                  int n_frames, int width, int height, void* stream);
+
+/* Host-buffer variants (the call a user without device buffers makes): copy h_frames / h_bits to a
+ * context-owned device staging area, run the chunk on `stream`, copy the result back, synchronise.
+ * *nbytes receives the stream size.  Return the device status of the call. */
+ufvc_status ufvc_encode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_frames, int n_frames, int width, int height,
+                                   int qp, uint8_t* h_bits, size_t capacity, size_t* nbytes, void* stream);
+ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bits, size_t nbytes, uint8_t* h_frames,
+                                   int n_frames, int width, int height, void* stream);
+
+/* Synchronise `stream`, then return and clear the device status word (UFVC_OK if no device-side
+ * error was recorded since the last call). */
+ufvc_status ufvc_sync_status(ufvc_ctx* ctx, void* stream);
+
+/* ---- stage entry points (tests and benchmarks call these; same kernels as the chunk calls) ---- */
+
+/* Encoder front half: d_y float32 [Hy][Wy][Cy] (latent before quantisation), d_zhat int16
+ * [Hz][Wz][Cz] (z^ = clamp(rint(z), -255, 255)), d_iz uint8 [Cz] (per-channel z^ scale index),
+ * d_mu / d_logsig float32 [Hy][Wy][Cy], d_rhat int16 and d_idx uint8 [Hy][Wy][Cy].  Any output
+ * pointer may be NULL. */
+ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int qp, float* d_y,
+                               int16_t* d_zhat, uint8_t* d_iz, float* d_mu, float* d_logsig, int16_t* d_rhat,
+                               uint8_t* d_idx, void* stream);
+
+/* Hyper-synthesis alone (single-step parameter estimation, Sec. 3.4), deterministic FP32 with a fixed
+ * reduction order: d_zhat int16 [Hz][Wz][Cz] -> d_mu, d_logsig float32 [Hy][Wy][Cy]. */
+ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat, int Hz, int Wz, int Hy, int Wy,
+                                 float* d_mu, float* d_logsig, void* stream);
+
+/* Quantise + scale index (Sec. 3.4): r^ = clamp(rint((y - mu) / q), -255, 255) (FP32, no FMA
+ * contraction), idx = #{k : thr_qp[k] < log sigma}.  n elements, all device buffers. */
+ufvc_status ufvc_quantize(ufvc_ctx* ctx, const float* d_y, const float* d_mu, const float* d_logsig, size_t n,
+                          int qp, int16_t* d_rhat, uint8_t* d_idx, void* stream);
+
+/* Frame-specific synthesis (Sec. 3.2) from a dequantised latent d_yhat float32 [Hy][Wy][Cy] to
+ * d_frames float32 [N][H][W][3] in [0, 1]. */
+ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int width, int height, float* d_frames,
+                            void* stream);
+
+/* One rANS section (the single consolidated coding step, Sec. 3.4) over n symbols with the context's
+ * 64 Gaussian tables: symbol i in [-255, 255] uses table d_idx[i] (0..63) and goes to lane i mod
+ * lanes.  Encode writes the section (lanes u32 word counts + lane streams, zero-padded to 4 bytes)
+ * to d_out and its byte size to *d_nbytes; decode reads a section of at most `nbytes` bytes.
+ * Errors (capacity / corrupt) go to the status word. */
+ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t* d_idx, size_t n, int lanes,
+                             uint8_t* d_out, size_t capacity, uint64_t* d_nbytes, void* stream);
+ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, const uint8_t* d_idx, size_t n,
+                             int lanes, int16_t* d_sym, void* stream);
+
+/* Host copies of the tables the context uses: freq / cum uint32 [64][511] / [64][512] (may be NULL),
+ * thr float32 [63] for rate qp (may be NULL).  No device work.  ctx may be NULL: the tables are then
+ * built on the host (FP64) without touching any device. */
+ufvc_status ufvc_get_tables(const ufvc_ctx* ctx, uint32_t* freq, uint32_t* cum, int qp, float* thr);
+
+/* Per-stage device timing of the chunk calls, measured with CUDA events on the calling stream.
+ * enable != 0 turns recording on (and discards unread entries).  Entries accumulate over calls;
+ * ufvc_get_profile waits for them, copies up to `max`: names (NUL-terminated, 32 bytes each),
+ * milliseconds and kernel launches per stage, returns the count in *count, and starts a new list. */
+ufvc_status ufvc_set_profiling(ufvc_ctx* ctx, int enable);
+ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, int* launches, int max, int* count);
+
+/* Human-readable description of the last error on this context ("" if none). */
+const char* ufvc_last_error(const ufvc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UFVC_H */

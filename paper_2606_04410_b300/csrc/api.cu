@@ -1,0 +1,771 @@
+// C-ABI entry points of libufvc: context, per-shape plans, and the chunk encode / decode pipelines.
+//
+// Encode (Sec. 3.1, 3.4): pack -> analysis A1..A3, cross-frame interaction X, A4 -> y; hyper-analysis
+// H1, H2 -> z; z^ and its per-channel index; hyper-synthesis S1..S3 -> (mu, log sigma) for every
+// latent element in ONE pass; r^ and scale indices; both rANS sections in one launch; header and
+// lane layout.  Decode: header + lane counts; z^ section; the same hyper-synthesis; indices; the whole
+// latent in ONE decoding step fused with y^ = r^ q + mu; the N frame-specific decoders (Sec. 3.2) as
+// grouped launches (group = frame position, each with its own weights).
+#include "ufvc_internal.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+using namespace ufvc;
+
+namespace {
+
+struct LayerW {
+    int cout = 0, k = 0, cin = 0, cin_p = 0, groups = 1;
+    float* w = nullptr;  // FP32 SIMT layout [k*k][cin_p][cout] per group, groups back to back
+    float* b = nullptr;  // [cout] per group
+    long long w_gs = 0, b_gs = 0;
+};
+
+struct Plan {
+    int W = 0, H = 0, Hp = 0, Wp = 0, C0p = 0;
+    int h1 = 0, w1 = 0, h2 = 0, w2 = 0, h3 = 0, w3 = 0, Hy = 0, Wy = 0, hh = 0, wh = 0, Hz = 0, Wz = 0;
+    size_t ny = 0, nz = 0, hdr = 0;
+    int Kz = 0, cap_z = 0, cap_y = 0;
+    // encoder buffers
+    float *x = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *xt = nullptr, *y = nullptr, *hb = nullptr,
+          *z = nullptr, *zf = nullptr, *s1 = nullptr, *s2 = nullptr, *mu = nullptr, *ls = nullptr;
+    int16_t *zhat = nullptr, *rhat = nullptr;
+    uint8_t *iz = nullptr, *idx = nullptr;
+    uint16_t *scr_z = nullptr, *scr_y = nullptr;
+    uint32_t *cnt_z = nullptr, *cnt_y = nullptr;
+    uint64_t *off_ws = nullptr, *zthr = nullptr;
+    // decoder buffers
+    int16_t* dzhat = nullptr;
+    uint8_t *diz = nullptr, *didx = nullptr;
+    int* qp_dev = nullptr;
+    uint64_t *lo_z = nullptr, *lo_y = nullptr, *next_z = nullptr, *next_y = nullptr;
+    uint32_t *lw_z = nullptr, *lw_y = nullptr;
+    float *dzf = nullptr, *ds1 = nullptr, *ds2 = nullptr, *dmu = nullptr, *dls = nullptr, *yhat = nullptr;
+    float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
+    bool enc_ready = false, dec_ready = false;
+    std::vector<void*> allocs;
+};
+
+struct ProfEntry {
+    char name[32];
+    cudaEvent_t a = nullptr, b = nullptr;
+    int launches = 0;
+};
+
+}  // namespace
+
+struct ufvc_ctx {
+    ufvc_config cfg{};
+    Arch arch{};
+    int N = 0;
+    HostTables tabs;
+    uint32_t* d_packed = nullptr;
+    float *d_thr = nullptr, *d_qstep = nullptr, *d_qinv = nullptr;
+    int* d_status = nullptr;
+    LayerW enc[L_NENC];
+    LayerW dec[D_NDEC];
+    std::map<long long, Plan*> plans;
+    std::string err;
+    // standalone rANS scratch
+    uint16_t* r_scr = nullptr;
+    uint32_t* r_cnt = nullptr;
+    uint64_t* r_off = nullptr;
+    size_t r_scr_words = 0, r_lanes = 0;
+    // host-API staging
+    uint8_t *st_frames = nullptr, *st_bits = nullptr;
+    uint64_t* st_nbytes = nullptr;
+    size_t st_frames_sz = 0, st_bits_sz = 0;
+    // profiling
+    bool prof_on = false;
+    std::vector<ProfEntry> prof;
+    size_t prof_n = 0;
+};
+
+// ------------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------------
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                         \
+            return e_ == cudaErrorMemoryAllocation ? UFVC_ERR_OOM : UFVC_ERR_CUDA;                 \
+        }                                                                                          \
+    } while (0)
+
+static ufvc_status fail(ufvc_ctx* ctx, ufvc_status s, const char* msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+template <class T>
+static ufvc_status dalloc(ufvc_ctx* ctx, Plan* p, T** ptr, size_t count) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, count ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        ctx->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return UFVC_ERR_OOM;
+    }
+    if (p) p->allocs.push_back(v);
+    *ptr = (T*)v;
+    return UFVC_OK;
+}
+
+static void prof_begin(ufvc_ctx* ctx, const char* name, cudaStream_t s) {
+    if (!ctx->prof_on) return;
+    if (ctx->prof_n == ctx->prof.size()) {
+        ProfEntry e;
+        cudaEventCreate(&e.a);
+        cudaEventCreate(&e.b);
+        ctx->prof.push_back(e);
+    }
+    ProfEntry& e = ctx->prof[ctx->prof_n];
+    snprintf(e.name, sizeof(e.name), "%s", name);
+    e.launches = 0;
+    cudaEventRecord(e.a, s);
+}
+
+static void prof_end(ufvc_ctx* ctx, cudaStream_t s, int launches) {
+    if (!ctx->prof_on) return;
+    ProfEntry& e = ctx->prof[ctx->prof_n++];
+    e.launches = launches;
+    cudaEventRecord(e.b, s);
+}
+
+static int ceil_div(int a, int b) { return (a + b - 1) / b; }
+static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1; }
+
+static void conv(ufvc_ctx* ctx, const LayerW& L, const float* in, int H, int W, int stride, int act, int mode,
+                 void* out, int out_h, int out_w, cudaStream_t s, const float* res = nullptr,
+                 float* out2 = nullptr, int split = 0, long long in_gs = 0, long long out_gs = 0,
+                 long long res_gs = 0, int groups = 1) {
+    (void)ctx;
+    ConvDesc d;
+    d.in = in; d.in_gs = in_gs; d.H = H; d.W = W; d.Cin = L.cin_p;
+    d.w = L.w; d.w_gs = L.w_gs; d.b = L.b; d.b_gs = L.b_gs;
+    d.Cout = L.cout; d.k = L.k; d.stride = stride; d.mode = mode; d.act = act;
+    d.out = out; d.out_gs = out_gs; d.out_h = out_h; d.out_w = out_w;
+    d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
+    launch_conv_simt(d, s);
+}
+
+// ------------------------------------------------------------------------------------------------
+// plans
+// ------------------------------------------------------------------------------------------------
+static void free_plan(Plan* p) {
+    for (void* v : p->allocs) cudaFree(v);
+    delete p;
+}
+
+static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out) {
+    const long long key = ((long long)W << 20) | H;
+    Plan* p;
+    auto it = ctx->plans.find(key);
+    if (it == ctx->plans.end()) {
+        p = new Plan();
+        p->W = W; p->H = H;
+        p->Hp = ceil_div(H, 16) * 16; p->Wp = ceil_div(W, 16) * 16;
+        p->C0p = ceil_div(3 * ctx->N, 16) * 16;
+        p->h1 = conv_out(p->Hp, 3, 2); p->w1 = conv_out(p->Wp, 3, 2);
+        p->h2 = conv_out(p->h1, 3, 2); p->w2 = conv_out(p->w1, 3, 2);
+        p->h3 = conv_out(p->h2, 3, 2); p->w3 = conv_out(p->w2, 3, 2);
+        p->Hy = conv_out(p->h3, 3, 2); p->Wy = conv_out(p->w3, 3, 2);
+        p->hh = conv_out(p->Hy, 3, 2); p->wh = conv_out(p->Wy, 3, 2);
+        p->Hz = conv_out(p->hh, 3, 2); p->Wz = conv_out(p->wh, 3, 2);
+        p->ny = (size_t)p->Hy * p->Wy * ctx->arch.cy;
+        p->nz = (size_t)p->Hz * p->Wz * ctx->arch.cz;
+        p->Kz = (size_t)ctx->cfg.lanes < p->nz ? ctx->cfg.lanes : (int)p->nz;
+        p->cap_z = (int)(p->nz / p->Kz + 3);
+        p->cap_y = (int)(p->ny / ctx->cfg.lanes + 3);
+        p->hdr = (20 + (size_t)ctx->arch.cz + 3) & ~(size_t)3;
+        ctx->plans[key] = p;
+    } else {
+        p = it->second;
+    }
+    const Arch& a = ctx->arch;
+    const int N = ctx->N, K = ctx->cfg.lanes;
+    ufvc_status st = UFVC_OK;
+#define AL(ptr, n) if ((st = dalloc(ctx, p, &(ptr), (n))) != UFVC_OK) return st
+    if (!for_decode && !p->enc_ready) {
+        AL(p->x, (size_t)p->Hp * p->Wp * p->C0p);
+        AL(p->a1, (size_t)p->h1 * p->w1 * a.e0);
+        AL(p->a2, (size_t)p->h2 * p->w2 * a.e1);
+        AL(p->a3, (size_t)p->h3 * p->w3 * a.e2);
+        AL(p->xt, (size_t)p->h3 * p->w3 * a.e2);
+        AL(p->y, p->ny);
+        AL(p->hb, (size_t)p->hh * p->wh * a.cz);
+        AL(p->z, p->nz);
+        AL(p->zf, p->nz);
+        AL(p->s1, (size_t)4 * p->Hz * p->Wz * a.cz);
+        AL(p->s2, (size_t)p->Hy * p->Wy * a.cz);
+        AL(p->mu, p->ny);
+        AL(p->ls, p->ny);
+        AL(p->zhat, p->nz);
+        AL(p->rhat, p->ny);
+        AL(p->iz, (size_t)a.cz);
+        AL(p->idx, p->ny);
+        AL(p->scr_z, (size_t)p->Kz * p->cap_z);
+        AL(p->scr_y, (size_t)K * p->cap_y);
+        AL(p->cnt_z, (size_t)p->Kz);
+        AL(p->cnt_y, (size_t)K);
+        AL(p->off_ws, (size_t)p->Kz + K);
+        AL(p->zthr, (size_t)kBins - 1);
+        // z^ RMS thresholds for this shape: T_k = floor(npos * exp(2 t_k)), FP64 on the host
+        std::vector<uint64_t> zt(kBins - 1);
+        const double npos = (double)p->Hz * p->Wz;
+        for (int k = 0; k < kBins - 1; ++k) zt[k] = (uint64_t)std::floor(npos * std::exp(2.0 * ctx->tabs.log_thr[k]));
+        CK(cudaMemcpy(p->zthr, zt.data(), zt.size() * 8, cudaMemcpyHostToDevice));
+        p->enc_ready = true;
+    }
+    if (for_decode && !p->dec_ready) {
+        AL(p->dzhat, p->nz);
+        AL(p->diz, (size_t)a.cz);
+        AL(p->didx, p->ny);
+        AL(p->qp_dev, 1);
+        AL(p->lo_z, (size_t)p->Kz);
+        AL(p->lo_y, (size_t)K);
+        AL(p->lw_z, (size_t)p->Kz);
+        AL(p->lw_y, (size_t)K);
+        AL(p->next_z, 1);
+        AL(p->next_y, 1);
+        AL(p->dzf, p->nz);
+        AL(p->ds1, (size_t)4 * p->Hz * p->Wz * a.cz);
+        AL(p->ds2, (size_t)p->Hy * p->Wy * a.cz);
+        AL(p->dmu, p->ny);
+        AL(p->dls, p->ny);
+        AL(p->yhat, p->ny);
+        const size_t n1 = (size_t)N * 4 * p->Hy * p->Wy * a.cd1;
+        const size_t n2 = (size_t)N * 16 * p->Hy * p->Wy * a.cd2;
+        const size_t n3 = (size_t)N * 64 * p->Hy * p->Wy * a.cd2;
+        AL(p->bufA, n1);
+        AL(p->bufT, n1);
+        AL(p->bufB, n2);
+        AL(p->bufT2, n2);
+        AL(p->bufC, n3);
+        p->dec_ready = true;
+    }
+#undef AL
+    *out = p;
+    return UFVC_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// create / destroy
+// ------------------------------------------------------------------------------------------------
+extern "C" size_t ufvc_weight_count(int arch, int chunk_len) { return weight_count(arch, chunk_len); }
+
+extern "C" ufvc_status ufvc_layer_shape(int arch, int chunk_len, int layer, int* cout, int* k, int* cin) {
+    return layer_shape(arch, chunk_len, layer, cout, k, cin) ? UFVC_OK : UFVC_ERR_ARG;
+}
+
+extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy, int* Wy, int* Hz, int* Wz, int* Cy,
+                                        int* Cz) {
+    Arch a;
+    if (!get_arch(arch, &a) || width < 1 || height < 1) return UFVC_ERR_ARG;
+    const int hy = ceil_div(height, 16), wy = ceil_div(width, 16);
+    if (Hy) *Hy = hy;
+    if (Wy) *Wy = wy;
+    if (Hz) *Hz = ceil_div(hy, 4);
+    if (Wz) *Wz = ceil_div(wy, 4);
+    if (Cy) *Cy = a.cy;
+    if (Cz) *Cz = a.cz;
+    return UFVC_OK;
+}
+
+static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups) {
+    int co, k, ci;
+    layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
+    L.cout = co; L.k = k; L.cin = ci; L.cin_p = ceil_div(ci, 16) * 16; L.groups = groups;
+    L.w_gs = (long long)k * k * L.cin_p * co;
+    L.b_gs = co;
+    std::vector<float> w((size_t)groups * L.w_gs, 0.f), b((size_t)groups * co);
+    for (int g = 0; g < groups; ++g) {
+        const int l = first + g * D_NDEC;
+        const float* src = blob + offs[l];
+        for (int o = 0; o < co; ++o)
+            for (int t = 0; t < k * k; ++t)
+                for (int i = 0; i < ci; ++i)
+                    w[g * L.w_gs + ((size_t)t * L.cin_p + i) * co + o] = src[((size_t)o * k * k + t) * ci + i];
+        for (int o = 0; o < co; ++o) b[(size_t)g * co + o] = src[(size_t)co * k * k * ci + o];
+    }
+    ufvc_status st;
+    if ((st = dalloc(ctx, nullptr, &L.w, w.size())) != UFVC_OK) return st;
+    if ((st = dalloc(ctx, nullptr, &L.b, b.size())) != UFVC_OK) return st;
+    CK(cudaMemcpy(L.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.b, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+    return UFVC_OK;
+}
+
+extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->cfg.device);
+    cudaDeviceSynchronize();
+    for (auto& kv : ctx->plans) free_plan(kv.second);
+    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); }
+    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); }
+    cudaFree(ctx->d_packed); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
+    cudaFree(ctx->st_frames); cudaFree(ctx->st_bits); cudaFree(ctx->st_nbytes);
+    for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    delete ctx;
+}
+
+extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights, size_t n_weights, ufvc_ctx** out) {
+    if (!cfg || !weights || !out) return UFVC_ERR_ARG;
+    Arch a;
+    if (!get_arch(cfg->arch, &a) || cfg->chunk_len < 1 || cfg->chunk_len > 16 || cfg->lanes < 1 ||
+        cfg->lanes > 65536 || cfg->precision < 0 || cfg->precision > 2)
+        return UFVC_ERR_ARG;
+    if (n_weights != weight_count(cfg->arch, cfg->chunk_len)) return UFVC_ERR_ARG;
+    if (cfg->precision != UFVC_FP32) return UFVC_ERR_UNSUPPORTED;
+    ufvc_ctx* ctx = new ufvc_ctx();
+    ctx->cfg = *cfg;
+    ctx->arch = a;
+    ctx->N = cfg->chunk_len;
+    auto bail = [&](ufvc_status s) { ufvc_destroy(ctx); return s; };
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(UFVC_ERR_CUDA);
+    build_host_tables(ctx->tabs);
+    ufvc_status st;
+    if ((st = dalloc(ctx, nullptr, &ctx->d_packed, ctx->tabs.packed.size())) != UFVC_OK) return bail(st);
+    if ((st = dalloc(ctx, nullptr, &ctx->d_thr, ctx->tabs.thr.size())) != UFVC_OK) return bail(st);
+    if ((st = dalloc(ctx, nullptr, &ctx->d_qstep, 64)) != UFVC_OK) return bail(st);
+    if ((st = dalloc(ctx, nullptr, &ctx->d_qinv, 64)) != UFVC_OK) return bail(st);
+    if ((st = dalloc(ctx, nullptr, &ctx->d_status, 1)) != UFVC_OK) return bail(st);
+    if (cudaMemcpy(ctx->d_packed, ctx->tabs.packed.data(), ctx->tabs.packed.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_thr, ctx->tabs.thr.data(), ctx->tabs.thr.size() * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_qstep, ctx->tabs.qstep.data(), 64 * 4, cudaMemcpyHostToDevice) ||
+        cudaMemcpy(ctx->d_qinv, ctx->tabs.qinv.data(), 64 * 4, cudaMemcpyHostToDevice) ||
+        cudaMemset(ctx->d_status, 0, 4))
+        return bail(UFVC_ERR_CUDA);
+    // weight blob offsets
+    const int nl = L_NENC + D_NDEC * ctx->N;
+    std::vector<size_t> offs(nl);
+    size_t off = 0;
+    for (int l = 0; l < nl; ++l) {
+        int co, k, ci;
+        layer_shape(cfg->arch, ctx->N, l, &co, &k, &ci);
+        offs[l] = off;
+        off += (size_t)co * k * k * ci + co;
+    }
+    for (int l = 0; l < L_NENC; ++l)
+        if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1)) != UFVC_OK) return bail(st);
+    for (int j = 0; j < D_NDEC; ++j)
+        if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N)) != UFVC_OK) return bail(st);
+    *out = ctx;
+    return UFVC_OK;
+}
+
+extern "C" const char* ufvc_last_error(const ufvc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" size_t ufvc_max_bitstream_bytes(const ufvc_ctx* ctx, int width, int height) {
+    if (!ctx || width < 1 || height < 1) return 0;
+    const int hy = ceil_div(height, 16), wy = ceil_div(width, 16);
+    const size_t ny = (size_t)hy * wy * ctx->arch.cy;
+    const size_t nz = (size_t)ceil_div(hy, 4) * ceil_div(wy, 4) * ctx->arch.cz;
+    const size_t K = ctx->cfg.lanes, Kz = K < nz ? K : nz;
+    const size_t hdr = (20 + (size_t)ctx->arch.cz + 3) & ~(size_t)3;
+    return hdr + (4 * Kz + 2 * (nz + 2 * Kz) + 3) + (4 * K + 2 * (ny + 2 * K) + 3);
+}
+
+extern "C" ufvc_status ufvc_sync_status(ufvc_ctx* ctx, void* stream) {
+    if (!ctx) return UFVC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s));
+    int v = 0;
+    CK(cudaMemcpy(&v, ctx->d_status, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(ctx->d_status, 0, 4));
+    if (v != 0) ctx->err = "device status " + std::to_string(v);
+    return (ufvc_status)v;
+}
+
+// ------------------------------------------------------------------------------------------------
+// pipeline stages
+// ------------------------------------------------------------------------------------------------
+static bool check_shape(ufvc_ctx* ctx, int n_frames, int width, int height) {
+    return n_frames == ctx->N && width >= 1 && height >= 1 && width <= 65535 && height <= 65535;
+}
+
+// hyper-synthesis: zhat (int16) -> mu, logsig; deterministic FP32 path in every precision
+static void run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zhat, float* zf, float* s1, float* s2,
+                                float* mu, float* ls, cudaStream_t s) {
+    const Arch& a = ctx->arch;
+    prof_begin(ctx, "hyper_synthesis", s);
+    launch_i16_to_f32(zhat, p->nz, zf, s);
+    conv(ctx, ctx->enc[L_S1], zf, p->Hz, p->Wz, 1, 1, OUT_PS, s1, 2 * p->Hz, 2 * p->Wz, s);
+    conv(ctx, ctx->enc[L_S2], s1, 2 * p->Hz, 2 * p->Wz, 1, 1, OUT_PS, s2, p->Hy, p->Wy, s);  // crop
+    conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy);
+    prof_end(ctx, s, 4);
+}
+
+static void run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
+    const Arch& a = ctx->arch;
+    prof_begin(ctx, "pack", s);
+    launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "analysis", s);
+    conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s);
+    conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s);
+    conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s);
+    conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s);
+    conv(ctx, ctx->enc[L_XB], p->xt, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3);  // residual, in place
+    conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s);
+    prof_end(ctx, s, 6);
+    prof_begin(ctx, "hyper_analysis", s);
+    conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s);
+    conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s);
+    launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
+    prof_end(ctx, s, 3);
+    run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s);
+    prof_begin(ctx, "quantize", s);
+    launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);
+    prof_end(ctx, s, 1);
+}
+
+static void run_decoders(ufvc_ctx* ctx, Plan* p, const float* yhat, void* frames_out, int final_mode, cudaStream_t s) {
+    const Arch& a = ctx->arch;
+    const int N = ctx->N;
+    const int h1 = 2 * p->Hy, w1 = 2 * p->Wy, h2 = 4 * p->Hy, w2 = 4 * p->Wy, h3 = 8 * p->Hy, w3 = 8 * p->Wy;
+    const long long g1 = (long long)h1 * w1 * a.cd1, g2 = (long long)h2 * w2 * a.cd2, g3 = (long long)h3 * w3 * a.cd2;
+    const long long gf = (long long)p->H * p->W * 3;
+    prof_begin(ctx, "dec.D0", s);
+    conv(ctx, ctx->dec[D_D0], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, p->bufA, h1, w1, s, nullptr, nullptr, 0, 0, g1, 0, N);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "dec.R1", s);
+    conv(ctx, ctx->dec[D_R1A], p->bufA, h1, w1, 1, 1, OUT_NHWC, p->bufT, h1, w1, s, nullptr, nullptr, 0, g1, g1, 0, N);
+    conv(ctx, ctx->dec[D_R1B], p->bufT, h1, w1, 1, 0, OUT_NHWC, p->bufA, h1, w1, s, p->bufA, nullptr, 0, g1, g1, g1, N);
+    prof_end(ctx, s, 2);
+    prof_begin(ctx, "dec.U1", s);
+    conv(ctx, ctx->dec[D_U1], p->bufA, h1, w1, 1, 1, OUT_PS, p->bufB, h2, w2, s, nullptr, nullptr, 0, g1, g2, 0, N);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "dec.R2", s);
+    conv(ctx, ctx->dec[D_R2A], p->bufB, h2, w2, 1, 1, OUT_NHWC, p->bufT2, h2, w2, s, nullptr, nullptr, 0, g2, g2, 0, N);
+    conv(ctx, ctx->dec[D_R2B], p->bufT2, h2, w2, 1, 0, OUT_NHWC, p->bufB, h2, w2, s, p->bufB, nullptr, 0, g2, g2, g2, N);
+    prof_end(ctx, s, 2);
+    prof_begin(ctx, "dec.U2", s);
+    conv(ctx, ctx->dec[D_U2], p->bufB, h2, w2, 1, 1, OUT_PS, p->bufC, h3, w3, s, nullptr, nullptr, 0, g2, g3, 0, N);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "dec.U3", s);
+    conv(ctx, ctx->dec[D_U3], p->bufC, h3, w3, 1, 0, final_mode, frames_out, p->H, p->W, s, nullptr, nullptr, 0, g3, gf,
+         0, N);
+    prof_end(ctx, s, 1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// chunk encode / decode
+// ------------------------------------------------------------------------------------------------
+extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height,
+                                         int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, void* stream) {
+    if (!ctx || !d_frames || !d_bits || !d_nbytes || !check_shape(ctx, n_frames, width, height) || qp < 0 || qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "encode_chunk: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    Plan* p;
+    ufvc_status st = get_plan(ctx, width, height, false, &p);
+    if (st) return st;
+
+    run_encoder_front(ctx, p, d_frames, qp, s);
+    prof_begin(ctx, "rans_encode", s);
+    RansSection secs[2];
+    secs[0] = RansSection{p->zhat, p->iz, ctx->arch.cz, p->nz, p->Kz, p->scr_z, p->cap_z, p->cnt_z, ctx->d_status};
+    secs[1] = RansSection{p->rhat, p->idx, 0, p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, p->cnt_y, ctx->d_status};
+    launch_rans_encode(secs, 2, ctx->d_packed, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "bitstream", s);
+    launch_write_header(d_bits, ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz, p->iz, ctx->arch.cz,
+                        capacity, ctx->d_status, s);
+    launch_rans_finalize(secs, 2, d_bits, p->hdr, capacity, d_nbytes, p->off_ws, ctx->d_status, s);
+    prof_end(ctx, s, 3);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, void* d_frames, int final_mode,
+                               int n_frames, int width, int height, void* stream) {
+    if (!ctx || !d_bits || !d_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
+        return fail(ctx, UFVC_ERR_ARG, "decode_chunk: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    Plan* p;
+    ufvc_status st = get_plan(ctx, width, height, true, &p);
+    if (st) return st;
+
+    const Arch& a = ctx->arch;
+    prof_begin(ctx, "parse", s);
+    launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, p->qp_dev,
+                        p->diz, ctx->d_status, s);
+    RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
+                     p->dzhat, nullptr, nullptr, ctx->d_qstep, p->qp_dev};
+    RansDecodeJob jy{d_bits, nbytes, 0, p->next_z, p->didx, 0, p->ny, ctx->cfg.lanes, p->lo_y, p->lw_y, p->next_y,
+                     nullptr, p->yhat, p->dmu, ctx->d_qstep, p->qp_dev};
+    launch_rans_parse(jz, ctx->d_status, s);
+    launch_rans_parse_expect(jy, nbytes, ctx->d_status, s);
+    prof_end(ctx, s, 3);
+    prof_begin(ctx, "rans_decode_z", s);
+    launch_rans_decode(jz, ctx->d_packed, ctx->d_status, s);
+    prof_end(ctx, s, 1);
+    run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s);
+    prof_begin(ctx, "scale_index", s);
+    launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "rans_decode_y", s);
+    launch_rans_decode(jy, ctx->d_packed, ctx->d_status, s);
+    prof_end(ctx, s, 1);
+    run_decoders(ctx, p, p->yhat, d_frames, final_mode, s);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_decode_chunk(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, uint8_t* d_frames,
+                                         int n_frames, int width, int height, void* stream) {
+    return decode_impl(ctx, d_bits, nbytes, d_frames, OUT_PS_FINAL_U8, n_frames, width, height, stream);
+}
+
+extern "C" ufvc_status ufvc_decode_chunk_f32(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, float* d_frames,
+                                             int n_frames, int width, int height, void* stream) {
+    return decode_impl(ctx, d_bits, nbytes, d_frames, OUT_PS_FINAL_F32, n_frames, width, height, stream);
+}
+
+// ------------------------------------------------------------------------------------------------
+// host-buffer variants
+// ------------------------------------------------------------------------------------------------
+static ufvc_status ensure_staging(ufvc_ctx* ctx, size_t frames_sz, size_t bits_sz) {
+    if (frames_sz > ctx->st_frames_sz) {
+        cudaFree(ctx->st_frames);
+        ctx->st_frames = nullptr;
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->st_frames, frames_sz);
+        if (st) return st;
+        ctx->st_frames_sz = frames_sz;
+    }
+    if (bits_sz > ctx->st_bits_sz) {
+        cudaFree(ctx->st_bits);
+        ctx->st_bits = nullptr;
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->st_bits, bits_sz);
+        if (st) return st;
+        ctx->st_bits_sz = bits_sz;
+    }
+    if (!ctx->st_nbytes) {
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->st_nbytes, 1);
+        if (st) return st;
+    }
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_encode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_frames, int n_frames, int width,
+                                              int height, int qp, uint8_t* h_bits, size_t capacity, size_t* nbytes,
+                                              void* stream) {
+    if (!ctx || !h_frames || !h_bits || !nbytes || !check_shape(ctx, n_frames, width, height))
+        return fail(ctx, UFVC_ERR_ARG, "encode_chunk_host: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    const size_t fsz = (size_t)n_frames * width * height * 3;
+    const size_t bmax = ufvc_max_bitstream_bytes(ctx, width, height);
+    ufvc_status st = ensure_staging(ctx, fsz, bmax);
+    if (st) return st;
+    CK(cudaMemcpyAsync(ctx->st_frames, h_frames, fsz, cudaMemcpyHostToDevice, s));
+    st = ufvc_encode_chunk(ctx, ctx->st_frames, n_frames, width, height, qp, ctx->st_bits, bmax, ctx->st_nbytes, stream);
+    if (st) return st;
+    uint64_t nb = 0;
+    CK(cudaMemcpyAsync(&nb, ctx->st_nbytes, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *nbytes = nb;
+    if (nb > capacity) return fail(ctx, UFVC_ERR_CAPACITY, "encode_chunk_host: capacity");
+    CK(cudaMemcpyAsync(h_bits, ctx->st_bits, nb, cudaMemcpyDeviceToHost, s));
+    return ufvc_sync_status(ctx, stream);
+}
+
+extern "C" ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bits, size_t nbytes, uint8_t* h_frames,
+                                              int n_frames, int width, int height, void* stream) {
+    if (!ctx || !h_bits || !h_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
+        return fail(ctx, UFVC_ERR_ARG, "decode_chunk_host: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    const size_t fsz = (size_t)n_frames * width * height * 3;
+    ufvc_status st = ensure_staging(ctx, fsz, nbytes);
+    if (st) return st;
+    CK(cudaMemcpyAsync(ctx->st_bits, h_bits, nbytes, cudaMemcpyHostToDevice, s));
+    st = ufvc_decode_chunk(ctx, ctx->st_bits, nbytes, ctx->st_frames, n_frames, width, height, stream);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h_frames, ctx->st_frames, fsz, cudaMemcpyDeviceToHost, s));
+    return ufvc_sync_status(ctx, stream);
+}
+
+// ------------------------------------------------------------------------------------------------
+// stage entry points
+// ------------------------------------------------------------------------------------------------
+extern "C" ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int qp,
+                                          float* d_y, int16_t* d_zhat, uint8_t* d_iz, float* d_mu, float* d_logsig,
+                                          int16_t* d_rhat, uint8_t* d_idx, void* stream) {
+    if (!ctx || !d_frames || !check_shape(ctx, ctx->N, width, height) || qp < 0 || qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "encode_stages: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    Plan* p;
+    ufvc_status st = get_plan(ctx, width, height, false, &p);
+    if (st) return st;
+
+    run_encoder_front(ctx, p, d_frames, qp, s);
+    const Arch& a = ctx->arch;
+    if (d_y) CK(cudaMemcpyAsync(d_y, p->y, p->ny * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_zhat) CK(cudaMemcpyAsync(d_zhat, p->zhat, p->nz * 2, cudaMemcpyDeviceToDevice, s));
+    if (d_iz) CK(cudaMemcpyAsync(d_iz, p->iz, a.cz, cudaMemcpyDeviceToDevice, s));
+    if (d_mu) CK(cudaMemcpyAsync(d_mu, p->mu, p->ny * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_logsig) CK(cudaMemcpyAsync(d_logsig, p->ls, p->ny * 4, cudaMemcpyDeviceToDevice, s));
+    if (d_rhat) CK(cudaMemcpyAsync(d_rhat, p->rhat, p->ny * 2, cudaMemcpyDeviceToDevice, s));
+    if (d_idx) CK(cudaMemcpyAsync(d_idx, p->idx, p->ny, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat, int Hz, int Wz, int Hy, int Wy,
+                                            float* d_mu, float* d_logsig, void* stream) {
+    if (!ctx || !d_zhat || !d_mu || !d_logsig || Hz < 1 || Wz < 1 || Hy < 1 || Wy < 1 || 4 * Hz < Hy || 4 * Wz < Wy)
+        return fail(ctx, UFVC_ERR_ARG, "hyper_synthesis: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    const Arch& a = ctx->arch;
+    Plan tmp;
+    tmp.Hz = Hz; tmp.Wz = Wz; tmp.Hy = Hy; tmp.Wy = Wy;
+    tmp.nz = (size_t)Hz * Wz * a.cz;
+    float *zf, *s1, *s2;
+    ufvc_status st;
+    if ((st = dalloc(ctx, &tmp, &zf, tmp.nz)) || (st = dalloc(ctx, &tmp, &s1, 4 * tmp.nz)) ||
+        (st = dalloc(ctx, &tmp, &s2, (size_t)Hy * Wy * a.cz))) {
+        for (void* v : tmp.allocs) cudaFree(v);
+        return st;
+    }
+
+    run_hyper_synthesis(ctx, &tmp, d_zhat, zf, s1, s2, d_mu, d_logsig, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    for (void* v : tmp.allocs) cudaFree(v);
+    if (e != cudaSuccess) return fail(ctx, UFVC_ERR_CUDA, cudaGetErrorString(e));
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_quantize(ufvc_ctx* ctx, const float* d_y, const float* d_mu, const float* d_logsig,
+                                     size_t n, int qp, int16_t* d_rhat, uint8_t* d_idx, void* stream) {
+    if (!ctx || !d_y || !d_mu || !d_logsig || !d_rhat || !d_idx || qp < 0 || qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "quantize: bad argument");
+    CK(cudaSetDevice(ctx->cfg.device));
+    if (n) launch_quantize(d_y, d_mu, d_logsig, n, ctx->d_thr, ctx->d_qinv, nullptr, qp, d_rhat, d_idx, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int width, int height, float* d_frames,
+                                       void* stream) {
+    if (!ctx || !d_yhat || !d_frames || !check_shape(ctx, ctx->N, width, height))
+        return fail(ctx, UFVC_ERR_ARG, "synthesize: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    Plan* p;
+    ufvc_status st = get_plan(ctx, width, height, true, &p);
+    if (st) return st;
+
+    run_decoders(ctx, p, d_yhat, d_frames, OUT_PS_FINAL_F32, s);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+static ufvc_status ensure_rans_scratch(ufvc_ctx* ctx, size_t words, size_t lanes) {
+    if (words > ctx->r_scr_words) {
+        cudaFree(ctx->r_scr);
+        ctx->r_scr = nullptr;
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->r_scr, words);
+        if (st) return st;
+        ctx->r_scr_words = words;
+    }
+    if (lanes > ctx->r_lanes) {
+        cudaFree(ctx->r_cnt);
+        cudaFree(ctx->r_off);
+        ctx->r_cnt = nullptr;
+        ctx->r_off = nullptr;
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->r_cnt, lanes);
+        if (st) return st;
+        st = dalloc(ctx, nullptr, &ctx->r_off, lanes);
+        if (st) return st;
+        ctx->r_lanes = lanes;
+    }
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t* d_idx, size_t n, int lanes,
+                                        uint8_t* d_out, size_t capacity, uint64_t* d_nbytes, void* stream) {
+    if (!ctx || (!d_sym && n) || (!d_idx && n) || !d_out || !d_nbytes || lanes < 1 || lanes > 65536)
+        return fail(ctx, UFVC_ERR_ARG, "rans_encode: bad argument");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int cap_lane = (int)(n / lanes + 3);
+    ufvc_status st = ensure_rans_scratch(ctx, (size_t)lanes * cap_lane, lanes);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RansSection sec{d_sym, d_idx, 0, n, lanes, ctx->r_scr, cap_lane, ctx->r_cnt, ctx->d_status};
+
+    prof_begin(ctx, "rans_encode", s);
+    launch_rans_encode(&sec, 1, ctx->d_packed, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "rans_finalize", s);
+    launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, ctx->r_off, ctx->d_status, s);
+    prof_end(ctx, s, 2);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, const uint8_t* d_idx,
+                                        size_t n, int lanes, int16_t* d_sym, void* stream) {
+    if (!ctx || !d_in || (!d_idx && n) || (!d_sym && n) || lanes < 1 || lanes > 65536)
+        return fail(ctx, UFVC_ERR_ARG, "rans_decode: bad argument");
+    CK(cudaSetDevice(ctx->cfg.device));
+    ufvc_status st = ensure_rans_scratch(ctx, 16, lanes);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    // lane offsets (u64) in r_off, lane word counts (u32) in r_cnt
+    RansDecodeJob j{d_in, nbytes, 0, nullptr, d_idx, 0, n, lanes, ctx->r_off, ctx->r_cnt, nullptr,
+                    d_sym, nullptr, nullptr, ctx->d_qstep, nullptr};
+
+    prof_begin(ctx, "rans_parse", s);
+    launch_rans_parse(j, ctx->d_status, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "rans_decode", s);
+    launch_rans_decode(j, ctx->d_packed, ctx->d_status, s);
+    prof_end(ctx, s, 1);
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_get_tables(const ufvc_ctx* ctx, uint32_t* freq, uint32_t* cum, int qp, float* thr) {
+    if (qp < 0 || qp > 63) return UFVC_ERR_ARG;
+    HostTables local;
+    if (!ctx) build_host_tables(local);  // no context: build on the host, no device involved
+    const HostTables& t = ctx ? ctx->tabs : local;
+    if (freq) memcpy(freq, t.freq.data(), t.freq.size() * 4);
+    if (cum) memcpy(cum, t.cum.data(), t.cum.size() * 4);
+    if (thr) memcpy(thr, &t.thr[qp * (kBins - 1)], (kBins - 1) * 4);
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_set_profiling(ufvc_ctx* ctx, int enable) {
+    if (!ctx) return UFVC_ERR_ARG;
+    ctx->prof_on = enable != 0;
+
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, int* launches, int max, int* count) {
+    if (!ctx || !count) return UFVC_ERR_ARG;
+    int n = 0;
+    for (size_t i = 0; i < ctx->prof_n && n < max; ++i, ++n) {
+        ProfEntry& e = ctx->prof[i];
+        CK(cudaEventSynchronize(e.b));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e.a, e.b));
+        if (names) snprintf(names + 32 * n, 32, "%s", e.name);
+        if (ms) ms[n] = t;
+        if (launches) launches[n] = e.launches;
+    }
+    *count = n;
+    ctx->prof_n = 0;  // entries accumulate over calls until read
+    return UFVC_OK;
+}

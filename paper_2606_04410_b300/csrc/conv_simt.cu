@@ -1,0 +1,186 @@
+// FP32 implicit-GEMM convolution on CUDA cores (FFMA), NHWC.
+//
+// Used for the whole FP32 path and, in every precision, for the hyper-synthesis (the single-step
+// parameter estimation of Sec. 3.4): encoder and decoder must derive bit-identical (mu, log sigma)
+// from z^, so this kernel is deterministic and batch-invariant: every output element accumulates
+// its k*k*Cin products in the same fixed order (taps row-major, then input channels ascending) with
+// explicit fmaf, whatever its tile, group or launch; there is no split-K and no atomic.
+//
+// Tile: 128 output pixels x BN output channels per 256-thread CTA, K staged 16 input channels at a
+// time through double-buffered shared memory.  Epilogue: bias, optional GELU, optional residual,
+// optional pixel shuffle x2 / crop / split of the channels into two tensors, or the final frame
+// mapping x^ = clamp(0.5 + o, 0, 1) (float or uint8).
+#include "ufvc_internal.h"
+
+namespace ufvc {
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ void store_out(const ConvDesc& d, int g, int oh, int ow, int co, float v) {
+    if (d.mode == OUT_NHWC) {
+        if (oh >= d.out_h || ow >= d.out_w) return;
+        const size_t pix = (size_t)oh * d.out_w + ow;
+        if (d.split && co >= d.split) {
+            const int c2 = d.Cout - d.split;
+            d.out2[(size_t)g * d.out_gs + pix * c2 + (co - d.split)] = v;
+            return;
+        }
+        const int C = d.split ? d.split : d.Cout;
+        const size_t o = (size_t)g * d.out_gs + pix * C + co;
+        if (d.res) v += ((const float*)d.res)[(size_t)g * d.res_gs + pix * C + co];
+        ((float*)d.out)[o] = v;
+        return;
+    }
+    const int c = co >> 2, y = 2 * oh + ((co >> 1) & 1), x = 2 * ow + (co & 1);
+    if (y >= d.out_h || x >= d.out_w) return;
+    const int C = d.Cout >> 2;
+    const size_t o = (size_t)g * d.out_gs + ((size_t)y * d.out_w + x) * C + c;
+    if (d.mode == OUT_PS) {
+        if (d.res) v += ((const float*)d.res)[(size_t)g * d.res_gs + ((size_t)y * d.out_w + x) * C + c];
+        ((float*)d.out)[o] = v;
+    } else {
+        v = fminf(fmaxf(0.5f + v, 0.0f), 1.0f);
+        if (d.mode == OUT_PS_FINAL_F32)
+            ((float*)d.out)[o] = v;
+        else
+            ((uint8_t*)d.out)[o] = (uint8_t)rintf(v * 255.0f);
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho, int Wo) {
+    constexpr int BM = 128, BK = 16;
+    constexpr int TN = BN / 4;    // threads along N, 4 output channels each
+    constexpr int TM = 256 / TN;  // threads along M
+    constexpr int PM = BM / TM;   // pixels per thread: 8 (BN = 64) or 2 (BN = 16)
+    static_assert(PM == 8 || PM == 2, "tile");
+    __shared__ __align__(16) float As[2][BK][BM + 4];  // +4: fewer bank conflicts on the transposed store
+    __shared__ __align__(16) float Bs[2][BK][BN];
+
+    const int g = blockIdx.z;
+    const float* in = (const float*)d.in + (size_t)g * d.in_gs;
+    const float* w = d.w + (size_t)g * d.w_gs;
+    const float* bias = d.b + (size_t)g * d.b_gs;
+    const int M = Ho * Wo;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x;
+    const int H = d.H, W = d.W, Cin = d.Cin, Cout = d.Cout, k = d.k, s = d.stride, p = d.k / 2;
+
+    // A loads: 2 float4 per thread (pixel q >> 2, channels 4 * (q & 3) .. +3 of the 16-channel chunk)
+    int a_oh[2], a_ow[2];
+    bool a_ok[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int m = m0 + ((tid + r * 256) >> 2);
+        a_ok[r] = m < M;
+        a_oh[r] = a_ok[r] ? m / Wo : 0;
+        a_ow[r] = a_ok[r] ? m - a_oh[r] * Wo : 0;
+    }
+    const int a_cg = tid & 3;
+    // B loads: BK * BN / 4 float4 (row = i / (BN/4), 4 output channels)
+    const bool b_act = tid < BK * BN / 4;
+    const int b_row = tid / (BN / 4), b_cg = tid % (BN / 4);
+    const int b_co = n0 + b_cg * 4;
+
+    const int nck = Cin / BK, nsteps = k * k * nck;
+    float4 ra[2], rb;
+
+    auto load_regs = [&](int step) {
+        const int tap = step / nck, c0 = (step - tap * nck) * BK;
+        const int ky = tap / k, kx = tap - ky * k;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int ih = a_oh[r] * s + ky - p, iw = a_ow[r] * s + kx - p;
+            if (a_ok[r] && ih >= 0 && ih < H && iw >= 0 && iw < W)
+                ra[r] = *reinterpret_cast<const float4*>(in + ((size_t)ih * W + iw) * Cin + c0 + a_cg * 4);
+            else
+                ra[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (b_act) {
+            if (b_co < Cout)
+                rb = *reinterpret_cast<const float4*>(w + ((size_t)tap * Cin + c0 + b_row) * Cout + b_co);
+            else
+                rb = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store_smem = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int pix = (tid + r * 256) >> 2;
+            As[buf][a_cg * 4 + 0][pix] = ra[r].x;
+            As[buf][a_cg * 4 + 1][pix] = ra[r].y;
+            As[buf][a_cg * 4 + 2][pix] = ra[r].z;
+            As[buf][a_cg * 4 + 3][pix] = ra[r].w;
+        }
+        if (b_act) *reinterpret_cast<float4*>(&Bs[buf][b_row][b_cg * 4]) = rb;
+    };
+
+    const int tn = tid % TN, tm = tid / TN;
+    float acc[PM][4];
+#pragma unroll
+    for (int i = 0; i < PM; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    load_regs(0);
+    store_smem(0);
+    __syncthreads();
+    for (int step = 0; step < nsteps; ++step) {
+        const int buf = step & 1;
+        if (step + 1 < nsteps) load_regs(step + 1);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tn * 4]);
+            float a[PM];
+            if constexpr (PM == 8) {
+                const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tm * 4]);
+                const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tm * 4]);
+                a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+                a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+            } else {
+                const float2 a0 = *reinterpret_cast<const float2*>(&As[buf][kk][tm * 2]);
+                a[0] = a0.x; a[1] = a0.y;
+            }
+#pragma unroll
+            for (int i = 0; i < PM; ++i) {
+                acc[i][0] = fmaf(a[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(a[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(a[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(a[i], b.w, acc[i][3]);
+            }
+        }
+        if (step + 1 < nsteps) store_smem(buf ^ 1);
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < PM; ++i) {
+        const int pix = (PM == 8) ? (i < 4 ? tm * 4 + i : 64 + tm * 4 + (i - 4)) : tm * 2 + i;
+        const int m = m0 + pix;
+        if (m >= M) continue;
+        const int oh = m / Wo, ow = m - (m / Wo) * Wo;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int co = n0 + tn * 4 + j;
+            if (co >= Cout) continue;
+            float v = acc[i][j] + bias[co];
+            if (d.act) v = gelu_erf(v);
+            store_out(d, g, oh, ow, co, v);
+        }
+    }
+}
+
+void launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
+    const int p = d.k / 2;
+    const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
+    const int M = Ho * Wo;
+    if (d.Cout <= 16) {
+        dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
+        conv_simt_kernel<16><<<grid, 256, 0, st>>>(d, Ho, Wo);
+    } else {
+        dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
+        conv_simt_kernel<64><<<grid, 256, 0, st>>>(d, Ho, Wo);
+    }
+}
+
+}  // namespace ufvc

@@ -1,0 +1,142 @@
+// Internal declarations of libufvc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <map>
+#include <memory>
+
+#include "../../include/ufvc.h"
+
+namespace ufvc {
+
+constexpr int kBins = 64;          // scale bins s_k, k = 0..63, log-spaced on [0.11, 64]
+constexpr int kRmax = 255;         // |r^| <= 255
+constexpr int kNsym = 511;         // symbols -255..255
+constexpr uint32_t kProbM = 1u << 16;
+constexpr uint32_t kRansL = 1u << 16;
+
+// ---------------------------------------------------------------------------------------------
+// Host-side tables (FP64 construction, built once per context)
+// ---------------------------------------------------------------------------------------------
+struct HostTables {
+    std::vector<uint32_t> freq;   // [64][511]
+    std::vector<uint32_t> cum;    // [64][512]
+    std::vector<uint32_t> packed; // [64][511]  (freq << 16) | cum   (both fit in 16 bits)
+    std::vector<float> thr;       // [64 qp][63]  float(t_k + ln q(qp))
+    std::vector<float> qstep;     // [64]  q(qp) as float
+    std::vector<float> qinv;      // [64]  1/q(qp) as float
+    std::vector<double> log_thr;  // [63]  t_k in FP64 (z^ RMS index)
+};
+void build_host_tables(HostTables& t);
+double qstep_fp64(int qp);
+
+// ---------------------------------------------------------------------------------------------
+// Architecture
+// ---------------------------------------------------------------------------------------------
+struct Arch { int e0, e1, e2, cy, cz, cd1, cd2; };
+bool get_arch(int arch, Arch* a);
+bool layer_shape(int arch, int N, int l, int* cout, int* k, int* cin);
+size_t weight_count(int arch, int N);
+
+enum EncLayer { L_A1 = 0, L_A2, L_A3, L_XA, L_XB, L_A4, L_H1, L_H2, L_S1, L_S2, L_S3, L_NENC };
+enum DecLayer { D_D0 = 0, D_R1A, D_R1B, D_U1, D_R2A, D_R2B, D_U2, D_U3, D_NDEC };
+
+// ---------------------------------------------------------------------------------------------
+// Convolution launch descriptor (shared by the FP32 SIMT and the tcgen05 kernels)
+// ---------------------------------------------------------------------------------------------
+enum OutMode { OUT_NHWC = 0, OUT_PS = 1, OUT_PS_FINAL_F32 = 2, OUT_PS_FINAL_U8 = 3 };
+
+struct ConvDesc {
+    const void* in = nullptr;   // NHWC [H][W][Cin] (float or bf16 by kernel)
+    long long in_gs = 0;        // elements between groups (0: shared input)
+    int H = 0, W = 0, Cin = 0;  // Cin: padded channel count of the stored tensor
+    const float* w = nullptr;   // SIMT: [k*k][Cin][Cout] float
+    long long w_gs = 0;
+    const float* b = nullptr;   // [Cout]
+    long long b_gs = 0;
+    int Cout = 0, k = 3, stride = 1;
+    int mode = OUT_NHWC;
+    int act = 0;                // 1: GELU (exact erf form)
+    void* out = nullptr;        // destination tensor
+    long long out_gs = 0;
+    int out_h = 0, out_w = 0;   // destination spatial dims (positions outside are dropped: crop)
+    const void* res = nullptr;  // residual added after the activation (same layout as out)
+    long long res_gs = 0;
+    float* out2 = nullptr;      // channels >= split go to out2 (NHWC with Cout - split channels)
+    int split = 0;
+    int groups = 1;
+    int out_bf16 = 0;           // tensor-core path: store bf16 instead of float
+};
+
+void launch_conv_simt(const ConvDesc& d, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------------
+// Elementwise / entropy kernels
+// ---------------------------------------------------------------------------------------------
+void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s);
+void launch_zquant(const float* z, int npos, int cz, const uint64_t* zthr, int16_t* zhat, uint8_t* iz,
+                   cudaStream_t s);
+void launch_quantize(const float* y, const float* mu, const float* logsig, size_t n, const float* thr_all,
+                     const float* qinv_all, const int* qp_dev, int qp_host, int16_t* rhat, uint8_t* idx,
+                     cudaStream_t s);
+void launch_scale_index(const float* logsig, size_t n, const float* thr_all, const int* qp_dev, uint8_t* idx,
+                        cudaStream_t s);
+void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s);
+
+// rANS: a "section job" describes one section of one stream
+struct RansSection {
+    const int16_t* sym;       // encode input
+    const uint8_t* idx;       // table index per element, or per channel if idx_period > 0
+    int idx_period;
+    size_t n;
+    int K;
+    // encode scratch
+    uint16_t* scratch;        // [K][cap_lane]
+    int cap_lane;
+    uint32_t* counts;         // [K] word counts
+    int* status;              // device status word (caller errors: symbol / index out of range)
+};
+void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s);
+
+// Lay out one or two encoded sections after `hdr_bytes` of header in `out`: write lane counts, copy the
+// words, write the total size to *nbytes.  Capacity violations set *status = UFVC_ERR_CAPACITY.
+void launch_rans_finalize(const RansSection* secs, int nsec, uint8_t* out, size_t hdr_bytes, size_t capacity,
+                          uint64_t* nbytes, uint64_t* offsets_ws, int* status, cudaStream_t s);
+
+// Decoding: parse the lane counts of a section starting at byte `sec_off` (device value or host
+// constant), validate and produce word offsets.
+struct RansDecodeJob {
+    const uint8_t* bits;      // stream base
+    size_t nbytes;            // bytes available from the stream base
+    size_t sec_off_host;      // section offset if known on the host ...
+    const uint64_t* sec_off_dev; // ... or read from the device (then sec_off_host is ignored)
+    const uint8_t* idx;
+    int idx_period;
+    size_t n;
+    int K;
+    uint64_t* lane_off;       // [K] byte offsets of each lane stream (from the stream base)
+    uint32_t* lane_words;     // [K]
+    uint64_t* next_off;       // device: byte offset just past this section
+    int16_t* sym;             // output symbols (or nullptr)
+    float* yhat;              // output y^ = r^ q + mu (or nullptr)
+    const float* mu;
+    const float* qstep_all;   // [64]
+    const int* qp_dev;
+};
+void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s);
+// as launch_rans_parse, and the section must end exactly at byte `expect_end` of the stream
+void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, int* status, cudaStream_t s);
+void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, int* status, cudaStream_t s);
+
+// Container header
+void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,
+                         int Cz, size_t capacity, int* status, cudaStream_t s);
+void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
+                         int* qp_dev, uint8_t* iz, int* status, cudaStream_t s);
+
+}  // namespace ufvc

@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libufvc.so (include/ufvc.h).  Argument marshalling only: every step of the
+chunk path runs in the library's CUDA kernels.  Device buffers are torch CUDA tensors; the stream is
+torch's current stream unless one is given.  There is no CPU fallback: if the library cannot be
+loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(f"libufvc.so not built ({_LIB_PATH}); run `python -m paper_2606_04410_b300.build`")
+lib = C.CDLL(_LIB_PATH)
+
+UFVC_OK, UFVC_ERR_ARG, UFVC_ERR_CAPACITY, UFVC_ERR_CORRUPT, UFVC_ERR_OOM, UFVC_ERR_CUDA, UFVC_ERR_TIMEOUT, \
+    UFVC_ERR_UNSUPPORTED, UFVC_PENDING = range(9)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CAPACITY", "ERR_CORRUPT", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT",
+                "ERR_UNSUPPORTED", "PENDING"]
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = [
+    "ufvc_weight_count", "ufvc_create", "ufvc_destroy", "ufvc_layer_shape", "ufvc_latent_dims",
+    "ufvc_max_bitstream_bytes", "ufvc_encode_chunk", "ufvc_decode_chunk", "ufvc_decode_chunk_f32",
+    "ufvc_encode_chunk_host", "ufvc_decode_chunk_host", "ufvc_sync_status", "ufvc_encode_stages",
+    "ufvc_hyper_synthesis", "ufvc_quantize", "ufvc_synthesize", "ufvc_rans_encode", "ufvc_rans_decode",
+    "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error",
+]
+
+
+class ufvc_config(C.Structure):
+    _fields_ = [("arch", C.c_int), ("chunk_len", C.c_int), ("lanes", C.c_int), ("precision", C.c_int),
+                ("device", C.c_int)]
+
+
+_vp, _sz, _i = C.c_void_p, C.c_size_t, C.c_int
+_sigs = {
+    "ufvc_weight_count": (_sz, [_i, _i]),
+    "ufvc_create": (_i, [C.POINTER(ufvc_config), _vp, _sz, C.POINTER(_vp)]),
+    "ufvc_destroy": (None, [_vp]),
+    "ufvc_layer_shape": (_i, [_i, _i, _i, _vp, _vp, _vp]),
+    "ufvc_latent_dims": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ufvc_max_bitstream_bytes": (_sz, [_vp, _i, _i]),
+    "ufvc_encode_chunk": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
+    "ufvc_decode_chunk": (_i, [_vp, _vp, _sz, _vp, _i, _i, _i, _vp]),
+    "ufvc_decode_chunk_f32": (_i, [_vp, _vp, _sz, _vp, _i, _i, _i, _vp]),
+    "ufvc_encode_chunk_host": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, C.POINTER(_sz), _vp]),
+    "ufvc_decode_chunk_host": (_i, [_vp, _vp, _sz, _vp, _i, _i, _i, _vp]),
+    "ufvc_sync_status": (_i, [_vp, _vp]),
+    "ufvc_encode_stages": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "ufvc_hyper_synthesis": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "ufvc_quantize": (_i, [_vp, _vp, _vp, _vp, _sz, _i, _vp, _vp, _vp]),
+    "ufvc_synthesize": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
+    "ufvc_rans_encode": (_i, [_vp, _vp, _vp, _sz, _i, _vp, _sz, _vp, _vp]),
+    "ufvc_rans_decode": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _vp, _vp]),
+    "ufvc_get_tables": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "ufvc_set_profiling": (_i, [_vp, _i]),
+    "ufvc_get_profile": (_i, [_vp, _vp, _vp, _vp, _i, C.POINTER(_i)]),
+    "ufvc_last_error": (C.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class UfvcError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"{STATUS_NAMES[code] if 0 <= code < len(STATUS_NAMES) else code}: {msg}")
+        self.code = code
+
+
+def _ptr(t) -> C.c_void_p | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous()
+        return C.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return C.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def weight_count(arch: int, chunk_len: int) -> int:
+    return int(lib.ufvc_weight_count(arch, chunk_len))
+
+
+def latent_dims(arch: int, width: int, height: int) -> dict:
+    v = [C.c_int() for _ in range(6)]
+    rc = lib.ufvc_latent_dims(arch, width, height, *[C.byref(x) for x in v])
+    if rc:
+        raise UfvcError(rc, "latent_dims")
+    return dict(zip(["Hy", "Wy", "Hz", "Wz", "Cy", "Cz"], [x.value for x in v]))
+
+
+class Codec:
+    """One ufvc_ctx.  Methods mirror the C entry points (ufvc_<name>)."""
+
+    def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "fp32",
+                 device: int = 0):
+        self.arch, self.N, self.K, self.precision = arch, chunk_len, lanes, precision
+        self.device = device
+        cfg = ufvc_config(arch, chunk_len, lanes, PRECISIONS[precision], device)
+        w = np.ascontiguousarray(weights, np.float32)
+        h = C.c_void_p()
+        rc = lib.ufvc_create(C.byref(cfg), _ptr(w), w.size, C.byref(h))
+        if rc:
+            raise UfvcError(rc, "ufvc_create")
+        self.h = h
+        dims = latent_dims(arch, 16, 16)
+        self.Cy, self.Cz = dims["Cy"], dims["Cz"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ufvc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc:
+            raise UfvcError(rc, f"{what}: {lib.ufvc_last_error(self.h).decode()}")
+
+    # ---- chunk calls
+    def max_bitstream_bytes(self, width: int, height: int) -> int:
+        return int(lib.ufvc_max_bitstream_bytes(self.h, width, height))
+
+    def encode_chunk(self, frames: torch.Tensor, qp: int = 32, bits: torch.Tensor | None = None,
+                     nbytes: torch.Tensor | None = None, stream=None):
+        """frames: cuda uint8 [N][H][W][3] -> (bits cuda uint8 [capacity], nbytes cuda int64 [1])."""
+        N, H, W, _ = frames.shape
+        if bits is None:
+            bits = torch.empty(self.max_bitstream_bytes(W, H), dtype=torch.uint8, device=frames.device)
+        if nbytes is None:
+            nbytes = torch.zeros(1, dtype=torch.int64, device=frames.device)
+        self._check(lib.ufvc_encode_chunk(self.h, _ptr(frames), N, W, H, qp, _ptr(bits), bits.numel(), _ptr(nbytes),
+                                          _stream(stream)), "encode_chunk")
+        return bits, nbytes
+
+    def decode_chunk(self, bits: torch.Tensor, nbytes: int, width: int, height: int, out: torch.Tensor | None = None,
+                     f32: bool = False, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.N, height, width, 3), dtype=torch.float32 if f32 else torch.uint8,
+                              device=bits.device)
+        fn = lib.ufvc_decode_chunk_f32 if f32 else lib.ufvc_decode_chunk
+        self._check(fn(self.h, _ptr(bits), int(nbytes), _ptr(out), self.N, width, height, _stream(stream)),
+                    "decode_chunk")
+        return out
+
+    def encode_chunk_host(self, frames: np.ndarray | torch.Tensor, qp: int = 32, stream=None) -> bytes:
+        N, H, W, _ = frames.shape
+        cap = self.max_bitstream_bytes(W, H)
+        out = torch.empty(cap, dtype=torch.uint8).pin_memory() if torch.cuda.is_available() else np.empty(cap, np.uint8)
+        nb = C.c_size_t()
+        rc = lib.ufvc_encode_chunk_host(self.h, _ptr(frames), N, W, H, qp, _ptr(out), cap, C.byref(nb),
+                                        _stream(stream))
+        self._check(rc, "encode_chunk_host")
+        return bytes(out[:nb.value].numpy() if isinstance(out, torch.Tensor) else out[:nb.value])
+
+    def decode_chunk_host(self, bits, width: int, height: int, out=None, stream=None):
+        if out is None:
+            out = np.empty((self.N, height, width, 3), np.uint8)
+        src = bits if isinstance(bits, (np.ndarray, torch.Tensor)) else np.frombuffer(bits, np.uint8).copy()
+        n = src.numel() if isinstance(src, torch.Tensor) else src.size
+        self._check(lib.ufvc_decode_chunk_host(self.h, _ptr(src), n, _ptr(out), self.N, width, height,
+                                               _stream(stream)), "decode_chunk_host")
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return int(lib.ufvc_sync_status(self.h, _stream(stream)))
+
+    # ---- stages
+    def encode_stages(self, frames: torch.Tensor, qp: int = 32, stream=None) -> dict:
+        N, H, W, _ = frames.shape
+        d = latent_dims(self.arch, W, H)
+        dev = frames.device
+        yshape = (d["Hy"], d["Wy"], d["Cy"])
+        out = dict(y=torch.empty(yshape, device=dev), zhat=torch.empty((d["Hz"], d["Wz"], d["Cz"]), dtype=torch.int16,
+                                                                        device=dev),
+                   iz=torch.empty(d["Cz"], dtype=torch.uint8, device=dev), mu=torch.empty(yshape, device=dev),
+                   logsig=torch.empty(yshape, device=dev), rhat=torch.empty(yshape, dtype=torch.int16, device=dev),
+                   idx=torch.empty(yshape, dtype=torch.uint8, device=dev))
+        self._check(lib.ufvc_encode_stages(self.h, _ptr(frames), W, H, qp, *[_ptr(out[k]) for k in
+                                                                             ("y", "zhat", "iz", "mu", "logsig", "rhat",
+                                                                              "idx")], _stream(stream)),
+                    "encode_stages")
+        return out
+
+    def hyper_synthesis(self, zhat: torch.Tensor, Hy: int, Wy: int, stream=None):
+        Hz, Wz, _ = zhat.shape
+        mu = torch.empty((Hy, Wy, self.Cy), device=zhat.device)
+        ls = torch.empty((Hy, Wy, self.Cy), device=zhat.device)
+        self._check(lib.ufvc_hyper_synthesis(self.h, _ptr(zhat), Hz, Wz, Hy, Wy, _ptr(mu), _ptr(ls), _stream(stream)),
+                    "hyper_synthesis")
+        return mu, ls
+
+    def quantize(self, y, mu, logsig, qp: int = 32, stream=None):
+        rhat = torch.empty(y.shape, dtype=torch.int16, device=y.device)
+        idx = torch.empty(y.shape, dtype=torch.uint8, device=y.device)
+        self._check(lib.ufvc_quantize(self.h, _ptr(y), _ptr(mu), _ptr(logsig), y.numel(), qp, _ptr(rhat), _ptr(idx),
+                                      _stream(stream)), "quantize")
+        return rhat, idx
+
+    def synthesize(self, yhat: torch.Tensor, width: int, height: int, stream=None) -> torch.Tensor:
+        out = torch.empty((self.N, height, width, 3), device=yhat.device)
+        self._check(lib.ufvc_synthesize(self.h, _ptr(yhat), width, height, _ptr(out), _stream(stream)), "synthesize")
+        return out
+
+    def rans_encode(self, sym: torch.Tensor, idx: torch.Tensor, lanes: int, capacity: int | None = None,
+                    stream=None):
+        n = sym.numel()
+        if capacity is None:
+            capacity = 4 * lanes + 2 * (n + 2 * lanes) + 4
+        out = torch.empty(capacity, dtype=torch.uint8, device=sym.device)
+        nb = torch.zeros(1, dtype=torch.int64, device=sym.device)
+        self._check(lib.ufvc_rans_encode(self.h, _ptr(sym), _ptr(idx), n, lanes, _ptr(out), capacity, _ptr(nb),
+                                         _stream(stream)), "rans_encode")
+        return out, nb
+
+    def rans_decode(self, data: torch.Tensor, nbytes: int, idx: torch.Tensor, n: int, lanes: int, stream=None):
+        sym = torch.empty(max(n, 1), dtype=torch.int16, device=data.device)
+        self._check(lib.ufvc_rans_decode(self.h, _ptr(data), int(nbytes), _ptr(idx), n, lanes, _ptr(sym),
+                                         _stream(stream)), "rans_decode")
+        return sym[:n]
+
+    def get_tables(self, qp: int = 32):
+        freq = np.empty((64, 511), np.uint32)
+        cum = np.empty((64, 512), np.uint32)
+        thr = np.empty(63, np.float32)
+        self._check(lib.ufvc_get_tables(self.h, _ptr(freq), _ptr(cum), qp, _ptr(thr)), "get_tables")
+        return freq, cum, thr
+
+    def set_profiling(self, enable: bool):
+        self._check(lib.ufvc_set_profiling(self.h, int(enable)), "set_profiling")
+
+    def get_profile(self, max_entries: int = 64) -> list[tuple[str, float, int]]:
+        names = C.create_string_buffer(32 * max_entries)
+        ms = np.zeros(max_entries, np.float32)
+        launches = np.zeros(max_entries, np.int32)
+        cnt = C.c_int()
+        self._check(lib.ufvc_get_profile(self.h, names, _ptr(ms), _ptr(launches), max_entries, C.byref(cnt)),
+                    "get_profile")
+        raw = names.raw
+        return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), float(ms[i]), int(launches[i]))
+                for i in range(cnt.value)]
