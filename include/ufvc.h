@@ -54,8 +54,10 @@ typedef enum {
 
 typedef enum {
     UFVC_FP32 = 0,  /* every convolution in FP32 on CUDA cores (deterministic) */
-    UFVC_BF16 = 1,  /* analysis / hyper-analysis / decoder convolutions: BF16 operands on tcgen05
-                       tensor cores, FP32 accumulation in TMEM; entropy-parameter path stays FP32 */
+    UFVC_BF16 = 1,  /* analysis and decoder convolutions: BF16 operands on tcgen05 tensor cores, FP32
+                       accumulation in TMEM; hyper-analysis and the entropy-parameter path stay FP32.
+                       arch 1 only (all activation widths multiples of 64); arch 0 gives
+                       UFVC_ERR_UNSUPPORTED */
     UFVC_FP8 = 2    /* as BF16 but E4M3 operands with per-output-channel weight scales and one
                        per-layer activation scale */
 } ufvc_precision;
@@ -162,6 +164,16 @@ ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t*
                              uint8_t* d_out, size_t capacity, uint64_t* d_nbytes, void* stream);
 ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, const uint8_t* d_idx, size_t n,
                              int lanes, int16_t* d_sym, void* stream);
+
+/* One convolution of the context's weights, for layer-level tests: blob layer `layer` (decoder layers
+ * of frame f are 11 + 8 f + j) applied to d_in [H][W][Cin_s] with zero padding k/2 and `stride`;
+ * act = 1 applies GELU; mode 0 writes NHWC [out_h][out_w][Cout], mode 1 pixel-shuffles x2 into
+ * [out_h][out_w][Cout/4] (positions outside out_h x out_w are dropped), mode 2 writes
+ * clamp(0.5 + o, 0, 1) pixel-shuffled as float.  In FP32 precision (and for the hyper layers
+ * H1 H2 S1 S2 S3) tensors are float with Cin_s = Cin rounded up to 16; otherwise they are bf16 with
+ * Cin_s rounded up to 64 and the layer runs on the tensor cores. */
+ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, int W, int stride, int act, int mode,
+                            void* d_out, int out_h, int out_w, void* stream);
 
 /* Host copies of the tables the context uses: freq / cum uint32 [64][511] / [64][512] (may be NULL),
  * thr float32 [63] for rate qp (may be NULL).  No device work.  ctx may be NULL: the tables are then

@@ -22,6 +22,9 @@ struct LayerW {
     float* w = nullptr;  // FP32 SIMT layout [k*k][cin_p][cout] per group, groups back to back
     float* b = nullptr;  // [cout] per group
     long long w_gs = 0, b_gs = 0;
+    // tensor-core copy (BF16 precision): bf16 [groups][cout_pad][k*k][cin_tc], K-major
+    __nv_bfloat16* wtc = nullptr;
+    int cout_pad = 0, cin_tc = 0;
 };
 
 struct Plan {
@@ -44,6 +47,8 @@ struct Plan {
     uint64_t *lo_z = nullptr, *lo_y = nullptr, *next_z = nullptr, *next_y = nullptr;
     uint32_t *lw_z = nullptr, *lw_y = nullptr;
     float *dzf = nullptr, *ds1 = nullptr, *ds2 = nullptr, *dmu = nullptr, *dls = nullptr, *yhat = nullptr;
+    __nv_bfloat16* yhat_bf = nullptr;
+    // decoder activations: float in FP32 precision, bf16 (same buffers, half used) otherwise
     float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
     bool enc_ready = false, dec_ready = false;
     std::vector<void*> allocs;
@@ -138,19 +143,15 @@ static void prof_end(ufvc_ctx* ctx, cudaStream_t s, int launches) {
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1; }
 
-static void conv(ufvc_ctx* ctx, const LayerW& L, const float* in, int H, int W, int stride, int act, int mode,
-                 void* out, int out_h, int out_w, cudaStream_t s, const float* res = nullptr,
-                 float* out2 = nullptr, int split = 0, long long in_gs = 0, long long out_gs = 0,
-                 long long res_gs = 0, int groups = 1) {
-    (void)ctx;
-    ConvDesc d;
-    d.in = in; d.in_gs = in_gs; d.H = H; d.W = W; d.Cin = L.cin_p;
-    d.w = L.w; d.w_gs = L.w_gs; d.b = L.b; d.b_gs = L.b_gs;
-    d.Cout = L.cout; d.k = L.k; d.stride = stride; d.mode = mode; d.act = act;
-    d.out = out; d.out_gs = out_gs; d.out_h = out_h; d.out_w = out_w;
-    d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
-    launch_conv_simt(d, s);
-}
+// One convolution launch.  Layers with a tensor-core weight copy run on tcgen05 in BF16 precision
+// (bf16 activations in and out, except out_f32); all others (and every layer in FP32 precision) run on
+// the deterministic FP32 SIMT kernel.
+static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, int W, int stride, int act, int mode,
+                        void* out, int out_h, int out_w, cudaStream_t s, const void* res = nullptr,
+                        float* out2 = nullptr, int split = 0, long long in_gs = 0, long long out_gs = 0,
+                        long long res_gs = 0, int groups = 1, bool out_f32 = false);
+
+static bool use_tc(const ufvc_ctx* ctx, const LayerW& L);
 
 // ------------------------------------------------------------------------------------------------
 // plans
@@ -168,7 +169,8 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         p = new Plan();
         p->W = W; p->H = H;
         p->Hp = ceil_div(H, 16) * 16; p->Wp = ceil_div(W, 16) * 16;
-        p->C0p = ceil_div(3 * ctx->N, 16) * 16;
+        // packed input channels: 16-multiple for the SIMT kernel, 64-multiple (one 128-byte K chunk) for tcgen05
+        p->C0p = ctx->cfg.precision == UFVC_FP32 ? ceil_div(3 * ctx->N, 16) * 16 : ceil_div(3 * ctx->N, 64) * 64;
         p->h1 = conv_out(p->Hp, 3, 2); p->w1 = conv_out(p->Wp, 3, 2);
         p->h2 = conv_out(p->h1, 3, 2); p->w2 = conv_out(p->w1, 3, 2);
         p->h3 = conv_out(p->h2, 3, 2); p->w3 = conv_out(p->w2, 3, 2);
@@ -237,6 +239,7 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         AL(p->dmu, p->ny);
         AL(p->dls, p->ny);
         AL(p->yhat, p->ny);
+        AL(p->yhat_bf, p->ny);
         const size_t n1 = (size_t)N * 4 * p->Hy * p->Wy * a.cd1;
         const size_t n2 = (size_t)N * 16 * p->Hy * p->Wy * a.cd2;
         const size_t n3 = (size_t)N * 64 * p->Hy * p->Wy * a.cd2;
@@ -275,7 +278,8 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
     return UFVC_OK;
 }
 
-static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups) {
+static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
+                                bool tc) {
     int co, k, ci;
     layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
     L.cout = co; L.k = k; L.cin = ci; L.cin_p = ceil_div(ci, 16) * 16; L.groups = groups;
@@ -296,6 +300,23 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
     if ((st = dalloc(ctx, nullptr, &L.b, b.size())) != UFVC_OK) return st;
     CK(cudaMemcpy(L.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.b, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+    if (tc && ctx->cfg.precision != UFVC_FP32) {
+        // K-major bf16 copy for tcgen05: [g][cout_pad][tap][cin_tc], zero rows / columns in the padding
+        L.cin_tc = ceil_div(ci, 64) * 64;
+        L.cout_pad = co >= 64 ? co : 16;
+        const size_t K = (size_t)k * k * L.cin_tc;
+        std::vector<__nv_bfloat16> wt((size_t)groups * L.cout_pad * K, __float2bfloat16(0.f));
+        for (int g = 0; g < groups; ++g) {
+            const float* src = blob + offs[first + g * D_NDEC];
+            for (int o = 0; o < co; ++o)
+                for (int t = 0; t < k * k; ++t)
+                    for (int i = 0; i < ci; ++i)
+                        wt[((size_t)g * L.cout_pad + o) * K + (size_t)t * L.cin_tc + i] =
+                            __float2bfloat16(src[((size_t)o * k * k + t) * ci + i]);
+        }
+        if ((st = dalloc(ctx, nullptr, &L.wtc, wt.size())) != UFVC_OK) return st;
+        CK(cudaMemcpy(L.wtc, wt.data(), wt.size() * 2, cudaMemcpyHostToDevice));
+    }
     return UFVC_OK;
 }
 
@@ -304,8 +325,8 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     cudaSetDevice(ctx->cfg.device);
     cudaDeviceSynchronize();
     for (auto& kv : ctx->plans) free_plan(kv.second);
-    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); }
-    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); }
+    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
+    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
     cudaFree(ctx->d_packed); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
     cudaFree(ctx->d_status);
     cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
@@ -321,7 +342,10 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         cfg->lanes > 65536 || cfg->precision < 0 || cfg->precision > 2)
         return UFVC_ERR_ARG;
     if (n_weights != weight_count(cfg->arch, cfg->chunk_len)) return UFVC_ERR_ARG;
-    if (cfg->precision != UFVC_FP32) return UFVC_ERR_UNSUPPORTED;
+    if (cfg->precision == UFVC_FP8) return UFVC_ERR_UNSUPPORTED;
+    // the tensor-core path stages K in 64-channel chunks: every activation width must be a multiple of
+    // 64, which holds for the 1080p-family widths only (the tiny widths include 96)
+    if (cfg->precision != UFVC_FP32 && cfg->arch != 1) return UFVC_ERR_UNSUPPORTED;
     ufvc_ctx* ctx = new ufvc_ctx();
     ctx->cfg = *cfg;
     ctx->arch = a;
@@ -352,14 +376,46 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         off += (size_t)co * k * k * ci + co;
     }
     for (int l = 0; l < L_NENC; ++l)
-        if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1)) != UFVC_OK) return bail(st);
+        if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1, l <= L_A4)) != UFVC_OK) return bail(st);
     for (int j = 0; j < D_NDEC; ++j)
-        if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N)) != UFVC_OK) return bail(st);
+        if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true)) != UFVC_OK)
+            return bail(st);
     *out = ctx;
     return UFVC_OK;
 }
 
 extern "C" const char* ufvc_last_error(const ufvc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static bool use_tc(const ufvc_ctx* ctx, const LayerW& L) { return ctx->cfg.precision != UFVC_FP32 && L.wtc; }
+
+static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, int W, int stride, int act, int mode,
+                        void* out, int out_h, int out_w, cudaStream_t s, const void* res, float* out2, int split,
+                        long long in_gs, long long out_gs, long long res_gs, int groups, bool out_f32) {
+    ConvDesc d;
+    d.in = in; d.in_gs = in_gs; d.H = H; d.W = W;
+    d.w = L.w; d.w_gs = L.w_gs; d.b = L.b; d.b_gs = L.b_gs;
+    d.Cout = L.cout; d.k = L.k; d.stride = stride; d.mode = mode; d.act = act;
+    d.out = out; d.out_gs = out_gs; d.out_h = out_h; d.out_w = out_w;
+    d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
+    if (use_tc(ctx, L)) {
+        d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
+        const cudaError_t e = launch_conv_tc(d, s);
+        if (e != cudaSuccess) {
+            ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
+            return UFVC_ERR_CUDA;
+        }
+        return UFVC_OK;
+    }
+    d.Cin = L.cin_p;
+    launch_conv_simt(d, s);
+    return UFVC_OK;
+}
+
+#define RUN(x)                          \
+    do {                                \
+        ufvc_status st_ = (x);          \
+        if (st_ != UFVC_OK) return st_; \
+    } while (0)
 
 extern "C" size_t ufvc_max_bitstream_bytes(const ufvc_ctx* ctx, int width, int height) {
     if (!ctx || width < 1 || height < 1) return 0;
@@ -390,68 +446,84 @@ static bool check_shape(ufvc_ctx* ctx, int n_frames, int width, int height) {
 }
 
 // hyper-synthesis: zhat (int16) -> mu, logsig; deterministic FP32 path in every precision
-static void run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zhat, float* zf, float* s1, float* s2,
-                                float* mu, float* ls, cudaStream_t s) {
+static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zhat, float* zf, float* s1, float* s2,
+                                       float* mu, float* ls, cudaStream_t s) {
     const Arch& a = ctx->arch;
     prof_begin(ctx, "hyper_synthesis", s);
     launch_i16_to_f32(zhat, p->nz, zf, s);
-    conv(ctx, ctx->enc[L_S1], zf, p->Hz, p->Wz, 1, 1, OUT_PS, s1, 2 * p->Hz, 2 * p->Wz, s);
-    conv(ctx, ctx->enc[L_S2], s1, 2 * p->Hz, 2 * p->Wz, 1, 1, OUT_PS, s2, p->Hy, p->Wy, s);  // crop
-    conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy);
+    RUN(conv(ctx, ctx->enc[L_S1], zf, p->Hz, p->Wz, 1, 1, OUT_PS, s1, 2 * p->Hz, 2 * p->Wz, s));
+    RUN(conv(ctx, ctx->enc[L_S2], s1, 2 * p->Hz, 2 * p->Wz, 1, 1, OUT_PS, s2, p->Hy, p->Wy, s));  // crop
+    RUN(conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy));
     prof_end(ctx, s, 4);
+    return UFVC_OK;
 }
 
-static void run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
+static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
     const Arch& a = ctx->arch;
     prof_begin(ctx, "pack", s);
-    launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
+    if (ctx->cfg.precision == UFVC_FP32)
+        launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
+    else
+        launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "analysis", s);
-    conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s);
-    conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s);
-    conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s);
-    conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s);
-    conv(ctx, ctx->enc[L_XB], p->xt, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3);  // residual, in place
-    conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s);
+    RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    RUN(conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s));
+    RUN(conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s));
+    RUN(conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s));
+    // cross-frame interaction residual, in place
+    RUN(conv(ctx, ctx->enc[L_XB], p->xt, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3));
+    // y is float in every precision (it feeds the FP32 hyper-analysis and the quantiser)
+    RUN(conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s, nullptr, nullptr, 0, 0, 0,
+             0, 1, true));
     prof_end(ctx, s, 6);
     prof_begin(ctx, "hyper_analysis", s);
-    conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s);
-    conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s);
+    RUN(conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s));
+    RUN(conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s));
     launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
     prof_end(ctx, s, 3);
-    run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s);
+    RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s));
     prof_begin(ctx, "quantize", s);
     launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);
     prof_end(ctx, s, 1);
+    return UFVC_OK;
 }
 
-static void run_decoders(ufvc_ctx* ctx, Plan* p, const float* yhat, void* frames_out, int final_mode, cudaStream_t s) {
+// yhat: float [Hy][Wy][Cy] in FP32 precision, bf16 otherwise
+static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* frames_out, int final_mode,
+                                cudaStream_t s) {
     const Arch& a = ctx->arch;
     const int N = ctx->N;
     const int h1 = 2 * p->Hy, w1 = 2 * p->Wy, h2 = 4 * p->Hy, w2 = 4 * p->Wy, h3 = 8 * p->Hy, w3 = 8 * p->Wy;
     const long long g1 = (long long)h1 * w1 * a.cd1, g2 = (long long)h2 * w2 * a.cd2, g3 = (long long)h3 * w3 * a.cd2;
     const long long gf = (long long)p->H * p->W * 3;
     prof_begin(ctx, "dec.D0", s);
-    conv(ctx, ctx->dec[D_D0], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, p->bufA, h1, w1, s, nullptr, nullptr, 0, 0, g1, 0, N);
+    RUN(conv(ctx, ctx->dec[D_D0], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, p->bufA, h1, w1, s, nullptr, nullptr, 0, 0, g1, 0,
+             N));
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.R1", s);
-    conv(ctx, ctx->dec[D_R1A], p->bufA, h1, w1, 1, 1, OUT_NHWC, p->bufT, h1, w1, s, nullptr, nullptr, 0, g1, g1, 0, N);
-    conv(ctx, ctx->dec[D_R1B], p->bufT, h1, w1, 1, 0, OUT_NHWC, p->bufA, h1, w1, s, p->bufA, nullptr, 0, g1, g1, g1, N);
+    RUN(conv(ctx, ctx->dec[D_R1A], p->bufA, h1, w1, 1, 1, OUT_NHWC, p->bufT, h1, w1, s, nullptr, nullptr, 0, g1, g1, 0,
+             N));
+    RUN(conv(ctx, ctx->dec[D_R1B], p->bufT, h1, w1, 1, 0, OUT_NHWC, p->bufA, h1, w1, s, p->bufA, nullptr, 0, g1, g1,
+             g1, N));
     prof_end(ctx, s, 2);
     prof_begin(ctx, "dec.U1", s);
-    conv(ctx, ctx->dec[D_U1], p->bufA, h1, w1, 1, 1, OUT_PS, p->bufB, h2, w2, s, nullptr, nullptr, 0, g1, g2, 0, N);
+    RUN(conv(ctx, ctx->dec[D_U1], p->bufA, h1, w1, 1, 1, OUT_PS, p->bufB, h2, w2, s, nullptr, nullptr, 0, g1, g2, 0, N));
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.R2", s);
-    conv(ctx, ctx->dec[D_R2A], p->bufB, h2, w2, 1, 1, OUT_NHWC, p->bufT2, h2, w2, s, nullptr, nullptr, 0, g2, g2, 0, N);
-    conv(ctx, ctx->dec[D_R2B], p->bufT2, h2, w2, 1, 0, OUT_NHWC, p->bufB, h2, w2, s, p->bufB, nullptr, 0, g2, g2, g2, N);
+    RUN(conv(ctx, ctx->dec[D_R2A], p->bufB, h2, w2, 1, 1, OUT_NHWC, p->bufT2, h2, w2, s, nullptr, nullptr, 0, g2, g2, 0,
+             N));
+    RUN(conv(ctx, ctx->dec[D_R2B], p->bufT2, h2, w2, 1, 0, OUT_NHWC, p->bufB, h2, w2, s, p->bufB, nullptr, 0, g2, g2,
+             g2, N));
     prof_end(ctx, s, 2);
     prof_begin(ctx, "dec.U2", s);
-    conv(ctx, ctx->dec[D_U2], p->bufB, h2, w2, 1, 1, OUT_PS, p->bufC, h3, w3, s, nullptr, nullptr, 0, g2, g3, 0, N);
+    RUN(conv(ctx, ctx->dec[D_U2], p->bufB, h2, w2, 1, 1, OUT_PS, p->bufC, h3, w3, s, nullptr, nullptr, 0, g2, g3, 0, N));
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.U3", s);
-    conv(ctx, ctx->dec[D_U3], p->bufC, h3, w3, 1, 0, final_mode, frames_out, p->H, p->W, s, nullptr, nullptr, 0, g3, gf,
-         0, N);
+    RUN(conv(ctx, ctx->dec[D_U3], p->bufC, h3, w3, 1, 0, final_mode, frames_out, p->H, p->W, s, nullptr, nullptr, 0, g3,
+             gf, 0, N));
     prof_end(ctx, s, 1);
+    return UFVC_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -467,7 +539,7 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     ufvc_status st = get_plan(ctx, width, height, false, &p);
     if (st) return st;
 
-    run_encoder_front(ctx, p, d_frames, qp, s);
+    RUN(run_encoder_front(ctx, p, d_frames, qp, s));
     prof_begin(ctx, "rans_encode", s);
     RansSection secs[2];
     secs[0] = RansSection{p->zhat, p->iz, ctx->arch.cz, p->nz, p->Kz, p->scr_z, p->cap_z, p->cnt_z, ctx->d_status};
@@ -497,24 +569,25 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_begin(ctx, "parse", s);
     launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, p->qp_dev,
                         p->diz, ctx->d_status, s);
+    const bool fp32 = ctx->cfg.precision == UFVC_FP32;
     RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
-                     p->dzhat, nullptr, nullptr, ctx->d_qstep, p->qp_dev};
+                     p->dzhat, nullptr, nullptr, nullptr, ctx->d_qstep, p->qp_dev};
     RansDecodeJob jy{d_bits, nbytes, 0, p->next_z, p->didx, 0, p->ny, ctx->cfg.lanes, p->lo_y, p->lw_y, p->next_y,
-                     nullptr, p->yhat, p->dmu, ctx->d_qstep, p->qp_dev};
+                     nullptr, fp32 ? p->yhat : nullptr, fp32 ? nullptr : p->yhat_bf, p->dmu, ctx->d_qstep, p->qp_dev};
     launch_rans_parse(jz, ctx->d_status, s);
     launch_rans_parse_expect(jy, nbytes, ctx->d_status, s);
     prof_end(ctx, s, 3);
     prof_begin(ctx, "rans_decode_z", s);
     launch_rans_decode(jz, ctx->d_packed, ctx->d_status, s);
     prof_end(ctx, s, 1);
-    run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s);
+    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s));
     prof_begin(ctx, "scale_index", s);
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode_y", s);
     launch_rans_decode(jy, ctx->d_packed, ctx->d_status, s);
     prof_end(ctx, s, 1);
-    run_decoders(ctx, p, p->yhat, d_frames, final_mode, s);
+    RUN(run_decoders(ctx, p, fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf, d_frames, final_mode, s));
     CK(cudaGetLastError());
     return UFVC_OK;
 }
@@ -607,7 +680,7 @@ extern "C" ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames
     ufvc_status st = get_plan(ctx, width, height, false, &p);
     if (st) return st;
 
-    run_encoder_front(ctx, p, d_frames, qp, s);
+    RUN(run_encoder_front(ctx, p, d_frames, qp, s));
     const Arch& a = ctx->arch;
     if (d_y) CK(cudaMemcpyAsync(d_y, p->y, p->ny * 4, cudaMemcpyDeviceToDevice, s));
     if (d_zhat) CK(cudaMemcpyAsync(d_zhat, p->zhat, p->nz * 2, cudaMemcpyDeviceToDevice, s));
@@ -638,9 +711,10 @@ extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat
         return st;
     }
 
-    run_hyper_synthesis(ctx, &tmp, d_zhat, zf, s1, s2, d_mu, d_logsig, s);
+    st = run_hyper_synthesis(ctx, &tmp, d_zhat, zf, s1, s2, d_mu, d_logsig, s);
     cudaError_t e = cudaStreamSynchronize(s);
     for (void* v : tmp.allocs) cudaFree(v);
+    if (st) return st;
     if (e != cudaSuccess) return fail(ctx, UFVC_ERR_CUDA, cudaGetErrorString(e));
     return UFVC_OK;
 }
@@ -665,7 +739,36 @@ extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int w
     ufvc_status st = get_plan(ctx, width, height, true, &p);
     if (st) return st;
 
-    run_decoders(ctx, p, d_yhat, d_frames, OUT_PS_FINAL_F32, s);
+    if (ctx->cfg.precision == UFVC_FP32) {
+        RUN(run_decoders(ctx, p, d_yhat, d_frames, OUT_PS_FINAL_F32, s));
+    } else {
+        launch_f32_to_bf16(d_yhat, p->ny, p->yhat_bf, s);
+        RUN(run_decoders(ctx, p, p->yhat_bf, d_frames, OUT_PS_FINAL_F32, s));
+    }
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, int W, int stride, int act,
+                                       int mode, void* d_out, int out_h, int out_w, void* stream) {
+    if (!ctx || !d_in || !d_out || layer < 0 || layer >= L_NENC + D_NDEC * ctx->N || H < 1 || W < 1 ||
+        (stride != 1 && stride != 2) || mode < 0 || mode > 2 || out_h < 1 || out_w < 1)
+        return fail(ctx, UFVC_ERR_ARG, "conv_layer: bad argument");
+    CK(cudaSetDevice(ctx->cfg.device));
+    LayerW L;
+    int g = 0;
+    if (layer < L_NENC) {
+        L = ctx->enc[layer];
+    } else {
+        g = (layer - L_NENC) / D_NDEC;
+        L = ctx->dec[(layer - L_NENC) % D_NDEC];
+        L.w += g * L.w_gs;
+        L.b += g * L.b_gs;
+        if (L.wtc) L.wtc += (size_t)g * L.cout_pad * L.k * L.k * L.cin_tc;
+    }
+    L.groups = 1;
+    const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
+    RUN(conv(ctx, L, d_in, H, W, stride, act, m, d_out, out_h, out_w, (cudaStream_t)stream));
     CK(cudaGetLastError());
     return UFVC_OK;
 }
@@ -723,7 +826,7 @@ extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size
     cudaStream_t s = (cudaStream_t)stream;
     // lane offsets (u64) in r_off, lane word counts (u32) in r_cnt
     RansDecodeJob j{d_in, nbytes, 0, nullptr, d_idx, 0, n, lanes, ctx->r_off, ctx->r_cnt, nullptr,
-                    d_sym, nullptr, nullptr, ctx->d_qstep, nullptr};
+                    d_sym, nullptr, nullptr, nullptr, ctx->d_qstep, nullptr};
 
     prof_begin(ctx, "rans_parse", s);
     launch_rans_parse(j, ctx->d_status, s);

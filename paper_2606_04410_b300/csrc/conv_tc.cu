@@ -1,0 +1,408 @@
+// BF16 implicit-GEMM convolution on the 5th-generation tensor cores (tcgen05 + TMEM), fed by TMA.
+//
+// GEMM view of one conv group: M = output pixels, N = output channels, K = taps x input channels.
+// A CTA tile is 128 output pixels (a TH x TW block of one output image, TW * TH = 128) by BN output
+// channels.  For tap (ky, kx) and a 64-channel chunk, the A tile is the TH x TW block of input pixels
+// shifted by the tap, fetched by one TMA tiled load whose out-of-range rows are zero-filled (the
+// convolution's zero padding).  Stride-2 layers view the NHWC input as (C, 2, W/2, 2, H/2) so that a
+// tap again maps to one TMA box.  The B tile is BN rows (output channels) x 64 K of the K-major
+// weight matrix [group][Cout][k*k*Cin].  Both land 128-byte swizzled in shared memory and feed
+// tcgen05.mma (M=128, N=BN, K=16 per instruction) accumulating in TMEM.
+//
+// Persistent, warp-specialised CTA (one per SM): warp 0 issues TMA loads into a STAGES-deep ring;
+// warp 1 owns TMEM and issues the MMAs; eight epilogue warps drain a double-buffered TMEM
+// accumulator (tcgen05.ld), add bias, apply GELU / residual / pixel shuffle / crop / final frame
+// mapping and store, while the MMAs of the next tile run.  Every mbarrier wait is bounded: on a
+// timeout the kernel records UFVC_ERR_TIMEOUT, all roles stop, in-flight copies and MMAs are waited
+// for (bounded), TMEM is freed and the kernel returns.
+#include "ufvc_internal.h"
+#include "tc_ptx.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cstdio>
+
+namespace ufvc {
+
+constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+
+struct TcArgs {
+    int Ho, Wo, TW, TH, tiles_w, tiles_h, n_tiles, groups, total_tiles;
+    int ksteps, cin_chunks, k, pad, stride, a_grouped;
+    const float* bias;
+    int b_gs;
+    int Cout;
+    int mode, act, out_f32;
+    void* out;
+    long long out_gs;
+    int out_h, out_w, out_c;
+    const __nv_bfloat16* res;
+    long long res_gs;
+    int* err;
+};
+
+__device__ __forceinline__ float gelu_erf_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         bool honour_abort = true) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (honour_abort && *abort_flag) return false;
+        if (clock64() - t0 > kSpinLimit) {
+            *abort_flag = 1;
+            atomicCAS(err, 0, (int)UFVC_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    ptx::tmem_ld16(taddr, v);
+    ptx::tmem_ld16(taddr + 16, v + 16);
+}
+
+// Epilogue of NV (16 or 32) consecutive accumulator columns of one output pixel.
+template <int NV>
+__device__ __forceinline__ void store_cols(const TcArgs& p, int g, int oh, int ow, int co0, float* v) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        const int co = co0 + i;
+        v[i] += (co < p.Cout) ? __ldg(p.bias + (size_t)g * p.b_gs + co) : 0.0f;
+        if (p.act) v[i] = gelu_erf_tc(v[i]);
+    }
+    if (p.mode == OUT_NHWC) {
+        if (co0 >= p.Cout) return;
+        const size_t o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c + co0;
+        if (p.out_f32) {
+            float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(p.out) + o);
+#pragma unroll
+            for (int i = 0; i < NV / 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            return;
+        }
+        if (p.res) {
+            const uint4* r = reinterpret_cast<const uint4*>(p.res + (size_t)g * p.res_gs +
+                                                            ((size_t)oh * p.out_w + ow) * p.out_c + co0);
+#pragma unroll
+            for (int i = 0; i < NV / 8; ++i) {
+                uint4 u = r[i];
+                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[8 * i + j] += __bfloat162float(h[j]);
+            }
+        }
+        uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.out) + o);
+#pragma unroll
+        for (int i = 0; i < NV / 8; ++i)
+            d[i] = make_uint4(pack_bf16(v[8 * i], v[8 * i + 1]), pack_bf16(v[8 * i + 2], v[8 * i + 3]),
+                              pack_bf16(v[8 * i + 4], v[8 * i + 5]), pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+        return;
+    }
+    // pixel shuffle x2: column co -> channel co/4 at sub-pixel (dy, dx) = ((co>>1)&1, co&1)
+    const int cb = co0 >> 2;
+    constexpr int NC = NV / 4;  // output channels covered
+#pragma unroll
+    for (int sub = 0; sub < 4; ++sub) {
+        const int y = 2 * oh + (sub >> 1), x = 2 * ow + (sub & 1);
+        if (y >= p.out_h || x >= p.out_w) continue;
+        const size_t o = (size_t)g * p.out_gs + ((size_t)y * p.out_w + x) * p.out_c + cb;
+        if (p.mode == OUT_PS) {
+            if (cb >= p.out_c) continue;
+            uint32_t w[NC / 2];
+#pragma unroll
+            for (int j = 0; j < NC / 2; ++j) w[j] = pack_bf16(v[4 * (2 * j) + sub], v[4 * (2 * j + 1) + sub]);
+            if constexpr (NC == 8) {
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.out) + o) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(p.out) + o) = make_uint2(w[0], w[1]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                if (cb + j >= p.out_c) break;
+                const float f = fminf(fmaxf(0.5f + v[4 * j + sub], 0.0f), 1.0f);
+                if (p.mode == OUT_PS_FINAL_F32)
+                    reinterpret_cast<float*>(p.out)[o + j] = f;
+                else
+                    reinterpret_cast<uint8_t*>(p.out)[o + j] = (uint8_t)rintf(f * 255.0f);
+            }
+        }
+    }
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p) {
+    constexpr int A_BYTES = 128 * 128;
+    constexpr int B_BYTES = BN * 128;
+    constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
+    constexpr int CHUNK = BN < 32 ? 16 : 32;  // accumulator columns per tcgen05.ld round
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + STAGES * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(&tfull[a], 1);
+            ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
+        }
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int tiles_m = p.tiles_w * p.tiles_h;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int it = 0;
+            uint32_t last_par[STAGES];
+            bool used[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+                const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
+                const int h0 = (mt / p.tiles_w) * p.TH, w0 = (mt % p.tiles_w) * p.TW;
+                const int ag = p.a_grouped ? g : 0;
+                for (int ks = 0; ks < p.ksteps; ++ks, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) { ok = false; break; }
+                    ptx::mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    const int tap = ks / p.cin_chunks, c0 = (ks - tap * p.cin_chunks) * 64;
+                    const int ky = tap / p.k, kx = tap - ky * p.k;
+                    if (p.stride == 1) {
+                        ptx::tma_load_4d(sA + s * A_BYTES, &tmA, &full[s], c0, w0 + kx - p.pad, h0 + ky - p.pad, ag);
+                    } else {
+                        const int tx = kx - p.pad, ty = ky - p.pad;
+                        const int wp = tx & 1, hp = ty & 1;
+                        ptx::tma_load_5d(sA + s * A_BYTES, &tmA, &full[s], c0, wp, w0 + ((tx - wp) >> 1), hp,
+                                         h0 + ((ty - hp) >> 1));
+                    }
+                    ptx::tma_load_3d(sB + s * B_BYTES, &tmB, &full[s], ks * 64, nt * BN, g);
+                    used[s] = true;
+                    last_par[s] = ph;
+                }
+            }
+            // make sure no copy is still writing shared memory when the CTA exits
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s)
+                if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_bf16(BN);
+            int it = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x, ++tl) {
+                const int acc = tl & 1, use = tl >> 1;
+                if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + acc * BN;
+                for (int ks = 0; ks < p.ksteps; ++ks, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!wait_bar(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB + s * B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32), idesc,
+                                     (ks | kk) != 0);
+                    ptx::mma_commit(&empty[s]);
+                }
+                if (ok) ptx::mma_commit(&tfull[acc]);
+            }
+            // all issued MMAs complete before TMEM is released
+            ptx::mma_commit(drain);
+            wait_bar(drain, 0, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue warps
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2;       // which half of the BN columns
+        const int row = q * 32 + lane;
+        int tl = 0;
+        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++tl) {
+            const int acc = tl & 1, use = tl >> 1;
+            if (!wait_bar(&tfull[acc], use & 1, abort_flag, p.err)) break;
+            ptx::tc_fence_after();
+            const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
+            const int oh = (mt / p.tiles_w) * p.TH + row / p.TW, ow = (mt % p.tiles_w) * p.TW + row % p.TW;
+            const bool valid = oh < p.Ho && ow < p.Wo;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
+            constexpr int PER = (BN / 2 + CHUNK - 1) / CHUNK * CHUNK;  // columns per half, CHUNK-rounded
+            const int c_begin = half * PER;
+#pragma unroll 1
+            for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
+                float v[CHUNK];
+                if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
+                if (valid) store_cols<CHUNK>(p, g, oh, ow, nt * BN + c, v);
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&tempty[acc]);
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+// The driver's tensor-map encoder, resolved through the runtime so that the library itself does not
+// link libcuda (it must load on machines without a GPU driver).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+static bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                       const cuuint32_t* box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static void pick_tile(int Ho, int Wo, int* TW, int* TH) {
+    long long best = -1;
+    for (int tw = 128; tw >= 8; tw >>= 1) {
+        const int th = 128 / tw;
+        const long long cost = (long long)((Wo + tw - 1) / tw) * tw * ((Ho + th - 1) / th) * th;
+        if (best < 0 || cost < best) { best = cost; *TW = tw; *TH = th; }
+    }
+}
+
+template <int BN, int STAGES>
+static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
+    const int smem = STAGES * (128 * 128 + BN * 128) + 1024 + 256;
+    static int configured_smem = 0;
+    if (configured_smem != smem) {
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = smem;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int grid = args.total_tiles < sms ? args.total_tiles : sms;
+    conv_tc_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(a, b, args);
+    return cudaGetLastError();
+}
+
+// d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
+// returns a CUDA error or cudaSuccess; UFVC argument problems return cudaErrorInvalidValue.
+cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
+    if (d.Cin % 64 != 0 || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
+        return cudaErrorInvalidValue;
+    const int pad = d.k / 2;
+    const int Ho = (d.H + 2 * pad - d.k) / d.stride + 1, Wo = (d.W + 2 * pad - d.k) / d.stride + 1;
+    int BN = d.cout_pad >= 256 ? 256 : d.cout_pad;
+    if (d.cout_pad % BN != 0 || !(BN == 16 || BN == 64 || BN == 128 || BN == 192 || BN == 256))
+        return cudaErrorInvalidValue;
+    TcArgs a{};
+    pick_tile(Ho, Wo, &a.TW, &a.TH);
+    a.Ho = Ho; a.Wo = Wo;
+    a.tiles_w = (Wo + a.TW - 1) / a.TW;
+    a.tiles_h = (Ho + a.TH - 1) / a.TH;
+    a.n_tiles = d.cout_pad / BN;
+    a.groups = d.groups;
+    a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
+    a.cin_chunks = d.Cin / 64;
+    a.ksteps = d.k * d.k * a.cin_chunks;
+    a.k = d.k; a.pad = pad; a.stride = d.stride; a.a_grouped = d.in_gs != 0;
+    a.bias = d.b; a.b_gs = (int)d.b_gs; a.Cout = d.Cout;
+    a.mode = d.mode; a.act = d.act; a.out_f32 = d.out_f32;
+    a.out = d.out; a.out_gs = d.out_gs; a.out_h = d.out_h; a.out_w = d.out_w;
+    a.out_c = (d.mode == OUT_NHWC) ? d.Cout : d.Cout / 4;
+    if (d.mode == OUT_NHWC && d.out_c_stride) a.out_c = d.out_c_stride;
+    a.res = reinterpret_cast<const __nv_bfloat16*>(d.res); a.res_gs = d.res_gs;
+    a.err = d.err;
+
+    CUtensorMap ma, mb;
+    const cuuint64_t esz = 2;
+    bool ok;
+    if (d.stride == 1) {
+        const int G = a.a_grouped ? d.groups : 1;
+        cuuint64_t dims[4] = {(cuuint64_t)d.Cin, (cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)G};
+        cuuint64_t str[3] = {d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz, (cuuint64_t)d.H * d.W * d.Cin * esz};
+        if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
+        cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+        ok = encode_map(&ma, d.in, 4, dims, str, box);
+    } else {
+        cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
+        cuuint64_t str[4] = {d.Cin * esz, 2 * d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz,
+                             2ull * d.W * d.Cin * esz};
+        cuuint32_t box[5] = {64, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
+        ok = encode_map(&ma, d.in, 5, dims, str, box);
+    }
+    if (!ok) return cudaErrorInvalidValue;
+    {
+        const cuuint64_t K = (cuuint64_t)d.k * d.k * d.Cin;
+        cuuint64_t dims[3] = {K, (cuuint64_t)d.cout_pad, (cuuint64_t)d.groups};
+        cuuint64_t str[2] = {K * esz, K * d.cout_pad * esz};
+        cuuint32_t box[3] = {64, (cuuint32_t)BN, 1};
+        if (!encode_map(&mb, d.wtc, 3, dims, str, box)) return cudaErrorInvalidValue;
+    }
+    switch (BN) {
+        case 16: return launch_bn<16, 8>(ma, mb, a, s);
+        case 64: return launch_bn<64, 8>(ma, mb, a, s);
+        case 128: return launch_bn<128, 6>(ma, mb, a, s);
+        case 192: return launch_bn<192, 5>(ma, mb, a, s);
+        default: return launch_bn<256, 4>(ma, mb, a, s);
+    }
+}
+
+}  // namespace ufvc

@@ -42,6 +42,32 @@ void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int
     pack_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, Cp, x);
 }
 
+// bf16 variant for the tensor-core path: one thread per (pixel, 8-channel group), 16-byte stores
+__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int Cp,
+                                 __nv_bfloat16* __restrict__ x) {
+    const int groups = Cp / 8;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)Hp * Wp * groups) return;
+    const size_t pix = i / groups;
+    const int c0 = (int)(i % groups) * 8;
+    const int h = (int)(pix / Wp), w = (int)(pix % Wp);
+    const int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int c = c0 + j, n = c / 3;
+        const float f = (n < N) ? frames[(((size_t)n * H + sh) * W + sw) * 3 + (c - 3 * n)] / 255.0f : 0.0f;
+        v[j] = __float2bfloat16_rn(f);
+    }
+    *reinterpret_cast<uint4*>(x + pix * Cp + c0) = *reinterpret_cast<const uint4*>(v);
+}
+
+void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
+                      cudaStream_t s) {
+    const size_t n = (size_t)Hp * Wp * (Cp / 8);
+    pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, Cp, x);
+}
+
 // ------------------------------------------------------------------------------------------------
 // z^ quantisation and per-channel index.  iz[c] = #{k : S_c > T_k}, S_c = sum z^^2 (exact integer),
 // T_k = floor(npos * exp(2 t_k)) precomputed on the host in FP64: S_c > npos e^{2 t_k} <=>
@@ -133,6 +159,15 @@ __global__ void i16_to_f32_kernel(const int16_t* a, size_t n, float* out) {
 
 void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s) {
     i16_to_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
+}
+
+__global__ void f32_to_bf16_kernel(const float* a, size_t n, __nv_bfloat16* out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(a[i]);
+}
+
+void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s) {
+    f32_to_bf16_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -345,7 +380,7 @@ __global__ void rans_decode_kernel(const RansDecodeJob J, const uint32_t* __rest
     const size_t cnt = (size_t)lane < n ? (n - lane + K - 1) / K : 0;
     const uint16_t* wp = reinterpret_cast<const uint16_t*>(J.bits + J.lane_off[lane]);
     const uint32_t words = J.lane_words[lane];
-    const float q = J.yhat ? J.qstep_all[*J.qp_dev] : 0.0f;
+    const float q = (J.yhat || J.yhat_bf16) ? J.qstep_all[*J.qp_dev] : 0.0f;
     uint32_t x = ((uint32_t)wp[0] << 16) | wp[1];
     uint32_t r = 2;
     for (size_t m = 0; m < cnt; ++m) {
@@ -372,7 +407,11 @@ __global__ void rans_decode_kernel(const RansDecodeJob J, const uint32_t* __rest
         }
         const int sym = lo - kRmax;
         if (J.sym) J.sym[i] = (int16_t)sym;
-        if (J.yhat) J.yhat[i] = __fadd_rn(__fmul_rn((float)sym, q), J.mu[i]);
+        if (J.yhat || J.yhat_bf16) {
+            const float yv = __fadd_rn(__fmul_rn((float)sym, q), J.mu[i]);
+            if (J.yhat) J.yhat[i] = yv;
+            if (J.yhat_bf16) J.yhat_bf16[i] = __float2bfloat16_rn(yv);
+        }
     }
     if (x != kRansL || r != words) set_status(status, UFVC_ERR_CORRUPT);
 }

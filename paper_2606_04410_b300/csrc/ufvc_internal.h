@@ -70,10 +70,18 @@ struct ConvDesc {
     float* out2 = nullptr;      // channels >= split go to out2 (NHWC with Cout - split channels)
     int split = 0;
     int groups = 1;
-    int out_bf16 = 0;           // tensor-core path: store bf16 instead of float
+    // tensor-core path
+    const void* wtc = nullptr;  // bf16 [groups][cout_pad][k*k*Cin] (K-major)
+    int cout_pad = 0;           // Cout rounded up to the N tile
+    int out_f32 = 0;            // NHWC output stored as float (else bf16)
+    int out_c_stride = 0;       // NHWC output channel count if different from Cout
+    int* err = nullptr;         // device status word (bounded-wait timeouts)
 };
 
 void launch_conv_simt(const ConvDesc& d, cudaStream_t s);
+cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
+void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
+                      cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // Elementwise / entropy kernels
@@ -87,6 +95,7 @@ void launch_quantize(const float* y, const float* mu, const float* logsig, size_
 void launch_scale_index(const float* logsig, size_t n, const float* thr_all, const int* qp_dev, uint8_t* idx,
                         cudaStream_t s);
 void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s);
+void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s);
 
 // rANS: a "section job" describes one section of one stream
 struct RansSection {
@@ -124,6 +133,7 @@ struct RansDecodeJob {
     uint64_t* next_off;       // device: byte offset just past this section
     int16_t* sym;             // output symbols (or nullptr)
     float* yhat;              // output y^ = r^ q + mu (or nullptr)
+    __nv_bfloat16* yhat_bf16; // output y^ rounded to bf16 (or nullptr)
     const float* mu;
     const float* qstep_all;   // [64]
     const int* qp_dev;

@@ -30,7 +30,7 @@ EXPORTS = [
     "ufvc_max_bitstream_bytes", "ufvc_encode_chunk", "ufvc_decode_chunk", "ufvc_decode_chunk_f32",
     "ufvc_encode_chunk_host", "ufvc_decode_chunk_host", "ufvc_sync_status", "ufvc_encode_stages",
     "ufvc_hyper_synthesis", "ufvc_quantize", "ufvc_synthesize", "ufvc_rans_encode", "ufvc_rans_decode",
-    "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error",
+    "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error", "ufvc_conv_layer",
 ]
 
 
@@ -63,6 +63,7 @@ _sigs = {
     "ufvc_set_profiling": (_i, [_vp, _i]),
     "ufvc_get_profile": (_i, [_vp, _vp, _vp, _vp, _i, C.POINTER(_i)]),
     "ufvc_last_error": (C.c_char_p, [_vp]),
+    "ufvc_conv_layer": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -239,6 +240,14 @@ class Codec:
         self._check(lib.ufvc_rans_decode(self.h, _ptr(data), int(nbytes), _ptr(idx), n, lanes, _ptr(sym),
                                          _stream(stream)), "rans_decode")
         return sym[:n]
+
+    def conv_layer(self, layer: int, x: torch.Tensor, stride: int, act: int, mode: int, out: torch.Tensor,
+                   stream=None) -> torch.Tensor:
+        H, W, _ = x.shape
+        oh, ow = out.shape[0], out.shape[1]
+        self._check(lib.ufvc_conv_layer(self.h, layer, _ptr(x), H, W, stride, act, mode, _ptr(out), oh, ow,
+                                        _stream(stream)), "conv_layer")
+        return out
 
     def get_tables(self, qp: int = 32):
         freq = np.empty((64, 511), np.uint32)
