@@ -41,7 +41,7 @@ struct Plan {
     uint32_t *cnt_z = nullptr, *cnt_y = nullptr;
     uint64_t *off_ws = nullptr, *zthr = nullptr;
     // decoder buffers
-    int16_t* dzhat = nullptr;
+    int16_t *dzhat = nullptr, *drhat = nullptr;
     uint8_t *diz = nullptr, *didx = nullptr;
     int* qp_dev = nullptr;
     uint64_t *lo_z = nullptr, *lo_y = nullptr, *next_z = nullptr, *next_y = nullptr;
@@ -68,6 +68,7 @@ struct ufvc_ctx {
     int N = 0;
     HostTables tabs;
     uint32_t* d_packed = nullptr;
+    uint16_t* d_coarse = nullptr;
     float *d_thr = nullptr, *d_qstep = nullptr, *d_qinv = nullptr;
     int* d_status = nullptr;
     LayerW enc[L_NENC];
@@ -240,6 +241,7 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         AL(p->dls, p->ny);
         AL(p->yhat, p->ny);
         AL(p->yhat_bf, p->ny);
+        AL(p->drhat, p->ny);
         const size_t n1 = (size_t)N * 4 * p->Hy * p->Wy * a.cd1;
         const size_t n2 = (size_t)N * 16 * p->Hy * p->Wy * a.cd2;
         const size_t n3 = (size_t)N * 64 * p->Hy * p->Wy * a.cd2;
@@ -327,7 +329,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     for (auto& kv : ctx->plans) free_plan(kv.second);
     for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
     for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
-    cudaFree(ctx->d_packed); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
+    cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
     cudaFree(ctx->d_status);
     cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
     cudaFree(ctx->st_frames); cudaFree(ctx->st_bits); cudaFree(ctx->st_nbytes);
@@ -355,6 +357,9 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
     build_host_tables(ctx->tabs);
     ufvc_status st;
     if ((st = dalloc(ctx, nullptr, &ctx->d_packed, ctx->tabs.packed.size())) != UFVC_OK) return bail(st);
+    if ((st = dalloc(ctx, nullptr, &ctx->d_coarse, ctx->tabs.coarse.size())) != UFVC_OK) return bail(st);
+    if (cudaMemcpy(ctx->d_coarse, ctx->tabs.coarse.data(), ctx->tabs.coarse.size() * 2, cudaMemcpyHostToDevice))
+        return bail(UFVC_ERR_CUDA);
     if ((st = dalloc(ctx, nullptr, &ctx->d_thr, ctx->tabs.thr.size())) != UFVC_OK) return bail(st);
     if ((st = dalloc(ctx, nullptr, &ctx->d_qstep, 64)) != UFVC_OK) return bail(st);
     if ((st = dalloc(ctx, nullptr, &ctx->d_qinv, 64)) != UFVC_OK) return bail(st);
@@ -571,22 +576,24 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
                         p->diz, ctx->d_status, s);
     const bool fp32 = ctx->cfg.precision == UFVC_FP32;
     RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
-                     p->dzhat, nullptr, nullptr, nullptr, ctx->d_qstep, p->qp_dev};
+                     p->dzhat};
     RansDecodeJob jy{d_bits, nbytes, 0, p->next_z, p->didx, 0, p->ny, ctx->cfg.lanes, p->lo_y, p->lw_y, p->next_y,
-                     nullptr, fp32 ? p->yhat : nullptr, fp32 ? nullptr : p->yhat_bf, p->dmu, ctx->d_qstep, p->qp_dev};
+                     p->drhat};
     launch_rans_parse(jz, ctx->d_status, s);
     launch_rans_parse_expect(jy, nbytes, ctx->d_status, s);
     prof_end(ctx, s, 3);
     prof_begin(ctx, "rans_decode_z", s);
-    launch_rans_decode(jz, ctx->d_packed, ctx->d_status, s);
+    launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
     prof_end(ctx, s, 1);
     RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s));
     prof_begin(ctx, "scale_index", s);
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode_y", s);
-    launch_rans_decode(jy, ctx->d_packed, ctx->d_status, s);
-    prof_end(ctx, s, 1);
+    launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
+    launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
+                   fp32 ? nullptr : p->yhat_bf, s);
+    prof_end(ctx, s, 2);
     RUN(run_decoders(ctx, p, fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf, d_frames, final_mode, s));
     CK(cudaGetLastError());
     return UFVC_OK;
@@ -826,13 +833,13 @@ extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size
     cudaStream_t s = (cudaStream_t)stream;
     // lane offsets (u64) in r_off, lane word counts (u32) in r_cnt
     RansDecodeJob j{d_in, nbytes, 0, nullptr, d_idx, 0, n, lanes, ctx->r_off, ctx->r_cnt, nullptr,
-                    d_sym, nullptr, nullptr, nullptr, ctx->d_qstep, nullptr};
+                    d_sym};
 
     prof_begin(ctx, "rans_parse", s);
     launch_rans_parse(j, ctx->d_status, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode", s);
-    launch_rans_decode(j, ctx->d_packed, ctx->d_status, s);
+    launch_rans_decode(j, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
     prof_end(ctx, s, 1);
     CK(cudaGetLastError());
     return UFVC_OK;

@@ -47,13 +47,15 @@ __device__ __forceinline__ void store_out(const ConvDesc& d, int g, int oh, int 
     }
 }
 
-template <int BN>
+template <int BM, int BN>
 __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho, int Wo) {
-    constexpr int BM = 128, BK = 16;
+    constexpr int BK = 16;
     constexpr int TN = BN / 4;    // threads along N, 4 output channels each
     constexpr int TM = 256 / TN;  // threads along M
-    constexpr int PM = BM / TM;   // pixels per thread: 8 (BN = 64) or 2 (BN = 16)
+    constexpr int PM = BM / TM;   // pixels per thread: 8 (128 x 64), 2 (128 x 16 or 32 x 64)
+    constexpr int RA = (BM * BK / 4 + 255) / 256;  // float4 A loads per thread
     static_assert(PM == 8 || PM == 2, "tile");
+    static_assert(PM == 2 || BM == 128, "interleaved mapping needs BM = 128");
     __shared__ __align__(16) float As[2][BK][BM + 4];  // +4: fewer bank conflicts on the transposed store
     __shared__ __align__(16) float Bs[2][BK][BN];
 
@@ -66,13 +68,13 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho
     const int tid = threadIdx.x;
     const int H = d.H, W = d.W, Cin = d.Cin, Cout = d.Cout, k = d.k, s = d.stride, p = d.k / 2;
 
-    // A loads: 2 float4 per thread (pixel q >> 2, channels 4 * (q & 3) .. +3 of the 16-channel chunk)
-    int a_oh[2], a_ow[2];
-    bool a_ok[2];
+    // A loads: RA float4 per thread (pixel q >> 2, channels 4 * (q & 3) .. +3 of the 16-channel chunk)
+    int a_oh[RA], a_ow[RA];
+    bool a_ok[RA];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < RA; ++r) {
         const int m = m0 + ((tid + r * 256) >> 2);
-        a_ok[r] = m < M;
+        a_ok[r] = ((tid + r * 256) >> 2) < BM && m < M;
         a_oh[r] = a_ok[r] ? m / Wo : 0;
         a_ow[r] = a_ok[r] ? m - a_oh[r] * Wo : 0;
     }
@@ -83,13 +85,13 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho
     const int b_co = n0 + b_cg * 4;
 
     const int nck = Cin / BK, nsteps = k * k * nck;
-    float4 ra[2], rb;
+    float4 ra[RA], rb;
 
     auto load_regs = [&](int step) {
         const int tap = step / nck, c0 = (step - tap * nck) * BK;
         const int ky = tap / k, kx = tap - ky * k;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < RA; ++r) {
             const int ih = a_oh[r] * s + ky - p, iw = a_ow[r] * s + kx - p;
             if (a_ok[r] && ih >= 0 && ih < H && iw >= 0 && iw < W)
                 ra[r] = *reinterpret_cast<const float4*>(in + ((size_t)ih * W + iw) * Cin + c0 + a_cg * 4);
@@ -105,8 +107,9 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho
     };
     auto store_smem = [&](int buf) {
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < RA; ++r) {
             const int pix = (tid + r * 256) >> 2;
+            if (pix >= BM) continue;
             As[buf][a_cg * 4 + 0][pix] = ra[r].x;
             As[buf][a_cg * 4 + 1][pix] = ra[r].y;
             As[buf][a_cg * 4 + 2][pix] = ra[r].z;
@@ -176,10 +179,18 @@ void launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
     const int M = Ho * Wo;
     if (d.Cout <= 16) {
         dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
-        conv_simt_kernel<16><<<grid, 256, 0, st>>>(d, Ho, Wo);
+        conv_simt_kernel<128, 16><<<grid, 256, 0, st>>>(d, Ho, Wo);
+        return;
+    }
+    const long long ctas128 = (long long)((M + 127) / 128) * ((d.Cout + 63) / 64) * d.groups;
+    if (ctas128 < 2 * 148) {
+        // small layers (hyper-analysis / hyper-synthesis): 32-pixel tiles fill the GPU; the per-element
+        // reduction order is the same as with 128-pixel tiles
+        dim3 grid((M + 31) / 32, (d.Cout + 63) / 64, d.groups);
+        conv_simt_kernel<32, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
     } else {
         dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
-        conv_simt_kernel<64><<<grid, 256, 0, st>>>(d, Ho, Wo);
+        conv_simt_kernel<128, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
     }
 }
 

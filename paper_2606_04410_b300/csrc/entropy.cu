@@ -9,6 +9,7 @@
 //                    to lane i mod K; 32-bit state in [2^16, 2^32), 16-bit probabilities, 16-bit words,
 //                    at most one renormalisation word per symbol.
 #include "ufvc_internal.h"
+#include "tc_ptx.h"
 
 #include <cub/block/block_scan.cuh>
 
@@ -42,30 +43,42 @@ void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int
     pack_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, Cp, x);
 }
 
-// bf16 variant for the tensor-core path: one thread per (pixel, 8-channel group), 16-byte stores
-__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int Cp,
+__device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// bf16 variant for the tensor-core path (Cp = 64, N <= 16): one thread per pixel gathers its N RGB
+// triplets and writes the 64-channel row with 16-byte stores
+__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp,
                                  __nv_bfloat16* __restrict__ x) {
-    const int groups = Cp / 8;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)Hp * Wp * groups) return;
-    const size_t pix = i / groups;
-    const int c0 = (int)(i % groups) * 8;
+    const size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= (size_t)Hp * Wp) return;
     const int h = (int)(pix / Wp), w = (int)(pix % Wp);
     const int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
-    __align__(16) __nv_bfloat16 v[8];
+    const size_t plane = (size_t)H * W * 3, at = ((size_t)sh * W + sw) * 3;
+    float v[48];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = c0 + j, n = c / 3;
-        const float f = (n < N) ? frames[(((size_t)n * H + sh) * W + sw) * 3 + (c - 3 * n)] / 255.0f : 0.0f;
-        v[j] = __float2bfloat16_rn(f);
+    for (int n = 0; n < 16; ++n) {
+        const bool live = n < N;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[3 * n + c] = live ? __ldg(frames + n * plane + at + c) / 255.0f : 0.0f;
     }
-    *reinterpret_cast<uint4*>(x + pix * Cp + c0) = *reinterpret_cast<const uint4*>(v);
+    uint32_t packed[32];
+#pragma unroll
+    for (int j = 0; j < 24; ++j) packed[j] = pack_bf16_pair(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+    for (int j = 24; j < 32; ++j) packed[j] = 0u;
+    uint4* o = reinterpret_cast<uint4*>(x + pix * 64);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
 }
 
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s) {
-    const size_t n = (size_t)Hp * Wp * (Cp / 8);
-    pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, Cp, x);
+    (void)Cp;  // always 64 on this path (3N <= 48 < 64)
+    const size_t n = (size_t)Hp * Wp;
+    pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, x);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -177,10 +190,56 @@ void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream
 // ------------------------------------------------------------------------------------------------
 struct RansSecPair { RansSection s[2]; int nsec; };
 
-__global__ void rans_encode_kernel(const RansSecPair P, const uint32_t* __restrict__ tables) {
-    extern __shared__ uint32_t tab[];  // [64][511] (freq << 16) | cum
-    for (int i = threadIdx.x; i < kBins * kNsym; i += blockDim.x) tab[i] = tables[i];
+constexpr int kRansThreads = 128;
+constexpr int kTabBytes = kBins * kNsym * 4;       // 130816, a multiple of 16
+constexpr int kCoarseBytes = kBins * kCoarse * 2;  // 65536
+constexpr int kPF = 16;                            // per-lane prefetch depth (symbols / table indices)
+constexpr long long kLoadSpin = 4000000000LL;      // ~2 s bounded wait for the table copy
+
+// The packed tables (and optionally the coarse decoding index) land in shared memory by TMA bulk copies
+// issued by one thread; every thread waits on the copy's mbarrier, bounded in time.  Returns false (and
+// records UFVC_ERR_TIMEOUT) if the copy did not complete.
+__device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __restrict__ tables, uint16_t* coarse,
+                                            const uint16_t* __restrict__ coarse_g, uint64_t* bar, int* status) {
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(bar, 1);
+        ptx::fence_mbar_init();
+    }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        ptx::mbar_arrive_expect_tx(bar, kTabBytes + (coarse ? kCoarseBytes : 0));
+        for (int off = 0; off < kTabBytes; off += 32768) {
+            const int n = kTabBytes - off < 32768 ? kTabBytes - off : 32768;
+            ptx::bulk_load(reinterpret_cast<uint8_t*>(tab) + off, reinterpret_cast<const uint8_t*>(tables) + off, n, bar);
+        }
+        if (coarse)
+            for (int off = 0; off < kCoarseBytes; off += 32768)
+                ptx::bulk_load(reinterpret_cast<uint8_t*>(coarse) + off,
+                               reinterpret_cast<const uint8_t*>(coarse_g) + off, 32768, bar);
+    }
+    const long long t0 = clock64();
+    while (!ptx::mbar_try_wait(bar, 0)) {
+        if (clock64() - t0 > kLoadSpin) {
+            set_status(status, UFVC_ERR_TIMEOUT);
+            if (threadIdx.x == 0) {  // the issuing thread waits once more, bounded, for its copies in flight
+                const long long t1 = clock64();
+                while (!ptx::mbar_try_wait(bar, 0) && clock64() - t1 < kLoadSpin) {
+                }
+            }
+            return false;  // (no block barrier here: threads may reach this point at different times)
+        }
+    }
+    return true;
+}
+
+// rANS encode: one thread per lane, lanes of up to two sections in one launch.  Each lane runs its
+// elements backwards (last first) and writes its words backwards into its scratch row, so that the
+// row's tail [cap_lane - words, cap_lane) is the lane stream in decoding order.
+__global__ void __launch_bounds__(kRansThreads) rans_encode_kernel(const RansSecPair P,
+                                                                   const uint32_t* __restrict__ tables) {
+    extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum
+    __shared__ uint64_t bar;
+    if (!load_tables(tab, tables, nullptr, nullptr, &bar, P.s[0].status)) return;
     int lane = blockIdx.x * blockDim.x + threadIdx.x;
     int si = 0;
     if (lane >= P.s[0].K) { lane -= P.s[0].K; si = 1; }
@@ -188,27 +247,49 @@ __global__ void rans_encode_kernel(const RansSecPair P, const uint32_t* __restri
     const RansSection& S = P.s[si];
     if (lane >= S.K) return;
     const size_t n = S.n, K = (size_t)S.K;
-    const size_t cnt = (size_t)lane < n ? (n - lane + K - 1) / K : 0;
+    const long long cnt = (size_t)lane < n ? (long long)((n - lane + K - 1) / K) : 0;
     uint16_t* row = S.scratch + (size_t)lane * S.cap_lane;
     int wp = S.cap_lane;
     uint32_t x = kRansL;
-    for (size_t m = cnt; m-- > 0;) {
-        const size_t i = (size_t)lane + m * K;
-        int t = S.idx_period ? S.idx[i % S.idx_period] : S.idx[i];
-        int v = S.sym[i];
-        if (t >= kBins || v < -kRmax || v > kRmax) {  // caller error: never index outside the tables
-            set_status(S.status, UFVC_ERR_ARG);
-            t = 0;
-            v = 0;
+    // The (table, symbol) pairs of the next kPF elements are fetched while the current kPF are coded,
+    // so the serial state chain does not wait on memory.
+    int tc[kPF], vc[kPF], tn[kPF], vn[kPF];
+    auto fetch = [&](long long mtop, int* td, int* vd) {
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const long long m = mtop - u;
+            td[u] = 0;
+            vd[u] = 0;
+            if (m >= 0) {
+                const size_t i = (size_t)lane + (size_t)m * K;
+                td[u] = S.idx_period ? S.idx[i % S.idx_period] : S.idx[i];
+                vd[u] = S.sym[i];
+            }
         }
-        const uint32_t e = tab[t * kNsym + (v + kRmax)];
-        const uint32_t f = e >> 16, c = e & 0xFFFFu;
-        if (x >= (f << 16)) {  // f << 16 < 2^32 as f <= 65026
-            row[--wp] = (uint16_t)(x & 0xFFFFu);
-            x >>= 16;
+    };
+    fetch(cnt - 1, tc, vc);
+    for (long long mtop = cnt - 1; mtop >= 0; mtop -= kPF) {
+        fetch(mtop - kPF, tn, vn);
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            if (mtop - u < 0) break;
+            int t = tc[u], v = vc[u];
+            if (t >= kBins || v < -kRmax || v > kRmax) {  // caller error: never index outside the tables
+                set_status(S.status, UFVC_ERR_ARG);
+                t = 0;
+                v = 0;
+            }
+            const uint32_t e = tab[t * kNsym + (v + kRmax)];
+            const uint32_t f = e >> 16, c = e & 0xFFFFu;
+            if (x >= (f << 16)) {  // f << 16 < 2^32 as f <= 65026
+                row[--wp] = (uint16_t)(x & 0xFFFFu);
+                x >>= 16;
+            }
+            const uint32_t q = x / f;
+            x = (q << 16) + (x - q * f) + c;
         }
-        const uint32_t q = x / f;
-        x = (q << 16) + (x - q * f) + c;
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) { tc[u] = tn[u]; vc[u] = vn[u]; }
     }
     row[--wp] = (uint16_t)(x & 0xFFFFu);
     row[--wp] = (uint16_t)(x >> 16);
@@ -220,14 +301,12 @@ void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packe
     P.nsec = nsec;
     int total = 0;
     for (int i = 0; i < nsec; ++i) { P.s[i] = secs[i]; total += secs[i].K; }
-    const int smem = kBins * kNsym * 4;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes);
         attr = true;
     }
-    const int threads = 64;
-    rans_encode_kernel<<<(total + threads - 1) / threads, threads, smem, s>>>(P, packed_tables);
+    rans_encode_kernel<<<(total + kRansThreads - 1) / kRansThreads, kRansThreads, kTabBytes, s>>>(P, packed_tables);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -369,10 +448,13 @@ void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, int* st
     rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, status);
 }
 
-__global__ void rans_decode_kernel(const RansDecodeJob J, const uint32_t* __restrict__ tables, int* status) {
-    extern __shared__ uint32_t tab[];
-    for (int i = threadIdx.x; i < kBins * kNsym; i += blockDim.x) tab[i] = tables[i];
-    __syncthreads();
+__global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDecodeJob J,
+                                                                   const uint32_t* __restrict__ tables,
+                                                                   const uint16_t* __restrict__ coarse_g, int* status) {
+    extern __shared__ __align__(16) uint32_t tab[];                      // [64][511] (freq << 16) | cum
+    uint16_t* coarse = reinterpret_cast<uint16_t*>(tab + kBins * kNsym);  // [64][kCoarse]
+    __shared__ uint64_t bar;
+    if (!load_tables(tab, tables, coarse, coarse_g, &bar, status)) return;
     if (*(volatile int*)status != 0) return;
     const int lane = blockIdx.x * blockDim.x + threadIdx.x;
     if (lane >= J.K) return;
@@ -380,51 +462,82 @@ __global__ void rans_decode_kernel(const RansDecodeJob J, const uint32_t* __rest
     const size_t cnt = (size_t)lane < n ? (n - lane + K - 1) / K : 0;
     const uint16_t* wp = reinterpret_cast<const uint16_t*>(J.bits + J.lane_off[lane]);
     const uint32_t words = J.lane_words[lane];
-    const float q = (J.yhat || J.yhat_bf16) ? J.qstep_all[*J.qp_dev] : 0.0f;
     uint32_t x = ((uint32_t)wp[0] << 16) | wp[1];
     uint32_t r = 2;
-    for (size_t m = 0; m < cnt; ++m) {
-        const size_t i = (size_t)lane + m * K;
-        int t = J.idx_period ? J.idx[i % J.idx_period] : J.idx[i];
-        if (t >= kBins) {
-            set_status(status, UFVC_ERR_ARG);
-            t = 0;
+    uint32_t nw = r < words ? wp[r] : 0u;  // next renormalisation word, fetched ahead of its use
+    // table indices of the next kPF symbols are fetched while the current kPF are decoded
+    int tc[kPF], tn[kPF];
+    auto fetch = [&](size_t m0, int* td) {
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const size_t m = m0 + u;
+            td[u] = 0;
+            if (m < cnt) {
+                const size_t i = (size_t)lane + m * K;
+                td[u] = J.idx_period ? J.idx[i % J.idx_period] : J.idx[i];
+            }
         }
-        const uint32_t* T = tab + t * kNsym;
-        const uint32_t slot = x & 0xFFFFu;
-        // largest s with cum(s) <= slot
-        int lo = 0, hi = kNsym - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if ((T[mid] & 0xFFFFu) <= slot) lo = mid; else hi = mid - 1;
+    };
+    fetch(0, tc);
+    for (size_t m0 = 0; m0 < cnt; m0 += kPF) {
+        fetch(m0 + kPF, tn);
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) {
+            const size_t m = m0 + u;
+            if (m >= cnt) break;
+            int t = tc[u];
+            if (t >= kBins) {
+                set_status(status, UFVC_ERR_ARG);
+                t = 0;
+            }
+            const uint32_t* T = tab + t * kNsym;
+            const uint32_t slot = x & 0xFFFFu;
+            // symbol s with cum(s) <= slot < cum(s+1): start at the symbol owning the first slot of the
+            // slot's 128-wide bucket, then step over the (few) symbol boundaries inside the bucket
+            int s = coarse[t * kCoarse + (slot >> kCoarseShift)];
+            while (s < kNsym - 1 && (T[s + 1] & 0xFFFFu) <= slot) ++s;
+            const uint32_t e = T[s];
+            x = (e >> 16) * (x >> 16) + slot - (e & 0xFFFFu);
+            if (x < kRansL) {
+                x = (x << 16) | nw;
+                ++r;
+                nw = r < words ? wp[r] : 0u;
+            }
+            J.sym[(size_t)lane + m * K] = (int16_t)(s - kRmax);
         }
-        const uint32_t e = T[lo];
-        x = (e >> 16) * (x >> 16) + slot - (e & 0xFFFFu);
-        if (x < kRansL) {
-            const uint32_t w = r < words ? wp[r] : 0u;
-            x = (x << 16) | w;
-            ++r;
-        }
-        const int sym = lo - kRmax;
-        if (J.sym) J.sym[i] = (int16_t)sym;
-        if (J.yhat || J.yhat_bf16) {
-            const float yv = __fadd_rn(__fmul_rn((float)sym, q), J.mu[i]);
-            if (J.yhat) J.yhat[i] = yv;
-            if (J.yhat_bf16) J.yhat_bf16[i] = __float2bfloat16_rn(yv);
-        }
+#pragma unroll
+        for (int u = 0; u < kPF; ++u) tc[u] = tn[u];
     }
     if (x != kRansL || r != words) set_status(status, UFVC_ERR_CORRUPT);
 }
 
-void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, int* status, cudaStream_t s) {
-    const int smem = kBins * kNsym * 4;
+void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
+                        cudaStream_t s) {
+    const int smem = kTabBytes + kCoarseBytes;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(rans_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    const int threads = 64;
-    rans_decode_kernel<<<(j.K + threads - 1) / threads, threads, smem, s>>>(j, packed_tables, status);
+    rans_decode_kernel<<<(j.K + kRansThreads - 1) / kRansThreads, kRansThreads, smem, s>>>(j, packed_tables, coarse,
+                                                                                           status);
+}
+
+// y^ = r^ q + mu (explicitly rounded ops), to float and / or bf16; q from the parsed rate
+__global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __restrict__ mu, size_t n,
+                               const float* __restrict__ qstep_all, const int* __restrict__ qp_dev,
+                               float* __restrict__ yf, __nv_bfloat16* __restrict__ yb) {
+    const float q = qstep_all[*qp_dev];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = __fadd_rn(__fmul_rn((float)rhat[i], q), mu[i]);
+        if (yf) yf[i] = v;
+        if (yb) yb[i] = __float2bfloat16_rn(v);
+    }
+}
+
+void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s) {
+    dequant_kernel<<<grid_for(n, 256), 256, 0, s>>>(rhat, mu, n, qstep_all, qp_dev, yf, yb);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -62,6 +62,17 @@ void build_host_tables(HostTables& t) {
         for (int i = 0; i < kNsym; ++i) c[i + 1] = c[i] + f[i];
         for (int i = 0; i < kNsym; ++i) t.packed[k * kNsym + i] = (f[i] << 16) | c[i];
     }
+    // decoder index: for bucket b, the symbol whose interval [cum_s, cum_s + f_s) holds slot b << shift
+    t.coarse.assign(kBins * kCoarse, 0);
+    for (int k = 0; k < kBins; ++k) {
+        const uint32_t* c = &t.cum[k * (kNsym + 1)];
+        int s = 0;
+        for (int b = 0; b < kCoarse; ++b) {
+            const uint32_t slot = (uint32_t)b << kCoarseShift;
+            while (c[s + 1] <= slot) ++s;
+            t.coarse[k * kCoarse + b] = (uint16_t)s;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -19,6 +19,8 @@ constexpr int kRmax = 255;         // |r^| <= 255
 constexpr int kNsym = 511;         // symbols -255..255
 constexpr uint32_t kProbM = 1u << 16;
 constexpr uint32_t kRansL = 1u << 16;
+constexpr int kCoarseShift = 7;                    // decoder slot -> symbol index: 128-slot buckets
+constexpr int kCoarse = 1 << (16 - kCoarseShift);  // 512 buckets per table
 
 // ---------------------------------------------------------------------------------------------
 // Host-side tables (FP64 construction, built once per context)
@@ -31,6 +33,7 @@ struct HostTables {
     std::vector<float> qstep;     // [64]  q(qp) as float
     std::vector<float> qinv;      // [64]  1/q(qp) as float
     std::vector<double> log_thr;  // [63]  t_k in FP64 (z^ RMS index)
+    std::vector<uint16_t> coarse; // [64][kCoarse]  symbol owning slot b << kCoarseShift
 };
 void build_host_tables(HostTables& t);
 double qstep_fp64(int qp);
@@ -131,17 +134,16 @@ struct RansDecodeJob {
     uint64_t* lane_off;       // [K] byte offsets of each lane stream (from the stream base)
     uint32_t* lane_words;     // [K]
     uint64_t* next_off;       // device: byte offset just past this section
-    int16_t* sym;             // output symbols (or nullptr)
-    float* yhat;              // output y^ = r^ q + mu (or nullptr)
-    __nv_bfloat16* yhat_bf16; // output y^ rounded to bf16 (or nullptr)
-    const float* mu;
-    const float* qstep_all;   // [64]
-    const int* qp_dev;
+    int16_t* sym;             // output symbols
 };
 void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s);
 // as launch_rans_parse, and the section must end exactly at byte `expect_end` of the stream
 void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, int* status, cudaStream_t s);
-void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, int* status, cudaStream_t s);
+void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
+                        cudaStream_t s);
+// y^ = r^ q + mu with q = qstep_all[*qp_dev]; yf and / or yb may be null
+void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s);
 
 // Container header
 void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,
