@@ -191,6 +191,23 @@ void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream
 struct RansSecPair { RansSection s[2]; int nsec; };
 
 constexpr int kRansThreads = 128;
+
+// Loads issued where they stand: the per-lane prefetches below must not be moved down next to their use.
+__device__ __forceinline__ int ld_early_u8(const uint8_t* p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return (int)v;
+}
+__device__ __forceinline__ int ld_early_s16(const int16_t* p) {
+    short v;
+    asm volatile("ld.global.nc.s16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (int)v;
+}
+__device__ __forceinline__ uint32_t ld_early_u16(const uint16_t* p) {
+    unsigned short v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return (uint32_t)v;
+}
 constexpr int kTabBytes = kBins * kNsym * 4;       // 130816, a multiple of 16
 constexpr int kCoarseBytes = kBins * kCoarse * 2;  // 65536
 constexpr int kPF = 16;                            // per-lane prefetch depth (symbols / table indices)
@@ -262,8 +279,8 @@ __global__ void __launch_bounds__(kRansThreads) rans_encode_kernel(const RansSec
             vd[u] = 0;
             if (m >= 0) {
                 const size_t i = (size_t)lane + (size_t)m * K;
-                td[u] = S.idx_period ? S.idx[i % S.idx_period] : S.idx[i];
-                vd[u] = S.sym[i];
+                td[u] = ld_early_u8(S.idx + (S.idx_period ? i % S.idx_period : i));
+                vd[u] = ld_early_s16(S.sym + i);
             }
         }
     };
@@ -464,7 +481,9 @@ __global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDec
     const uint32_t words = J.lane_words[lane];
     uint32_t x = ((uint32_t)wp[0] << 16) | wp[1];
     uint32_t r = 2;
-    uint32_t nw = r < words ? wp[r] : 0u;  // next renormalisation word, fetched ahead of its use
+    // the next two renormalisation words, fetched ahead of their use
+    uint32_t nw0 = r < words ? ld_early_u16(wp + r) : 0u;
+    uint32_t nw1 = r + 1 < words ? ld_early_u16(wp + r + 1) : 0u;
     // table indices of the next kPF symbols are fetched while the current kPF are decoded
     int tc[kPF], tn[kPF];
     auto fetch = [&](size_t m0, int* td) {
@@ -474,7 +493,7 @@ __global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDec
             td[u] = 0;
             if (m < cnt) {
                 const size_t i = (size_t)lane + m * K;
-                td[u] = J.idx_period ? J.idx[i % J.idx_period] : J.idx[i];
+                td[u] = ld_early_u8(J.idx + (J.idx_period ? i % J.idx_period : i));
             }
         }
     };
@@ -492,16 +511,23 @@ __global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDec
             }
             const uint32_t* T = tab + t * kNsym;
             const uint32_t slot = x & 0xFFFFu;
-            // symbol s with cum(s) <= slot < cum(s+1): start at the symbol owning the first slot of the
-            // slot's 128-wide bucket, then step over the (few) symbol boundaries inside the bucket
-            int s = coarse[t * kCoarse + (slot >> kCoarseShift)];
-            while (s < kNsym - 1 && (T[s + 1] & 0xFFFFu) <= slot) ++s;
+            // symbol s with cum(s) <= slot < cum(s+1).  It lies between the owners of the first slots of
+            // the slot's 128-wide bucket and of the next bucket; a binary search over that range takes at
+            // most 7 steps (the tails of the tables, where every slot is a symbol, are the worst case).
+            const int b = slot >> kCoarseShift;
+            int s = coarse[t * kCoarse + b];
+            int hi = b + 1 < kCoarse ? coarse[t * kCoarse + b + 1] : kNsym - 1;
+            while (s < hi) {
+                const int mid = (s + hi + 1) >> 1;
+                if ((T[mid] & 0xFFFFu) <= slot) s = mid; else hi = mid - 1;
+            }
             const uint32_t e = T[s];
             x = (e >> 16) * (x >> 16) + slot - (e & 0xFFFFu);
             if (x < kRansL) {
-                x = (x << 16) | nw;
+                x = (x << 16) | nw0;
                 ++r;
-                nw = r < words ? wp[r] : 0u;
+                nw0 = nw1;
+                nw1 = r + 1 < words ? ld_early_u16(wp + r + 1) : 0u;
             }
             J.sym[(size_t)lane + m * K] = (int16_t)(s - kRmax);
         }
