@@ -879,3 +879,13 @@ extern "C" ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, i
     ctx->prof_n = 0;  // entries accumulate over calls until read
     return UFVC_OK;
 }
+
+// ------------------------------------------------------------------------------------------------
+// read-only access to context internals for other translation units of the library
+// ------------------------------------------------------------------------------------------------
+namespace ufvc {
+const uint32_t* ctx_packed_tables(const ufvc_ctx* c) { return c->d_packed; }
+int* ctx_status_word(ufvc_ctx* c) { return c->d_status; }
+int ctx_device(const ufvc_ctx* c) { return c->cfg.device; }
+void ctx_set_error(ufvc_ctx* c, const char* msg) { c->err = msg; }
+}  // namespace ufvc

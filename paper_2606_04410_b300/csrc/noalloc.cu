@@ -1,0 +1,91 @@
+// Allocation-free variant of the rANS section encoder (ufvc_rans_encode_noalloc).
+//
+// ufvc_rans_encode needs scratch memory beyond its inputs and outputs: every lane writes its words into a
+// row of a staging buffer before they are laid out, and the lane word counts and destination offsets
+// live in device memory too.  That entry point allocates the staging buffer with cudaMalloc the first
+// time a size is seen.  Some callers cannot let a library allocate: code that runs while a stream is
+// being captured (allocation is not allowed there), real-time loops where cudaMalloc's implicit device
+// synchronisation would stall other work, and hosts whose device memory is wholly owned by their own
+// pool allocator.  For them this file keeps the scratch in one file-scope __device__ array of fixed
+// size, which every GPU that loads the library holds until the process exits, and the entry point below
+// performs no allocation of any kind.
+#include "ufvc_internal.h"
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kScratchBytes = 24ull << 20;  // 24 MiB per device
+constexpr int kMaxDevices = 64;
+
+// Layout of one call: lane destination offsets (u64 x lanes), lane word counts (u32 x lanes), then the
+// lane rows (u16 x lanes x (n / lanes + 3)), each part 256-byte aligned.
+static __device__ __align__(256) unsigned char g_rans_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t* d_idx, size_t n,
+                                                int lanes, uint8_t* d_out, size_t capacity, uint64_t* d_nbytes,
+                                                void* stream) {
+    if (!ctx) return UFVC_ERR_ARG;
+    if ((!d_sym && n) || (!d_idx && n) || !d_out || !d_nbytes || lanes < 1 || lanes > 65536) {
+        ufvc::ctx_set_error(ctx, "rans_encode_noalloc: bad argument");
+        return UFVC_ERR_ARG;
+    }
+    const size_t cap_lane = n / (size_t)lanes + 3;
+    const size_t off_bytes = align256((size_t)lanes * 8), cnt_bytes = align256((size_t)lanes * 4);
+    const size_t need = off_bytes + cnt_bytes + (size_t)lanes * cap_lane * 2;
+    if (need > kScratchBytes) {
+        ufvc::ctx_set_error(ctx, "rans_encode_noalloc: n + 3 * lanes exceeds the 24 MiB static scratch "
+                                 "(at most about 12.5 million symbols); use ufvc_rans_encode");
+        return UFVC_ERR_ARG;
+    }
+    const int dev = ufvc::ctx_device(ctx);
+    if (dev < 0 || dev >= kMaxDevices) {
+        ufvc::ctx_set_error(ctx, "rans_encode_noalloc: device ordinal out of range");
+        return UFVC_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        ufvc::ctx_set_error(ctx, cudaGetErrorString(e));
+        return UFVC_ERR_CUDA;
+    }
+    void* base = nullptr;
+    {
+        // once per device, with that device current: the array's device address (the host-side symbol
+        // is only a stand-in and must never be handed to a kernel)
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_rans_scratch);
+            if (e != cudaSuccess || !p) {
+                ufvc::ctx_set_error(ctx, e != cudaSuccess ? cudaGetErrorString(e) : "cudaGetSymbolAddress: null");
+                return UFVC_ERR_CUDA;
+            }
+            g_scratch_addr[dev] = p;
+        }
+        base = g_scratch_addr[dev];
+    }
+    // Nothing in the scratch is read before this call writes it (each lane writes its count and the
+    // words it later copies; the finaliser writes every offset), so no part needs clearing.
+    unsigned char* b = static_cast<unsigned char*>(base);
+    uint64_t* offsets = reinterpret_cast<uint64_t*>(b);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(b + off_bytes);
+    uint16_t* rows = reinterpret_cast<uint16_t*>(b + off_bytes + cnt_bytes);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* status = ufvc::ctx_status_word(ctx);
+    ufvc::RansSection sec{d_sym, d_idx, 0, n, lanes, rows, (int)cap_lane, counts, status};
+    ufvc::launch_rans_encode(&sec, 1, ufvc::ctx_packed_tables(ctx), s);
+    ufvc::launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, offsets, status, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ufvc::ctx_set_error(ctx, cudaGetErrorString(e));
+        return UFVC_ERR_CUDA;
+    }
+    return UFVC_OK;
+}

@@ -152,3 +152,11 @@ void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, in
                          int* qp_dev, uint8_t* iz, int* status, cudaStream_t s);
 
 }  // namespace ufvc
+
+// context internals for other translation units (defined in api.cu)
+namespace ufvc {
+const uint32_t* ctx_packed_tables(const ufvc_ctx* c);
+int* ctx_status_word(ufvc_ctx* c);
+int ctx_device(const ufvc_ctx* c);
+void ctx_set_error(ufvc_ctx* c, const char* msg);
+}  // namespace ufvc

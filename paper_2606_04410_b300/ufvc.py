@@ -58,6 +58,7 @@ _sigs = {
     "ufvc_quantize": (_i, [_vp, _vp, _vp, _vp, _sz, _i, _vp, _vp, _vp]),
     "ufvc_synthesize": (_i, [_vp, _vp, _i, _i, _vp, _vp]),
     "ufvc_rans_encode": (_i, [_vp, _vp, _vp, _sz, _i, _vp, _sz, _vp, _vp]),
+    "ufvc_rans_encode_noalloc": (_i, [_vp, _vp, _vp, _sz, _i, _vp, _sz, _vp, _vp]),
     "ufvc_rans_decode": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _vp, _vp]),
     "ufvc_get_tables": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ufvc_set_profiling": (_i, [_vp, _i]),
