@@ -10,7 +10,7 @@
 // tcgen05.mma (M=128, N=BN, K=16 per instruction) accumulating in TMEM.
 //
 // Persistent, warp-specialised CTA (one per SM): warp 0 issues TMA loads into a STAGES-deep ring;
-// warp 1 owns TMEM and issues the MMAs; eight epilogue warps drain a double-buffered TMEM
+// warp 1 owns TMEM and issues the MMAs; sixteen epilogue warps drain a double-buffered TMEM
 // accumulator (tcgen05.ld), add bias, apply GELU / residual / pixel shuffle / crop / final frame
 // mapping and store, while the MMAs of the next tile run.  Every mbarrier wait is bounded: on a
 // timeout the kernel records UFVC_ERR_TIMEOUT, all roles stop, in-flight copies and MMAs are waited
@@ -25,7 +25,7 @@
 namespace ufvc {
 
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;  // four per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct TcArgs {
@@ -43,7 +43,24 @@ struct TcArgs {
     int* err;
 };
 
-__device__ __forceinline__ float gelu_erf_tc(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// GELU x * Phi(x), Phi(x) = (1 + erf(x / sqrt 2)) / 2, with erf from Abramowitz & Stegun (1964) formula
+// 7.1.28: erf(a) = 1 - (1 + c1 a + ... + c6 a^6)^-16 for a >= 0, absolute error <= 3e-7 (one reciprocal,
+// no exponential), far below the bf16 rounding of the stored activations.
+__device__ __forceinline__ float gelu_tc(float x) {
+    const float a = fabsf(x) * 0.70710678118654752f;
+    float p = fmaf(a, 4.30638e-5f, 2.765672e-4f);
+    p = fmaf(p, a, 1.520143e-4f);
+    p = fmaf(p, a, 9.2705272e-3f);
+    p = fmaf(p, a, 4.22820123e-2f);
+    p = fmaf(p, a, 7.05230784e-2f);
+    p = fmaf(p, a, 1.0f);
+    p = p * p;
+    p = p * p;
+    p = p * p;
+    p = p * p;                                       // (..)^16; overflows to inf for large a: erf -> 1
+    const float erf_a = 1.0f - __fdividef(1.0f, p);
+    return 0.5f * x * (1.0f + copysignf(erf_a, x));
+}
 
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          bool honour_abort = true) {
@@ -65,19 +82,25 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-    ptx::tmem_ld16(taddr, v);
-    ptx::tmem_ld16(taddr + 16, v + 16);
-}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) { ptx::tmem_ld32(taddr, v); }
 
 // Epilogue of NV (16 or 32) consecutive accumulator columns of one output pixel.
 template <int NV>
 __device__ __forceinline__ void store_cols(const TcArgs& p, int g, int oh, int ow, int co0, float* v) {
+    const float* bias = p.bias + (size_t)g * p.b_gs + co0;
+    if (co0 + NV <= p.Cout) {  // warp-uniform 16-byte loads (every lane reads the same columns)
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        const int co = co0 + i;
-        v[i] += (co < p.Cout) ? __ldg(p.bias + (size_t)g * p.b_gs + co) : 0.0f;
-        if (p.act) v[i] = gelu_erf_tc(v[i]);
+        for (int i = 0; i < NV / 4; ++i) {
+            const float4 b = __ldg(reinterpret_cast<const float4*>(bias) + i);
+            v[4 * i] += b.x; v[4 * i + 1] += b.y; v[4 * i + 2] += b.z; v[4 * i + 3] += b.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += (co0 + i < p.Cout) ? __ldg(bias + i) : 0.0f;
+    }
+    if (p.act) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = gelu_tc(v[i]);
     }
     if (p.mode == OUT_NHWC) {
         if (co0 >= p.Cout) return;
@@ -144,7 +167,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int A_BYTES = 128 * 128;
     constexpr int B_BYTES = BN * 128;
     constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
-    constexpr int CHUNK = BN < 32 ? 16 : 32;  // accumulator columns per tcgen05.ld round
+    // each of the four epilogue warps of a lane quarter drains a quarter of the BN columns
+    constexpr int PER = BN / 4 < 16 ? 16 : BN / 4;
+    constexpr int CHUNK = PER % 32 == 0 ? 32 : 16;  // accumulator columns per tcgen05.ld round
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -254,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue warps
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;       // which half of the BN columns
+        const int colq = (warp - 2) >> 2;       // which quarter of the BN columns
         const int row = q * 32 + lane;
         int tl = 0;
         for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++tl) {
@@ -265,8 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int oh = (mt / p.tiles_w) * p.TH + row / p.TW, ow = (mt % p.tiles_w) * p.TW + row % p.TW;
             const bool valid = oh < p.Ho && ow < p.Wo;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
-            constexpr int PER = (BN / 2 + CHUNK - 1) / CHUNK * CHUNK;  // columns per half, CHUNK-rounded
-            const int c_begin = half * PER;
+            const int c_begin = colq * PER;
 #pragma unroll 1
             for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
                 float v[CHUNK];
