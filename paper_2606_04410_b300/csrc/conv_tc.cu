@@ -309,6 +309,177 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+
+// ------------------------------------------------------------------------------------------------
+// Stride-1 3x3 layers with 64 input channels (U2, R2, U3 of the decoders): the layer's weights stay
+// resident in shared memory (9 taps x BN columns, BN <= 64), and a tile is a strip of 128 output
+// pixels of one row, so its A operand for all nine taps comes from the three input rows above, on and
+// below it (130 pixels each, one TMA box per row, zero-filled outside the image): tap (ky, kx) is the
+// 128-row window starting kx rows into row ky.  Input traffic per tile drops from 9 tiles to 3 rows
+// and weight traffic to one load per CTA and (group, N tile).  Tiles are handed out in contiguous
+// ranges so a CTA changes weights at most a few times; a change waits until the MMAs that read the old
+// weights have completed.
+// ------------------------------------------------------------------------------------------------
+constexpr int kHaloRowBytes = 17 * 1024;  // 130 rows x 128 B, rounded up to the 1024-B swizzle repeat
+constexpr int kHaloBoxBytes = 130 * 128;
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        const TcArgs p) {
+    constexpr int A_BYTES = 3 * kHaloRowBytes;
+    constexpr int B_BYTES = 9 * BN * 128;
+    constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : 128;
+    constexpr int PER = BN / 4 < 16 ? 16 : BN / 4;
+    constexpr int CHUNK = 16;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sB = smem;
+    uint8_t* sA = smem + B_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sA + STAGES * A_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* bfull = tempty + 2;
+    uint64_t* bfree = bfull + 1;
+    uint64_t* drain = bfree + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(&tfull[a], 1);
+            ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
+        }
+        ptx::mbar_init(bfull, 1);
+        ptx::mbar_init(bfree, 1);
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    // tile t = ((g * n_tiles + nt) * Ho + oh) * tiles_w + strip; this CTA owns [t_begin, t_end)
+    const int t_begin = (int)((long long)p.total_tiles * blockIdx.x / gridDim.x);
+    const int t_end = (int)((long long)p.total_tiles * (blockIdx.x + 1) / gridDim.x);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, cur_key = -1, nb = 0;
+            uint32_t bfree_par = 0, last_par[STAGES];
+            bool used[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
+            for (int t = t_begin; t < t_end; ++t, ++it) {
+                const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, key = r / p.Ho;
+                const int nt = key % p.n_tiles, g = key / p.n_tiles;
+                if (key != cur_key) {
+                    if (cur_key >= 0) {  // the MMAs that read the previous weights must be complete
+                        if (!wait_bar(bfree, bfree_par, abort_flag, p.err)) break;
+                        bfree_par ^= 1;
+                    }
+                    ptx::mbar_arrive_expect_tx(bfull, B_BYTES);
+                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * BN * 128, &tmB, bfull, tap * 64, nt * BN, g);
+                    cur_key = key;
+                    ++nb;
+                }
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) break;
+                ptx::mbar_arrive_expect_tx(&full[s], 3 * kHaloBoxBytes);
+                const int ag = p.a_grouped ? g : 0, w0 = strip * 128;
+                for (int ky = 0; ky < 3; ++ky)
+                    ptx::tma_load_4d(sA + s * A_BYTES + ky * kHaloRowBytes, &tmA, &full[s], 0, w0 - 1, oh + ky - 1, ag);
+                used[s] = true;
+                last_par[s] = ph;
+            }
+            // make sure no copy is still writing shared memory when the CTA exits
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s)
+                if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+            if (nb) wait_bar(bfull, (nb - 1) & 1, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_bf16(BN);
+            int it = 0, tl = 0, cur_key = -1;
+            uint32_t bfull_par = 0;
+            for (int t = t_begin; t < t_end; ++t, ++it, ++tl) {
+                const int key = t / p.tiles_w / p.Ho;
+                if (key != cur_key) {
+                    if (cur_key >= 0) ptx::mma_commit(bfree);  // old weights free once these MMAs finish
+                    if (!wait_bar(bfull, bfull_par, abort_flag, p.err)) break;
+                    bfull_par ^= 1;
+                    ptx::tc_fence_after();
+                    cur_key = key;
+                }
+                const int acc = tl & 1, use = tl >> 1;
+                if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!wait_bar(&full[s], ph, abort_flag, p.err)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + acc * BN;
+                const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB);
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap % 3;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        ptx::mma_f16(d, ptx::sdesc_sw128_at(a0 + ky * kHaloRowBytes + kx * 128 + kk * 32),
+                                     ptx::sdesc_sw128(b0 + tap * BN * 128 + kk * 32), idesc, (tap | kk) != 0);
+                }
+                ptx::mma_commit(&empty[s]);
+                ptx::mma_commit(&tfull[acc]);
+            }
+            ptx::mma_commit(drain);
+            wait_bar(drain, 0, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3, colq = (warp - 2) >> 2, row = q * 32 + lane;
+        int tl = 0;
+        for (int t = t_begin; t < t_end; ++t, ++tl) {
+            const int acc = tl & 1, use = tl >> 1;
+            if (!wait_bar(&tfull[acc], use & 1, abort_flag, p.err)) break;
+            ptx::tc_fence_after();
+            const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, key = r / p.Ho;
+            const int nt = key % p.n_tiles, g = key / p.n_tiles;
+            const int ow = strip * 128 + row;
+            const bool valid = ow < p.Wo;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
+            const int c_begin = colq * PER;
+#pragma unroll 1
+            for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
+                float v[CHUNK];
+                ptx::tmem_ld16(taddr + c, v);
+                if (valid) store_cols<CHUNK>(p, g, oh, ow, nt * BN + c, v);
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&tempty[acc]);
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------------
@@ -368,6 +539,27 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const T
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
 // returns a CUDA error or cudaSuccess; UFVC argument problems return cudaErrorInvalidValue.
+template <int BN, int STAGES>
+static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
+    const int smem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + 1024 + 256;
+    static int configured_smem = 0;
+    if (configured_smem != smem) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_tc_halo_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured_smem = smem;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int grid = args.total_tiles < sms ? args.total_tiles : sms;
+    conv_tc_halo_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(a, b, args);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     if (d.Cin % 64 != 0 || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
         return cudaErrorInvalidValue;
@@ -376,8 +568,11 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     int BN = d.cout_pad >= 256 ? 256 : d.cout_pad;
     if (d.cout_pad % BN != 0 || !(BN == 16 || BN == 64 || BN == 128 || BN == 192 || BN == 256))
         return cudaErrorInvalidValue;
+    // stride-1 3x3 layers with 64 input channels: resident weights, three input rows per 128-pixel strip
+    const bool halo = d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad % 64 == 0);
+    if (halo) BN = d.cout_pad == 16 ? 16 : 64;
     TcArgs a{};
-    pick_tile(Ho, Wo, &a.TW, &a.TH);
+    if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH);
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
     a.tiles_h = (Ho + a.TH - 1) / a.TH;
@@ -404,6 +599,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t str[3] = {d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz, (cuuint64_t)d.H * d.W * d.Cin * esz};
         if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
         cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+        if (halo) { box[1] = 130; box[2] = 1; }
         ok = encode_map(&ma, d.in, 4, dims, str, box);
     } else {
         cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
@@ -420,6 +616,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint32_t box[3] = {64, (cuuint32_t)BN, 1};
         if (!encode_map(&mb, d.wtc, 3, dims, str, box)) return cudaErrorInvalidValue;
     }
+    if (halo) return BN == 16 ? launch_halo<16, 3>(ma, mb, a, s) : launch_halo<64, 2>(ma, mb, a, s);
     switch (BN) {
         case 16: return launch_bn<16, 8>(ma, mb, a, s);
         case 64: return launch_bn<64, 8>(ma, mb, a, s);

@@ -70,6 +70,9 @@ LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
     (1, 2, 17, 24, 40, 1, 1, 1, 64),     # U2: 64 -> 256 PS
     (1, 2, 18, 24, 40, 1, 0, 2, 64),     # U3: 64 -> 12 PS, final mapping
     (1, 2, 26, 31, 29, 1, 0, 2, 64),     # U3 frame 1, ragged (crop)
+    (1, 2, 15, 17, 300, 1, 1, 0, 64),    # R2a over three 128-pixel strips (ragged last strip)
+    (1, 2, 17, 9, 260, 1, 1, 1, 64),     # U2 (four N tiles of 64) over three strips
+    (1, 2, 26, 5, 390, 1, 0, 2, 64),     # U3 frame 1 over four strips, final mapping
 ]
 
 
