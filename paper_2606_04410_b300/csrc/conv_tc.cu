@@ -311,11 +311,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 
 // ------------------------------------------------------------------------------------------------
-// Stride-1 3x3 layers with 64 input channels (U2, R2, U3 of the decoders): the layer's weights stay
+// Stride-1 3x3 layers with 64 input channels and <= 64 outputs (R2, U3 of the decoders): the weights stay
 // resident in shared memory (9 taps x BN columns, BN <= 64), and a tile is a strip of 128 output
 // pixels of one row, so its A operand for all nine taps comes from the three input rows above, on and
 // below it (130 pixels each, one TMA box per row, zero-filled outside the image): tap (ky, kx) is the
-// 128-row window starting kx rows into row ky.  Input traffic per tile drops from 9 tiles to 3 rows
+// 128-row window starting kx rows into row ky.  The 128-byte swizzle is a function of the shared-memory
+// address (as TMA writes it), so such a window is described by its start address alone (base offset 0),
+// exactly like the 32-byte K-slice advance.  Input traffic per tile drops from 9 tiles to 3 rows
 // and weight traffic to one load per CTA and (group, N tile).  Tiles are handed out in contiguous
 // ranges so a CTA changes weights at most a few times; a change waits until the MMAs that read the old
 // weights have completed.
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int ky = tap / 3, kx = tap % 3;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        ptx::mma_f16(d, ptx::sdesc_sw128_at(a0 + ky * kHaloRowBytes + kx * 128 + kk * 32),
+                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * kHaloRowBytes + kx * 128 + kk * 32),
                                      ptx::sdesc_sw128(b0 + tap * BN * 128 + kk * 32), idesc, (tap | kk) != 0);
                 }
                 ptx::mma_commit(&empty[s]);
@@ -568,9 +570,11 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     int BN = d.cout_pad >= 256 ? 256 : d.cout_pad;
     if (d.cout_pad % BN != 0 || !(BN == 16 || BN == 64 || BN == 128 || BN == 192 || BN == 256))
         return cudaErrorInvalidValue;
-    // stride-1 3x3 layers with 64 input channels: resident weights, three input rows per 128-pixel strip
-    const bool halo = d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad % 64 == 0);
-    if (halo) BN = d.cout_pad == 16 ? 16 : 64;
+    // stride-1 3x3 layers with 64 input channels and at most 64 output channels: resident weights,
+    // three input rows per 128-pixel strip (wider layers keep one N tile on the streaming kernel, which
+    // re-reads the input less than several N tiles would)
+    const bool halo = d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
+    if (halo) BN = d.cout_pad;
     TcArgs a{};
     if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH);
     a.Ho = Ho; a.Wo = Wo;

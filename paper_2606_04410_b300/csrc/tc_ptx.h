@@ -150,12 +150,6 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Same, for a matrix that starts part-way into a 1024-byte swizzle repeat (a whole number of 128-byte
-// rows in): the descriptor's base-offset field carries (start >> 7) & 7.
-__device__ __forceinline__ uint64_t sdesc_sw128_at(uint32_t saddr) {
-    return sdesc_sw128(saddr) | ((uint64_t)((saddr >> 7) & 7) << 49);
-}
-
 // Instruction descriptor: D = FP32, A = B = BF16 (kind::f16) or E4M3 (kind::f8f6f4), both K-major,
 // M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n) {
