@@ -27,6 +27,10 @@ namespace ufvc {
 constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kBiasMax = 4096;                       // biases staged in shared memory (16 KB)
+constexpr int kSmemExtra = 1024 + 256 + 16 + 4 * kBiasMax;  // alignment slack, barriers, bias table
+
+
 
 struct TcArgs {
     int Ho, Wo, TW, TH, tiles_w, tiles_h, n_tiles, groups, total_tiles;
@@ -42,6 +46,15 @@ struct TcArgs {
     long long res_gs;
     int* err;
 };
+
+// All groups' biases (groups x Cout floats) copied once into shared memory when they fit; the epilogue
+// then reads them from there instead of global memory.
+__device__ __forceinline__ const float* stage_bias(const TcArgs& p, float* sbias) {
+    const int total = p.groups * p.b_gs;
+    if (total > kBiasMax) return p.bias;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) sbias[i] = __ldg(p.bias + i);
+    return sbias;  // visible after the block barrier that follows the set-up
+}
 
 // GELU x * Phi(x), Phi(x) = (1 + erf(x / sqrt 2)) / 2, with erf from Abramowitz & Stegun (1964) formula
 // 7.1.28: erf(a) = 1 - (1 + c1 a + ... + c6 a^6)^-16 for a >= 0, absolute error <= 3e-7 (one reciprocal,
@@ -86,8 +99,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) { ptx::tmem_
 
 // Epilogue of NV (16 or 32) consecutive accumulator columns of one output pixel.
 template <int NV>
-__device__ __forceinline__ void store_cols(const TcArgs& p, int g, int oh, int ow, int co0, float* v) {
-    const float* bias = p.bias + (size_t)g * p.b_gs + co0;
+__device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
+                                           float* v) {
+    const float* bias = bias_all + (size_t)g * p.b_gs + co0;
     if (co0 + NV <= p.Cout) {  // warp-uniform 16-byte loads (every lane reads the same columns)
 #pragma unroll
         for (int i = 0; i < NV / 4; ++i) {
@@ -181,6 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
+    const float* bias_all = stage_bias(p, sbias);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -295,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
                 float v[CHUNK];
                 if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
-                if (valid) store_cols<CHUNK>(p, g, oh, ow, nt * BN + c, v);
+                if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[acc]);
@@ -347,6 +363,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = bfree + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
+    const float* bias_all = stage_bias(p, sbias);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -468,7 +486,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
                 float v[CHUNK];
                 ptx::tmem_ld16(taddr + c, v);
-                if (valid) store_cols<CHUNK>(p, g, oh, ow, nt * BN + c, v);
+                if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[acc]);
@@ -521,7 +539,7 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH) {
 
 template <int BN, int STAGES>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
-    const int smem = STAGES * (128 * 128 + BN * 128) + 1024 + 256;
+    const int smem = STAGES * (128 * 128 + BN * 128) + kSmemExtra;
     static int configured_smem = 0;
     if (configured_smem != smem) {
         cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -543,7 +561,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const T
 // returns a CUDA error or cudaSuccess; UFVC argument problems return cudaErrorInvalidValue.
 template <int BN, int STAGES>
 static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
-    const int smem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + 1024 + 256;
+    const int smem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + kSmemExtra;
     static int configured_smem = 0;
     if (configured_smem != smem) {
         cudaError_t e =
