@@ -105,12 +105,12 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
     if (co0 + NV <= p.Cout) {  // warp-uniform 16-byte loads (every lane reads the same columns)
 #pragma unroll
         for (int i = 0; i < NV / 4; ++i) {
-            const float4 b = __ldg(reinterpret_cast<const float4*>(bias) + i);
+            const float4 b = reinterpret_cast<const float4*>(bias)[i];  // shared or global: plain loads
             v[4 * i] += b.x; v[4 * i + 1] += b.y; v[4 * i + 2] += b.z; v[4 * i + 3] += b.w;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] += (co0 + i < p.Cout) ? __ldg(bias + i) : 0.0f;
+        for (int i = 0; i < NV; ++i) v[i] += (co0 + i < p.Cout) ? bias[i] : 0.0f;
     }
     if (p.act) {
 #pragma unroll
