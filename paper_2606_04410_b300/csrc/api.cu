@@ -25,6 +25,11 @@ struct LayerW {
     // tensor-core copy (BF16 precision): bf16 [groups][cout_pad][k*k][cin_tc], K-major
     __nv_bfloat16* wtc = nullptr;
     int cout_pad = 0, cin_tc = 0;
+    // pixel-shuffle layers: tensor-core rows (accumulator columns) in sub-pixel-major order, row
+    // s * cout/4 + c = output channel 4c + s, so that a run of columns is a run of channels of ONE
+    // output pixel; btc holds the biases in the same order
+    int ps_major = 0;
+    float* btc = nullptr;
 };
 
 struct Plan {
@@ -281,7 +286,7 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
 }
 
 static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
-                                bool tc) {
+                                bool tc, bool pixel_shuffle = false) {
     int co, k, ci;
     layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
     L.cout = co; L.k = k; L.cin = ci; L.cin_p = ceil_div(ci, 16) * 16; L.groups = groups;
@@ -306,18 +311,28 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
         // K-major bf16 copy for tcgen05: [g][cout_pad][tap][cin_tc], zero rows / columns in the padding
         L.cin_tc = ceil_div(ci, 64) * 64;
         L.cout_pad = co >= 64 ? co : 16;
+        L.ps_major = pixel_shuffle && co % 128 == 0;  // runs of 32 channels per sub-pixel in every N tile
+        const int cq = co / 4;
+        auto row = [&](int o) { return L.ps_major ? (o & 3) * cq + (o >> 2) : o; };
         const size_t K = (size_t)k * k * L.cin_tc;
         std::vector<__nv_bfloat16> wt((size_t)groups * L.cout_pad * K, __float2bfloat16(0.f));
+        std::vector<float> bt(b.size());
         for (int g = 0; g < groups; ++g) {
             const float* src = blob + offs[first + g * D_NDEC];
-            for (int o = 0; o < co; ++o)
+            for (int o = 0; o < co; ++o) {
                 for (int t = 0; t < k * k; ++t)
                     for (int i = 0; i < ci; ++i)
-                        wt[((size_t)g * L.cout_pad + o) * K + (size_t)t * L.cin_tc + i] =
+                        wt[((size_t)g * L.cout_pad + row(o)) * K + (size_t)t * L.cin_tc + i] =
                             __float2bfloat16(src[((size_t)o * k * k + t) * ci + i]);
+                bt[(size_t)g * co + row(o)] = b[(size_t)g * co + o];
+            }
         }
         if ((st = dalloc(ctx, nullptr, &L.wtc, wt.size())) != UFVC_OK) return st;
         CK(cudaMemcpy(L.wtc, wt.data(), wt.size() * 2, cudaMemcpyHostToDevice));
+        if (L.ps_major) {
+            if ((st = dalloc(ctx, nullptr, &L.btc, bt.size())) != UFVC_OK) return st;
+            CK(cudaMemcpy(L.btc, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice));
+        }
     }
     return UFVC_OK;
 }
@@ -327,8 +342,8 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     cudaSetDevice(ctx->cfg.device);
     cudaDeviceSynchronize();
     for (auto& kv : ctx->plans) free_plan(kv.second);
-    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
-    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
+    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
+    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
     cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
     cudaFree(ctx->d_status);
     cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
@@ -383,7 +398,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
     for (int l = 0; l < L_NENC; ++l)
         if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1, l <= L_A4)) != UFVC_OK) return bail(st);
     for (int j = 0; j < D_NDEC; ++j)
-        if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true)) != UFVC_OK)
+        if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true,
+                                   j == D_D0 || j == D_U1 || j == D_U2)) != UFVC_OK)
             return bail(st);
     *out = ctx;
     return UFVC_OK;
@@ -404,6 +420,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
     d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
     if (use_tc(ctx, L)) {
         d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
+        d.btc = L.btc; d.ps_major = L.ps_major;
         const cudaError_t e = launch_conv_tc(d, s);
         if (e != cudaSuccess) {
             ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
@@ -772,9 +789,12 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
         L.w += g * L.w_gs;
         L.b += g * L.b_gs;
         if (L.wtc) L.wtc += (size_t)g * L.cout_pad * L.k * L.k * L.cin_tc;
+        if (L.btc) L.btc += g * L.b_gs;
     }
     L.groups = 1;
     const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
+    if (use_tc(ctx, L) && L.ps_major && m != OUT_PS)
+        return fail(ctx, UFVC_ERR_ARG, "conv_layer: this layer's tensor-core weights are laid out for pixel shuffle");
     RUN(conv(ctx, L, d_in, H, W, stride, act, m, d_out, out_h, out_w, (cudaStream_t)stream));
     CK(cudaGetLastError());
     return UFVC_OK;

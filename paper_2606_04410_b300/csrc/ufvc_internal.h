@@ -78,6 +78,8 @@ struct ConvDesc {
     int cout_pad = 0;           // Cout rounded up to the N tile
     int out_f32 = 0;            // NHWC output stored as float (else bf16)
     int out_c_stride = 0;       // NHWC output channel count if different from Cout
+    const float* btc = nullptr; // tensor-core bias in accumulator-column order (nullptr: same as b)
+    int ps_major = 0;           // tensor-core weights in sub-pixel-major column order (pixel shuffle layers)
     int* err = nullptr;         // device status word (bounded-wait timeouts)
 };
 

@@ -167,3 +167,16 @@ def test_bf16_chunk(arch, N, H, W, K):
     assert report["recon_rms_vs_oracle"] < 1.5e-2
     assert abs(report["dpsnr"]) < 0.05
     assert abs(report["dbitrate"]) < 0.005 + 64.0 / n32
+
+
+def test_ps_layer_rejects_other_modes():
+    """Pixel-shuffle layers keep their tensor-core weights in sub-pixel-major column order, so the
+    single-layer entry point refuses to run them with any other output mode."""
+    u = U()
+    blob = synthetic.draw_weights(1, 2, seed=3)
+    codec = u.Codec(1, 2, 64, blob, "bf16")
+    x = torch.zeros((8, 8, 64), dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros((8, 8, 256), dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(u.UfvcError) as e:
+        codec.conv_layer(17, x, 1, 1, 0, out)
+    assert e.value.code == u.UFVC_ERR_ARG
