@@ -45,6 +45,7 @@ struct TcArgs {
     const __nv_bfloat16* res;
     long long res_gs;
     int ps_major;  // pixel shuffle with sub-pixel-major accumulator columns (column = sub * out_c + channel)
+    int c_rank;    // staged epilogue: 4 = NHWC store map (C, W, H, G); 5 = pixel-shuffle map (C', dx, W, dy, G*H)
     int* err;
 };
 
@@ -95,10 +96,11 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) { ptx::tmem_ld32(taddr, v); }
 
-// Epilogue of NV (16 or 32) consecutive accumulator columns of one output pixel.
+// Bias, activation and (bf16 NHWC output with a residual) the residual, in place, for NV (16 or 32)
+// consecutive accumulator columns of one output pixel.
 template <int NV>
-__device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
-                                           float* v) {
+__device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
+                                            float* v) {
     const float* bias = bias_all + (size_t)g * p.b_gs + co0;
     if (co0 + NV <= p.Cout) {  // warp-uniform 16-byte loads (every lane reads the same columns)
 #pragma unroll
@@ -114,6 +116,24 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 #pragma unroll
         for (int i = 0; i < NV; ++i) v[i] = gelu_tc(v[i]);
     }
+    if (p.mode == OUT_NHWC && !p.out_f32 && p.res && co0 < p.Cout) {
+        const uint4* r = reinterpret_cast<const uint4*>(p.res + (size_t)g * p.res_gs +
+                                                        ((size_t)oh * p.out_w + ow) * p.out_c + co0);
+#pragma unroll
+        for (int i = 0; i < NV / 8; ++i) {
+            uint4 u = r[i];
+            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[8 * i + j] += __bfloat162float(h[j]);
+        }
+    }
+}
+
+// Epilogue of NV (16 or 32) consecutive accumulator columns of one output pixel, stored by this thread.
+template <int NV>
+__device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
+                                           float* v) {
+    finish_cols<NV>(p, bias_all, g, oh, ow, co0, v);
     if (p.mode == OUT_NHWC) {
         if (co0 >= p.Cout) return;
         const size_t o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c + co0;
@@ -122,17 +142,6 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 #pragma unroll
             for (int i = 0; i < NV / 4; ++i) d[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             return;
-        }
-        if (p.res) {
-            const uint4* r = reinterpret_cast<const uint4*>(p.res + (size_t)g * p.res_gs +
-                                                            ((size_t)oh * p.out_w + ow) * p.out_c + co0);
-#pragma unroll
-            for (int i = 0; i < NV / 8; ++i) {
-                uint4 u = r[i];
-                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&u);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) v[8 * i + j] += __bfloat162float(h[j]);
-            }
         }
         uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(p.out) + o);
 #pragma unroll
@@ -186,25 +195,36 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
     }
 }
 
-template <int BN, int STAGES>
+// STAGED: the epilogue writes the bf16 output tile into a 128-byte-swizzled staging tile in shared memory
+// (64-column slabs of 128 rows x 128 B, the layout a TMA box of 64 channels x TW x TH has) and one thread
+// per slab group stores it with TMA tiled stores, which clip at the tensor edges.  Otherwise every
+// epilogue thread stores its own pixel's columns.
+template <int BN, int STAGES, bool STAGED>
 __global__ void __launch_bounds__(kThreads, 1)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs p) {
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
     constexpr int A_BYTES = 128 * 128;
     constexpr int B_BYTES = BN * 128;
+    constexpr int C_BYTES = STAGED ? 128 * BN * 2 : 0;
     constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
     // each of the four epilogue warps of a lane quarter drains a quarter of the BN columns
     constexpr int PER = BN / 4 < 16 ? 16 : BN / 4;
     constexpr int CHUNK = PER % 32 == 0 ? 32 : 16;  // accumulator columns per tcgen05.ld round
+    // slab groups of the staged epilogue: GQ column quarters that share 64-column slabs
+    constexpr int GQ = (PER % 64 == 0) ? 1 : (64 % PER == 0 ? 64 / PER : 4);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + STAGES * A_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+    uint8_t* sC = sB + STAGES * B_BYTES;  // staging tile (STAGED), 1024-byte aligned
+    uint64_t* full = reinterpret_cast<uint64_t*>(sC + C_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* cwritten = drain + 1;   // per slab group: all its threads wrote the staging tile
+    uint64_t* cfree = cwritten + 4;   // per slab group: its previous TMA stores have read the staging tile
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
     const float* bias_all = stage_bias(p, sbias);
@@ -220,6 +240,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
         }
         ptx::mbar_init(drain, 1);
+        for (int gq = 0; gq < 4; ++gq) {
+            ptx::mbar_init(&cwritten[gq], 128 * GQ);
+            ptx::mbar_init(&cfree[gq], 1);
+        }
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -227,6 +251,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0 && lane == 0) {
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
+        if (STAGED) ptx::prefetch_tmap(&tmC);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -308,25 +333,76 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int colq = (warp - 2) >> 2;       // which quarter of the BN columns
         const int row = q * 32 + lane;
+        const int grp = colq / GQ;              // slab group (staged epilogue)
+        const bool elected = STAGED && warp == 2 + grp * GQ * 4 && lane == 0;
         int tl = 0;
         for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++tl) {
             const int acc = tl & 1, use = tl >> 1;
-            if (!wait_bar(&tfull[acc], use & 1, abort_flag, p.err)) break;
+            if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
             const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
-            const int oh = (mt / p.tiles_w) * p.TH + row / p.TW, ow = (mt % p.tiles_w) * p.TW + row % p.TW;
+            const int h0 = (mt / p.tiles_w) * p.TH, w0 = (mt % p.tiles_w) * p.TW;
+            const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
             const bool valid = oh < p.Ho && ow < p.Wo;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
             const int c_begin = colq * PER;
+            bool ok = true;
 #pragma unroll 1
             for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
                 float v[CHUNK];
                 if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
-                if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                if constexpr (STAGED) {
+                    if (valid) finish_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                    if (c == c_begin && tl > 0) {
+                        // the previous tile's TMA stores must have read the staging tile
+                        if (elected) {
+                            ptx::bulk_wait_read0();
+                            ptx::mbar_arrive(&cfree[grp]);
+                        }
+                        ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (tl - 1) & 1, abort_flag, p.err));
+                        if (!ok) break;  // warp-uniform: the next tcgen05.ld needs the whole warp
+                    }
+                    // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
+                    const uint32_t base = ptx::smem_u32(sC) + (c >> 6) * (128 * 128) + row * 128;
+#pragma unroll
+                    for (int i = 0; i < CHUNK / 8; ++i) {
+                        const int j = ((c & 63) >> 3) + i;
+                        ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                          pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                          pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                    }
+                } else {
+                    if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                }
             }
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[acc]);
+            if (!ok) break;
+            if constexpr (STAGED) {
+                ptx::fence_proxy_async();  // this thread's staging writes -> visible to the TMA (async proxy)
+                ptx::mbar_arrive(&cwritten[grp]);
+                if (warp == 2 + grp * GQ * 4) {  // the elected thread's warp (warp-uniform)
+                    bool w_ok = true;
+                    if (lane == 0) w_ok = wait_bar(&cwritten[grp], tl & 1, abort_flag, p.err);
+                    if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
+                }
+                if (elected) {
+                    const int lo = grp * GQ * PER, hi = (grp + 1) * GQ * PER < BN ? (grp + 1) * GQ * PER : BN;
+                    for (int sl = lo >> 6; sl < (hi + 63) >> 6; ++sl) {
+                        const int col0 = nt * BN + sl * 64;
+                        const uint8_t* src = sC + sl * (128 * 128);
+                        if (p.c_rank == 4) {
+                            ptx::tma_store_4d(&tmC, src, col0, w0, h0, g);
+                        } else {
+                            const int sub = col0 / p.out_c, c0 = col0 - sub * p.out_c;
+                            ptx::tma_store_5d(&tmC, src, c0, sub & 1, w0, sub >> 1, g * p.Ho + h0);
+                        }
+                    }
+                    ptx::bulk_commit();
+                }
+            }
         }
+        if (elected) ptx::bulk_wait0();  // stores complete before the CTA (and its shared memory) ends
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -539,21 +615,27 @@ static bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint6
     return r == CUDA_SUCCESS;
 }
 
-static void pick_tile(int Ho, int Wo, int* TW, int* TH) {
+// Output tile TW x TH = 128 pixels with the least padding; with th_divides, TH must divide Ho.
+static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false) {
     long long best = -1;
     for (int tw = 128; tw >= 8; tw >>= 1) {
         const int th = 128 / tw;
+        if (th_divides && Ho % th != 0) continue;
         const long long cost = (long long)((Wo + tw - 1) / tw) * tw * ((Ho + th - 1) / th) * th;
         if (best < 0 || cost < best) { best = cost; *TW = tw; *TH = th; }
     }
 }
 
-template <int BN, int STAGES>
-static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
-    const int smem = STAGES * (128 * 128 + BN * 128) + kSmemExtra;
+template <int BN, int STAGES, bool STAGED>
+static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
+                             cudaStream_t s) {
+    const int smem = STAGES * (128 * 128 + BN * 128) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra;
+    static_assert(STAGES * (128 * 128 + BN * 128) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra <= 227 * 1024,
+                  "shared memory per CTA");
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
     }
@@ -564,7 +646,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const T
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(a, b, args);
+    conv_tc_kernel<BN, STAGES, STAGED><<<grid, kThreads, smem, s>>>(a, b, c, args);
     return cudaGetLastError();
 }
 
@@ -604,8 +686,20 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // re-reads the input less than several N tiles would)
     const bool halo = d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
     if (halo) BN = d.cout_pad;
+    // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
+    // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
+    // stored through one map whose row dimension spans all groups, so tiles must not cross a group's
+    // last row (TH divides Ho)
+    const int Cq = d.Cout / 4;
+    const bool ps_stage = !halo && BN >= 64 && d.mode == OUT_PS && d.ps_major && Cq % 64 == 0 &&
+                          d.out_h == 2 * Ho && d.out_w == 2 * Wo &&
+                          (d.groups == 1 || d.out_gs == 4LL * Ho * Wo * Cq);
+    const int out_c = (d.mode == OUT_NHWC && d.out_c_stride) ? d.out_c_stride : d.Cout;
+    const bool nhwc_stage = !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 &&
+                            d.out_gs % 8 == 0;
+    const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
-    if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH);
+    if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
     a.tiles_h = (Ho + a.TH - 1) / a.TH;
@@ -623,6 +717,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     if (d.mode == OUT_NHWC && d.out_c_stride) a.out_c = d.out_c_stride;
     a.res = reinterpret_cast<const __nv_bfloat16*>(d.res); a.res_gs = d.res_gs;
     a.err = d.err;
+    a.c_rank = ps_stage ? 5 : 4;
 
     CUtensorMap ma, mb;
     const cuuint64_t esz = 2;
@@ -651,12 +746,38 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (!encode_map(&mb, d.wtc, 3, dims, str, box)) return cudaErrorInvalidValue;
     }
     if (halo) return BN == 16 ? launch_halo<16, 3>(ma, mb, a, s) : launch_halo<64, 2>(ma, mb, a, s);
+    CUtensorMap mc = mb;  // unused by the unstaged kernels
+    if (staged) {
+        bool okc;
+        if (ps_stage) {
+            // [G][2Ho][2Wo][Cq] viewed as (Cq, dx, Wo, dy, G*Ho)
+            cuuint64_t dims[5] = {(cuuint64_t)Cq, 2, (cuuint64_t)Wo, 2, (cuuint64_t)Ho * d.groups};
+            cuuint64_t str[4] = {Cq * esz, 2 * Cq * esz, 2ull * Wo * Cq * esz, 4ull * Wo * Cq * esz};
+            cuuint32_t box[5] = {64, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
+            okc = encode_map(&mc, d.out, 5, dims, str, box);
+        } else {
+            // [G][out_h][out_w][out_c], positions beyond Ho x Wo dropped
+            const int Hd = d.out_h < Ho ? d.out_h : Ho, Wd = d.out_w < Wo ? d.out_w : Wo;
+            cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
+            cuuint64_t str[3] = {out_c * esz, (cuuint64_t)d.out_w * out_c * esz,
+                                 d.groups > 1 ? (cuuint64_t)d.out_gs * esz : (cuuint64_t)d.out_h * d.out_w * out_c * esz};
+            cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+            okc = encode_map(&mc, d.out, 4, dims, str, box);
+        }
+        if (!okc) return cudaErrorInvalidValue;
+        switch (BN) {
+            case 64: return launch_bn<64, 8, true>(ma, mb, mc, a, s);
+            case 128: return launch_bn<128, 5, true>(ma, mb, mc, a, s);
+            case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
+            default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);
+        }
+    }
     switch (BN) {
-        case 16: return launch_bn<16, 8>(ma, mb, a, s);
-        case 64: return launch_bn<64, 8>(ma, mb, a, s);
-        case 128: return launch_bn<128, 6>(ma, mb, a, s);
-        case 192: return launch_bn<192, 5>(ma, mb, a, s);
-        default: return launch_bn<256, 4>(ma, mb, a, s);
+        case 16: return launch_bn<16, 8, false>(ma, mb, mc, a, s);
+        case 64: return launch_bn<64, 8, false>(ma, mb, mc, a, s);
+        case 128: return launch_bn<128, 6, false>(ma, mb, mc, a, s);
+        case 192: return launch_bn<192, 5, false>(ma, mb, mc, a, s);
+        default: return launch_bn<256, 4, false>(ma, mb, mc, a, s);
     }
 }
 

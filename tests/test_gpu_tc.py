@@ -78,6 +78,17 @@ LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
 
 @pytest.mark.parametrize("arch,N,layer,H,W,stride,act,mode,cin_pad", LAYERS)
 def test_tc_layer_vs_float64(arch, N, layer, H, W, stride, act, mode, cin_pad):
+    _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad)
+
+
+@pytest.mark.parametrize("layer,H,W,crop", [(17, 9, 20, (1, 3)), (14, 12, 10, (2, 0)), (11, 5, 7, (0, 1))])
+def test_tc_pixel_shuffle_cropped(layer, H, W, crop):
+    """Pixel-shuffle outputs cropped below 2H x 2W: the per-thread store path of the sub-pixel-major
+    layers (whole outputs go through the shared-memory staging tile and TMA stores)."""
+    _check_layer(1, 2, layer, H, W, 1, 1, 1, 256 if layer == 11 else (128 if layer == 14 else 64), crop)
+
+
+def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0)):
     u = U()
     blob = synthetic.draw_weights(arch, N, seed=3, bias_std=0.1)
     codec = u.Codec(arch, N, 64, blob, "bf16")
@@ -91,7 +102,7 @@ def test_tc_layer_vs_float64(arch, N, layer, H, W, stride, act, mode, cin_pad):
         out = torch.zeros((Ho, Wo, co), dtype=torch.bfloat16, device="cuda")
         oh, ow = Ho, Wo
     elif mode == 1:
-        oh, ow = 2 * Ho, 2 * Wo
+        oh, ow = 2 * Ho - crop[0], 2 * Wo - crop[1]
         out = torch.zeros((oh, ow, co // 4), dtype=torch.bfloat16, device="cuda")
     else:
         oh, ow = 2 * Ho - 3, 2 * Wo - 1      # crop
