@@ -428,27 +428,39 @@ __global__ void __launch_bounds__(kThreads, 1)
 constexpr int kHaloRowBytes = 17 * 1024;  // 130 rows x 128 B, rounded up to the 1024-B swizzle repeat
 constexpr int kHaloBoxBytes = 130 * 128;
 
-template <int BN, int STAGES>
+// Epilogue of the resident-weight kernel.  A tile's BN columns are drained by BN/16 column quarters of
+// 16 columns each (four warps per quarter, one per TMEM lane quarter); with BN = 16 the four quarters
+// form four independent groups that drain four different tiles at once (four TMEM accumulators).
+// OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC through the swizzled staging tile and a
+// TMA store; 2 = final u8 frame (clamp(0.5 + o, 0, 1) x 255, pixel shuffle) through a staging block of
+// the tile's two output rows (3 x 256 bytes each) and TMA stores of 256-byte boxes.
+template <int BN, int STAGES, int OUTK>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        const TcArgs p) {
+                        const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
     constexpr int A_BYTES = 3 * kHaloRowBytes;
     constexpr int B_BYTES = 9 * BN * 128;
-    constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : 128;
-    constexpr int PER = BN / 4 < 16 ? 16 : BN / 4;
-    constexpr int CHUNK = 16;
+    constexpr int CPT = BN / 16;             // column quarters per tile
+    constexpr int EG = 4 / CPT;              // tiles drained concurrently (epilogue groups)
+    constexpr int NACC = EG > 2 ? EG : 2;    // TMEM accumulators
+    constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : 128;
+    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : OUTK == 2 ? EG * 1536 : 0;
+    static_assert(BN == 16 || BN == 64, "resident-weight kernel: N tile of 16 or 64");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sB = smem;
     uint8_t* sA = smem + B_BYTES;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sA + STAGES * A_BYTES);
+    uint8_t* sC = sA + STAGES * A_BYTES;  // staging (OUTK != 0), 1024-byte aligned
+    uint64_t* full = reinterpret_cast<uint64_t*>(sC + C_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* bfull = tempty + 2;
+    uint64_t* tempty = tfull + NACC;
+    uint64_t* bfull = tempty + NACC;
     uint64_t* bfree = bfull + 1;
     uint64_t* drain = bfree + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* cwritten = drain + 1;
+    uint64_t* cfree = cwritten + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
     const float* bias_all = stage_bias(p, sbias);
@@ -459,13 +471,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             ptx::mbar_init(&tfull[a], 1);
-            ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
+            ptx::mbar_init(&tempty[a], 128 * CPT);
         }
         ptx::mbar_init(bfull, 1);
         ptx::mbar_init(bfree, 1);
         ptx::mbar_init(drain, 1);
+        for (int gq = 0; gq < 4; ++gq) {
+            ptx::mbar_init(&cwritten[gq], 128 * CPT);
+            ptx::mbar_init(&cfree[gq], 1);
+        }
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -473,6 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0 && lane == 0) {
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
+        if (OUTK) ptx::prefetch_tmap(&tmC);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -533,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ptx::tc_fence_after();
                     cur_key = key;
                 }
-                const int acc = tl & 1, use = tl >> 1;
+                const int acc = tl % NACC, use = tl / NACC;
                 if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
@@ -558,26 +575,76 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         const int q = warp & 3, colq = (warp - 2) >> 2, row = q * 32 + lane;
-        int tl = 0;
-        for (int t = t_begin; t < t_end; ++t, ++tl) {
-            const int acc = tl & 1, use = tl >> 1;
-            if (!wait_bar(&tfull[acc], use & 1, abort_flag, p.err)) break;
+        const int grp = colq / CPT, cq = colq % CPT;
+        const bool lead_warp = warp == 2 + grp * CPT * 4;
+        const bool elected = OUTK != 0 && lead_warp && lane == 0;
+        int tl = grp, k = 0;
+        for (int t = t_begin + grp; t < t_end; t += EG, tl += EG, ++k) {
+            const int acc = tl % NACC, use = tl / NACC;
+            if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
             const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, key = r / p.Ho;
             const int nt = key % p.n_tiles, g = key / p.n_tiles;
             const int ow = strip * 128 + row;
             const bool valid = ow < p.Wo;
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
-            const int c_begin = colq * PER;
-#pragma unroll 1
-            for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
-                float v[CHUNK];
-                ptx::tmem_ld16(taddr + c, v);
-                if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
-            }
+            const int co0 = nt * BN + cq * 16;
+            float v[16];
+            ptx::tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + cq * 16, v);
             ptx::tc_fence_before();
-            ptx::mbar_arrive(&tempty[acc]);
+            ptx::mbar_arrive(&tempty[acc]);  // the accumulator is in registers: TMEM free for the next tile
+            if constexpr (OUTK == 0) {
+                if (valid) store_cols<16>(p, bias_all, g, oh, ow, co0, v);
+            } else {
+                if (valid) finish_cols<16>(p, bias_all, g, oh, ow, co0, v);
+                if (k > 0) {  // the group's previous TMA stores must have read its staging block
+                    if (elected) {
+                        ptx::bulk_wait_read0();
+                        ptx::mbar_arrive(&cfree[grp]);
+                    }
+                    if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
+                }
+                if constexpr (OUTK == 1) {
+                    const uint32_t base = ptx::smem_u32(sC) + row * 128;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int j = cq * 2 + i;
+                        ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                          pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                          pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                    }
+                } else {
+                    // column co (< 12) = channel co / 4 of sub-pixel (dy, dx) = ((co >> 1) & 1, co & 1); the
+                    // block holds output rows 2 oh + dy, bytes 768 strip + [0, 768) as three 2 x 256 boxes
+                    uint8_t* blk = sC + grp * 1536;
+                    if (valid) {
+#pragma unroll
+                        for (int co = 0; co < 12; ++co) {
+                            const float f = fminf(fmaxf(0.5f + v[co], 0.0f), 1.0f);
+                            const int dy = (co >> 1) & 1, xb = (2 * row + (co & 1)) * 3 + (co >> 2);
+                            blk[(xb >> 8) * 512 + dy * 256 + (xb & 255)] = (uint8_t)rintf(f * 255.0f);
+                        }
+                    }
+                }
+                ptx::fence_proxy_async();
+                ptx::mbar_arrive(&cwritten[grp]);
+                if (lead_warp) {
+                    bool w_ok = true;
+                    if (lane == 0) w_ok = wait_bar(&cwritten[grp], k & 1, abort_flag, p.err);
+                    if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
+                }
+                if (elected) {
+                    if constexpr (OUTK == 1) {
+                        ptx::tma_store_4d(&tmC, sC, nt * BN, strip * 128, oh, g);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            ptx::tma_store_3d(&tmC, sC + grp * 1536 + b * 512, strip * 768 + b * 256, 2 * oh, g);
+                    }
+                    ptx::bulk_commit();
+                }
+            }
         }
+        if (elected) ptx::bulk_wait0();
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -606,12 +673,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 static bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                       const cuuint32_t* box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
+                       const cuuint32_t* box, CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
     cuuint32_t es[5] = {1, 1, 1, 1, 1};
     CUresult r = enc(m, dt, rank, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -652,13 +720,17 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
 // returns a CUDA error or cudaSuccess; UFVC argument problems return cudaErrorInvalidValue.
-template <int BN, int STAGES>
-static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
-    const int smem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + kSmemExtra;
+template <int BN, int STAGES, int OUTK>
+static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
+                               cudaStream_t s) {
+    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : OUTK == 2 ? (64 / BN) * 1536 : 0;
+    constexpr int kSmem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + C_BYTES + kSmemExtra;
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+    const int smem = kSmem;
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e =
-            cudaFuncSetAttribute(conv_tc_halo_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, STAGES, OUTK>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
     }
@@ -669,7 +741,7 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_halo_kernel<BN, STAGES><<<grid, kThreads, smem, s>>>(a, b, args);
+    conv_tc_halo_kernel<BN, STAGES, OUTK><<<grid, kThreads, smem, s>>>(a, b, c, args);
     return cudaGetLastError();
 }
 
@@ -745,8 +817,33 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint32_t box[3] = {64, (cuuint32_t)BN, 1};
         if (!encode_map(&mb, d.wtc, 3, dims, str, box)) return cudaErrorInvalidValue;
     }
-    if (halo) return BN == 16 ? launch_halo<16, 3>(ma, mb, a, s) : launch_halo<64, 2>(ma, mb, a, s);
     CUtensorMap mc = mb;  // unused by the unstaged kernels
+    if (halo) {
+        // staged stores: bf16 NHWC (64 channels per strip pixel), or the final u8 frame whose rows are a
+        // multiple of 16 bytes (three 256-byte boxes per output row pair of a strip)
+        const bool st_nhwc = BN == 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 && d.out_gs % 8 == 0;
+        const bool st_u8 = BN == 16 && d.mode == OUT_PS_FINAL_U8 && d.Cout == 12 && (d.out_w * 3) % 16 == 0 &&
+                           d.out_w <= 2 * Wo && (d.groups == 1 || d.out_gs == (long long)d.out_h * d.out_w * 3);
+        if (st_nhwc) {
+            const int Hd = d.out_h < Ho ? d.out_h : Ho, Wd = d.out_w < Wo ? d.out_w : Wo;
+            cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
+            cuuint64_t str[3] = {out_c * esz, (cuuint64_t)d.out_w * out_c * esz,
+                                 d.groups > 1 ? (cuuint64_t)d.out_gs * esz : (cuuint64_t)d.out_h * d.out_w * out_c * esz};
+            cuuint32_t box[4] = {64, 128, 1, 1};
+            if (!encode_map(&mc, d.out, 4, dims, str, box)) return cudaErrorInvalidValue;
+            return launch_halo<64, 2, 1>(ma, mb, mc, a, s);
+        }
+        if (st_u8) {
+            // [G][out_h][out_w * 3] bytes
+            cuuint64_t dims[3] = {(cuuint64_t)d.out_w * 3, (cuuint64_t)d.out_h, (cuuint64_t)d.groups};
+            cuuint64_t str[2] = {(cuuint64_t)d.out_w * 3, (cuuint64_t)d.out_h * d.out_w * 3};
+            cuuint32_t box[3] = {256, 2, 1};
+            if (!encode_map(&mc, d.out, 3, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE))
+                return cudaErrorInvalidValue;
+            return launch_halo<16, 3, 2>(ma, mb, mc, a, s);
+        }
+        return BN == 16 ? launch_halo<16, 3, 0>(ma, mb, mc, a, s) : launch_halo<64, 2, 0>(ma, mb, mc, a, s);
+    }
     if (staged) {
         bool okc;
         if (ps_stage) {

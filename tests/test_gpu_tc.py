@@ -191,3 +191,17 @@ def test_ps_layer_rejects_other_modes():
     with pytest.raises(u.UfvcError) as e:
         codec.conv_layer(17, x, 1, 1, 0, out)
     assert e.value.code == u.UFVC_ERR_ARG
+
+
+@pytest.mark.parametrize("N,H,W", [(8, 72, 160), (2, 50, 328), (4, 64, 96)])
+def test_bf16_u8_frames_match_f32(N, H, W):
+    """The u8 frame output (TMA stores of whole byte rows where a frame row is a multiple of 16 bytes,
+    per-thread stores otherwise) equals rint(255 x) of the float frame output of the same decode."""
+    u = U()
+    frames = synthetic.moving_texture(11 + W, N, H, W, max_step=8, refresh=0.1)
+    bf = u.Codec(1, N, 256, synthetic.draw_weights(1, N, seed=5), "bf16")
+    bits, n = _run_chunk(bf, torch.from_numpy(frames).cuda(), 32)
+    f = bf.decode_chunk(bits, n, W, H, f32=True)
+    b = bf.decode_chunk(bits, n, W, H)
+    assert bf.sync_status() == 0
+    assert torch.equal(b, torch.round(f * 255.0).to(torch.uint8))
