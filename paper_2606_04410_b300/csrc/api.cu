@@ -53,6 +53,9 @@ struct Plan {
     uint32_t *lw_z = nullptr, *lw_y = nullptr;
     float *dzf = nullptr, *ds1 = nullptr, *ds2 = nullptr, *dmu = nullptr, *dls = nullptr, *yhat = nullptr;
     __nv_bfloat16* yhat_bf = nullptr;
+    // BF16 hyper-analysis inputs, rows and columns rounded up to even sizes (zero) for the stride-2 view
+    int Hye = 0, Wye = 0, hhe = 0, whe = 0;
+    __nv_bfloat16 *y_bf = nullptr, *hb_bf = nullptr;
     // decoder activations: float in FP32 precision, bf16 (same buffers, half used) otherwise
     float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
     bool enc_ready = false, dec_ready = false;
@@ -183,6 +186,8 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         p->Hy = conv_out(p->h3, 3, 2); p->Wy = conv_out(p->w3, 3, 2);
         p->hh = conv_out(p->Hy, 3, 2); p->wh = conv_out(p->Wy, 3, 2);
         p->Hz = conv_out(p->hh, 3, 2); p->Wz = conv_out(p->wh, 3, 2);
+        p->Hye = p->Hy + (p->Hy & 1); p->Wye = p->Wy + (p->Wy & 1);
+        p->hhe = p->hh + (p->hh & 1); p->whe = p->wh + (p->wh & 1);
         p->ny = (size_t)p->Hy * p->Wy * ctx->arch.cy;
         p->nz = (size_t)p->Hz * p->Wz * ctx->arch.cz;
         p->Kz = (size_t)ctx->cfg.lanes < p->nz ? ctx->cfg.lanes : (int)p->nz;
@@ -221,6 +226,12 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         AL(p->cnt_y, (size_t)K);
         AL(p->off_ws, (size_t)p->Kz + K);
         AL(p->zthr, (size_t)kBins - 1);
+        if (ctx->cfg.precision != UFVC_FP32) {
+            AL(p->y_bf, (size_t)p->Hye * p->Wye * a.cy);
+            AL(p->hb_bf, (size_t)p->hhe * p->whe * a.cz);
+            CK(cudaMemset(p->y_bf, 0, (size_t)p->Hye * p->Wye * a.cy * 2));
+            CK(cudaMemset(p->hb_bf, 0, (size_t)p->hhe * p->whe * a.cz * 2));
+        }
         // z^ RMS thresholds for this shape: T_k = floor(npos * exp(2 t_k)), FP64 on the host
         std::vector<uint64_t> zt(kBins - 1);
         const double npos = (double)p->Hz * p->Wz;
@@ -396,7 +407,7 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         off += (size_t)co * k * k * ci + co;
     }
     for (int l = 0; l < L_NENC; ++l)
-        if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1, l <= L_A4)) != UFVC_OK) return bail(st);
+        if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1, l <= L_H2)) != UFVC_OK) return bail(st);
     for (int j = 0; j < D_NDEC; ++j)
         if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true,
                                    j == D_D0 || j == D_U1 || j == D_U2)) != UFVC_OK)
@@ -495,15 +506,26 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     RUN(conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s));
     // cross-frame interaction residual, in place
     RUN(conv(ctx, ctx->enc[L_XB], p->xt, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3));
-    // y is float in every precision (it feeds the FP32 hyper-analysis and the quantiser)
+    // y is float in every precision (it feeds the quantiser)
     RUN(conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s, nullptr, nullptr, 0, 0, 0,
              0, 1, true));
     prof_end(ctx, s, 6);
     prof_begin(ctx, "hyper_analysis", s);
-    RUN(conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s));
-    RUN(conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s));
-    launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
-    prof_end(ctx, s, 3);
+    if (use_tc(ctx, ctx->enc[L_H1])) {
+        // BF16 tensor cores: only the encoder computes z (z^ travels in the bit-stream), so the
+        // hyper-analysis needs no bit-exact twin on the decoder side
+        launch_f32_to_bf16_rows(p->y, p->Hy, p->Wy, a.cy, p->y_bf, p->Wye, s);
+        RUN(conv(ctx, ctx->enc[L_H1], p->y_bf, p->Hye, p->Wye, 2, 1, OUT_NHWC, p->hb_bf, p->hhe, p->whe, s));
+        RUN(conv(ctx, ctx->enc[L_H2], p->hb_bf, p->hhe, p->whe, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s, nullptr,
+                 nullptr, 0, 0, 0, 0, 1, true));
+        launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
+        prof_end(ctx, s, 4);
+    } else {
+        RUN(conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s));
+        RUN(conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s));
+        launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
+        prof_end(ctx, s, 3);
+    }
     RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s));
     prof_begin(ctx, "quantize", s);
     launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);

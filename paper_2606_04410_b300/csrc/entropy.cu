@@ -183,6 +183,23 @@ void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream
     f32_to_bf16_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
 }
 
+// [H][W][C] float -> bf16 rows of pitch Wd pixels (C a multiple of 4); positions beyond W are left as they are
+__global__ void f32_to_bf16_rows_kernel(const float4* a, int H, int W, int C4, __nv_bfloat16* out, int Wd) {
+    const size_t n = (size_t)H * W * C4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / ((size_t)W * C4), rem = i - row * W * C4;
+        const float4 v = a[i];
+        __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(out + (row * Wd * C4 + rem) * 4);
+        d[0] = __floats2bfloat162_rn(v.x, v.y);
+        d[1] = __floats2bfloat162_rn(v.z, v.w);
+    }
+}
+
+void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16* out, int Wd, cudaStream_t s) {
+    const size_t n = (size_t)H * W * (C / 4);
+    f32_to_bf16_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(a), H, W, C / 4, out, Wd);
+}
+
 // ------------------------------------------------------------------------------------------------
 // rANS encode: one thread per lane, lanes of up to two sections in one launch.  Each lane runs its
 // elements backwards (last first) and writes its words backwards into its scratch row, so that the

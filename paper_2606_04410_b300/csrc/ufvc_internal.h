@@ -101,6 +101,7 @@ void launch_scale_index(const float* logsig, size_t n, const float* thr_all, con
                         cudaStream_t s);
 void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s);
 void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s);
+void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16* out, int Wd, cudaStream_t s);
 
 // rANS: a "section job" describes one section of one stream
 struct RansSection {
