@@ -32,6 +32,13 @@ struct LayerW {
     float* btc = nullptr;
 };
 
+// Split-K workspace of the SIMT convolution, grown on first use.  One per direction of a plan (an
+// encode and a decode may run concurrently on different streams) and one for the stage entry points.
+struct Workspace {
+    float* p = nullptr;
+    size_t cap = 0;
+};
+
 struct Plan {
     int W = 0, H = 0, Hp = 0, Wp = 0, C0p = 0;
     int h1 = 0, w1 = 0, h2 = 0, w2 = 0, h3 = 0, w3 = 0, Hy = 0, Wy = 0, hh = 0, wh = 0, Hz = 0, Wz = 0;
@@ -60,6 +67,7 @@ struct Plan {
     float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
     bool enc_ready = false, dec_ready = false;
     std::vector<void*> allocs;
+    Workspace ws_enc, ws_dec;
 };
 
 struct ProfEntry {
@@ -96,6 +104,9 @@ struct ufvc_ctx {
     bool prof_on = false;
     std::vector<ProfEntry> prof;
     size_t prof_n = 0;
+    // SIMT split-K workspace for the stage entry points, and the one the running call uses
+    Workspace ws_stage;
+    Workspace* cur_ws = &ws_stage;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -167,6 +178,8 @@ static bool use_tc(const ufvc_ctx* ctx, const LayerW& L);
 // ------------------------------------------------------------------------------------------------
 static void free_plan(Plan* p) {
     for (void* v : p->allocs) cudaFree(v);
+    cudaFree(p->ws_enc.p);
+    cudaFree(p->ws_dec.p);
     delete p;
 }
 
@@ -359,6 +372,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     cudaFree(ctx->d_status);
     cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
     cudaFree(ctx->st_frames); cudaFree(ctx->st_bits); cudaFree(ctx->st_nbytes);
+    cudaFree(ctx->ws_stage.p);
     for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     delete ctx;
 }
@@ -440,7 +454,20 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
         return UFVC_OK;
     }
     d.Cin = L.cin_p;
-    launch_conv_simt(d, s);
+    const size_t need = conv_simt_workspace(d);
+    if (need) {
+        Workspace* ws = ctx->cur_ws;
+        if (need > ws->cap) {  // first use of this shape: grow (cudaFree waits for the old buffer's users)
+            cudaFree(ws->p);
+            ws->p = nullptr;
+            ws->cap = 0;
+            CK(cudaMalloc(&ws->p, need * sizeof(float)));
+            ws->cap = need;
+        }
+        d.ws = ws->p;
+        d.ws_cap = ws->cap;
+    }
+    CK(launch_conv_simt(d, s));
     return UFVC_OK;
 }
 
@@ -493,6 +520,7 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
 
 static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
     const Arch& a = ctx->arch;
+    ctx->cur_ws = &p->ws_enc;
     prof_begin(ctx, "pack", s);
     if (ctx->cfg.precision == UFVC_FP32)
         launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
@@ -624,6 +652,7 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_begin(ctx, "rans_decode_z", s);
     launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
     prof_end(ctx, s, 1);
+    ctx->cur_ws = &p->ws_dec;
     RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s));
     prof_begin(ctx, "scale_index", s);
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
@@ -757,6 +786,7 @@ extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat
         return st;
     }
 
+    ctx->cur_ws = &ctx->ws_stage;
     st = run_hyper_synthesis(ctx, &tmp, d_zhat, zf, s1, s2, d_mu, d_logsig, s);
     cudaError_t e = cudaStreamSynchronize(s);
     for (void* v : tmp.allocs) cudaFree(v);
@@ -785,6 +815,7 @@ extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int w
     ufvc_status st = get_plan(ctx, width, height, true, &p);
     if (st) return st;
 
+    ctx->cur_ws = &p->ws_dec;
     if (ctx->cfg.precision == UFVC_FP32) {
         RUN(run_decoders(ctx, p, d_yhat, d_frames, OUT_PS_FINAL_F32, s));
     } else {
@@ -817,6 +848,7 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
     const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
     if (use_tc(ctx, L) && L.ps_major && m != OUT_PS)
         return fail(ctx, UFVC_ERR_ARG, "conv_layer: this layer's tensor-core weights are laid out for pixel shuffle");
+    ctx->cur_ws = &ctx->ws_stage;
     RUN(conv(ctx, L, d_in, H, W, stride, act, m, d_out, out_h, out_w, (cudaStream_t)stream));
     CK(cudaGetLastError());
     return UFVC_OK;

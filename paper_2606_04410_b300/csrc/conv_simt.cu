@@ -2,14 +2,16 @@
 //
 // Used for the whole FP32 path and, in every precision, for the hyper-synthesis (the single-step
 // parameter estimation of Sec. 3.4): encoder and decoder must derive bit-identical (mu, log sigma)
-// from z^, so this kernel is deterministic and batch-invariant: every output element accumulates
-// its k*k*Cin products in the same fixed order (taps row-major, then input channels ascending) with
-// explicit fmaf, whatever its tile, group or launch; there is no split-K and no atomic.
+// from z^, so this kernel is deterministic: the arithmetic of an output element depends only on the
+// layer's shapes, never on timing — products accumulate with explicit fmaf in a fixed order (taps
+// row-major, then input channels ascending) and, where the K steps are split into KS contiguous
+// ranges to fill the GPU, the range sums are added in range order by a second kernel.  No atomics.
 //
-// Tile: 128 output pixels x BN output channels per 256-thread CTA, K staged 16 input channels at a
-// time through double-buffered shared memory.  Epilogue: bias, optional GELU, optional residual,
-// optional pixel shuffle x2 / crop / split of the channels into two tensors, or the final frame
-// mapping x^ = clamp(0.5 + o, 0, 1) (float or uint8).
+// Kernels: 128 x BN tiles (BN = 64, or 16 for the narrow final layers) for large layers; 64 x 64
+// tiles with 4 x 4 outputs per thread, optionally split along K, for the small hyper layers.  K is
+// staged 16 input channels at a time through double-buffered shared memory.  Epilogue: bias, optional
+// GELU, optional residual, optional pixel shuffle x2 / crop / split of the channels into two tensors,
+// or the final frame mapping x^ = clamp(0.5 + o, 0, 1) (float or uint8).
 #include "ufvc_internal.h"
 
 namespace ufvc {
@@ -173,25 +175,221 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho
     }
 }
 
-void launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
+// 64 x 64 tile, 256 threads, 4 x 4 outputs per thread (pixels tm*4.., channels tn*4..), K staged BK
+// input channels per step; global loads run two steps ahead of the FMAs (two register sets) and the
+// shared-memory tiles are double-buffered.  blockIdx.z = g * KS + ks: K steps [ks * nsteps / KS,
+// (ks + 1) * nsteps / KS).  PARTIAL: write the range sums to ws[g][ks][m][co] (added by
+// conv_simt_reduce_kernel); otherwise finish the outputs here (KS = 1).
+template <bool PARTIAL, int BK>
+__global__ void __launch_bounds__(256) conv_simt64_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
+    constexpr int BM = 64, BN = 64;
+    constexpr int AV = BM * BK / 4 / 256;  // float4 A loads per thread
+    constexpr int BV = BK * BN / 4 / 256;  // float4 B loads per thread
+    constexpr int CG = BK / 4;             // float4 groups per pixel
+    __shared__ __align__(16) float As[2][BK][BM + 4];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+
+    const int g = blockIdx.z / KS, ks = blockIdx.z - g * KS;
+    const float* in = (const float*)d.in + (size_t)g * d.in_gs;
+    const float* w = d.w + (size_t)g * d.w_gs;
+    const int M = Ho * Wo;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x;
+    const int H = d.H, W = d.W, Cin = d.Cin, Cout = d.Cout, k = d.k, s = d.stride, p = d.k / 2;
+
+    int a_oh[AV], a_ow[AV];
+    bool a_ok[AV];
+#pragma unroll
+    for (int r = 0; r < AV; ++r) {
+        const int m = m0 + (tid + r * 256) / CG;
+        a_ok[r] = m < M;
+        a_oh[r] = a_ok[r] ? m / Wo : 0;
+        a_ow[r] = a_ok[r] ? m - a_oh[r] * Wo : 0;
+    }
+    const int nck = Cin / BK, nsteps = k * k * nck;
+    const int s_begin = (int)((long long)ks * nsteps / KS), s_end = (int)((long long)(ks + 1) * nsteps / KS);
+    float4 ra[2][AV], rb[2][BV];
+    auto load_regs = [&](int step, float4* qa, float4* qb) {
+        const int tap = step / nck, c0 = (step - tap * nck) * BK;
+        const int ky = tap / k, kx = tap - ky * k;
+#pragma unroll
+        for (int r = 0; r < AV; ++r) {
+            const int ih = a_oh[r] * s + ky - p, iw = a_ow[r] * s + kx - p;
+            const int cg = (tid + r * 256) % CG;
+            if (a_ok[r] && ih >= 0 && ih < H && iw >= 0 && iw < W)
+                qa[r] = *reinterpret_cast<const float4*>(in + ((size_t)ih * W + iw) * Cin + c0 + cg * 4);
+            else
+                qa[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < BV; ++r) {
+            const int q = tid + r * 256, row = q >> 4, co = n0 + (q & 15) * 4;
+            if (co < Cout)
+                qb[r] = *reinterpret_cast<const float4*>(w + ((size_t)tap * Cin + c0 + row) * Cout + co);
+            else
+                qb[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store_smem = [&](int buf, const float4* qa, const float4* qb) {
+#pragma unroll
+        for (int r = 0; r < AV; ++r) {
+            const int q = tid + r * 256, pix = q / CG, cg = q % CG;
+            As[buf][cg * 4 + 0][pix] = qa[r].x;
+            As[buf][cg * 4 + 1][pix] = qa[r].y;
+            As[buf][cg * 4 + 2][pix] = qa[r].z;
+            As[buf][cg * 4 + 3][pix] = qa[r].w;
+        }
+#pragma unroll
+        for (int r = 0; r < BV; ++r) {
+            const int q = tid + r * 256;
+            *reinterpret_cast<float4*>(&Bs[buf][q >> 4][(q & 15) * 4]) = qb[r];
+        }
+    };
+
+    const int tn = tid & 15, tm = tid >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    auto fma_tile = [&](int buf) {
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(&As[buf][kk][tm * 4]);
+            const float4 b = *reinterpret_cast<const float4*>(&Bs[buf][kk][tn * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[i][0] = fmaf(av[i], b.x, acc[i][0]);
+                acc[i][1] = fmaf(av[i], b.y, acc[i][1]);
+                acc[i][2] = fmaf(av[i], b.z, acc[i][2]);
+                acc[i][3] = fmaf(av[i], b.w, acc[i][3]);
+            }
+        }
+    };
+    // step t = s_begin + i uses shared buffer i & 1 and register set i & 1; the body is written out
+    // for both parities so that the register sets stay registers
+    if (s_begin < s_end) load_regs(s_begin, ra[0], rb[0]);
+    if (s_begin + 1 < s_end) load_regs(s_begin + 1, ra[1], rb[1]);
+    if (s_begin < s_end) store_smem(0, ra[0], rb[0]);
+    __syncthreads();
+    for (int t = s_begin; t < s_end; t += 2) {
+        if (t + 2 < s_end) load_regs(t + 2, ra[0], rb[0]);
+        fma_tile(0);
+        if (t + 1 < s_end) store_smem(1, ra[1], rb[1]);
+        __syncthreads();
+        if (t + 1 >= s_end) break;
+        if (t + 3 < s_end) load_regs(t + 3, ra[1], rb[1]);
+        fma_tile(1);
+        if (t + 2 < s_end) store_smem(0, ra[0], rb[0]);
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + tm * 4 + i;
+        if (m >= M) continue;
+        const int co0 = n0 + tn * 4;
+        if (PARTIAL) {
+            float* dst = ws + (((size_t)g * KS + ks) * M + m) * Cout + co0;
+            if (co0 + 3 < Cout) {
+                *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (co0 + j < Cout) dst[j] = acc[i][j];
+            }
+            continue;
+        }
+        const int oh = m / Wo, ow = m - oh * Wo;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int co = co0 + j;
+            if (co >= Cout) continue;
+            float v = acc[i][j] + d.b[(size_t)g * d.b_gs + co];
+            if (d.act) v = gelu_erf(v);
+            store_out(d, g, oh, ow, co, v);
+        }
+    }
+}
+
+// out = bias + (((range 0) + range 1) + ...), then the layer's activation and output mapping
+__global__ void conv_simt_reduce_kernel(const ConvDesc d, int Ho, int Wo, int KS, const float* ws) {
+    const int M = Ho * Wo, Cout = d.Cout;
+    const size_t per_g = (size_t)M * Cout, total = per_g * d.groups;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(i / per_g);
+        const size_t r = i - (size_t)g * per_g;
+        const int m = (int)(r / Cout), co = (int)(r - (size_t)m * Cout);
+        const float* src = ws + (size_t)g * KS * per_g + r;
+        float v = src[0];
+        for (int ks = 1; ks < KS; ++ks) v += src[(size_t)ks * per_g];
+        v += d.b[(size_t)g * d.b_gs + co];
+        if (d.act) v = gelu_erf(v);
+        const int oh = m / Wo, ow = m - oh * Wo;
+        store_out(d, g, oh, ow, co, v);
+    }
+}
+
+// The launch rule, shared by the launcher and the workspace query.  Returns the tile kind
+// (0: 128 x 16, 1: 128 x 64, 2: 64 x 64) and, for kind 2, the number of K ranges.
+static int simt_plan(const ConvDesc& d, int* KS) {
+    const int p = d.k / 2;
+    const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
+    const long long M = (long long)Ho * Wo;
+    *KS = 1;
+    if (d.Cout <= 16) return 0;
+    const long long ctas128 = ((M + 127) / 128) * ((d.Cout + 63) / 64) * d.groups;
+    if (ctas128 >= 4 * 148) return 1;
+    // small layers (hyper-analysis / hyper-synthesis): 64 x 64 tiles, K split until two CTAs per SM
+    const long long ctas64 = ((M + 63) / 64) * ((d.Cout + 63) / 64) * d.groups;
+    const int nsteps = d.k * d.k * (d.Cin / (d.Cin % 32 == 0 ? 32 : 16));
+    long long ks = (2 * 148 + ctas64 - 1) / ctas64;
+    if (ks > 9) ks = 9;
+    if (ks > nsteps) ks = nsteps;
+    *KS = (int)(ks < 1 ? 1 : ks);
+    return 2;
+}
+
+size_t conv_simt_workspace(const ConvDesc& d) {
+    int KS;
+    if (simt_plan(d, &KS) != 2 || KS == 1) return 0;
+    const int p = d.k / 2;
+    const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
+    return (size_t)KS * d.groups * Ho * Wo * d.Cout;
+}
+
+cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
     const int p = d.k / 2;
     const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
     const int M = Ho * Wo;
-    if (d.Cout <= 16) {
+    int KS;
+    const int kind = simt_plan(d, &KS);
+    if (kind == 0) {
         dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
         conv_simt_kernel<128, 16><<<grid, 256, 0, st>>>(d, Ho, Wo);
-        return;
-    }
-    const long long ctas128 = (long long)((M + 127) / 128) * ((d.Cout + 63) / 64) * d.groups;
-    if (ctas128 < 2 * 148) {
-        // small layers (hyper-analysis / hyper-synthesis): 32-pixel tiles fill the GPU; the per-element
-        // reduction order is the same as with 128-pixel tiles
-        dim3 grid((M + 31) / 32, (d.Cout + 63) / 64, d.groups);
-        conv_simt_kernel<32, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
-    } else {
+    } else if (kind == 1) {
         dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
         conv_simt_kernel<128, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
+    } else if (KS > 1) {
+        if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;  // caller's workspace
+        dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups * KS);
+        if (d.Cin % 32 == 0)
+            conv_simt64_kernel<true, 32><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+        else
+            conv_simt64_kernel<true, 16><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+        const size_t total = (size_t)d.groups * M * d.Cout;
+        const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+        conv_simt_reduce_kernel<<<blocks, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+    } else {
+        dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups);
+        if (d.Cin % 32 == 0)
+            conv_simt64_kernel<false, 32><<<grid, 256, 0, st>>>(d, Ho, Wo, 1, nullptr);
+        else
+            conv_simt64_kernel<false, 16><<<grid, 256, 0, st>>>(d, Ho, Wo, 1, nullptr);
     }
+    return cudaGetLastError();
 }
 
 }  // namespace ufvc

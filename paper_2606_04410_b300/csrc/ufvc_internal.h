@@ -80,10 +80,14 @@ struct ConvDesc {
     int out_c_stride = 0;       // NHWC output channel count if different from Cout
     const float* btc = nullptr; // tensor-core bias in accumulator-column order (nullptr: same as b)
     int ps_major = 0;           // tensor-core weights in sub-pixel-major column order (pixel shuffle layers)
+    float* ws = nullptr;        // SIMT split-K workspace (conv_simt_workspace(d) floats), or nullptr
+    size_t ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
 };
 
-void launch_conv_simt(const ConvDesc& d, cudaStream_t s);
+cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s);
+// floats of split-K workspace the SIMT launch of d uses (0: none)
+size_t conv_simt_workspace(const ConvDesc& d);
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s);
