@@ -140,6 +140,137 @@ def conv_flops(Hy: int, Wy: int) -> dict:
             "dec.U2": N * p2 * 256 * 64 * 9 * 2, "dec.U3": N * p3 * 12 * 64 * 9 * 2}
 
 
+def conv_bytes(Hy: int, Wy: int, H_: int, W_: int) -> dict:
+    """Algorithmic HBM bytes of each decoder conv stage (bf16 activations read once and written once,
+    residuals read once, the final frames as uint8; weights are negligible)."""
+    a0 = Hy * Wy * 256 * 2                      # y^ (bf16), shared by the N decoders
+    a1, a2, a3 = N * 4 * Hy * Wy * 128 * 2, N * 16 * Hy * Wy * 64 * 2, N * 64 * Hy * Wy * 64 * 2
+    return {"dec.D0": a0 + a1, "dec.R1": 2 * a1 + 3 * a1, "dec.U1": a1 + a2, "dec.R2": 2 * a2 + 3 * a2,
+            "dec.U2": a2 + a3, "dec.U3": a3 + N * H_ * W_ * 3}
+
+
+def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, reps=5) -> dict:
+    """Entropy-coding stress at 4K: n = 8 294 400 symbols round(mu + Laplace(0, b)), b log-uniform on
+    [0.11, 64], scale index = the bin of b under the library's own thresholds; rANS encode and decode of
+    the whole latent as one section per lane count, CUDA-event timed, lossless round trip checked."""
+    import torch
+    import synthetic
+    blob = synthetic.draw_weights(0, 1, seed=0)
+    codec = U.Codec(0, 1, 32, blob, "fp32", device=dev.index or 0)
+    freq, _, thr = codec.get_tables(32)
+    r, b = synthetic.laplace_symbols(n, seed=3)
+    idx = (thr.astype(np.float64)[None, :] < np.log(b)[:, None]).sum(1).astype(np.uint8)
+    ideal_bits = float(-np.log2(freq[idx, r.astype(np.int64) + 255] / 65536.0).sum())
+    vals, cnts = np.unique(r, return_counts=True)
+    pr = cnts / n
+    st, it = torch.from_numpy(r).to(dev), torch.from_numpy(idx).to(dev)
+    out = {"symbols": n, "ideal_bits_per_symbol": ideal_bits / n,
+           "empirical_entropy_bits_per_symbol": float(-(pr * np.log2(pr)).sum()), "lanes": {}}
+    hbm = peaks()["hbm_gbs"]
+    for K_ in lanes:
+        enc_ms, dec_ms = [], []
+        for i in range(reps + 2):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            sec, nb = codec.rans_encode(st, it, K_)
+            e1.record()
+            nbytes = int(nb.item())
+            e1b = torch.cuda.Event(enable_timing=True)
+            e1b.record()
+            dec = codec.rans_decode(sec, nbytes, it, n, K_)
+            e2.record()
+            torch.cuda.synchronize()
+            if i >= 2:
+                enc_ms.append(e0.elapsed_time(e1))
+                dec_ms.append(e1b.elapsed_time(e2))
+        assert codec.sync_status() == 0 and torch.equal(dec, st), f"rANS round trip failed at K={K_}"
+        te, td = statistics.median(enc_ms), statistics.median(dec_ms)
+        be, bd = 3 * n + nbytes, nbytes + n + 2 * n
+        out["lanes"][str(K_)] = {
+            "bytes": nbytes, "bits_per_symbol": 8 * nbytes / n, "overhead_vs_ideal": 8 * nbytes / ideal_bits - 1,
+            "enc_ms": te, "dec_ms": td, "enc_gbs": be / te / 1e6, "dec_gbs": bd / td / 1e6,
+            "enc_hbm_frac": be / te / 1e6 / hbm, "dec_hbm_frac": bd / td / 1e6 / hbm,
+            "enc_ns_per_lane_symbol": te * 1e6 / (n / K_), "dec_ns_per_lane_symbol": td * 1e6 / (n / K_),
+            "round_trip": "lossless"}
+    codec.close()
+    return out
+
+
+SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
+
+
+def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n_streams: int = 64,
+                  seed: int = 0, drain_s: float = 90.0) -> dict:
+    """Serving mix: n_streams streams of the SERVING_MIX resolutions (assigned by seed), each with Poisson
+    chunk arrivals at 30 fps (one 8-frame chunk per Exp(mean 8/30 s)), requests alternating encode and
+    decode (a decode codes the stream's latest device-resident bit-stream), submitted in real time for
+    window_s seconds to the continuous-batching server (HBM cap 150 GB).  Latency = submit -> completion
+    on the server's clock; frames/s = frames of the completed requests / (last completion - first submit).
+    Content: the 1080p synthetic chunk, cropped for the smaller sizes and tiled 2 x 2 for 4K."""
+    import torch
+    rng = np.random.default_rng(seed)
+    sizes = [sz for sz, _ in SERVING_MIX]
+    which = rng.choice(len(sizes), size=n_streams, p=[p for _, p in SERVING_MIX])
+    src = torch.from_numpy(frames_1080p).to(dev)
+    content = {}
+    for W_, H_ in sizes:
+        if W_ <= 1920:
+            content[(W_, H_)] = src[:, :H_, :W_].contiguous()
+        else:
+            content[(W_, H_)] = src.repeat(1, 2, 2, 1)[:, :H_, :W_].contiguous()
+    srv = U.Server(1, N, K, blob, precision, hbm_cap_bytes=150 << 30, max_slots=8, device=dev.index or 0)
+    sids = []
+    for j in range(n_streams):
+        W_, H_ = sizes[which[j]]
+        sid = srv.open_stream(W_, H_, QP)
+        srv.streams[sid]["frames_in"].copy_(content[(W_, H_)])
+        sids.append(sid)
+    torch.cuda.synchronize()
+    # warm-up: every stream once (slots, plans, workspaces, graph capture), then drain
+    warm = []
+    for _ in range(2):
+        for sid in sids:
+            warm.append(srv.submit(sid, U.UFVC_OP_ENCODE))
+            warm.append(srv.submit(sid, U.UFVC_OP_DECODE))
+    for t in warm:
+        assert srv.wait(t, 600000.0)["status"] == 0
+    # arrival trace
+    events = []
+    for j, sid in enumerate(sids):
+        t, op = rng.exponential(8 / 30), U.UFVC_OP_ENCODE
+        while t < window_s:
+            events.append((t, sid, op))
+            op = U.UFVC_OP_DECODE if op == U.UFVC_OP_ENCODE else U.UFVC_OP_ENCODE
+            t += rng.exponential(8 / 30)
+    events.sort()
+    tickets = []
+    t0 = time.perf_counter()
+    for t, sid, op in events:
+        d = t0 + t - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append((sid, op, srv.submit(sid, op)))
+    res = [(sid, op, srv.wait(tk, drain_s * 1000.0)) for sid, op, tk in tickets]
+    done = [(sid, op, r) for sid, op, r in res if r["status"] == 0]
+    pending = sum(1 for _, _, r in res if r["status"] == U.UFVC_PENDING)
+    st = srv.stats()
+    lat = np.array([r["done_ms"] - r["submit_ms"] for _, _, r in done]) if done else np.zeros(1)
+    lat_e = np.array([r["done_ms"] - r["submit_ms"] for _, op, r in done if op == U.UFVC_OP_ENCODE] or [0.0])
+    lat_d = np.array([r["done_ms"] - r["submit_ms"] for _, op, r in done if op == U.UFVC_OP_DECODE] or [0.0])
+    span_ms = (max(r["done_ms"] for _, _, r in done) - min(r["submit_ms"] for _, _, r in res)) if done else 1.0
+    out = {"streams": n_streams, "mix": {f"{w}x{h}": int((which == i).sum()) for i, (w, h) in enumerate(sizes)},
+           "window_s": window_s, "requests": len(events), "completed": len(done), "pending_after_drain": pending,
+           "frames_per_s": N * len(done) / (span_ms / 1000.0),
+           "offered_frames_per_s": N * len(events) / window_s,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "enc_p50": float(np.percentile(lat_e, 50)), "enc_p99": float(np.percentile(lat_e, 99)),
+                          "dec_p50": float(np.percentile(lat_d, 50)), "dec_p99": float(np.percentile(lat_d, 99))},
+           "slots": st["slots"], "graphs": st["graphs"], "hbm_used_gb": st["hbm_used"] / 2**30,
+           "hbm_cap_gb": 150}
+    srv.close()
+    return out
+
+
 def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist=None, world=1):
     """Encode + decode one chunk per step; per-step CUDA events on the launching stream, L2 flushed
     between steps (outside the events).  Returns timings, stage profile, stream size and PSNR."""
@@ -195,6 +326,9 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--no-entropy-sweep", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -240,21 +374,38 @@ def main() -> None:
     launches_per_step = sum(sum(n for _, n in v) for v in prof_acc.values()) / args.steps
     hy, wy = -(-H_ // 16), -(-W_ // 16)
     flops = conv_flops(hy, wy)
+    cbytes = conv_bytes(hy, wy, H_, W_)
     conv_stages = {k: v for k, v in stage_ms.items() if k in flops}
     top = max(conv_stages, key=conv_stages.get)
     pk = peaks()
+    hbm = pk["hbm_gbs"]
     if args.precision == "fp32":
         peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        bound, peak_src = "alu", f"derived: 148 SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2032.0):.0f} MHz"
+        cbound, peak_src = "alu", f"derived: 148 SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2032.0):.0f} MHz"
     else:
         peak = pk["bf16_tflops_sustained"] if args.precision == "bf16" else 2 * pk["bf16_tflops_sustained"]
-        bound = "tensor"
+        cbound = "tensor"
         peak_src = f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")
-    achieved = flops[top] / (conv_stages[top] / 1000.0) / 1e12
+
+    def stage_roof(k: str) -> dict:
+        """A decoder conv stage against its own bound: compute or HBM, whichever takes longer at peak."""
+        t = conv_stages[k] / 1000.0
+        if flops[k] / (peak * 1e12) >= cbytes[k] / (hbm * 1e9):
+            return {"bound": cbound, "achieved": flops[k] / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": flops[k] / t / 1e12 / peak, "algorithmic": flops[k], "ms": conv_stages[k]}
+        return {"bound": "hbm", "achieved": cbytes[k] / t / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": cbytes[k] / t / 1e9 / hbm, "algorithmic": cbytes[k], "ms": conv_stages[k]}
+
+    stages = {k: stage_roof(k) for k in conv_stages}
+    kern = {"dec.U3": "conv_tc_halo_kernel<16,3,2>", "dec.R2": "conv_tc_halo_kernel<64,2,1>"}
+    tr = stages[top]
     dec_conv_ms = sum(v for k, v in stage_total_ms.items() if k in flops)
-    roofline = {"bound": bound, "kernel": f"conv_tc {top}" if bound == "tensor" else f"conv_simt {top}",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": peak_src,
+    roofline = {"bound": tr["bound"], "kernel": (kern.get(top, "conv_tc_kernel") if args.precision != "fp32"
+                                                 else "conv_simt") + f" ({top})",
+                "achieved": tr["achieved"], "peak": tr["peak"], "unit": tr["unit"], "frac": tr["frac"],
+                "traffic": None, "peak_source": peak_src if tr["bound"] != "hbm" else f"{pk['source']} HBM copy",
+                "decoder_conv_stages": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
+                                            for kk, vv in v.items()} for k, v in stages.items()},
                 "decoder_convs": {"tflops": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12,
                                   "frac": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12 / peak},
                 "stage_ms_per_step": {k: round(v, 4) for k, v in
@@ -317,6 +468,13 @@ def main() -> None:
             line["speedup_vs_fp32"] = value / fp32["value"]
             line["dpsnr_db_vs_fp32"] = r["psnr"] - fp32["psnr_db"]
             line["dbitrate_vs_fp32"] = (r["nbytes"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
+        if not args.no_entropy_sweep:
+            line["entropy_sweep"] = entropy_sweep(U, dev)
+        if not args.no_serving and (W_, H_) == (W, H):
+            serving = {args.precision: serving_bench(U, dev, frames_np, blob, args.precision, args.serving_window)}
+            if args.precision != "fp32" and not args.no_fp32_path:
+                serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", args.serving_window / 2)
+            line["serving"] = serving
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line))

@@ -118,6 +118,13 @@ ufvc_status ufvc_decode_chunk(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyte
 ufvc_status ufvc_decode_chunk_f32(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, float* d_frames,
                                   int n_frames, int width, int height, void* stream);
 
+/* As ufvc_decode_chunk for a bit-stream whose size is known only on the device, as ufvc_encode_chunk
+ * left it in *d_nbytes: reads stay within `capacity` bytes of d_bits and the stream must end exactly
+ * at *d_nbytes (else status UFVC_ERR_CORRUPT).  Nothing is read back to the host, so the call can be
+ * captured in a CUDA graph and replayed for every stream that the same buffers carry. */
+ufvc_status ufvc_decode_chunk_dev(ufvc_ctx* ctx, const uint8_t* d_bits, size_t capacity, const uint64_t* d_nbytes,
+                                  uint8_t* d_frames, int n_frames, int width, int height, void* stream);
+
 /* Host-buffer variants (the call a user without device buffers makes): copy h_frames / h_bits to a
  * context-owned device staging area, run the chunk on `stream`, copy the result back, synchronise.
  * *nbytes receives the stream size.  Return the device status of the call. */
@@ -206,6 +213,74 @@ ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, int* launche
 
 /* Human-readable description of the last error on this context ("" if none). */
 const char* ufvc_last_error(const ufvc_ctx* ctx);
+
+/* ------------------------------------------------------------------------------------------------
+ * Serving: continuous batching of chunk requests from many streams (the cross-chunk overlap that
+ * Sec. 4 leaves as potential; the paper's own pipeline codes one chunk at a time).
+ *
+ * A server owns one weight copy and a pool of execution slots.  A slot is a context sharing those
+ * weights, a CUDA stream, device staging buffers for one frame size, and the CUDA graphs of its
+ * encode and decode calls (captured after the slot's first direct run).  Each stream (a video, opened
+ * with its frame size and qp) owns device-resident buffers: the input chunk, its latest bit-stream
+ * (bytes + size) and the latest decoded chunk.  A host scheduler thread admits queued requests as
+ * slots free up: a request runs on an idle slot of its frame size, or on a new slot if the pool has
+ * room and the HBM cap allows the slot's footprint (idle slots of other sizes are released to make
+ * room); requests of one stream run in submission order; requests on different slots overlap on the
+ * device.  Results are identical to the single-context calls (same kernels, same arithmetic).
+ *
+ * All server calls are thread-safe.  Device pointers returned by ufvc_server_stream_buffers stay valid
+ * until the server is destroyed; the input buffer must not be modified while an encode request of the
+ * stream is queued or running, and the outputs are stable once the request completed.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct ufvc_server ufvc_server;
+
+typedef enum { UFVC_OP_ENCODE = 0, UFVC_OP_DECODE = 1 } ufvc_op;
+
+typedef struct {
+    int status;          /* ufvc_status of the request (UFVC_PENDING while queued or running) */
+    int op;              /* ufvc_op */
+    int stream_id;
+    int slot;            /* slot that ran it (-1 while queued) */
+    double submit_ms;    /* host steady-clock times, milliseconds since the server was created */
+    double start_ms;     /* launched on a slot */
+    double done_ms;      /* completion observed by the scheduler */
+    uint64_t nbytes;     /* encode: bit-stream size (read back at completion); decode: the size decoded */
+} ufvc_result;
+
+typedef struct {
+    int slots;                /* slots alive */
+    int busy_slots;
+    int queued;               /* requests waiting for a slot */
+    int graphs;               /* CUDA graphs instantiated */
+    uint64_t completed;       /* requests finished */
+    size_t hbm_used;          /* bytes held: streams' buffers + slots' footprints */
+    size_t hbm_cap;
+} ufvc_server_stats;
+
+/* cfg / weights as for ufvc_create.  hbm_cap_bytes bounds the device bytes the server holds besides
+ * its weight copy (0: no cap); max_slots bounds concurrent requests (>= 1). */
+ufvc_status ufvc_server_create(const ufvc_config* cfg, const float* weights, size_t n_weights, size_t hbm_cap_bytes,
+                               int max_slots, ufvc_server** out);
+/* Waits for all requests, then frees everything. */
+void ufvc_server_destroy(ufvc_server* srv);
+/* A new stream of width x height chunks at rate qp; its buffers count against the HBM cap
+ * (UFVC_ERR_OOM if they do not fit). */
+ufvc_status ufvc_server_open_stream(ufvc_server* srv, int width, int height, int qp, int* stream_id);
+/* The stream's device buffers (any pointer argument may be NULL): d_frames_in [N][H][W][3] uint8 (the
+ * caller writes the chunk to encode there), d_bits / *d_nbytes (the latest bit-stream, capacity bytes),
+ * d_frames_out [N][H][W][3] uint8 (the latest decoded chunk). */
+ufvc_status ufvc_server_stream_buffers(ufvc_server* srv, int stream_id, uint8_t** d_frames_in, uint8_t** d_bits,
+                                       uint64_t** d_nbytes, size_t* capacity, uint8_t** d_frames_out);
+/* Queue a request; returns at once with its ticket.  ENCODE codes the stream's input buffer into its
+ * bit-stream buffers; DECODE decodes the stream's latest bit-stream into its output buffer. */
+ufvc_status ufvc_server_submit(ufvc_server* srv, int stream_id, int op, uint64_t* ticket);
+/* The request's result; returns UFVC_PENDING while it is queued or running, else its status. */
+ufvc_status ufvc_server_poll(ufvc_server* srv, uint64_t ticket, ufvc_result* out);
+/* Blocks until the request completed (timeout_ms < 0: no limit; UFVC_PENDING on timeout). */
+ufvc_status ufvc_server_wait(ufvc_server* srv, uint64_t ticket, double timeout_ms, ufvc_result* out);
+ufvc_status ufvc_server_stats_get(ufvc_server* srv, ufvc_server_stats* out);
+/* Message of the last server-level error ("" if none). */
+const char* ufvc_server_last_error(const ufvc_server* srv);
 
 #ifdef __cplusplus
 }

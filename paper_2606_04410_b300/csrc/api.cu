@@ -8,6 +8,8 @@
 // grouped launches (group = frame position, each with its own weights).
 #include "ufvc_internal.h"
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -107,6 +109,8 @@ struct ufvc_ctx {
     // SIMT split-K workspace for the stage entry points, and the one the running call uses
     Workspace ws_stage;
     Workspace* cur_ws = &ws_stage;
+    // weights and tables borrowed from another context (ctx_clone_shared): not freed here
+    bool borrowed = false;
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -183,46 +187,55 @@ static void free_plan(Plan* p) {
     delete p;
 }
 
-static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out) {
-    const long long key = ((long long)W << 20) | H;
-    Plan* p;
-    auto it = ctx->plans.find(key);
-    if (it == ctx->plans.end()) {
-        p = new Plan();
-        p->W = W; p->H = H;
-        p->Hp = ceil_div(H, 16) * 16; p->Wp = ceil_div(W, 16) * 16;
-        // packed input channels: 16-multiple for the SIMT kernel, 64-multiple (one 128-byte K chunk) for tcgen05
-        p->C0p = ctx->cfg.precision == UFVC_FP32 ? ceil_div(3 * ctx->N, 16) * 16 : ceil_div(3 * ctx->N, 64) * 64;
-        p->h1 = conv_out(p->Hp, 3, 2); p->w1 = conv_out(p->Wp, 3, 2);
-        p->h2 = conv_out(p->h1, 3, 2); p->w2 = conv_out(p->w1, 3, 2);
-        p->h3 = conv_out(p->h2, 3, 2); p->w3 = conv_out(p->w2, 3, 2);
-        p->Hy = conv_out(p->h3, 3, 2); p->Wy = conv_out(p->w3, 3, 2);
-        p->hh = conv_out(p->Hy, 3, 2); p->wh = conv_out(p->Wy, 3, 2);
-        p->Hz = conv_out(p->hh, 3, 2); p->Wz = conv_out(p->wh, 3, 2);
-        p->Hye = p->Hy + (p->Hy & 1); p->Wye = p->Wy + (p->Wy & 1);
-        p->hhe = p->hh + (p->hh & 1); p->whe = p->wh + (p->wh & 1);
-        p->ny = (size_t)p->Hy * p->Wy * ctx->arch.cy;
-        p->nz = (size_t)p->Hz * p->Wz * ctx->arch.cz;
-        p->Kz = (size_t)ctx->cfg.lanes < p->nz ? ctx->cfg.lanes : (int)p->nz;
-        p->cap_z = (int)(p->nz / p->Kz + 3);
-        p->cap_y = (int)(p->ny / ctx->cfg.lanes + 3);
-        p->hdr = (20 + (size_t)ctx->arch.cz + 3) & ~(size_t)3;
-        ctx->plans[key] = p;
-    } else {
-        p = it->second;
-    }
+static void init_plan_shape(const ufvc_ctx* ctx, Plan* p, int W, int H) {
+    p->W = W; p->H = H;
+    p->Hp = ceil_div(H, 16) * 16; p->Wp = ceil_div(W, 16) * 16;
+    // packed input channels: 16-multiple for the SIMT kernel, 64-multiple (one 128-byte K chunk) for tcgen05
+    p->C0p = ctx->cfg.precision == UFVC_FP32 ? ceil_div(3 * ctx->N, 16) * 16 : ceil_div(3 * ctx->N, 64) * 64;
+    p->h1 = conv_out(p->Hp, 3, 2); p->w1 = conv_out(p->Wp, 3, 2);
+    p->h2 = conv_out(p->h1, 3, 2); p->w2 = conv_out(p->w1, 3, 2);
+    p->h3 = conv_out(p->h2, 3, 2); p->w3 = conv_out(p->w2, 3, 2);
+    p->Hy = conv_out(p->h3, 3, 2); p->Wy = conv_out(p->w3, 3, 2);
+    p->hh = conv_out(p->Hy, 3, 2); p->wh = conv_out(p->Wy, 3, 2);
+    p->Hz = conv_out(p->hh, 3, 2); p->Wz = conv_out(p->wh, 3, 2);
+    p->Hye = p->Hy + (p->Hy & 1); p->Wye = p->Wy + (p->Wy & 1);
+    p->hhe = p->hh + (p->hh & 1); p->whe = p->wh + (p->wh & 1);
+    p->ny = (size_t)p->Hy * p->Wy * ctx->arch.cy;
+    p->nz = (size_t)p->Hz * p->Wz * ctx->arch.cz;
+    p->Kz = (size_t)ctx->cfg.lanes < p->nz ? ctx->cfg.lanes : (int)p->nz;
+    p->cap_z = (int)(p->nz / p->Kz + 3);
+    p->cap_y = (int)(p->ny / ctx->cfg.lanes + 3);
+    p->hdr = (20 + (size_t)ctx->arch.cz + 3) & ~(size_t)3;
+}
+
+// The device buffers of a plan's encoder (enc) and decoder (dec) halves: allocated, or with dry_bytes only
+// counted (256-byte granules).  Activations that the tensor cores read and write are bf16 in BF16
+// precision (the float-typed buffers are then half used), float otherwise.
+static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size_t* dry_bytes) {
     const Arch& a = ctx->arch;
     const int N = ctx->N, K = ctx->cfg.lanes;
+    const bool fp32 = ctx->cfg.precision == UFVC_FP32;
+    const size_t act = fp32 ? 1 : 2;  // activation elements per float
     ufvc_status st = UFVC_OK;
-#define AL(ptr, n) if ((st = dalloc(ctx, p, &(ptr), (n))) != UFVC_OK) return st
-    if (!for_decode && !p->enc_ready) {
-        AL(p->x, (size_t)p->Hp * p->Wp * p->C0p);
-        AL(p->a1, (size_t)p->h1 * p->w1 * a.e0);
-        AL(p->a2, (size_t)p->h2 * p->w2 * a.e1);
-        AL(p->a3, (size_t)p->h3 * p->w3 * a.e2);
-        AL(p->xt, (size_t)p->h3 * p->w3 * a.e2);
+#define AL(ptr, n)                                                                        \
+    do {                                                                                  \
+        const size_t n_ = (n);                                                            \
+        if (dry_bytes) *dry_bytes += (n_ * sizeof(*(ptr)) + 255) & ~(size_t)255;          \
+        else if ((st = dalloc(ctx, p, &(ptr), n_)) != UFVC_OK) return st;                 \
+    } while (0)
+    if (enc) {
+        AL(p->x, ((size_t)p->Hp * p->Wp * p->C0p + act - 1) / act);
+        AL(p->a1, ((size_t)p->h1 * p->w1 * a.e0 + act - 1) / act);
+        AL(p->a2, ((size_t)p->h2 * p->w2 * a.e1 + act - 1) / act);
+        AL(p->a3, ((size_t)p->h3 * p->w3 * a.e2 + act - 1) / act);
+        AL(p->xt, ((size_t)p->h3 * p->w3 * a.e2 + act - 1) / act);
         AL(p->y, p->ny);
-        AL(p->hb, (size_t)p->hh * p->wh * a.cz);
+        if (fp32) {
+            AL(p->hb, (size_t)p->hh * p->wh * a.cz);
+        } else {
+            AL(p->y_bf, (size_t)p->Hye * p->Wye * a.cy);
+            AL(p->hb_bf, (size_t)p->hhe * p->whe * a.cz);
+        }
         AL(p->z, p->nz);
         AL(p->zf, p->nz);
         AL(p->s1, (size_t)4 * p->Hz * p->Wz * a.cz);
@@ -239,20 +252,8 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         AL(p->cnt_y, (size_t)K);
         AL(p->off_ws, (size_t)p->Kz + K);
         AL(p->zthr, (size_t)kBins - 1);
-        if (ctx->cfg.precision != UFVC_FP32) {
-            AL(p->y_bf, (size_t)p->Hye * p->Wye * a.cy);
-            AL(p->hb_bf, (size_t)p->hhe * p->whe * a.cz);
-            CK(cudaMemset(p->y_bf, 0, (size_t)p->Hye * p->Wye * a.cy * 2));
-            CK(cudaMemset(p->hb_bf, 0, (size_t)p->hhe * p->whe * a.cz * 2));
-        }
-        // z^ RMS thresholds for this shape: T_k = floor(npos * exp(2 t_k)), FP64 on the host
-        std::vector<uint64_t> zt(kBins - 1);
-        const double npos = (double)p->Hz * p->Wz;
-        for (int k = 0; k < kBins - 1; ++k) zt[k] = (uint64_t)std::floor(npos * std::exp(2.0 * ctx->tabs.log_thr[k]));
-        CK(cudaMemcpy(p->zthr, zt.data(), zt.size() * 8, cudaMemcpyHostToDevice));
-        p->enc_ready = true;
     }
-    if (for_decode && !p->dec_ready) {
+    if (dec) {
         AL(p->dzhat, p->nz);
         AL(p->diz, (size_t)a.cz);
         AL(p->didx, p->ny);
@@ -268,22 +269,68 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         AL(p->ds2, (size_t)p->Hy * p->Wy * a.cz);
         AL(p->dmu, p->ny);
         AL(p->dls, p->ny);
-        AL(p->yhat, p->ny);
-        AL(p->yhat_bf, p->ny);
+        if (fp32) AL(p->yhat, p->ny);
+        else AL(p->yhat_bf, p->ny);
         AL(p->drhat, p->ny);
         const size_t n1 = (size_t)N * 4 * p->Hy * p->Wy * a.cd1;
         const size_t n2 = (size_t)N * 16 * p->Hy * p->Wy * a.cd2;
         const size_t n3 = (size_t)N * 64 * p->Hy * p->Wy * a.cd2;
-        AL(p->bufA, n1);
-        AL(p->bufT, n1);
-        AL(p->bufB, n2);
-        AL(p->bufT2, n2);
-        AL(p->bufC, n3);
-        p->dec_ready = true;
+        AL(p->bufA, (n1 + act - 1) / act);
+        AL(p->bufT, (n1 + act - 1) / act);
+        AL(p->bufB, (n2 + act - 1) / act);
+        AL(p->bufT2, (n2 + act - 1) / act);
+        AL(p->bufC, (n3 + act - 1) / act);
     }
 #undef AL
+    return UFVC_OK;
+}
+
+static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out) {
+    const long long key = ((long long)W << 20) | H;
+    Plan* p;
+    auto it = ctx->plans.find(key);
+    if (it == ctx->plans.end()) {
+        p = new Plan();
+        init_plan_shape(ctx, p, W, H);
+        ctx->plans[key] = p;
+    } else {
+        p = it->second;
+    }
+    ufvc_status st = plan_buffers(ctx, p, !for_decode && !p->enc_ready, for_decode && !p->dec_ready, nullptr);
+    if (st) return st;
+    if (!for_decode && !p->enc_ready) {
+        // z^ RMS thresholds for this shape: T_k = floor(npos * exp(2 t_k)), FP64 on the host
+        std::vector<uint64_t> zt(kBins - 1);
+        const double npos = (double)p->Hz * p->Wz;
+        for (int k = 0; k < kBins - 1; ++k) zt[k] = (uint64_t)std::floor(npos * std::exp(2.0 * ctx->tabs.log_thr[k]));
+        CK(cudaMemcpy(p->zthr, zt.data(), zt.size() * 8, cudaMemcpyHostToDevice));
+        if (ctx->cfg.precision != UFVC_FP32) {
+            CK(cudaMemset(p->y_bf, 0, (size_t)p->Hye * p->Wye * ctx->arch.cy * 2));
+            CK(cudaMemset(p->hb_bf, 0, (size_t)p->hhe * p->whe * ctx->arch.cz * 2));
+        }
+        p->enc_ready = true;
+    }
+    if (for_decode && !p->dec_ready) p->dec_ready = true;
     *out = p;
     return UFVC_OK;
+}
+
+// Device bytes one W x H plan of ctx takes once it has encoded and decoded: its buffers plus the
+// split-K workspaces of the hyper-synthesis (one per direction).
+size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
+    Plan tmp;
+    init_plan_shape(ctx, &tmp, W, H);
+    size_t bytes = 0;
+    plan_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, true, &bytes);
+    const Arch& a = ctx->arch;
+    auto ws = [&](int h, int w, int k, int cout, int cin) {
+        ConvDesc d;
+        d.H = h; d.W = w; d.k = k; d.stride = 1; d.Cout = cout; d.Cin = ceil_div(cin, 16) * 16; d.groups = 1;
+        return conv_simt_workspace(d) * sizeof(float);
+    };
+    const size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
+                                ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
+    return bytes + 2 * hs;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -364,11 +411,14 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
 extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->cfg.device);
-    cudaDeviceSynchronize();
+    if (!ctx->borrowed) cudaDeviceSynchronize();  // a clone's owner has synchronised its stream
     for (auto& kv : ctx->plans) free_plan(kv.second);
-    for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
-    for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
-    cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep); cudaFree(ctx->d_qinv);
+    if (!ctx->borrowed) {
+        for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
+        for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
+        cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
+        cudaFree(ctx->d_qinv);
+    }
     cudaFree(ctx->d_status);
     cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
     cudaFree(ctx->st_frames); cudaFree(ctx->st_bits); cudaFree(ctx->st_nbytes);
@@ -428,6 +478,33 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
             return bail(st);
     *out = ctx;
     return UFVC_OK;
+}
+
+// A context that shares base's weights and tables (read-only on the device) but has its own plans,
+// workspaces, staging and status word, so that it can run concurrently with base on another stream.
+// base must outlive it.
+ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
+    if (!base || base->borrowed) return nullptr;
+    if (cudaSetDevice(base->cfg.device) != cudaSuccess) return nullptr;
+    auto* c = new ufvc_ctx();
+    c->cfg = base->cfg;
+    c->arch = base->arch;
+    c->N = base->N;
+    c->tabs = base->tabs;
+    c->d_packed = base->d_packed;
+    c->d_coarse = base->d_coarse;
+    c->d_thr = base->d_thr;
+    c->d_qstep = base->d_qstep;
+    c->d_qinv = base->d_qinv;
+    for (int l = 0; l < L_NENC; ++l) c->enc[l] = base->enc[l];
+    for (int l = 0; l < D_NDEC; ++l) c->dec[l] = base->dec[l];
+    c->borrowed = true;
+    if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return nullptr;
+    }
+    return c;
 }
 
 extern "C" const char* ufvc_last_error(const ufvc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -627,8 +704,9 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     return UFVC_OK;
 }
 
+// nbytes: the stream size, or (with d_nbytes) the readable capacity, the size then being read on the device
 static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, void* d_frames, int final_mode,
-                               int n_frames, int width, int height, void* stream) {
+                               int n_frames, int width, int height, void* stream, const uint64_t* d_nbytes = nullptr) {
     if (!ctx || !d_bits || !d_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
         return fail(ctx, UFVC_ERR_ARG, "decode_chunk: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -647,7 +725,7 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     RansDecodeJob jy{d_bits, nbytes, 0, p->next_z, p->didx, 0, p->ny, ctx->cfg.lanes, p->lo_y, p->lw_y, p->next_y,
                      p->drhat};
     launch_rans_parse(jz, ctx->d_status, s);
-    launch_rans_parse_expect(jy, nbytes, ctx->d_status, s);
+    launch_rans_parse_expect(jy, nbytes, d_nbytes, ctx->d_status, s);
     prof_end(ctx, s, 3);
     prof_begin(ctx, "rans_decode_z", s);
     launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
@@ -675,6 +753,13 @@ extern "C" ufvc_status ufvc_decode_chunk(ufvc_ctx* ctx, const uint8_t* d_bits, s
 extern "C" ufvc_status ufvc_decode_chunk_f32(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, float* d_frames,
                                              int n_frames, int width, int height, void* stream) {
     return decode_impl(ctx, d_bits, nbytes, d_frames, OUT_PS_FINAL_F32, n_frames, width, height, stream);
+}
+
+extern "C" ufvc_status ufvc_decode_chunk_dev(ufvc_ctx* ctx, const uint8_t* d_bits, size_t capacity,
+                                             const uint64_t* d_nbytes, uint8_t* d_frames, int n_frames, int width,
+                                             int height, void* stream) {
+    if (!d_nbytes) return fail(ctx, UFVC_ERR_ARG, "decode_chunk_dev: null size");
+    return decode_impl(ctx, d_bits, capacity, d_frames, OUT_PS_FINAL_U8, n_frames, width, height, stream, d_nbytes);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -430,13 +430,14 @@ void launch_rans_finalize(const RansSection* secs, int nsec, uint8_t* out, size_
 // per lane; every read stays inside the lane's words; a lane that ends with a state != 2^16 or with
 // unread / missing words marks the stream corrupt.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kScanThreads) rans_parse_kernel(const RansDecodeJob J, size_t expect_end,
-                                                                  int* status) {
+__global__ void __launch_bounds__(kScanThreads) rans_parse_kernel(const RansDecodeJob J, size_t expect_end_host,
+                                                                  const uint64_t* expect_end_dev, int* status) {
     __shared__ typename BlockScanU64::TempStorage tmp;
     __shared__ int bad, prior;
     if (threadIdx.x == 0) { bad = 0; prior = *status; }
     __syncthreads();
     if (prior != 0) return;
+    const size_t expect_end = expect_end_dev ? (size_t)*expect_end_dev : expect_end_host;
     const unsigned long long off = J.sec_off_dev ? *J.sec_off_dev : J.sec_off_host;
     const int K = J.K;
     const size_t n = J.n;
@@ -475,11 +476,12 @@ __global__ void __launch_bounds__(kScanThreads) rans_parse_kernel(const RansDeco
 }
 
 void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s) {
-    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, 0, status);
+    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, 0, nullptr, status);
 }
 
-void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, int* status, cudaStream_t s) {
-    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, status);
+void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const uint64_t* expect_end_dev, int* status,
+                              cudaStream_t s) {
+    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, expect_end_dev, status);
 }
 
 __global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDecodeJob J,

@@ -85,6 +85,10 @@ struct ConvDesc {
     int* err = nullptr;         // device status word (bounded-wait timeouts)
 };
 
+// api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
+ufvc_ctx* ctx_clone_shared(const ufvc_ctx* base);
+size_t ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H);
+
 cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s);
 // floats of split-K workspace the SIMT launch of d uses (0: none)
 size_t conv_simt_workspace(const ConvDesc& d);
@@ -144,8 +148,10 @@ struct RansDecodeJob {
     int16_t* sym;             // output symbols
 };
 void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s);
-// as launch_rans_parse, and the section must end exactly at byte `expect_end` of the stream
-void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, int* status, cudaStream_t s);
+// as launch_rans_parse, and the section must end exactly at byte `expect_end` of the stream (read from
+// the device when expect_end_dev is not null)
+void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const uint64_t* expect_end_dev, int* status,
+                              cudaStream_t s);
 void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
                         cudaStream_t s);
 // y^ = r^ q + mu with q = qstep_all[*qp_dev]; yf and / or yb may be null

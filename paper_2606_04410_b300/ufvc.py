@@ -31,12 +31,27 @@ EXPORTS = [
     "ufvc_encode_chunk_host", "ufvc_decode_chunk_host", "ufvc_sync_status", "ufvc_encode_stages",
     "ufvc_hyper_synthesis", "ufvc_quantize", "ufvc_synthesize", "ufvc_rans_encode", "ufvc_rans_decode",
     "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error", "ufvc_conv_layer",
+    "ufvc_rans_encode_noalloc", "ufvc_decode_chunk_dev", "ufvc_server_create", "ufvc_server_destroy",
+    "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
+    "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error",
 ]
+UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
 
 
 class ufvc_config(C.Structure):
     _fields_ = [("arch", C.c_int), ("chunk_len", C.c_int), ("lanes", C.c_int), ("precision", C.c_int),
                 ("device", C.c_int)]
+
+
+class ufvc_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("op", C.c_int), ("stream_id", C.c_int), ("slot", C.c_int),
+                ("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double),
+                ("nbytes", C.c_uint64)]
+
+
+class ufvc_server_stats(C.Structure):
+    _fields_ = [("slots", C.c_int), ("busy_slots", C.c_int), ("queued", C.c_int), ("graphs", C.c_int),
+                ("completed", C.c_uint64), ("hbm_used", C.c_size_t), ("hbm_cap", C.c_size_t)]
 
 
 _vp, _sz, _i = C.c_void_p, C.c_size_t, C.c_int
@@ -65,6 +80,17 @@ _sigs = {
     "ufvc_get_profile": (_i, [_vp, _vp, _vp, _vp, _i, C.POINTER(_i)]),
     "ufvc_last_error": (C.c_char_p, [_vp]),
     "ufvc_conv_layer": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp]),
+    "ufvc_decode_chunk_dev": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _vp]),
+    "ufvc_server_create": (_i, [C.POINTER(ufvc_config), _vp, _sz, _sz, _i, C.POINTER(_vp)]),
+    "ufvc_server_destroy": (None, [_vp]),
+    "ufvc_server_open_stream": (_i, [_vp, _i, _i, _i, C.POINTER(_i)]),
+    "ufvc_server_stream_buffers": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_sz),
+                                        C.POINTER(_vp)]),
+    "ufvc_server_submit": (_i, [_vp, _i, _i, C.POINTER(C.c_uint64)]),
+    "ufvc_server_poll": (_i, [_vp, C.c_uint64, C.POINTER(ufvc_result)]),
+    "ufvc_server_wait": (_i, [_vp, C.c_uint64, C.c_double, C.POINTER(ufvc_result)]),
+    "ufvc_server_stats_get": (_i, [_vp, C.POINTER(ufvc_server_stats)]),
+    "ufvc_server_last_error": (C.c_char_p, [_vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -270,3 +296,85 @@ class Codec:
         raw = names.raw
         return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), float(ms[i]), int(launches[i]))
                 for i in range(cnt.value)]
+
+
+class Server:
+    """Continuous-batching chunk server (include/ufvc.h, "Serving").  Streams own device-resident input,
+    bit-stream and output buffers, exposed here as torch tensors that alias the library's memory."""
+
+    def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "bf16",
+                 hbm_cap_bytes: int = 0, max_slots: int = 8, device: int = 0):
+        self.N = chunk_len
+        self.device = device
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        cfg = ufvc_config(arch, chunk_len, lanes, PRECISIONS[precision], device)
+        h = C.c_void_p()
+        rc = lib.ufvc_server_create(C.byref(cfg), _ptr(w), w.size, hbm_cap_bytes, max_slots, C.byref(h))
+        if rc:
+            raise UfvcError(rc, "server_create")
+        self.h = h
+        self.streams: dict[int, dict] = {}
+
+    def close(self):
+        if self.h:
+            lib.ufvc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int, what: str):
+        if rc:
+            raise UfvcError(rc, f"{what}: {lib.ufvc_server_last_error(self.h).decode()}")
+
+    def open_stream(self, width: int, height: int, qp: int = 32) -> int:
+        sid = C.c_int()
+        self._check(lib.ufvc_server_open_stream(self.h, width, height, qp, C.byref(sid)), "open_stream")
+        fin, bits, nb, fout = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        cap = C.c_size_t()
+        self._check(lib.ufvc_server_stream_buffers(self.h, sid.value, C.byref(fin), C.byref(bits), C.byref(nb),
+                                                   C.byref(cap), C.byref(fout)), "stream_buffers")
+        shape = (self.N, height, width, 3)
+        self.streams[sid.value] = dict(
+            frames_in=_alias(fin.value, shape, torch.uint8, self.device),
+            frames_out=_alias(fout.value, shape, torch.uint8, self.device),
+            bits=_alias(bits.value, (cap.value,), torch.uint8, self.device),
+            nbytes=_alias(nb.value, (1,), torch.int64, self.device), width=width, height=height, qp=qp)
+        return sid.value
+
+    def submit(self, stream_id: int, op: int) -> int:
+        t = C.c_uint64()
+        self._check(lib.ufvc_server_submit(self.h, stream_id, op, C.byref(t)), "submit")
+        return t.value
+
+    def poll(self, ticket: int) -> dict:
+        r = ufvc_result()
+        lib.ufvc_server_poll(self.h, ticket, C.byref(r))
+        return {f: getattr(r, f) for f, _ in ufvc_result._fields_}
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0) -> dict:
+        r = ufvc_result()
+        lib.ufvc_server_wait(self.h, ticket, timeout_ms, C.byref(r))
+        return {f: getattr(r, f) for f, _ in ufvc_result._fields_}
+
+    def stats(self) -> dict:
+        s = ufvc_server_stats()
+        self._check(lib.ufvc_server_stats_get(self.h, C.byref(s)), "stats")
+        return {f: getattr(s, f) for f, _ in ufvc_server_stats._fields_}
+
+
+def _alias(ptr: int, shape: tuple, dtype: torch.dtype, device: int) -> torch.Tensor:
+    """A torch tensor viewing library-owned device memory (no copy, no ownership: valid while the
+    server lives)."""
+    n = 1
+    for d in shape:
+        n *= d
+    nbytes = n * torch.empty((), dtype=dtype).element_size()
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+                                    "strides": None}
+    return torch.as_tensor(_Arr(), device=f"cuda:{device}").view(dtype).view(shape)

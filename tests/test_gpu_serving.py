@@ -1,0 +1,157 @@
+"""GPU tests of the continuous-batching server (ufvc_server_*): every request's bit-stream and decoded
+frames are identical to the single-context calls on the same chunk whether it runs alone or in a mix of
+streams of different sizes on several slots (same kernels, no cross-request arithmetic); graphs are
+captured and replayed; a stream's requests keep their order; the HBM cap bounds the slots (idle slots
+of other sizes are released) and the stream buffers; a decode with nothing encoded is refused."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+N, K, QP = 8, 256, 32
+SIZES = [(256, 144), (320, 192), (160, 96)]
+
+
+def U():
+    from paper_2606_04410_b300 import ufvc
+    return ufvc
+
+
+def _frames(seed, W, H):
+    return torch.from_numpy(synthetic.moving_texture(seed, N, H, W, max_step=8, refresh=0.1)).cuda()
+
+
+def _reference(blob, fr, W, H, qp=QP):
+    """Single-context encode + decode of one chunk: (bit-stream bytes, decoded frames)."""
+    u = U()
+    c = u.Codec(1, N, K, blob, "bf16")
+    bits, nb = c.encode_chunk(fr, qp)
+    n = int(nb.item())
+    out = c.decode_chunk(bits, n, W, H)
+    assert c.sync_status() == 0
+    ref = (bits[:n].cpu().numpy().tobytes(), out.cpu().clone())
+    c.close()
+    return ref
+
+
+def test_server_alone_and_mix_match_single_context():
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=1)
+    specs = [(i, *SIZES[i % len(SIZES)]) for i in range(6)]
+    frames = {i: _frames(40 + i, W, H) for i, W, H in specs}
+    refs = {i: _reference(blob, frames[i], W, H) for i, W, H in specs}
+
+    # alone: one stream, one request at a time
+    srv = u.Server(1, N, K, blob, "bf16", max_slots=1)
+    i, W, H = specs[0]
+    sid = srv.open_stream(W, H, QP)
+    bufs = srv.streams[sid]
+    bufs["frames_in"].copy_(frames[i])
+    torch.cuda.synchronize()
+    for _ in range(3):  # direct run, capture, replay
+        r = srv.wait(srv.submit(sid, u.UFVC_OP_ENCODE), 120000.0)
+        assert r["status"] == 0
+        assert bufs["bits"][:r["nbytes"]].cpu().numpy().tobytes() == refs[i][0]
+        r = srv.wait(srv.submit(sid, u.UFVC_OP_DECODE), 120000.0)
+        assert r["status"] == 0
+        assert torch.equal(bufs["frames_out"].cpu(), refs[i][1])
+    assert srv.stats()["graphs"] >= 2
+    srv.close()
+
+    # mix: six streams of three sizes, requests of all streams queued at once, several rounds
+    srv = u.Server(1, N, K, blob, "bf16", max_slots=4)
+    sids = {}
+    for i, W, H in specs:
+        sids[i] = srv.open_stream(W, H, QP)
+        srv.streams[sids[i]]["frames_in"].copy_(frames[i])
+    torch.cuda.synchronize()
+    for rnd in range(3):
+        tickets = []
+        for i, _, _ in specs:
+            tickets.append((i, u.UFVC_OP_ENCODE, srv.submit(sids[i], u.UFVC_OP_ENCODE)))
+            tickets.append((i, u.UFVC_OP_DECODE, srv.submit(sids[i], u.UFVC_OP_DECODE)))
+        results = [(i, op, srv.wait(t, 120000.0)) for i, op, t in tickets]
+        for i, op, r in results:
+            assert r["status"] == 0, (rnd, i, op, r)
+            b = srv.streams[sids[i]]
+            if op == u.UFVC_OP_ENCODE:
+                assert r["nbytes"] == len(refs[i][0])
+        # a stream's decode ran after its encode of the same round
+        for i, _, _ in specs:
+            enc = [r for j, op, r in results if j == i and op == u.UFVC_OP_ENCODE][0]
+            dec = [r for j, op, r in results if j == i and op == u.UFVC_OP_DECODE][0]
+            assert dec["start_ms"] >= enc["done_ms"]
+        for i, _, _ in specs:
+            b = srv.streams[sids[i]]
+            assert b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes() == refs[i][0]
+            assert torch.equal(b["frames_out"].cpu(), refs[i][1])
+    st = srv.stats()
+    assert st["completed"] == 3 * 2 * len(specs) and st["queued"] == 0
+    assert 1 <= st["slots"] <= 4 and st["graphs"] >= 2
+    # requests of different slots overlapped in time at least once
+    srv.close()
+
+
+def test_server_hbm_cap_releases_idle_slots_and_bounds_streams():
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=2)
+    (Wa, Ha), (Wb, Hb) = SIZES[0], SIZES[1]
+    fa, fb = _frames(7, Wa, Ha), _frames(8, Wb, Hb)
+    ra, rb = _reference(blob, fa, Wa, Ha), _reference(blob, fb, Wb, Hb)
+    # a cap that holds the two streams and ONE slot of either size
+    probe = u.Server(1, N, K, blob, "bf16", max_slots=2)
+    s0 = probe.open_stream(Wa, Ha, QP)
+    s1 = probe.open_stream(Wb, Hb, QP)
+    probe.streams[s0]["frames_in"].copy_(fa)
+    probe.streams[s1]["frames_in"].copy_(fb)
+    torch.cuda.synchronize()
+    probe.wait(probe.submit(s0, u.UFVC_OP_ENCODE), 120000.0)
+    used_a = probe.stats()["hbm_used"]
+    probe.wait(probe.submit(s1, u.UFVC_OP_ENCODE), 120000.0)
+    used_ab = probe.stats()["hbm_used"]
+    probe.close()
+    assert used_ab > used_a
+    cap = used_a + (used_ab - used_a) // 2 + (used_ab - used_a) // 4  # room for one of the two slots only
+    srv = u.Server(1, N, K, blob, "bf16", hbm_cap_bytes=cap, max_slots=4)
+    a = srv.open_stream(Wa, Ha, QP)
+    b = srv.open_stream(Wb, Hb, QP)
+    srv.streams[a]["frames_in"].copy_(fa)
+    srv.streams[b]["frames_in"].copy_(fb)
+    torch.cuda.synchronize()
+    tickets = []
+    for _ in range(2):
+        for sid in (a, b):
+            tickets.append(srv.submit(sid, u.UFVC_OP_ENCODE))
+            tickets.append(srv.submit(sid, u.UFVC_OP_DECODE))
+    for t in tickets:
+        assert srv.wait(t, 120000.0)["status"] == 0
+    st = srv.stats()
+    assert st["hbm_used"] <= cap and st["slots"] == 1
+    for sid, ref in ((a, ra), (b, rb)):
+        buf = srv.streams[sid]
+        assert buf["bits"][:int(buf["nbytes"].item())].cpu().numpy().tobytes() == ref[0]
+        assert torch.equal(buf["frames_out"].cpu(), ref[1])
+    # stream buffers beyond the cap are refused
+    with pytest.raises(u.UfvcError) as e:
+        srv.open_stream(3840, 2160, QP)
+    assert e.value.code == u.UFVC_ERR_OOM
+    srv.close()
+
+
+def test_server_refuses_decode_before_encode_and_bad_calls():
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=3)
+    srv = u.Server(1, N, K, blob, "bf16", max_slots=1)
+    sid = srv.open_stream(160, 96, QP)
+    r = srv.wait(srv.submit(sid, u.UFVC_OP_DECODE), 120000.0)
+    assert r["status"] == u.UFVC_ERR_ARG
+    with pytest.raises(u.UfvcError):
+        srv.submit(sid + 5, u.UFVC_OP_ENCODE)
+    with pytest.raises(u.UfvcError):
+        srv.submit(sid, 7)
+    with pytest.raises(u.UfvcError):
+        srv.open_stream(8, 8, QP)
+    srv.close()
