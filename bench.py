@@ -4,13 +4,17 @@ scale index, both rANS sections, bit-stream layout; header/lane parse, z^ decode
 scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 frames).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
-                    [--width W --height H]
+                    [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
+                    [--no-serving] [--serving-window S]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
-it under the same methodology and reported with the PSNR and bitrate deltas.  Under torchrun every rank
-codes its own chunks (weak scaling, no data-path collective); the timed region is bracketed by a
-barrier and a synchronize, max over ranks.  --impl reference times the FP64 CPU oracle on a bounded
-sample of the same workload.
+it under the same methodology and reported with the PSNR and bitrate deltas.  Extra keys: the decoder
+conv stages against their own bounds (tensor or HBM), the entropy-coding stress at 4K (8.29 M symbols,
+lane counts 1024..65536), and the serving mix (64 streams of four sizes, Poisson arrivals, through the
+continuous-batching server) for BF16 and FP32.  Under torchrun every rank codes its own chunks and
+serves its share of the streams (weak scaling, no data-path collective); the timed region is bracketed
+by a barrier and a synchronize, max over ranks.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -200,14 +204,17 @@ SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((
 
 
 def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n_streams: int = 64,
-                  seed: int = 0, drain_s: float = 90.0) -> dict:
+                  seed: int = 0, drain_s: float = 90.0, dist=None, rank: int = 0, world: int = 1) -> dict:
     """Serving mix: n_streams streams of the SERVING_MIX resolutions (assigned by seed), each with Poisson
     chunk arrivals at 30 fps (one 8-frame chunk per Exp(mean 8/30 s)), requests alternating encode and
     decode (a decode codes the stream's latest device-resident bit-stream), submitted in real time for
     window_s seconds to the continuous-batching server (HBM cap 150 GB).  Latency = submit -> completion
     on the server's clock; frames/s = frames of the completed requests / (last completion - first submit).
-    Content: the 1080p synthetic chunk, cropped for the smaller sizes and tiled 2 x 2 for 4K."""
+    Content: the 1080p synthetic chunk, cropped for the smaller sizes and tiled 2 x 2 for 4K.  Under
+    torchrun every rank serves the streams s with s mod world == rank (same global trace); frames and
+    the span are aggregated over ranks (sum, slowest), latencies gathered."""
     import torch
+    from paper_2606_04410_b300 import shard
     rng = np.random.default_rng(seed)
     sizes = [sz for sz, _ in SERVING_MIX]
     which = rng.choice(len(sizes), size=n_streams, p=[p for _, p in SERVING_MIX])
@@ -219,30 +226,34 @@ def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n
         else:
             content[(W_, H_)] = src.repeat(1, 2, 2, 1)[:, :H_, :W_].contiguous()
     srv = U.Server(1, N, K, blob, precision, hbm_cap_bytes=150 << 30, max_slots=8, device=dev.index or 0)
-    sids = []
-    for j in range(n_streams):
+    owned = shard.shard(list(range(n_streams)), rank, world)
+    sids = {}
+    for j in owned:
         W_, H_ = sizes[which[j]]
         sid = srv.open_stream(W_, H_, QP)
         srv.streams[sid]["frames_in"].copy_(content[(W_, H_)])
-        sids.append(sid)
+        sids[j] = sid
     torch.cuda.synchronize()
     # warm-up: every stream once (slots, plans, workspaces, graph capture), then drain
     warm = []
     for _ in range(2):
-        for sid in sids:
+        for sid in sids.values():
             warm.append(srv.submit(sid, U.UFVC_OP_ENCODE))
             warm.append(srv.submit(sid, U.UFVC_OP_DECODE))
     for t in warm:
         assert srv.wait(t, 600000.0)["status"] == 0
     # arrival trace
     events = []
-    for j, sid in enumerate(sids):
+    for j in range(n_streams):  # the global trace (same on every rank), then this rank's share
         t, op = rng.exponential(8 / 30), U.UFVC_OP_ENCODE
         while t < window_s:
-            events.append((t, sid, op))
+            if j in sids:
+                events.append((t, sids[j], op))
             op = U.UFVC_OP_DECODE if op == U.UFVC_OP_ENCODE else U.UFVC_OP_ENCODE
             t += rng.exponential(8 / 30)
     events.sort()
+    if dist is not None and world > 1:
+        dist.barrier()
     tickets = []
     t0 = time.perf_counter()
     for t, sid, op in events:
@@ -254,14 +265,22 @@ def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n
     done = [(sid, op, r) for sid, op, r in res if r["status"] == 0]
     pending = sum(1 for _, _, r in res if r["status"] == U.UFVC_PENDING)
     st = srv.stats()
-    lat = np.array([r["done_ms"] - r["submit_ms"] for _, _, r in done]) if done else np.zeros(1)
-    lat_e = np.array([r["done_ms"] - r["submit_ms"] for _, op, r in done if op == U.UFVC_OP_ENCODE] or [0.0])
-    lat_d = np.array([r["done_ms"] - r["submit_ms"] for _, op, r in done if op == U.UFVC_OP_DECODE] or [0.0])
+    lats = [(op, r["done_ms"] - r["submit_ms"]) for _, op, r in done]
     span_ms = (max(r["done_ms"] for _, _, r in done) - min(r["submit_ms"] for _, _, r in res)) if done else 1.0
+    n_req, n_pend = len(events), pending
+    if dist is not None and world > 1:
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (lats, n_req, n_pend))
+        lats = [x for g in gathered for x in g[0]]
+        n_req, n_pend = sum(g[1] for g in gathered), sum(g[2] for g in gathered)
+    n_done, span_ms = shard.aggregate(len(done), span_ms, dist if world > 1 else None, dev)
+    lat = np.array([v for _, v in lats] or [0.0])
+    lat_e = np.array([v for op, v in lats if op == U.UFVC_OP_ENCODE] or [0.0])
+    lat_d = np.array([v for op, v in lats if op == U.UFVC_OP_DECODE] or [0.0])
     out = {"streams": n_streams, "mix": {f"{w}x{h}": int((which == i).sum()) for i, (w, h) in enumerate(sizes)},
-           "window_s": window_s, "requests": len(events), "completed": len(done), "pending_after_drain": pending,
-           "frames_per_s": N * len(done) / (span_ms / 1000.0),
-           "offered_frames_per_s": N * len(events) / window_s,
+           "window_s": window_s, "requests": n_req, "completed": int(n_done), "pending_after_drain": n_pend,
+           "frames_per_s": N * n_done / (span_ms / 1000.0),
+           "offered_frames_per_s": N * n_req / window_s, "ranks": world,
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "enc_p50": float(np.percentile(lat_e, 50)), "enc_p99": float(np.percentile(lat_e, 99)),
                           "dec_p50": float(np.percentile(lat_d, 50)), "dec_p99": float(np.percentile(lat_d, 99))},
@@ -339,6 +358,7 @@ def main() -> None:
     import torch.distributed as dist
 
     import synthetic
+    from paper_2606_04410_b300 import shard
     from paper_2606_04410_b300 import ufvc as U
 
     rank, world, local = env_rank()
@@ -360,12 +380,8 @@ def main() -> None:
     r = time_codec(codec, fr, frames_np, W_, H_, args.steps, args.warmup, True, flush, dist, world)
     clocks = sampler.stop()
     t_step = [a + b for a, b in zip(r["t_enc"], r["t_dec"])]
-    total_ms = sum(t_step)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = N * args.steps * world / (total_ms / 1000.0)
+    frames_all, total_ms = shard.aggregate(N * args.steps, sum(t_step), dist if world > 1 else None, dev)
+    value = frames_all / (total_ms / 1000.0)
 
     # ---- dominant kernel roofline (per-stage events recorded inside the same timed steps)
     prof_acc = r["prof"]
@@ -445,6 +461,16 @@ def main() -> None:
            "h2d_bytes_per_step": int(h_frames.numel() + nbh.value),
            "d2h_bytes_per_step": int(nbh.value + h_out.numel() + 8)}
 
+    # serving mix (every rank serves its share of the streams)
+    serving = None
+    if not args.no_serving and (W_, H_) == (W, H):
+        dd = dist if world > 1 else None
+        serving = {args.precision: serving_bench(U, dev, frames_np, blob, args.precision, args.serving_window,
+                                                 dist=dd, rank=rank, world=world)}
+        if args.precision != "fp32" and not args.no_fp32_path:
+            serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", args.serving_window / 2, dist=dd,
+                                            rank=rank, world=world)
+
     if rank == 0:
         workload = WORKLOAD if (W_, H_) == (W, H) else \
             WORKLOAD.replace("1080p 8-frame chunk (1920x1080 padded to 1920x1088)", f"{W_}x{H_} 8-frame chunk")
@@ -470,10 +496,7 @@ def main() -> None:
             line["dbitrate_vs_fp32"] = (r["nbytes"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
         if not args.no_entropy_sweep:
             line["entropy_sweep"] = entropy_sweep(U, dev)
-        if not args.no_serving and (W_, H_) == (W, H):
-            serving = {args.precision: serving_bench(U, dev, frames_np, blob, args.precision, args.serving_window)}
-            if args.precision != "fp32" and not args.no_fp32_path:
-                serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", args.serving_window / 2)
+        if serving is not None:
             line["serving"] = serving
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
