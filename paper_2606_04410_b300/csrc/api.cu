@@ -32,6 +32,10 @@ struct LayerW {
     // output pixel; btc holds the biases in the same order
     int ps_major = 0;
     float* btc = nullptr;
+    // final layer (3x3, 64 -> 12, pixel shuffle, frame mapping) in scatter form: bf16 [groups][128][64],
+    // row 32 (c / 3) + 9 ky + 3 kx + c % 3 = the 64 input-channel weights of output channel c at tap
+    // (ky, kx); the other rows zero
+    __nv_bfloat16* wsc = nullptr;
 };
 
 // Split-K workspace of the SIMT convolution, grown on first use.  One per direction of a plan (an
@@ -357,7 +361,7 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
 }
 
 static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
-                                bool tc, bool pixel_shuffle = false) {
+                                bool tc, bool pixel_shuffle = false, bool final_layer = false) {
     int co, k, ci;
     layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
     L.cout = co; L.k = k; L.cin = ci; L.cin_p = ceil_div(ci, 16) * 16; L.groups = groups;
@@ -404,6 +408,19 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
             if ((st = dalloc(ctx, nullptr, &L.btc, bt.size())) != UFVC_OK) return st;
             CK(cudaMemcpy(L.btc, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice));
         }
+        if (final_layer && co == 12 && k == 3 && ci == 64) {
+            std::vector<__nv_bfloat16> ws((size_t)groups * 128 * 64, __float2bfloat16(0.f));
+            for (int g = 0; g < groups; ++g) {
+                const float* src = blob + offs[first + g * D_NDEC];
+                for (int c = 0; c < 12; ++c)
+                    for (int t = 0; t < 9; ++t)
+                        for (int i = 0; i < 64; ++i)
+                            ws[((size_t)g * 128 + 32 * (c / 3) + 3 * t + c % 3) * 64 + i] =
+                                __float2bfloat16(src[((size_t)c * 9 + t) * 64 + i]);
+            }
+            if ((st = dalloc(ctx, nullptr, &L.wsc, ws.size())) != UFVC_OK) return st;
+            CK(cudaMemcpy(L.wsc, ws.data(), ws.size() * 2, cudaMemcpyHostToDevice));
+        }
     }
     return UFVC_OK;
 }
@@ -414,8 +431,8 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     if (!ctx->borrowed) cudaDeviceSynchronize();  // a clone's owner has synchronised its stream
     for (auto& kv : ctx->plans) free_plan(kv.second);
     if (!ctx->borrowed) {
-        for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
-        for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
+        for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc); }
+        for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc); }
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
     }
@@ -474,7 +491,7 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         if ((st = upload_layer(ctx, ctx->enc[l], weights, offs.data(), l, 1, l <= L_H2)) != UFVC_OK) return bail(st);
     for (int j = 0; j < D_NDEC; ++j)
         if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true,
-                                   j == D_D0 || j == D_U1 || j == D_U2)) != UFVC_OK)
+                                   j == D_D0 || j == D_U1 || j == D_U2, j == D_U3)) != UFVC_OK)
             return bail(st);
     *out = ctx;
     return UFVC_OK;
@@ -522,7 +539,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
     d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
     if (use_tc(ctx, L)) {
         d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
-        d.btc = L.btc; d.ps_major = L.ps_major;
+        d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc;
         const cudaError_t e = launch_conv_tc(d, s);
         if (e != cudaSuccess) {
             ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
@@ -928,6 +945,7 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
         L.b += g * L.b_gs;
         if (L.wtc) L.wtc += (size_t)g * L.cout_pad * L.k * L.k * L.cin_tc;
         if (L.btc) L.btc += g * L.b_gs;
+        if (L.wsc) L.wsc += (size_t)g * 128 * 64;
     }
     L.groups = 1;
     const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;

@@ -431,9 +431,8 @@ constexpr int kHaloBoxBytes = 130 * 128;
 // Epilogue of the resident-weight kernel.  A tile's BN columns are drained by BN/16 column quarters of
 // 16 columns each (four warps per quarter, one per TMEM lane quarter); with BN = 16 the four quarters
 // form four independent groups that drain four different tiles at once (four TMEM accumulators).
-// OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC through the swizzled staging tile and a
-// TMA store; 2 = final u8 frame (clamp(0.5 + o, 0, 1) x 255, pixel shuffle) through a staging block of
-// the tile's two output rows (3 x 256 bytes each) and TMA stores of 256-byte boxes.
+// OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC (BN = 64) through the swizzled staging
+// tile and a TMA store.  (The final frame layer has its own kernel, conv_tc_final_kernel.)
 template <int BN, int STAGES, int OUTK>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -444,8 +443,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int EG = 4 / CPT;              // tiles drained concurrently (epilogue groups)
     constexpr int NACC = EG > 2 ? EG : 2;    // TMEM accumulators
     constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : 128;
-    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : OUTK == 2 ? EG * 1536 : 0;
+    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : 0;
     static_assert(BN == 16 || BN == 64, "resident-weight kernel: N tile of 16 or 64");
+    static_assert(OUTK == 0 || (OUTK == 1 && BN == 64), "staged stores: bf16 NHWC with N = 64");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sB = smem;
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
                 }
-                if constexpr (OUTK == 1) {
+                {
                     const uint32_t base = ptx::smem_u32(sC) + row * 128;
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
@@ -611,18 +611,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
                                           pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
                                           pack_bf16(v[8 * i + 6], v[8 * i + 7]));
-                    }
-                } else {
-                    // column co (< 12) = channel co / 4 of sub-pixel (dy, dx) = ((co >> 1) & 1, co & 1); the
-                    // block holds output rows 2 oh + dy, bytes 768 strip + [0, 768) as three 2 x 256 boxes
-                    uint8_t* blk = sC + grp * 1536;
-                    if (valid) {
-#pragma unroll
-                        for (int co = 0; co < 12; ++co) {
-                            const float f = fminf(fmaxf(0.5f + v[co], 0.0f), 1.0f);
-                            const int dy = (co >> 1) & 1, xb = (2 * row + (co & 1)) * 3 + (co >> 2);
-                            blk[(xb >> 8) * 512 + dy * 256 + (xb & 255)] = (uint8_t)rintf(f * 255.0f);
-                        }
                     }
                 }
                 ptx::fence_proxy_async();
@@ -633,16 +621,290 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
                 }
                 if (elected) {
-                    if constexpr (OUTK == 1) {
-                        ptx::tma_store_4d(&tmC, sC, nt * BN, strip * 128, oh, g);
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < 3; ++b)
-                            ptx::tma_store_3d(&tmC, sC + grp * 1536 + b * 512, strip * 768 + b * 256, 2 * oh, g);
-                    }
+                    ptx::tma_store_4d(&tmC, sC, nt * BN, strip * 128, oh, g);
                     ptx::bulk_commit();
                 }
             }
+        }
+        if (elected) ptx::bulk_wait0();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Final decoder layer (3x3, 64 -> 12 channels, pixel shuffle, x^ = clamp(0.5 + o, 0, 1)) in scatter
+// form.  With only 12 outputs, the gather form would stream every input pixel nine times through the
+// tensor cores (one K=64 slice per tap) for an N of 16.  Instead each input pixel is multiplied ONCE by
+// the 64 x 108 matrix of all (tap, channel) weights:
+//     P[r][x][(ky, kx, c)] = sum_ci in[r][x][ci] w[c][ky][kx][ci]          (M = pixels, N = 108, K = 64)
+//     o[y][x][c] = b[c] + sum_{ky, kx} P[y + ky - 1][x + kx - 1][(ky, kx, c)]  (zero outside the image)
+// Tiles are input rows of a 120-pixel strip, taken in row order, so each input row is loaded once per
+// strip.  Warp q of the 128 accumulator rows holds input pixels x0 + 30 q - 1 .. x0 + 30 q + 30 (one TMA
+// box of 32 pixels each; the one-pixel halos overlap) and produces the outputs of its lanes 1..30, so
+// the kx neighbours are warp shuffles.  Four TMEM buffers (128 columns each) hold the P rows of the
+// three input rows an output row needs while the next one is computed.  Accumulator column of
+// (ky, kx, c): 32 (c / 3) + 9 ky + 3 kx + c % 3, so epilogue column group k (warps 2+4k..5+4k) owns
+// output channels 3k..3k+2 and reads one aligned 32-column block per P row.
+// OUTK: 0 = every thread stores its outputs; 1 = uint8 frame rows through a staging block and TMA
+// stores (three 240-byte boxes per output row pair of a strip); 2 = the same for float frames.
+// ------------------------------------------------------------------------------------------------
+constexpr int kFinStrip = 120;  // output pixels per strip
+
+template <int OUTK>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_final_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                         const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
+    constexpr int STAGES = 8, A_BYTES = 128 * 128, B_BYTES = 128 * 128, NACC = 4;
+    constexpr uint32_t TMEM_COLS = 512;
+    constexpr int C_BYTES = OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0;
+    // staging box stride in elements: every box starts 128-byte aligned (a TMA requirement on the
+    // shared-memory address): 512 B for uint8, 480 floats = 1920 B for float
+    constexpr int BOXE = OUTK == 1 ? 512 : 480;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sB = smem;
+    uint8_t* sA = sB + B_BYTES;
+    uint8_t* sC = sA + STAGES * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sC + C_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + NACC;
+    uint64_t* bfull = tempty + NACC;
+    uint64_t* bfree = bfull + 1;
+    uint64_t* drain = bfree + 1;
+    uint64_t* cwritten = drain + 1;
+    uint64_t* cfree = cwritten + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
+    const float* bias_all = stage_bias(p, sbias);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < NACC; ++a) {
+            ptx::mbar_init(&tfull[a], 1);
+            ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
+        }
+        ptx::mbar_init(bfull, 1);
+        ptx::mbar_init(bfree, 1);
+        ptx::mbar_init(drain, 1);
+        ptx::mbar_init(cwritten, 32 * kEpiWarps);
+        ptx::mbar_init(cfree, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+        if (OUTK) ptx::prefetch_tmap(&tmC);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    // work item t = (g * tiles_w + strip) * Ho + y (one output row of one strip); this CTA owns
+    // [t_begin, t_end), cut into runs of one (g, strip)
+    const int t_begin = (int)((long long)p.total_tiles * blockIdx.x / gridDim.x);
+    const int t_end = (int)((long long)p.total_tiles * (blockIdx.x + 1) / gridDim.x);
+    const int Ho = p.Ho;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer: one input row per P row
+        if (lane == 0) {
+            int it = 0, cur_g = -1, nb = 0;
+            uint32_t bfree_par = 0, last_par[STAGES];
+            bool used[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
+            bool ok = true;
+            for (int t = t_begin; t < t_end && ok;) {
+                const int ya = t % Ho, r = t / Ho, strip = r % p.tiles_w, g = r / p.tiles_w;
+                const int te = min(t_end, (r + 1) * Ho), yb = ya + (te - t) - 1;
+                if (g != cur_g) {
+                    if (cur_g >= 0) {  // the MMAs that read the previous weights must be complete
+                        if (!wait_bar(bfree, bfree_par, abort_flag, p.err)) break;
+                        bfree_par ^= 1;
+                    }
+                    ptx::mbar_arrive_expect_tx(bfull, B_BYTES);
+                    ptx::tma_load_3d(sB, &tmB, bfull, 0, 0, g);
+                    cur_g = g;
+                    ++nb;
+                }
+                const int r0 = max(ya - 1, 0), r1 = min(yb + 1, Ho - 1), ag = p.a_grouped ? g : 0;
+                for (int row = r0; row <= r1; ++row, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) { ok = false; break; }
+                    ptx::mbar_arrive_expect_tx(&full[s], A_BYTES);
+                    for (int q = 0; q < 4; ++q)
+                        ptx::tma_load_4d(sA + s * A_BYTES + q * 4096, &tmA, &full[s], 0,
+                                         strip * kFinStrip + 30 * q - 1, row, ag);
+                    used[s] = true;
+                    last_par[s] = ph;
+                }
+                t = te;
+            }
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s)
+                if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+            if (nb) wait_bar(bfull, (nb - 1) & 1, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer: P row = 4 MMAs (K = 64)
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_bf16(128);
+            int it = 0, pr = 0, cur_g = -1;
+            uint32_t bfull_par = 0;
+            bool ok = true;
+            for (int t = t_begin; t < t_end && ok;) {
+                const int ya = t % Ho, r = t / Ho, g = r / p.tiles_w;
+                const int te = min(t_end, (r + 1) * Ho), yb = ya + (te - t) - 1;
+                if (g != cur_g) {
+                    if (cur_g >= 0) ptx::mma_commit(bfree);
+                    if (!wait_bar(bfull, bfull_par, abort_flag, p.err)) break;
+                    bfull_par ^= 1;
+                    ptx::tc_fence_after();
+                    cur_g = g;
+                }
+                const int r0 = max(ya - 1, 0), r1 = min(yb + 1, Ho - 1);
+                for (int row = r0; row <= r1; ++row, ++it, ++pr) {
+                    const int acc = pr % NACC, use = pr / NACC;
+                    if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) { ok = false; break; }
+                    const int s = it % STAGES;
+                    if (!wait_bar(&full[s], (it / STAGES) & 1, abort_flag, p.err)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        ptx::mma_f16(tmem_base + acc * 128, ptx::sdesc_sw128(a0 + kk * 32),
+                                     ptx::sdesc_sw128(b0 + kk * 32), idesc, kk != 0);
+                    ptx::mma_commit(&empty[s]);
+                    ptx::mma_commit(&tfull[acc]);
+                }
+                t = te;
+            }
+            ptx::mma_commit(drain);
+            wait_bar(drain, 0, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue: one output row at a time
+        const int q = warp & 3, k = (warp - 2) >> 2;
+        const bool elected = OUTK != 0 && warp == 2 && lane == 0;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + 32 * k;
+        int pr = 0, waited = 0, o = 0;
+        bool ok = true;
+        for (int t = t_begin; t < t_end && ok;) {
+            const int ya = t % Ho, r = t / Ho, strip = r % p.tiles_w, g = r / p.tiles_w;
+            const int te = min(t_end, (r + 1) * Ho), yb = ya + (te - t) - 1;
+            const int r0 = max(ya - 1, 0), r1 = min(yb + 1, Ho - 1);
+            const float* bias = bias_all + (size_t)g * p.b_gs + 3 * k;
+            const float b0 = bias[0], b1 = bias[1], b2 = bias[2];
+            const int xo = strip * kFinStrip + 30 * q + lane - 1;
+            const bool xvalid = lane >= 1 && lane <= 30 && xo < p.Wo;
+            for (int y = ya; y <= yb; ++y) {
+                const int hi = min(y + 1, Ho - 1);
+                while (waited <= pr + (hi - r0)) {  // P rows up to y + 1 are in TMEM
+                    if (!__all_sync(0xffffffffu, wait_bar(&tfull[waited % NACC], (waited / NACC) & 1, abort_flag,
+                                                          p.err))) { ok = false; break; }
+                    ++waited;
+                }
+                if (!ok) break;
+                ptx::tc_fence_after();
+                float S[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) S[i] = 0.f;
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky) {
+                    const int row = y + ky - 1;
+                    if (row < 0 || row >= Ho) continue;
+                    float v[32];
+                    tmem_ld32(lane_base + ((pr + row - r0) % NACC) * 128, v);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) S[i] += v[9 * ky + i];
+                }
+                // P row y - 1 is not needed by later outputs of this run
+                if (y - 1 >= r0) {
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&tempty[(pr + y - 1 - r0) % NACC]);
+                }
+                float outv[3];
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float left = __shfl_up_sync(0xffffffffu, S[cc], 1);        // kx = 0 of pixel x - 1
+                    const float right = __shfl_down_sync(0xffffffffu, S[6 + cc], 1);  // kx = 2 of pixel x + 1
+                    const float bb = cc == 0 ? b0 : cc == 1 ? b1 : b2;
+                    outv[cc] = fminf(fmaxf(0.5f + (bb + left + S[3 + cc] + right), 0.0f), 1.0f);
+                }
+                if constexpr (OUTK == 0) {
+                    if (xvalid) {
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            const int c = 3 * k + cc, ch = c >> 2, oy = 2 * y + ((c >> 1) & 1), ox = 2 * xo + (c & 1);
+                            if (oy >= p.out_h || ox >= p.out_w) continue;
+                            const size_t off = (size_t)g * p.out_gs + ((size_t)oy * p.out_w + ox) * 3 + ch;
+                            if (p.mode == OUT_PS_FINAL_F32) reinterpret_cast<float*>(p.out)[off] = outv[cc];
+                            else reinterpret_cast<uint8_t*>(p.out)[off] = (uint8_t)rintf(outv[cc] * 255.0f);
+                        }
+                    }
+                } else {
+                    if (o > 0) {  // the previous row's TMA stores must have read the staging block
+                        if (elected) {
+                            ptx::bulk_wait_read0();
+                            ptx::mbar_arrive(cfree);
+                        }
+                        if (!__all_sync(0xffffffffu, wait_bar(cfree, (o - 1) & 1, abort_flag, p.err))) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (xvalid) {
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            // element xb of the strip's 720-element output row pair: box xb / 240
+                            const int c = 3 * k + cc, dy = (c >> 1) & 1;
+                            const int xb = (2 * (30 * q + lane - 1) + (c & 1)) * 3 + (c >> 2);
+                            const int e = (xb / 240) * BOXE + dy * 240 + xb % 240;
+                            if constexpr (OUTK == 1) sC[e] = (uint8_t)rintf(outv[cc] * 255.0f);
+                            else reinterpret_cast<float*>(sC)[e] = outv[cc];
+                        }
+                    }
+                    ptx::fence_proxy_async();
+                    ptx::mbar_arrive(cwritten);
+                    if (warp == 2) {
+                        bool w_ok = true;
+                        if (lane == 0) w_ok = wait_bar(cwritten, o & 1, abort_flag, p.err);
+                        if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) { ok = false; break; }
+                    }
+                    if (elected) {
+#pragma unroll
+                        for (int b = 0; b < 3; ++b)
+                            ptx::tma_store_3d(&tmC, sC + b * BOXE * (OUTK == 1 ? 1 : 4),
+                                              strip * 2 * kFinStrip * 3 + b * 240, 2 * y, g);
+                        ptx::bulk_commit();
+                    }
+                    ++o;
+                }
+            }
+            if (!ok) break;
+            // rows yb .. r1 of this run are released now
+            for (int row = max(yb, r0); row <= r1; ++row) {
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&tempty[(pr + row - r0) % NACC]);
+            }
+            pr += r1 - r0 + 1;
+            t = te;
         }
         if (elected) ptx::bulk_wait0();
     }
@@ -723,7 +985,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
 template <int BN, int STAGES, int OUTK>
 static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                                cudaStream_t s) {
-    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : OUTK == 2 ? (64 / BN) * 1536 : 0;
+    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : 0;
     constexpr int kSmem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + C_BYTES + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
@@ -745,7 +1007,84 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
     return cudaGetLastError();
 }
 
+template <int OUTK>
+static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
+                                cudaStream_t s) {
+    constexpr int kSmem = 128 * 128 + 8 * 128 * 128 + (OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0) + kSmemExtra;
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+    static int configured_smem = 0;
+    if (configured_smem != kSmem) {
+        cudaError_t e =
+            cudaFuncSetAttribute(conv_tc_final_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess) return e;
+        configured_smem = kSmem;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int grid = args.total_tiles < sms ? args.total_tiles : sms;
+    conv_tc_final_kernel<OUTK><<<grid, kThreads, kSmem, s>>>(a, b, c, args);
+    return cudaGetLastError();
+}
+
+// The final decoder layer in scatter form (d.wsc: bf16 [groups][128][64], row 32 (c / 3) + 9 ky + 3 kx
+// + c % 3 = tap (ky, kx) of output channel c, other rows zero).
+static cudaError_t launch_conv_final(const ConvDesc& d, cudaStream_t s) {
+    const int Ho = d.H, Wo = d.W;
+    TcArgs a{};
+    a.Ho = Ho; a.Wo = Wo;
+    a.TW = kFinStrip; a.TH = 1;
+    a.tiles_w = (Wo + kFinStrip - 1) / kFinStrip;
+    a.tiles_h = Ho;
+    a.n_tiles = 1;
+    a.groups = d.groups;
+    a.total_tiles = a.tiles_w * Ho * d.groups;
+    a.k = 3; a.pad = 1; a.stride = 1; a.a_grouped = d.in_gs != 0;
+    a.bias = d.b; a.b_gs = (int)d.b_gs; a.Cout = d.Cout;
+    a.mode = d.mode; a.act = 0;
+    a.out = d.out; a.out_gs = d.out_gs; a.out_h = d.out_h; a.out_w = d.out_w; a.out_c = 3;
+    a.err = d.err;
+    const cuuint64_t esz = 2;
+    CUtensorMap ma, mb, mc;
+    {
+        const int G = a.a_grouped ? d.groups : 1;
+        cuuint64_t dims[4] = {64, (cuuint64_t)Wo, (cuuint64_t)Ho, (cuuint64_t)G};
+        cuuint64_t str[3] = {64 * esz, (cuuint64_t)Wo * 64 * esz,
+                             a.a_grouped ? (cuuint64_t)d.in_gs * esz : (cuuint64_t)Ho * Wo * 64 * esz};
+        cuuint32_t box[4] = {64, 32, 1, 1};
+        if (!encode_map(&ma, d.in, 4, dims, str, box)) return cudaErrorInvalidValue;
+    }
+    {
+        cuuint64_t dims[3] = {64, 128, (cuuint64_t)d.groups};
+        cuuint64_t str[2] = {64 * esz, 128 * 64 * esz};
+        cuuint32_t box[3] = {64, 128, 1};
+        if (!encode_map(&mb, d.wsc, 3, dims, str, box)) return cudaErrorInvalidValue;
+    }
+    const bool f32 = d.mode == OUT_PS_FINAL_F32;
+    const size_t es = f32 ? 4 : 1;
+    const bool contiguous = d.groups == 1 || d.out_gs == (long long)d.out_h * d.out_w * 3;
+    const bool staged = contiguous && (d.out_w * 3 * es) % 16 == 0;
+    mc = mb;
+    if (staged) {
+        cuuint64_t dims[3] = {(cuuint64_t)d.out_w * 3, (cuuint64_t)d.out_h, (cuuint64_t)d.groups};
+        cuuint64_t str[2] = {(cuuint64_t)d.out_w * 3 * es, (cuuint64_t)d.out_h * d.out_w * 3 * es};
+        cuuint32_t box[3] = {240, 2, 1};
+        if (!encode_map(&mc, d.out, 3, dims, str, box,
+                        f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                        CU_TENSOR_MAP_SWIZZLE_NONE))
+            return cudaErrorInvalidValue;
+        return f32 ? launch_final<2>(ma, mb, mc, a, s) : launch_final<1>(ma, mb, mc, a, s);
+    }
+    return launch_final<0>(ma, mb, mc, a, s);
+}
+
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
+    if (d.wsc && (d.mode == OUT_PS_FINAL_U8 || d.mode == OUT_PS_FINAL_F32) && d.k == 3 && d.stride == 1 &&
+        d.Cin == 64 && d.Cout == 12)
+        return launch_conv_final(d, s);
     if (d.Cin % 64 != 0 || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
         return cudaErrorInvalidValue;
     const int pad = d.k / 2;
@@ -822,8 +1161,6 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         // staged stores: bf16 NHWC (64 channels per strip pixel), or the final u8 frame whose rows are a
         // multiple of 16 bytes (three 256-byte boxes per output row pair of a strip)
         const bool st_nhwc = BN == 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 && d.out_gs % 8 == 0;
-        const bool st_u8 = BN == 16 && d.mode == OUT_PS_FINAL_U8 && d.Cout == 12 && (d.out_w * 3) % 16 == 0 &&
-                           d.out_w <= 2 * Wo && (d.groups == 1 || d.out_gs == (long long)d.out_h * d.out_w * 3);
         if (st_nhwc) {
             const int Hd = d.out_h < Ho ? d.out_h : Ho, Wd = d.out_w < Wo ? d.out_w : Wo;
             cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
@@ -832,15 +1169,6 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             cuuint32_t box[4] = {64, 128, 1, 1};
             if (!encode_map(&mc, d.out, 4, dims, str, box)) return cudaErrorInvalidValue;
             return launch_halo<64, 2, 1>(ma, mb, mc, a, s);
-        }
-        if (st_u8) {
-            // [G][out_h][out_w * 3] bytes
-            cuuint64_t dims[3] = {(cuuint64_t)d.out_w * 3, (cuuint64_t)d.out_h, (cuuint64_t)d.groups};
-            cuuint64_t str[2] = {(cuuint64_t)d.out_w * 3, (cuuint64_t)d.out_h * d.out_w * 3};
-            cuuint32_t box[3] = {256, 2, 1};
-            if (!encode_map(&mc, d.out, 3, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE))
-                return cudaErrorInvalidValue;
-            return launch_halo<16, 3, 2>(ma, mb, mc, a, s);
         }
         return BN == 16 ? launch_halo<16, 3, 0>(ma, mb, mc, a, s) : launch_halo<64, 2, 0>(ma, mb, mc, a, s);
     }

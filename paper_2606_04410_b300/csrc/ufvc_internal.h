@@ -80,6 +80,7 @@ struct ConvDesc {
     int out_c_stride = 0;       // NHWC output channel count if different from Cout
     const float* btc = nullptr; // tensor-core bias in accumulator-column order (nullptr: same as b)
     int ps_major = 0;           // tensor-core weights in sub-pixel-major column order (pixel shuffle layers)
+    const void* wsc = nullptr;  // final layer, scatter form: bf16 [groups][128][64] (row = tap x channel)
     float* ws = nullptr;        // SIMT split-K workspace (conv_simt_workspace(d) floats), or nullptr
     size_t ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
