@@ -200,6 +200,11 @@ def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, r
     return out
 
 
+# DRAM bytes per 1080p launch from one ncu capture of the SAME kernel build (dram__bytes_read.sum +
+# dram__bytes_write.sum on the 960x544 chunk, scaled by the 4x pixel count): profiles/<kernel>_<layer>_960x544.md.
+# An entry must be removed when its kernel changes.
+NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.910656e6 + 73.642752e6), "dec.U3": 4 * (138.86592e6 + 6.572032e6)}
+
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
 
 
@@ -419,7 +424,8 @@ def main() -> None:
     roofline = {"bound": tr["bound"], "kernel": (kern.get(top, "conv_tc_kernel") if args.precision != "fp32"
                                                  else "conv_simt") + f" ({top})",
                 "achieved": tr["achieved"], "peak": tr["peak"], "unit": tr["unit"], "frac": tr["frac"],
-                "traffic": None, "peak_source": peak_src if tr["bound"] != "hbm" else f"{pk['source']} HBM copy",
+                "traffic": NCU_TRAFFIC_1080P.get(top) if (W_, H_) == (W, H) and args.precision == "bf16" else None,
+                "traffic_unit": "bytes per launch", "peak_source": peak_src if tr["bound"] != "hbm" else f"{pk['source']} HBM copy",
                 "decoder_conv_stages": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
                                             for kk, vv in v.items()} for k, v in stages.items()},
                 "decoder_convs": {"tflops": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12,

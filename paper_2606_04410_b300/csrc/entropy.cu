@@ -48,37 +48,39 @@ __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// bf16 variant for the tensor-core path (Cp = 64, N <= 16): one thread per pixel gathers its N RGB
-// triplets and writes the 64-channel row with 16-byte stores
-__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp,
+// bf16 variant for the tensor-core path (rows of Cp = 64 channels, 3N <= 48 of them real): one thread per
+// (pixel, 8-channel group) writes one 16-byte group, so consecutive threads write consecutive bytes of a
+// pixel row.  Only the ceil(3N / 8) groups that hold frame channels are written; the rest of each row
+// is zero from the buffer's creation and stays zero (the weights of those channels are zero too).
+__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int G,
                                  __nv_bfloat16* __restrict__ x) {
-    const size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= (size_t)Hp * Wp) return;
-    const int h = (int)(pix / Wp), w = (int)(pix % Wp);
-    const int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
-    const size_t plane = (size_t)H * W * 3, at = ((size_t)sh * W + sw) * 3;
-    float v[48];
+    // grid: x over the (pixel, group) pairs of one row (32-bit: Wp * G < 2^20), y over rows
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (uint32_t)Wp * (uint32_t)G) return;
+    const int w = (int)(t / (uint32_t)G), j = (int)(t - (uint32_t)w * (uint32_t)G);
+    const int sw = w < W ? w : W - 1;
+    const size_t plane = (size_t)H * W * 3;
+    for (int h = blockIdx.y; h < Hp; h += gridDim.y) {
+        const int sh = h < H ? h : H - 1;
+        const size_t at = ((size_t)sh * W + sw) * 3;
+        float v[8];
 #pragma unroll
-    for (int n = 0; n < 16; ++n) {
-        const bool live = n < N;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) v[3 * n + c] = live ? __ldg(frames + n * plane + at + c) / 255.0f : 0.0f;
+        for (int i = 0; i < 8; ++i) {
+            const int ch = 8 * j + i, n = ch / 3;
+            v[i] = n < N ? __ldg(frames + n * plane + at + (ch - 3 * n)) / 255.0f : 0.0f;
+        }
+        *reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w) * 64 + 8 * j) =
+            make_uint4(pack_bf16_pair(v[0], v[1]), pack_bf16_pair(v[2], v[3]), pack_bf16_pair(v[4], v[5]),
+                       pack_bf16_pair(v[6], v[7]));
     }
-    uint32_t packed[32];
-#pragma unroll
-    for (int j = 0; j < 24; ++j) packed[j] = pack_bf16_pair(v[2 * j], v[2 * j + 1]);
-#pragma unroll
-    for (int j = 24; j < 32; ++j) packed[j] = 0u;
-    uint4* o = reinterpret_cast<uint4*>(x + pix * 64);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) o[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
 }
 
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s) {
     (void)Cp;  // always 64 on this path (3N <= 48 < 64)
-    const size_t n = (size_t)Hp * Wp;
-    pack_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+    const int G = (3 * N + 7) / 8;
+    const dim3 grid((unsigned)(((size_t)Wp * G + 255) / 256), (unsigned)(Hp < 65535 ? Hp : 65535));
+    pack_bf16_kernel<<<grid, 256, 0, s>>>(frames, N, H, W, Hp, Wp, G, x);
 }
 
 // ------------------------------------------------------------------------------------------------
