@@ -309,8 +309,6 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         for (int k = 0; k < kBins - 1; ++k) zt[k] = (uint64_t)std::floor(npos * std::exp(2.0 * ctx->tabs.log_thr[k]));
         CK(cudaMemcpy(p->zthr, zt.data(), zt.size() * 8, cudaMemcpyHostToDevice));
         if (ctx->cfg.precision != UFVC_FP32) {
-            // channels 3N..63 of the packed input are never written by the packer: zero them once
-            CK(cudaMemset(p->x, 0, (size_t)p->Hp * p->Wp * p->C0p * 2));
             CK(cudaMemset(p->y_bf, 0, (size_t)p->Hye * p->Wye * ctx->arch.cy * 2));
             CK(cudaMemset(p->hb_bf, 0, (size_t)p->hhe * p->whe * ctx->arch.cz * 2));
         }

@@ -48,39 +48,66 @@ __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// bf16 variant for the tensor-core path (rows of Cp = 64 channels, 3N <= 48 of them real): one thread per
-// (pixel, 8-channel group) writes one 16-byte group, so consecutive threads write consecutive bytes of a
-// pixel row.  Only the ceil(3N / 8) groups that hold frame channels are written; the rest of each row
-// is zero from the buffer's creation and stays zero (the weights of those channels are zero too).
-__global__ void pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int G,
-                                 __nv_bfloat16* __restrict__ x) {
-    // grid: x over the (pixel, group) pairs of one row (32-bit: Wp * G < 2^20), y over rows
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (uint32_t)Wp * (uint32_t)G) return;
-    const int w = (int)(t / (uint32_t)G), j = (int)(t - (uint32_t)w * (uint32_t)G);
-    const int sw = w < W ? w : W - 1;
+// bf16 variant for the tensor-core path (rows of 64 channels, 3N <= 48 of them real).  A block packs a
+// segment of 128 pixels of one row, one thread per pixel: the thread reads its 3N bytes (a warp reads
+// 96 consecutive bytes of each frame row), converts them, and writes its 128-byte row into a
+// shared-memory tile (16-byte chunk k of row p at chunk k ^ (p & 7): no bank conflicts); the block then
+// copies the 16 KB tile to global memory with consecutive threads writing consecutive 16-byte chunks.
+constexpr int kPackPix = 128;
+
+__global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H,
+                                                             int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
+    __shared__ uint4 tile[kPackPix * 8];
+    __shared__ uint16_t lut[256];  // bf16 bits of v / 255 (a division per entry, not per pixel)
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 255.0f));
+    __syncthreads();
+    const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
+    const int sw = w < W ? w : W - 1;  // replicate the last column
     const size_t plane = (size_t)H * W * 3;
     for (int h = blockIdx.y; h < Hp; h += gridDim.y) {
-        const int sh = h < H ? h : H - 1;
-        const size_t at = ((size_t)sh * W + sw) * 3;
-        float v[8];
+        const int sh = h < H ? h : H - 1;  // replicate the last row
+        const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
+        uint32_t pk[32];
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            // channels 3n, 3n+1, 3n+2 -> bf16 halves 3n .. 3n+2 of the packed row
+            uint32_t b0 = 0, b1 = 0, b2 = 0;
+            if (n < N) {
+                b0 = lut[__ldg(src + n * plane)];
+                b1 = lut[__ldg(src + n * plane + 1)];
+                b2 = lut[__ldg(src + n * plane + 2)];
+            }
+            // halves 3n, 3n+1, 3n+2 land in words (3n)/2 .. (3n+2)/2 (n even: w, w, w+1 low; n odd: w high, w+1)
+            if ((n & 1) == 0) {
+                pk[3 * n / 2] = b0 | (b1 << 16);
+                pk[3 * n / 2 + 1] = b2;
+            } else {
+                pk[(3 * n - 1) / 2] |= b0 << 16;
+                pk[(3 * n + 1) / 2] = b1 | (b2 << 16);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint4 c = k < 6 ? make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3])
+                                  : make_uint4(0u, 0u, 0u, 0u);
+            tile[p * 8 + (k ^ (p & 7))] = c;
+        }
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w0) * 64);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const int ch = 8 * j + i, n = ch / 3;
-            v[i] = n < N ? __ldg(frames + n * plane + at + (ch - 3 * n)) / 255.0f : 0.0f;
+            const int idx = p + kPackPix * i, pr = idx >> 3, k = idx & 7;
+            if (w0 + pr < Wp) dst[idx] = tile[pr * 8 + (k ^ (pr & 7))];
         }
-        *reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w) * 64 + 8 * j) =
-            make_uint4(pack_bf16_pair(v[0], v[1]), pack_bf16_pair(v[2], v[3]), pack_bf16_pair(v[4], v[5]),
-                       pack_bf16_pair(v[6], v[7]));
+        __syncthreads();
     }
 }
 
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s) {
-    (void)Cp;  // always 64 on this path (3N <= 48 < 64)
-    const int G = (3 * N + 7) / 8;
-    const dim3 grid((unsigned)(((size_t)Wp * G + 255) / 256), (unsigned)(Hp < 65535 ? Hp : 65535));
-    pack_bf16_kernel<<<grid, 256, 0, s>>>(frames, N, H, W, Hp, Wp, G, x);
+    (void)Cp;  // always 64 on this path (3N <= 48 < 64, N <= 16)
+    const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
+    pack_bf16_kernel<<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
 }
 
 // ------------------------------------------------------------------------------------------------
