@@ -54,12 +54,14 @@ typedef enum {
 
 typedef enum {
     UFVC_FP32 = 0,  /* every convolution in FP32 on CUDA cores (deterministic) */
-    UFVC_BF16 = 1,  /* analysis and decoder convolutions: BF16 operands on tcgen05 tensor cores, FP32
-                       accumulation in TMEM; hyper-analysis and the entropy-parameter path stay FP32.
-                       arch 1 only (all activation widths multiples of 64); arch 0 gives
-                       UFVC_ERR_UNSUPPORTED */
-    UFVC_FP8 = 2    /* as BF16 but E4M3 operands with per-output-channel weight scales and one
-                       per-layer activation scale */
+    UFVC_BF16 = 1,  /* analysis, hyper-analysis and decoder convolutions: BF16 operands on tcgen05
+                       tensor cores, FP32 accumulation in TMEM; the entropy-parameter path (hyper-
+                       synthesis) stays deterministic FP32.  arch 1 only (all activation widths
+                       multiples of 64); arch 0 gives UFVC_ERR_UNSUPPORTED */
+    UFVC_FP8 = 2    /* as BF16 but the tensor-core layers (all except the final frame layer, which
+                       stays BF16) take E4M3 operands: weights with one scale per output channel
+                       (absmax / 448), activations with one scale per tensor from
+                       ufvc_calibrate_fp8; FP32 accumulation.  Needs calibration before use */
 } ufvc_precision;
 
 typedef struct {
@@ -213,6 +215,17 @@ ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, int* launche
 
 /* Human-readable description of the last error on this context ("" if none). */
 const char* ufvc_last_error(const ufvc_ctx* ctx);
+
+/* FP8 calibration: the FP32 path of the context's weights codes the given chunk (device frames, as for
+ * ufvc_encode_chunk) and every activation tensor of the E4M3 layers gets the scale absmax / 448 (the
+ * packed input in [0, 1] uses 1 / 448).  Only for precision UFVC_FP8; synchronises `stream`.  Until it
+ * has run, an FP8 context refuses the chunk calls with UFVC_ERR_ARG.  Calibrating again replaces the
+ * scales. */
+ufvc_status ufvc_calibrate_fp8(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height, int qp,
+                               void* stream);
+/* The calibrated activation scales, n >= 15 entries: packed input, A1, A2, A3, interaction hidden,
+ * A3 + interaction, y (hyper-analysis input), H1, y^, D0, R1a, R1b, U1, R2a, R2b. */
+ufvc_status ufvc_get_fp8_scales(const ufvc_ctx* ctx, float* act_scales, int n);
 
 /* ------------------------------------------------------------------------------------------------
  * Serving: continuous batching of chunk requests from many streams (the cross-chunk overlap that

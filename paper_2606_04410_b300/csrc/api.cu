@@ -9,6 +9,7 @@
 #include "ufvc_internal.h"
 
 #include <algorithm>
+#include <cuda_fp8.h>
 
 #include <cmath>
 #include <cstdio>
@@ -36,7 +37,20 @@ struct LayerW {
     // row 32 (c / 3) + 9 ky + 3 kx + c % 3 = the 64 input-channel weights of output channel c at tap
     // (ky, kx); the other rows zero
     __nv_bfloat16* wsc = nullptr;
+    // FP8 E4M3 copy (precision UFVC_FP8): E4M3 codes [groups][cout_pad][tap][cin_tc] in the row order of
+    // wtc, weight = code * wscale[g][row] with wscale = absmax over the output channel's weights / 448;
+    // after calibration cs8[g][row] = (input tensor scale) * wscale, out_inv = 1 / (output tensor scale)
+    // (0: the output is bf16 or float), res_s = the residual tensor's scale
+    uint8_t* w8 = nullptr;
+    std::vector<float> wscale;
+    float* cs8 = nullptr;
+    float out_inv = 0.f, res_s = 0.f;
 };
+
+// Activation tensors of the FP8 path, each with one per-tensor scale (absmax / 448 on the FP32 path of a
+// calibration chunk; the packed input in [0, 1] has 1 / 448).
+enum Fp8Tensor { T_X = 0, T_A1, T_A2, T_A3, T_XT, T_A3R, T_Y, T_HB, T_YHAT, T_D0, T_R1A, T_R1B, T_U1, T_R2A,
+                 T_R2B, T_NT };
 
 // Split-K workspace of the SIMT convolution, grown on first use.  One per direction of a plan (an
 // encode and a decode may run concurrently on different streams) and one for the stage entry points.
@@ -115,6 +129,10 @@ struct ufvc_ctx {
     Workspace* cur_ws = &ws_stage;
     // weights and tables borrowed from another context (ctx_clone_shared): not freed here
     bool borrowed = false;
+    // FP8: per-tensor activation scales (calibrated), and the absmax probe of a calibration run
+    bool fp8_ready = false;
+    float act_scale[T_NT] = {};
+    float* amax = nullptr;  // device [T_NT] while a calibration run records activation maxima
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -408,6 +426,27 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
             if ((st = dalloc(ctx, nullptr, &L.btc, bt.size())) != UFVC_OK) return st;
             CK(cudaMemcpy(L.btc, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice));
         }
+        if (ctx->cfg.precision == UFVC_FP8 && !final_layer) {
+            // E4M3 copy with one scale per output channel (per group): code = e4m3(w / s), s = absmax / 448
+            std::vector<uint8_t> w8((size_t)groups * L.cout_pad * K, 0);
+            L.wscale.assign((size_t)groups * co, 1.f);
+            for (int g = 0; g < groups; ++g) {
+                const float* src = blob + offs[first + g * D_NDEC];
+                for (int o = 0; o < co; ++o) {
+                    float amax = 0.f;
+                    for (size_t e = 0; e < (size_t)k * k * ci; ++e) amax = std::max(amax, std::fabs(src[(size_t)o * k * k * ci + e]));
+                    const float sc = amax > 0.f ? amax / 448.f : 1.f;
+                    L.wscale[(size_t)g * co + row(o)] = sc;
+                    for (int t = 0; t < k * k; ++t)
+                        for (int i = 0; i < ci; ++i)
+                            w8[((size_t)g * L.cout_pad + row(o)) * K + (size_t)t * L.cin_tc + i] = (uint8_t)
+                                __nv_cvt_float_to_fp8(src[((size_t)o * k * k + t) * ci + i] / sc, __NV_SATFINITE, __NV_E4M3);
+                }
+            }
+            if ((st = dalloc(ctx, nullptr, &L.w8, w8.size())) != UFVC_OK) return st;
+            CK(cudaMemcpy(L.w8, w8.data(), w8.size(), cudaMemcpyHostToDevice));
+            if ((st = dalloc(ctx, nullptr, &L.cs8, L.wscale.size())) != UFVC_OK) return st;
+        }
         if (final_layer && co == 12 && k == 3 && ci == 64) {
             std::vector<__nv_bfloat16> ws((size_t)groups * 128 * 64, __float2bfloat16(0.f));
             for (int g = 0; g < groups; ++g) {
@@ -431,8 +470,14 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     if (!ctx->borrowed) cudaDeviceSynchronize();  // a clone's owner has synchronised its stream
     for (auto& kv : ctx->plans) free_plan(kv.second);
     if (!ctx->borrowed) {
-        for (auto& L : ctx->enc) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc); }
-        for (auto& L : ctx->dec) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc); }
+        for (auto* Ls : {&ctx->enc[0], &ctx->dec[0]}) {
+            const int nl = Ls == &ctx->enc[0] ? L_NENC : D_NDEC;
+            for (int l = 0; l < nl; ++l) {
+                LayerW& L = Ls[l];
+                cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc);
+                cudaFree(L.w8); cudaFree(L.cs8);
+            }
+        }
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
     }
@@ -451,7 +496,6 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         cfg->lanes > 65536 || cfg->precision < 0 || cfg->precision > 2)
         return UFVC_ERR_ARG;
     if (n_weights != weight_count(cfg->arch, cfg->chunk_len)) return UFVC_ERR_ARG;
-    if (cfg->precision == UFVC_FP8) return UFVC_ERR_UNSUPPORTED;
     // the tensor-core path stages K in 64-channel chunks: every activation width must be a multiple of
     // 64, which holds for the 1080p-family widths only (the tiny widths include 96)
     if (cfg->precision != UFVC_FP32 && cfg->arch != 1) return UFVC_ERR_UNSUPPORTED;
@@ -540,6 +584,9 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
     if (use_tc(ctx, L)) {
         d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
         d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc;
+        if (ctx->cfg.precision == UFVC_FP8 && L.w8) {
+            d.w8 = L.w8; d.cscale = L.cs8; d.out_inv = L.out_inv; d.res_s = L.res_s;
+        }
         const cudaError_t e = launch_conv_tc(d, s);
         if (e != cudaSuccess) {
             ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
@@ -595,6 +642,9 @@ extern "C" ufvc_status ufvc_sync_status(ufvc_ctx* ctx, void* stream) {
 // ------------------------------------------------------------------------------------------------
 // pipeline stages
 // ------------------------------------------------------------------------------------------------
+// An FP8 context computes with calibrated activation scales (ufvc_calibrate_fp8)
+static bool fp8_unready(ufvc_ctx* ctx) { return ctx->cfg.precision == UFVC_FP8 && !ctx->fp8_ready; }
+
 static bool check_shape(ufvc_ctx* ctx, int n_frames, int width, int height) {
     return n_frames == ctx->N && width >= 1 && height >= 1 && width <= 65535 && height <= 65535;
 }
@@ -612,31 +662,49 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
     return UFVC_OK;
 }
 
+// FP8 calibration run (FP32 path): record max |x| of activation tensor t
+static void probe(ufvc_ctx* ctx, int t, const float* x, size_t n, cudaStream_t s) {
+    if (ctx->amax) launch_absmax(x, n, ctx->amax + t, s);
+}
+
 static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
     const Arch& a = ctx->arch;
+    const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     ctx->cur_ws = &p->ws_enc;
     prof_begin(ctx, "pack", s);
     if (ctx->cfg.precision == UFVC_FP32)
         launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
+    else if (fp8)
+        launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s);
     else
         launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "analysis", s);
     RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    probe(ctx, T_A1, p->a1, (size_t)p->h1 * p->w1 * a.e0, s);
     RUN(conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s));
+    probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);
     RUN(conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s));
+    probe(ctx, T_A3, p->a3, (size_t)p->h3 * p->w3 * a.e2, s);
     RUN(conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s));
+    probe(ctx, T_XT, p->xt, (size_t)p->h3 * p->w3 * a.e2, s);
     // cross-frame interaction residual, in place
     RUN(conv(ctx, ctx->enc[L_XB], p->xt, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3));
+    probe(ctx, T_A3R, p->a3, (size_t)p->h3 * p->w3 * a.e2, s);
     // y is float in every precision (it feeds the quantiser)
     RUN(conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s, nullptr, nullptr, 0, 0, 0,
              0, 1, true));
+    probe(ctx, T_Y, p->y, p->ny, s);
     prof_end(ctx, s, 6);
     prof_begin(ctx, "hyper_analysis", s);
     if (use_tc(ctx, ctx->enc[L_H1])) {
-        // BF16 tensor cores: only the encoder computes z (z^ travels in the bit-stream), so the
-        // hyper-analysis needs no bit-exact twin on the decoder side
-        launch_f32_to_bf16_rows(p->y, p->Hy, p->Wy, a.cy, p->y_bf, p->Wye, s);
+        // tensor cores: only the encoder computes z (z^ travels in the bit-stream), so the hyper-analysis
+        // needs no bit-exact twin on the decoder side
+        if (fp8)
+            launch_f32_to_e4m3_rows(p->y, p->Hy, p->Wy, a.cy, 1.f / ctx->act_scale[T_Y],
+                                    reinterpret_cast<uint8_t*>(p->y_bf), p->Wye, s);
+        else
+            launch_f32_to_bf16_rows(p->y, p->Hy, p->Wy, a.cy, p->y_bf, p->Wye, s);
         RUN(conv(ctx, ctx->enc[L_H1], p->y_bf, p->Hye, p->Wye, 2, 1, OUT_NHWC, p->hb_bf, p->hhe, p->whe, s));
         RUN(conv(ctx, ctx->enc[L_H2], p->hb_bf, p->hhe, p->whe, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s, nullptr,
                  nullptr, 0, 0, 0, 0, 1, true));
@@ -644,6 +712,7 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
         prof_end(ctx, s, 4);
     } else {
         RUN(conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s));
+        probe(ctx, T_HB, p->hb, (size_t)p->hh * p->wh * a.cz, s);
         RUN(conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s));
         launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
         prof_end(ctx, s, 3);
@@ -666,21 +735,27 @@ static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* 
     prof_begin(ctx, "dec.D0", s);
     RUN(conv(ctx, ctx->dec[D_D0], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, p->bufA, h1, w1, s, nullptr, nullptr, 0, 0, g1, 0,
              N));
+    probe(ctx, T_D0, (const float*)p->bufA, (size_t)N * h1 * w1 * a.cd1, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.R1", s);
     RUN(conv(ctx, ctx->dec[D_R1A], p->bufA, h1, w1, 1, 1, OUT_NHWC, p->bufT, h1, w1, s, nullptr, nullptr, 0, g1, g1, 0,
              N));
+    probe(ctx, T_R1A, (const float*)p->bufT, (size_t)N * h1 * w1 * a.cd1, s);
     RUN(conv(ctx, ctx->dec[D_R1B], p->bufT, h1, w1, 1, 0, OUT_NHWC, p->bufA, h1, w1, s, p->bufA, nullptr, 0, g1, g1,
              g1, N));
+    probe(ctx, T_R1B, (const float*)p->bufA, (size_t)N * h1 * w1 * a.cd1, s);
     prof_end(ctx, s, 2);
     prof_begin(ctx, "dec.U1", s);
     RUN(conv(ctx, ctx->dec[D_U1], p->bufA, h1, w1, 1, 1, OUT_PS, p->bufB, h2, w2, s, nullptr, nullptr, 0, g1, g2, 0, N));
+    probe(ctx, T_U1, (const float*)p->bufB, (size_t)N * h2 * w2 * a.cd2, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.R2", s);
     RUN(conv(ctx, ctx->dec[D_R2A], p->bufB, h2, w2, 1, 1, OUT_NHWC, p->bufT2, h2, w2, s, nullptr, nullptr, 0, g2, g2, 0,
              N));
+    probe(ctx, T_R2A, (const float*)p->bufT2, (size_t)N * h2 * w2 * a.cd2, s);
     RUN(conv(ctx, ctx->dec[D_R2B], p->bufT2, h2, w2, 1, 0, OUT_NHWC, p->bufB, h2, w2, s, p->bufB, nullptr, 0, g2, g2,
              g2, N));
+    probe(ctx, T_R2B, (const float*)p->bufB, (size_t)N * h2 * w2 * a.cd2, s);
     prof_end(ctx, s, 2);
     prof_begin(ctx, "dec.U2", s);
     RUN(conv(ctx, ctx->dec[D_U2], p->bufB, h2, w2, 1, 1, OUT_PS, p->bufC, h3, w3, s, nullptr, nullptr, 0, g2, g3, 0, N));
@@ -699,6 +774,7 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
                                          int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, void* stream) {
     if (!ctx || !d_frames || !d_bits || !d_nbytes || !check_shape(ctx, n_frames, width, height) || qp < 0 || qp > 63)
         return fail(ctx, UFVC_ERR_ARG, "encode_chunk: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "encode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
     Plan* p;
@@ -726,6 +802,7 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
                                int n_frames, int width, int height, void* stream, const uint64_t* d_nbytes = nullptr) {
     if (!ctx || !d_bits || !d_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
         return fail(ctx, UFVC_ERR_ARG, "decode_chunk: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "decode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
     Plan* p;
@@ -754,8 +831,11 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode_y", s);
     launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
+    const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
-                   fp32 ? nullptr : p->yhat_bf, s);
+                   fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
+                   fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
+    if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
     prof_end(ctx, s, 2);
     RUN(run_decoders(ctx, p, fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf, d_frames, final_mode, s));
     CK(cudaGetLastError());
@@ -851,6 +931,7 @@ extern "C" ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames
                                           int16_t* d_rhat, uint8_t* d_idx, void* stream) {
     if (!ctx || !d_frames || !check_shape(ctx, ctx->N, width, height) || qp < 0 || qp > 63)
         return fail(ctx, UFVC_ERR_ARG, "encode_stages: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "encode_stages: FP8 context not calibrated (ufvc_calibrate_fp8)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
     Plan* p;
@@ -911,6 +992,7 @@ extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int w
                                        void* stream) {
     if (!ctx || !d_yhat || !d_frames || !check_shape(ctx, ctx->N, width, height))
         return fail(ctx, UFVC_ERR_ARG, "synthesize: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "synthesize: FP8 context not calibrated (ufvc_calibrate_fp8)");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
     Plan* p;
@@ -921,7 +1003,11 @@ extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int w
     if (ctx->cfg.precision == UFVC_FP32) {
         RUN(run_decoders(ctx, p, d_yhat, d_frames, OUT_PS_FINAL_F32, s));
     } else {
-        launch_f32_to_bf16(d_yhat, p->ny, p->yhat_bf, s);
+        if (ctx->cfg.precision == UFVC_FP8)
+            launch_f32_to_e4m3_rows(d_yhat, p->Hy, p->Wy, ctx->arch.cy, 1.f / ctx->act_scale[T_YHAT],
+                                    reinterpret_cast<uint8_t*>(p->yhat_bf), p->Wy, s);
+        else
+            launch_f32_to_bf16(d_yhat, p->ny, p->yhat_bf, s);
         RUN(run_decoders(ctx, p, p->yhat_bf, d_frames, OUT_PS_FINAL_F32, s));
     }
     CK(cudaGetLastError());
@@ -933,6 +1019,7 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
     if (!ctx || !d_in || !d_out || layer < 0 || layer >= L_NENC + D_NDEC * ctx->N || H < 1 || W < 1 ||
         (stride != 1 && stride != 2) || mode < 0 || mode > 2 || out_h < 1 || out_w < 1)
         return fail(ctx, UFVC_ERR_ARG, "conv_layer: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "conv_layer: FP8 context not calibrated (ufvc_calibrate_fp8)");
     CK(cudaSetDevice(ctx->cfg.device));
     LayerW L;
     int g = 0;
@@ -946,6 +1033,8 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
         if (L.wtc) L.wtc += (size_t)g * L.cout_pad * L.k * L.k * L.cin_tc;
         if (L.btc) L.btc += g * L.b_gs;
         if (L.wsc) L.wsc += (size_t)g * 128 * 64;
+        if (L.w8) L.w8 += (size_t)g * L.cout_pad * L.k * L.k * L.cin_tc;
+        if (L.cs8) L.cs8 += g * L.b_gs;
     }
     L.groups = 1;
     const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
@@ -1066,3 +1155,80 @@ int* ctx_status_word(ufvc_ctx* c) { return c->d_status; }
 int ctx_device(const ufvc_ctx* c) { return c->cfg.device; }
 void ctx_set_error(ufvc_ctx* c, const char* msg) { c->err = msg; }
 }  // namespace ufvc
+
+// FP8 layer roles: input, output (-1: bf16 / float output) and residual activation tensors
+static void fp8_roles(bool enc, int l, int* tin, int* tout, int* tres) {
+    static const int E[L_NENC][3] = {{T_X, T_A1, -1},  {T_A1, T_A2, -1}, {T_A2, T_A3, -1}, {T_A3, T_XT, -1},
+                                     {T_XT, T_A3R, T_A3}, {T_A3R, -1, -1}, {T_Y, T_HB, -1},  {T_HB, -1, -1},
+                                     {-1, -1, -1},      {-1, -1, -1},     {-1, -1, -1}};
+    static const int D[D_NDEC][3] = {{T_YHAT, T_D0, -1}, {T_D0, T_R1A, -1}, {T_R1A, T_R1B, T_D0}, {T_R1B, T_U1, -1},
+                                     {T_U1, T_R2A, -1},  {T_R2A, T_R2B, T_U1}, {T_R2B, -1, -1},   {-1, -1, -1}};
+    const int* r = enc ? E[l] : D[l];
+    *tin = r[0]; *tout = r[1]; *tres = r[2];
+}
+
+extern "C" ufvc_status ufvc_calibrate_fp8(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width,
+                                          int height, int qp, void* stream) {
+    if (!ctx || !d_frames || !check_shape(ctx, n_frames, width, height) || qp < 0 || qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "calibrate_fp8: bad argument");
+    if (ctx->cfg.precision != UFVC_FP8) return fail(ctx, UFVC_ERR_ARG, "calibrate_fp8: not an FP8 context");
+    CK(cudaSetDevice(ctx->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the FP32 path of the same weights (a clone sharing them) codes the chunk and records the maxima
+    ufvc_ctx* c = ctx_clone_shared(ctx);
+    if (!c) return fail(ctx, UFVC_ERR_OOM, "calibrate_fp8: context clone failed");
+    c->cfg.precision = UFVC_FP32;
+    const size_t cap = ufvc_max_bitstream_bytes(ctx, width, height);
+    uint8_t *bits = nullptr, *out = nullptr;
+    uint64_t* nb = nullptr;
+    ufvc_status st = UFVC_OK;
+    float amax[T_NT] = {};
+    if (cudaMalloc(&c->amax, T_NT * sizeof(float)) != cudaSuccess || cudaMemset(c->amax, 0, T_NT * 4) != cudaSuccess ||
+        cudaMalloc(&bits, cap) != cudaSuccess || cudaMalloc(&nb, 8) != cudaSuccess ||
+        cudaMalloc(&out, (size_t)n_frames * width * height * 3) != cudaSuccess) {
+        cudaGetLastError();
+        st = UFVC_ERR_OOM;
+    }
+    if (st == UFVC_OK) st = ufvc_encode_chunk(c, d_frames, n_frames, width, height, qp, bits, cap, nb, stream);
+    if (st == UFVC_OK) st = ufvc_sync_status(c, stream);
+    uint64_t n = 0;
+    if (st == UFVC_OK && cudaMemcpy(&n, nb, 8, cudaMemcpyDeviceToHost) != cudaSuccess) st = UFVC_ERR_CUDA;
+    if (st == UFVC_OK) st = ufvc_decode_chunk(c, bits, n, out, n_frames, width, height, stream);
+    if (st == UFVC_OK) st = ufvc_sync_status(c, stream);
+    if (st == UFVC_OK && cudaMemcpy(amax, c->amax, sizeof(amax), cudaMemcpyDeviceToHost) != cudaSuccess)
+        st = UFVC_ERR_CUDA;
+    if (st != UFVC_OK) ctx->err = std::string("calibrate_fp8: FP32 run failed: ") + c->err;
+    cudaFree(c->amax);
+    c->amax = nullptr;
+    cudaFree(bits);
+    cudaFree(nb);
+    cudaFree(out);
+    ufvc_destroy(c);
+    (void)s;
+    if (st != UFVC_OK) return st;
+    for (int t = 0; t < T_NT; ++t) ctx->act_scale[t] = amax[t] > 0.f ? amax[t] / 448.f : 1.f / 448.f;
+    ctx->act_scale[T_X] = 1.f / 448.f;
+    // per-layer accumulator scales and output / residual scales
+    for (int pass = 0; pass < 2; ++pass) {
+        const int nl = pass == 0 ? L_NENC : D_NDEC;
+        for (int l = 0; l < nl; ++l) {
+            LayerW& L = pass == 0 ? ctx->enc[l] : ctx->dec[l];
+            if (!L.w8) continue;
+            int tin, tout, tres;
+            fp8_roles(pass == 0, l, &tin, &tout, &tres);
+            std::vector<float> cs(L.wscale.size());
+            for (size_t i = 0; i < cs.size(); ++i) cs[i] = ctx->act_scale[tin] * L.wscale[i];
+            CK(cudaMemcpy(L.cs8, cs.data(), cs.size() * 4, cudaMemcpyHostToDevice));
+            L.out_inv = tout >= 0 ? 1.f / ctx->act_scale[tout] : 0.f;
+            L.res_s = tres >= 0 ? ctx->act_scale[tres] : 0.f;
+        }
+    }
+    ctx->fp8_ready = true;
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_get_fp8_scales(const ufvc_ctx* ctx, float* act_scales, int n) {
+    if (!ctx || !act_scales || n < (int)T_NT || ctx->cfg.precision != UFVC_FP8 || !ctx->fp8_ready) return UFVC_ERR_ARG;
+    for (int t = 0; t < T_NT; ++t) act_scales[t] = ctx->act_scale[t];
+    return UFVC_OK;
+}

@@ -19,6 +19,7 @@
 #include "tc_ptx.h"
 
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 #include <cstdio>
 
@@ -46,6 +47,13 @@ struct TcArgs {
     long long res_gs;
     int ps_major;  // pixel shuffle with sub-pixel-major accumulator columns (column = sub * out_c + channel)
     int c_rank;    // staged epilogue: 4 = NHWC store map (C, W, H, G); 5 = pixel-shuffle map (C', dx, W, dy, G*H)
+    // FP8 E4M3 operands: accumulator column co is scaled by cscale[g * b_gs + co] (input tensor scale x the
+    // output channel's weight scale); out_inv != 0: the output is E4M3 code = value * out_inv; res8: an
+    // E4M3 residual of scale res_s
+    const float* cscale;
+    float out_inv;
+    const uint8_t* res8;
+    float res_s;
     int* err;
 };
 
@@ -101,6 +109,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) { ptx::tmem_
 template <int NV>
 __device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
                                             float* v) {
+    if (p.cscale) {  // FP8: undo the operand scales first
+        const float* cs = p.cscale + (size_t)g * p.b_gs + co0;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] *= (co0 + i < p.Cout) ? __ldg(cs + i) : 0.0f;
+    }
     const float* bias = bias_all + (size_t)g * p.b_gs + co0;
     if (co0 + NV <= p.Cout) {  // warp-uniform 16-byte loads (every lane reads the same columns)
 #pragma unroll
@@ -115,6 +128,21 @@ __device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_a
     if (p.act) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) v[i] = gelu_tc(v[i]);
+    }
+    if (p.mode == OUT_NHWC && p.res8 && co0 < p.Cout) {
+        const uint4* r = reinterpret_cast<const uint4*>(p.res8 + (size_t)g * p.res_gs +
+                                                        ((size_t)oh * p.out_w + ow) * p.out_c + co0);
+#pragma unroll
+        for (int i = 0; i < NV / 16; ++i) {
+            uint4 u = r[i];
+            const __nv_fp8x2_storage_t* h = reinterpret_cast<const __nv_fp8x2_storage_t*>(&u);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[j], __NV_E4M3)));
+                v[16 * i + 2 * j] += f.x * p.res_s;
+                v[16 * i + 2 * j + 1] += f.y * p.res_s;
+            }
+        }
     }
     if (p.mode == OUT_NHWC && !p.out_f32 && p.res && co0 < p.Cout) {
         const uint4* r = reinterpret_cast<const uint4*>(p.res + (size_t)g * p.res_gs +
@@ -134,6 +162,32 @@ template <int NV>
 __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
                                            float* v) {
     finish_cols<NV>(p, bias_all, g, oh, ow, co0, v);
+    if (p.out_inv != 0.0f && (p.mode == OUT_NHWC || (p.mode == OUT_PS && p.ps_major))) {
+        // E4M3 output: NV consecutive channels of one pixel
+        size_t o;
+        if (p.mode == OUT_NHWC) {
+            if (co0 >= p.Cout) return;
+            o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c + co0;
+        } else {
+            const int sub = co0 / p.out_c, cb = co0 - sub * p.out_c;
+            const int y = 2 * oh + (sub >> 1), x = 2 * ow + (sub & 1);
+            if (sub > 3 || y >= p.out_h || x >= p.out_w) return;
+            o = (size_t)g * p.out_gs + ((size_t)y * p.out_w + x) * p.out_c + cb;
+        }
+        uint32_t w[NV / 4];
+#pragma unroll
+        for (int i = 0; i < NV / 4; ++i) {
+            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i] * p.out_inv, v[4 * i + 1] * p.out_inv),
+                                                         __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[4 * i + 2] * p.out_inv, v[4 * i + 3] * p.out_inv), __NV_SATFINITE, __NV_E4M3);
+            w[i] = lo | (hi << 16);
+        }
+        uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(p.out) + o);
+#pragma unroll
+        for (int i = 0; i < NV / 16; ++i) d[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+        return;
+    }
     if (p.mode == OUT_NHWC) {
         if (co0 >= p.Cout) return;
         const size_t o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c + co0;
@@ -199,12 +253,16 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 // (64-column slabs of 128 rows x 128 B, the layout a TMA box of 64 channels x TW x TH has) and one thread
 // per slab group stores it with TMA tiled stores, which clip at the tensor edges.  Otherwise every
 // epilogue thread stores its own pixel's columns.
-template <int BN, int STAGES, bool STAGED>
+// F8: E4M3 operands (kind::f8f6f4, K = 32 per MMA) in rows of 64 bytes with the 64-byte swizzle, so a
+// pipeline stage is again 64 input channels; the accumulators are rescaled in the epilogue.
+template <int BN, int STAGES, bool STAGED, bool F8 = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
-    constexpr int A_BYTES = 128 * 128;
-    constexpr int B_BYTES = BN * 128;
+    static_assert(!(F8 && STAGED), "FP8 outputs use the per-thread epilogue");
+    constexpr int ROWB = F8 ? 64 : 128;  // bytes of one K row (64 channels) of a stage
+    constexpr int A_BYTES = 128 * ROWB;
+    constexpr int B_BYTES = BN * ROWB;
     constexpr int C_BYTES = STAGED ? 128 * BN * 2 : 0;
     constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
     // each of the four epilogue warps of a lane quarter drains a quarter of the BN columns
@@ -301,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_bf16(BN);
+            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(BN) : ptx::idesc_bf16(BN);
             int it = 0, tl = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x, ++tl) {
@@ -315,10 +373,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!wait_bar(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
                     ptx::tc_fence_after();
                     const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB + s * B_BYTES);
+                    if constexpr (F8) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32), idesc,
-                                     (ks | kk) != 0);
+                        for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
+                            ptx::mma_f8(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
+                                        (ks | kk) != 0);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
+                            ptx::mma_f16(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32),
+                                         idesc, (ks | kk) != 0);
+                    }
                     ptx::mma_commit(&empty[s]);
                 }
                 if (ok) ptx::mma_commit(&tfull[acc]);
@@ -956,16 +1021,17 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED>
+template <int BN, int STAGES, bool STAGED, bool F8 = false>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
-    const int smem = STAGES * (128 * 128 + BN * 128) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra;
-    static_assert(STAGES * (128 * 128 + BN * 128) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra <= 227 * 1024,
-                  "shared memory per CTA");
+    constexpr int ROWB = F8 ? 64 : 128;
+    constexpr int kSmem = STAGES * (128 * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra;
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+    const int smem = kSmem;
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e =
-            cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, F8>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
     }
@@ -976,7 +1042,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_kernel<BN, STAGES, STAGED><<<grid, kThreads, smem, s>>>(a, b, c, args);
+    conv_tc_kernel<BN, STAGES, STAGED, F8><<<grid, kThreads, smem, s>>>(a, b, c, args);
     return cudaGetLastError();
 }
 
@@ -1095,18 +1161,19 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // stride-1 3x3 layers with 64 input channels and at most 64 output channels: resident weights,
     // three input rows per 128-pixel strip (wider layers keep one N tile on the streaming kernel, which
     // re-reads the input less than several N tiles would)
-    const bool halo = d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
+    const bool f8 = d.w8 != nullptr;  // E4M3 operands: streaming kernel, per-thread epilogue
+    const bool halo = !f8 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
     if (halo) BN = d.cout_pad;
     // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
     // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
     // stored through one map whose row dimension spans all groups, so tiles must not cross a group's
     // last row (TH divides Ho)
     const int Cq = d.Cout / 4;
-    const bool ps_stage = !halo && BN >= 64 && d.mode == OUT_PS && d.ps_major && Cq % 64 == 0 &&
+    const bool ps_stage = !f8 && !halo && BN >= 64 && d.mode == OUT_PS && d.ps_major && Cq % 64 == 0 &&
                           d.out_h == 2 * Ho && d.out_w == 2 * Wo &&
                           (d.groups == 1 || d.out_gs == 4LL * Ho * Wo * Cq);
     const int out_c = (d.mode == OUT_NHWC && d.out_c_stride) ? d.out_c_stride : d.Cout;
-    const bool nhwc_stage = !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 &&
+    const bool nhwc_stage = !f8 && !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 &&
                             d.out_gs % 8 == 0;
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
@@ -1129,9 +1196,18 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.res = reinterpret_cast<const __nv_bfloat16*>(d.res); a.res_gs = d.res_gs;
     a.err = d.err;
     a.c_rank = ps_stage ? 5 : 4;
+    if (f8) {
+        a.res = nullptr;
+        a.res8 = reinterpret_cast<const uint8_t*>(d.res);
+        a.res_s = d.res_s;
+        a.cscale = d.cscale;
+        a.out_inv = d.out_inv;
+    }
 
     CUtensorMap ma, mb;
-    const cuuint64_t esz = 2;
+    const cuuint64_t esz = f8 ? 1 : 2;
+    const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapSwizzle swz = f8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     bool ok;
     if (d.stride == 1) {
         const int G = a.a_grouped ? d.groups : 1;
@@ -1140,13 +1216,13 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
         cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
         if (halo) { box[1] = 130; box[2] = 1; }
-        ok = encode_map(&ma, d.in, 4, dims, str, box);
+        ok = encode_map(&ma, d.in, 4, dims, str, box, dt, swz);
     } else {
         cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
         cuuint64_t str[4] = {d.Cin * esz, 2 * d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz,
                              2ull * d.W * d.Cin * esz};
         cuuint32_t box[5] = {64, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
-        ok = encode_map(&ma, d.in, 5, dims, str, box);
+        ok = encode_map(&ma, d.in, 5, dims, str, box, dt, swz);
     }
     if (!ok) return cudaErrorInvalidValue;
     {
@@ -1154,9 +1230,19 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t dims[3] = {K, (cuuint64_t)d.cout_pad, (cuuint64_t)d.groups};
         cuuint64_t str[2] = {K * esz, K * d.cout_pad * esz};
         cuuint32_t box[3] = {64, (cuuint32_t)BN, 1};
-        if (!encode_map(&mb, d.wtc, 3, dims, str, box)) return cudaErrorInvalidValue;
+        if (!encode_map(&mb, f8 ? d.w8 : d.wtc, 3, dims, str, box, dt, swz)) return cudaErrorInvalidValue;
     }
     CUtensorMap mc = mb;  // unused by the unstaged kernels
+    if (f8) {
+        if (d.mode != OUT_NHWC && !(d.mode == OUT_PS && d.ps_major)) return cudaErrorInvalidValue;
+        switch (BN) {
+            case 16: return launch_bn<16, 8, false, true>(ma, mb, mc, a, s);
+            case 64: return launch_bn<64, 8, false, true>(ma, mb, mc, a, s);
+            case 128: return launch_bn<128, 8, false, true>(ma, mb, mc, a, s);
+            case 192: return launch_bn<192, 8, false, true>(ma, mb, mc, a, s);
+            default: return launch_bn<256, 7, false, true>(ma, mb, mc, a, s);
+        }
+    }
     if (halo) {
         // staged stores: bf16 NHWC (64 channels per strip pixel), or the final u8 frame whose rows are a
         // multiple of 16 bytes (three 256-byte boxes per output row pair of a strip)

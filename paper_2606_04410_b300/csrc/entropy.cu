@@ -9,6 +9,10 @@
 //                    to lane i mod K; 32-bit state in [2^16, 2^32), 16-bit probabilities, 16-bit words,
 //                    at most one renormalisation word per symbol.
 #include "ufvc_internal.h"
+
+#include <cuda_fp8.h>
+
+#include <algorithm>
 #include "tc_ptx.h"
 
 #include <cub/block/block_scan.cuh>
@@ -108,6 +112,85 @@ void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp
     (void)Cp;  // always 64 on this path (3N <= 48 < 64, N <= 16)
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
     pack_bf16_kernel<<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+}
+
+// E4M3 variant: the same segment scheme with 64-byte pixel rows; x = v / 255 is stored as the E4M3 code
+// of x * 448 (the per-tensor scale of [0, 1] data: 1 / 448).
+__global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __restrict__ frames, int N, int H,
+                                                            int W, int Hp, int Wp, uint8_t* __restrict__ x) {
+    __shared__ uint4 tile[kPackPix * 4];
+    __shared__ uint8_t lut[256];
+    for (int v = threadIdx.x; v < 256; v += blockDim.x)
+        lut[v] = (uint8_t)__nv_cvt_float_to_fp8((v / 255.0f) * 448.0f, __NV_SATFINITE, __NV_E4M3);
+    __syncthreads();
+    const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
+    const int sw = w < W ? w : W - 1;
+    const size_t plane = (size_t)H * W * 3;
+    for (int h = blockIdx.y; h < Hp; h += gridDim.y) {
+        const int sh = h < H ? h : H - 1;
+        const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pk[i] = 0u;
+#pragma unroll
+        for (int n = 0; n < 16; ++n) {
+            if (n < N) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const int b = 3 * n + c;  // byte b of the row: word b / 4, byte b % 4
+                    pk[b >> 2] |= (uint32_t)lut[__ldg(src + n * plane + c)] << (8 * (b & 3));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tile[p * 4 + (k ^ (p & 3))] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w0) * 64);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int idx = p + kPackPix * i, pr = idx >> 2, k = idx & 3;
+            if (w0 + pr < Wp) dst[idx] = tile[pr * 4 + (k ^ (pr & 3))];
+        }
+        __syncthreads();
+    }
+}
+
+void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s) {
+    const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
+    pack_fp8_kernel<<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+}
+
+// [H][W][C] float -> E4M3 codes of value * inv, rows of pitch Wd pixels (C a multiple of 4)
+__global__ void f32_to_e4m3_rows_kernel(const float4* a, int H, int W, int C4, float inv, uint8_t* out, int Wd) {
+    const size_t n = (size_t)H * W * C4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = i / ((size_t)W * C4), rem = i - row * W * C4;
+        const float4 v = a[i];
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v.x * inv, v.y * inv), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v.z * inv, v.w * inv), __NV_SATFINITE, __NV_E4M3);
+        *reinterpret_cast<uint32_t*>(out + (row * Wd * C4 + rem) * 4) = lo | (hi << 16);
+    }
+}
+
+void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s) {
+    const size_t n = (size_t)H * W * (C / 4);
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    f32_to_e4m3_rows_kernel<<<blocks ? blocks : 1, 256, 0, s>>>(reinterpret_cast<const float4*>(a), H, W, C / 4, inv,
+                                                             out, Wd);
+}
+
+// *slot = max(*slot, max |x[i]|) (slot zeroed by the caller); non-negative floats order as their bits
+__global__ void absmax_kernel(const float* __restrict__ x, size_t n, float* slot) {
+    float m = 0.f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(slot), __float_as_int(m));
+}
+
+void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s) {
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 2048);
+    absmax_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(x, n, slot);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -600,18 +683,20 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
 // y^ = r^ q + mu (explicitly rounded ops), to float and / or bf16; q from the parsed rate
 __global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __restrict__ mu, size_t n,
                                const float* __restrict__ qstep_all, const int* __restrict__ qp_dev,
-                               float* __restrict__ yf, __nv_bfloat16* __restrict__ yb) {
+                               float* __restrict__ yf, __nv_bfloat16* __restrict__ yb, uint8_t* __restrict__ y8,
+                               float inv8) {
     const float q = qstep_all[*qp_dev];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float v = __fadd_rn(__fmul_rn((float)rhat[i], q), mu[i]);
         if (yf) yf[i] = v;
         if (yb) yb[i] = __float2bfloat16_rn(v);
+        if (y8) y8[i] = (uint8_t)__nv_cvt_float_to_fp8(v * inv8, __NV_SATFINITE, __NV_E4M3);
     }
 }
 
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
-                    float* yf, __nv_bfloat16* yb, cudaStream_t s) {
-    dequant_kernel<<<grid_for(n, 256), 256, 0, s>>>(rhat, mu, n, qstep_all, qp_dev, yf, yb);
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8, float inv8) {
+    dequant_kernel<<<grid_for(n, 256), 256, 0, s>>>(rhat, mu, n, qstep_all, qp_dev, yf, yb, y8, inv8);
 }
 
 // ------------------------------------------------------------------------------------------------

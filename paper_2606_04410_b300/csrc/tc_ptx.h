@@ -178,6 +178,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
+// As sdesc_sw128 for the 64-byte swizzle: rows of 64 B, 8-row core groups 512 B apart (SBO).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;      // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)4 << 61;               // swizzle mode: 64 B
+    return d;
+}
+
 // Instruction descriptor: D = FP32, A = B = BF16 (kind::f16) or E4M3 (kind::f8f6f4), both K-major,
 // M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n) {

@@ -81,6 +81,13 @@ struct ConvDesc {
     const float* btc = nullptr; // tensor-core bias in accumulator-column order (nullptr: same as b)
     int ps_major = 0;           // tensor-core weights in sub-pixel-major column order (pixel shuffle layers)
     const void* wsc = nullptr;  // final layer, scatter form: bf16 [groups][128][64] (row = tap x channel)
+    // FP8 E4M3 (precision UFVC_FP8): weights [groups][cout_pad][k*k*Cin] E4M3; accumulator column co is
+    // multiplied by cscale[g * b_gs + co]; out_inv != 0: E4M3 output (code = value * out_inv), else the
+    // output is bf16 (or float with out_f32); res is then an E4M3 residual of scale res_s
+    const void* w8 = nullptr;
+    const float* cscale = nullptr;
+    float out_inv = 0.f;
+    float res_s = 0.f;
     float* ws = nullptr;        // SIMT split-K workspace (conv_simt_workspace(d) floats), or nullptr
     size_t ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
@@ -111,6 +118,10 @@ void launch_scale_index(const float* logsig, size_t n, const float* thr_all, con
 void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s);
 void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s);
 void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16* out, int Wd, cudaStream_t s);
+// FP8 E4M3 helpers: packed input rows of 64 bytes (scale 1/448), float -> E4M3 rows, |x| maximum
+void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s);
+void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s);
+void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s);
 
 // rANS: a "section job" describes one section of one stream
 struct RansSection {
@@ -157,7 +168,7 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
                         cudaStream_t s);
 // y^ = r^ q + mu with q = qstep_all[*qp_dev]; yf and / or yb may be null
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
-                    float* yf, __nv_bfloat16* yb, cudaStream_t s);
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f);
 
 // Container header
 void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,

@@ -33,7 +33,8 @@ EXPORTS = [
     "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error", "ufvc_conv_layer",
     "ufvc_rans_encode_noalloc", "ufvc_decode_chunk_dev", "ufvc_server_create", "ufvc_server_destroy",
     "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
-    "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error",
+    "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error", "ufvc_calibrate_fp8",
+    "ufvc_get_fp8_scales",
 ]
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
 
@@ -91,6 +92,8 @@ _sigs = {
     "ufvc_server_wait": (_i, [_vp, C.c_uint64, C.c_double, C.POINTER(ufvc_result)]),
     "ufvc_server_stats_get": (_i, [_vp, C.POINTER(ufvc_server_stats)]),
     "ufvc_server_last_error": (C.c_char_p, [_vp]),
+    "ufvc_calibrate_fp8": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
+    "ufvc_get_fp8_scales": (_i, [_vp, _vp, _i]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -165,6 +168,16 @@ class Codec:
     def _check(self, rc: int, what: str):
         if rc:
             raise UfvcError(rc, f"{what}: {lib.ufvc_last_error(self.h).decode()}")
+
+    # ---- FP8 calibration
+    def calibrate_fp8(self, frames: torch.Tensor, qp: int = 32, stream=None):
+        N, H, W, _ = frames.shape
+        self._check(lib.ufvc_calibrate_fp8(self.h, _ptr(frames), N, W, H, qp, _stream(stream)), "calibrate_fp8")
+
+    def fp8_scales(self) -> np.ndarray:
+        out = np.zeros(15, np.float32)
+        self._check(lib.ufvc_get_fp8_scales(self.h, _ptr(out), 15), "get_fp8_scales")
+        return out
 
     # ---- chunk calls
     def max_bitstream_bytes(self, width: int, height: int) -> int:
