@@ -351,6 +351,7 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-path", action="store_true")
     ap.add_argument("--no-entropy-sweep", action="store_true")
+    ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
@@ -381,6 +382,8 @@ def main() -> None:
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
     codec = U.Codec(1, N, K, blob, args.precision, device=local)
+    if args.precision == "fp8":  # activation scales from the FP32 path on this chunk (seed 0 on rank 0)
+        codec.calibrate_fp8(fr, QP)
     sampler = ClockSampler(local)
     r = time_codec(codec, fr, frames_np, W_, H_, args.steps, args.warmup, True, flush, dist, world)
     clocks = sampler.stop()
@@ -445,6 +448,21 @@ def main() -> None:
                 "bytes_per_chunk": r32["nbytes"], "steps": s32}
         c32.close()
 
+    # ---- the FP8 E4M3 variant under the same methodology (calibrated on this chunk)
+    fp8 = None
+    if args.precision == "bf16" and not args.no_fp8:
+        c8 = U.Codec(1, N, K, blob, "fp8", device=local)
+        c8.calibrate_fp8(fr, QP)
+        s8 = max(3, args.steps // 2)
+        r8 = time_codec(c8, fr, frames_np, W_, H_, s8, 3, True, flush)
+        v8 = N * s8 / (sum(a + b for a, b in zip(r8["t_enc"], r8["t_dec"])) / 1000.0)
+        fp8 = {"value": v8, "enc_fps": N / (statistics.mean(r8["t_enc"]) / 1000.0),
+               "dec_fps": N / (statistics.mean(r8["t_dec"]) / 1000.0), "psnr_db": r8["psnr"],
+               "bytes_per_chunk": r8["nbytes"], "steps": s8,
+               "stage_ms_per_step": {k: round(sum(m for m, _ in v) / s8, 4) for k, v in
+                                     sorted(r8["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}}
+        c8.close()
+
     # ---- end-to-end through the host-buffer C calls (pinned host memory, copies inside the region)
     cap = r["cap"]
     h_frames = torch.from_numpy(frames_np).pin_memory()
@@ -500,6 +518,12 @@ def main() -> None:
             line["speedup_vs_fp32"] = value / fp32["value"]
             line["dpsnr_db_vs_fp32"] = r["psnr"] - fp32["psnr_db"]
             line["dbitrate_vs_fp32"] = (r["nbytes"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
+        if fp8 is not None:
+            if fp32 is not None:
+                fp8["dpsnr_db_vs_fp32"] = fp8["psnr_db"] - fp32["psnr_db"]
+                fp8["dbitrate_vs_fp32"] = (fp8["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
+                fp8["speedup_vs_fp32"] = fp8["value"] / fp32["value"]
+            line["fp8_path"] = fp8
         if not args.no_entropy_sweep:
             line["entropy_sweep"] = entropy_sweep(U, dev)
         if serving is not None:
