@@ -319,7 +319,12 @@ void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16*
 // ------------------------------------------------------------------------------------------------
 struct RansSecPair { RansSection s[2]; int nsec; };
 
-constexpr int kRansThreads = 128;
+// Lanes per block: small blocks spread the lanes over the SMs (each block holds its own copy of the
+// tables), so that the lanes' dependent chains do not queue behind each other on one SM's shared
+// memory: the 4096 lanes of a 1080p latent section run on 128 SMs (decode) or the 2 x 4096 of the two
+// encoded sections on 128 SMs (encode).
+constexpr int kRansThreadsEnc = 64;
+constexpr int kRansThreadsDec = 32;
 
 // Loads issued where they stand: the per-lane prefetches below must not be moved down next to their use.
 __device__ __forceinline__ int ld_early_u8(const uint8_t* p) {
@@ -381,7 +386,7 @@ __device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __res
 // rANS encode: one thread per lane, lanes of up to two sections in one launch.  Each lane runs its
 // elements backwards (last first) and writes its words backwards into its scratch row, so that the
 // row's tail [cap_lane - words, cap_lane) is the lane stream in decoding order.
-__global__ void __launch_bounds__(kRansThreads) rans_encode_kernel(const RansSecPair P,
+__global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const RansSecPair P,
                                                                    const uint32_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum
     __shared__ uint64_t bar;
@@ -452,7 +457,7 @@ void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packe
         cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes);
         attr = true;
     }
-    rans_encode_kernel<<<(total + kRansThreads - 1) / kRansThreads, kRansThreads, kTabBytes, s>>>(P, packed_tables);
+    rans_encode_kernel<<<(total + kRansThreadsEnc - 1) / kRansThreadsEnc, kRansThreadsEnc, kTabBytes, s>>>(P, packed_tables);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -596,7 +601,7 @@ void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const u
     rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, expect_end_dev, status);
 }
 
-__global__ void __launch_bounds__(kRansThreads) rans_decode_kernel(const RansDecodeJob J,
+__global__ void __launch_bounds__(kRansThreadsDec) rans_decode_kernel(const RansDecodeJob J,
                                                                    const uint32_t* __restrict__ tables,
                                                                    const uint16_t* __restrict__ coarse_g, int* status) {
     extern __shared__ __align__(16) uint32_t tab[];                      // [64][511] (freq << 16) | cum
@@ -676,7 +681,7 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
         cudaFuncSetAttribute(rans_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    rans_decode_kernel<<<(j.K + kRansThreads - 1) / kRansThreads, kRansThreads, smem, s>>>(j, packed_tables, coarse,
+    rans_decode_kernel<<<(j.K + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(j, packed_tables, coarse,
                                                                                            status);
 }
 
