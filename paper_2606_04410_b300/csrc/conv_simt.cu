@@ -314,6 +314,131 @@ __global__ void __launch_bounds__(256) conv_simt64_kernel(const ConvDesc d, int 
     }
 }
 
+// 64 x 128 tile, 128 threads, 8 x 8 outputs per thread: pixels tm*4 .. +3 and 32 + tm*4 .. +3, channels
+// tn*4 .. +3 and 64 + tn*4 .. +3 (tm = tid / 16, tn = tid % 16), so each K step reads two float4 of A
+// and two of B from shared memory for 64 FMAs (the 4 x 4 tiles are bound by shared-memory bandwidth).
+// K staged 16 input channels per step, global loads two steps ahead, shared tiles double-buffered;
+// split-K ranges and the PARTIAL workspace exactly as in conv_simt64_kernel.  Cout % 128 == 0.
+template <bool PARTIAL>
+__global__ void __launch_bounds__(128) conv_simt88_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
+    constexpr int BM = 64, BN = 128, BK = 16;
+    __shared__ __align__(16) float As[2][BK][BM + 4];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+
+    const int g = blockIdx.z / KS, ks = blockIdx.z - g * KS;
+    const float* in = (const float*)d.in + (size_t)g * d.in_gs;
+    const float* w = d.w + (size_t)g * d.w_gs;
+    const int M = Ho * Wo;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x;
+    const int H = d.H, W = d.W, Cin = d.Cin, Cout = d.Cout, k = d.k, s = d.stride, p = d.k / 2;
+
+    // A loads: 2 float4 per thread (pixel q >> 2, channels 4 (q & 3) .. +3), q = tid + 128 r
+    int a_oh[2], a_ow[2];
+    bool a_ok[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int m = m0 + ((tid + 128 * r) >> 2);
+        a_ok[r] = m < M;
+        a_oh[r] = a_ok[r] ? m / Wo : 0;
+        a_ow[r] = a_ok[r] ? m - a_oh[r] * Wo : 0;
+    }
+    const int nck = Cin / BK, nsteps = k * k * nck;
+    const int s_begin = (int)((long long)ks * nsteps / KS), s_end = (int)((long long)(ks + 1) * nsteps / KS);
+    float4 ra[2][2], rb[2][4];
+    auto load_regs = [&](int step, float4* qa, float4* qb) {
+        const int tap = step / nck, c0 = (step - tap * nck) * BK;
+        const int ky = tap / k, kx = tap - ky * k;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int ih = a_oh[r] * s + ky - p, iw = a_ow[r] * s + kx - p;
+            if (a_ok[r] && ih >= 0 && ih < H && iw >= 0 && iw < W)
+                qa[r] = *reinterpret_cast<const float4*>(in + ((size_t)ih * W + iw) * Cin + c0 + ((tid + 128 * r) & 3) * 4);
+            else
+                qa[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {  // B: row q >> 5, channels n0 + 4 (q & 31) .. +3
+            const int q = tid + 128 * r;
+            qb[r] = *reinterpret_cast<const float4*>(w + ((size_t)tap * Cin + c0 + (q >> 5)) * Cout + n0 + (q & 31) * 4);
+        }
+    };
+    auto store_smem = [&](int buf, const float4* qa, const float4* qb) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int q = tid + 128 * r, pix = q >> 2, cg = q & 3;
+            As[buf][cg * 4 + 0][pix] = qa[r].x;
+            As[buf][cg * 4 + 1][pix] = qa[r].y;
+            As[buf][cg * 4 + 2][pix] = qa[r].z;
+            As[buf][cg * 4 + 3][pix] = qa[r].w;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int q = tid + 128 * r;
+            *reinterpret_cast<float4*>(&Bs[buf][q >> 5][(q & 31) * 4]) = qb[r];
+        }
+    };
+
+    const int tn = tid & 15, tm = tid >> 4;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    auto fma_tile = [&](int buf) {
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tm * 4]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][32 + tm * 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tn * 4]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tn * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+    };
+    if (s_begin < s_end) load_regs(s_begin, ra[0], rb[0]);
+    if (s_begin + 1 < s_end) load_regs(s_begin + 1, ra[1], rb[1]);
+    if (s_begin < s_end) store_smem(0, ra[0], rb[0]);
+    __syncthreads();
+    for (int t = s_begin; t < s_end; t += 2) {
+        if (t + 2 < s_end) load_regs(t + 2, ra[0], rb[0]);
+        fma_tile(0);
+        if (t + 1 < s_end) store_smem(1, ra[1], rb[1]);
+        __syncthreads();
+        if (t + 1 >= s_end) break;
+        if (t + 3 < s_end) load_regs(t + 3, ra[1], rb[1]);
+        fma_tile(1);
+        if (t + 2 < s_end) store_smem(0, ra[0], rb[0]);
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + (i < 4 ? tm * 4 + i : 32 + tm * 4 + i - 4);
+        if (m >= M) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co0 = n0 + h * 64 + tn * 4;
+            if (PARTIAL) {
+                *reinterpret_cast<float4*>(ws + (((size_t)g * KS + ks) * M + m) * Cout + co0) =
+                    make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+            } else {
+                const int oh = m / Wo, ow = m - oh * Wo;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float v = acc[i][4 * h + j] + d.b[(size_t)g * d.b_gs + co0 + j];
+                    if (d.act) v = gelu_erf(v);
+                    store_out(d, g, oh, ow, co0 + j, v);
+                }
+            }
+        }
+    }
+}
+
 // out = bias + (((range 0) + range 1) + ...), then the layer's activation and output mapping
 __global__ void conv_simt_reduce_kernel(const ConvDesc d, int Ho, int Wo, int KS, const float* ws) {
     const int M = Ho * Wo, Cout = d.Cout;
@@ -342,7 +467,18 @@ static int simt_plan(const ConvDesc& d, int* KS) {
     if (d.Cout <= 16) return 0;
     const long long ctas128 = ((M + 127) / 128) * ((d.Cout + 63) / 64) * d.groups;
     if (ctas128 >= 4 * 148) return 1;
-    // small layers (hyper-analysis / hyper-synthesis): 64 x 64 tiles, K split until two CTAs per SM
+    const int nsteps16 = d.k * d.k * (d.Cin / 16);
+    if (d.Cout % 128 == 0 && d.Cin % 16 == 0) {
+        // small layers with 128-multiple widths (the hyper-synthesis): 64 x 128 tiles of 8 x 8 per
+        // thread, K split until three CTAs per SM
+        const long long ctas = ((M + 63) / 64) * (d.Cout / 128) * d.groups;
+        long long ks = (3 * 148 + ctas - 1) / ctas;
+        if (ks > 9) ks = 9;
+        if (ks > nsteps16) ks = nsteps16;
+        *KS = (int)(ks < 1 ? 1 : ks);
+        return 3;
+    }
+    // other small layers: 64 x 64 tiles, K split until two CTAs per SM
     const long long ctas64 = ((M + 63) / 64) * ((d.Cout + 63) / 64) * d.groups;
     const int nsteps = d.k * d.k * (d.Cin / (d.Cin % 32 == 0 ? 32 : 16));
     long long ks = (2 * 148 + ctas64 - 1) / ctas64;
@@ -354,7 +490,8 @@ static int simt_plan(const ConvDesc& d, int* KS) {
 
 size_t conv_simt_workspace(const ConvDesc& d) {
     int KS;
-    if (simt_plan(d, &KS) != 2 || KS == 1) return 0;
+    const int kind = simt_plan(d, &KS);
+    if ((kind != 2 && kind != 3) || KS == 1) return 0;
     const int p = d.k / 2;
     const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
     return (size_t)KS * d.groups * Ho * Wo * d.Cout;
@@ -372,6 +509,17 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
     } else if (kind == 1) {
         dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
         conv_simt_kernel<128, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
+    } else if (kind == 3) {
+        dim3 grid((M + 63) / 64, d.Cout / 128, d.groups * KS);
+        if (KS > 1) {
+            if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;
+            conv_simt88_kernel<true><<<grid, 128, 0, st>>>(d, Ho, Wo, KS, d.ws);
+            const size_t total = (size_t)d.groups * M * d.Cout;
+            const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+            conv_simt_reduce_kernel<<<blocks, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+        } else {
+            conv_simt88_kernel<false><<<grid, 128, 0, st>>>(d, Ho, Wo, 1, nullptr);
+        }
     } else if (KS > 1) {
         if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;  // caller's workspace
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups * KS);
