@@ -180,7 +180,9 @@ ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, 
  * [out_h][out_w][Cout/4] (positions outside out_h x out_w are dropped), mode 2 writes
  * clamp(0.5 + o, 0, 1) pixel-shuffled as float.  In FP32 precision (and for the hyper-synthesis
  * layers S1 S2 S3) tensors are float with Cin_s = Cin rounded up to 16; otherwise they are bf16 with
- * Cin_s rounded up to 64 and the layer runs on the tensor cores (stride 2 needs even H and W).  The tensor-core weights of the
+ * Cin_s rounded up to 64 (32 for a layer with at most 32 input channels, i.e. the first layer for
+ * N <= 10) and the layer runs on the tensor cores (stride 2 needs even H and W).  In FP8 precision the
+ * tensors are E4M3 codes of the calibrated scales (Cin_s rounded up to 64).  The tensor-core weights of the
  * pixel-shuffle decoder layers (D0, U1, U2) are stored for mode 1 only: another mode on them returns
  * UFVC_ERR_ARG. */
 ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, int W, int stride, int act, int mode,

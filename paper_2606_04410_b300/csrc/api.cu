@@ -212,8 +212,11 @@ static void free_plan(Plan* p) {
 static void init_plan_shape(const ufvc_ctx* ctx, Plan* p, int W, int H) {
     p->W = W; p->H = H;
     p->Hp = ceil_div(H, 16) * 16; p->Wp = ceil_div(W, 16) * 16;
-    // packed input channels: 16-multiple for the SIMT kernel, 64-multiple (one 128-byte K chunk) for tcgen05
-    p->C0p = ctx->cfg.precision == UFVC_FP32 ? ceil_div(3 * ctx->N, 16) * 16 : ceil_div(3 * ctx->N, 64) * 64;
+    // packed input channels: 16-multiple for the SIMT kernel; for tcgen05 one 64-channel stage, or in BF16
+    // one 32-channel stage when the 3N frame channels fit (N <= 10)
+    p->C0p = ctx->cfg.precision == UFVC_FP32                              ? ceil_div(3 * ctx->N, 16) * 16
+             : (ctx->cfg.precision == UFVC_BF16 && 3 * ctx->N <= 32) ? 32
+                                                                     : ceil_div(3 * ctx->N, 64) * 64;
     p->h1 = conv_out(p->Hp, 3, 2); p->w1 = conv_out(p->Wp, 3, 2);
     p->h2 = conv_out(p->h1, 3, 2); p->w2 = conv_out(p->w1, 3, 2);
     p->h3 = conv_out(p->h2, 3, 2); p->w3 = conv_out(p->w2, 3, 2);
@@ -402,7 +405,8 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
     CK(cudaMemcpy(L.b, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
     if (tc && ctx->cfg.precision != UFVC_FP32) {
         // K-major bf16 copy for tcgen05: [g][cout_pad][tap][cin_tc], zero rows / columns in the padding
-        L.cin_tc = ceil_div(ci, 64) * 64;
+        // 64-channel stages; in BF16 a layer with at most 32 input channels (the first) uses 32-channel ones
+        L.cin_tc = (ci <= 32 && ctx->cfg.precision == UFVC_BF16) ? 32 : ceil_div(ci, 64) * 64;
         L.cout_pad = co >= 64 ? co : 16;
         L.ps_major = pixel_shuffle && co % 128 == 0;  // runs of 32 channels per sub-pixel in every N tile
         const int cq = co / 4;

@@ -253,14 +253,20 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 // (64-column slabs of 128 rows x 128 B, the layout a TMA box of 64 channels x TW x TH has) and one thread
 // per slab group stores it with TMA tiled stores, which clip at the tensor edges.  Otherwise every
 // epilogue thread stores its own pixel's columns.
-// F8: E4M3 operands (kind::f8f6f4, K = 32 per MMA) in rows of 64 bytes with the 64-byte swizzle, so a
-// pipeline stage is again 64 input channels; the accumulators are rescaled in the epilogue.
-template <int BN, int STAGES, bool STAGED, bool F8 = false>
+// OP selects the operand rows of a pipeline stage: OP_BF16 = 64 bf16 channels in 128-byte rows with the
+// 128-byte swizzle; OP_E4M3 = 64 E4M3 channels (kind::f8f6f4, K = 32 per MMA) in 64-byte rows with the
+// 64-byte swizzle, accumulators rescaled in the epilogue; OP_BF16_32 = 32 bf16 channels in 64-byte rows
+// (the first layer, whose 3N <= 30 input channels would fill only part of a 64-channel stage).
+enum { OP_BF16 = 0, OP_E4M3 = 1, OP_BF16_32 = 2 };
+
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
+    constexpr bool F8 = OP == OP_E4M3;
     static_assert(!(F8 && STAGED), "FP8 outputs use the per-thread epilogue");
-    constexpr int ROWB = F8 ? 64 : 128;  // bytes of one K row (64 channels) of a stage
+    constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
+    constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     constexpr int A_BYTES = 128 * ROWB;
     constexpr int B_BYTES = BN * ROWB;
     constexpr int C_BYTES = STAGED ? 128 * BN * 2 : 0;
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t ph = (it / STAGES) & 1;
                     if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) { ok = false; break; }
                     ptx::mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
-                    const int tap = ks / p.cin_chunks, c0 = (ks - tap * p.cin_chunks) * 64;
+                    const int tap = ks / p.cin_chunks, c0 = (ks - tap * p.cin_chunks) * CH;
                     const int ky = tap / p.k, kx = tap - ky * p.k;
                     if (p.stride == 1) {
                         ptx::tma_load_4d(sA + s * A_BYTES, &tmA, &full[s], c0, w0 + kx - p.pad, h0 + ky - p.pad, ag);
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ptx::tma_load_5d(sA + s * A_BYTES, &tmA, &full[s], c0, wp, w0 + ((tx - wp) >> 1), hp,
                                          h0 + ((ty - hp) >> 1));
                     }
-                    ptx::tma_load_3d(sB + s * B_BYTES, &tmB, &full[s], ks * 64, nt * BN, g);
+                    ptx::tma_load_3d(sB + s * B_BYTES, &tmB, &full[s], ks * CH, nt * BN, g);
                     used[s] = true;
                     last_par[s] = ph;
                 }
@@ -378,6 +384,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
                             ptx::mma_f8(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
                                         (ks | kk) != 0);
+                    } else if constexpr (OP == OP_BF16_32) {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk)  // 2 x K=16 BF16 per 64-byte row
+                            ptx::mma_f16(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
+                                         (ks | kk) != 0);
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
@@ -1021,16 +1032,16 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED, bool F8 = false>
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
-    constexpr int ROWB = F8 ? 64 : 128;
+    constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
     constexpr int kSmem = STAGES * (128 * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, F8>,
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
@@ -1042,7 +1053,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_kernel<BN, STAGES, STAGED, F8><<<grid, kThreads, smem, s>>>(a, b, c, args);
+    conv_tc_kernel<BN, STAGES, STAGED, OP><<<grid, kThreads, smem, s>>>(a, b, c, args);
     return cudaGetLastError();
 }
 
@@ -1151,7 +1162,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     if (d.wsc && (d.mode == OUT_PS_FINAL_U8 || d.mode == OUT_PS_FINAL_F32) && d.k == 3 && d.stride == 1 &&
         d.Cin == 64 && d.Cout == 12)
         return launch_conv_final(d, s);
-    if (d.Cin % 64 != 0 || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
+    const bool c32 = d.Cin == 32 && d.w8 == nullptr;  // one 32-channel stage per tap (bf16)
+    if ((d.Cin % 64 != 0 && !c32) || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
         return cudaErrorInvalidValue;
     const int pad = d.k / 2;
     const int Ho = (d.H + 2 * pad - d.k) / d.stride + 1, Wo = (d.W + 2 * pad - d.k) / d.stride + 1;
@@ -1162,7 +1174,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // three input rows per 128-pixel strip (wider layers keep one N tile on the streaming kernel, which
     // re-reads the input less than several N tiles would)
     const bool f8 = d.w8 != nullptr;  // E4M3 operands: streaming kernel, per-thread epilogue
-    const bool halo = !f8 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
+    const bool halo = !f8 && !c32 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
     if (halo) BN = d.cout_pad;
     // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
     // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
@@ -1184,7 +1196,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.n_tiles = d.cout_pad / BN;
     a.groups = d.groups;
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
-    a.cin_chunks = d.Cin / 64;
+    a.cin_chunks = c32 ? 1 : d.Cin / 64;
     a.ksteps = d.k * d.k * a.cin_chunks;
     a.k = d.k; a.pad = pad; a.stride = d.stride; a.a_grouped = d.in_gs != 0;
     a.bias = d.btc ? d.btc : d.b; a.b_gs = (int)d.b_gs; a.Cout = d.Cout;
@@ -1207,21 +1219,22 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     CUtensorMap ma, mb;
     const cuuint64_t esz = f8 ? 1 : 2;
     const CUtensorMapDataType dt = f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const CUtensorMapSwizzle swz = f8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    const CUtensorMapSwizzle swz = (f8 || c32) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+    const cuuint32_t boxc = c32 ? 32 : 64;  // channels of a stage
     bool ok;
     if (d.stride == 1) {
         const int G = a.a_grouped ? d.groups : 1;
         cuuint64_t dims[4] = {(cuuint64_t)d.Cin, (cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)G};
         cuuint64_t str[3] = {d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz, (cuuint64_t)d.H * d.W * d.Cin * esz};
         if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
-        cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+        cuuint32_t box[4] = {boxc, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
         if (halo) { box[1] = 130; box[2] = 1; }
         ok = encode_map(&ma, d.in, 4, dims, str, box, dt, swz);
     } else {
         cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
         cuuint64_t str[4] = {d.Cin * esz, 2 * d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz,
                              2ull * d.W * d.Cin * esz};
-        cuuint32_t box[5] = {64, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
+        cuuint32_t box[5] = {boxc, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
         ok = encode_map(&ma, d.in, 5, dims, str, box, dt, swz);
     }
     if (!ok) return cudaErrorInvalidValue;
@@ -1229,18 +1242,18 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         const cuuint64_t K = (cuuint64_t)d.k * d.k * d.Cin;
         cuuint64_t dims[3] = {K, (cuuint64_t)d.cout_pad, (cuuint64_t)d.groups};
         cuuint64_t str[2] = {K * esz, K * d.cout_pad * esz};
-        cuuint32_t box[3] = {64, (cuuint32_t)BN, 1};
+        cuuint32_t box[3] = {boxc, (cuuint32_t)BN, 1};
         if (!encode_map(&mb, f8 ? d.w8 : d.wtc, 3, dims, str, box, dt, swz)) return cudaErrorInvalidValue;
     }
     CUtensorMap mc = mb;  // unused by the unstaged kernels
     if (f8) {
         if (d.mode != OUT_NHWC && !(d.mode == OUT_PS && d.ps_major)) return cudaErrorInvalidValue;
         switch (BN) {
-            case 16: return launch_bn<16, 8, false, true>(ma, mb, mc, a, s);
-            case 64: return launch_bn<64, 8, false, true>(ma, mb, mc, a, s);
-            case 128: return launch_bn<128, 8, false, true>(ma, mb, mc, a, s);
-            case 192: return launch_bn<192, 8, false, true>(ma, mb, mc, a, s);
-            default: return launch_bn<256, 7, false, true>(ma, mb, mc, a, s);
+            case 16: return launch_bn<16, 8, false, OP_E4M3>(ma, mb, mc, a, s);
+            case 64: return launch_bn<64, 8, false, OP_E4M3>(ma, mb, mc, a, s);
+            case 128: return launch_bn<128, 8, false, OP_E4M3>(ma, mb, mc, a, s);
+            case 192: return launch_bn<192, 8, false, OP_E4M3>(ma, mb, mc, a, s);
+            default: return launch_bn<256, 7, false, OP_E4M3>(ma, mb, mc, a, s);
         }
     }
     if (halo) {
@@ -1276,6 +1289,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             okc = encode_map(&mc, d.out, 4, dims, str, box);
         }
         if (!okc) return cudaErrorInvalidValue;
+        if (c32) return BN == 64 ? launch_bn<64, 12, true, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
         switch (BN) {
             case 64: return launch_bn<64, 8, true>(ma, mb, mc, a, s);
             case 128: return launch_bn<128, 5, true>(ma, mb, mc, a, s);
@@ -1283,6 +1297,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);
         }
     }
+    if (c32) return BN == 64 ? launch_bn<64, 12, false, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
     switch (BN) {
         case 16: return launch_bn<16, 8, false>(ma, mb, mc, a, s);
         case 64: return launch_bn<64, 8, false>(ma, mb, mc, a, s);

@@ -52,16 +52,18 @@ __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// bf16 variant for the tensor-core path (rows of 64 channels, 3N <= 48 of them real).  A block packs a
-// segment of 128 pixels of one row, one thread per pixel: the thread reads its 3N bytes (a warp reads
-// 96 consecutive bytes of each frame row), converts them, and writes its 128-byte row into a
-// shared-memory tile (16-byte chunk k of row p at chunk k ^ (p & 7): no bank conflicts); the block then
-// copies the 16 KB tile to global memory with consecutive threads writing consecutive 16-byte chunks.
+// bf16 variant for the tensor-core path (rows of CP = 32 or 64 channels, 3N <= CP of them real).  A block
+// packs a segment of 128 pixels of one row, one thread per pixel: the thread reads its 3N bytes (a warp
+// reads 96 consecutive bytes of each frame row), converts them, and writes its row into a shared-memory
+// tile (16-byte chunk k of row p at chunk k ^ (p % chunks): no bank conflicts); the block then copies the
+// tile to global memory with consecutive threads writing consecutive 16-byte chunks.
 constexpr int kPackPix = 128;
 
+template <int CP>
 __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                              int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
-    __shared__ uint4 tile[kPackPix * 8];
+    constexpr int KC = CP / 8;  // 16-byte chunks per pixel row
+    __shared__ uint4 tile[kPackPix * KC];
     __shared__ uint16_t lut[256];  // bf16 bits of v / 255 (a division per entry, not per pixel)
     for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 255.0f));
     __syncthreads();
@@ -91,17 +93,17 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
             }
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < KC; ++k) {
             const uint4 c = k < 6 ? make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3])
                                   : make_uint4(0u, 0u, 0u, 0u);
-            tile[p * 8 + (k ^ (p & 7))] = c;
+            tile[p * KC + (k ^ (p & (KC - 1)))] = c;
         }
         __syncthreads();
-        uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w0) * 64);
+        uint4* dst = reinterpret_cast<uint4*>(x + ((size_t)h * Wp + w0) * CP);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int idx = p + kPackPix * i, pr = idx >> 3, k = idx & 7;
-            if (w0 + pr < Wp) dst[idx] = tile[pr * 8 + (k ^ (pr & 7))];
+        for (int i = 0; i < KC; ++i) {
+            const int idx = p + kPackPix * i, pr = idx / KC, k = idx % KC;
+            if (w0 + pr < Wp) dst[idx] = tile[pr * KC + (k ^ (pr & (KC - 1)))];
         }
         __syncthreads();
     }
@@ -109,9 +111,11 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
 
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s) {
-    (void)Cp;  // always 64 on this path (3N <= 48 < 64, N <= 16)
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
-    pack_bf16_kernel<<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+    if (Cp == 32)  // 3N <= 32
+        pack_bf16_kernel<32><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+    else
+        pack_bf16_kernel<64><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
 }
 
 // E4M3 variant: the same segment scheme with 64-byte pixel rows; x = v / 255 is stored as the E4M3 code

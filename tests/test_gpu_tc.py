@@ -57,7 +57,8 @@ def ref_layer(blob, arch, N, layer, x_bf, stride, act, mode, out_h, out_w):
 
 
 LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
-    (1, 2, 0, 64, 96, 2, 1, 0, 64),      # A1: 6 -> 64, stride 2, GELU (input channels padded to 64)
+    (1, 2, 0, 64, 96, 2, 1, 0, 32),      # A1: 6 -> 64, stride 2, GELU (one 32-channel stage per tap)
+    (1, 2, 0, 38, 50, 2, 1, 0, 32),      # A1, ragged output tiles (19 x 25)
     (1, 2, 1, 34, 50, 2, 1, 0, 64),      # A2: 64 -> 128 stride 2
     (1, 2, 3, 20, 30, 1, 1, 0, 192),     # Xa: 192 -> 192, 3x3
     (1, 2, 4, 17, 41, 1, 0, 0, 192),     # Xb: 1x1
