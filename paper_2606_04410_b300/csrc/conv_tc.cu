@@ -29,7 +29,12 @@ constexpr long long kSpinLimit = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kEpiWarps = 16;  // four per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kBiasMax = 4096;                       // biases staged in shared memory (16 KB)
-constexpr int kSmemExtra = 1024 + 256 + 16 + 4 * kBiasMax;  // alignment slack, barriers, bias table
+constexpr int kSmemExtra = 1024 + 512 + 16 + 4 * kBiasMax;  // alignment slack, barriers, bias table
+
+// Epilogue groups of the streaming kernel: EG groups of 16 / EG epilogue warps drain EG different tiles
+// at once (each tile's 128 accumulator rows by the group's 4 / EG warps per TMEM lane quarter), so the
+// per-tile latency of narrow tiles (staging barrier, TMA store) overlaps; 2 EG TMEM accumulators.
+__host__ __device__ constexpr int epi_groups(int BN) { return BN >= 192 ? 1 : BN == 128 ? 2 : 4; }
 
 
 
@@ -269,13 +274,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     constexpr int A_BYTES = 128 * ROWB;
     constexpr int B_BYTES = BN * ROWB;
-    constexpr int C_BYTES = STAGED ? 128 * BN * 2 : 0;
-    constexpr uint32_t TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
-    // each of the four epilogue warps of a lane quarter drains a quarter of the BN columns
-    constexpr int PER = BN / 4 < 16 ? 16 : BN / 4;
+    constexpr int EG = epi_groups(BN);  // epilogue groups (tiles drained concurrently)
+    constexpr int WPQ = 4 / EG;         // warps per TMEM lane quarter in a group
+    constexpr int NACC = 2 * EG;        // TMEM accumulators
+    constexpr int C_BYTES = STAGED ? 128 * BN * 2 * EG : 0;
+    constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : (NACC * BN <= 128) ? 128
+                                   : (NACC * BN <= 256) ? 256 : 512;
+    static_assert(NACC * BN <= 512, "TMEM columns");
+    // each of the WPQ warps of a lane quarter in a group drains PER of the BN columns
+    constexpr int PER = BN / WPQ < 16 ? 16 : BN / WPQ;
     constexpr int CHUNK = PER % 32 == 0 ? 32 : 16;  // accumulator columns per tcgen05.ld round
-    // slab groups of the staged epilogue: GQ column quarters that share 64-column slabs
-    constexpr int GQ = (PER % 64 == 0) ? 1 : (64 % PER == 0 ? 64 / PER : 4);
+    // slab groups of the staged epilogue: GQ column parts of a group that share 64-column slabs
+    constexpr int GQ = (PER % 64 == 0) ? 1 : (64 % PER == 0 ? 64 / PER : WPQ);
+    constexpr int SG = WPQ / GQ;  // slab groups per epilogue group
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -284,8 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(sC + C_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* tfull = empty + STAGES;
-    uint64_t* tempty = tfull + 2;
-    uint64_t* drain = tempty + 2;
+    uint64_t* tempty = tfull + NACC;
+    uint64_t* drain = tempty + NACC;
     uint64_t* cwritten = drain + 1;   // per slab group: all its threads wrote the staging tile
     uint64_t* cfree = cwritten + 4;   // per slab group: its previous TMA stores have read the staging tile
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 4);
@@ -299,9 +310,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < NACC; ++a) {
             ptx::mbar_init(&tfull[a], 1);
-            ptx::mbar_init(&tempty[a], 32 * kEpiWarps);
+            ptx::mbar_init(&tempty[a], 128 * WPQ);
         }
         ptx::mbar_init(drain, 1);
         for (int gq = 0; gq < 4; ++gq) {
@@ -369,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int it = 0, tl = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x, ++tl) {
-                const int acc = tl & 1, use = tl >> 1;
+                const int acc = tl % NACC, use = tl / NACC;
                 if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem_base + acc * BN;
@@ -406,14 +417,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue warps
-        const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int colq = (warp - 2) >> 2;       // which quarter of the BN columns
+        const int q = warp & 3;                   // TMEM lane quarter this warp may access
+        const int colq = (warp - 2) >> 2;         // 0..3: four warps (one per lane quarter) each
+        const int egrp = colq / WPQ, cpart = colq % WPQ;  // epilogue group, column part within it
         const int row = q * 32 + lane;
-        const int grp = colq / GQ;              // slab group (staged epilogue)
-        const bool elected = STAGED && warp == 2 + grp * GQ * 4 && lane == 0;
-        int tl = 0;
-        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++tl) {
-            const int acc = tl & 1, use = tl >> 1;
+        const int grp = egrp * SG + cpart / GQ;   // slab group (staged epilogue)
+        const int lead = 2 + 4 * (egrp * WPQ + (cpart / GQ) * GQ);  // first warp of the slab group
+        const bool elected = STAGED && warp == lead && lane == 0;
+        uint8_t* sCg = sC + egrp * (BN / 64) * (128 * 128);      // this group's staging slabs
+        int tl = egrp, k = 0;
+        for (int t = blockIdx.x + egrp * gridDim.x; t < p.total_tiles; t += EG * gridDim.x, tl += EG, ++k) {
+            const int acc = tl % NACC, use = tl / NACC;
             if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
             const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
@@ -421,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
             const bool valid = oh < p.Ho && ow < p.Wo;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
-            const int c_begin = colq * PER;
+            const int c_begin = cpart * PER;
             bool ok = true;
 #pragma unroll 1
             for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
@@ -429,17 +443,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
                 if constexpr (STAGED) {
                     if (valid) finish_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
-                    if (c == c_begin && tl > 0) {
-                        // the previous tile's TMA stores must have read the staging tile
+                    if (c == c_begin && k > 0) {
+                        // the group's previous TMA stores must have read its staging slabs
                         if (elected) {
                             ptx::bulk_wait_read0();
                             ptx::mbar_arrive(&cfree[grp]);
                         }
-                        ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (tl - 1) & 1, abort_flag, p.err));
+                        ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err));
                         if (!ok) break;  // warp-uniform: the next tcgen05.ld needs the whole warp
                     }
                     // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
-                    const uint32_t base = ptx::smem_u32(sC) + (c >> 6) * (128 * 128) + row * 128;
+                    const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * (128 * 128) + row * 128;
 #pragma unroll
                     for (int i = 0; i < CHUNK / 8; ++i) {
                         const int j = ((c & 63) >> 3) + i;
@@ -457,16 +471,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             if constexpr (STAGED) {
                 ptx::fence_proxy_async();  // this thread's staging writes -> visible to the TMA (async proxy)
                 ptx::mbar_arrive(&cwritten[grp]);
-                if (warp == 2 + grp * GQ * 4) {  // the elected thread's warp (warp-uniform)
+                if (warp == lead) {  // the elected thread's warp (warp-uniform)
                     bool w_ok = true;
-                    if (lane == 0) w_ok = wait_bar(&cwritten[grp], tl & 1, abort_flag, p.err);
+                    if (lane == 0) w_ok = wait_bar(&cwritten[grp], k & 1, abort_flag, p.err);
                     if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
                 }
                 if (elected) {
-                    const int lo = grp * GQ * PER, hi = (grp + 1) * GQ * PER < BN ? (grp + 1) * GQ * PER : BN;
+                    const int lo = (cpart / GQ) * GQ * PER;
+                    const int hi = lo + GQ * PER < BN ? lo + GQ * PER : BN;
                     for (int sl = lo >> 6; sl < (hi + 63) >> 6; ++sl) {
                         const int col0 = nt * BN + sl * 64;
-                        const uint8_t* src = sC + sl * (128 * 128);
+                        const uint8_t* src = sCg + sl * (128 * 128);
                         if (p.c_rank == 4) {
                             ptx::tma_store_4d(&tmC, src, col0, w0, h0, g);
                         } else {
@@ -1036,7 +1051,7 @@ template <int BN, int STAGES, bool STAGED, int OP = OP_BF16>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
-    constexpr int kSmem = STAGES * (128 * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 : 0) + kSmemExtra;
+    constexpr int kSmem = STAGES * (128 * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 * epi_groups(BN) : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
     static int configured_smem = 0;
@@ -1291,8 +1306,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (!okc) return cudaErrorInvalidValue;
         if (c32) return BN == 64 ? launch_bn<64, 12, true, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
         switch (BN) {
-            case 64: return launch_bn<64, 8, true>(ma, mb, mc, a, s);
-            case 128: return launch_bn<128, 5, true>(ma, mb, mc, a, s);
+            case 64: return launch_bn<64, 6, true>(ma, mb, mc, a, s);
+            case 128: return launch_bn<128, 4, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
             default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);
         }
