@@ -347,7 +347,7 @@ __device__ __forceinline__ uint32_t ld_early_u16(const uint16_t* p) {
     return (uint32_t)v;
 }
 constexpr int kTabBytes = kBins * kNsym * 4;       // 130816, a multiple of 16
-constexpr int kCoarseBytes = kBins * kCoarse * 2;  // 65536
+constexpr int kCoarseBytes = kBins * kCoarse * 2 + kBins * 4;  // 65792: bucket owners, then end-run lengths
 constexpr int kPF = 16;                            // per-lane prefetch depth (symbols / table indices)
 constexpr long long kLoadSpin = 4000000000LL;      // ~2 s bounded wait for the table copy
 
@@ -368,9 +368,11 @@ __device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __res
             ptx::bulk_load(reinterpret_cast<uint8_t*>(tab) + off, reinterpret_cast<const uint8_t*>(tables) + off, n, bar);
         }
         if (coarse)
-            for (int off = 0; off < kCoarseBytes; off += 32768)
+            for (int off = 0; off < kCoarseBytes; off += 32768) {
+                const int n = kCoarseBytes - off < 32768 ? kCoarseBytes - off : 32768;
                 ptx::bulk_load(reinterpret_cast<uint8_t*>(coarse) + off,
-                               reinterpret_cast<const uint8_t*>(coarse_g) + off, 32768, bar);
+                               reinterpret_cast<const uint8_t*>(coarse_g) + off, n, bar);
+            }
     }
     const long long t0 = clock64();
     while (!ptx::mbar_try_wait(bar, 0)) {
@@ -389,7 +391,9 @@ __device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __res
 
 // rANS encode: one thread per lane, lanes of up to two sections in one launch.  Each lane runs its
 // elements backwards (last first) and writes its words backwards into its scratch row, so that the
-// row's tail [cap_lane - words, cap_lane) is the lane stream in decoding order.
+// row's tail [cap_lane - words, cap_lane) is the lane stream in decoding order.  The step has no branch:
+// the renormalisation word is stored under a predicate, and out-of-range inputs are clamped and
+// reported once per lane.
 __global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const RansSecPair P,
                                                                    const uint32_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum
@@ -401,51 +405,68 @@ __global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const Rans
     if (si >= P.nsec) return;
     const RansSection& S = P.s[si];
     if (lane >= S.K) return;
-    const size_t n = S.n, K = (size_t)S.K;
-    const long long cnt = (size_t)lane < n ? (long long)((n - lane + K - 1) / K) : 0;
+    const size_t n = S.n;
+    const int K = S.K, per = S.idx_period;
+    const int cnt = (size_t)lane < n ? (int)((n - lane + K - 1) / K) : 0;
     uint16_t* row = S.scratch + (size_t)lane * S.cap_lane;
     int wp = S.cap_lane;
-    uint32_t x = kRansL;
+    uint32_t x = kRansL, bad = 0;
+    const int16_t* sym = S.sym + lane;
+    const uint8_t* idx = S.idx + lane;
     // The (table, symbol) pairs of the next kPF elements are fetched while the current kPF are coded,
     // so the serial state chain does not wait on memory.
     int tc[kPF], vc[kPF], tn[kPF], vn[kPF];
-    auto fetch = [&](long long mtop, int* td, int* vd) {
+    auto fetch = [&](int mtop, int* td, int* vd) {
+        if (per) {
 #pragma unroll
-        for (int u = 0; u < kPF; ++u) {
-            const long long m = mtop - u;
-            td[u] = 0;
-            vd[u] = 0;
-            if (m >= 0) {
-                const size_t i = (size_t)lane + (size_t)m * K;
-                td[u] = ld_early_u8(S.idx + (S.idx_period ? i % S.idx_period : i));
-                vd[u] = ld_early_s16(S.sym + i);
+            for (int u = 0; u < kPF; ++u) {
+                const int m = mtop - u;
+                td[u] = 0;
+                vd[u] = 0;
+                if (m >= 0) {
+                    td[u] = ld_early_u8(S.idx + ((size_t)lane + (size_t)m * K) % (size_t)per);
+                    vd[u] = ld_early_s16(sym + (size_t)m * K);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) {
+                const int m = mtop - u;
+                td[u] = 0;
+                vd[u] = 0;
+                if (m >= 0) {
+                    td[u] = ld_early_u8(idx + (size_t)m * K);
+                    vd[u] = ld_early_s16(sym + (size_t)m * K);
+                }
             }
         }
     };
+    auto step = [&](int t, int v) {
+        v += kRmax;
+        const bool ok = (uint32_t)t < (uint32_t)kBins && (uint32_t)v < (uint32_t)kNsym;
+        bad |= !ok;
+        const uint32_t e = tab[ok ? t * kNsym + v : kRmax];
+        const uint32_t f = e >> 16, c = e & 0xFFFFu;
+        const bool o = x >= (f << 16);  // f << 16 < 2^32 as f <= 65026
+        if (o) row[wp - 1] = (uint16_t)(x & 0xFFFFu);
+        wp -= o ? 1 : 0;
+        x = o ? x >> 16 : x;
+        const uint32_t q = x / f;
+        x = (q << 16) + (x - q * f) + c;
+    };
     fetch(cnt - 1, tc, vc);
-    for (long long mtop = cnt - 1; mtop >= 0; mtop -= kPF) {
+    int mtop = cnt - 1;
+    for (; mtop >= kPF - 1; mtop -= kPF) {  // full blocks of kPF elements
         fetch(mtop - kPF, tn, vn);
 #pragma unroll
-        for (int u = 0; u < kPF; ++u) {
-            if (mtop - u < 0) break;
-            int t = tc[u], v = vc[u];
-            if (t >= kBins || v < -kRmax || v > kRmax) {  // caller error: never index outside the tables
-                set_status(S.status, UFVC_ERR_ARG);
-                t = 0;
-                v = 0;
-            }
-            const uint32_t e = tab[t * kNsym + (v + kRmax)];
-            const uint32_t f = e >> 16, c = e & 0xFFFFu;
-            if (x >= (f << 16)) {  // f << 16 < 2^32 as f <= 65026
-                row[--wp] = (uint16_t)(x & 0xFFFFu);
-                x >>= 16;
-            }
-            const uint32_t q = x / f;
-            x = (q << 16) + (x - q * f) + c;
-        }
+        for (int u = 0; u < kPF; ++u) step(tc[u], vc[u]);
 #pragma unroll
         for (int u = 0; u < kPF; ++u) { tc[u] = tn[u]; vc[u] = vn[u]; }
     }
+#pragma unroll
+    for (int u = 0; u < kPF; ++u)  // the remaining mtop + 1 < kPF elements
+        if (u <= mtop) step(tc[u], vc[u]);
+    if (bad) set_status(S.status, UFVC_ERR_ARG);
     row[--wp] = (uint16_t)(x & 0xFFFFu);
     row[--wp] = (uint16_t)(x >> 16);
     S.counts[lane] = (uint32_t)(S.cap_lane - wp);
@@ -605,88 +626,182 @@ void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const u
     rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, expect_end_dev, status);
 }
 
+// rANS decode.  Each thread runs LPT lanes (g, g + G, ... with G = ceil(K / LPT)), their steps interleaved
+// so the serial state chains of different lanes overlap in one instruction stream.  PER: the table index
+// of element i is idx[i mod idx_period] (the hyper-latent's per-channel tables) instead of idx[i].
+// The common path of a step has no branch: the slot's bucket gives the candidate symbols, one predicated
+// bisection step settles buckets of one or two candidates, and only wider buckets (table tails) enter a
+// loop.  The renormalisation word is read every step at the lane's read position (a lane stream is read
+// sequentially, so it stays in L1) and selected when the state drops below L.
+template <int LPT, bool PER>
 __global__ void __launch_bounds__(kRansThreadsDec) rans_decode_kernel(const RansDecodeJob J,
                                                                    const uint32_t* __restrict__ tables,
                                                                    const uint16_t* __restrict__ coarse_g, int* status) {
     extern __shared__ __align__(16) uint32_t tab[];                      // [64][511] (freq << 16) | cum
-    uint16_t* coarse = reinterpret_cast<uint16_t*>(tab + kBins * kNsym);  // [64][kCoarse]
+    uint16_t* coarse = reinterpret_cast<uint16_t*>(tab + kBins * kNsym);  // [64][kCoarse], then [64] end runs
+    const uint32_t* runs = reinterpret_cast<const uint32_t*>(coarse + kBins * kCoarse);  // A | B << 16
     __shared__ uint64_t bar;
     if (!load_tables(tab, tables, coarse, coarse_g, &bar, status)) return;
     if (*(volatile int*)status != 0) return;
-    const int lane = blockIdx.x * blockDim.x + threadIdx.x;
-    if (lane >= J.K) return;
-    const size_t n = J.n, K = (size_t)J.K;
-    const size_t cnt = (size_t)lane < n ? (n - lane + K - 1) / K : 0;
-    const uint16_t* wp = reinterpret_cast<const uint16_t*>(J.bits + J.lane_off[lane]);
-    const uint32_t words = J.lane_words[lane];
-    uint32_t x = ((uint32_t)wp[0] << 16) | wp[1];
-    uint32_t r = 2;
-    // the next two renormalisation words, fetched ahead of their use
-    uint32_t nw0 = r < words ? ld_early_u16(wp + r) : 0u;
-    uint32_t nw1 = r + 1 < words ? ld_early_u16(wp + r + 1) : 0u;
-    // table indices of the next kPF symbols are fetched while the current kPF are decoded
-    int tc[kPF], tn[kPF];
-    auto fetch = [&](size_t m0, int* td) {
+    const int K = J.K, G = (K + LPT - 1) / LPT;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const size_t n = J.n;
+    int cnt[LPT], lane[LPT];
+    bool live[LPT];
+    uint32_t x[LPT], r[LPT], words[LPT];
+    const uint16_t* wp[LPT];
+    const uint8_t* ip[LPT];
+    int16_t* sp[LPT];
+    int cmin = 1 << 30;
 #pragma unroll
-        for (int u = 0; u < kPF; ++u) {
-            const size_t m = m0 + u;
-            td[u] = 0;
-            if (m < cnt) {
-                const size_t i = (size_t)lane + m * K;
-                td[u] = ld_early_u8(J.idx + (J.idx_period ? i % J.idx_period : i));
+    for (int j = 0; j < LPT; ++j) {
+        lane[j] = g + j * G;
+        live[j] = lane[j] < K;
+        const int l = live[j] ? lane[j] : g;  // a thread's missing lane mirrors its first lane, with no symbols
+        cnt[j] = live[j] && (size_t)l < n ? (int)((n - l + K - 1) / K) : 0;
+        if (live[j]) cmin = cnt[j] < cmin ? cnt[j] : cmin;
+        wp[j] = reinterpret_cast<const uint16_t*>(J.bits + J.lane_off[l]);
+        words[j] = J.lane_words[l];  // >= 2 (checked by the parse)
+        x[j] = ((uint32_t)wp[j][0] << 16) | wp[j][1];
+        r[j] = 2;
+        ip[j] = J.idx + l;
+        sp[j] = J.sym + l;
+    }
+    // table indices of the next kPF symbols of every lane are fetched while the current kPF are decoded
+    int tc[LPT][kPF], tn[LPT][kPF];
+    auto fetch = [&](int m0, int (*td)[kPF]) {
+#pragma unroll
+        for (int j = 0; j < LPT; ++j)
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) {
+                const int m = m0 + u;
+                td[j][u] = 0;
+                if (m < cnt[j]) {
+                    if (PER)
+                        td[j][u] = ld_early_u8(J.idx + ((size_t)lane[j] + (size_t)m * K) % (size_t)J.idx_period);
+                    else
+                        td[j][u] = ld_early_u8(ip[j] + (size_t)m * K);
+                }
+            }
+    };
+    uint32_t bad = 0;
+    // one symbol of every lane j with act[j]
+    auto step = [&](const int* t_in, const bool* act) {
+        int s[LPT], hi[LPT];
+        uint32_t slot[LPT], w[LPT];
+        const uint32_t* T[LPT];
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            int t = t_in[j];
+            bad |= (uint32_t)t >= (uint32_t)kBins;
+            t = (uint32_t)t < (uint32_t)kBins ? t : 0;
+            T[j] = tab + t * kNsym;
+            w[j] = __ldg(wp[j] + (r[j] < words[j] ? r[j] : words[j] - 1));
+            slot[j] = x[j] & 0xFFFFu;
+            const int b = (int)(slot[j] >> kCoarseShift);
+            const uint16_t* C = coarse + t * kCoarse;
+            const uint32_t ab = runs[t];
+            const int A = (int)(ab & 0xFFFFu), B = (int)(ab >> 16), sl = (int)slot[j];
+            // symbol s with cum(s) <= slot < cum(s+1): in the unit-frequency end runs it is the slot itself
+            // (shifted on the right), elsewhere it lies in [owner of the bucket's first slot, owner of the
+            // next bucket's first slot], clipped to the middle [A, 510 - B]
+            const bool tail_l = sl < A, tail_r = sl >= (int)kProbM - B;
+            const int lo = max((int)C[b], A), up = min(b + 1 < kCoarse ? (int)C[b + 1] : kNsym - 1, kNsym - 1 - B);
+            s[j] = tail_l ? sl : tail_r ? sl - ((int)kProbM - kNsym) : lo;
+            hi[j] = tail_l || tail_r ? s[j] : up;
+        }
+        // the first bisection step is predicated (mid = s when s == hi)
+        bool more = false;
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            const int mid = (s[j] + hi[j] + 1) >> 1;
+            const bool le = (T[j][mid] & 0xFFFFu) <= slot[j];
+            const bool go = s[j] < hi[j];
+            s[j] = go && le ? mid : s[j];
+            hi[j] = go && !le ? mid - 1 : hi[j];
+            more |= s[j] < hi[j];
+        }
+        if (more) {
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) {
+                while (s[j] < hi[j]) {
+                    const int mid = (s[j] + hi[j] + 1) >> 1;
+                    if ((T[j][mid] & 0xFFFFu) <= slot[j]) s[j] = mid; else hi[j] = mid - 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            const uint32_t e = T[j][s[j]];
+            const uint32_t xn = (e >> 16) * (x[j] >> 16) + slot[j] - (e & 0xFFFFu);
+            const bool rn = xn < kRansL;
+            if (act[j]) {
+                x[j] = rn ? (xn << 16) | w[j] : xn;
+                r[j] += rn ? 1u : 0u;
+                *sp[j] = (int16_t)(s[j] - kRmax);
+                sp[j] += K;
             }
         }
     };
     fetch(0, tc);
-    for (size_t m0 = 0; m0 < cnt; m0 += kPF) {
+    int m0 = 0;
+    for (; m0 + kPF <= cmin; m0 += kPF) {  // full blocks: every live lane has all kPF symbols
         fetch(m0 + kPF, tn);
 #pragma unroll
         for (int u = 0; u < kPF; ++u) {
-            const size_t m = m0 + u;
-            if (m >= cnt) break;
-            int t = tc[u];
-            if (t >= kBins) {
-                set_status(status, UFVC_ERR_ARG);
-                t = 0;
-            }
-            const uint32_t* T = tab + t * kNsym;
-            const uint32_t slot = x & 0xFFFFu;
-            // symbol s with cum(s) <= slot < cum(s+1).  It lies between the owners of the first slots of
-            // the slot's 128-wide bucket and of the next bucket; a binary search over that range takes at
-            // most 7 steps (the tails of the tables, where every slot is a symbol, are the worst case).
-            const int b = slot >> kCoarseShift;
-            int s = coarse[t * kCoarse + b];
-            int hi = b + 1 < kCoarse ? coarse[t * kCoarse + b + 1] : kNsym - 1;
-            while (s < hi) {
-                const int mid = (s + hi + 1) >> 1;
-                if ((T[mid] & 0xFFFFu) <= slot) s = mid; else hi = mid - 1;
-            }
-            const uint32_t e = T[s];
-            x = (e >> 16) * (x >> 16) + slot - (e & 0xFFFFu);
-            if (x < kRansL) {
-                x = (x << 16) | nw0;
-                ++r;
-                nw0 = nw1;
-                nw1 = r + 1 < words ? ld_early_u16(wp + r + 1) : 0u;
-            }
-            J.sym[(size_t)lane + m * K] = (int16_t)(s - kRmax);
+            int tu[LPT];
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) tu[j] = tc[j][u];
+            step(tu, live);
         }
 #pragma unroll
-        for (int u = 0; u < kPF; ++u) tc[u] = tn[u];
+        for (int j = 0; j < LPT; ++j)
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) tc[j][u] = tn[j][u];
     }
-    if (x != kRansL || r != words) set_status(status, UFVC_ERR_CORRUPT);
+    // the tail: live lanes' counts differ by at most one, so at most kPF symbols per lane remain
+#pragma unroll
+    for (int u = 0; u < kPF; ++u) {
+        int tu[LPT];
+        bool act[LPT], any = false;
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            tu[j] = tc[j][u];
+            act[j] = m0 + u < cnt[j];
+            any |= act[j];
+        }
+        if (!any) break;
+        step(tu, act);
+    }
+    if (bad) set_status(status, UFVC_ERR_ARG);
+#pragma unroll
+    for (int j = 0; j < LPT; ++j)
+        if (live[j] && (x[j] != kRansL || r[j] != words[j])) set_status(status, UFVC_ERR_CORRUPT);
 }
+
+#ifndef UFVC_RANS_DEC_LPT
+#define UFVC_RANS_DEC_LPT 1
+#endif
+constexpr int kRansDecLPT = UFVC_RANS_DEC_LPT;  // lanes per decoding thread
 
 void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
                         cudaStream_t s) {
     const int smem = kTabBytes + kCoarseBytes;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(rans_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(rans_decode_kernel<kRansDecLPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(rans_decode_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    rans_decode_kernel<<<(j.K + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(j, packed_tables, coarse,
-                                                                                           status);
+    if (j.idx_period) {
+        rans_decode_kernel<1, true><<<(j.K + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(
+            j, packed_tables, coarse, status);
+    } else {
+        const int G = (j.K + kRansDecLPT - 1) / kRansDecLPT;
+        rans_decode_kernel<kRansDecLPT, false><<<(G + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(
+            j, packed_tables, coarse, status);
+    }
 }
 
 // y^ = r^ q + mu (explicitly rounded ops), to float and / or bf16; q from the parsed rate

@@ -62,8 +62,10 @@ void build_host_tables(HostTables& t) {
         for (int i = 0; i < kNsym; ++i) c[i + 1] = c[i] + f[i];
         for (int i = 0; i < kNsym; ++i) t.packed[k * kNsym + i] = (f[i] << 16) | c[i];
     }
-    // decoder index: for bucket b, the symbol whose interval [cum_s, cum_s + f_s) holds slot b << shift
-    t.coarse.assign(kBins * kCoarse, 0);
+    // decoder index: for bucket b, the symbol whose interval [cum_s, cum_s + f_s) holds slot b << shift;
+    // then per table the lengths of its unit-frequency end runs (A: symbols 0..A-1, B: symbols 511-B..510
+    // have frequency 1, so there slot -> symbol is slot, resp. slot - 65025)
+    t.coarse.assign(kBins * kCoarse + 2 * kBins, 0);
     for (int k = 0; k < kBins; ++k) {
         const uint32_t* c = &t.cum[k * (kNsym + 1)];
         int s = 0;
@@ -72,6 +74,12 @@ void build_host_tables(HostTables& t) {
             while (c[s + 1] <= slot) ++s;
             t.coarse[k * kCoarse + b] = (uint16_t)s;
         }
+        const uint32_t* f = &t.packed[k * kNsym];
+        int a = 0, z = 0;
+        while (a < kNsym && (f[a] >> 16) == 1) ++a;
+        while (z < kNsym && (f[kNsym - 1 - z] >> 16) == 1) ++z;
+        t.coarse[kBins * kCoarse + 2 * k] = (uint16_t)a;
+        t.coarse[kBins * kCoarse + 2 * k + 1] = (uint16_t)z;
     }
 }
 

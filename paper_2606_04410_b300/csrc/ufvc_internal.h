@@ -33,7 +33,7 @@ struct HostTables {
     std::vector<float> qstep;     // [64]  q(qp) as float
     std::vector<float> qinv;      // [64]  1/q(qp) as float
     std::vector<double> log_thr;  // [63]  t_k in FP64 (z^ RMS index)
-    std::vector<uint16_t> coarse; // [64][kCoarse]  symbol owning slot b << kCoarseShift
+    std::vector<uint16_t> coarse; // [64][kCoarse] symbol owning slot b << kCoarseShift, then [64][2] end-run lengths
 };
 void build_host_tables(HostTables& t);
 double qstep_fp64(int qp);
