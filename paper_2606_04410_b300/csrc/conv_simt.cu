@@ -49,6 +49,33 @@ __device__ __forceinline__ void store_out(const ConvDesc& d, int g, int oh, int 
     }
 }
 
+// Output channels co..co+3 (co % 4 == 0) of one pixel: one 16-byte access when d.vec4 (NHWC output,
+// channel counts, split and group strides multiples of 4, 16-byte aligned tensors), else four scalar
+// stores.
+__device__ __forceinline__ void store_out4(const ConvDesc& d, int g, int oh, int ow, int co, float4 v) {
+    if (d.vec4) {
+        if (oh >= d.out_h || ow >= d.out_w) return;
+        const size_t pix = (size_t)oh * d.out_w + ow;
+        if (d.split && co >= d.split) {
+            const int c2 = d.Cout - d.split;
+            *reinterpret_cast<float4*>(d.out2 + (size_t)g * d.out_gs + pix * c2 + (co - d.split)) = v;
+            return;
+        }
+        const int C = d.split ? d.split : d.Cout;
+        const size_t o = (size_t)g * d.out_gs + pix * C + co;
+        if (d.res) {
+            const float4 r = *reinterpret_cast<const float4*>((const float*)d.res + (size_t)g * d.res_gs + pix * C + co);
+            v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
+        }
+        *reinterpret_cast<float4*>((float*)d.out + o) = v;
+        return;
+    }
+    store_out(d, g, oh, ow, co, v.x);
+    store_out(d, g, oh, ow, co + 1, v.y);
+    store_out(d, g, oh, ow, co + 2, v.z);
+    store_out(d, g, oh, ow, co + 3, v.w);
+}
+
 template <int BM, int BN>
 __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho, int Wo) {
     constexpr int BK = 16;
@@ -320,7 +347,7 @@ __global__ void __launch_bounds__(256) conv_simt64_kernel(const ConvDesc d, int 
 // K staged 16 input channels per step, global loads two steps ahead, shared tiles double-buffered;
 // split-K ranges and the PARTIAL workspace exactly as in conv_simt64_kernel.  Cout % 128 == 0.
 template <bool PARTIAL>
-__global__ void __launch_bounds__(128) conv_simt88_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
+__global__ void __launch_bounds__(128, 3) conv_simt88_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
     constexpr int BM = 64, BN = 128, BK = 16;
     __shared__ __align__(16) float As[2][BK][BM + 4];
     __shared__ __align__(16) float Bs[2][BK][BN];
@@ -428,12 +455,11 @@ __global__ void __launch_bounds__(128) conv_simt88_kernel(const ConvDesc d, int 
                     make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
             } else {
                 const int oh = m / Wo, ow = m - oh * Wo;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float v = acc[i][4 * h + j] + d.b[(size_t)g * d.b_gs + co0 + j];
-                    if (d.act) v = gelu_erf(v);
-                    store_out(d, g, oh, ow, co0 + j, v);
-                }
+                const float* b = d.b + (size_t)g * d.b_gs + co0;
+                float4 v = make_float4(acc[i][4 * h] + b[0], acc[i][4 * h + 1] + b[1], acc[i][4 * h + 2] + b[2],
+                                       acc[i][4 * h + 3] + b[3]);
+                if (d.act) { v.x = gelu_erf(v.x); v.y = gelu_erf(v.y); v.z = gelu_erf(v.z); v.w = gelu_erf(v.w); }
+                store_out4(d, g, oh, ow, co0, v);
             }
         }
     }
@@ -441,19 +467,26 @@ __global__ void __launch_bounds__(128) conv_simt88_kernel(const ConvDesc d, int 
 
 // out = bias + (((range 0) + range 1) + ...), then the layer's activation and output mapping
 __global__ void conv_simt_reduce_kernel(const ConvDesc d, int Ho, int Wo, int KS, const float* ws) {
-    const int M = Ho * Wo, Cout = d.Cout;
-    const size_t per_g = (size_t)M * Cout, total = per_g * d.groups;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int g = (int)(i / per_g);
-        const size_t r = i - (size_t)g * per_g;
-        const int m = (int)(r / Cout), co = (int)(r - (size_t)m * Cout);
-        const float* src = ws + (size_t)g * KS * per_g + r;
-        float v = src[0];
-        for (int ks = 1; ks < KS; ++ks) v += src[(size_t)ks * per_g];
-        v += d.b[(size_t)g * d.b_gs + co];
-        if (d.act) v = gelu_erf(v);
+    // four channels per thread (Cout % 4 == 0 for the split layers); 32-bit element indices per group
+    const int M = Ho * Wo, C4 = d.Cout >> 2;
+    const int per_g4 = M * C4;
+    const size_t per_g = (size_t)M * d.Cout;
+    const long long total4 = (long long)per_g4 * d.groups;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total4; i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i / per_g4);
+        const int r4 = (int)(i - (long long)g * per_g4);
+        const int m = r4 / C4, co = (r4 - m * C4) * 4;
+        const float* src = ws + (size_t)g * KS * per_g + (size_t)r4 * 4;
+        float4 v = *reinterpret_cast<const float4*>(src);
+        for (int ks = 1; ks < KS; ++ks) {
+            const float4 u = *reinterpret_cast<const float4*>(src + (size_t)ks * per_g);
+            v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+        }
+        const float* b = d.b + (size_t)g * d.b_gs + co;
+        v.x += b[0]; v.y += b[1]; v.z += b[2]; v.w += b[3];
+        if (d.act) { v.x = gelu_erf(v.x); v.y = gelu_erf(v.y); v.z = gelu_erf(v.z); v.w = gelu_erf(v.w); }
         const int oh = m / Wo, ow = m - oh * Wo;
-        store_out(d, g, oh, ow, co, v);
+        store_out4(d, g, oh, ow, co, v);
     }
 }
 
@@ -470,14 +503,15 @@ static int simt_plan(const ConvDesc& d, int* KS) {
     const int nsteps16 = d.k * d.k * (d.Cin / 16);
     if (d.Cout % 128 == 0 && d.Cin % 16 == 0) {
         // small layers with 128-multiple widths (the hyper-synthesis): 64 x 128 tiles of 8 x 8 per
-        // thread, K split until three CTAs per SM
+        // thread, K split into as many ranges as one wave of three CTAs per SM holds
         const long long ctas = ((M + 63) / 64) * (d.Cout / 128) * d.groups;
-        long long ks = (3 * 148 + ctas - 1) / ctas;
-        if (ks > 9) ks = 9;
+        long long ks = 3 * 148 / ctas;
+        if (ks > 16) ks = 16;
         if (ks > nsteps16) ks = nsteps16;
         *KS = (int)(ks < 1 ? 1 : ks);
         return 3;
     }
+    if (d.Cout % 4) return 2;  // (KS = 1: the split-K reduction handles four channels per thread)
     // other small layers: 64 x 64 tiles, K split until two CTAs per SM
     const long long ctas64 = ((M + 63) / 64) * ((d.Cout + 63) / 64) * d.groups;
     const int nsteps = d.k * d.k * (d.Cin / (d.Cin % 32 == 0 ? 32 : 16));
@@ -497,7 +531,18 @@ size_t conv_simt_workspace(const ConvDesc& d) {
     return (size_t)KS * d.groups * Ho * Wo * d.Cout;
 }
 
-cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+static unsigned reduce_blocks(const ConvDesc& d, int M) {  // one thread per four output channels
+    const size_t total4 = (size_t)d.groups * M * (d.Cout / 4);
+    return (unsigned)((total4 + 255) / 256 < 4096 ? (total4 + 255) / 256 : 4096);
+}
+
+cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
+    ConvDesc d = d_in;
+    d.vec4 = d.mode == OUT_NHWC && d.Cout % 4 == 0 && d.split % 4 == 0 && d.out_gs % 4 == 0 && aligned16(d.out) &&
+             (!d.split || (aligned16(d.out2) && (d.Cout - d.split) % 4 == 0)) &&
+             (!d.res || (aligned16(d.res) && d.res_gs % 4 == 0)) && aligned16(d.b) && d.b_gs % 4 == 0;
     const int p = d.k / 2;
     const int Ho = (d.H + 2 * p - d.k) / d.stride + 1, Wo = (d.W + 2 * p - d.k) / d.stride + 1;
     const int M = Ho * Wo;
@@ -514,9 +559,7 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
         if (KS > 1) {
             if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;
             conv_simt88_kernel<true><<<grid, 128, 0, st>>>(d, Ho, Wo, KS, d.ws);
-            const size_t total = (size_t)d.groups * M * d.Cout;
-            const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-            conv_simt_reduce_kernel<<<blocks, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+            conv_simt_reduce_kernel<<<reduce_blocks(d, M), 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
         } else {
             conv_simt88_kernel<false><<<grid, 128, 0, st>>>(d, Ho, Wo, 1, nullptr);
         }
@@ -527,9 +570,7 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t st) {
             conv_simt64_kernel<true, 32><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
         else
             conv_simt64_kernel<true, 16><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
-        const size_t total = (size_t)d.groups * M * d.Cout;
-        const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-        conv_simt_reduce_kernel<<<blocks, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+        conv_simt_reduce_kernel<<<reduce_blocks(d, M), 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
     } else {
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups);
         if (d.Cin % 32 == 0)

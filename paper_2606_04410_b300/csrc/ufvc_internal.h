@@ -91,6 +91,7 @@ struct ConvDesc {
     float* ws = nullptr;        // SIMT split-K workspace (conv_simt_workspace(d) floats), or nullptr
     size_t ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
+    int vec4 = 0;               // SIMT: set by the launcher when NHWC outputs may be written 16 bytes at a time
 };
 
 // api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
