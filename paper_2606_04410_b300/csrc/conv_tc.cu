@@ -60,6 +60,9 @@ struct TcArgs {
     const uint8_t* res8;
     float res_s;
     int* err;
+    // NHWC outputs: 1 when every pixel's channel run starts 16-byte aligned and Cout is a multiple of 32,
+    // so the epilogue may store NV consecutive channels as 16-byte vectors; else channel by channel
+    int vec_out;
 };
 
 // All groups' biases (groups x Cout floats) copied once into shared memory when they fit; the epilogue
@@ -167,6 +170,23 @@ template <int NV>
 __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
                                            float* v) {
     finish_cols<NV>(p, bias_all, g, oh, ow, co0, v);
+    if (p.mode == OUT_NHWC && !p.vec_out) {
+        // channel by channel (e.g. 12 outputs: a pixel's run is neither 16-byte aligned nor NV long)
+        const size_t o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int c = co0 + i;
+            if (c >= p.Cout) break;
+            if (p.out_inv != 0.0f)
+                reinterpret_cast<uint8_t*>(p.out)[o + c] =
+                    (uint8_t)__nv_cvt_float_to_fp8(v[i] * p.out_inv, __NV_SATFINITE, __NV_E4M3);
+            else if (p.out_f32)
+                reinterpret_cast<float*>(p.out)[o + c] = v[i];
+            else
+                reinterpret_cast<__nv_bfloat16*>(p.out)[o + c] = __float2bfloat16_rn(v[i]);
+        }
+        return;
+    }
     if (p.out_inv != 0.0f && (p.mode == OUT_NHWC || (p.mode == OUT_PS && p.ps_major))) {
         // E4M3 output: NV consecutive channels of one pixel
         size_t o;
@@ -517,24 +537,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 // weights have completed.
 // ------------------------------------------------------------------------------------------------
 constexpr int kHaloRowBytes = 17 * 1024;  // 130 rows x 128 B, rounded up to the 1024-B swizzle repeat
+__host__ __device__ constexpr int halo_groups(int BN) { return BN == 16 ? 4 : 2; }
 constexpr int kHaloBoxBytes = 130 * 128;
 
-// Epilogue of the resident-weight kernel.  A tile's BN columns are drained by BN/16 column quarters of
-// 16 columns each (four warps per quarter, one per TMEM lane quarter); with BN = 16 the four quarters
-// form four independent groups that drain four different tiles at once (four TMEM accumulators).
-// OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC (BN = 64) through the swizzled staging
-// tile and a TMA store.  (The final frame layer has its own kernel, conv_tc_final_kernel.)
+// Epilogue of the resident-weight kernel.  The 16 epilogue warps form halo_groups(BN) groups that drain
+// different tiles at once, each from its own pair of TMEM accumulators: BN = 64 -> two groups of eight
+// warps (two column halves of 32 x four TMEM lane quarters), BN = 16 -> four groups of four warps.
+// OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC (BN = 64) through a swizzled staging
+// tile per group and a TMA store.  (The final frame layer has its own kernel, conv_tc_final_kernel.)
 template <int BN, int STAGES, int OUTK>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
     constexpr int A_BYTES = 3 * kHaloRowBytes;
     constexpr int B_BYTES = 9 * BN * 128;
-    constexpr int CPT = BN / 16;             // column quarters per tile
-    constexpr int EG = 4 / CPT;              // tiles drained concurrently (epilogue groups)
-    constexpr int NACC = EG > 2 ? EG : 2;    // TMEM accumulators
-    constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : 128;
-    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : 0;
+    constexpr int EG = halo_groups(BN);      // tiles drained concurrently (epilogue groups)
+    constexpr int WPG = 16 / EG;             // warps per group: WPG / 4 column parts x 4 lane quarters
+    constexpr int CPW = BN / (WPG / 4);      // accumulator columns per warp (16 or 32)
+    constexpr int NACC = 2 * EG;             // TMEM accumulators
+    constexpr uint32_t TMEM_COLS = NACC * BN <= 128 ? 128 : 256;
+    constexpr int C_BYTES = OUTK == 1 ? EG * 128 * BN * 2 : 0;  // one staging tile per group
     static_assert(BN == 16 || BN == 64, "resident-weight kernel: N tile of 16 or 64");
     static_assert(OUTK == 0 || (OUTK == 1 && BN == 64), "staged stores: bf16 NHWC with N = 64");
     extern __shared__ uint8_t smem_raw[];
@@ -564,13 +586,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < NACC; ++a) {
             ptx::mbar_init(&tfull[a], 1);
-            ptx::mbar_init(&tempty[a], 128 * CPT);
+            ptx::mbar_init(&tempty[a], 32 * WPG);
         }
         ptx::mbar_init(bfull, 1);
         ptx::mbar_init(bfree, 1);
         ptx::mbar_init(drain, 1);
         for (int gq = 0; gq < 4; ++gq) {
-            ptx::mbar_init(&cwritten[gq], 128 * CPT);
+            ptx::mbar_init(&cwritten[gq], 32 * WPG);
             ptx::mbar_init(&cfree[gq], 1);
         }
         *abort_flag = 0;
@@ -665,10 +687,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         __syncwarp();
     } else {
+        // epilogue: warp 2 + 4 c + q reads TMEM lane quarter q; c = grp * (WPG / 4) + part
         const int q = warp & 3, colq = (warp - 2) >> 2, row = q * 32 + lane;
-        const int grp = colq / CPT, cq = colq % CPT;
-        const bool lead_warp = warp == 2 + grp * CPT * 4;
+        const int grp = colq / (WPG / 4), part = colq % (WPG / 4);
+        const bool lead_warp = warp == 2 + grp * WPG;
         const bool elected = OUTK != 0 && lead_warp && lane == 0;
+        uint8_t* sCg = sC + grp * (128 * BN * 2);
         int tl = grp, k = 0;
         for (int t = t_begin + grp; t < t_end; t += EG, tl += EG, ++k) {
             const int acc = tl % NACC, use = tl / NACC;
@@ -678,16 +702,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int nt = key % p.n_tiles, g = key / p.n_tiles;
             const int ow = strip * 128 + row;
             const bool valid = ow < p.Wo;
-            const int co0 = nt * BN + cq * 16;
-            float v[16];
-            ptx::tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + cq * 16, v);
+            const int co0 = nt * BN + part * CPW;
+            float v[CPW];
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN + part * CPW;
+            if constexpr (CPW == 32) ptx::tmem_ld32(taddr, v); else ptx::tmem_ld16(taddr, v);
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[acc]);  // the accumulator is in registers: TMEM free for the next tile
             if constexpr (OUTK == 0) {
-                if (valid) store_cols<16>(p, bias_all, g, oh, ow, co0, v);
+                if (valid) store_cols<CPW>(p, bias_all, g, oh, ow, co0, v);
             } else {
-                if (valid) finish_cols<16>(p, bias_all, g, oh, ow, co0, v);
-                if (k > 0) {  // the group's previous TMA stores must have read its staging block
+                if (valid) finish_cols<CPW>(p, bias_all, g, oh, ow, co0, v);
+                if (k > 0) {  // the group's previous TMA store must have read its staging tile
                     if (elected) {
                         ptx::bulk_wait_read0();
                         ptx::mbar_arrive(&cfree[grp]);
@@ -695,10 +720,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
                 }
                 {
-                    const uint32_t base = ptx::smem_u32(sC) + row * 128;
+                    const uint32_t base = ptx::smem_u32(sCg) + row * 128;
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int j = cq * 2 + i;
+                    for (int i = 0; i < CPW / 8; ++i) {
+                        const int j = part * (CPW / 8) + i;
                         ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
                                           pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
                                           pack_bf16(v[8 * i + 6], v[8 * i + 7]));
@@ -712,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
                 }
                 if (elected) {
-                    ptx::tma_store_4d(&tmC, sC, nt * BN, strip * 128, oh, g);
+                    ptx::tma_store_4d(&tmC, sCg, nt * BN, strip * 128, oh, g);
                     ptx::bulk_commit();
                 }
             }
@@ -1077,7 +1102,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
 template <int BN, int STAGES, int OUTK>
 static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                                cudaStream_t s) {
-    constexpr int C_BYTES = OUTK == 1 ? 128 * BN * 2 : 0;
+    constexpr int C_BYTES = OUTK == 1 ? halo_groups(BN) * 128 * BN * 2 : 0;
     constexpr int kSmem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + C_BYTES + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
@@ -1220,6 +1245,10 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.out = d.out; a.out_gs = d.out_gs; a.out_h = d.out_h; a.out_w = d.out_w;
     a.out_c = (d.mode == OUT_NHWC) ? d.Cout : d.Cout / 4;
     if (d.mode == OUT_NHWC && d.out_c_stride) a.out_c = d.out_c_stride;
+    a.vec_out = d.Cout % 32 == 0 && a.out_c % 16 == 0 && d.out_gs % 16 == 0 &&
+                (reinterpret_cast<uintptr_t>(d.out) & 15) == 0;
+    if (d.res && d.mode == OUT_NHWC && !(a.vec_out && d.res_gs % 16 == 0 && (reinterpret_cast<uintptr_t>(d.res) & 15) == 0))
+        return cudaErrorInvalidValue;  // residuals are read 16 bytes at a time
     a.res = reinterpret_cast<const __nv_bfloat16*>(d.res); a.res_gs = d.res_gs;
     a.err = d.err;
     a.c_rank = ps_stage ? 5 : 4;

@@ -74,6 +74,8 @@ LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
     (1, 2, 15, 17, 300, 1, 1, 0, 64),    # R2a over three 128-pixel strips (ragged last strip)
     (1, 2, 17, 9, 260, 1, 1, 1, 64),     # U2 (four N tiles of 64) over three strips
     (1, 2, 26, 5, 390, 1, 0, 2, 64),     # U3 frame 1 over four strips, final mapping
+    (1, 2, 15, 272, 300, 1, 1, 0, 64),   # R2a: 816 tiles, runs of rows per CTA through the row FIFO
+    (1, 2, 18, 150, 260, 1, 0, 0, 64),   # U3 as a plain NHWC layer: the N = 16 resident-weight kernel
 ]
 
 
