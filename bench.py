@@ -313,8 +313,10 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
     assert codec.sync_status() == 0
     rec = out.float().cpu().numpy() / 255.0
     psnr = float(10 * np.log10(1.0 / np.mean((rec - frames_np / 255.0) ** 2)))
+    # timed steps: no host synchronisation between steps (the library's stage events accumulate and are
+    # read once at the end), so the host enqueues ahead of the device as a serving loop does; the step
+    # events bracket exactly one encode and one decode
     codec.set_profiling(profile)
-    prof_acc: dict[str, list] = {}
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
     if dist is not None and world > 1:
         dist.barrier()
@@ -326,12 +328,13 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
         evs[i][1].record(stream)
         codec.decode_chunk(bits, nb, W_, H_, out)
         evs[i][2].record(stream)
-        if profile:
-            for name, ms, nl in codec.get_profile():
-                prof_acc.setdefault(name, []).append((ms, nl))
     torch.cuda.synchronize()
     if dist is not None and world > 1:
         dist.barrier()
+    prof_acc: dict[str, list] = {}
+    if profile:
+        for name, ms, nl in codec.get_profile(max_entries=64 * steps):
+            prof_acc.setdefault(name, []).append((ms, nl))
     codec.set_profiling(False)
     assert codec.sync_status() == 0
     t_enc = [evs[i][0].elapsed_time(evs[i][1]) for i in range(steps)]

@@ -45,6 +45,7 @@ struct LayerW {
     std::vector<float> wscale;
     float* cs8 = nullptr;
     float out_inv = 0.f, res_s = 0.f;
+    unsigned long long kmask = 0;  // tensor-core K steps that run (0: all); see ConvDesc::kmask
 };
 
 // Activation tensors of the FP8 path, each with one per-tensor scale (absmax / 448 on the FP32 path of a
@@ -109,6 +110,9 @@ struct ufvc_ctx {
     int* d_status = nullptr;
     LayerW enc[L_NENC];
     LayerW dec[D_NDEC];
+    // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
+    // taps regrouped by 2x2 super-pixel; weight rows [64][tap][sub-pixel][32]; bias shared with enc[L_A1])
+    LayerW a1s2d;
     std::map<long long, Plan*> plans;
     std::string err;
     // standalone rANS scratch
@@ -468,6 +472,39 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
     return UFVC_OK;
 }
 
+// A1 (3x3, stride 2, 3N -> e0) regrouped for space-to-depth input: super-pixel (Y, X) holds input pixels
+// (2Y + dy, 2X + dx) as channels [2 dy + dx][32].  Output pixel (oh, ow) reads input rows 2 oh - 1 .. 2 oh + 1,
+// i.e. sub-row 1 of super-row oh - 1 and both sub-rows of super-row oh: tap (sy, sx) of the 2x2 form at
+// super offsets (sy - 1, sx - 1) carries original tap (ky, kx) = (2 sy + dy - 1, 2 sx + dx - 1) where that
+// lies in 0..2, zero elsewhere.  K steps (tap, 64-channel chunk = sub-row dy): taps (0, 0) and (0, 1) have
+// no dy = 0 weights, so steps 0 and 2 are skipped.
+static ufvc_status upload_a1_s2d(ufvc_ctx* ctx, const float* src) {
+    const LayerW& A1 = ctx->enc[L_A1];
+    const int co = A1.cout, ci = A1.cin;  // ci = 3N <= 32
+    LayerW& L = ctx->a1s2d;
+    L.cout = co; L.k = 2; L.cin = 128; L.cin_p = 128; L.groups = 1;
+    L.b = A1.b; L.b_gs = A1.b_gs;
+    L.cin_tc = 128; L.cout_pad = co;
+    L.kmask = 0xFAull;
+    const size_t K = 4 * 128;
+    std::vector<__nv_bfloat16> wt((size_t)co * K, __float2bfloat16(0.f));
+    for (int o = 0; o < co; ++o)
+        for (int sy = 0; sy < 2; ++sy)
+            for (int sx = 0; sx < 2; ++sx)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int ky = 2 * sy + dy - 1, kx = 2 * sx + dx - 1;
+                        if (ky < 0 || kx < 0) continue;
+                        for (int c = 0; c < ci; ++c)
+                            wt[(size_t)o * K + (sy * 2 + sx) * 128 + (dy * 2 + dx) * 32 + c] =
+                                __float2bfloat16(src[((size_t)o * 9 + ky * 3 + kx) * ci + c]);
+                    }
+    ufvc_status st;
+    if ((st = dalloc(ctx, nullptr, &L.wtc, wt.size())) != UFVC_OK) return st;
+    CK(cudaMemcpy(L.wtc, wt.data(), wt.size() * 2, cudaMemcpyHostToDevice));
+    return UFVC_OK;
+}
+
 extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->cfg.device);
@@ -482,6 +519,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
                 cudaFree(L.w8); cudaFree(L.cs8);
             }
         }
+        cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
     }
@@ -541,6 +579,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         if ((st = upload_layer(ctx, ctx->dec[j], weights, offs.data(), L_NENC + j, ctx->N, true,
                                    j == D_D0 || j == D_U1 || j == D_U2, j == D_U3)) != UFVC_OK)
             return bail(st);
+    if (cfg->precision == UFVC_BF16 && 3 * ctx->N <= 32 && (st = upload_a1_s2d(ctx, weights + offs[L_A1])) != UFVC_OK)
+        return bail(st);
     *out = ctx;
     return UFVC_OK;
 }
@@ -563,6 +603,7 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     c->d_qinv = base->d_qinv;
     for (int l = 0; l < L_NENC; ++l) c->enc[l] = base->enc[l];
     for (int l = 0; l < D_NDEC; ++l) c->dec[l] = base->dec[l];
+    c->a1s2d = base->a1s2d;
     c->borrowed = true;
     if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
         cudaFree(c->d_status);
@@ -587,7 +628,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
     d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
     if (use_tc(ctx, L)) {
         d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
-        d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc;
+        d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc; d.kmask = L.kmask;
         if (ctx->cfg.precision == UFVC_FP8 && L.w8) {
             d.w8 = L.w8; d.cscale = L.cs8; d.out_inv = L.out_inv; d.res_s = L.res_s;
         }
@@ -674,6 +715,7 @@ static void probe(ufvc_ctx* ctx, int t, const float* x, size_t n, cudaStream_t s
 static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
     const Arch& a = ctx->arch;
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
+    const bool s2d = ctx->a1s2d.wtc != nullptr && p->C0p == 32;
     ctx->cur_ws = &p->ws_enc;
     prof_begin(ctx, "pack", s);
     if (ctx->cfg.precision == UFVC_FP32)
@@ -681,10 +723,14 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     else if (fp8)
         launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s);
     else
-        launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s);
+        launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s,
+                         s2d);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "analysis", s);
-    RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    if (s2d)  // the same layer as a 2x2 stride-1 convolution over the space-to-depth input
+        RUN(conv(ctx, ctx->a1s2d, p->x, p->Hp / 2, p->Wp / 2, 1, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    else
+        RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
     probe(ctx, T_A1, p->a1, (size_t)p->h1 * p->w1 * a.e0, s);
     RUN(conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s));
     probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);

@@ -63,6 +63,7 @@ struct TcArgs {
     // NHWC outputs: 1 when every pixel's channel run starts 16-byte aligned and Cout is a multiple of 32,
     // so the epilogue may store NV consecutive channels as 16-byte vectors; else channel by channel
     int vec_out;
+    unsigned long long kmask;  // K steps that run (bit ks); the others have all-zero weights
 };
 
 // All groups' biases (groups x Cout floats) copied once into shared memory when they fit; the epilogue
@@ -284,7 +285,8 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 // (the first layer, whose 3N <= 30 input channels would fill only part of a 64-channel stage).
 enum { OP_BF16 = 0, OP_E4M3 = 1, OP_BF16_32 = 2 };
 
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16>
+// KM: some K steps are skipped (TcArgs::kmask); otherwise every step runs and the loops carry no test.
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
@@ -367,9 +369,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
                 const int h0 = (mt / p.tiles_w) * p.TH, w0 = (mt % p.tiles_w) * p.TW;
                 const int ag = p.a_grouped ? g : 0;
-                for (int ks = 0; ks < p.ksteps; ++ks, ++it) {
+                for (int ks = 0; ks < p.ksteps; ++ks) {
+                    if (KM && !((p.kmask >> ks) & 1ull)) continue;  // all-zero weights: no stage
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
+                    ++it;
                     if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) { ok = false; break; }
                     ptx::mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
                     const int tap = ks / p.cin_chunks, c0 = (ks - tap * p.cin_chunks) * CH;
@@ -404,9 +408,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem_base + acc * BN;
-                for (int ks = 0; ks < p.ksteps; ++ks, ++it) {
+                bool first = true;  // the tile's first executed step overwrites the accumulator
+                for (int ks = 0; ks < p.ksteps; ++ks) {
+                    if (KM && !((p.kmask >> ks) & 1ull)) continue;
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
+                    ++it;
                     if (!wait_bar(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
                     ptx::tc_fence_after();
                     const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB + s * B_BYTES);
@@ -414,19 +421,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
                             ptx::mma_f8(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
-                                        (ks | kk) != 0);
+                                        !first || kk != 0);
                     } else if constexpr (OP == OP_BF16_32) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=16 BF16 per 64-byte row
                             ptx::mma_f16(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
-                                         (ks | kk) != 0);
+                                         !first || kk != 0);
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
                             ptx::mma_f16(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32),
-                                         idesc, (ks | kk) != 0);
+                                         idesc, !first || kk != 0);
                     }
                     ptx::mma_commit(&empty[s]);
+                    first = false;
                 }
                 if (ok) ptx::mma_commit(&tfull[acc]);
             }
@@ -1072,7 +1080,7 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16>
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
@@ -1081,7 +1089,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
     const int smem = kSmem;
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP>,
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP, KM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
@@ -1093,7 +1101,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_kernel<BN, STAGES, STAGED, OP><<<grid, kThreads, smem, s>>>(a, b, c, args);
+    conv_tc_kernel<BN, STAGES, STAGED, OP, KM><<<grid, kThreads, smem, s>>>(a, b, c, args);
     return cudaGetLastError();
 }
 
@@ -1206,7 +1214,11 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     if ((d.Cin % 64 != 0 && !c32) || (d.stride != 1 && d.stride != 2) || (d.stride == 2 && ((d.H | d.W) & 1)))
         return cudaErrorInvalidValue;
     const int pad = d.k / 2;
-    const int Ho = (d.H + 2 * pad - d.k) / d.stride + 1, Wo = (d.W + 2 * pad - d.k) / d.stride + 1;
+    // even k (the 2x2 form of a stride-2 layer on space-to-depth input): taps at offsets -k/2 .. k/2 - 1,
+    // the output has the input's size
+    const int Ho = (d.H + 2 * pad - d.k) / d.stride + 1 - (d.k % 2 == 0 ? 1 : 0);
+    const int Wo = (d.W + 2 * pad - d.k) / d.stride + 1 - (d.k % 2 == 0 ? 1 : 0);
+    if (d.k % 2 == 0 && d.stride != 1) return cudaErrorInvalidValue;
     int BN = d.cout_pad >= 256 ? 256 : d.cout_pad;
     if (d.cout_pad % BN != 0 || !(BN == 16 || BN == 64 || BN == 128 || BN == 192 || BN == 256))
         return cudaErrorInvalidValue;
@@ -1238,6 +1250,10 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
     a.cin_chunks = c32 ? 1 : d.Cin / 64;
     a.ksteps = d.k * d.k * a.cin_chunks;
+    if (a.ksteps > 64) return cudaErrorInvalidValue;
+    // steps skipped by kmask have all-zero weights, so a kernel that runs every step computes the same
+    // result: only the staged BF16 N = 64 kernel (the space-to-depth first layer) reads the mask
+    a.kmask = d.kmask ? d.kmask : ~0ull;
     a.k = d.k; a.pad = pad; a.stride = d.stride; a.a_grouped = d.in_gs != 0;
     a.bias = d.btc ? d.btc : d.b; a.b_gs = (int)d.b_gs; a.Cout = d.Cout;
     a.ps_major = d.mode == OUT_PS && d.ps_major;
@@ -1335,7 +1351,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (!okc) return cudaErrorInvalidValue;
         if (c32) return BN == 64 ? launch_bn<64, 12, true, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
         switch (BN) {
-            case 64: return launch_bn<64, 6, true>(ma, mb, mc, a, s);
+            case 64: return a.kmask != ~0ull ? launch_bn<64, 6, true, OP_BF16, true>(ma, mb, mc, a, s)
+                                             : launch_bn<64, 6, true>(ma, mb, mc, a, s);
             case 128: return launch_bn<128, 4, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
             default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);

@@ -109,10 +109,67 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
     }
 }
 
+// Space-to-depth variant (3N <= 32) for the first layer's 2x2 form: pixel (h, w) becomes sub-pixel
+// (h & 1, w & 1) of super-pixel (h / 2, w / 2), whose 128 channels are [2 (h & 1) + (w & 1)][32].  A block
+// packs a 128-pixel segment of both rows of a super-row, so its 64 super-pixels (16 KB) are written as one
+// contiguous run; shared-memory chunk c (16 bytes) of the segment is kept at c ^ ((c >> 4) & 7).
+__global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* __restrict__ frames, int N, int H,
+                                                                 int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
+    __shared__ uint4 tile[kPackPix * 8];
+    __shared__ uint16_t lut[256];
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 255.0f));
+    __syncthreads();
+    const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
+    const int sw = w < W ? w : W - 1;  // replicate the last column
+    const size_t plane = (size_t)H * W * 3;
+    const int Ws = Wp >> 1, npix = Wp - w0 < kPackPix ? Wp - w0 : kPackPix;
+    for (int Y = blockIdx.y; Y < (Hp >> 1); Y += gridDim.y) {
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int h = 2 * Y + dy, sh = h < H ? h : H - 1;  // replicate the last row
+            const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
+            uint32_t pk[24];
+#pragma unroll
+            for (int n = 0; n < 16; ++n) {
+                uint32_t b0 = 0, b1 = 0, b2 = 0;
+                if (n < N) {
+                    b0 = lut[__ldg(src + n * plane)];
+                    b1 = lut[__ldg(src + n * plane + 1)];
+                    b2 = lut[__ldg(src + n * plane + 2)];
+                }
+                if ((n & 1) == 0) {
+                    pk[3 * n / 2] = b0 | (b1 << 16);
+                    pk[3 * n / 2 + 1] = b2;
+                } else {
+                    pk[(3 * n - 1) / 2] |= b0 << 16;
+                    pk[(3 * n + 1) / 2] = b1 | (b2 << 16);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 c = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                const int ch = (p >> 1) * 16 + dy * 8 + (p & 1) * 4 + k;  // chunk within the segment
+                tile[ch ^ ((ch >> 4) & 7)] = c;
+            }
+        }
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(x) + ((size_t)Y * Ws + (w0 >> 1)) * 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ch = p + kPackPix * i;
+            if ((ch >> 4) < (npix >> 1)) dst[ch] = tile[ch ^ ((ch >> 4) & 7)];  // super-pixel ch / 16
+        }
+        __syncthreads();
+    }
+}
+
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool s2d) {
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
-    if (Cp == 32)  // 3N <= 32
+    if (Cp == 32 && s2d)  // Hp, Wp even
+        pack_bf16_s2d_kernel<<<dim3(grid.x, (unsigned)((Hp >> 1) < 65535 ? (Hp >> 1) : 65535)), kPackPix, 0, s>>>(
+            frames, N, H, W, Hp, Wp, x);
+    else if (Cp == 32)  // 3N <= 32
         pack_bf16_kernel<32><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
     else
         pack_bf16_kernel<64><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);

@@ -92,6 +92,9 @@ struct ConvDesc {
     size_t ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
     int vec4 = 0;               // SIMT: set by the launcher when NHWC outputs may be written 16 bytes at a time
+    // tensor-core path: K steps (tap x 64-channel chunk, tap-major) whose weights are all zero and are
+    // skipped (bit ks set = step ks runs; 0 = every step runs)
+    unsigned long long kmask = 0;
 };
 
 // api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
@@ -103,7 +106,8 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s);
 size_t conv_simt_workspace(const ConvDesc& d);
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
-                      cudaStream_t s);
+                      cudaStream_t s,
+                      bool s2d = false);
 
 // ---------------------------------------------------------------------------------------------
 // Elementwise / entropy kernels
