@@ -78,6 +78,8 @@ __device__ __forceinline__ void store_out4(const ConvDesc& d, int g, int oh, int
 
 template <int BM, int BN>
 __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho, int Wo) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int BK = 16;
     constexpr int TN = BN / 4;    // threads along N, 4 output channels each
     constexpr int TM = 256 / TN;  // threads along M
@@ -209,6 +211,8 @@ __global__ void __launch_bounds__(256) conv_simt_kernel(const ConvDesc d, int Ho
 // conv_simt_reduce_kernel); otherwise finish the outputs here (KS = 1).
 template <bool PARTIAL, int BK>
 __global__ void __launch_bounds__(256) conv_simt64_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int BM = 64, BN = 64;
     constexpr int AV = BM * BK / 4 / 256;  // float4 A loads per thread
     constexpr int BV = BK * BN / 4 / 256;  // float4 B loads per thread
@@ -348,6 +352,8 @@ __global__ void __launch_bounds__(256) conv_simt64_kernel(const ConvDesc d, int 
 // split-K ranges and the PARTIAL workspace exactly as in conv_simt64_kernel.  Cout % 128 == 0.
 template <bool PARTIAL>
 __global__ void __launch_bounds__(128, 3) conv_simt88_kernel(const ConvDesc d, int Ho, int Wo, int KS, float* ws) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int BM = 64, BN = 128, BK = 16;
     __shared__ __align__(16) float As[2][BK][BM + 4];
     __shared__ __align__(16) float Bs[2][BK][BN];
@@ -467,6 +473,8 @@ __global__ void __launch_bounds__(128, 3) conv_simt88_kernel(const ConvDesc d, i
 
 // out = bias + (((range 0) + range 1) + ...), then the layer's activation and output mapping
 __global__ void conv_simt_reduce_kernel(const ConvDesc d, int Ho, int Wo, int KS, const float* ws) {
+    pdl_trigger();
+    pdl_wait();
     // four channels per thread (Cout % 4 == 0 for the split layers); 32-bit element indices per group
     const int M = Ho * Wo, C4 = d.Cout >> 2;
     const int per_g4 = M * C4;
@@ -550,33 +558,33 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
     const int kind = simt_plan(d, &KS);
     if (kind == 0) {
         dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
-        conv_simt_kernel<128, 16><<<grid, 256, 0, st>>>(d, Ho, Wo);
+        (void)launch_pdl(conv_simt_kernel<128, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
     } else if (kind == 1) {
         dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
-        conv_simt_kernel<128, 64><<<grid, 256, 0, st>>>(d, Ho, Wo);
+        (void)launch_pdl(conv_simt_kernel<128, 64>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
     } else if (kind == 3) {
         dim3 grid((M + 63) / 64, d.Cout / 128, d.groups * KS);
         if (KS > 1) {
             if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;
-            conv_simt88_kernel<true><<<grid, 128, 0, st>>>(d, Ho, Wo, KS, d.ws);
-            conv_simt_reduce_kernel<<<reduce_blocks(d, M), 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+            (void)launch_pdl(conv_simt88_kernel<true>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
         } else {
-            conv_simt88_kernel<false><<<grid, 128, 0, st>>>(d, Ho, Wo, 1, nullptr);
+            (void)launch_pdl(conv_simt88_kernel<false>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
         }
     } else if (KS > 1) {
         if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;  // caller's workspace
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups * KS);
         if (d.Cin % 32 == 0)
-            conv_simt64_kernel<true, 32><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+            (void)launch_pdl(conv_simt64_kernel<true, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
         else
-            conv_simt64_kernel<true, 16><<<grid, 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
-        conv_simt_reduce_kernel<<<reduce_blocks(d, M), 256, 0, st>>>(d, Ho, Wo, KS, d.ws);
+            (void)launch_pdl(conv_simt64_kernel<true, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+        (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
     } else {
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups);
         if (d.Cin % 32 == 0)
-            conv_simt64_kernel<false, 32><<<grid, 256, 0, st>>>(d, Ho, Wo, 1, nullptr);
+            (void)launch_pdl(conv_simt64_kernel<false, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
         else
-            conv_simt64_kernel<false, 16><<<grid, 256, 0, st>>>(d, Ho, Wo, 1, nullptr);
+            (void)launch_pdl(conv_simt64_kernel<false, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
     }
     return cudaGetLastError();
 }

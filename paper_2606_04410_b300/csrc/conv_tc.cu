@@ -354,6 +354,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above (barriers, TMEM, biases, descriptor prefetch) may overlap the previous kernel's
+    // tail; its outputs are read, and this kernel's written, only after it has completed
+    pdl_trigger();
+    pdl_wait();
     const int tiles_m = p.tiles_w * p.tiles_h;
 
     if (warp == 0) {
@@ -616,6 +620,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above (barriers, TMEM, biases, descriptor prefetch) may overlap the previous kernel's
+    // tail; its outputs are read, and this kernel's written, only after it has completed
+    pdl_trigger();
+    pdl_wait();
     // tile t = ((g * n_tiles + nt) * Ho + oh) * tiles_w + strip; this CTA owns [t_begin, t_end)
     const int t_begin = (int)((long long)p.total_tiles * blockIdx.x / gridDim.x);
     const int t_end = (int)((long long)p.total_tiles * (blockIdx.x + 1) / gridDim.x);
@@ -836,6 +844,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above (barriers, TMEM, biases, descriptor prefetch) may overlap the previous kernel's
+    // tail; its outputs are read, and this kernel's written, only after it has completed
+    pdl_trigger();
+    pdl_wait();
     // work item t = (g * tiles_w + strip) * Ho + y (one output row of one strip); this CTA owns
     // [t_begin, t_end), cut into runs of one (g, strip)
     const int t_begin = (int)((long long)p.total_tiles * blockIdx.x / gridDim.x);
@@ -1101,8 +1113,7 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_kernel<BN, STAGES, STAGED, OP, KM><<<grid, kThreads, smem, s>>>(a, b, c, args);
-    return cudaGetLastError();
+    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
@@ -1128,8 +1139,7 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_halo_kernel<BN, STAGES, OUTK><<<grid, kThreads, smem, s>>>(a, b, c, args);
-    return cudaGetLastError();
+    return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
 
 template <int OUTK>
@@ -1151,8 +1161,7 @@ static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, cons
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    conv_tc_final_kernel<OUTK><<<grid, kThreads, kSmem, s>>>(a, b, c, args);
-    return cudaGetLastError();
+    return launch_pdl(conv_tc_final_kernel<OUTK>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, args);
 }
 
 // The final decoder layer in scatter form (d.wsc: bf16 [groups][128][64], row 32 (c / 3) + 9 ky + 3 kx

@@ -26,6 +26,8 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // ------------------------------------------------------------------------------------------------
 __global__ void pack_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int Cp,
                             float* __restrict__ x) {
+    pdl_trigger();
+    pdl_wait();
     const size_t pix = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pix >= (size_t)Hp * Wp) return;
     const int h = (int)(pix / Wp), w = (int)(pix % Wp);
@@ -44,7 +46,7 @@ __global__ void pack_kernel(const uint8_t* __restrict__ frames, int N, int H, in
 
 void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s) {
     const size_t npix = (size_t)Hp * Wp;
-    pack_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(frames, N, H, W, Hp, Wp, Cp, x);
+    (void)launch_pdl(pack_kernel, dim3((unsigned)((npix + 255) / 256)), dim3(256), (size_t)(0), s, frames, N, H, W, Hp, Wp, Cp, x);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
@@ -62,6 +64,8 @@ constexpr int kPackPix = 128;
 template <int CP>
 __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                              int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
+    pdl_trigger();
+    pdl_wait();
     constexpr int KC = CP / 8;  // 16-byte chunks per pixel row
     __shared__ uint4 tile[kPackPix * KC];
     __shared__ uint16_t lut[256];  // bf16 bits of v / 255 (a division per entry, not per pixel)
@@ -115,6 +119,8 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
 // contiguous run; shared-memory chunk c (16 bytes) of the segment is kept at c ^ ((c >> 4) & 7).
 __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                                  int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ uint4 tile[kPackPix * 8];
     __shared__ uint16_t lut[256];
     for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 255.0f));
@@ -167,18 +173,19 @@ void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp
                       cudaStream_t s, bool s2d) {
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
     if (Cp == 32 && s2d)  // Hp, Wp even
-        pack_bf16_s2d_kernel<<<dim3(grid.x, (unsigned)((Hp >> 1) < 65535 ? (Hp >> 1) : 65535)), kPackPix, 0, s>>>(
-            frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_s2d_kernel, dim3(dim3(grid.x, (unsigned)((Hp >> 1) < 65535 ? (Hp >> 1) : 65535))), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
     else if (Cp == 32)  // 3N <= 32
-        pack_bf16_kernel<32><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_kernel<32>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
     else
-        pack_bf16_kernel<64><<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_kernel<64>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
 }
 
 // E4M3 variant: the same segment scheme with 64-byte pixel rows; x = v / 255 is stored as the E4M3 code
 // of x * 448 (the per-tensor scale of [0, 1] data: 1 / 448).
 __global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                             int W, int Hp, int Wp, uint8_t* __restrict__ x) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ uint4 tile[kPackPix * 4];
     __shared__ uint8_t lut[256];
     for (int v = threadIdx.x; v < 256; v += blockDim.x)
@@ -218,11 +225,13 @@ __global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __res
 
 void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s) {
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
-    pack_fp8_kernel<<<grid, kPackPix, 0, s>>>(frames, N, H, W, Hp, Wp, x);
+    (void)launch_pdl(pack_fp8_kernel, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
 }
 
 // [H][W][C] float -> E4M3 codes of value * inv, rows of pitch Wd pixels (C a multiple of 4)
 __global__ void f32_to_e4m3_rows_kernel(const float4* a, int H, int W, int C4, float inv, uint8_t* out, int Wd) {
+    pdl_trigger();
+    pdl_wait();
     const size_t n = (size_t)H * W * C4;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t row = i / ((size_t)W * C4), rem = i - row * W * C4;
@@ -236,12 +245,14 @@ __global__ void f32_to_e4m3_rows_kernel(const float4* a, int H, int W, int C4, f
 void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s) {
     const size_t n = (size_t)H * W * (C / 4);
     const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
-    f32_to_e4m3_rows_kernel<<<blocks ? blocks : 1, 256, 0, s>>>(reinterpret_cast<const float4*>(a), H, W, C / 4, inv,
+    (void)launch_pdl(f32_to_e4m3_rows_kernel, dim3(blocks ? blocks : 1), dim3(256), (size_t)(0), s, reinterpret_cast<const float4*>(a), H, W, C / 4, inv,
                                                              out, Wd);
 }
 
 // *slot = max(*slot, max |x[i]|) (slot zeroed by the caller); non-negative floats order as their bits
 __global__ void absmax_kernel(const float* __restrict__ x, size_t n, float* slot) {
+    pdl_trigger();
+    pdl_wait();
     float m = 0.f;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         m = fmaxf(m, fabsf(x[i]));
@@ -251,7 +262,7 @@ __global__ void absmax_kernel(const float* __restrict__ x, size_t n, float* slot
 
 void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s) {
     const size_t blocks = std::min<size_t>((n + 255) / 256, 2048);
-    absmax_kernel<<<(unsigned)(blocks ? blocks : 1), 256, 0, s>>>(x, n, slot);
+    (void)launch_pdl(absmax_kernel, dim3((unsigned)(blocks ? blocks : 1)), dim3(256), (size_t)(0), s, x, n, slot);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -261,6 +272,8 @@ void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s) {
 // ------------------------------------------------------------------------------------------------
 __global__ void zquant_kernel(const float* __restrict__ z, int npos, int cz, const uint64_t* __restrict__ zthr,
                               int16_t* __restrict__ zhat, uint8_t* __restrict__ iz) {
+    pdl_trigger();
+    pdl_wait();
     const int c = blockIdx.x;
     unsigned long long S = 0;
     for (int p = threadIdx.x; p < npos; p += blockDim.x) {
@@ -285,7 +298,7 @@ __global__ void zquant_kernel(const float* __restrict__ z, int npos, int cz, con
 
 void launch_zquant(const float* z, int npos, int cz, const uint64_t* zthr, int16_t* zhat, uint8_t* iz,
                    cudaStream_t s) {
-    zquant_kernel<<<cz, 256, 0, s>>>(z, npos, cz, zthr, zhat, iz);
+    (void)launch_pdl(zquant_kernel, dim3(cz), dim3(256), (size_t)(0), s, z, npos, cz, zthr, zhat, iz);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -305,6 +318,8 @@ __global__ void quantize_kernel(const float* __restrict__ y, const float* __rest
                                 const float* __restrict__ logsig, size_t n, const float* __restrict__ thr_all,
                                 const float* __restrict__ qinv_all, const int* qp_dev, int qp_host,
                                 int16_t* __restrict__ rhat, uint8_t* __restrict__ idx) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ float thr[kBins - 1];
     const int qp = qp_dev ? *qp_dev : qp_host;
     if (threadIdx.x < kBins - 1) thr[threadIdx.x] = thr_all[qp * (kBins - 1) + threadIdx.x];
@@ -329,35 +344,41 @@ static unsigned grid_for(size_t n, int per_block) {
 void launch_quantize(const float* y, const float* mu, const float* logsig, size_t n, const float* thr_all,
                      const float* qinv_all, const int* qp_dev, int qp_host, int16_t* rhat, uint8_t* idx,
                      cudaStream_t s) {
-    quantize_kernel<<<grid_for(n, 256), 256, 0, s>>>(y, mu, logsig, n, thr_all, qinv_all, qp_dev, qp_host, rhat, idx);
+    (void)launch_pdl(quantize_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, y, mu, logsig, n, thr_all, qinv_all, qp_dev, qp_host, rhat, idx);
 }
 
 void launch_scale_index(const float* logsig, size_t n, const float* thr_all, const int* qp_dev, uint8_t* idx,
                         cudaStream_t s) {
-    quantize_kernel<<<grid_for(n, 256), 256, 0, s>>>(nullptr, nullptr, logsig, n, thr_all, thr_all, qp_dev, 0,
+    (void)launch_pdl(quantize_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, nullptr, nullptr, logsig, n, thr_all, thr_all, qp_dev, 0,
                                                     nullptr, idx);
 }
 
 __global__ void i16_to_f32_kernel(const int16_t* a, size_t n, float* out) {
+    pdl_trigger();
+    pdl_wait();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = (float)a[i];
 }
 
 void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s) {
-    i16_to_f32_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
+    (void)launch_pdl(i16_to_f32_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, a, n, out);
 }
 
 __global__ void f32_to_bf16_kernel(const float* a, size_t n, __nv_bfloat16* out) {
+    pdl_trigger();
+    pdl_wait();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         out[i] = __float2bfloat16_rn(a[i]);
 }
 
 void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s) {
-    f32_to_bf16_kernel<<<grid_for(n, 256), 256, 0, s>>>(a, n, out);
+    (void)launch_pdl(f32_to_bf16_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, a, n, out);
 }
 
 // [H][W][C] float -> bf16 rows of pitch Wd pixels (C a multiple of 4); positions beyond W are left as they are
 __global__ void f32_to_bf16_rows_kernel(const float4* a, int H, int W, int C4, __nv_bfloat16* out, int Wd) {
+    pdl_trigger();
+    pdl_wait();
     const size_t n = (size_t)H * W * C4;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t row = i / ((size_t)W * C4), rem = i - row * W * C4;
@@ -370,7 +391,7 @@ __global__ void f32_to_bf16_rows_kernel(const float4* a, int H, int W, int C4, _
 
 void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16* out, int Wd, cudaStream_t s) {
     const size_t n = (size_t)H * W * (C / 4);
-    f32_to_bf16_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(reinterpret_cast<const float4*>(a), H, W, C / 4, out, Wd);
+    (void)launch_pdl(f32_to_bf16_rows_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, reinterpret_cast<const float4*>(a), H, W, C / 4, out, Wd);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -456,6 +477,8 @@ __global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const Rans
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum
     __shared__ uint64_t bar;
     if (!load_tables(tab, tables, nullptr, nullptr, &bar, P.s[0].status)) return;
+    pdl_trigger();  // the tables above are constants: loaded while the previous kernel finishes
+    pdl_wait();
     int lane = blockIdx.x * blockDim.x + threadIdx.x;
     int si = 0;
     if (lane >= P.s[0].K) { lane -= P.s[0].K; si = 1; }
@@ -539,7 +562,7 @@ void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packe
         cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes);
         attr = true;
     }
-    rans_encode_kernel<<<(total + kRansThreadsEnc - 1) / kRansThreadsEnc, kRansThreadsEnc, kTabBytes, s>>>(P, packed_tables);
+    (void)launch_pdl(rans_encode_kernel, dim3((total + kRansThreadsEnc - 1) / kRansThreadsEnc), dim3(kRansThreadsEnc), (size_t)(kTabBytes), s, P, packed_tables);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -554,6 +577,8 @@ __global__ void __launch_bounds__(kScanThreads) rans_finalize_kernel(const RansS
                                                                      size_t hdr_bytes, size_t capacity,
                                                                      uint64_t* nbytes, uint64_t* off_ws,
                                                                      int* status) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ typename BlockScanU64::TempStorage tmp;
     __shared__ unsigned long long base_sh;
     if (threadIdx.x == 0) base_sh = hdr_bytes;
@@ -597,6 +622,8 @@ __global__ void __launch_bounds__(kScanThreads) rans_finalize_kernel(const RansS
 }
 
 __global__ void rans_copy_kernel(const RansSecPair P, uint8_t* out, size_t capacity, const uint64_t* off_ws) {
+    pdl_trigger();
+    pdl_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, l = threadIdx.x & 31;
     int lane = warp, si = 0;
     size_t ws = 0;
@@ -617,9 +644,9 @@ void launch_rans_finalize(const RansSection* secs, int nsec, uint8_t* out, size_
     P.nsec = nsec;
     int total = 0;
     for (int i = 0; i < nsec; ++i) { P.s[i] = secs[i]; total += secs[i].K; }
-    rans_finalize_kernel<<<1, kScanThreads, 0, s>>>(P, out, hdr_bytes, capacity, nbytes, offsets_ws, status);
+    (void)launch_pdl(rans_finalize_kernel, dim3(1), dim3(kScanThreads), (size_t)(0), s, P, out, hdr_bytes, capacity, nbytes, offsets_ws, status);
     const int threads = 256;
-    rans_copy_kernel<<<(unsigned)(((size_t)total * 32 + threads - 1) / threads), threads, 0, s>>>(P, out, capacity,
+    (void)launch_pdl(rans_copy_kernel, dim3((unsigned)(((size_t)total * 32 + threads - 1) / threads)), dim3(threads), (size_t)(0), s, P, out, capacity,
                                                                                                offsets_ws);
 }
 
@@ -631,6 +658,8 @@ void launch_rans_finalize(const RansSection* secs, int nsec, uint8_t* out, size_
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kScanThreads) rans_parse_kernel(const RansDecodeJob J, size_t expect_end_host,
                                                                   const uint64_t* expect_end_dev, int* status) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ typename BlockScanU64::TempStorage tmp;
     __shared__ int bad, prior;
     if (threadIdx.x == 0) { bad = 0; prior = *status; }
@@ -675,12 +704,12 @@ __global__ void __launch_bounds__(kScanThreads) rans_parse_kernel(const RansDeco
 }
 
 void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s) {
-    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, 0, nullptr, status);
+    (void)launch_pdl(rans_parse_kernel, dim3(1), dim3(kScanThreads), (size_t)(0), s, j, 0, nullptr, status);
 }
 
 void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const uint64_t* expect_end_dev, int* status,
                               cudaStream_t s) {
-    rans_parse_kernel<<<1, kScanThreads, 0, s>>>(j, expect_end, expect_end_dev, status);
+    (void)launch_pdl(rans_parse_kernel, dim3(1), dim3(kScanThreads), (size_t)(0), s, j, expect_end, expect_end_dev, status);
 }
 
 // rANS decode.  Each thread runs LPT lanes (g, g + G, ... with G = ceil(K / LPT)), their steps interleaved
@@ -699,6 +728,8 @@ __global__ void __launch_bounds__(kRansThreadsDec) rans_decode_kernel(const Rans
     const uint32_t* runs = reinterpret_cast<const uint32_t*>(coarse + kBins * kCoarse);  // A | B << 16
     __shared__ uint64_t bar;
     if (!load_tables(tab, tables, coarse, coarse_g, &bar, status)) return;
+    pdl_trigger();  // the tables above are constants: loaded while the previous kernel finishes
+    pdl_wait();
     if (*(volatile int*)status != 0) return;
     const int K = J.K, G = (K + LPT - 1) / LPT;
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -852,12 +883,10 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
         attr = true;
     }
     if (j.idx_period) {
-        rans_decode_kernel<1, true><<<(j.K + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(
-            j, packed_tables, coarse, status);
+        (void)launch_pdl(rans_decode_kernel<1, true>, dim3((j.K + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status);
     } else {
         const int G = (j.K + kRansDecLPT - 1) / kRansDecLPT;
-        rans_decode_kernel<kRansDecLPT, false><<<(G + kRansThreadsDec - 1) / kRansThreadsDec, kRansThreadsDec, smem, s>>>(
-            j, packed_tables, coarse, status);
+        (void)launch_pdl(rans_decode_kernel<kRansDecLPT, false>, dim3((G + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status);
     }
 }
 
@@ -866,6 +895,8 @@ __global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __
                                const float* __restrict__ qstep_all, const int* __restrict__ qp_dev,
                                float* __restrict__ yf, __nv_bfloat16* __restrict__ yb, uint8_t* __restrict__ y8,
                                float inv8) {
+    pdl_trigger();
+    pdl_wait();
     const float q = qstep_all[*qp_dev];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float v = __fadd_rn(__fmul_rn((float)rhat[i], q), mu[i]);
@@ -877,7 +908,7 @@ __global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __
 
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
                     float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8, float inv8) {
-    dequant_kernel<<<grid_for(n, 256), 256, 0, s>>>(rhat, mu, n, qstep_all, qp_dev, yf, yb, y8, inv8);
+    (void)launch_pdl(dequant_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, rhat, mu, n, qstep_all, qp_dev, yf, yb, y8, inv8);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -885,6 +916,8 @@ void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float*
 // ------------------------------------------------------------------------------------------------
 __global__ void write_header_kernel(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz,
                                     const uint8_t* iz, int Cz, size_t capacity, int* status) {
+    pdl_trigger();
+    pdl_wait();
     const size_t hdr = (20 + (size_t)Cz + 3) & ~(size_t)3;
     if (hdr > capacity) {
         if (threadIdx.x == 0) set_status(status, UFVC_ERR_CAPACITY);
@@ -908,11 +941,13 @@ __global__ void write_header_kernel(uint8_t* out, int arch, int N, int qp, int W
 
 void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,
                          int Cz, size_t capacity, int* status, cudaStream_t s) {
-    write_header_kernel<<<1, 256, 0, s>>>(out, arch, N, qp, W, H, K, Kz, iz, Cz, capacity, status);
+    (void)launch_pdl(write_header_kernel, dim3(1), dim3(256), (size_t)(0), s, out, arch, N, qp, W, H, K, Kz, iz, Cz, capacity, status);
 }
 
 __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, int N, int W, int H, int K, int Kz,
                                     int Cz, int* qp_dev, uint8_t* iz, int* status) {
+    pdl_trigger();
+    pdl_wait();
     if (threadIdx.x != 0) return;
     const size_t hdr = (20 + (size_t)Cz + 3) & ~(size_t)3;
     *qp_dev = 32;
@@ -935,7 +970,7 @@ __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, i
 
 void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
                          int* qp_dev, uint8_t* iz, int* status, cudaStream_t s) {
-    parse_header_kernel<<<1, 32, 0, s>>>(bits, nbytes, arch, N, W, H, K, Kz, Cz, qp_dev, iz, status);
+    (void)launch_pdl(parse_header_kernel, dim3(1), dim3(32), (size_t)(0), s, bits, nbytes, arch, N, W, H, K, Kz, Cz, qp_dev, iz, status);
 }
 
 }  // namespace ufvc

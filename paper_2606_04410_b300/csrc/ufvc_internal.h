@@ -14,6 +14,32 @@
 
 namespace ufvc {
 
+#ifdef __CUDACC__
+// Programmatic dependent launch.  Kernels of the coding path are launched with programmatic stream
+// serialization (launch_pdl): a kernel's CTAs may start while the previous kernel of the stream finishes,
+// so its set-up overlaps that kernel's tail.  Every such kernel calls pdl_wait() before it reads anything
+// an earlier kernel wrote or writes anything an earlier kernel reads (pdl_wait returns once the previous
+// kernel has completed and its writes are visible), and pdl_trigger() to let the next kernel start.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+#endif
+
 constexpr int kBins = 64;          // scale bins s_k, k = 0..63, log-spaced on [0.11, 64]
 constexpr int kRmax = 255;         // |r^| <= 255
 constexpr int kNsym = 511;         // symbols -255..255
