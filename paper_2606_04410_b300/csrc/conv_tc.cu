@@ -956,6 +956,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue: one output row at a time
+        // Each P row is read from TMEM once, right when it is complete, and its TMEM buffer released at
+        // once: P row j holds the ky = 0 taps of output row j + 1, ky = 1 of row j and ky = 2 of row j - 1,
+        // so three running tap sums (SA: output j - 1, SB: j, SC: j + 1) take its 27 values, and output
+        // j - 1 is finished after row j (taps added in row order, ky = 0, 1, 2).
         const int q = warp & 3, k = (warp - 2) >> 2;
         const bool elected = OUTK != 0 && warp == 2 && lane == 0;
         const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + 32 * k;
@@ -969,32 +973,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float b0 = bias[0], b1 = bias[1], b2 = bias[2];
             const int xo = strip * kFinStrip + 30 * q + lane - 1;
             const bool xvalid = lane >= 1 && lane <= 30 && xo < p.Wo;
-            for (int y = ya; y <= yb; ++y) {
-                const int hi = min(y + 1, Ho - 1);
-                while (waited <= pr + (hi - r0)) {  // P rows up to y + 1 are in TMEM
-                    if (!__all_sync(0xffffffffu, wait_bar(&tfull[waited % NACC], (waited / NACC) & 1, abort_flag,
-                                                          p.err))) { ok = false; break; }
-                    ++waited;
-                }
-                if (!ok) break;
-                ptx::tc_fence_after();
-                float S[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) S[i] = 0.f;
-#pragma unroll
-                for (int ky = 0; ky < 3; ++ky) {
-                    const int row = y + ky - 1;
-                    if (row < 0 || row >= Ho) continue;
-                    float v[32];
-                    tmem_ld32(lane_base + ((pr + row - r0) % NACC) * 128, v);
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) S[i] += v[9 * ky + i];
-                }
-                // P row y - 1 is not needed by later outputs of this run
-                if (y - 1 >= r0) {
-                    ptx::tc_fence_before();
-                    ptx::mbar_arrive(&tempty[(pr + y - 1 - r0) % NACC]);
-                }
+            // output row y from its nine tap sums S (kx-major within each channel's 9)
+            auto emit = [&](int y, const float* S) -> bool {
                 float outv[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
@@ -1020,10 +1000,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ptx::bulk_wait_read0();
                             ptx::mbar_arrive(cfree);
                         }
-                        if (!__all_sync(0xffffffffu, wait_bar(cfree, (o - 1) & 1, abort_flag, p.err))) {
-                            ok = false;
-                            break;
-                        }
+                        if (!__all_sync(0xffffffffu, wait_bar(cfree, (o - 1) & 1, abort_flag, p.err))) return false;
                     }
                     if (xvalid) {
 #pragma unroll
@@ -1041,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (warp == 2) {
                         bool w_ok = true;
                         if (lane == 0) w_ok = wait_bar(cwritten, o & 1, abort_flag, p.err);
-                        if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) { ok = false; break; }
+                        if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) return false;
                     }
                     if (elected) {
 #pragma unroll
@@ -1052,13 +1029,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     ++o;
                 }
+                return true;
+            };
+            float SA[9], SB[9], SC[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) { SA[i] = 0.f; SB[i] = 0.f; }
+            for (int j = r0; j <= r1; ++j) {
+                while (waited <= pr + (j - r0)) {  // P row j is in TMEM
+                    if (!__all_sync(0xffffffffu, wait_bar(&tfull[waited % NACC], (waited / NACC) & 1, abort_flag,
+                                                          p.err))) { ok = false; break; }
+                    ++waited;
+                }
+                if (!ok) break;
+                ptx::tc_fence_after();
+                float v[32];
+                tmem_ld32(lane_base + ((pr + j - r0) % NACC) * 128, v);
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&tempty[(pr + j - r0) % NACC]);  // the row is in registers
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    SA[i] += v[18 + i];
+                    SB[i] += v[9 + i];
+                    SC[i] = v[i];
+                }
+                if (j - 1 >= ya && !emit(j - 1, SA)) { ok = false; break; }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) { SA[i] = SB[i]; SB[i] = SC[i]; }
             }
             if (!ok) break;
-            // rows yb .. r1 of this run are released now
-            for (int row = max(yb, r0); row <= r1; ++row) {
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(&tempty[(pr + row - r0) % NACC]);
-            }
+            if (r1 == yb && !emit(yb, SA)) { ok = false; break; }  // the image's last row has no row below
             pr += r1 - r0 + 1;
             t = te;
         }
