@@ -50,6 +50,10 @@ def lib() -> C.CDLL:
         _lib.orc_qstep.argtypes = [C.c_int]
         _lib.orc_weight_count.restype = C.c_size_t
         _lib.orc_weight_count.argtypes = [C.c_int, C.c_int]
+        _lib.orc_mean_weight_count.restype = C.c_size_t
+        _lib.orc_mean_weight_count.argtypes = [C.c_int]
+        _lib.orc_partition.restype = C.c_int
+        _lib.orc_partition.argtypes = [C.c_int] * 4
         _lib.orc_rans_encode.restype = C.c_size_t
     return _lib
 
@@ -191,15 +195,63 @@ def quantize_z(z: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return zhat, iz
 
 
-def hyper_synthesis(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, weights: np.ndarray):
+def hyper_synthesis(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, weights: np.ndarray,
+                    want_s: bool = False):
+    """-> (mu, log sigma), or with want_s (mu, log sigma, s): s = the S2 feature map [Hy][Wy][Cz], the
+    prior of the progressive mean steps."""
     zhat = np.ascontiguousarray(zhat, np.int16)
     Hz, Wz, _ = zhat.shape
-    cy = {0: 128, 1: 256}[arch]
+    cy, cz = {0: (128, 64), 1: (256, 128)}[arch]
     mu = np.empty((Hy, Wy, cy), np.float64)
     ls = np.empty((Hy, Wy, cy), np.float64)
-    _check(lib().orc_hyper_synthesis(arch, N, _p(zhat), Hz, Wz, Hy, Wy, _p(weights), _p(mu), _p(ls)),
+    sp = np.empty((Hy, Wy, cz), np.float64)
+    _check(lib().orc_hyper_synthesis_s(arch, N, _p(zhat), Hz, Wz, Hy, Wy, _p(weights), _p(mu), _p(ls), _p(sp)),
            "hyper_synthesis")
-    return mu, ls
+    return (mu, ls, sp) if want_s else (mu, ls)
+
+
+# ---------------------------------------------------------------- progressive means (Sec. 3.4)
+def mean_weight_count(arch: int) -> int:
+    return int(lib().orc_mean_weight_count(arch))
+
+
+def partition(h: int, w: int, c: int, cy: int) -> int:
+    return int(lib().orc_partition(h, w, c, cy))
+
+
+def partition_map(Hy: int, Wy: int, cy: int) -> np.ndarray:
+    """[Hy][Wy][Cy] uint8: the partition (0..3) of each latent element."""
+    out = np.empty((Hy, Wy, cy), np.uint8)
+    lib().orc_partition_map(Hy, Wy, cy, _p(out))
+    return out
+
+
+def mean_step(arch: int, k: int, yhat: np.ndarray, s: np.ndarray, mean_weights: np.ndarray) -> np.ndarray:
+    """mu^k (k = 1..3) from yhat restricted to partitions < k and the prior s."""
+    yhat = np.ascontiguousarray(yhat, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    mw = np.ascontiguousarray(mean_weights, np.float32)
+    Hy, Wy, cy = yhat.shape
+    mu = np.empty((Hy, Wy, cy), np.float64)
+    _check(lib().orc_mean_step(arch, k, _p(yhat), _p(s), Hy, Wy, _p(mw), _p(mu)), "mean_step")
+    return mu
+
+
+def progressive_means(arch: int, y: np.ndarray | None, rhat: np.ndarray, mu0: np.ndarray, s: np.ndarray, qp: int,
+                      mean_weights: np.ndarray):
+    """The four partition steps.  Encoder (y given): -> (rhat, yhat, mu_used) with rhat recomputed on
+    partitions 1..3; decoder (y None): rhat is the decoded one."""
+    mu0 = np.ascontiguousarray(mu0, np.float64)
+    s = np.ascontiguousarray(s, np.float64)
+    mw = np.ascontiguousarray(mean_weights, np.float32)
+    rh = np.array(rhat, dtype=np.int16, order="C", copy=True)
+    Hy, Wy, _ = mu0.shape
+    yhat = np.empty(mu0.shape, np.float64)
+    mu_used = np.empty(mu0.shape, np.float64)
+    yy = None if y is None else np.ascontiguousarray(y, np.float64)
+    _check(lib().orc_progressive_means(arch, _p(yy) if yy is not None else None, _p(rh), _p(mu0), _p(s), Hy, Wy,
+                                       qp, _p(mw), _p(yhat), _p(mu_used)), "progressive_means")
+    return rh, yhat, mu_used
 
 
 def quantize_y(y: np.ndarray, mu: np.ndarray, logsig: np.ndarray, qp: int):
@@ -227,11 +279,14 @@ def synthesis(arch: int, N: int, yhat: np.ndarray, H: int, W: int, weights: np.n
 
 
 class _Debug(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("y", "z", "zhat", "iz", "mu", "logsig", "rhat", "idx")]
+    _fields_ = [(n, C.c_void_p) for n in ("y", "z", "zhat", "iz", "mu", "logsig", "rhat", "idx", "s", "yhat")]
 
 
-def encode_chunk(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.ndarray, debug: bool = False):
-    """-> bit-stream bytes (and, with debug, a dict of every intermediate)."""
+def encode_chunk(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.ndarray, debug: bool = False,
+                 mean_weights: np.ndarray | None = None):
+    """-> bit-stream bytes (and, with debug, a dict of every intermediate).  With mean_weights the
+    stream is version 2 (progressive means on partitions 1..3; debug "mu" is the mean each element was
+    coded with)."""
     frames = np.ascontiguousarray(frames, np.uint8)
     N, H, W, _ = frames.shape
     d = latent_dims(arch, H, W)
@@ -247,9 +302,12 @@ def encode_chunk(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.nda
                     zhat=np.empty((d["Hz"], d["Wz"], d["Cz"]), np.int16), iz=np.empty(d["Cz"], np.uint8),
                     mu=np.empty((d["Hy"], d["Wy"], d["Cy"])), logsig=np.empty((d["Hy"], d["Wy"], d["Cy"])),
                     rhat=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.int16),
-                    idx=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.uint8))
+                    idx=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.uint8),
+                    s=np.empty((d["Hy"], d["Wy"], d["Cz"])), yhat=np.empty((d["Hy"], d["Wy"], d["Cy"])))
         dbg = _Debug(**{k: v.ctypes.data for k, v in arrs.items()})
-    rc = lib().orc_encode_chunk(arch, N, _p(frames), H, W, qp, K, _p(weights), _p(out), C.c_size_t(cap),
+    mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
+    rc = lib().orc_encode_chunk(arch, N, _p(frames), H, W, qp, K, _p(weights), _p(mw) if mw is not None else None,
+                                _p(out), C.c_size_t(cap),
                                 C.byref(nbytes), C.byref(dbg) if dbg is not None else None)
     _check(rc, "encode_chunk")
     bits = out[:nbytes.value].tobytes()
@@ -257,13 +315,15 @@ def encode_chunk(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.nda
 
 
 def decode_chunk(arch: int, N: int, bits: bytes, H: int, W: int, weights: np.ndarray,
-                 want_frames: bool = True):
+                 want_frames: bool = True, mean_weights: np.ndarray | None = None):
     """-> (frames [N][H][W][3] float64 in [0,1] or None, yhat [Hy][Wy][Cy])."""
     d = latent_dims(arch, H, W)
     a = np.frombuffer(bits, np.uint8).copy()
     yhat = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
     frames = np.empty((N, H, W, 3), np.float64) if want_frames else None
+    mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
     rc = lib().orc_decode_chunk(arch, N, _p(a), C.c_size_t(len(bits)), H, W, _p(weights),
+                                _p(mw) if mw is not None else None,
                                 _p(frames) if want_frames else None, _p(yhat))
     _check(rc, "decode_chunk")
     return frames, yhat

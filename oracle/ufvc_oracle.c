@@ -301,8 +301,8 @@ int orc_quantize_z(const double* z, int npos, int cz, int16_t* zhat, uint8_t* iz
 /* Hyper-synthesis (single-step parameter estimation, Sec. 3.4): from z^ alone, one pass gives mu and
  * log sigma for every latent element.  S1, S2: 3x3 conv Cz -> 4Cz, pixel shuffle x2, GELU; crop to
  * (Hy, Wy); S3: 1x1 conv Cz -> 2Cy; channels [0, Cy) are mu, [Cy, 2Cy) are log sigma. */
-int orc_hyper_synthesis(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
-                        const float* wts, double* mu, double* logsig) {
+int orc_hyper_synthesis_s(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
+                          const float* wts, double* mu, double* logsig, double* s_out) {
     arch_t a;
     if (get_arch(arch, &a) || 4 * Hz < Hy || 4 * Wz < Wy) return ORC_ERR_ARG;
     const float *wk, *bk;
@@ -333,8 +333,16 @@ int orc_hyper_synthesis(int arch, int N, const int16_t* zhat, int Hz, int Wz, in
         memcpy(mu + i * a.cy, p + i * 2 * a.cy, sizeof(double) * a.cy);
         memcpy(logsig + i * a.cy, p + i * 2 * a.cy + a.cy, sizeof(double) * a.cy);
     }
+    if (s_out) memcpy(s_out, s2c, sizeof(double) * Hy * Wy * cz);
     free(zd); free(t); free(s1); free(t2); free(s2); free(s2c); free(p);
     return ORC_OK;
+}
+
+/* The same pass without the feature map.  s_out of orc_hyper_synthesis_s, when not NULL, receives the
+ * S2 output s = [Hy][Wy][Cz] (after GELU and crop): the prior that the progressive mean steps read. */
+int orc_hyper_synthesis(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
+                        const float* wts, double* mu, double* logsig) {
+    return orc_hyper_synthesis_s(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, logsig, NULL);
 }
 
 /* Latent quantisation at rate qp: r^ = clamp(rint((y - mu) / q), -255, 255) and the scale index
@@ -365,6 +373,123 @@ int orc_scale_index(const double* logsig, size_t n, int qp, uint8_t* idx) {
         for (int j = 0; j < NBINS - 1; j++) k += (double)thr[j] < logsig[i];
         idx[i] = (uint8_t)k;
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* Progressive means (Sec. 3.4, Fig. 4a and 4c)                                                      */
+/* ------------------------------------------------------------------------------------------------ */
+/* The latent is split into four partitions, quadtree-like in space and channel.  The parameter
+ * network gives the scales of ALL four partitions and the means of partition 0 in one pass (the
+ * hyper-synthesis above: mu^0 and log sigma); the means of partitions 1, 2, 3 are then estimated one
+ * partition at a time, each from the partitions already reconstructed.  The bit-stream depends on the
+ * scales only, so the whole latent is still entropy coded in one step.
+ *
+ * Reading of the partition (the paper shows it only as a figure): channels are split into four
+ * consecutive groups g = c / (Cy / 4); inside each 2x2 spatial block the position t = 2 (h mod 2) +
+ * (w mod 2); element (h, w, c) belongs to partition (t + g) mod 4.  Every partition thus holds one
+ * position of every 2x2 block in every channel group, a different one per group. */
+int orc_partition(int h, int w, int c, int cy) {
+    int g = c / (cy / 4);
+    int t = 2 * (h % 2) + (w % 2);
+    return (t + g) % 4;
+}
+
+void orc_partition_map(int Hy, int Wy, int cy, uint8_t* out) {
+    for (int h = 0; h < Hy; h++)
+        for (int w = 0; w < Wy; w++)
+            for (int c = 0; c < cy; c++) out[((size_t)h * Wy + w) * cy + c] = (uint8_t)orc_partition(h, w, c, cy);
+}
+
+/* Reading of the mean-estimation network of step k = 1..3 (figure only in the paper): its input is the
+ * reconstructed latent restricted to partitions 0..k-1 (zero elsewhere), Cy channels, followed by the
+ * prior s, Cz channels; Pk_a: 3x3 conv (Cy + Cz -> Cz) + GELU; Pk_b: 1x1 conv (Cz -> Cy) gives mu^k.
+ * Blob (separate from the codec's): P1a, P1b, P2a, P2b, P3a, P3b, each kernel [Cout][k][k][Cin] then
+ * bias [Cout]. */
+int orc_mean_layer_shape(int arch, int l, int* cout, int* k, int* cin) {
+    arch_t a;
+    if (get_arch(arch, &a) || l < 0 || l >= 6) return ORC_ERR_ARG;
+    if (l % 2 == 0) { *cout = a.cz; *k = 3; *cin = a.cy + a.cz; }
+    else            { *cout = a.cy; *k = 1; *cin = a.cz; }
+    return ORC_OK;
+}
+
+size_t orc_mean_weight_count(int arch) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < 6; l++) {
+        if (orc_mean_layer_shape(arch, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
+static void mean_layer_ptr(int arch, const float* blob, int l, const float** w, const float** b) {
+    size_t off = 0;
+    int co, k, ci;
+    for (int i = 0; i < l; i++) {
+        orc_mean_layer_shape(arch, i, &co, &k, &ci);
+        off += (size_t)co * k * k * ci + co;
+    }
+    orc_mean_layer_shape(arch, l, &co, &k, &ci);
+    *w = blob + off;
+    *b = blob + off + (size_t)co * k * k * ci;
+}
+
+/* Step k (1..3): mu_k [Hy][Wy][Cy] from yhat (only its partitions < k are read) and s [Hy][Wy][Cz]. */
+int orc_mean_step(int arch, int k, const double* yhat, const double* s, int Hy, int Wy, const float* pm,
+                  double* mu_k) {
+    arch_t a;
+    if (get_arch(arch, &a) || k < 1 || k > 3 || a.cy % 4) return ORC_ERR_ARG;
+    const int cin = a.cy + a.cz;
+    const size_t npix = (size_t)Hy * Wy;
+    double* in = dalloc(npix * cin);
+    for (int h = 0; h < Hy; h++)
+        for (int w = 0; w < Wy; w++) {
+            size_t pix = (size_t)h * Wy + w;
+            for (int c = 0; c < a.cy; c++)
+                in[pix * cin + c] = orc_partition(h, w, c, a.cy) < k ? yhat[pix * a.cy + c] : 0.0;
+            for (int c = 0; c < a.cz; c++) in[pix * cin + a.cy + c] = s[pix * a.cz + c];
+        }
+    const float *wk, *bk;
+    double* t = dalloc(npix * a.cz);
+    mean_layer_ptr(arch, pm, 2 * (k - 1), &wk, &bk);
+    orc_conv2d(in, Hy, Wy, cin, wk, bk, a.cz, 3, 1, t);
+    gelu_inplace(t, npix * a.cz);
+    mean_layer_ptr(arch, pm, 2 * (k - 1) + 1, &wk, &bk);
+    orc_conv2d(t, Hy, Wy, a.cz, wk, bk, a.cy, 1, 1, mu_k);
+    free(in); free(t);
+    return ORC_OK;
+}
+
+/* The four steps, in the paper's order.  Encoder (y != NULL): for partition 0, r^ = clamp(rint((y -
+ * mu^0) / q)); then for k = 1..3, mu^k from the partitions before k and, on partition k, r^ =
+ * clamp(rint((y - mu^k) / q)).  Decoder (y == NULL): rhat is given (decoded in one step) and only the
+ * reconstruction runs.  Both: y^ = r^ q + mu on each partition with that partition's mean, so the
+ * decoder repeats the encoder's means exactly.  mu_used[i] receives the mean element i was coded with
+ * (mu^0 on partition 0, mu^k on partition k); yhat receives the reconstructed latent. */
+int orc_progressive_means(int arch, const double* y, int16_t* rhat, const double* mu0, const double* s, int Hy,
+                          int Wy, int qp, const float* pm, double* yhat, double* mu_used) {
+    arch_t a;
+    if (get_arch(arch, &a) || qp < 0 || qp > 63 || !pm || a.cy % 4) return ORC_ERR_ARG;
+    const double q = orc_qstep(qp);
+    const size_t ny = (size_t)Hy * Wy * a.cy;
+    double* muk = dalloc(ny);
+    for (size_t i = 0; i < ny; i++) yhat[i] = 0.0;
+    for (int k = 0; k < 4; k++) {
+        if (k > 0) orc_mean_step(arch, k, yhat, s, Hy, Wy, pm, muk);
+        for (int h = 0; h < Hy; h++)
+            for (int w = 0; w < Wy; w++)
+                for (int c = 0; c < a.cy; c++) {
+                    if (orc_partition(h, w, c, a.cy) != k) continue;
+                    size_t i = ((size_t)h * Wy + w) * a.cy + c;
+                    double m = k == 0 ? mu0[i] : muk[i];
+                    if (y) rhat[i] = (int16_t)clampd(rint((y[i] - m) / q), -RMAX, RMAX);
+                    yhat[i] = rhat[i] * q + m;
+                    mu_used[i] = m;
+                }
+    }
+    free(muk);
     return ORC_OK;
 }
 
@@ -561,9 +686,11 @@ int orc_synthesis(int arch, int N, const double* yhat, int Hy, int Wy, int H, in
 /* ------------------------------------------------------------------------------------------------ */
 /* Whole chunk: encode and decode with the bit-stream container                                     */
 /* ------------------------------------------------------------------------------------------------ */
-/* Container (little-endian): "UFVC", u8 version = 1, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K,
+/* Container (little-endian): "UFVC", u8 version, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K,
  * u32 Kz, Cz bytes iz[c]; zero-padded to a multiple of 4; then the z^ section (Kz lanes, Kz = min(K,
- * n_z)), then the y^ section (K lanes).  Both sections as in orc_rans_encode. */
+ * n_z)), then the y^ section (K lanes).  Both sections as in orc_rans_encode.  Version 1: every mean
+ * comes from the single parameter pass; version 2: partitions 1..3 take the progressive means
+ * (orc_progressive_means), which the decoder must then repeat with the same mean-network weights. */
 
 static void put16(uint8_t* p, uint32_t v) { p[0] = v & 0xFF; p[1] = (v >> 8) & 0xFF; }
 static void put32(uint8_t* p, uint32_t v) { put16(p, v & 0xFFFF); put16(p + 2, v >> 16); }
@@ -579,6 +706,8 @@ typedef struct {
     double* logsig;
     int16_t* rhat;
     uint8_t* idx;
+    double* s;        /* [Hy][Wy][Cz] prior of the mean steps */
+    double* yhat;     /* [Hy][Wy][Cy] the encoder's reconstruction */
 } orc_debug;
 
 int orc_latent_dims(int arch, int H, int W, int* Hy, int* Wy, int* Hz, int* Wz, int* Cy, int* Cz) {
@@ -592,8 +721,9 @@ int orc_latent_dims(int arch, int H, int W, int* Hy, int* Wy, int* Hz, int* Wz, 
     return ORC_OK;
 }
 
+/* pm: the mean-network blob (version-2 stream with progressive means), or NULL (version 1). */
 int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int qp, int K, const float* wts,
-                     uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg) {
+                     const float* pm, uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg) {
     int Hy, Wy, Hz, Wz, Cy, Cz;
     if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz) || N < 1 || N > 255 || qp < 0 || qp > 63 ||
         K < 1 || W > 65535 || H > 65535)
@@ -610,20 +740,32 @@ int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int q
     uint8_t* zidx = (uint8_t*)malloc(nz);
     uint32_t* freq = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * NSYM);
     uint32_t* cum = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * (NSYM + 1));
+    double* sp = dalloc((size_t)Hy * Wy * Cz);
+    double* yh = dalloc(ny);
     int rc = ORC_OK;
     orc_build_tables(freq, cum);
     orc_analysis(arch, N, frames, H, W, wts, y);
     orc_hyper_analysis(arch, N, y, Hy, Wy, wts, z);
     orc_quantize_z(z, Hz * Wz, Cz, zhat, iz);
-    orc_hyper_synthesis(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls);
+    orc_hyper_synthesis_s(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls, sp);
     orc_quantize_y(y, mu, ls, ny, qp, rhat, idx);
+    if (pm) {
+        double* mu0 = dalloc(ny);
+        memcpy(mu0, mu, sizeof(double) * ny);
+        rc = orc_progressive_means(arch, y, rhat, mu0, sp, Hy, Wy, qp, pm, yh, mu);
+        free(mu0);
+        if (rc) goto done;
+    } else {
+        double q = orc_qstep(qp);
+        for (size_t i = 0; i < ny; i++) yh[i] = rhat[i] * q + mu[i];
+    }
     for (size_t i = 0; i < nz; i++) zidx[i] = iz[i % Cz];
     size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
     int Kz = (size_t)K < nz ? K : (int)nz;
     if (cap < hdr) { rc = ORC_ERR_CAPACITY; goto done; }
     memset(out, 0, hdr);
     memcpy(out, "UFVC", 4);
-    out[4] = 1; out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
+    out[4] = pm ? 2 : 1; out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
     put16(out + 8, (uint32_t)W); put16(out + 10, (uint32_t)H);
     put32(out + 12, (uint32_t)K); put32(out + 16, (uint32_t)Kz);
     memcpy(out + 20, iz, Cz);
@@ -641,21 +783,26 @@ int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int q
         if (dbg->logsig) memcpy(dbg->logsig, ls, sizeof(double) * ny);
         if (dbg->rhat) memcpy(dbg->rhat, rhat, 2 * ny);
         if (dbg->idx) memcpy(dbg->idx, idx, ny);
+        if (dbg->s) memcpy(dbg->s, sp, sizeof(double) * Hy * Wy * Cz);
+        if (dbg->yhat) memcpy(dbg->yhat, yh, sizeof(double) * ny);
     }
 done:
     free(y); free(z); free(zhat); free(mu); free(ls); free(rhat); free(idx); free(zidx); free(freq); free(cum);
+    free(sp); free(yh);
     return rc;
 }
 
 /* Decode: parse the container, decode z^ (single step), hyper-synthesis -> mu, log sigma -> indices,
- * decode r^ for the whole latent in one step, y^ = r^ q + mu, then the N frame-specific decoders.
+ * decode r^ for the whole latent in one step, y^ = r^ q + mu (version 2: the progressive means, which
+ * need the mean-network blob pm), then the N frame-specific decoders.
  * frames_out: [N][H][W][3] doubles in [0, 1]; yhat_out (optional): [Hy][Wy][Cy]. */
 int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H, int W, const float* wts,
-                     double* frames_out, double* yhat_out) {
+                     const float* pm, double* frames_out, double* yhat_out) {
     int Hy, Wy, Hz, Wz, Cy, Cz;
     if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz)) return ORC_ERR_ARG;
     size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
-    if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] != 1) return ORC_ERR_CORRUPT;
+    if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] < 1 || bits[4] > 2) return ORC_ERR_CORRUPT;
+    if (bits[4] == 2 && !pm) return ORC_ERR_ARG;
     if (bits[5] != arch || bits[6] != N || get16(bits + 8) != (uint32_t)W || get16(bits + 10) != (uint32_t)H)
         return ORC_ERR_ARG;
     int qp = bits[7];
@@ -675,22 +822,28 @@ int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H,
     uint8_t* idx = (uint8_t*)malloc(ny);
     int16_t* rhat = (int16_t*)malloc(2 * ny);
     double* yhat = dalloc(ny);
+    double* sp = dalloc((size_t)Hy * Wy * Cz);
     size_t used1 = 0, used2 = 0;
     int rc = orc_rans_decode(bits + hdr, nbytes - hdr, zidx, nz, Kz, freq, cum, NSYM, RMAX, zhat, &used1);
     if (rc) goto done;
-    orc_hyper_synthesis(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls);
+    orc_hyper_synthesis_s(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls, sp);
     orc_scale_index(ls, ny, qp, idx);
     rc = orc_rans_decode(bits + hdr + used1, nbytes - hdr - used1, idx, ny, K, freq, cum, NSYM, RMAX, rhat, &used2);
     if (rc) goto done;
     if (hdr + used1 + used2 != nbytes) { rc = ORC_ERR_CORRUPT; goto done; }
-    {
+    if (bits[4] == 2) {
+        double* mu_used = dalloc(ny);
+        rc = orc_progressive_means(arch, NULL, rhat, mu, sp, Hy, Wy, qp, pm, yhat, mu_used);
+        free(mu_used);
+        if (rc) goto done;
+    } else {
         double q = orc_qstep(qp);
         for (size_t i = 0; i < ny; i++) yhat[i] = rhat[i] * q + mu[i];
     }
     if (yhat_out) memcpy(yhat_out, yhat, sizeof(double) * ny);
     if (frames_out) orc_synthesis(arch, N, yhat, Hy, Wy, H, W, wts, frames_out);
 done:
-    free(freq); free(cum); free(zhat); free(zidx); free(mu); free(ls); free(idx); free(rhat); free(yhat);
+    free(freq); free(cum); free(zhat); free(zidx); free(mu); free(ls); free(idx); free(rhat); free(yhat); free(sp);
     return rc;
 }
 

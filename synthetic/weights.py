@@ -65,3 +65,34 @@ def split_weights(blob: np.ndarray, arch: int, n_frames: int) -> dict[str, tuple
         off += n + co
     assert off == blob.size
     return out
+
+
+def mean_layer_table(arch: int) -> list[tuple[str, int, int, int]]:
+    """[(name, Cout, k, Cin)] of the progressive-mean blob."""
+    a = ARCHS[arch]
+    cy, cz = a["cy"], a["cz"]
+    t = []
+    for k in (1, 2, 3):
+        t += [(f"P{k}a", cz, 3, cy + cz), (f"P{k}b", cy, 1, cz)]
+    return t
+
+
+def draw_mean_weights(arch: int, seed: int = 0, bias_std: float = 0.01) -> np.ndarray:
+    """Flat float32 blob of the progressive-mean layers, N(0, 2/fan_in) kernels (own random stream)."""
+    rng = np.random.default_rng([seed, 4])
+    parts = []
+    for _, co, k, ci in mean_layer_table(arch):
+        fan_in = k * k * ci
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
+        parts.append(rng.normal(0.0, bias_std, size=co).astype(np.float32))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def split_mean_weights(blob: np.ndarray, arch: int) -> dict[str, tuple[np.ndarray, np.ndarray]]:
+    out, off = {}, 0
+    for name, co, k, ci in mean_layer_table(arch):
+        n = co * k * k * ci
+        out[name] = (blob[off:off + n].reshape(co, k, k, ci), blob[off + n:off + n + co])
+        off += n + co
+    assert off == blob.size
+    return out
