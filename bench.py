@@ -203,7 +203,7 @@ def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, r
 # DRAM bytes per 1080p launch from one ncu capture of the SAME kernel build (dram__bytes_read.sum +
 # dram__bytes_write.sum on the 960x544 chunk, scaled by the 4x pixel count): profiles/<kernel>_<layer>_960x544.md.
 # An entry must be removed when its kernel changes.
-NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.866624e6 + 73.490944e6), "dec.U3": 4 * (138.87104e6 + 6.404864e6)}
+NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.866624e6 + 73.490944e6), "dec.U3": 4 * (138.866688e6 + 6.584832e6)}
 
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
 
@@ -424,7 +424,7 @@ def main() -> None:
                 "frac": cbytes[k] / t / 1e9 / hbm, "algorithmic": cbytes[k], "ms": conv_stages[k]}
 
     stages = {k: stage_roof(k) for k in conv_stages}
-    kern = {"dec.U3": "conv_tc_halo_kernel<16,3,2>", "dec.R2": "conv_tc_halo_kernel<64,2,1>"}
+    kern = {"dec.U3": "conv_tc_final_kernel<1>", "dec.R2": "conv_tc_halo_kernel<64,2,1>"}
     tr = stages[top]
     dec_conv_ms = sum(v for k, v in stage_total_ms.items() if k in flops)
     roofline = {"bound": tr["bound"], "kernel": (kern.get(top, "conv_tc_kernel") if args.precision != "fp32"
