@@ -5,7 +5,7 @@ scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
                     [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
-                    [--no-serving] [--serving-window S]
+                    [--no-serving] [--no-fp8] [--no-pm] [--serving-window S]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
 it under the same methodology and reported with the PSNR and bitrate deltas.  Extra keys: the decoder
@@ -356,6 +356,7 @@ def main() -> None:
     ap.add_argument("--no-entropy-sweep", action="store_true")
     ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-pm", action="store_true", help="skip the progressive-means variant")
     ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -466,6 +467,25 @@ def main() -> None:
                                      sorted(r8["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}}
         c8.close()
 
+    # ---- the four-partition progressive means (BF16, same methodology): the paper's full entropy model,
+    #      scales still from one pass so the stream is still coded in one step
+    pm = None
+    if args.precision == "bf16" and not args.no_pm:
+        cpm = U.Codec(1, N, K, blob, "bf16", device=local, mean_weights=synthetic.draw_mean_weights(1, seed=0))
+        spm = max(3, args.steps // 2)
+        rp = time_codec(cpm, fr, frames_np, W_, H_, spm, 3, True, flush)
+        vp = N * spm / (sum(a + b for a, b in zip(rp["t_enc"], rp["t_dec"])) / 1000.0)
+        stage_pm = {k: round(sum(m for m, _ in v) / spm, 4) for k, v in
+                    sorted(rp["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}
+        pm = {"value": vp, "enc_fps": N / (statistics.mean(rp["t_enc"]) / 1000.0),
+              "dec_fps": N / (statistics.mean(rp["t_dec"]) / 1000.0), "psnr_db": rp["psnr"],
+              "bytes_per_chunk": rp["nbytes"], "steps": spm,
+              "dbitrate_vs_single_pass": (rp["nbytes"] - r["nbytes"]) / r["nbytes"],
+              "dpsnr_db_vs_single_pass": rp["psnr"] - r["psnr"],
+              "progressive_means_ms_per_step": stage_pm.get("progressive_means"),
+              "stage_ms_per_step": stage_pm}
+        cpm.close()
+
     # ---- end-to-end through the host-buffer C calls (pinned host memory, copies inside the region)
     cap = r["cap"]
     h_frames = torch.from_numpy(frames_np).pin_memory()
@@ -527,6 +547,11 @@ def main() -> None:
                 fp8["dbitrate_vs_fp32"] = (fp8["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
                 fp8["speedup_vs_fp32"] = fp8["value"] / fp32["value"]
             line["fp8_path"] = fp8
+        if pm is not None:
+            if fp32 is not None:
+                pm["dbitrate_vs_fp32"] = (pm["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
+                pm["dpsnr_db_vs_fp32"] = pm["psnr_db"] - fp32["psnr_db"]
+            line["progressive_means_path"] = pm
         if not args.no_entropy_sweep:
             line["entropy_sweep"] = entropy_sweep(U, dev)
         if serving is not None:

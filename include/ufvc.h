@@ -102,7 +102,8 @@ size_t ufvc_max_bitstream_bytes(const ufvc_ctx* ctx, int width, int height);
  * qp in [0, 63] sets the quantisation step q = 2^((qp-32)/8).  The bit-stream is written to d_bits
  * (capacity bytes) and its size to *d_nbytes (device uint64).  If the stream would not fit,
  * nothing past `capacity` is written and the status word becomes UFVC_ERR_CAPACITY.
- * Bit-stream layout: "UFVC", u8 version=1, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K, u32 Kz,
+ * Bit-stream layout: "UFVC", u8 version (1; 2 with progressive means, see ufvc_set_progressive_means),
+ * u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K, u32 Kz,
  * Cz bytes of per-channel hyper-latent scale indices, zero padding to 4 bytes; then the z^ section
  * (Kz = min(K, #z^) lanes) and the y^ section (K lanes), each = K u32 lane word counts followed by
  * the lane streams (u16 words in decoding order), zero-padded to 4 bytes.  Little-endian. */
@@ -153,6 +154,38 @@ ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames, int width
  * reduction order: d_zhat int16 [Hz][Wz][Cz] -> d_mu, d_logsig float32 [Hy][Wy][Cy]. */
 ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat, int Hz, int Wz, int Hy, int Wy,
                                  float* d_mu, float* d_logsig, void* stream);
+
+/* ---- progressive means (Sec. 3.4, Fig. 4a and 4c) ----
+ * The latent is split into four partitions: channel group g = c / (Cy / 4), position t = 2 (h mod 2)
+ * + (w mod 2) in its 2x2 block, partition (t + g) mod 4 (a reading of the paper's figure).  The single
+ * parameter pass gives every scale and the means of partition 0; the means of partitions 1, 2, 3 then
+ * come one partition at a time from a small network over the partitions already reconstructed and the
+ * hyper-synthesis features s (S2's output, [Hy][Wy][Cz]):
+ *     mu^k = P_k,b(GELU(P_k,a([y^ on partitions < k, zero elsewhere ; s])))     k = 1, 2, 3
+ * with P_k,a a 3x3 convolution Cy + Cz -> Cz and P_k,b a 1x1 convolution Cz -> Cy.  Partition k is
+ * quantised with mu^k (r^ = clamp(rint((y - mu^k) / q))) and reconstructed as y^ = r^ q + mu^k.  The
+ * scales, and so the single entropy-coding step, are unchanged; the decoder repeats the steps after
+ * it and reproduces the encoder's means exactly (same kernels, same inputs). */
+
+/* Number of floats of the mean-network blob: for P1a P1b P2a P2b P3a P3b the kernel [Cout][k][k][Cin]
+ * followed by the bias [Cout]. */
+size_t ufvc_mean_weight_count(int arch);
+
+/* Give the context the mean network (host float32 blob of ufvc_mean_weight_count(arch) floats; it is
+ * uploaded, the caller keeps ownership).  From then on ufvc_encode_chunk writes version-2 streams, and
+ * the decode calls accept version 1 (single-pass means) and version 2.  A context without it reports
+ * UFVC_ERR_UNSUPPORTED (status word) for a version-2 stream.  Call once, before the context is shared
+ * (servers, clones); UFVC_ERR_ARG on a count mismatch or a second call.  The mean network runs on bf16
+ * operands on the tensor cores in BF16 and FP8 contexts and on the FP32 SIMT kernel in FP32 contexts. */
+ufvc_status ufvc_set_progressive_means(ufvc_ctx* ctx, const float* weights, size_t n_weights);
+
+/* The progressive steps alone, for tests.  Encoder form (d_y != NULL): d_y, d_mu0 float32 [Hy][Wy][Cy],
+ * d_s float32 [Hy][Wy][Cz] -> d_rhat int16 (every partition quantised with its mean), d_mu float32 (the
+ * mean each element is coded with), d_yhat float32 = r^ q + mu.  Decoder form (d_y == NULL): d_rhat_in
+ * gives r^ (copied to d_rhat).  Synchronises `stream`; needs ufvc_set_progressive_means. */
+ufvc_status ufvc_progressive_means(ufvc_ctx* ctx, const float* d_y, const int16_t* d_rhat_in, const float* d_mu0,
+                                   const float* d_s, int Hy, int Wy, int qp, int16_t* d_rhat, float* d_mu,
+                                   float* d_yhat, void* stream);
 
 /* Quantise + scale index (Sec. 3.4): r^ = clamp(rint((y - mu) / q), -255, 255) (FP32, no FMA
  * contraction), idx = #{k : thr_qp[k] < log sigma}.  n elements, all device buffers. */

@@ -86,6 +86,12 @@ struct Plan {
     __nv_bfloat16 *y_bf = nullptr, *hb_bf = nullptr;
     // decoder activations: float in FP32 precision, bf16 (same buffers, half used) otherwise
     float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
+    int* ver_dev = nullptr;  // decoder: container version of the stream being decoded
+    // progressive means, per direction: the mean network's input [Hy][Wy][Cy + Cz] and hidden layer
+    // [Hy][Wy][Cz] (float in FP32 precision, bf16 otherwise), and the step's means [Hy][Wy][Cy] (float)
+    float *pm_in_e = nullptr, *pm_h_e = nullptr, *pm_mu_e = nullptr;
+    float *pm_in_d = nullptr, *pm_h_d = nullptr, *pm_mu_d = nullptr;
+    bool pm_enc_ready = false, pm_dec_ready = false;
     bool enc_ready = false, dec_ready = false;
     std::vector<void*> allocs;
     Workspace ws_enc, ws_dec;
@@ -113,6 +119,10 @@ struct ufvc_ctx {
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
     // taps regrouped by 2x2 super-pixel; weight rows [64][tap][sub-pixel][32]; bias shared with enc[L_A1])
     LayerW a1s2d;
+    // progressive means (ufvc_set_progressive_means): P1a P1b P2a P2b P3a P3b; pm_on selects version-2
+    // streams (partitions 1..3 coded with the progressive means)
+    LayerW pm[kMeanLayers];
+    bool pm_on = false;
     std::map<long long, Plan*> plans;
     std::string err;
     // standalone rANS scratch
@@ -287,6 +297,7 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
         AL(p->diz, (size_t)a.cz);
         AL(p->didx, p->ny);
         AL(p->qp_dev, 1);
+        AL(p->ver_dev, 1);
         AL(p->lo_z, (size_t)p->Kz);
         AL(p->lo_y, (size_t)K);
         AL(p->lw_z, (size_t)p->Kz);
@@ -311,6 +322,21 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
         AL(p->bufC, (n3 + act - 1) / act);
     }
 #undef AL
+    return UFVC_OK;
+}
+
+// The progressive-means buffers of one direction of a plan (allocated, or counted into dry_bytes).
+static ufvc_status pm_buffers(ufvc_ctx* ctx, Plan* p, bool enc, size_t* dry_bytes) {
+    const Arch& a = ctx->arch;
+    const size_t act = ctx->cfg.precision == UFVC_FP32 ? 1 : 2;
+    const size_t npix = (size_t)p->Hy * p->Wy;
+    ufvc_status st = UFVC_OK;
+    float** bufs[3] = {enc ? &p->pm_in_e : &p->pm_in_d, enc ? &p->pm_h_e : &p->pm_h_d, enc ? &p->pm_mu_e : &p->pm_mu_d};
+    const size_t n[3] = {(npix * (a.cy + a.cz) + act - 1) / act, (npix * a.cz + act - 1) / act, npix * a.cy};
+    for (int i = 0; i < 3; ++i) {
+        if (dry_bytes) *dry_bytes += (n[i] * sizeof(float) + 255) & ~(size_t)255;
+        else if ((st = dalloc(ctx, p, bufs[i], n[i])) != UFVC_OK) return st;
+    }
     return UFVC_OK;
 }
 
@@ -340,6 +366,10 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         p->enc_ready = true;
     }
     if (for_decode && !p->dec_ready) p->dec_ready = true;
+    if (ctx->pm_on && (for_decode ? !p->pm_dec_ready : !p->pm_enc_ready)) {
+        if ((st = pm_buffers(ctx, p, !for_decode, nullptr)) != UFVC_OK) return st;
+        (for_decode ? p->pm_dec_ready : p->pm_enc_ready) = true;
+    }
     *out = p;
     return UFVC_OK;
 }
@@ -357,8 +387,14 @@ size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
         d.H = h; d.W = w; d.k = k; d.stride = 1; d.Cout = cout; d.Cin = ceil_div(cin, 16) * 16; d.groups = 1;
         return conv_simt_workspace(d) * sizeof(float);
     };
-    const size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
-                                ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
+    size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
+                          ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
+    if (ctx->pm_on) {
+        pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
+        pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, false, &bytes);
+        if (ctx->cfg.precision == UFVC_FP32)
+            hs = std::max({hs, ws(tmp.Hy, tmp.Wy, 3, a.cz, a.cy + a.cz), ws(tmp.Hy, tmp.Wy, 1, a.cy, a.cz)});
+    }
     return bytes + 2 * hs;
 }
 
@@ -385,10 +421,14 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
     return UFVC_OK;
 }
 
+// shape (cout, k, cin), when given, replaces the codec blob's layer table (the progressive-mean blob);
+// no_fp8 keeps an FP8 context's layer on bf16 operands
 static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
-                                bool tc, bool pixel_shuffle = false, bool final_layer = false) {
+                                bool tc, bool pixel_shuffle = false, bool final_layer = false,
+                                const int* shape = nullptr, bool no_fp8 = false) {
     int co, k, ci;
-    layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
+    if (shape) { co = shape[0]; k = shape[1]; ci = shape[2]; }
+    else layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
     L.cout = co; L.k = k; L.cin = ci; L.cin_p = ceil_div(ci, 16) * 16; L.groups = groups;
     L.w_gs = (long long)k * k * L.cin_p * co;
     L.b_gs = co;
@@ -434,7 +474,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
             if ((st = dalloc(ctx, nullptr, &L.btc, bt.size())) != UFVC_OK) return st;
             CK(cudaMemcpy(L.btc, bt.data(), bt.size() * 4, cudaMemcpyHostToDevice));
         }
-        if (ctx->cfg.precision == UFVC_FP8 && !final_layer) {
+        if (ctx->cfg.precision == UFVC_FP8 && !final_layer && !no_fp8) {
             // E4M3 copy with one scale per output channel (per group): code = e4m3(w / s), s = absmax / 448
             std::vector<uint8_t> w8((size_t)groups * L.cout_pad * K, 0);
             L.wscale.assign((size_t)groups * co, 1.f);
@@ -519,6 +559,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
                 cudaFree(L.w8); cudaFree(L.cs8);
             }
         }
+        for (LayerW& L : ctx->pm) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
         cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
@@ -604,6 +645,8 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     for (int l = 0; l < L_NENC; ++l) c->enc[l] = base->enc[l];
     for (int l = 0; l < D_NDEC; ++l) c->dec[l] = base->dec[l];
     c->a1s2d = base->a1s2d;
+    for (int l = 0; l < kMeanLayers; ++l) c->pm[l] = base->pm[l];
+    c->pm_on = base->pm_on;
     c->borrowed = true;
     if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
         cudaFree(c->d_status);
@@ -707,6 +750,30 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
     return UFVC_OK;
 }
 
+// Progressive means (Sec. 3.4, Fig. 4c): after the single parameter pass, the means of partitions 1, 2, 3,
+// each from the partitions before it and the hyper-synthesis features s (see progressive.cu).  Encoder
+// (y != null): quantises partition 0 with mu^0 and partition k with mu^k, writing r^; decoder: r^ is the
+// decoded one.  Both leave in mu the mean every element is coded with (y^ = r^ q + mu).  The mean
+// network runs on the tensor cores (bf16 operands, also in FP8 contexts) or, in FP32 precision, on
+// the SIMT kernel.  in / h / muk: the plan's buffers of this direction.
+static ufvc_status run_progressive(ufvc_ctx* ctx, int Hy, int Wy, const float* y, int16_t* rhat, float* mu,
+                                   const float* sfeat, const int* qp_dev, int qp_host, const int* ver_dev, float* in,
+                                   float* h, float* muk, cudaStream_t s) {
+    const Arch& a = ctx->arch;
+    const bool f32 = ctx->cfg.precision == UFVC_FP32;
+    prof_begin(ctx, "progressive_means", s);
+    launch_pm_init(y, rhat, mu, sfeat, Hy, Wy, a.cy, a.cz, ctx->d_qstep, ctx->d_qinv, qp_dev, qp_host, in, f32, s);
+    for (int k = 1; k <= 3; ++k) {
+        RUN(conv(ctx, ctx->pm[2 * k - 2], in, Hy, Wy, 1, 1, OUT_NHWC, h, Hy, Wy, s));
+        RUN(conv(ctx, ctx->pm[2 * k - 1], h, Hy, Wy, 1, 0, OUT_NHWC, muk, Hy, Wy, s, nullptr, nullptr, 0, 0, 0, 0, 1,
+                 true));
+        launch_pm_step(k, y, rhat, mu, muk, Hy, Wy, a.cy, a.cz, ctx->d_qstep, ctx->d_qinv, qp_dev, qp_host, ver_dev,
+                       in, f32, s);
+    }
+    prof_end(ctx, s, 10);
+    return UFVC_OK;
+}
+
 // FP8 calibration run (FP32 path): record max |x| of activation tensor t
 static void probe(ufvc_ctx* ctx, int t, const float* x, size_t n, cudaStream_t s) {
     if (ctx->amax) launch_absmax(x, n, ctx->amax + t, s);
@@ -771,6 +838,9 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     prof_begin(ctx, "quantize", s);
     launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);
     prof_end(ctx, s, 1);
+    if (ctx->pm_on)
+        RUN(run_progressive(ctx, p->Hy, p->Wy, p->y, p->rhat, p->mu, p->s2, nullptr, qp, nullptr, p->pm_in_e, p->pm_h_e,
+                            p->pm_mu_e, s));
     return UFVC_OK;
 }
 
@@ -839,8 +909,8 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     launch_rans_encode(secs, 2, ctx->d_packed, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "bitstream", s);
-    launch_write_header(d_bits, ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz, p->iz, ctx->arch.cz,
-                        capacity, ctx->d_status, s);
+    launch_write_header(d_bits, ctx->pm_on ? 2 : 1, ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz,
+                        p->iz, ctx->arch.cz, capacity, ctx->d_status, s);
     launch_rans_finalize(secs, 2, d_bits, p->hdr, capacity, d_nbytes, p->off_ws, ctx->d_status, s);
     prof_end(ctx, s, 3);
     CK(cudaGetLastError());
@@ -861,8 +931,8 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
 
     const Arch& a = ctx->arch;
     prof_begin(ctx, "parse", s);
-    launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, p->qp_dev,
-                        p->diz, ctx->d_status, s);
+    launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, ctx->pm_on,
+                        p->qp_dev, p->ver_dev, p->diz, ctx->d_status, s);
     const bool fp32 = ctx->cfg.precision == UFVC_FP32;
     RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
                      p->dzhat};
@@ -881,12 +951,18 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode_y", s);
     launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
+    if (ctx->pm_on) {  // a version-1 stream leaves the means of the single pass (the steps check the version)
+        prof_end(ctx, s, 1);
+        RUN(run_progressive(ctx, p->Hy, p->Wy, nullptr, p->drhat, p->dmu, p->ds2, p->qp_dev, 0, p->ver_dev, p->pm_in_d,
+                            p->pm_h_d, p->pm_mu_d, s));
+        prof_begin(ctx, "dequant", s);
+    }
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
                    fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
                    fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
     if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
-    prof_end(ctx, s, 2);
+    prof_end(ctx, s, ctx->pm_on ? 1 : 2);
     RUN(run_decoders(ctx, p, fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf, d_frames, final_mode, s));
     CK(cudaGetLastError());
     return UFVC_OK;
@@ -1022,6 +1098,66 @@ extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat
     ctx->cur_ws = &ctx->ws_stage;
     st = run_hyper_synthesis(ctx, &tmp, d_zhat, zf, s1, s2, d_mu, d_logsig, s);
     cudaError_t e = cudaStreamSynchronize(s);
+    for (void* v : tmp.allocs) cudaFree(v);
+    if (st) return st;
+    if (e != cudaSuccess) return fail(ctx, UFVC_ERR_CUDA, cudaGetErrorString(e));
+    return UFVC_OK;
+}
+
+extern "C" size_t ufvc_mean_weight_count(int arch) { return mean_weight_count(arch); }
+
+extern "C" ufvc_status ufvc_set_progressive_means(ufvc_ctx* ctx, const float* weights, size_t n_weights) {
+    if (!ctx || !weights) return fail(ctx, UFVC_ERR_ARG, "set_progressive_means: bad argument");
+    if (ctx->borrowed) return fail(ctx, UFVC_ERR_ARG, "set_progressive_means: context shares another's weights");
+    if (ctx->pm_on) return fail(ctx, UFVC_ERR_ARG, "set_progressive_means: already set");
+    if (n_weights != mean_weight_count(ctx->cfg.arch)) return fail(ctx, UFVC_ERR_ARG, "set_progressive_means: weight count");
+    CK(cudaSetDevice(ctx->cfg.device));
+    size_t offs[kMeanLayers], off = 0;
+    for (int l = 0; l < kMeanLayers; ++l) {
+        int sh[3];
+        mean_layer_shape(ctx->cfg.arch, l, &sh[0], &sh[1], &sh[2]);
+        offs[l] = off;
+        off += (size_t)sh[0] * sh[1] * sh[1] * sh[2] + sh[0];
+    }
+    for (int l = 0; l < kMeanLayers; ++l) {
+        int sh[3];
+        mean_layer_shape(ctx->cfg.arch, l, &sh[0], &sh[1], &sh[2]);
+        ufvc_status st = upload_layer(ctx, ctx->pm[l], weights, offs, l, 1, true, false, false, sh, true);
+        if (st != UFVC_OK) return st;
+    }
+    ctx->pm_on = true;
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_progressive_means(ufvc_ctx* ctx, const float* d_y, const int16_t* d_rhat_in,
+                                              const float* d_mu0, const float* d_s, int Hy, int Wy, int qp,
+                                              int16_t* d_rhat, float* d_mu, float* d_yhat, void* stream) {
+    if (!ctx || !d_mu0 || !d_s || !d_rhat || !d_mu || !d_yhat || (!d_y && !d_rhat_in) || Hy < 1 || Wy < 1 || qp < 0 ||
+        qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "progressive_means: bad argument");
+    if (!ctx->pm_on) return fail(ctx, UFVC_ERR_ARG, "progressive_means: no mean network (ufvc_set_progressive_means)");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->cfg.device));
+    const Arch& a = ctx->arch;
+    Plan tmp;
+    tmp.Hy = Hy; tmp.Wy = Wy;
+    const size_t ny = (size_t)Hy * Wy * a.cy;
+    int* qpd = nullptr;
+    ufvc_status st;
+    if ((st = pm_buffers(ctx, &tmp, true, nullptr)) || (st = dalloc(ctx, &tmp, &qpd, 1))) {
+        for (void* v : tmp.allocs) cudaFree(v);
+        return st;
+    }
+    ctx->cur_ws = &ctx->ws_stage;
+    cudaError_t e = cudaMemcpyAsync(d_mu, d_mu0, ny * 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && !d_y) e = cudaMemcpyAsync(d_rhat, d_rhat_in, ny * 2, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qpd, &qp, 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        st = run_progressive(ctx, Hy, Wy, d_y, d_rhat, d_mu, d_s, nullptr, qp, nullptr, tmp.pm_in_e, tmp.pm_h_e,
+                             tmp.pm_mu_e, s);
+        if (st == UFVC_OK) launch_dequant(d_rhat, d_mu, ny, ctx->d_qstep, qpd, d_yhat, nullptr, s);
+        e = cudaStreamSynchronize(s);
+    }
     for (void* v : tmp.allocs) cudaFree(v);
     if (st) return st;
     if (e != cudaSuccess) return fail(ctx, UFVC_ERR_CUDA, cudaGetErrorString(e));

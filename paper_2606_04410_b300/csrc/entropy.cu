@@ -914,7 +914,7 @@ void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float*
 // ------------------------------------------------------------------------------------------------
 // container header
 // ------------------------------------------------------------------------------------------------
-__global__ void write_header_kernel(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz,
+__global__ void write_header_kernel(uint8_t* out, int version, int arch, int N, int qp, int W, int H, int K, int Kz,
                                     const uint8_t* iz, int Cz, size_t capacity, int* status) {
     pdl_trigger();
     pdl_wait();
@@ -926,7 +926,7 @@ __global__ void write_header_kernel(uint8_t* out, int arch, int N, int qp, int W
     for (int i = threadIdx.x; i < (int)hdr; i += blockDim.x) {
         uint8_t v = 0;
         if (i < 4) v = "UFVC"[i];
-        else if (i == 4) v = 1;
+        else if (i == 4) v = (uint8_t)version;
         else if (i == 5) v = (uint8_t)arch;
         else if (i == 6) v = (uint8_t)N;
         else if (i == 7) v = (uint8_t)qp;
@@ -939,21 +939,27 @@ __global__ void write_header_kernel(uint8_t* out, int arch, int N, int qp, int W
     }
 }
 
-void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,
-                         int Cz, size_t capacity, int* status, cudaStream_t s) {
-    (void)launch_pdl(write_header_kernel, dim3(1), dim3(256), (size_t)(0), s, out, arch, N, qp, W, H, K, Kz, iz, Cz, capacity, status);
+void launch_write_header(uint8_t* out, int version, int arch, int N, int qp, int W, int H, int K, int Kz,
+                         const uint8_t* iz, int Cz, size_t capacity, int* status, cudaStream_t s) {
+    (void)launch_pdl(write_header_kernel, dim3(1), dim3(256), (size_t)(0), s, out, version, arch, N, qp, W, H, K, Kz, iz,
+                     Cz, capacity, status);
 }
 
 __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, int N, int W, int H, int K, int Kz,
-                                    int Cz, int* qp_dev, uint8_t* iz, int* status) {
+                                    int Cz, int allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status) {
     pdl_trigger();
     pdl_wait();
     if (threadIdx.x != 0) return;
     const size_t hdr = (20 + (size_t)Cz + 3) & ~(size_t)3;
     *qp_dev = 32;
+    *ver_dev = 1;
     for (int c = 0; c < Cz; ++c) iz[c] = 0;
-    if (nbytes < hdr || b[0] != 'U' || b[1] != 'F' || b[2] != 'V' || b[3] != 'C' || b[4] != 1) {
+    if (nbytes < hdr || b[0] != 'U' || b[1] != 'F' || b[2] != 'V' || b[3] != 'C' || b[4] < 1 || b[4] > 2) {
         set_status(status, UFVC_ERR_CORRUPT);
+        return;
+    }
+    if (b[4] == 2 && !allow_v2) {  // progressive means, but the context has no mean network
+        set_status(status, UFVC_ERR_UNSUPPORTED);
         return;
     }
     const int w = b[8] | (b[9] << 8), h = b[10] | (b[11] << 8);
@@ -966,11 +972,13 @@ __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, i
         iz[c] = b[20 + c];
     }
     *qp_dev = b[7];
+    *ver_dev = b[4];
 }
 
 void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
-                         int* qp_dev, uint8_t* iz, int* status, cudaStream_t s) {
-    (void)launch_pdl(parse_header_kernel, dim3(1), dim3(32), (size_t)(0), s, bits, nbytes, arch, N, W, H, K, Kz, Cz, qp_dev, iz, status);
+                         bool allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status, cudaStream_t s) {
+    (void)launch_pdl(parse_header_kernel, dim3(1), dim3(32), (size_t)(0), s, bits, nbytes, arch, N, W, H, K, Kz, Cz,
+                     (int)allow_v2, qp_dev, ver_dev, iz, status);
 }
 
 }  // namespace ufvc

@@ -121,4 +121,23 @@ size_t weight_count(int arch, int N) {
     return n;
 }
 
+// Progressive-mean layers of step k = 1..3: P_k,a (3x3, Cy + Cz -> Cz, GELU) then P_k,b (1x1, Cz -> Cy).
+bool mean_layer_shape(int arch, int l, int* cout, int* k, int* cin) {
+    Arch a;
+    if (!get_arch(arch, &a) || l < 0 || l >= kMeanLayers) return false;
+    if (l % 2 == 0) { *cout = a.cz; *k = 3; *cin = a.cy + a.cz; }
+    else            { *cout = a.cy; *k = 1; *cin = a.cz; }
+    return true;
+}
+
+size_t mean_weight_count(int arch) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < kMeanLayers; ++l) {
+        if (!mean_layer_shape(arch, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
 }  // namespace ufvc

@@ -71,6 +71,10 @@ struct Arch { int e0, e1, e2, cy, cz, cd1, cd2; };
 bool get_arch(int arch, Arch* a);
 bool layer_shape(int arch, int N, int l, int* cout, int* k, int* cin);
 size_t weight_count(int arch, int N);
+// progressive-mean blob: P1a P1b P2a P2b P3a P3b (a: 3x3, Cy + Cz -> Cz; b: 1x1, Cz -> Cy)
+bool mean_layer_shape(int arch, int l, int* cout, int* k, int* cin);
+size_t mean_weight_count(int arch);
+constexpr int kMeanLayers = 6;
 
 enum EncLayer { L_A1 = 0, L_A2, L_A3, L_XA, L_XB, L_A4, L_H1, L_H2, L_S1, L_S2, L_S3, L_NENC };
 enum DecLayer { D_D0 = 0, D_R1A, D_R1B, D_U1, D_R2A, D_R2B, D_U2, D_U3, D_NDEC };
@@ -201,11 +205,23 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
                     float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f);
 
-// Container header
-void launch_write_header(uint8_t* out, int arch, int N, int qp, int W, int H, int K, int Kz, const uint8_t* iz,
-                         int Cz, size_t capacity, int* status, cudaStream_t s);
+// Container header.  version 1: single-pass means; version 2: progressive means on partitions 1..3.
+// The parser accepts version 1, and version 2 when allow_v2; it writes the version to *ver_dev.
+void launch_write_header(uint8_t* out, int version, int arch, int N, int qp, int W, int H, int K, int Kz,
+                         const uint8_t* iz, int Cz, size_t capacity, int* status, cudaStream_t s);
 void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
-                         int* qp_dev, uint8_t* iz, int* status, cudaStream_t s);
+                         bool allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status, cudaStream_t s);
+
+// Progressive means (progressive.cu).  `in` is the mean network's input [Hy][Wy][Cy + Cz], float (f32)
+// or bf16.  init: y^ of partition 0 (the encoder, y != null, first quantises partition 0 with mu0 into
+// rhat) and the features s; step k: on partition k, mu <- muk, encoder r^ re-quantised, y^ into `in`
+// (skipped when ver_dev is given and *ver_dev != 2).  qp from *qp_dev, else qp_host.
+void launch_pm_init(const float* y, int16_t* rhat, const float* mu0, const float* s, int Hy, int Wy, int cy, int cz,
+                    const float* qstep_all, const float* qinv_all, const int* qp_dev, int qp_host, void* in, bool f32,
+                    cudaStream_t st);
+void launch_pm_step(int k, const float* y, int16_t* rhat, float* mu, const float* muk, int Hy, int Wy, int cy, int cz,
+                    const float* qstep_all, const float* qinv_all, const int* qp_dev, int qp_host, const int* ver_dev,
+                    void* in, bool f32, cudaStream_t st);
 
 }  // namespace ufvc
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "ufvc_rans_encode_noalloc", "ufvc_decode_chunk_dev", "ufvc_server_create", "ufvc_server_destroy",
     "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
     "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error", "ufvc_calibrate_fp8",
-    "ufvc_get_fp8_scales",
+    "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
 ]
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
 
@@ -94,6 +94,9 @@ _sigs = {
     "ufvc_server_last_error": (C.c_char_p, [_vp]),
     "ufvc_calibrate_fp8": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "ufvc_get_fp8_scales": (_i, [_vp, _vp, _i]),
+    "ufvc_mean_weight_count": (_sz, [_i]),
+    "ufvc_set_progressive_means": (_i, [_vp, _vp, _sz]),
+    "ufvc_progressive_means": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -129,6 +132,10 @@ def weight_count(arch: int, chunk_len: int) -> int:
     return int(lib.ufvc_weight_count(arch, chunk_len))
 
 
+def mean_weight_count(arch: int) -> int:
+    return int(lib.ufvc_mean_weight_count(arch))
+
+
 def latent_dims(arch: int, width: int, height: int) -> dict:
     v = [C.c_int() for _ in range(6)]
     rc = lib.ufvc_latent_dims(arch, width, height, *[C.byref(x) for x in v])
@@ -141,7 +148,7 @@ class Codec:
     """One ufvc_ctx.  Methods mirror the C entry points (ufvc_<name>)."""
 
     def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "fp32",
-                 device: int = 0):
+                 device: int = 0, mean_weights: np.ndarray | None = None):
         self.arch, self.N, self.K, self.precision = arch, chunk_len, lanes, precision
         self.device = device
         cfg = ufvc_config(arch, chunk_len, lanes, PRECISIONS[precision], device)
@@ -153,6 +160,9 @@ class Codec:
         self.h = h
         dims = latent_dims(arch, 16, 16)
         self.Cy, self.Cz = dims["Cy"], dims["Cz"]
+        if mean_weights is not None:
+            mw = np.ascontiguousarray(mean_weights, np.float32)
+            self._check(lib.ufvc_set_progressive_means(self.h, _ptr(mw), mw.size), "set_progressive_means")
 
     def close(self):
         if getattr(self, "h", None):
@@ -251,6 +261,18 @@ class Codec:
         self._check(lib.ufvc_hyper_synthesis(self.h, _ptr(zhat), Hz, Wz, Hy, Wy, _ptr(mu), _ptr(ls), _stream(stream)),
                     "hyper_synthesis")
         return mu, ls
+
+    def progressive_means(self, mu0: torch.Tensor, s: torch.Tensor, qp: int = 32, y: torch.Tensor | None = None,
+                          rhat: torch.Tensor | None = None, stream=None):
+        """The four-partition mean steps: encoder form (y given) or decoder form (rhat given) ->
+        (rhat, mu the mean each element is coded with, yhat = rhat q + mu)."""
+        Hy, Wy, _ = mu0.shape
+        r = torch.empty(mu0.shape, dtype=torch.int16, device=mu0.device)
+        mu = torch.empty_like(mu0)
+        yhat = torch.empty_like(mu0)
+        self._check(lib.ufvc_progressive_means(self.h, _ptr(y), _ptr(rhat), _ptr(mu0), _ptr(s), Hy, Wy, qp, _ptr(r),
+                                               _ptr(mu), _ptr(yhat), _stream(stream)), "progressive_means")
+        return r, mu, yhat
 
     def quantize(self, y, mu, logsig, qp: int = 32, stream=None):
         rhat = torch.empty(y.shape, dtype=torch.int16, device=y.device)
