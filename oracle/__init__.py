@@ -167,7 +167,43 @@ def rans_decode(buf: bytes, tab: np.ndarray, n: int, K: int, freq: np.ndarray | 
     return sym[:n], used.value
 
 
+# ---------------------------------------------------------------- colour interface
+RGB, RGB_BT709, YUV444P, YUV420P = 0, 1, 2, 3
+
+
+def frame_bytes(fmt: int, H: int, W: int) -> int:
+    lib().orc_frame_bytes.restype = C.c_size_t
+    return int(lib().orc_frame_bytes(fmt, H, W))
+
+
+def color_in(fmt: int, frames: np.ndarray, N: int, H: int, W: int) -> np.ndarray:
+    """Caller's frames (N * frame_bytes uint8) -> the network's channels [N][H][W][3] in [0, 1]."""
+    f = np.ascontiguousarray(frames, np.uint8).ravel()
+    assert f.size == N * frame_bytes(fmt, H, W)
+    x = np.empty((N, H, W, 3), np.float64)
+    _check(lib().orc_color_in(fmt, _p(f), N, H, W, _p(x)), "color_in")
+    return x
+
+
+def color_out(fmt: int, x: np.ndarray, N: int, H: int, W: int) -> np.ndarray:
+    """Reconstruction [N][H][W][3] in [0, 1] -> the format's layout as values in [0, 1] (N * frame_bytes)."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty(N * frame_bytes(fmt, H, W), np.float64)
+    _check(lib().orc_color_out(fmt, _p(x), N, H, W, _p(out)), "color_out")
+    return out
+
+
 # ---------------------------------------------------------------- network stages
+def analysis_x(arch: int, x: np.ndarray, weights: np.ndarray) -> np.ndarray:
+    """Latent from the network's input channels x [N][H][W][3] in [0, 1]."""
+    x = np.ascontiguousarray(x, np.float64)
+    N, H, W, _ = x.shape
+    d = latent_dims(arch, H, W)
+    y = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
+    _check(lib().orc_analysis_x(arch, N, _p(x), H, W, _p(weights), _p(y)), "analysis_x")
+    return y
+
+
 def analysis(arch: int, frames: np.ndarray, weights: np.ndarray) -> np.ndarray:
     frames = np.ascontiguousarray(frames, np.uint8)
     N, H, W, _ = frames.shape

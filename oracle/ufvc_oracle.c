@@ -150,6 +150,7 @@ void orc_pixel_shuffle(const double* in, int H, int W, int C, double* out) {
 }
 
 static double* dalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
+static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1; }
 
@@ -157,10 +158,110 @@ static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1;
 /* Analysis (patchify + chunk encoder + cross-frame interaction), Sec. 3.1, Fig. 3                 */
 /* ------------------------------------------------------------------------------------------------ */
 
-/* Chunk -> latent y [Hy][Wy][Cy].  The N frames' RGB are stacked into 3N input channels (frame n ->
- * channels 3n..3n+2), scaled by 1/255 and replicate-padded to multiples of 16.  Then
- * A1..A3 (3x3 stride 2 + GELU), the interaction block h + Xb(GELU(Xa(h))), A4 (3x3 stride 2). */
-int orc_analysis(int arch, int N, const uint8_t* frames, int H, int W, const float* wts, double* y) {
+/* ------------------------------------------------------------------------------------------------ */
+/* Colour interface (Appendix: YUV444 is the model's input and output; RGB and YUV420 are converted)   */
+/* ------------------------------------------------------------------------------------------------ */
+/* Formats: 0 = RGB u8 interleaved [N][H][W][3], the channels fed to the network as they are;
+ * 1 = RGB u8 interleaved, converted to YUV444 with BT.709 (full range, chroma centred at 0.5) before the
+ *     network and back after it;  2 = YUV444 u8 planar [N][3][H][W];  3 = YUV420 u8 planar per frame
+ *     (Y [H][W], then U and V [ceil(H/2)][ceil(W/2)]), chroma replicated over its 2x2 block on input
+ *     and averaged over the block's pixels inside the frame on output.
+ * BT.709 on [0, 1] values: Y = 0.2126 R + 0.7152 G + 0.0722 B, U = (B - Y) / 1.8556 + 0.5,
+ * V = (R - Y) / 1.5748 + 0.5; inverse R = Y + 1.5748 (V - 0.5), B = Y + 1.8556 (U - 0.5),
+ * G = (Y - 0.2126 R - 0.0722 B) / 0.7152. */
+size_t orc_frame_bytes(int fmt, int H, int W) {
+    if (fmt == 3) return (size_t)H * W + 2 * (size_t)((H + 1) / 2) * ((W + 1) / 2);
+    return (size_t)3 * H * W;
+}
+
+static void bt709_fwd(double r, double g, double b, double* o) {
+    double y = 0.2126 * r + 0.7152 * g + 0.0722 * b;
+    o[0] = y;
+    o[1] = (b - y) / 1.8556 + 0.5;
+    o[2] = (r - y) / 1.5748 + 0.5;
+}
+
+static void bt709_inv(const double* yuv, double* rgb) {
+    double r = yuv[0] + 1.5748 * (yuv[2] - 0.5);
+    double b = yuv[0] + 1.8556 * (yuv[1] - 0.5);
+    rgb[0] = r;
+    rgb[1] = (yuv[0] - 0.2126 * r - 0.0722 * b) / 0.7152;
+    rgb[2] = b;
+}
+
+/* Caller's frames -> the network's channels in [0, 1]: x [N][H][W][3]. */
+int orc_color_in(int fmt, const uint8_t* frames, int N, int H, int W, double* x) {
+    if (fmt < 0 || fmt > 3 || N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
+    const size_t fb = orc_frame_bytes(fmt, H, W);
+    const int Wc = (W + 1) / 2, Hc = (H + 1) / 2;
+    for (int n = 0; n < N; n++) {
+        const uint8_t* f = frames + n * fb;
+        for (int h = 0; h < H; h++)
+            for (int w = 0; w < W; w++) {
+                double* o = x + (((size_t)n * H + h) * W + w) * 3;
+                const size_t i = (size_t)h * W + w;
+                if (fmt == 0 || fmt == 1) {
+                    double r = f[3 * i] / 255.0, g = f[3 * i + 1] / 255.0, b = f[3 * i + 2] / 255.0;
+                    if (fmt == 0) { o[0] = r; o[1] = g; o[2] = b; }
+                    else bt709_fwd(r, g, b, o);
+                } else if (fmt == 2) {
+                    for (int c = 0; c < 3; c++) o[c] = f[(size_t)c * H * W + i] / 255.0;
+                } else {
+                    const size_t ci = (size_t)(h / 2) * Wc + w / 2;
+                    o[0] = f[i] / 255.0;
+                    o[1] = f[(size_t)H * W + ci] / 255.0;
+                    o[2] = f[(size_t)H * W + (size_t)Hc * Wc + ci] / 255.0;
+                }
+            }
+    }
+    return ORC_OK;
+}
+
+/* The network's reconstruction x [N][H][W][3] (already clamped to [0, 1]) -> the caller's format, as
+ * values in [0, 1] laid out like the format's bytes (out: N * frame_bytes doubles).  BT.709 results are
+ * clamped to [0, 1] again; YUV420 chroma is the mean of the 2x2 block's pixels that lie in the frame. */
+int orc_color_out(int fmt, const double* x, int N, int H, int W, double* out) {
+    if (fmt < 0 || fmt > 3 || N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
+    const size_t fb = orc_frame_bytes(fmt, H, W);
+    const int Wc = (W + 1) / 2, Hc = (H + 1) / 2;
+    for (int n = 0; n < N; n++) {
+        double* f = out + n * fb;
+        const double* xf = x + (size_t)n * H * W * 3;
+        if (fmt == 3) {
+            for (size_t i = 0; i < (size_t)H * W; i++) f[i] = xf[3 * i];
+            for (int hc = 0; hc < Hc; hc++)
+                for (int wc = 0; wc < Wc; wc++)
+                    for (int c = 1; c < 3; c++) {
+                        double s = 0.0;
+                        int cnt = 0;
+                        for (int dy = 0; dy < 2; dy++)
+                            for (int dx = 0; dx < 2; dx++) {
+                                int h = 2 * hc + dy, w = 2 * wc + dx;
+                                if (h < H && w < W) { s += xf[((size_t)h * W + w) * 3 + c]; cnt++; }
+                            }
+                        f[(size_t)H * W + (size_t)(c - 1) * Hc * Wc + (size_t)hc * Wc + wc] = s / cnt;
+                    }
+            continue;
+        }
+        for (size_t i = 0; i < (size_t)H * W; i++) {
+            const double* v = xf + 3 * i;
+            if (fmt == 0) { f[3 * i] = v[0]; f[3 * i + 1] = v[1]; f[3 * i + 2] = v[2]; }
+            else if (fmt == 1) {
+                double rgb[3];
+                bt709_inv(v, rgb);
+                for (int c = 0; c < 3; c++) f[3 * i + c] = clampd(rgb[c], 0.0, 1.0);
+            } else {
+                for (int c = 0; c < 3; c++) f[(size_t)c * H * W + i] = v[c];
+            }
+        }
+    }
+    return ORC_OK;
+}
+
+/* Chunk -> latent y [Hy][Wy][Cy] from the network's input channels x [N][H][W][3] in [0, 1]: frame n
+ * -> channels 3n..3n+2, replicate-padded to multiples of 16.  Then A1..A3 (3x3 stride 2 + GELU), the
+ * interaction block h + Xb(GELU(Xa(h))), A4 (3x3 stride 2). */
+int orc_analysis_x(int arch, int N, const double* xin, int H, int W, const float* wts, double* y) {
     arch_t a;
     if (get_arch(arch, &a) || N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
     int Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16, C0 = 3 * N;
@@ -170,8 +271,7 @@ int orc_analysis(int arch, int N, const uint8_t* frames, int H, int W, const flo
             for (int n = 0; n < N; n++)
                 for (int c = 0; c < 3; c++) {
                     int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
-                    x[((size_t)h * Wp + w) * C0 + 3 * n + c] =
-                        frames[(((size_t)n * H + sh) * W + sw) * 3 + c] / 255.0;
+                    x[((size_t)h * Wp + w) * C0 + 3 * n + c] = xin[(((size_t)n * H + sh) * W + sw) * 3 + c];
                 }
     const float *wk, *bk;
     int h1 = conv_out(Hp, 3, 2), w1 = conv_out(Wp, 3, 2);
@@ -203,6 +303,16 @@ int orc_analysis(int arch, int N, const uint8_t* frames, int H, int W, const flo
     orc_conv2d(t3, h3, w3, a.e2, wk, bk, a.cy, 3, 2, y);
     free(x); free(t1); free(t2); free(t3); free(u); free(v);
     return ORC_OK;
+}
+
+/* The same from RGB u8 frames [N][H][W][3] fed as they are (format 0): x = frames / 255. */
+int orc_analysis(int arch, int N, const uint8_t* frames, int H, int W, const float* wts, double* y) {
+    if (N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
+    double* x = dalloc((size_t)N * H * W * 3);
+    orc_color_in(0, frames, N, H, W, x);
+    int rc = orc_analysis_x(arch, N, x, H, W, wts, y);
+    free(x);
+    return rc;
 }
 
 /* Hyper-analysis: z = H2(GELU(H1(y))), both 3x3 stride 2.  z: [ceil(Hy/4)][ceil(Wy/4)][Cz]. */
@@ -275,7 +385,6 @@ void orc_build_tables(uint32_t* freq, uint32_t* cum) {
 /* Quantisation (Sec. 3.4: r^ = round(y - mu), y^ = r^ + mu) and scale indexing                      */
 /* ------------------------------------------------------------------------------------------------ */
 
-static double clampd(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* Hyper-latent: z^ = clamp(rint(z), -255, 255).  Per channel c, the scale index used to code z^ is the
  * nearest log bin of the channel's RMS: iz[c] = #{k : t_k < ln sqrt(S_c / n)}, S_c = sum z^^2 over the
