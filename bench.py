@@ -5,7 +5,7 @@ scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
                     [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
-                    [--no-serving] [--no-fp8] [--no-pm] [--serving-window S]
+                    [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--serving-window S]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
 it under the same methodology and reported with the PSNR and bitrate deltas.  Extra keys: the decoder
@@ -303,16 +303,17 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
     cap = codec.max_bitstream_bytes(W_, H_)
     bits = torch.empty(cap, dtype=torch.uint8, device=dev)
     nbytes = torch.zeros(1, dtype=torch.int64, device=dev)
-    out = torch.empty((N, H_, W_, 3), dtype=torch.uint8, device=dev)
+    from paper_2606_04410_b300 import ufvc as U
+    out = torch.empty(N * U.frame_bytes(codec.color, W_, H_), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     nb = 0
     for _ in range(warmup):  # also establishes the stream size, which the decoder call takes from the host
-        codec.encode_chunk(fr, QP, bits, nbytes)
+        codec.encode_chunk(fr, QP, bits, nbytes, width=W_, height=H_)
         nb = int(nbytes.item())
         codec.decode_chunk(bits, nb, W_, H_, out)
     assert codec.sync_status() == 0
     rec = out.float().cpu().numpy() / 255.0
-    psnr = float(10 * np.log10(1.0 / np.mean((rec - frames_np / 255.0) ** 2)))
+    psnr = float(10 * np.log10(1.0 / np.mean((rec - frames_np.ravel() / 255.0) ** 2)))
     # timed steps: no host synchronisation between steps (the library's stage events accumulate and are
     # read once at the end), so the host enqueues ahead of the device as a serving loop does; the step
     # events bracket exactly one encode and one decode
@@ -324,7 +325,7 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
     for i in range(steps):
         flush.fill_(i & 0xFF)
         evs[i][0].record(stream)
-        codec.encode_chunk(fr, QP, bits, nbytes)
+        codec.encode_chunk(fr, QP, bits, nbytes, width=W_, height=H_)
         evs[i][1].record(stream)
         codec.decode_chunk(bits, nb, W_, H_, out)
         evs[i][2].record(stream)
@@ -357,6 +358,7 @@ def main() -> None:
     ap.add_argument("--no-fp8", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-pm", action="store_true", help="skip the progressive-means variant")
+    ap.add_argument("--no-color", action="store_true", help="skip the colour-format variants")
     ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -486,6 +488,28 @@ def main() -> None:
               "stage_ms_per_step": stage_pm}
         cpm.close()
 
+    # ---- colour interface (YUV444 model interface): BT.709 RGB and YUV420 chunks of the same content
+    color = None
+    if args.precision == "bf16" and not args.no_color and (W_, H_) == (W, H):
+        color = {}
+        for name, fmt in (("rgb_bt709", U.COLOR_RGB_BT709), ("yuv420p", U.COLOR_YUV420P)):
+            cc = U.Codec(1, N, K, blob, "bf16", device=local, color=fmt)
+            if fmt == U.COLOR_YUV420P:  # the chunk's channels as Y, U, V with U, V subsampled 2x2
+                u_, v_ = frames_np[:, ::2, ::2, 1], frames_np[:, ::2, ::2, 2]
+                src = np.concatenate([frames_np[..., 0].reshape(N, -1), u_.reshape(N, -1), v_.reshape(N, -1)], 1)
+            else:
+                src = frames_np
+            src = np.ascontiguousarray(src)
+            fr_c = torch.from_numpy(src).to(dev)
+            sc = max(3, args.steps // 4)
+            rc_ = time_codec(cc, fr_c, src, W_, H_, sc, 3, True, flush)
+            vc = N * sc / (sum(a + b for a, b in zip(rc_["t_enc"], rc_["t_dec"])) / 1000.0)
+            st_c = {k: round(sum(m for m, _ in v) / sc, 4) for k, v in rc_["prof"].items()}
+            color[name] = {"value": vc, "frame_bytes": U.frame_bytes(fmt, W_, H_), "psnr_db": rc_["psnr"],
+                           "bytes_per_chunk": rc_["nbytes"], "pack_ms": st_c.get("pack"),
+                           "color_out_ms": st_c.get("color_out"), "dec_u3_ms": st_c.get("dec.U3"), "steps": sc}
+            cc.close()
+
     # ---- end-to-end through the host-buffer C calls (pinned host memory, copies inside the region)
     cap = r["cap"]
     h_frames = torch.from_numpy(frames_np).pin_memory()
@@ -547,6 +571,8 @@ def main() -> None:
                 fp8["dbitrate_vs_fp32"] = (fp8["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]
                 fp8["speedup_vs_fp32"] = fp8["value"] / fp32["value"]
             line["fp8_path"] = fp8
+        if color is not None:
+            line["color_formats"] = color
         if pm is not None:
             if fp32 is not None:
                 pm["dbitrate_vs_fp32"] = (pm["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]

@@ -155,6 +155,30 @@ ufvc_status ufvc_encode_stages(ufvc_ctx* ctx, const uint8_t* d_frames, int width
 ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat, int Hz, int Wz, int Hy, int Wy,
                                  float* d_mu, float* d_logsig, void* stream);
 
+/* ---- colour interface (Appendix: the model reads and writes YUV444; RGB and YUV420 are converted) ----
+ * The frame buffers of the chunk calls (d_frames / h_frames of encode and decode) hold N frames in the
+ * context's colour format, ufvc_frame_bytes(format, W, H) bytes each (float32 values in [0, 1] instead of
+ * bytes for ufvc_decode_chunk_f32):
+ *   UFVC_COLOR_RGB       RGB interleaved [H][W][3], fed to the network as its three channels (default);
+ *   UFVC_COLOR_RGB_BT709 RGB interleaved [H][W][3], converted to YUV444 with BT.709 (full range, chroma
+ *                        centred at 0.5: Y = 0.2126 R + 0.7152 G + 0.0722 B, U = (B - Y) / 1.8556 + 0.5,
+ *                        V = (R - Y) / 1.5748 + 0.5) before the network and back (clamped) after it;
+ *   UFVC_COLOR_YUV444P   YUV444 planar [3][H][W];
+ *   UFVC_COLOR_YUV420P   YUV420 planar: Y [H][W], U and V [ceil(H/2)][ceil(W/2)]; each chroma sample
+ *                        serves its 2x2 block on input, and on output is the mean of the block's pixels
+ *                        inside the frame.
+ * Decoded values are x^ = clamp(0.5 + o, 0, 1) converted to the format; bytes are rint(255 v).  The
+ * bit-stream does not record the format: it codes the network's channels, and the decoding context's
+ * format decides the output conversion. */
+typedef enum { UFVC_COLOR_RGB = 0, UFVC_COLOR_RGB_BT709 = 1, UFVC_COLOR_YUV444P = 2, UFVC_COLOR_YUV420P = 3 } ufvc_color;
+
+/* Bytes of one frame of width x height in `format` (0 for an unknown format). */
+size_t ufvc_frame_bytes(int format, int width, int height);
+
+/* Set the context's colour format (ufvc_color); it applies to the calls that follow.  UFVC_ERR_ARG for an
+ * unknown format.  No device work. */
+ufvc_status ufvc_set_color_format(ufvc_ctx* ctx, int format);
+
 /* ---- progressive means (Sec. 3.4, Fig. 4a and 4c) ----
  * The latent is split into four partitions: channel group g = c / (Cy / 4), position t = 2 (h mod 2)
  * + (w mod 2) in its 2x2 block, partition (t + g) mod 4 (a reading of the paper's figure).  The single

@@ -87,6 +87,7 @@ struct Plan {
     // decoder activations: float in FP32 precision, bf16 (same buffers, half used) otherwise
     float *bufA = nullptr, *bufT = nullptr, *bufB = nullptr, *bufT2 = nullptr, *bufC = nullptr;
     int* ver_dev = nullptr;  // decoder: container version of the stream being decoded
+    float* fstage = nullptr; // decoder, colour formats other than RGB: x^ float [N][H][W][3] before conversion
     // progressive means, per direction: the mean network's input [Hy][Wy][Cy + Cz] and hidden layer
     // [Hy][Wy][Cz] (float in FP32 precision, bf16 otherwise), and the step's means [Hy][Wy][Cy] (float)
     float *pm_in_e = nullptr, *pm_h_e = nullptr, *pm_mu_e = nullptr;
@@ -123,6 +124,7 @@ struct ufvc_ctx {
     // streams (partitions 1..3 coded with the progressive means)
     LayerW pm[kMeanLayers];
     bool pm_on = false;
+    int color = UFVC_COLOR_RGB;  // the caller's frame format (ufvc_color)
     std::map<long long, Plan*> plans;
     std::string err;
     // standalone rANS scratch
@@ -366,6 +368,9 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         p->enc_ready = true;
     }
     if (for_decode && !p->dec_ready) p->dec_ready = true;
+    if (for_decode && ctx->color != UFVC_COLOR_RGB && !p->fstage &&
+        (st = dalloc(ctx, p, &p->fstage, (size_t)ctx->N * p->H * p->W * 3)) != UFVC_OK)
+        return st;
     if (ctx->pm_on && (for_decode ? !p->pm_dec_ready : !p->pm_enc_ready)) {
         if ((st = pm_buffers(ctx, p, !for_decode, nullptr)) != UFVC_OK) return st;
         (for_decode ? p->pm_dec_ready : p->pm_enc_ready) = true;
@@ -389,6 +394,7 @@ size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
     };
     size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
                           ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
+    if (ctx->color != UFVC_COLOR_RGB) bytes += ((size_t)ctx->N * H * W * 3 * sizeof(float) + 255) & ~(size_t)255;
     if (ctx->pm_on) {
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, false, &bytes);
@@ -647,6 +653,7 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     c->a1s2d = base->a1s2d;
     for (int l = 0; l < kMeanLayers; ++l) c->pm[l] = base->pm[l];
     c->pm_on = base->pm_on;
+    c->color = base->color;
     c->borrowed = true;
     if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
         cudaFree(c->d_status);
@@ -786,12 +793,12 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     ctx->cur_ws = &p->ws_enc;
     prof_begin(ctx, "pack", s);
     if (ctx->cfg.precision == UFVC_FP32)
-        launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s);
+        launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s, ctx->color);
     else if (fp8)
-        launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s);
+        launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s, ctx->color);
     else
         launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s,
-                         s2d);
+                         s2d, ctx->color);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "analysis", s);
     if (s2d)  // the same layer as a 2x2 stride-1 convolution over the space-to-depth input
@@ -881,9 +888,16 @@ static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* 
     RUN(conv(ctx, ctx->dec[D_U2], p->bufB, h2, w2, 1, 1, OUT_PS, p->bufC, h3, w3, s, nullptr, nullptr, 0, g2, g3, 0, N));
     prof_end(ctx, s, 1);
     prof_begin(ctx, "dec.U3", s);
-    RUN(conv(ctx, ctx->dec[D_U3], p->bufC, h3, w3, 1, 0, final_mode, frames_out, p->H, p->W, s, nullptr, nullptr, 0, g3,
-             gf, 0, N));
+    // colour formats other than RGB: x^ as float into the plan's staging, then the format conversion
+    const bool conv_out = ctx->color != UFVC_COLOR_RGB && (final_mode == OUT_PS_FINAL_U8 || final_mode == OUT_PS_FINAL_F32);
+    RUN(conv(ctx, ctx->dec[D_U3], p->bufC, h3, w3, 1, 0, conv_out ? OUT_PS_FINAL_F32 : final_mode,
+             conv_out ? (void*)p->fstage : frames_out, p->H, p->W, s, nullptr, nullptr, 0, g3, gf, 0, N));
     prof_end(ctx, s, 1);
+    if (conv_out) {
+        prof_begin(ctx, "color_out", s);
+        launch_color_out(ctx->color, final_mode == OUT_PS_FINAL_F32, p->fstage, N, p->H, p->W, frames_out, s);
+        prof_end(ctx, s, 1);
+    }
     return UFVC_OK;
 }
 
@@ -1017,7 +1031,7 @@ extern "C" ufvc_status ufvc_encode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_fr
         return fail(ctx, UFVC_ERR_ARG, "encode_chunk_host: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
-    const size_t fsz = (size_t)n_frames * width * height * 3;
+    const size_t fsz = (size_t)n_frames * frame_bytes(ctx->color, width, height);
     const size_t bmax = ufvc_max_bitstream_bytes(ctx, width, height);
     ufvc_status st = ensure_staging(ctx, fsz, bmax);
     if (st) return st;
@@ -1039,7 +1053,7 @@ extern "C" ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bi
         return fail(ctx, UFVC_ERR_ARG, "decode_chunk_host: bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->cfg.device));
-    const size_t fsz = (size_t)n_frames * width * height * 3;
+    const size_t fsz = (size_t)n_frames * frame_bytes(ctx->color, width, height);
     ufvc_status st = ensure_staging(ctx, fsz, nbytes);
     if (st) return st;
     CK(cudaMemcpyAsync(ctx->st_bits, h_bits, nbytes, cudaMemcpyHostToDevice, s));
@@ -1105,6 +1119,18 @@ extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat
 }
 
 extern "C" size_t ufvc_mean_weight_count(int arch) { return mean_weight_count(arch); }
+
+extern "C" size_t ufvc_frame_bytes(int format, int width, int height) {
+    if (format < UFVC_COLOR_RGB || format > UFVC_COLOR_YUV420P || width < 1 || height < 1) return 0;
+    return frame_bytes(format, width, height);
+}
+
+extern "C" ufvc_status ufvc_set_color_format(ufvc_ctx* ctx, int format) {
+    if (!ctx || format < UFVC_COLOR_RGB || format > UFVC_COLOR_YUV420P)
+        return fail(ctx, UFVC_ERR_ARG, "set_color_format: unknown format");
+    ctx->color = format;
+    return UFVC_OK;
+}
 
 extern "C" ufvc_status ufvc_set_progressive_means(ufvc_ctx* ctx, const float* weights, size_t n_weights) {
     if (!ctx || !weights) return fail(ctx, UFVC_ERR_ARG, "set_progressive_means: bad argument");

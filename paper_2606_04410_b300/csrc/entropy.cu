@@ -24,6 +24,49 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // ------------------------------------------------------------------------------------------------
 // pack
 // ------------------------------------------------------------------------------------------------
+// Colour interface (the model's input is YUV444; callers give RGB or YUV): the three bytes of frame n's
+// pixel (sh, sw) in the caller's format.  0, 1: RGB interleaved [N][H][W][3] (1 is converted with
+// BT.709); 2: YUV444 planar [N][3][H][W]; 3: YUV420 planar per frame, Y [H][W] then U and V
+// [ceil(H/2)][ceil(W/2)], each chroma sample serving its 2x2 block.
+template <int FMT>
+__device__ __forceinline__ void px_bytes(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W,
+                                         uint32_t* b) {
+    if (FMT <= 1) {
+        const uint8_t* p = fr + ((size_t)n * H * W + (size_t)sh * W + sw) * 3;
+        b[0] = __ldg(p); b[1] = __ldg(p + 1); b[2] = __ldg(p + 2);
+    } else if (FMT == 2) {
+        const size_t pl = (size_t)H * W;
+        const uint8_t* p = fr + (size_t)n * 3 * pl + (size_t)sh * W + sw;
+        b[0] = __ldg(p); b[1] = __ldg(p + pl); b[2] = __ldg(p + 2 * pl);
+    } else {
+        const int Wc = (W + 1) >> 1, Hc = (H + 1) >> 1;
+        const size_t pl = (size_t)H * W, cpl = (size_t)Hc * Wc;
+        const uint8_t* f = fr + (size_t)n * (pl + 2 * cpl);
+        const size_t ci = (size_t)(sh >> 1) * Wc + (sw >> 1);
+        b[0] = __ldg(f + (size_t)sh * W + sw); b[1] = __ldg(f + pl + ci); b[2] = __ldg(f + pl + cpl + ci);
+    }
+}
+
+// BT.709, full range, chroma centred at 0.5: Y = 0.2126 R + 0.7152 G + 0.0722 B, U = (B - Y) / 1.8556 + 0.5,
+// V = (R - Y) / 1.5748 + 0.5, on RGB bytes / 255
+__device__ __forceinline__ void bt709_from_bytes(const uint32_t* b, float* v) {
+    const float r = b[0] / 255.0f, g = b[1] / 255.0f, bl = b[2] / 255.0f;
+    const float y = fmaf(0.0722f, bl, fmaf(0.7152f, g, 0.2126f * r));
+    v[0] = y;
+    v[1] = fmaf(bl - y, 1.0f / 1.8556f, 0.5f);
+    v[2] = fmaf(r - y, 1.0f / 1.5748f, 0.5f);
+}
+
+// frame n's three network channels of pixel (sh, sw), as floats in [0, 1]
+template <int FMT>
+__device__ __forceinline__ void px_values(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W, float* v) {
+    uint32_t b[3];
+    px_bytes<FMT>(fr, n, sh, sw, H, W, b);
+    if (FMT == 1) bt709_from_bytes(b, v);
+    else { v[0] = b[0] / 255.0f; v[1] = b[1] / 255.0f; v[2] = b[2] / 255.0f; }
+}
+
+template <int FMT>
 __global__ void pack_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Hp, int Wp, int Cp,
                             float* __restrict__ x) {
     pdl_trigger();
@@ -33,20 +76,47 @@ __global__ void pack_kernel(const uint8_t* __restrict__ frames, int N, int H, in
     const int h = (int)(pix / Wp), w = (int)(pix % Wp);
     const int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
     float* o = x + pix * Cp;
+    float cur[3] = {0.f, 0.f, 0.f};
+    int cur_n = -1;
     for (int c0 = 0; c0 < Cp; c0 += 4) {
         float v[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int c = c0 + j, n = c / 3;
-            v[j] = (n < N) ? frames[(((size_t)n * H + sh) * W + sw) * 3 + (c - 3 * n)] / 255.0f : 0.0f;
+            if (n < N && n != cur_n) { px_values<FMT>(frames, n, sh, sw, H, W, cur); cur_n = n; }
+            v[j] = (n < N) ? cur[c - 3 * n] : 0.0f;
         }
         *reinterpret_cast<float4*>(o + c0) = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
-void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s) {
+void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s,
+                 int fmt) {
     const size_t npix = (size_t)Hp * Wp;
-    (void)launch_pdl(pack_kernel, dim3((unsigned)((npix + 255) / 256)), dim3(256), (size_t)(0), s, frames, N, H, W, Hp, Wp, Cp, x);
+    const dim3 g((unsigned)((npix + 255) / 256));
+    switch (fmt) {
+        case 1: (void)launch_pdl(pack_kernel<1>, g, dim3(256), 0, s, frames, N, H, W, Hp, Wp, Cp, x); break;
+        case 2: (void)launch_pdl(pack_kernel<2>, g, dim3(256), 0, s, frames, N, H, W, Hp, Wp, Cp, x); break;
+        case 3: (void)launch_pdl(pack_kernel<3>, g, dim3(256), 0, s, frames, N, H, W, Hp, Wp, Cp, x); break;
+        default: (void)launch_pdl(pack_kernel<0>, g, dim3(256), 0, s, frames, N, H, W, Hp, Wp, Cp, x); break;
+    }
+}
+
+// bf16 bits of frame n's three channels: bytes through the v / 255 table, BT.709 in float
+template <int FMT>
+__device__ __forceinline__ void px_bf16(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W,
+                                        const uint16_t* lut, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
+    uint32_t b[3];
+    px_bytes<FMT>(fr, n, sh, sw, H, W, b);
+    if (FMT == 1) {
+        float v[3];
+        bt709_from_bytes(b, v);
+        b0 = __bfloat16_as_ushort(__float2bfloat16_rn(v[0]));
+        b1 = __bfloat16_as_ushort(__float2bfloat16_rn(v[1]));
+        b2 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2]));
+    } else {
+        b0 = lut[b[0]]; b1 = lut[b[1]]; b2 = lut[b[2]];
+    }
 }
 
 __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
@@ -61,7 +131,7 @@ __device__ __forceinline__ uint32_t pack_bf16_pair(float a, float b) {
 // tile to global memory with consecutive threads writing consecutive 16-byte chunks.
 constexpr int kPackPix = 128;
 
-template <int CP>
+template <int CP, int FMT>
 __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                              int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
     pdl_trigger();
@@ -73,20 +143,14 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
     __syncthreads();
     const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
     const int sw = w < W ? w : W - 1;  // replicate the last column
-    const size_t plane = (size_t)H * W * 3;
     for (int h = blockIdx.y; h < Hp; h += gridDim.y) {
         const int sh = h < H ? h : H - 1;  // replicate the last row
-        const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
         uint32_t pk[32];
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
             // channels 3n, 3n+1, 3n+2 -> bf16 halves 3n .. 3n+2 of the packed row
             uint32_t b0 = 0, b1 = 0, b2 = 0;
-            if (n < N) {
-                b0 = lut[__ldg(src + n * plane)];
-                b1 = lut[__ldg(src + n * plane + 1)];
-                b2 = lut[__ldg(src + n * plane + 2)];
-            }
+            if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, b0, b1, b2);
             // halves 3n, 3n+1, 3n+2 land in words (3n)/2 .. (3n+2)/2 (n even: w, w, w+1 low; n odd: w high, w+1)
             if ((n & 1) == 0) {
                 pk[3 * n / 2] = b0 | (b1 << 16);
@@ -117,6 +181,7 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
 // (h & 1, w & 1) of super-pixel (h / 2, w / 2), whose 128 channels are [2 (h & 1) + (w & 1)][32].  A block
 // packs a 128-pixel segment of both rows of a super-row, so its 64 super-pixels (16 KB) are written as one
 // contiguous run; shared-memory chunk c (16 bytes) of the segment is kept at c ^ ((c >> 4) & 7).
+template <int FMT>
 __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                                  int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
     pdl_trigger();
@@ -127,22 +192,16 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* 
     __syncthreads();
     const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
     const int sw = w < W ? w : W - 1;  // replicate the last column
-    const size_t plane = (size_t)H * W * 3;
     const int Ws = Wp >> 1, npix = Wp - w0 < kPackPix ? Wp - w0 : kPackPix;
     for (int Y = blockIdx.y; Y < (Hp >> 1); Y += gridDim.y) {
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
             const int h = 2 * Y + dy, sh = h < H ? h : H - 1;  // replicate the last row
-            const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
             uint32_t pk[24];
 #pragma unroll
             for (int n = 0; n < 16; ++n) {
                 uint32_t b0 = 0, b1 = 0, b2 = 0;
-                if (n < N) {
-                    b0 = lut[__ldg(src + n * plane)];
-                    b1 = lut[__ldg(src + n * plane + 1)];
-                    b2 = lut[__ldg(src + n * plane + 2)];
-                }
+                if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, b0, b1, b2);
                 if ((n & 1) == 0) {
                     pk[3 * n / 2] = b0 | (b1 << 16);
                     pk[3 * n / 2 + 1] = b2;
@@ -169,19 +228,31 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* 
     }
 }
 
-void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
-                      cudaStream_t s, bool s2d) {
+template <int FMT>
+static void launch_pack_bf16_fmt(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp,
+                                 __nv_bfloat16* x, cudaStream_t s, bool s2d) {
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
     if (Cp == 32 && s2d)  // Hp, Wp even
-        (void)launch_pdl(pack_bf16_s2d_kernel, dim3(dim3(grid.x, (unsigned)((Hp >> 1) < 65535 ? (Hp >> 1) : 65535))), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_s2d_kernel<FMT>, dim3(dim3(grid.x, (unsigned)((Hp >> 1) < 65535 ? (Hp >> 1) : 65535))), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
     else if (Cp == 32)  // 3N <= 32
-        (void)launch_pdl(pack_bf16_kernel<32>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_kernel<32, FMT>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
     else
-        (void)launch_pdl(pack_bf16_kernel<64>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
+        (void)launch_pdl(pack_bf16_kernel<64, FMT>, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
+}
+
+void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
+                      cudaStream_t s, bool s2d, int fmt) {
+    switch (fmt) {
+        case 1: launch_pack_bf16_fmt<1>(frames, N, H, W, Hp, Wp, Cp, x, s, s2d); break;
+        case 2: launch_pack_bf16_fmt<2>(frames, N, H, W, Hp, Wp, Cp, x, s, s2d); break;
+        case 3: launch_pack_bf16_fmt<3>(frames, N, H, W, Hp, Wp, Cp, x, s, s2d); break;
+        default: launch_pack_bf16_fmt<0>(frames, N, H, W, Hp, Wp, Cp, x, s, s2d); break;
+    }
 }
 
 // E4M3 variant: the same segment scheme with 64-byte pixel rows; x = v / 255 is stored as the E4M3 code
 // of x * 448 (the per-tensor scale of [0, 1] data: 1 / 448).
+template <int FMT>
 __global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                             int W, int Hp, int Wp, uint8_t* __restrict__ x) {
     pdl_trigger();
@@ -193,20 +264,29 @@ __global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __res
     __syncthreads();
     const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
     const int sw = w < W ? w : W - 1;
-    const size_t plane = (size_t)H * W * 3;
     for (int h = blockIdx.y; h < Hp; h += gridDim.y) {
         const int sh = h < H ? h : H - 1;
-        const uint8_t* src = frames + ((size_t)sh * W + sw) * 3;
         uint32_t pk[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) pk[i] = 0u;
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
             if (n < N) {
+                uint32_t bytes[3], code[3];
+                px_bytes<FMT>(frames, n, sh, sw, H, W, bytes);
+                if (FMT == 1) {
+                    float v[3];
+                    bt709_from_bytes(bytes, v);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) code[c] = (uint8_t)__nv_cvt_float_to_fp8(v[c] * 448.0f, __NV_SATFINITE, __NV_E4M3);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) code[c] = lut[bytes[c]];
+                }
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const int b = 3 * n + c;  // byte b of the row: word b / 4, byte b % 4
-                    pk[b >> 2] |= (uint32_t)lut[__ldg(src + n * plane + c)] << (8 * (b & 3));
+                    pk[b >> 2] |= code[c] << (8 * (b & 3));
                 }
             }
         }
@@ -223,9 +303,14 @@ __global__ void __launch_bounds__(kPackPix) pack_fp8_kernel(const uint8_t* __res
     }
 }
 
-void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s) {
+void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s, int fmt) {
     const dim3 grid((unsigned)((Wp + kPackPix - 1) / kPackPix), (unsigned)(Hp < 65535 ? Hp : 65535));
-    (void)launch_pdl(pack_fp8_kernel, dim3(grid), dim3(kPackPix), (size_t)(0), s, frames, N, H, W, Hp, Wp, x);
+    switch (fmt) {
+        case 1: (void)launch_pdl(pack_fp8_kernel<1>, grid, dim3(kPackPix), 0, s, frames, N, H, W, Hp, Wp, x); break;
+        case 2: (void)launch_pdl(pack_fp8_kernel<2>, grid, dim3(kPackPix), 0, s, frames, N, H, W, Hp, Wp, x); break;
+        case 3: (void)launch_pdl(pack_fp8_kernel<3>, grid, dim3(kPackPix), 0, s, frames, N, H, W, Hp, Wp, x); break;
+        default: (void)launch_pdl(pack_fp8_kernel<0>, grid, dim3(kPackPix), 0, s, frames, N, H, W, Hp, Wp, x); break;
+    }
 }
 
 // [H][W][C] float -> E4M3 codes of value * inv, rows of pitch Wd pixels (C a multiple of 4)

@@ -135,14 +135,19 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s);
 // floats of split-K workspace the SIMT launch of d uses (0: none)
 size_t conv_simt_workspace(const ConvDesc& d);
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
+// fmt: the caller's colour format (ufvc_color); the network reads its three channels per frame
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
-                      cudaStream_t s,
-                      bool s2d = false);
+                      cudaStream_t s, bool s2d, int fmt);
+// colour interface, output side (color.cu): x^ float [N][H][W][3] -> the caller's format (fmt 1..3), float
+// or uint8; frame_bytes = bytes of one frame in format fmt
+size_t frame_bytes(int fmt, int W, int H);
+void launch_color_out(int fmt, bool f32, const float* x, int N, int H, int W, void* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------------
 // Elementwise / entropy kernels
 // ---------------------------------------------------------------------------------------------
-void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s);
+void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, float* x, cudaStream_t s,
+                 int fmt);
 void launch_zquant(const float* z, int npos, int cz, const uint64_t* zthr, int16_t* zhat, uint8_t* iz,
                    cudaStream_t s);
 void launch_quantize(const float* y, const float* mu, const float* logsig, size_t n, const float* thr_all,
@@ -154,7 +159,7 @@ void launch_i16_to_f32(const int16_t* a, size_t n, float* out, cudaStream_t s);
 void launch_f32_to_bf16(const float* a, size_t n, __nv_bfloat16* out, cudaStream_t s);
 void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16* out, int Wd, cudaStream_t s);
 // FP8 E4M3 helpers: packed input rows of 64 bytes (scale 1/448), float -> E4M3 rows, |x| maximum
-void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s);
+void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, uint8_t* x, cudaStream_t s, int fmt);
 void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s);
 void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s);
 

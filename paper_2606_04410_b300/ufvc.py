@@ -35,7 +35,9 @@ EXPORTS = [
     "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
     "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error", "ufvc_calibrate_fp8",
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
+    "ufvc_frame_bytes", "ufvc_set_color_format",
 ]
+COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
 
 
@@ -95,6 +97,8 @@ _sigs = {
     "ufvc_calibrate_fp8": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "ufvc_get_fp8_scales": (_i, [_vp, _vp, _i]),
     "ufvc_mean_weight_count": (_sz, [_i]),
+    "ufvc_frame_bytes": (_sz, [_i, _i, _i]),
+    "ufvc_set_color_format": (_i, [_vp, _i]),
     "ufvc_set_progressive_means": (_i, [_vp, _vp, _sz]),
     "ufvc_progressive_means": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
 }
@@ -132,6 +136,10 @@ def weight_count(arch: int, chunk_len: int) -> int:
     return int(lib.ufvc_weight_count(arch, chunk_len))
 
 
+def frame_bytes(color: int, width: int, height: int) -> int:
+    return int(lib.ufvc_frame_bytes(color, width, height))
+
+
 def mean_weight_count(arch: int) -> int:
     return int(lib.ufvc_mean_weight_count(arch))
 
@@ -148,7 +156,7 @@ class Codec:
     """One ufvc_ctx.  Methods mirror the C entry points (ufvc_<name>)."""
 
     def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "fp32",
-                 device: int = 0, mean_weights: np.ndarray | None = None):
+                 device: int = 0, mean_weights: np.ndarray | None = None, color: int = COLOR_RGB):
         self.arch, self.N, self.K, self.precision = arch, chunk_len, lanes, precision
         self.device = device
         cfg = ufvc_config(arch, chunk_len, lanes, PRECISIONS[precision], device)
@@ -163,6 +171,24 @@ class Codec:
         if mean_weights is not None:
             mw = np.ascontiguousarray(mean_weights, np.float32)
             self._check(lib.ufvc_set_progressive_means(self.h, _ptr(mw), mw.size), "set_progressive_means")
+        self.color = COLOR_RGB
+        if color != COLOR_RGB:
+            self.set_color_format(color)
+
+    def set_color_format(self, color: int):
+        self._check(lib.ufvc_set_color_format(self.h, color), "set_color_format")
+        self.color = color
+
+    def frame_dims(self, frames, width=None, height=None) -> tuple[int, int]:
+        """(W, H) of a chunk tensor: [N][H][W][3] for RGB formats, [N][3][H][W] for YUV444 planar; YUV420
+        chunks ([N][frame bytes]) need width and height."""
+        if width is not None:
+            return width, height
+        if self.color in (COLOR_RGB, COLOR_RGB_BT709):
+            return frames.shape[2], frames.shape[1]
+        if self.color == COLOR_YUV444P:
+            return frames.shape[3], frames.shape[2]
+        raise ValueError("YUV420 chunks need width and height")
 
     def close(self):
         if getattr(self, "h", None):
@@ -180,8 +206,9 @@ class Codec:
             raise UfvcError(rc, f"{what}: {lib.ufvc_last_error(self.h).decode()}")
 
     # ---- FP8 calibration
-    def calibrate_fp8(self, frames: torch.Tensor, qp: int = 32, stream=None):
-        N, H, W, _ = frames.shape
+    def calibrate_fp8(self, frames: torch.Tensor, qp: int = 32, stream=None, width=None, height=None):
+        N = frames.shape[0]
+        W, H = self.frame_dims(frames, width, height)
         self._check(lib.ufvc_calibrate_fp8(self.h, _ptr(frames), N, W, H, qp, _stream(stream)), "calibrate_fp8")
 
     def fp8_scales(self) -> np.ndarray:
@@ -194,9 +221,11 @@ class Codec:
         return int(lib.ufvc_max_bitstream_bytes(self.h, width, height))
 
     def encode_chunk(self, frames: torch.Tensor, qp: int = 32, bits: torch.Tensor | None = None,
-                     nbytes: torch.Tensor | None = None, stream=None):
-        """frames: cuda uint8 [N][H][W][3] -> (bits cuda uint8 [capacity], nbytes cuda int64 [1])."""
-        N, H, W, _ = frames.shape
+                     nbytes: torch.Tensor | None = None, stream=None, width=None, height=None):
+        """frames: cuda uint8 chunk in the context's colour format -> (bits cuda uint8 [capacity], nbytes
+        cuda int64 [1])."""
+        N = frames.shape[0]
+        W, H = self.frame_dims(frames, width, height)
         if bits is None:
             bits = torch.empty(self.max_bitstream_bytes(W, H), dtype=torch.uint8, device=frames.device)
         if nbytes is None:
@@ -208,15 +237,18 @@ class Codec:
     def decode_chunk(self, bits: torch.Tensor, nbytes: int, width: int, height: int, out: torch.Tensor | None = None,
                      f32: bool = False, stream=None) -> torch.Tensor:
         if out is None:
-            out = torch.empty((self.N, height, width, 3), dtype=torch.float32 if f32 else torch.uint8,
-                              device=bits.device)
+            shape = (self.N, height, width, 3) if self.color in (COLOR_RGB, COLOR_RGB_BT709) else \
+                (self.N, 3, height, width) if self.color == COLOR_YUV444P else (self.N, frame_bytes(self.color, width, height))
+            out = torch.empty(shape, dtype=torch.float32 if f32 else torch.uint8, device=bits.device)
         fn = lib.ufvc_decode_chunk_f32 if f32 else lib.ufvc_decode_chunk
         self._check(fn(self.h, _ptr(bits), int(nbytes), _ptr(out), self.N, width, height, _stream(stream)),
                     "decode_chunk")
         return out
 
-    def encode_chunk_host(self, frames: np.ndarray | torch.Tensor, qp: int = 32, stream=None) -> bytes:
-        N, H, W, _ = frames.shape
+    def encode_chunk_host(self, frames: np.ndarray | torch.Tensor, qp: int = 32, stream=None, width=None,
+                          height=None) -> bytes:
+        N = frames.shape[0]
+        W, H = self.frame_dims(frames, width, height)
         cap = self.max_bitstream_bytes(W, H)
         out = torch.empty(cap, dtype=torch.uint8).pin_memory() if torch.cuda.is_available() else np.empty(cap, np.uint8)
         nb = C.c_size_t()
@@ -227,7 +259,9 @@ class Codec:
 
     def decode_chunk_host(self, bits, width: int, height: int, out=None, stream=None):
         if out is None:
-            out = np.empty((self.N, height, width, 3), np.uint8)
+            out = np.empty(self.N * frame_bytes(self.color, width, height), np.uint8)
+            if self.color in (COLOR_RGB, COLOR_RGB_BT709):
+                out = out.reshape(self.N, height, width, 3)
         src = bits if isinstance(bits, (np.ndarray, torch.Tensor)) else np.frombuffer(bits, np.uint8).copy()
         n = src.numel() if isinstance(src, torch.Tensor) else src.size
         self._check(lib.ufvc_decode_chunk_host(self.h, _ptr(src), n, _ptr(out), self.N, width, height,
@@ -238,8 +272,8 @@ class Codec:
         return int(lib.ufvc_sync_status(self.h, _stream(stream)))
 
     # ---- stages
-    def encode_stages(self, frames: torch.Tensor, qp: int = 32, stream=None) -> dict:
-        N, H, W, _ = frames.shape
+    def encode_stages(self, frames: torch.Tensor, qp: int = 32, stream=None, width=None, height=None) -> dict:
+        W, H = self.frame_dims(frames, width, height)
         d = latent_dims(self.arch, W, H)
         dev = frames.device
         yshape = (d["Hy"], d["Wy"], d["Cy"])
