@@ -365,5 +365,120 @@ def decode_chunk(arch: int, N: int, bits: bytes, H: int, W: int, weights: np.nda
     return frames, yhat
 
 
+# ---------------------------------------------------------------- temporal chunk context
+class _Opts(C.Structure):
+    _fields_ = [("pm", C.c_void_p), ("tw", C.c_void_p), ("c_in", C.c_void_p), ("c_out", C.c_void_p)]
+
+
+def temporal_weight_count(arch: int, N: int) -> int:
+    lib().orc_temporal_weight_count.restype = C.c_size_t
+    return int(lib().orc_temporal_weight_count(arch, N))
+
+
+def context_dims(arch: int, H: int, W: int) -> tuple[int, int, int]:
+    v = [C.c_int() for _ in range(3)]
+    _check(lib().orc_context_dims(arch, H, W, *[C.byref(t) for t in v]), "context_dims")
+    return tuple(t.value for t in v)
+
+
+def chunk_feature(arch: int, N: int, yhat: np.ndarray, tw: np.ndarray, c_in: np.ndarray | None) -> np.ndarray:
+    """F_i = GELU(PS(FD(y^))) + FC(C_i)  [2Hy][2Wy][64]; c_in None = the first chunk (C = 0)."""
+    yhat = np.ascontiguousarray(yhat, np.float64)
+    tw = np.ascontiguousarray(tw, np.float32)
+    Hy, Wy, _ = yhat.shape
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    F = np.empty((2 * Hy, 2 * Wy, 64), np.float64)
+    _check(lib().orc_chunk_feature(arch, N, _p(yhat), Hy, Wy, _p(tw), _p(ci) if ci is not None else None, _p(F)),
+           "chunk_feature")
+    return F
+
+
+def context_next(arch: int, N: int, F: np.ndarray, tw: np.ndarray) -> np.ndarray:
+    F = np.ascontiguousarray(F, np.float64)
+    tw = np.ascontiguousarray(tw, np.float32)
+    H8, W8, _ = F.shape
+    c = np.empty((H8, W8, 64), np.float64)
+    _check(lib().orc_context_next(arch, N, _p(F), H8, W8, _p(tw), _p(c)), "context_next")
+    return c
+
+
+def context_terms(arch: int, N: int, c_in: np.ndarray | None, H8: int, W8: int, tw: np.ndarray):
+    """(EC(C_i) [H8][W8][e2], PC(C_i) [H8/2][W8/2][Cz])."""
+    tw = np.ascontiguousarray(tw, np.float32)
+    e2, cz = {0: (128, 64), 1: (192, 128)}[arch]
+    ec = np.empty((H8, W8, e2), np.float64)
+    pc = np.empty((H8 // 2, W8 // 2, cz), np.float64)
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    _check(lib().orc_context_terms(arch, N, _p(ci) if ci is not None else None, H8, W8, _p(tw), _p(ec), _p(pc)),
+           "context_terms")
+    return ec, pc
+
+
+def synthesis_f(arch: int, N: int, yhat: np.ndarray, F: np.ndarray, H: int, W: int, weights: np.ndarray,
+                tw: np.ndarray) -> np.ndarray:
+    yhat = np.ascontiguousarray(yhat, np.float64)
+    F = np.ascontiguousarray(F, np.float64)
+    tw = np.ascontiguousarray(tw, np.float32)
+    Hy, Wy, _ = yhat.shape
+    out = np.empty((N, H, W, 3), np.float64)
+    _check(lib().orc_synthesis_f(arch, N, _p(yhat), Hy, Wy, H, W, _p(weights), _p(F), _p(tw), _p(out)),
+           "synthesis_f")
+    return out
+
+
+def encode_chunk_t(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.ndarray, tw: np.ndarray,
+                   c_in: np.ndarray | None, mean_weights: np.ndarray | None = None, debug: bool = False):
+    """Temporal-context encode: -> (bits, C_{i+1}) or, with debug, (bits, C_{i+1}, intermediates)."""
+    frames = np.ascontiguousarray(frames, np.uint8)
+    N, H, W, _ = frames.shape
+    d = latent_dims(arch, H, W)
+    H8, W8, Cc = context_dims(arch, H, W)
+    ny = d["Hy"] * d["Wy"] * d["Cy"]
+    nz = d["Hz"] * d["Wz"] * d["Cz"]
+    cap = 64 + d["Cz"] + 4 * (K + min(K, nz)) + 2 * (ny + nz + 4 * K) + 16
+    out = np.empty(cap, np.uint8)
+    nbytes = C.c_size_t()
+    tw = np.ascontiguousarray(tw, np.float32)
+    mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    c_out = np.empty((H8, W8, Cc), np.float64)
+    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data, ci.ctypes.data if ci is not None else None,
+              c_out.ctypes.data)
+    arrs, dbg = {}, None
+    if debug:
+        arrs = dict(y=np.empty((d["Hy"], d["Wy"], d["Cy"])), z=np.empty((d["Hz"], d["Wz"], d["Cz"])),
+                    zhat=np.empty((d["Hz"], d["Wz"], d["Cz"]), np.int16), iz=np.empty(d["Cz"], np.uint8),
+                    mu=np.empty((d["Hy"], d["Wy"], d["Cy"])), logsig=np.empty((d["Hy"], d["Wy"], d["Cy"])),
+                    rhat=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.int16),
+                    idx=np.empty((d["Hy"], d["Wy"], d["Cy"]), np.uint8),
+                    s=np.empty((d["Hy"], d["Wy"], d["Cz"])), yhat=np.empty((d["Hy"], d["Wy"], d["Cy"])))
+        dbg = _Debug(**{k: v.ctypes.data for k, v in arrs.items()})
+    rc = lib().orc_encode_chunk_opts(arch, N, _p(frames), H, W, qp, K, _p(weights), C.byref(o), _p(out),
+                                     C.c_size_t(cap), C.byref(nbytes), C.byref(dbg) if dbg is not None else None)
+    _check(rc, "encode_chunk_opts")
+    bits = out[:nbytes.value].tobytes()
+    return (bits, c_out, arrs) if debug else (bits, c_out)
+
+
+def decode_chunk_t(arch: int, N: int, bits: bytes, H: int, W: int, weights: np.ndarray, tw: np.ndarray,
+                   c_in: np.ndarray | None, mean_weights: np.ndarray | None = None):
+    """Temporal-context decode: -> (frames [N][H][W][3] in [0, 1], y^, C_{i+1})."""
+    d = latent_dims(arch, H, W)
+    H8, W8, Cc = context_dims(arch, H, W)
+    a = np.frombuffer(bits, np.uint8).copy()
+    yhat = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
+    frames = np.empty((N, H, W, 3), np.float64)
+    tw = np.ascontiguousarray(tw, np.float32)
+    mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    c_out = np.empty((H8, W8, Cc), np.float64)
+    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data, ci.ctypes.data if ci is not None else None,
+              c_out.ctypes.data)
+    rc = lib().orc_decode_chunk_opts(arch, N, _p(a), C.c_size_t(len(bits)), H, W, _p(weights), C.byref(o),
+                                     _p(frames), _p(yhat))
+    _check(rc, "decode_chunk_opts")
+    return frames, yhat, c_out
+
+
 def num_threads() -> int:
     return int(lib().orc_num_threads())

@@ -46,6 +46,8 @@
 #define PROB_BITS 16
 #define PROB_M (1u << PROB_BITS)
 #define RANS_L (1u << 16) /* lower bound of the 32-bit rANS state */
+#define ORC_CF 64         /* temporal chunk feature channels */
+#define ORC_CC 64         /* temporal context channels */
 
 /* ------------------------------------------------------------------------------------------------ */
 /* Architecture (plain reading of Fig. 3; widths per workload)                                      */
@@ -261,7 +263,17 @@ int orc_color_out(int fmt, const double* x, int N, int H, int W, double* out) {
 /* Chunk -> latent y [Hy][Wy][Cy] from the network's input channels x [N][H][W][3] in [0, 1]: frame n
  * -> channels 3n..3n+2, replicate-padded to multiples of 16.  Then A1..A3 (3x3 stride 2 + GELU), the
  * interaction block h + Xb(GELU(Xa(h))), A4 (3x3 stride 2). */
+static int analysis_core(int arch, int N, const double* xin, int H, int W, const float* wts, const double* add_h3,
+                         double* y);
+
 int orc_analysis_x(int arch, int N, const double* xin, int H, int W, const float* wts, double* y) {
+    return analysis_core(arch, N, xin, H, W, wts, NULL, y);
+}
+
+/* add_h3 (optional, [H/8][W/8][e2] of the padded size): added to the A3 output before the interaction
+ * block (the temporal-context conditioning of the chunk encoder). */
+static int analysis_core(int arch, int N, const double* xin, int H, int W, const float* wts, const double* add_h3,
+                         double* y) {
     arch_t a;
     if (get_arch(arch, &a) || N < 1 || H < 1 || W < 1) return ORC_ERR_ARG;
     int Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16, C0 = 3 * N;
@@ -290,6 +302,8 @@ int orc_analysis_x(int arch, int N, const double* xin, int H, int W, const float
     layer_ptr(arch, N, wts, 2, &wk, &bk);
     orc_conv2d(t2, h2, w2, a.e1, wk, bk, a.e2, 3, 2, t3);
     gelu_inplace(t3, n3);
+    if (add_h3)
+        for (size_t i = 0; i < n3; i++) t3[i] += add_h3[i];
     /* cross-frame interaction: h + Xb(GELU(Xa(h))) */
     double* u = dalloc(n3);
     double* v = dalloc(n3);
@@ -410,8 +424,17 @@ int orc_quantize_z(const double* z, int npos, int cz, int16_t* zhat, uint8_t* iz
 /* Hyper-synthesis (single-step parameter estimation, Sec. 3.4): from z^ alone, one pass gives mu and
  * log sigma for every latent element.  S1, S2: 3x3 conv Cz -> 4Cz, pixel shuffle x2, GELU; crop to
  * (Hy, Wy); S3: 1x1 conv Cz -> 2Cy; channels [0, Cy) are mu, [Cy, 2Cy) are log sigma. */
+static int hyper_synthesis_core(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
+                                const float* wts, const double* add_s, double* mu, double* logsig, double* s_out);
+
 int orc_hyper_synthesis_s(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
                           const float* wts, double* mu, double* logsig, double* s_out) {
+    return hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, NULL, mu, logsig, s_out);
+}
+
+/* add_s (optional, [Hy][Wy][Cz]): added to the S2 features before S3 (the prior's temporal context). */
+static int hyper_synthesis_core(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
+                                const float* wts, const double* add_s, double* mu, double* logsig, double* s_out) {
     arch_t a;
     if (get_arch(arch, &a) || 4 * Hz < Hy || 4 * Wz < Wy) return ORC_ERR_ARG;
     const float *wk, *bk;
@@ -435,6 +458,8 @@ int orc_hyper_synthesis_s(int arch, int N, const int16_t* zhat, int Hz, int Wz, 
     double* s2c = dalloc((size_t)Hy * Wy * cz);
     for (int h = 0; h < Hy; h++)
         memcpy(s2c + (size_t)h * Wy * cz, s2 + (size_t)h * (2 * W1) * cz, sizeof(double) * Wy * cz);
+    if (add_s)
+        for (size_t i = 0; i < (size_t)Hy * Wy * cz; i++) s2c[i] += add_s[i];
     double* p = dalloc((size_t)Hy * Wy * 2 * a.cy);
     layer_ptr(arch, N, wts, 10, &wk, &bk);
     orc_conv2d(s2c, Hy, Wy, cz, wk, bk, 2 * a.cy, 1, 1, p);
@@ -717,8 +742,20 @@ int orc_rans_decode(const uint8_t* in, size_t avail, const uint8_t* tab, size_t 
 /* Decoder f: D0 3x3 Cy->4Cd1, PS, GELU; R1: h + R1b(GELU(R1a(h))); U1 3x3 Cd1->4Cd2, PS, GELU;
  * R2: h + R2b(GELU(R2a(h))); U2 3x3 Cd2->4Cd2, PS, GELU; U3 3x3 Cd2->12, PS -> o (3 channels);
  * x^ = clamp(0.5 + o, 0, 1), cropped to H x W.  frames: [N][H][W][3] doubles in [0, 1]. */
+static int synthesis_core(int arch, int N, const double* yhat, int Hy, int Wy, int H, int W, const float* wts,
+                          const double* F, const float* tw, double* frames);
+
 int orc_synthesis(int arch, int N, const double* yhat, int Hy, int Wy, int H, int W, const float* wts,
                   double* frames) {
+    return synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, NULL, NULL, frames);
+}
+
+static void temporal_layer_ptr(int arch, int N, const float* blob, int l, const float** w, const float** b);
+
+/* F (optional, the chunk feature [2Hy][2Wy][Cf]) with the temporal blob tw: each frame decoder adds its
+ * own 1x1 projection DF_f(F) to its D0 output. */
+static int synthesis_core(int arch, int N, const double* yhat, int Hy, int Wy, int H, int W, const float* wts,
+                          const double* F, const float* tw, double* frames) {
     arch_t a;
     if (get_arch(arch, &a) || 16 * Hy < H || 16 * Wy < W) return ORC_ERR_ARG;
     for (int f = 0; f < N; f++) {
@@ -735,6 +772,14 @@ int orc_synthesis(int arch, int N, const double* yhat, int Hy, int Wy, int H, in
         h *= 2; w *= 2;
         size_t n1 = (size_t)h * w * a.cd1;
         gelu_inplace(h1, n1);
+        if (F && tw) {
+            const float *wd, *bd;
+            double* df = dalloc(n1);
+            temporal_layer_ptr(arch, N, tw, 5 + f, &wd, &bd);
+            orc_conv2d(F, h, w, ORC_CF, wd, bd, a.cd1, 1, 1, df);
+            for (size_t i = 0; i < n1; i++) h1[i] += df[i];
+            free(df);
+        }
         /* R1 */
         double* u = dalloc(n1);
         double* v = dalloc(n1);
@@ -793,6 +838,116 @@ int orc_synthesis(int arch, int N, const double* yhat, int Hy, int Wy, int H, in
 }
 
 /* ------------------------------------------------------------------------------------------------ */
+/* Temporal chunk context (Sec. 3.1, Fig. 3; Sec. 3.3)                                              */
+/* ------------------------------------------------------------------------------------------------ */
+/* Chunk i is coded conditioned on a context C_i generated from chunk i-1's decoded feature.  Reading of
+ * the figure on the plain layers (Cf = Cc = 64 channels, all at 1/8 of the padded frame size):
+ *   chunk feature   F_i     = GELU(PS(FD(y^_i))) + FC(C_i)       FD 3x3 Cy -> 4 Cf, FC 1x1 Cc -> Cf
+ *   next context    C_{i+1} = GELU(CG(F_i))                      CG 3x3 Cf -> Cc
+ *   encoder         A3 output + EC(C_i) before the interaction   EC 1x1 Cc -> e2
+ *   prior           S2 features + PC(C_i) before S3              PC 3x3 stride 2 Cc -> Cz
+ *   frame decoder f D0 output + DF_f(F_i)                        DF_f 1x1 Cf -> Cd1
+ * The first chunk of a stream uses C_0 = 0.  Blob: EC, FD, FC, CG, PC, then DF_f for f = 0..N-1, each
+ * kernel [Cout][k][k][Cin] then bias [Cout]. */
+int orc_temporal_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
+    arch_t a;
+    if (get_arch(arch, &a) || N < 1 || l < 0 || l >= 5 + N) return ORC_ERR_ARG;
+    int t[5][3] = {{a.e2, 1, ORC_CC}, {4 * ORC_CF, 3, a.cy}, {ORC_CF, 1, ORC_CC}, {ORC_CC, 3, ORC_CF},
+                   {a.cz, 3, ORC_CC}};
+    if (l < 5) { *cout = t[l][0]; *k = t[l][1]; *cin = t[l][2]; }
+    else { *cout = a.cd1; *k = 1; *cin = ORC_CF; }
+    return ORC_OK;
+}
+
+size_t orc_temporal_weight_count(int arch, int N) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < 5 + N; l++) {
+        if (orc_temporal_layer_shape(arch, N, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
+static void temporal_layer_ptr(int arch, int N, const float* blob, int l, const float** w, const float** b) {
+    size_t off = 0;
+    int co, k, ci;
+    for (int i = 0; i < l; i++) {
+        orc_temporal_layer_shape(arch, N, i, &co, &k, &ci);
+        off += (size_t)co * k * k * ci + co;
+    }
+    orc_temporal_layer_shape(arch, N, l, &co, &k, &ci);
+    *w = blob + off;
+    *b = blob + off + (size_t)co * k * k * ci;
+}
+
+/* Context dims: [H8][W8][Cc] with H8, W8 = the padded frame size / 8 (= 2 Hy, 2 Wy). */
+int orc_context_dims(int arch, int H, int W, int* H8, int* W8, int* Cc) {
+    arch_t a;
+    if (get_arch(arch, &a) || H < 1 || W < 1) return ORC_ERR_ARG;
+    *H8 = (H + 15) / 16 * 2;
+    *W8 = (W + 15) / 16 * 2;
+    *Cc = ORC_CC;
+    return ORC_OK;
+}
+
+/* One 1x1 / 3x3 temporal layer l on x [H][W][cin] (c == NULL stands for the all-zero first context). */
+static void temporal_conv(int arch, int N, const float* tw, int l, const double* x, int H, int W, int stride,
+                          double* out) {
+    const float *wk, *bk;
+    int co, k, ci;
+    orc_temporal_layer_shape(arch, N, l, &co, &k, &ci);
+    temporal_layer_ptr(arch, N, tw, l, &wk, &bk);
+    if (x) {
+        orc_conv2d(x, H, W, ci, wk, bk, co, k, stride, out);
+    } else {
+        int Ho = conv_out(H, k, stride), Wo = conv_out(W, k, stride);
+        for (size_t i = 0; i < (size_t)Ho * Wo; i++)
+            for (int c = 0; c < co; c++) out[i * co + c] = bk[c];
+    }
+}
+
+/* F_i from y^_i [Hy][Wy][Cy] and C_i (NULL: zero), F: [2Hy][2Wy][Cf]. */
+int orc_chunk_feature(int arch, int N, const double* yhat, int Hy, int Wy, const float* tw, const double* c_in,
+                      double* F) {
+    arch_t a;
+    if (get_arch(arch, &a) || !tw) return ORC_ERR_ARG;
+    const size_t n8 = (size_t)4 * Hy * Wy;
+    double* t = dalloc(n8 * ORC_CF);
+    double* fc = dalloc(n8 * ORC_CF);
+    temporal_conv(arch, N, tw, 1, yhat, Hy, Wy, 1, t);
+    orc_pixel_shuffle(t, Hy, Wy, ORC_CF, F);
+    gelu_inplace(F, n8 * ORC_CF);
+    temporal_conv(arch, N, tw, 2, c_in, 2 * Hy, 2 * Wy, 1, fc);
+    for (size_t i = 0; i < n8 * ORC_CF; i++) F[i] += fc[i];
+    free(t); free(fc);
+    return ORC_OK;
+}
+
+/* C_{i+1} = GELU(CG(F_i)), [H8][W8][Cc]. */
+int orc_context_next(int arch, int N, const double* F, int H8, int W8, const float* tw, double* c_out) {
+    if (!tw) return ORC_ERR_ARG;
+    temporal_conv(arch, N, tw, 3, F, H8, W8, 1, c_out);
+    gelu_inplace(c_out, (size_t)H8 * W8 * ORC_CC);
+    return ORC_OK;
+}
+
+/* The conditioning terms from C_i: EC(C_i) [H8][W8][e2] (encoder) and PC(C_i) [H8/2][W8/2][Cz] (prior). */
+int orc_context_terms(int arch, int N, const double* c_in, int H8, int W8, const float* tw, double* ec, double* pc) {
+    if (!tw) return ORC_ERR_ARG;
+    if (ec) temporal_conv(arch, N, tw, 0, c_in, H8, W8, 1, ec);
+    if (pc) temporal_conv(arch, N, tw, 4, c_in, H8, W8, 2, pc);
+    return ORC_OK;
+}
+
+/* Frame-specific synthesis with the chunk feature (temporal mode). */
+int orc_synthesis_f(int arch, int N, const double* yhat, int Hy, int Wy, int H, int W, const float* wts,
+                    const double* F, const float* tw, double* frames) {
+    if (!F || !tw) return ORC_ERR_ARG;
+    return synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, F, tw, frames);
+}
+
+/* ------------------------------------------------------------------------------------------------ */
 /* Whole chunk: encode and decode with the bit-stream container                                     */
 /* ------------------------------------------------------------------------------------------------ */
 /* Container (little-endian): "UFVC", u8 version, u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K,
@@ -830,9 +985,29 @@ int orc_latent_dims(int arch, int H, int W, int* Hy, int* Wy, int* Hz, int* Wz, 
     return ORC_OK;
 }
 
-/* pm: the mean-network blob (version-2 stream with progressive means), or NULL (version 1). */
+/* Coding options: pm = the mean-network blob (progressive means) or NULL; tw = the temporal-context blob
+ * or NULL; c_in = C_i [H8][W8][Cc] (NULL: the first chunk, C = 0); c_out = C_{i+1} (may be NULL).
+ * Container version = 1 + (pm != NULL) + 2 (tw != NULL). */
+typedef struct {
+    const float* pm;
+    const float* tw;
+    const double* c_in;
+    double* c_out;
+} orc_opts;
+
+int orc_encode_chunk_opts(int arch, int N, const uint8_t* frames, int H, int W, int qp, int K, const float* wts,
+                          const orc_opts* o, uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg);
+
 int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int qp, int K, const float* wts,
                      const float* pm, uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg) {
+    orc_opts o = {pm, NULL, NULL, NULL};
+    return orc_encode_chunk_opts(arch, N, frames, H, W, qp, K, wts, &o, out, cap, nbytes, dbg);
+}
+
+int orc_encode_chunk_opts(int arch, int N, const uint8_t* frames, int H, int W, int qp, int K, const float* wts,
+                          const orc_opts* o, uint8_t* out, size_t cap, size_t* nbytes, orc_debug* dbg) {
+    const float* pm = o->pm;
+    const float* tw = o->tw;
     int Hy, Wy, Hz, Wz, Cy, Cz;
     if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz) || N < 1 || N > 255 || qp < 0 || qp > 63 ||
         K < 1 || W > 65535 || H > 65535)
@@ -851,12 +1026,19 @@ int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int q
     uint32_t* cum = (uint32_t*)malloc(sizeof(uint32_t) * NBINS * (NSYM + 1));
     double* sp = dalloc((size_t)Hy * Wy * Cz);
     double* yh = dalloc(ny);
+    double* xin = dalloc((size_t)N * H * W * 3);
+    int e2 = 0, k_, c_;
+    orc_layer_shape(arch, N, 2, &e2, &k_, &c_);  /* A3's width: the encoder features at 1/8 */
+    double* ec = tw ? dalloc((size_t)4 * Hy * Wy * e2) : NULL;
+    double* pc = tw ? dalloc((size_t)Hy * Wy * Cz) : NULL;
     int rc = ORC_OK;
     orc_build_tables(freq, cum);
-    orc_analysis(arch, N, frames, H, W, wts, y);
+    orc_color_in(0, frames, N, H, W, xin);
+    if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, ec, pc);
+    analysis_core(arch, N, xin, H, W, wts, ec, y);
     orc_hyper_analysis(arch, N, y, Hy, Wy, wts, z);
     orc_quantize_z(z, Hz * Wz, Cz, zhat, iz);
-    orc_hyper_synthesis_s(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls, sp);
+    hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, pc, mu, ls, sp);
     orc_quantize_y(y, mu, ls, ny, qp, rhat, idx);
     if (pm) {
         double* mu0 = dalloc(ny);
@@ -868,13 +1050,19 @@ int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int q
         double q = orc_qstep(qp);
         for (size_t i = 0; i < ny; i++) yh[i] = rhat[i] * q + mu[i];
     }
+    if (tw && o->c_out) {  /* the encoder tracks the decoder's context: F and C_{i+1} from its own y^ */
+        double* F = dalloc((size_t)4 * Hy * Wy * ORC_CF);
+        orc_chunk_feature(arch, N, yh, Hy, Wy, tw, o->c_in, F);
+        orc_context_next(arch, N, F, 2 * Hy, 2 * Wy, tw, o->c_out);
+        free(F);
+    }
     for (size_t i = 0; i < nz; i++) zidx[i] = iz[i % Cz];
     size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
     int Kz = (size_t)K < nz ? K : (int)nz;
     if (cap < hdr) { rc = ORC_ERR_CAPACITY; goto done; }
     memset(out, 0, hdr);
     memcpy(out, "UFVC", 4);
-    out[4] = pm ? 2 : 1; out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
+    out[4] = (uint8_t)(1 + (pm ? 1 : 0) + (tw ? 2 : 0)); out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
     put16(out + 8, (uint32_t)W); put16(out + 10, (uint32_t)H);
     put32(out + 12, (uint32_t)K); put32(out + 16, (uint32_t)Kz);
     memcpy(out + 20, iz, Cz);
@@ -897,7 +1085,7 @@ int orc_encode_chunk(int arch, int N, const uint8_t* frames, int H, int W, int q
     }
 done:
     free(y); free(z); free(zhat); free(mu); free(ls); free(rhat); free(idx); free(zidx); free(freq); free(cum);
-    free(sp); free(yh);
+    free(sp); free(yh); free(xin); free(ec); free(pc);
     return rc;
 }
 
@@ -905,13 +1093,27 @@ done:
  * decode r^ for the whole latent in one step, y^ = r^ q + mu (version 2: the progressive means, which
  * need the mean-network blob pm), then the N frame-specific decoders.
  * frames_out: [N][H][W][3] doubles in [0, 1]; yhat_out (optional): [Hy][Wy][Cy]. */
+int orc_decode_chunk_opts(int arch, int N, const uint8_t* bits, size_t nbytes, int H, int W, const float* wts,
+                          const orc_opts* o, double* frames_out, double* yhat_out);
+
 int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H, int W, const float* wts,
                      const float* pm, double* frames_out, double* yhat_out) {
+    orc_opts o = {pm, NULL, NULL, NULL};
+    return orc_decode_chunk_opts(arch, N, bits, nbytes, H, W, wts, &o, frames_out, yhat_out);
+}
+
+/* Version 3 / 4 (temporal context) streams need o->tw and decode against o->c_in; versions 1 / 2 need
+ * tw == NULL.  With tw, c_out receives C_{i+1}. */
+int orc_decode_chunk_opts(int arch, int N, const uint8_t* bits, size_t nbytes, int H, int W, const float* wts,
+                          const orc_opts* o, double* frames_out, double* yhat_out) {
+    const float* pm = o->pm;
+    const float* tw = o->tw;
     int Hy, Wy, Hz, Wz, Cy, Cz;
     if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz)) return ORC_ERR_ARG;
     size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
-    if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] < 1 || bits[4] > 2) return ORC_ERR_CORRUPT;
-    if (bits[4] == 2 && !pm) return ORC_ERR_ARG;
+    if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] < 1 || bits[4] > 4) return ORC_ERR_CORRUPT;
+    const int v_pm = bits[4] == 2 || bits[4] == 4, v_tc = bits[4] >= 3;
+    if ((v_pm && !pm) || (v_tc != (tw != NULL))) return ORC_ERR_ARG;
     if (bits[5] != arch || bits[6] != N || get16(bits + 8) != (uint32_t)W || get16(bits + 10) != (uint32_t)H)
         return ORC_ERR_ARG;
     int qp = bits[7];
@@ -932,15 +1134,18 @@ int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H,
     int16_t* rhat = (int16_t*)malloc(2 * ny);
     double* yhat = dalloc(ny);
     double* sp = dalloc((size_t)Hy * Wy * Cz);
+    double* pc = tw ? dalloc((size_t)Hy * Wy * Cz) : NULL;
+    double* F = tw ? dalloc((size_t)4 * Hy * Wy * ORC_CF) : NULL;
     size_t used1 = 0, used2 = 0;
     int rc = orc_rans_decode(bits + hdr, nbytes - hdr, zidx, nz, Kz, freq, cum, NSYM, RMAX, zhat, &used1);
     if (rc) goto done;
-    orc_hyper_synthesis_s(arch, N, zhat, Hz, Wz, Hy, Wy, wts, mu, ls, sp);
+    if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, NULL, pc);
+    hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, pc, mu, ls, sp);
     orc_scale_index(ls, ny, qp, idx);
     rc = orc_rans_decode(bits + hdr + used1, nbytes - hdr - used1, idx, ny, K, freq, cum, NSYM, RMAX, rhat, &used2);
     if (rc) goto done;
     if (hdr + used1 + used2 != nbytes) { rc = ORC_ERR_CORRUPT; goto done; }
-    if (bits[4] == 2) {
+    if (v_pm) {
         double* mu_used = dalloc(ny);
         rc = orc_progressive_means(arch, NULL, rhat, mu, sp, Hy, Wy, qp, pm, yhat, mu_used);
         free(mu_used);
@@ -950,9 +1155,14 @@ int orc_decode_chunk(int arch, int N, const uint8_t* bits, size_t nbytes, int H,
         for (size_t i = 0; i < ny; i++) yhat[i] = rhat[i] * q + mu[i];
     }
     if (yhat_out) memcpy(yhat_out, yhat, sizeof(double) * ny);
-    if (frames_out) orc_synthesis(arch, N, yhat, Hy, Wy, H, W, wts, frames_out);
+    if (tw) {
+        orc_chunk_feature(arch, N, yhat, Hy, Wy, tw, o->c_in, F);
+        if (o->c_out) orc_context_next(arch, N, F, 2 * Hy, 2 * Wy, tw, o->c_out);
+    }
+    if (frames_out) synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, F, tw, frames_out);
 done:
     free(freq); free(cum); free(zhat); free(zidx); free(mu); free(ls); free(idx); free(rhat); free(yhat); free(sp);
+    free(pc); free(F);
     return rc;
 }
 

@@ -10,5 +10,6 @@ This package draws random numbers and lays them out; it holds none of the codec'
 * :mod:`synthetic.symbols` -- quantised-latent stress symbols round(mu + Laplace(0, b)).
 """
 from .video import moving_texture, chunk_frames  # noqa: F401
-from .weights import layer_table, draw_weights, ARCHS, mean_layer_table, draw_mean_weights  # noqa: F401
+from .weights import layer_table, draw_weights, ARCHS, mean_layer_table, draw_mean_weights, \
+    temporal_layer_table, draw_temporal_weights  # noqa: F401
 from .symbols import laplace_symbols  # noqa: F401

@@ -96,3 +96,34 @@ def split_mean_weights(blob: np.ndarray, arch: int) -> dict[str, tuple[np.ndarra
         off += n + co
     assert off == blob.size
     return out
+
+
+def temporal_layer_table(arch: int, n_frames: int) -> list[tuple[str, int, int, int]]:
+    """[(name, Cout, k, Cin)] of the temporal-context blob (Cf = Cc = 64)."""
+    a = ARCHS[arch]
+    cf = cc = 64
+    t = [("EC", a["enc"][2], 1, cc), ("FD", 4 * cf, 3, a["cy"]), ("FC", cf, 1, cc), ("CG", cc, 3, cf),
+         ("PC", a["cz"], 3, cc)]
+    t += [(f"DF.{f}", a["cd1"], 1, cf) for f in range(n_frames)]
+    return t
+
+
+def draw_temporal_weights(arch: int, n_frames: int, seed: int = 0, bias_std: float = 0.01) -> np.ndarray:
+    """Flat float32 blob of the temporal-context layers, N(0, 2/fan_in) kernels (own random stream)."""
+    rng = np.random.default_rng([seed, 7])
+    parts = []
+    for _, co, k, ci in temporal_layer_table(arch, n_frames):
+        fan_in = k * k * ci
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
+        parts.append(rng.normal(0.0, bias_std, size=co).astype(np.float32))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def split_temporal_weights(blob: np.ndarray, arch: int, n_frames: int) -> dict[str, tuple[np.ndarray, np.ndarray]]:
+    out, off = {}, 0
+    for name, co, k, ci in temporal_layer_table(arch, n_frames):
+        n = co * k * k * ci
+        out[name] = (blob[off:off + n].reshape(co, k, k, ci), blob[off + n:off + n + co])
+        off += n + co
+    assert off == blob.size
+    return out
