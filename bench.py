@@ -5,7 +5,8 @@ scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
                     [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
-                    [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--serving-window S]
+                    [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--no-temporal]
+                    [--serving-window S]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
 it under the same methodology and reported with the PSNR and bitrate deltas.  Extra keys: the decoder
@@ -295,9 +296,11 @@ def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n
     return out
 
 
-def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist=None, world=1):
+def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist=None, world=1, temporal=False):
     """Encode + decode one chunk per step; per-step CUDA events on the launching stream, L2 flushed
-    between steps (outside the events).  Returns timings, stage profile, stream size and PSNR."""
+    between steps (outside the events).  Returns timings, stage profile, stream size and PSNR.  With
+    temporal, consecutive steps form one stream: each step's chunk is coded against the context the
+    previous step produced (encoder and decoder each double-buffer their own)."""
     import torch
     dev = fr.device
     cap = codec.max_bitstream_bytes(W_, H_)
@@ -307,10 +310,30 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
     out = torch.empty(N * U.frame_bytes(codec.color, W_, H_), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
     nb = 0
+    ce = [codec.new_context(W_, H_), codec.new_context(W_, H_)] if temporal else None
+    cd = [codec.new_context(W_, H_), codec.new_context(W_, H_)] if temporal else None
+    k = [0]
+
+    def enc():
+        if temporal:
+            codec.encode_chunk_tc(fr, ce[k[0] % 2] if k[0] else None, ce[(k[0] + 1) % 2], QP, bits, nbytes,
+                                  width=W_, height=H_)
+        else:
+            codec.encode_chunk(fr, QP, bits, nbytes, width=W_, height=H_)
+
+    def dec():
+        if temporal:
+            # the stream size changes from chunk to chunk: the decoder reads it on the device
+            codec.decode_chunk_tc(bits, bits.numel(), W_, H_, cd[k[0] % 2] if k[0] else None, cd[(k[0] + 1) % 2], out,
+                                  d_nbytes=nbytes)
+            k[0] += 1
+        else:
+            codec.decode_chunk(bits, nb, W_, H_, out)
+
     for _ in range(warmup):  # also establishes the stream size, which the decoder call takes from the host
-        codec.encode_chunk(fr, QP, bits, nbytes, width=W_, height=H_)
+        enc()
         nb = int(nbytes.item())
-        codec.decode_chunk(bits, nb, W_, H_, out)
+        dec()
     assert codec.sync_status() == 0
     rec = out.float().cpu().numpy() / 255.0
     psnr = float(10 * np.log10(1.0 / np.mean((rec - frames_np.ravel() / 255.0) ** 2)))
@@ -325,9 +348,9 @@ def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist
     for i in range(steps):
         flush.fill_(i & 0xFF)
         evs[i][0].record(stream)
-        codec.encode_chunk(fr, QP, bits, nbytes, width=W_, height=H_)
+        enc()
         evs[i][1].record(stream)
-        codec.decode_chunk(bits, nb, W_, H_, out)
+        dec()
         evs[i][2].record(stream)
     torch.cuda.synchronize()
     if dist is not None and world > 1:
@@ -359,6 +382,7 @@ def main() -> None:
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-pm", action="store_true", help="skip the progressive-means variant")
     ap.add_argument("--no-color", action="store_true", help="skip the colour-format variants")
+    ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-context variant")
     ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -488,6 +512,21 @@ def main() -> None:
               "stage_ms_per_step": stage_pm}
         cpm.close()
 
+    # ---- the temporal chunk context (BF16): every step's chunk coded against the previous step's context
+    tcx = None
+    if args.precision == "bf16" and not args.no_temporal:
+        ct = U.Codec(1, N, K, blob, "bf16", device=local, temporal_weights=synthetic.draw_temporal_weights(1, N, seed=0))
+        stc = max(3, args.steps // 2)
+        rt = time_codec(ct, fr, frames_np, W_, H_, stc, 3, True, flush, temporal=True)
+        vt = N * stc / (sum(a + b for a, b in zip(rt["t_enc"], rt["t_dec"])) / 1000.0)
+        st_t = {k: round(sum(m for m, _ in v) / stc, 4) for k, v in
+                sorted(rt["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}
+        tcx = {"value": vt, "enc_fps": N / (statistics.mean(rt["t_enc"]) / 1000.0),
+               "dec_fps": N / (statistics.mean(rt["t_dec"]) / 1000.0), "psnr_db": rt["psnr"],
+               "bytes_per_chunk": rt["nbytes"], "steps": stc, "chunk_context_ms_per_step": st_t.get("chunk_context"),
+               "stage_ms_per_step": st_t}
+        ct.close()
+
     # ---- colour interface (YUV444 model interface): BT.709 RGB and YUV420 chunks of the same content
     color = None
     if args.precision == "bf16" and not args.no_color and (W_, H_) == (W, H):
@@ -573,6 +612,8 @@ def main() -> None:
             line["fp8_path"] = fp8
         if color is not None:
             line["color_formats"] = color
+        if tcx is not None:
+            line["temporal_context_path"] = tcx
         if pm is not None:
             if fp32 is not None:
                 pm["dbitrate_vs_fp32"] = (pm["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]

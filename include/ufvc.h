@@ -102,7 +102,8 @@ size_t ufvc_max_bitstream_bytes(const ufvc_ctx* ctx, int width, int height);
  * qp in [0, 63] sets the quantisation step q = 2^((qp-32)/8).  The bit-stream is written to d_bits
  * (capacity bytes) and its size to *d_nbytes (device uint64).  If the stream would not fit,
  * nothing past `capacity` is written and the status word becomes UFVC_ERR_CAPACITY.
- * Bit-stream layout: "UFVC", u8 version (1; 2 with progressive means, see ufvc_set_progressive_means),
+ * Bit-stream layout: "UFVC", u8 version (1, + 1 with progressive means, + 2 with the temporal context;
+ * see ufvc_set_progressive_means and ufvc_set_temporal_context),
  * u8 arch, u8 N, u8 qp, u16 W, u16 H, u32 K, u32 Kz,
  * Cz bytes of per-channel hyper-latent scale indices, zero padding to 4 bytes; then the z^ section
  * (Kz = min(K, #z^) lanes) and the y^ section (K lanes), each = K u32 lane word counts followed by
@@ -178,6 +179,52 @@ size_t ufvc_frame_bytes(int format, int width, int height);
 /* Set the context's colour format (ufvc_color); it applies to the calls that follow.  UFVC_ERR_ARG for an
  * unknown format.  No device work. */
 ufvc_status ufvc_set_color_format(ufvc_ctx* ctx, int format);
+
+/* ---- temporal chunk context (Sec. 3.1, Fig. 3) ----
+ * Chunk i of a stream is coded conditioned on a context C_i that the decoder generated from chunk i-1:
+ * the chunk feature F_i = GELU(PS(FD(y^_i))) + FC(C_i) (64 channels at 1/8 of the padded frame size) feeds
+ * the frame-specific decoders (each adds its 1x1 projection DF_f(F_i) to its first layer's output) and
+ * gives the next context C_{i+1} = GELU(CG(F_i)) (64 channels at 1/8 size).  The encoder adds EC(C_i)
+ * (1x1) to its patch-embedded features before the cross-frame interaction, and the prior adds PC(C_i)
+ * (3x3 stride 2) to the hyper-synthesis features before their last layer, so the scales depend on C_i:
+ * a chunk decodes only against the context its encoder used.  The encoder recomputes F_i and C_{i+1} from
+ * its own y^ = r^ q + mu, so it tracks the decoder's context exactly (same kernels, same inputs; the
+ * context is in the context's activation type, so a stream decodes in a context of the same precision).
+ * A stream's first chunk uses C_0 = 0.  Layer shapes (a reading of the figure on the plain layers):
+ * EC 1x1 64 -> e2, FD 3x3 Cy -> 256 (pixel shuffle), FC 1x1 64 -> 64, CG 3x3 64 -> 64, PC 3x3/2 64 -> Cz,
+ * DF_f 1x1 64 -> Cd1.  Streams coded this way have container version 3 (4 with progressive means). */
+
+/* Floats of the temporal blob: EC FD FC CG PC, then DF_f for f = 0..chunk_len-1, each the kernel
+ * [Cout][k][k][Cin] followed by the bias [Cout]. */
+size_t ufvc_temporal_weight_count(int arch, int chunk_len);
+
+/* Give the context the temporal-context layers (host blob, uploaded; the caller keeps it).  From then on
+ * every chunk call codes version-3/4 streams; ufvc_encode_chunk / ufvc_decode_chunk act as a stream's
+ * first chunk (C = 0, next context discarded) and the _tc calls below carry the context.  A context
+ * without it reports UFVC_ERR_UNSUPPORTED (status word) for version 3/4 and one with it for version 1/2.
+ * Not for FP8 contexts (UFVC_ERR_UNSUPPORTED).  Call once, before the context is shared. */
+ufvc_status ufvc_set_temporal_context(ufvc_ctx* ctx, const float* weights, size_t n_weights);
+
+/* Bytes of one context buffer for width x height chunks: [ceil(H/16) 2][ceil(W/16) 2][64] of bf16 (BF16
+ * contexts) or float32 (FP32 contexts). */
+size_t ufvc_context_bytes(const ufvc_ctx* ctx, int width, int height);
+
+/* Chunk calls with the stream's context: d_ctx_in = C_i (device, ufvc_context_bytes; NULL for the first
+ * chunk of a stream), d_ctx_out = receives C_{i+1} (NULL: not wanted).  Both 16-byte aligned and distinct;
+ * the caller owns them (double-buffer them across chunks).  Otherwise as ufvc_encode_chunk /
+ * ufvc_decode_chunk(_f32) (f32 != 0: float frames); with d_nbytes (device) the stream size is read on the
+ * device and nbytes is the readable capacity, as in ufvc_decode_chunk_dev.  UFVC_ERR_ARG without
+ * ufvc_set_temporal_context. */
+ufvc_status ufvc_encode_chunk_tc(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height, int qp,
+                                 uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, const void* d_ctx_in,
+                                 void* d_ctx_out, void* stream);
+ufvc_status ufvc_decode_chunk_tc(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, const uint64_t* d_nbytes,
+                                 void* d_frames, int f32, int n_frames, int width, int height, const void* d_ctx_in,
+                                 void* d_ctx_out, void* stream);
+/* ufvc_encode_stages against the context C_i (d_ctx_in, NULL = first chunk). */
+ufvc_status ufvc_encode_stages_tc(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int qp,
+                                  const void* d_ctx_in, float* d_y, int16_t* d_zhat, uint8_t* d_iz, float* d_mu,
+                                  float* d_logsig, int16_t* d_rhat, uint8_t* d_idx, void* stream);
 
 /* ---- progressive means (Sec. 3.4, Fig. 4a and 4c) ----
  * The latent is split into four partitions: channel group g = c / (Cy / 4), position t = 2 (h mod 2)

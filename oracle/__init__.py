@@ -414,6 +414,21 @@ def context_terms(arch: int, N: int, c_in: np.ndarray | None, H8: int, W8: int, 
     return ec, pc
 
 
+def hyper_synthesis_add(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, weights: np.ndarray,
+                        add_s: np.ndarray):
+    """Hyper-synthesis with add_s [Hy][Wy][Cz] added to the features before S3 -> (mu, log sigma, s)."""
+    zhat = np.ascontiguousarray(zhat, np.int16)
+    Hz, Wz, _ = zhat.shape
+    cy, cz = {0: (128, 64), 1: (256, 128)}[arch]
+    mu = np.empty((Hy, Wy, cy), np.float64)
+    ls = np.empty((Hy, Wy, cy), np.float64)
+    sp = np.empty((Hy, Wy, cz), np.float64)
+    add = np.ascontiguousarray(add_s, np.float64)
+    _check(lib().orc_hyper_synthesis_add(arch, N, _p(zhat), Hz, Wz, Hy, Wy, _p(weights), _p(add), _p(mu), _p(ls),
+                                         _p(sp)), "hyper_synthesis_add")
+    return mu, ls, sp
+
+
 def synthesis_f(arch: int, N: int, yhat: np.ndarray, F: np.ndarray, H: int, W: int, weights: np.ndarray,
                 tw: np.ndarray) -> np.ndarray:
     yhat = np.ascontiguousarray(yhat, np.float64)

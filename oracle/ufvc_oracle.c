@@ -432,6 +432,12 @@ int orc_hyper_synthesis_s(int arch, int N, const int16_t* zhat, int Hz, int Wz, 
     return hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, NULL, mu, logsig, s_out);
 }
 
+/* The same pass with the temporal context's term added to the features before S3. */
+int orc_hyper_synthesis_add(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy, const float* wts,
+                            const double* add_s, double* mu, double* logsig, double* s_out) {
+    return hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, add_s, mu, logsig, s_out);
+}
+
 /* add_s (optional, [Hy][Wy][Cz]): added to the S2 features before S3 (the prior's temporal context). */
 static int hyper_synthesis_core(int arch, int N, const int16_t* zhat, int Hz, int Wz, int Hy, int Wy,
                                 const float* wts, const double* add_s, double* mu, double* logsig, double* s_out) {

@@ -93,6 +93,12 @@ struct Plan {
     float *pm_in_e = nullptr, *pm_h_e = nullptr, *pm_mu_e = nullptr;
     float *pm_in_d = nullptr, *pm_h_d = nullptr, *pm_mu_d = nullptr;
     bool pm_enc_ready = false, pm_dec_ready = false;
+    // temporal context: the all-zero context of a stream's first chunk [H8][W8][Cc], the chunk feature
+    // [H8][W8][Cf] (activation type) and the prior's context term [Hy][Wy][Cz] (float) per direction, and
+    // the encoder's own y^ (activation type) from which it tracks the decoder's context
+    float *t_zero = nullptr, *t_F_e = nullptr, *t_pc_e = nullptr, *t_yh_e = nullptr, *t_F_d = nullptr,
+          *t_pc_d = nullptr;
+    bool t_enc_ready = false, t_dec_ready = false;
     bool enc_ready = false, dec_ready = false;
     std::vector<void*> allocs;
     Workspace ws_enc, ws_dec;
@@ -125,6 +131,13 @@ struct ufvc_ctx {
     LayerW pm[kMeanLayers];
     bool pm_on = false;
     int color = UFVC_COLOR_RGB;  // the caller's frame format (ufvc_color)
+    // temporal chunk context (ufvc_set_temporal_context): EC FD FC CG PC and the per-frame DF (grouped);
+    // cur_cin / cur_cout: the context buffers of the call in progress (null: first chunk / not wanted)
+    LayerW tl[TL_N];
+    LayerW tdf;
+    bool tc_on = false;
+    const void* cur_cin = nullptr;
+    void* cur_cout = nullptr;
     std::map<long long, Plan*> plans;
     std::string err;
     // standalone rANS scratch
@@ -342,6 +355,24 @@ static ufvc_status pm_buffers(ufvc_ctx* ctx, Plan* p, bool enc, size_t* dry_byte
     return UFVC_OK;
 }
 
+// The temporal-context buffers of one direction of a plan (the zero context with the encoder half).
+static ufvc_status tc_buffers(ufvc_ctx* ctx, Plan* p, bool enc, size_t* dry_bytes) {
+    const size_t act = ctx->cfg.precision == UFVC_FP32 ? 1 : 2;
+    const size_t n8 = (size_t)4 * p->Hy * p->Wy, ny = p->ny;
+    ufvc_status st = UFVC_OK;
+    struct { float** b; size_t n; } bufs[4] = {
+        {enc ? &p->t_F_e : &p->t_F_d, (n8 * kCf + act - 1) / act},
+        {enc ? &p->t_pc_e : &p->t_pc_d, (size_t)p->Hy * p->Wy * ctx->arch.cz},
+        {enc ? &p->t_yh_e : nullptr, (ny + act - 1) / act},
+        {enc ? &p->t_zero : nullptr, (n8 * kCc + act - 1) / act}};
+    for (auto& e : bufs) {
+        if (!e.b) continue;
+        if (dry_bytes) *dry_bytes += (e.n * sizeof(float) + 255) & ~(size_t)255;
+        else if ((st = dalloc(ctx, p, e.b, e.n)) != UFVC_OK) return st;
+    }
+    return UFVC_OK;
+}
+
 static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out) {
     const long long key = ((long long)W << 20) | H;
     Plan* p;
@@ -371,6 +402,15 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
     if (for_decode && ctx->color != UFVC_COLOR_RGB && !p->fstage &&
         (st = dalloc(ctx, p, &p->fstage, (size_t)ctx->N * p->H * p->W * 3)) != UFVC_OK)
         return st;
+    if (ctx->tc_on && !p->t_enc_ready) {  // the zero context lives with the encoder half: allocate it first
+        if ((st = tc_buffers(ctx, p, true, nullptr)) != UFVC_OK) return st;
+        CK(cudaMemset(p->t_zero, 0, (size_t)4 * p->Hy * p->Wy * kCc * (ctx->cfg.precision == UFVC_FP32 ? 4 : 2)));
+        p->t_enc_ready = true;
+    }
+    if (ctx->tc_on && for_decode && !p->t_dec_ready) {
+        if ((st = tc_buffers(ctx, p, false, nullptr)) != UFVC_OK) return st;
+        p->t_dec_ready = true;
+    }
     if (ctx->pm_on && (for_decode ? !p->pm_dec_ready : !p->pm_enc_ready)) {
         if ((st = pm_buffers(ctx, p, !for_decode, nullptr)) != UFVC_OK) return st;
         (for_decode ? p->pm_dec_ready : p->pm_enc_ready) = true;
@@ -395,6 +435,10 @@ size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
     size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
                           ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
     if (ctx->color != UFVC_COLOR_RGB) bytes += ((size_t)ctx->N * H * W * 3 * sizeof(float) + 255) & ~(size_t)255;
+    if (ctx->tc_on) {
+        tc_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
+        tc_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, false, &bytes);
+    }
     if (ctx->pm_on) {
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, false, &bytes);
@@ -431,7 +475,7 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
 // no_fp8 keeps an FP8 context's layer on bf16 operands
 static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
                                 bool tc, bool pixel_shuffle = false, bool final_layer = false,
-                                const int* shape = nullptr, bool no_fp8 = false) {
+                                const int* shape = nullptr, bool no_fp8 = false, int gstride = D_NDEC) {
     int co, k, ci;
     if (shape) { co = shape[0]; k = shape[1]; ci = shape[2]; }
     else layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
@@ -440,7 +484,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
     L.b_gs = co;
     std::vector<float> w((size_t)groups * L.w_gs, 0.f), b((size_t)groups * co);
     for (int g = 0; g < groups; ++g) {
-        const int l = first + g * D_NDEC;
+        const int l = first + g * gstride;
         const float* src = blob + offs[l];
         for (int o = 0; o < co; ++o)
             for (int t = 0; t < k * k; ++t)
@@ -465,7 +509,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
         std::vector<__nv_bfloat16> wt((size_t)groups * L.cout_pad * K, __float2bfloat16(0.f));
         std::vector<float> bt(b.size());
         for (int g = 0; g < groups; ++g) {
-            const float* src = blob + offs[first + g * D_NDEC];
+            const float* src = blob + offs[first + g * gstride];
             for (int o = 0; o < co; ++o) {
                 for (int t = 0; t < k * k; ++t)
                     for (int i = 0; i < ci; ++i)
@@ -485,7 +529,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
             std::vector<uint8_t> w8((size_t)groups * L.cout_pad * K, 0);
             L.wscale.assign((size_t)groups * co, 1.f);
             for (int g = 0; g < groups; ++g) {
-                const float* src = blob + offs[first + g * D_NDEC];
+                const float* src = blob + offs[first + g * gstride];
                 for (int o = 0; o < co; ++o) {
                     float amax = 0.f;
                     for (size_t e = 0; e < (size_t)k * k * ci; ++e) amax = std::max(amax, std::fabs(src[(size_t)o * k * k * ci + e]));
@@ -504,7 +548,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
         if (final_layer && co == 12 && k == 3 && ci == 64) {
             std::vector<__nv_bfloat16> ws((size_t)groups * 128 * 64, __float2bfloat16(0.f));
             for (int g = 0; g < groups; ++g) {
-                const float* src = blob + offs[first + g * D_NDEC];
+                const float* src = blob + offs[first + g * gstride];
                 for (int c = 0; c < 12; ++c)
                     for (int t = 0; t < 9; ++t)
                         for (int i = 0; i < 64; ++i)
@@ -566,6 +610,9 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
             }
         }
         for (LayerW& L : ctx->pm) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
+        for (LayerW* L : {&ctx->tl[0], &ctx->tl[1], &ctx->tl[2], &ctx->tl[3], &ctx->tl[4], &ctx->tdf}) {
+            cudaFree(L->w); cudaFree(L->b); cudaFree(L->wtc); cudaFree(L->btc);
+        }
         cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
@@ -654,6 +701,9 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     for (int l = 0; l < kMeanLayers; ++l) c->pm[l] = base->pm[l];
     c->pm_on = base->pm_on;
     c->color = base->color;
+    for (int l = 0; l < TL_N; ++l) c->tl[l] = base->tl[l];
+    c->tdf = base->tdf;
+    c->tc_on = base->tc_on;
     c->borrowed = true;
     if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
         cudaFree(c->d_status);
@@ -745,15 +795,36 @@ static bool check_shape(ufvc_ctx* ctx, int n_frames, int width, int height) {
 }
 
 // hyper-synthesis: zhat (int16) -> mu, logsig; deterministic FP32 path in every precision
+// cin (temporal context C_i, [2Hy][2Wy][Cc]) and pc_tmp ([Hy][Wy][Cz] float): the prior's features get
+// PC(C_i) added before S3 (both null without the temporal context)
 static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zhat, float* zf, float* s1, float* s2,
-                                       float* mu, float* ls, cudaStream_t s) {
+                                       float* mu, float* ls, cudaStream_t s, const void* cin = nullptr,
+                                       float* pc_tmp = nullptr) {
     const Arch& a = ctx->arch;
     prof_begin(ctx, "hyper_synthesis", s);
     launch_i16_to_f32(zhat, p->nz, zf, s);
     RUN(conv(ctx, ctx->enc[L_S1], zf, p->Hz, p->Wz, 1, 1, OUT_PS, s1, 2 * p->Hz, 2 * p->Wz, s));
     RUN(conv(ctx, ctx->enc[L_S2], s1, 2 * p->Hz, 2 * p->Wz, 1, 1, OUT_PS, s2, p->Hy, p->Wy, s));  // crop
+    if (cin) {
+        RUN(conv(ctx, ctx->tl[TL_PC], cin, 2 * p->Hy, 2 * p->Wy, 2, 0, OUT_NHWC, pc_tmp, p->Hy, p->Wy, s, nullptr,
+                 nullptr, 0, 0, 0, 0, 1, true));
+        launch_add_f32(s2, pc_tmp, (size_t)p->Hy * p->Wy * a.cz, s);
+    }
     RUN(conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy));
-    prof_end(ctx, s, 4);
+    prof_end(ctx, s, cin ? 6 : 4);
+    return UFVC_OK;
+}
+
+// The chunk feature F_i = GELU(PS(FD(y^))) + FC(C_i) and, with cout, the next context C_{i+1} = GELU(CG(F_i))
+// (temporal context; y^ and the contexts in the activation type).
+static ufvc_status run_chunk_feature(ufvc_ctx* ctx, Plan* p, const void* yhat, const void* cin, float* F, void* cout,
+                                     cudaStream_t s) {
+    const int H8 = 2 * p->Hy, W8 = 2 * p->Wy;
+    prof_begin(ctx, "chunk_context", s);
+    RUN(conv(ctx, ctx->tl[TL_FD], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, F, H8, W8, s));
+    RUN(conv(ctx, ctx->tl[TL_FC], cin, H8, W8, 1, 0, OUT_NHWC, F, H8, W8, s, F));
+    if (cout) RUN(conv(ctx, ctx->tl[TL_CG], F, H8, W8, 1, 1, OUT_NHWC, cout, H8, W8, s));
+    prof_end(ctx, s, cout ? 3 : 2);
     return UFVC_OK;
 }
 
@@ -810,6 +881,9 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);
     RUN(conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s));
     probe(ctx, T_A3, p->a3, (size_t)p->h3 * p->w3 * a.e2, s);
+    const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
+    if (cin)  // temporal context: the patch-embedded features + EC(C_i), in place
+        RUN(conv(ctx, ctx->tl[TL_EC], cin, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3));
     RUN(conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s));
     probe(ctx, T_XT, p->xt, (size_t)p->h3 * p->w3 * a.e2, s);
     // cross-frame interaction residual, in place
@@ -841,19 +915,26 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
         launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
         prof_end(ctx, s, 3);
     }
-    RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s));
+    RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s, cin, p->t_pc_e));
     prof_begin(ctx, "quantize", s);
     launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);
     prof_end(ctx, s, 1);
     if (ctx->pm_on)
         RUN(run_progressive(ctx, p->Hy, p->Wy, p->y, p->rhat, p->mu, p->s2, nullptr, qp, nullptr, p->pm_in_e, p->pm_h_e,
                             p->pm_mu_e, s));
+    if (cin && ctx->cur_cout) {  // the encoder tracks the decoder's context from its own y^ = r^ q + mu
+        const bool f32 = ctx->cfg.precision == UFVC_FP32;
+        launch_dequant(p->rhat, p->mu, p->ny, ctx->d_qstep, nullptr, f32 ? p->t_yh_e : nullptr,
+                       f32 ? nullptr : reinterpret_cast<__nv_bfloat16*>(p->t_yh_e), s, nullptr, 0.f, qp);
+        RUN(run_chunk_feature(ctx, p, p->t_yh_e, cin, p->t_F_e, ctx->cur_cout, s));
+    }
     return UFVC_OK;
 }
 
 // yhat: float [Hy][Wy][Cy] in FP32 precision, bf16 otherwise
+// F: the chunk feature (temporal context), added to every frame decoder's D0 output through its DF_f
 static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* frames_out, int final_mode,
-                                cudaStream_t s) {
+                                cudaStream_t s, const void* F = nullptr) {
     const Arch& a = ctx->arch;
     const int N = ctx->N;
     const int h1 = 2 * p->Hy, w1 = 2 * p->Wy, h2 = 4 * p->Hy, w2 = 4 * p->Wy, h3 = 8 * p->Hy, w3 = 8 * p->Wy;
@@ -862,8 +943,10 @@ static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* 
     prof_begin(ctx, "dec.D0", s);
     RUN(conv(ctx, ctx->dec[D_D0], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, p->bufA, h1, w1, s, nullptr, nullptr, 0, 0, g1, 0,
              N));
+    if (F)
+        RUN(conv(ctx, ctx->tdf, F, h1, w1, 1, 0, OUT_NHWC, p->bufA, h1, w1, s, p->bufA, nullptr, 0, 0, g1, g1, N));
     probe(ctx, T_D0, (const float*)p->bufA, (size_t)N * h1 * w1 * a.cd1, s);
-    prof_end(ctx, s, 1);
+    prof_end(ctx, s, F ? 2 : 1);
     prof_begin(ctx, "dec.R1", s);
     RUN(conv(ctx, ctx->dec[D_R1A], p->bufA, h1, w1, 1, 1, OUT_NHWC, p->bufT, h1, w1, s, nullptr, nullptr, 0, g1, g1, 0,
              N));
@@ -923,7 +1006,7 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     launch_rans_encode(secs, 2, ctx->d_packed, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "bitstream", s);
-    launch_write_header(d_bits, ctx->pm_on ? 2 : 1, ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz,
+    launch_write_header(d_bits, 1 + (ctx->pm_on ? 1 : 0) + (ctx->tc_on ? 2 : 0), ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz,
                         p->iz, ctx->arch.cz, capacity, ctx->d_status, s);
     launch_rans_finalize(secs, 2, d_bits, p->hdr, capacity, d_nbytes, p->off_ws, ctx->d_status, s);
     prof_end(ctx, s, 3);
@@ -946,7 +1029,7 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     const Arch& a = ctx->arch;
     prof_begin(ctx, "parse", s);
     launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, ctx->pm_on,
-                        p->qp_dev, p->ver_dev, p->diz, ctx->d_status, s);
+                        ctx->tc_on, p->qp_dev, p->ver_dev, p->diz, ctx->d_status, s);
     const bool fp32 = ctx->cfg.precision == UFVC_FP32;
     RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
                      p->dzhat};
@@ -959,7 +1042,8 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
     prof_end(ctx, s, 1);
     ctx->cur_ws = &p->ws_dec;
-    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s));
+    const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
+    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s, cin, p->t_pc_d));
     prof_begin(ctx, "scale_index", s);
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
     prof_end(ctx, s, 1);
@@ -977,7 +1061,9 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
                    fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
     if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
     prof_end(ctx, s, ctx->pm_on ? 1 : 2);
-    RUN(run_decoders(ctx, p, fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf, d_frames, final_mode, s));
+    const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
+    if (cin) RUN(run_chunk_feature(ctx, p, yh, cin, p->t_F_d, ctx->cur_cout, s));
+    RUN(run_decoders(ctx, p, yh, d_frames, final_mode, s, cin ? (const void*)p->t_F_d : nullptr));
     CK(cudaGetLastError());
     return UFVC_OK;
 }
@@ -1119,6 +1205,88 @@ extern "C" ufvc_status ufvc_hyper_synthesis(ufvc_ctx* ctx, const int16_t* d_zhat
 }
 
 extern "C" size_t ufvc_mean_weight_count(int arch) { return mean_weight_count(arch); }
+
+extern "C" size_t ufvc_temporal_weight_count(int arch, int chunk_len) { return temporal_weight_count(arch, chunk_len); }
+
+extern "C" ufvc_status ufvc_set_temporal_context(ufvc_ctx* ctx, const float* weights, size_t n_weights) {
+    if (!ctx || !weights) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: bad argument");
+    if (ctx->borrowed) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: context shares another's weights");
+    if (ctx->tc_on) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: already set");
+    if (ctx->cfg.precision == UFVC_FP8)
+        return fail(ctx, UFVC_ERR_UNSUPPORTED, "set_temporal_context: not available in FP8 contexts");
+    if (n_weights != temporal_weight_count(ctx->cfg.arch, ctx->N))
+        return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: weight count");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int nl = TL_N + ctx->N;
+    std::vector<size_t> offs(nl);
+    size_t off = 0;
+    for (int l = 0; l < nl; ++l) {
+        int co, k, ci;
+        temporal_layer_shape(ctx->cfg.arch, ctx->N, l, &co, &k, &ci);
+        offs[l] = off;
+        off += (size_t)co * k * k * ci + co;
+    }
+    for (int l = 0; l <= TL_N; ++l) {  // the five shared layers, then DF grouped over the frame positions
+        int sh[3];
+        temporal_layer_shape(ctx->cfg.arch, ctx->N, l, &sh[0], &sh[1], &sh[2]);
+        LayerW& L = l < TL_N ? ctx->tl[l] : ctx->tdf;
+        ufvc_status st = upload_layer(ctx, L, weights, offs.data(), l, l < TL_N ? 1 : ctx->N, true, l == TL_FD, false,
+                                      sh, true, 1);
+        if (st != UFVC_OK) return st;
+    }
+    ctx->tc_on = true;
+    return UFVC_OK;
+}
+
+extern "C" size_t ufvc_context_bytes(const ufvc_ctx* ctx, int width, int height) {
+    if (!ctx || width < 1 || height < 1) return 0;
+    const size_t es = ctx->cfg.precision == UFVC_FP32 ? 4 : 2;
+    return (size_t)((height + 15) / 16 * 2) * ((width + 15) / 16 * 2) * kCc * es;
+}
+
+// runs fn with the call's context buffers installed (temporal-context contexts only)
+template <class Fn>
+static ufvc_status with_context(ufvc_ctx* ctx, const void* d_ctx_in, void* d_ctx_out, const char* what, Fn fn) {
+    if (!ctx) return UFVC_ERR_ARG;
+    if (!ctx->tc_on) return fail(ctx, UFVC_ERR_ARG, (std::string(what) + ": no temporal context (ufvc_set_temporal_context)").c_str());
+    if (((uintptr_t)d_ctx_in & 15) || ((uintptr_t)d_ctx_out & 15))
+        return fail(ctx, UFVC_ERR_ARG, (std::string(what) + ": context buffers must be 16-byte aligned").c_str());
+    if (d_ctx_in && d_ctx_in == d_ctx_out)
+        return fail(ctx, UFVC_ERR_ARG, (std::string(what) + ": context in and out must differ").c_str());
+    ctx->cur_cin = d_ctx_in;
+    ctx->cur_cout = d_ctx_out;
+    const ufvc_status st = fn();
+    ctx->cur_cin = nullptr;
+    ctx->cur_cout = nullptr;
+    return st;
+}
+
+extern "C" ufvc_status ufvc_encode_chunk_tc(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width,
+                                            int height, int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes,
+                                            const void* d_ctx_in, void* d_ctx_out, void* stream) {
+    return with_context(ctx, d_ctx_in, d_ctx_out, "encode_chunk_tc", [&] {
+        return ufvc_encode_chunk(ctx, d_frames, n_frames, width, height, qp, d_bits, capacity, d_nbytes, stream);
+    });
+}
+
+extern "C" ufvc_status ufvc_decode_chunk_tc(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, const uint64_t* d_nbytes,
+                                            void* d_frames, int f32, int n_frames, int width, int height,
+                                            const void* d_ctx_in, void* d_ctx_out, void* stream) {
+    return with_context(ctx, d_ctx_in, d_ctx_out, "decode_chunk_tc", [&] {
+        return decode_impl(ctx, d_bits, nbytes, d_frames, f32 ? OUT_PS_FINAL_F32 : OUT_PS_FINAL_U8, n_frames, width,
+                           height, stream, d_nbytes);
+    });
+}
+
+extern "C" ufvc_status ufvc_encode_stages_tc(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int qp,
+                                             const void* d_ctx_in, float* d_y, int16_t* d_zhat, uint8_t* d_iz,
+                                             float* d_mu, float* d_logsig, int16_t* d_rhat, uint8_t* d_idx,
+                                             void* stream) {
+    return with_context(ctx, d_ctx_in, nullptr, "encode_stages_tc", [&] {
+        return ufvc_encode_stages(ctx, d_frames, width, height, qp, d_y, d_zhat, d_iz, d_mu, d_logsig, d_rhat, d_idx,
+                                  stream);
+    });
+}
 
 extern "C" size_t ufvc_frame_bytes(int format, int width, int height) {
     if (format < UFVC_COLOR_RGB || format > UFVC_COLOR_YUV420P || width < 1 || height < 1) return 0;

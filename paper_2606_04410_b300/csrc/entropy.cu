@@ -979,10 +979,10 @@ void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, c
 __global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __restrict__ mu, size_t n,
                                const float* __restrict__ qstep_all, const int* __restrict__ qp_dev,
                                float* __restrict__ yf, __nv_bfloat16* __restrict__ yb, uint8_t* __restrict__ y8,
-                               float inv8) {
+                               float inv8, int qp_host) {
     pdl_trigger();
     pdl_wait();
-    const float q = qstep_all[*qp_dev];
+    const float q = qstep_all[qp_dev ? *qp_dev : qp_host];
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float v = __fadd_rn(__fmul_rn((float)rhat[i], q), mu[i]);
         if (yf) yf[i] = v;
@@ -992,8 +992,9 @@ __global__ void dequant_kernel(const int16_t* __restrict__ rhat, const float* __
 }
 
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
-                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8, float inv8) {
-    (void)launch_pdl(dequant_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, rhat, mu, n, qstep_all, qp_dev, yf, yb, y8, inv8);
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8, float inv8, int qp_host) {
+    (void)launch_pdl(dequant_kernel, dim3(grid_for(n, 256)), dim3(256), (size_t)(0), s, rhat, mu, n, qstep_all, qp_dev, yf,
+                     yb, y8, inv8, qp_host);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1031,7 +1032,8 @@ void launch_write_header(uint8_t* out, int version, int arch, int N, int qp, int
 }
 
 __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, int N, int W, int H, int K, int Kz,
-                                    int Cz, int allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status) {
+                                    int Cz, int allow_pm, int temporal, int* qp_dev, int* ver_dev, uint8_t* iz,
+                                    int* status) {
     pdl_trigger();
     pdl_wait();
     if (threadIdx.x != 0) return;
@@ -1039,11 +1041,13 @@ __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, i
     *qp_dev = 32;
     *ver_dev = 1;
     for (int c = 0; c < Cz; ++c) iz[c] = 0;
-    if (nbytes < hdr || b[0] != 'U' || b[1] != 'F' || b[2] != 'V' || b[3] != 'C' || b[4] < 1 || b[4] > 2) {
+    if (nbytes < hdr || b[0] != 'U' || b[1] != 'F' || b[2] != 'V' || b[3] != 'C' || b[4] < 1 || b[4] > 4) {
         set_status(status, UFVC_ERR_CORRUPT);
         return;
     }
-    if (b[4] == 2 && !allow_v2) {  // progressive means, but the context has no mean network
+    const int v_pm = b[4] == 2 || b[4] == 4, v_tc = b[4] >= 3;
+    // progressive means without a mean network, or a temporal-context mismatch with the context
+    if ((v_pm && !allow_pm) || v_tc != temporal) {
         set_status(status, UFVC_ERR_UNSUPPORTED);
         return;
     }
@@ -1057,13 +1061,14 @@ __global__ void parse_header_kernel(const uint8_t* b, size_t nbytes, int arch, i
         iz[c] = b[20 + c];
     }
     *qp_dev = b[7];
-    *ver_dev = b[4];
+    *ver_dev = v_pm ? 2 : 1;
 }
 
 void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
-                         bool allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status, cudaStream_t s) {
+                         bool allow_pm, bool temporal, int* qp_dev, int* ver_dev, uint8_t* iz, int* status,
+                         cudaStream_t s) {
     (void)launch_pdl(parse_header_kernel, dim3(1), dim3(32), (size_t)(0), s, bits, nbytes, arch, N, W, H, K, Kz, Cz,
-                     (int)allow_v2, qp_dev, ver_dev, iz, status);
+                     (int)allow_pm, (int)temporal, qp_dev, ver_dev, iz, status);
 }
 
 }  // namespace ufvc

@@ -130,6 +130,27 @@ bool mean_layer_shape(int arch, int l, int* cout, int* k, int* cin) {
     return true;
 }
 
+// Temporal chunk context (Cf = Cc = 64): EC (1x1, Cc -> e2), FD (3x3, Cy -> 4 Cf), FC (1x1, Cc -> Cf),
+// CG (3x3, Cf -> Cc), PC (3x3 stride 2, Cc -> Cz), then DF_f (1x1, Cf -> Cd1) for each frame position f.
+bool temporal_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
+    Arch a;
+    if (!get_arch(arch, &a) || N < 1 || l < 0 || l >= TL_N + N) return false;
+    const int t[TL_N][3] = {{a.e2, 1, kCc}, {4 * kCf, 3, a.cy}, {kCf, 1, kCc}, {kCc, 3, kCf}, {a.cz, 3, kCc}};
+    if (l < TL_N) { *cout = t[l][0]; *k = t[l][1]; *cin = t[l][2]; }
+    else { *cout = a.cd1; *k = 1; *cin = kCf; }
+    return true;
+}
+
+size_t temporal_weight_count(int arch, int N) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < TL_N + N; ++l) {
+        if (!temporal_layer_shape(arch, N, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
 size_t mean_weight_count(int arch) {
     size_t n = 0;
     int co, k, ci;

@@ -75,6 +75,11 @@ size_t weight_count(int arch, int N);
 bool mean_layer_shape(int arch, int l, int* cout, int* k, int* cin);
 size_t mean_weight_count(int arch);
 constexpr int kMeanLayers = 6;
+// temporal chunk context: feature and context channels, and the shared layers (then DF per frame)
+constexpr int kCf = 64, kCc = 64;
+enum TemporalLayer { TL_EC = 0, TL_FD, TL_FC, TL_CG, TL_PC, TL_N };
+bool temporal_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin);
+size_t temporal_weight_count(int arch, int N);
 
 enum EncLayer { L_A1 = 0, L_A2, L_A3, L_XA, L_XB, L_A4, L_H1, L_H2, L_S1, L_S2, L_S3, L_NENC };
 enum DecLayer { D_D0 = 0, D_R1A, D_R1B, D_U1, D_R2A, D_R2B, D_U2, D_U3, D_NDEC };
@@ -206,21 +211,28 @@ void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const u
                               cudaStream_t s);
 void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
                         cudaStream_t s);
-// y^ = r^ q + mu with q = qstep_all[*qp_dev]; yf and / or yb may be null
+// y^ = r^ q + mu with q = qstep_all[*qp_dev] (qp_dev null: qstep_all[qp_host]); yf and / or yb may be null
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
-                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f);
+                    float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f,
+                    int qp_host = 0);
 
-// Container header.  version 1: single-pass means; version 2: progressive means on partitions 1..3.
-// The parser accepts version 1, and version 2 when allow_v2; it writes the version to *ver_dev.
+// Container header (version 1 + (progressive means) + 2 (temporal context)).
 void launch_write_header(uint8_t* out, int version, int arch, int N, int qp, int W, int H, int K, int Kz,
                          const uint8_t* iz, int Cz, size_t capacity, int* status, cudaStream_t s);
+// Versions: 1 + (progressive means) + 2 (temporal context).  The parser accepts progressive means when
+// allow_pm, requires the temporal flag to equal temporal, and writes *ver_dev = 2 for a progressive-means
+// stream, else 1.
 void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
-                         bool allow_v2, int* qp_dev, int* ver_dev, uint8_t* iz, int* status, cudaStream_t s);
+                         bool allow_pm, bool temporal, int* qp_dev, int* ver_dev, uint8_t* iz, int* status,
+                         cudaStream_t s);
 
 // Progressive means (progressive.cu).  `in` is the mean network's input [Hy][Wy][Cy + Cz], float (f32)
 // or bf16.  init: y^ of partition 0 (the encoder, y != null, first quantises partition 0 with mu0 into
 // rhat) and the features s; step k: on partition k, mu <- muk, encoder r^ re-quantised, y^ into `in`
 // (skipped when ver_dev is given and *ver_dev != 2).  qp from *qp_dev, else qp_host.
+// temporal context (temporal.cu): a += b over n floats
+void launch_add_f32(float* a, const float* b, size_t n, cudaStream_t s);
+
 void launch_pm_init(const float* y, int16_t* rhat, const float* mu0, const float* s, int Hy, int Wy, int cy, int cz,
                     const float* qstep_all, const float* qinv_all, const int* qp_dev, int qp_host, void* in, bool f32,
                     cudaStream_t st);

@@ -35,7 +35,8 @@ EXPORTS = [
     "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
     "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error", "ufvc_calibrate_fp8",
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
-    "ufvc_frame_bytes", "ufvc_set_color_format",
+    "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
+    "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
 ]
 COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
@@ -99,6 +100,12 @@ _sigs = {
     "ufvc_mean_weight_count": (_sz, [_i]),
     "ufvc_frame_bytes": (_sz, [_i, _i, _i]),
     "ufvc_set_color_format": (_i, [_vp, _i]),
+    "ufvc_temporal_weight_count": (_sz, [_i, _i]),
+    "ufvc_set_temporal_context": (_i, [_vp, _vp, _sz]),
+    "ufvc_context_bytes": (_sz, [_vp, _i, _i]),
+    "ufvc_encode_chunk_tc": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp, _vp, _vp]),
+    "ufvc_decode_chunk_tc": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "ufvc_encode_stages_tc": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "ufvc_set_progressive_means": (_i, [_vp, _vp, _sz]),
     "ufvc_progressive_means": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
 }
@@ -140,6 +147,10 @@ def frame_bytes(color: int, width: int, height: int) -> int:
     return int(lib.ufvc_frame_bytes(color, width, height))
 
 
+def temporal_weight_count(arch: int, chunk_len: int) -> int:
+    return int(lib.ufvc_temporal_weight_count(arch, chunk_len))
+
+
 def mean_weight_count(arch: int) -> int:
     return int(lib.ufvc_mean_weight_count(arch))
 
@@ -156,7 +167,8 @@ class Codec:
     """One ufvc_ctx.  Methods mirror the C entry points (ufvc_<name>)."""
 
     def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "fp32",
-                 device: int = 0, mean_weights: np.ndarray | None = None, color: int = COLOR_RGB):
+                 device: int = 0, mean_weights: np.ndarray | None = None, color: int = COLOR_RGB,
+                 temporal_weights: np.ndarray | None = None):
         self.arch, self.N, self.K, self.precision = arch, chunk_len, lanes, precision
         self.device = device
         cfg = ufvc_config(arch, chunk_len, lanes, PRECISIONS[precision], device)
@@ -174,6 +186,45 @@ class Codec:
         self.color = COLOR_RGB
         if color != COLOR_RGB:
             self.set_color_format(color)
+        if temporal_weights is not None:
+            tw = np.ascontiguousarray(temporal_weights, np.float32)
+            self._check(lib.ufvc_set_temporal_context(self.h, _ptr(tw), tw.size), "set_temporal_context")
+            self._temporal = True
+
+    # ---- temporal chunk context
+    def context_bytes(self, width: int, height: int) -> int:
+        return int(lib.ufvc_context_bytes(self.h, width, height))
+
+    def new_context(self, width: int, height: int, device=None) -> torch.Tensor:
+        """A context buffer [2 ceil(H/16)][2 ceil(W/16)][64] (bf16, or float32 in FP32 contexts)."""
+        dt = torch.float32 if self.precision == "fp32" else torch.bfloat16
+        return torch.empty((2 * (-(-height // 16)), 2 * (-(-width // 16)), 64), dtype=dt,
+                           device=device or torch.device(f"cuda:{self.device}"))
+
+    def encode_chunk_tc(self, frames: torch.Tensor, ctx_in, ctx_out, qp: int = 32, bits=None, nbytes=None,
+                        stream=None, width=None, height=None):
+        N = frames.shape[0]
+        W, H = self.frame_dims(frames, width, height)
+        if bits is None:
+            bits = torch.empty(self.max_bitstream_bytes(W, H), dtype=torch.uint8, device=frames.device)
+        if nbytes is None:
+            nbytes = torch.zeros(1, dtype=torch.int64, device=frames.device)
+        self._check(lib.ufvc_encode_chunk_tc(self.h, _ptr(frames), N, W, H, qp, _ptr(bits), bits.numel(), _ptr(nbytes),
+                                             _ptr(ctx_in), _ptr(ctx_out), _stream(stream)), "encode_chunk_tc")
+        return bits, nbytes
+
+    def decode_chunk_tc(self, bits: torch.Tensor, nbytes: int, width: int, height: int, ctx_in, ctx_out, out=None,
+                        f32: bool = False, stream=None, d_nbytes: torch.Tensor | None = None) -> torch.Tensor:
+        """Decode against the stream's context; with d_nbytes (device int64) the size is read on the device
+        and nbytes is the readable capacity."""
+        if out is None:
+            shape = (self.N, height, width, 3) if self.color in (COLOR_RGB, COLOR_RGB_BT709) else \
+                (self.N, 3, height, width) if self.color == COLOR_YUV444P else (self.N, frame_bytes(self.color, width, height))
+            out = torch.empty(shape, dtype=torch.float32 if f32 else torch.uint8, device=bits.device)
+        self._check(lib.ufvc_decode_chunk_tc(self.h, _ptr(bits), int(nbytes), _ptr(d_nbytes), _ptr(out), int(f32),
+                                             self.N, width,
+                                             height, _ptr(ctx_in), _ptr(ctx_out), _stream(stream)), "decode_chunk_tc")
+        return out
 
     def set_color_format(self, color: int):
         self._check(lib.ufvc_set_color_format(self.h, color), "set_color_format")
@@ -272,7 +323,8 @@ class Codec:
         return int(lib.ufvc_sync_status(self.h, _stream(stream)))
 
     # ---- stages
-    def encode_stages(self, frames: torch.Tensor, qp: int = 32, stream=None, width=None, height=None) -> dict:
+    def encode_stages(self, frames: torch.Tensor, qp: int = 32, stream=None, width=None, height=None,
+                      ctx_in=None) -> dict:
         W, H = self.frame_dims(frames, width, height)
         d = latent_dims(self.arch, W, H)
         dev = frames.device
@@ -282,10 +334,13 @@ class Codec:
                    iz=torch.empty(d["Cz"], dtype=torch.uint8, device=dev), mu=torch.empty(yshape, device=dev),
                    logsig=torch.empty(yshape, device=dev), rhat=torch.empty(yshape, dtype=torch.int16, device=dev),
                    idx=torch.empty(yshape, dtype=torch.uint8, device=dev))
-        self._check(lib.ufvc_encode_stages(self.h, _ptr(frames), W, H, qp, *[_ptr(out[k]) for k in
-                                                                             ("y", "zhat", "iz", "mu", "logsig", "rhat",
-                                                                              "idx")], _stream(stream)),
-                    "encode_stages")
+        keys = ("y", "zhat", "iz", "mu", "logsig", "rhat", "idx")
+        if ctx_in is not None or getattr(self, "_temporal", False):
+            self._check(lib.ufvc_encode_stages_tc(self.h, _ptr(frames), W, H, qp, _ptr(ctx_in),
+                                                  *[_ptr(out[k]) for k in keys], _stream(stream)), "encode_stages_tc")
+        else:
+            self._check(lib.ufvc_encode_stages(self.h, _ptr(frames), W, H, qp, *[_ptr(out[k]) for k in keys],
+                                               _stream(stream)), "encode_stages")
         return out
 
     def hyper_synthesis(self, zhat: torch.Tensor, Hy: int, Wy: int, stream=None):

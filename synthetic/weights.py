@@ -108,13 +108,21 @@ def temporal_layer_table(arch: int, n_frames: int) -> list[tuple[str, int, int, 
     return t
 
 
-def draw_temporal_weights(arch: int, n_frames: int, seed: int = 0, bias_std: float = 0.01) -> np.ndarray:
-    """Flat float32 blob of the temporal-context layers, N(0, 2/fan_in) kernels (own random stream)."""
+LOOP_GAIN = 0.1  # std factor of EC and FC, the two layers that feed a chunk's context into the next one
+
+
+def draw_temporal_weights(arch: int, n_frames: int, seed: int = 0, bias_std: float = 0.01,
+                          loop_gain: float = LOOP_GAIN) -> np.ndarray:
+    """Flat float32 blob of the temporal-context layers, N(0, 2/fan_in) kernels (own random stream).  EC and
+    FC, through which C_i reaches C_{i+1} (C_i -> EC -> y -> y^ -> F, and C_i -> FC -> F, then CG), are drawn
+    with loop_gain times the standard deviation, so that the untrained recursion contracts instead of
+    growing from chunk to chunk (at loop_gain = 1 the context grows about tenfold every few chunks)."""
     rng = np.random.default_rng([seed, 7])
     parts = []
-    for _, co, k, ci in temporal_layer_table(arch, n_frames):
+    for name, co, k, ci in temporal_layer_table(arch, n_frames):
         fan_in = k * k * ci
-        parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
+        g = loop_gain if name in ("EC", "FC") else 1.0
+        parts.append(rng.normal(0.0, g * np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
         parts.append(rng.normal(0.0, bias_std, size=co).astype(np.float32))
     return np.ascontiguousarray(np.concatenate(parts))
 
