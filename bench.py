@@ -209,7 +209,7 @@ NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.866624e6 + 73.490944e6), "dec.U3": 4 * (1
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
 
 
-def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n_streams: int = 64,
+def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n_streams: int = 64, temporal=None,
                   seed: int = 0, drain_s: float = 90.0, dist=None, rank: int = 0, world: int = 1) -> dict:
     """Serving mix: n_streams streams of the SERVING_MIX resolutions (assigned by seed), each with Poisson
     chunk arrivals at 30 fps (one 8-frame chunk per Exp(mean 8/30 s)), requests alternating encode and
@@ -231,7 +231,8 @@ def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n
             content[(W_, H_)] = src[:, :H_, :W_].contiguous()
         else:
             content[(W_, H_)] = src.repeat(1, 2, 2, 1)[:, :H_, :W_].contiguous()
-    srv = U.Server(1, N, K, blob, precision, hbm_cap_bytes=150 << 30, max_slots=8, device=dev.index or 0)
+    srv = U.Server(1, N, K, blob, precision, hbm_cap_bytes=150 << 30, max_slots=8, device=dev.index or 0,
+                   temporal_weights=temporal)
     owned = shard.shard(list(range(n_streams)), rank, world)
     sids = {}
     for j in owned:
@@ -580,6 +581,10 @@ def main() -> None:
         if args.precision != "fp32" and not args.no_fp32_path:
             serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", args.serving_window / 2, dist=dd,
                                             rank=rank, world=world)
+        if args.precision == "bf16" and not args.no_temporal:  # every stream carries its context chain
+            serving["bf16_temporal"] = serving_bench(U, dev, frames_np, blob, "bf16", args.serving_window, dist=dd,
+                                                     rank=rank, world=world,
+                                                     temporal=synthetic.draw_temporal_weights(1, N, seed=0))
 
     if rank == 0:
         workload = WORKLOAD if (W_, H_) == (W, H) else \

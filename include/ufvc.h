@@ -401,6 +401,14 @@ ufvc_status ufvc_server_stats_get(ufvc_server* srv, ufvc_server_stats* out);
 /* Message of the last server-level error ("" if none). */
 const char* ufvc_server_last_error(const ufvc_server* srv);
 
+/* Optional networks of the served codec (as ufvc_set_temporal_context / ufvc_set_progressive_means), set
+ * before the first stream is opened (UFVC_ERR_ARG afterwards).  With the temporal context every stream
+ * carries its own coding state on the device: the encoder's and the decoder's context, advanced by each
+ * of the stream's encode and decode requests in submission order (the first chunk uses C_0 = 0); the
+ * stream's chunks therefore have to be encoded and decoded in order, as for a single context. */
+ufvc_status ufvc_server_set_temporal_context(ufvc_server* srv, const float* weights, size_t n_weights);
+ufvc_status ufvc_server_set_progressive_means(ufvc_server* srv, const float* weights, size_t n_weights);
+
 #ifdef __cplusplus
 }
 #endif

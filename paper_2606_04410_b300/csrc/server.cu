@@ -12,6 +12,12 @@
 //
 // Every slot computes with the same kernels as a single context, and none of them depends on what
 // runs beside it, so a request's bit-stream and frames are the same alone and in a mix.
+//
+// With the temporal chunk context (ufvc_server_set_temporal_context) each stream also owns its coding
+// state on the device: the encoder's and the decoder's context C_i.  A request copies the stream's
+// context into the slot's input buffer (zeros for the stream's first chunk, which equals C_0 = 0),
+// runs, and copies the slot's output context back, so the slot's graphs keep fixed pointers and a
+// stream's chunks form one context chain whatever slots they run on.
 #include "ufvc_internal.h"
 
 #include <algorithm>
@@ -55,6 +61,10 @@ struct StreamBuf {
     uint64_t* nbytes = nullptr;
     size_t cap = 0, frame_bytes = 0, bytes = 0;
     bool running = false, has_bits = false;
+    // temporal context: the encoder's and the decoder's C_i, and how many chunks each side has coded
+    void *ctx_enc = nullptr, *ctx_dec = nullptr;
+    size_t ctx_bytes = 0;
+    uint64_t enc_chunks = 0, dec_chunks = 0;
 };
 
 struct Req {
@@ -69,6 +79,7 @@ struct Slot {
     cudaEvent_t ev = nullptr;
     uint8_t *frames = nullptr, *bits = nullptr, *out = nullptr;
     uint64_t* nbytes = nullptr;
+    void *cin = nullptr, *cout = nullptr;  // temporal context in / out of the slot's calls
     size_t cap = 0, footprint = 0;
     bool busy = false;
     uint64_t ticket = 0;
@@ -91,6 +102,7 @@ struct ufvc_server {
     int max_slots = 1, next_slot_id = 0;
     std::atomic<int> graphs{0};
     uint64_t completed = 0, next_ticket = 1;
+    bool temporal = false;  // streams carry the temporal chunk context
     std::vector<Slot*> slots;
     std::vector<std::unique_ptr<StreamBuf>> streams;
     std::deque<uint64_t> queue;
@@ -112,6 +124,8 @@ void destroy_slot(ufvc_server* S, Slot* sl) {
     for (auto& kv : sl->g_enc) cudaGraphExecDestroy(kv.second);
     if (sl->g_dec) cudaGraphExecDestroy(sl->g_dec);
     ufvc_destroy(sl->ctx);
+    cudaFree(sl->cin);
+    cudaFree(sl->cout);
     cudaFree(sl->frames);
     cudaFree(sl->bits);
     cudaFree(sl->out);
@@ -138,8 +152,9 @@ bool evict_one(ufvc_server* S, int W, int H, bool any_size) {
 Slot* make_slot(ufvc_server* S, int W, int H) {
     const size_t frame_bytes = (size_t)S->N * W * H * 3;
     const size_t cap = ufvc_max_bitstream_bytes(S->base, W, H);
+    const size_t cb = S->temporal ? ufvc_context_bytes(S->base, W, H) : 0;
     // plan buffers + workspaces + staging + a margin for the rANS scratch, graphs and allocator rounding
-    const size_t fp = ctx_plan_bytes(S->base, W, H) + 2 * frame_bytes + cap + (64ull << 20);
+    const size_t fp = ctx_plan_bytes(S->base, W, H) + 2 * frame_bytes + cap + 2 * cb + (64ull << 20);
     if ((int)S->slots.size() >= S->max_slots && !evict_one(S, W, H, false)) return nullptr;
     while (S->cap && S->used + fp > S->cap)
         if (!evict_one(S, W, H, false)) return nullptr;
@@ -153,13 +168,16 @@ Slot* make_slot(ufvc_server* S, int W, int H) {
     bool ok = sl->ctx && cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&sl->frames, frame_bytes) == cudaSuccess && cudaMalloc(&sl->bits, cap) == cudaSuccess &&
-              cudaMalloc(&sl->out, frame_bytes) == cudaSuccess && cudaMalloc(&sl->nbytes, 8) == cudaSuccess;
+              cudaMalloc(&sl->out, frame_bytes) == cudaSuccess && cudaMalloc(&sl->nbytes, 8) == cudaSuccess &&
+              (!cb || (cudaMalloc(&sl->cin, cb) == cudaSuccess && cudaMalloc(&sl->cout, cb) == cudaSuccess));
     if (!ok) {
         S->err = "server: slot creation failed";
         cudaGetLastError();
         if (sl->ctx) ufvc_destroy(sl->ctx);
         if (sl->st) cudaStreamDestroy(sl->st);
         if (sl->ev) cudaEventDestroy(sl->ev);
+        cudaFree(sl->cin);
+        cudaFree(sl->cout);
         cudaFree(sl->frames);
         cudaFree(sl->bits);
         cudaFree(sl->out);
@@ -208,12 +226,22 @@ ufvc_status run_call(ufvc_server* S, Slot* sl, cudaGraphExec_t* g, bool* ran, bo
 void launch(ufvc_server* S, Slot* sl, StreamBuf* sb, int op) {
     ufvc_status st = UFVC_OK;
     const int N = S->N, W = sb->W, H = sb->H;
+    // the stream's context into the slot (zeros before its first chunk: C_0 = 0)
+    auto ctx_in = [&](const void* c, uint64_t chunks) {
+        if (!S->temporal) return;
+        if (chunks) cudaMemcpyAsync(sl->cin, c, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
+        else cudaMemsetAsync(sl->cin, 0, sb->ctx_bytes, sl->st);
+    };
     if (op == UFVC_OP_ENCODE) {
         cudaMemcpyAsync(sl->frames, sb->in, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
+        ctx_in(sb->ctx_enc, sb->enc_chunks);
         auto it = sl->g_enc.find(sb->qp);
         cudaGraphExec_t g = it == sl->g_enc.end() ? nullptr : it->second;
         bool ran = sl->enc_ran.count(sb->qp) != 0, nograph = sl->enc_nograph.count(sb->qp) != 0;
         st = run_call(S, sl, &g, &ran, &nograph, [&] {
+            if (S->temporal)
+                return ufvc_encode_chunk_tc(sl->ctx, sl->frames, N, W, H, sb->qp, sl->bits, sl->cap, sl->nbytes,
+                                            sl->cin, sl->cout, sl->st);
             return ufvc_encode_chunk(sl->ctx, sl->frames, N, W, H, sb->qp, sl->bits, sl->cap, sl->nbytes, sl->st);
         });
         if (g) sl->g_enc[sb->qp] = g;
@@ -222,14 +250,28 @@ void launch(ufvc_server* S, Slot* sl, StreamBuf* sb, int op) {
         if (st == UFVC_OK) {
             copy_sized(sb->bits, sl->bits, sl->nbytes, sb->cap, sl->st);
             cudaMemcpyAsync(sb->nbytes, sl->nbytes, 8, cudaMemcpyDeviceToDevice, sl->st);
+            if (S->temporal) {
+                cudaMemcpyAsync(sb->ctx_enc, sl->cout, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
+                ++sb->enc_chunks;
+            }
         }
     } else {
         copy_sized(sl->bits, sb->bits, sb->nbytes, sl->cap, sl->st);
         cudaMemcpyAsync(sl->nbytes, sb->nbytes, 8, cudaMemcpyDeviceToDevice, sl->st);
+        ctx_in(sb->ctx_dec, sb->dec_chunks);
         st = run_call(S, sl, &sl->g_dec, &sl->dec_ran, &sl->dec_nograph, [&] {
+            if (S->temporal)
+                return ufvc_decode_chunk_tc(sl->ctx, sl->bits, sl->cap, sl->nbytes, sl->out, 0, N, W, H, sl->cin,
+                                            sl->cout, sl->st);
             return ufvc_decode_chunk_dev(sl->ctx, sl->bits, sl->cap, sl->nbytes, sl->out, N, W, H, sl->st);
         });
-        if (st == UFVC_OK) cudaMemcpyAsync(sb->out, sl->out, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
+        if (st == UFVC_OK) {
+            cudaMemcpyAsync(sb->out, sl->out, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
+            if (S->temporal) {
+                cudaMemcpyAsync(sb->ctx_dec, sl->cout, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
+                ++sb->dec_chunks;
+            }
+        }
     }
     if (st == UFVC_OK && cudaGetLastError() != cudaSuccess) st = UFVC_ERR_CUDA;
     sl->launch_status = st;
@@ -367,6 +409,8 @@ extern "C" void ufvc_server_destroy(ufvc_server* S) {
         cudaFree(sb->bits);
         cudaFree(sb->out);
         cudaFree(sb->nbytes);
+        cudaFree(sb->ctx_enc);
+        cudaFree(sb->ctx_dec);
     }
     ufvc_destroy(S->base);
     delete S;
@@ -382,15 +426,20 @@ extern "C" ufvc_status ufvc_server_open_stream(ufvc_server* S, int width, int he
     sb->qp = qp;
     sb->frame_bytes = (size_t)S->N * width * height * 3;
     sb->cap = ufvc_max_bitstream_bytes(S->base, width, height);
-    sb->bytes = 2 * sb->frame_bytes + sb->cap + 256;
+    sb->ctx_bytes = S->temporal ? ufvc_context_bytes(S->base, width, height) : 0;
+    sb->bytes = 2 * sb->frame_bytes + sb->cap + 256 + 2 * sb->ctx_bytes;
     if (S->cap && S->used + sb->bytes > S->cap) {
         S->err = "server: stream buffers exceed the HBM cap";
         return UFVC_ERR_OOM;
     }
     if (cudaSetDevice(S->device) != cudaSuccess || cudaMalloc(&sb->in, sb->frame_bytes) != cudaSuccess ||
         cudaMalloc(&sb->bits, sb->cap) != cudaSuccess || cudaMalloc(&sb->out, sb->frame_bytes) != cudaSuccess ||
-        cudaMalloc(&sb->nbytes, 8) != cudaSuccess || cudaMemset(sb->nbytes, 0, 8) != cudaSuccess) {
+        cudaMalloc(&sb->nbytes, 8) != cudaSuccess || cudaMemset(sb->nbytes, 0, 8) != cudaSuccess ||
+        (sb->ctx_bytes && (cudaMalloc(&sb->ctx_enc, sb->ctx_bytes) != cudaSuccess ||
+                           cudaMalloc(&sb->ctx_dec, sb->ctx_bytes) != cudaSuccess))) {
         cudaGetLastError();
+        cudaFree(sb->ctx_enc);
+        cudaFree(sb->ctx_dec);
         cudaFree(sb->in);
         cudaFree(sb->bits);
         cudaFree(sb->out);
@@ -475,3 +524,30 @@ extern "C" ufvc_status ufvc_server_stats_get(ufvc_server* S, ufvc_server_stats* 
 }
 
 extern "C" const char* ufvc_server_last_error(const ufvc_server* S) { return S ? S->err.c_str() : "null server"; }
+
+// The optional networks are set on the server's weight copy before any slot clones it.
+template <class Fn>
+static ufvc_status server_configure(ufvc_server* S, const char* what, Fn fn) {
+    if (!S) return UFVC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->streams.empty() || !S->slots.empty()) {
+        S->err = std::string(what) + ": only before the first stream is opened";
+        return UFVC_ERR_ARG;
+    }
+    const ufvc_status st = fn();
+    if (st != UFVC_OK) S->err = std::string(what) + ": " + ufvc_last_error(S->base);
+    return st;
+}
+
+extern "C" ufvc_status ufvc_server_set_temporal_context(ufvc_server* S, const float* weights, size_t n_weights) {
+    return server_configure(S, "server_set_temporal_context", [&] {
+        const ufvc_status st = ufvc_set_temporal_context(S->base, weights, n_weights);
+        if (st == UFVC_OK) S->temporal = true;
+        return st;
+    });
+}
+
+extern "C" ufvc_status ufvc_server_set_progressive_means(ufvc_server* S, const float* weights, size_t n_weights) {
+    return server_configure(S, "server_set_progressive_means",
+                            [&] { return ufvc_set_progressive_means(S->base, weights, n_weights); });
+}

@@ -37,6 +37,7 @@ EXPORTS = [
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
     "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
     "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
+    "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means",
 ]
 COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
@@ -102,6 +103,8 @@ _sigs = {
     "ufvc_set_color_format": (_i, [_vp, _i]),
     "ufvc_temporal_weight_count": (_sz, [_i, _i]),
     "ufvc_set_temporal_context": (_i, [_vp, _vp, _sz]),
+    "ufvc_server_set_temporal_context": (_i, [_vp, _vp, _sz]),
+    "ufvc_server_set_progressive_means": (_i, [_vp, _vp, _sz]),
     "ufvc_context_bytes": (_sz, [_vp, _i, _i]),
     "ufvc_encode_chunk_tc": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp, _vp, _vp]),
     "ufvc_decode_chunk_tc": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -427,7 +430,8 @@ class Server:
     bit-stream and output buffers, exposed here as torch tensors that alias the library's memory."""
 
     def __init__(self, arch: int, chunk_len: int, lanes: int, weights: np.ndarray, precision: str = "bf16",
-                 hbm_cap_bytes: int = 0, max_slots: int = 8, device: int = 0):
+                 hbm_cap_bytes: int = 0, max_slots: int = 8, device: int = 0,
+                 temporal_weights: np.ndarray | None = None, mean_weights: np.ndarray | None = None):
         self.N = chunk_len
         self.device = device
         w = np.ascontiguousarray(weights, dtype=np.float32)
@@ -438,6 +442,12 @@ class Server:
             raise UfvcError(rc, "server_create")
         self.h = h
         self.streams: dict[int, dict] = {}
+        if temporal_weights is not None:
+            tw = np.ascontiguousarray(temporal_weights, np.float32)
+            self._check(lib.ufvc_server_set_temporal_context(self.h, _ptr(tw), tw.size), "server_set_temporal_context")
+        if mean_weights is not None:
+            mw = np.ascontiguousarray(mean_weights, np.float32)
+            self._check(lib.ufvc_server_set_progressive_means(self.h, _ptr(mw), mw.size), "server_set_progressive_means")
 
     def close(self):
         if self.h:

@@ -155,3 +155,52 @@ def test_server_refuses_decode_before_encode_and_bad_calls():
     with pytest.raises(u.UfvcError):
         srv.open_stream(8, 8, QP)
     srv.close()
+
+
+def test_server_streams_carry_temporal_context():
+    """Each stream's chunks form one context chain on the server (its encoder's and decoder's context kept
+    on the device between requests, on whatever slots they run): bit-streams and frames equal a single
+    context coding the same chunks in order, with progressive means as well (version-4 streams)."""
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=4)
+    tw = synthetic.draw_temporal_weights(1, N, seed=3)
+    mw = synthetic.draw_mean_weights(1, seed=3)
+    specs = [(0, *SIZES[0]), (1, *SIZES[2]), (2, *SIZES[0])]
+    rounds = 3
+    chunks = {i: [_frames(70 + 10 * i + r, W, H) for r in range(rounds)] for i, W, H in specs}
+    refs = {}
+    for i, W, H in specs:  # single-context reference chains
+        c = u.Codec(1, N, K, blob, "bf16", temporal_weights=tw, mean_weights=mw)
+        ce = [c.new_context(W, H), c.new_context(W, H)]
+        cd = [c.new_context(W, H), c.new_context(W, H)]
+        out = []
+        for r in range(rounds):
+            bits, nb = c.encode_chunk_tc(chunks[i][r], ce[r % 2] if r else None, ce[(r + 1) % 2], QP)
+            n = int(nb.item())
+            fr = c.decode_chunk_tc(bits, n, W, H, cd[r % 2] if r else None, cd[(r + 1) % 2])
+            assert c.sync_status() == 0
+            out.append((bits[:n].cpu().numpy().tobytes(), fr.cpu().clone()))
+        refs[i] = out
+        c.close()
+    srv = u.Server(1, N, K, blob, "bf16", max_slots=2, temporal_weights=tw, mean_weights=mw)
+    sids = {i: srv.open_stream(W, H, QP) for i, W, H in specs}
+    # the optional networks are set before the first stream only
+    assert u.lib.ufvc_server_set_progressive_means(srv.h, u._ptr(mw), mw.size) == u.UFVC_ERR_ARG
+    for r in range(rounds):
+        for i, _, _ in specs:
+            srv.streams[sids[i]]["frames_in"].copy_(chunks[i][r])
+        torch.cuda.synchronize()
+        tickets = []
+        for i, _, _ in specs:
+            tickets.append((i, srv.submit(sids[i], u.UFVC_OP_ENCODE)))
+            tickets.append((i, srv.submit(sids[i], u.UFVC_OP_DECODE)))
+        for i, t in tickets:
+            assert srv.wait(t, 120000.0)["status"] == 0
+        for i, _, _ in specs:
+            b = srv.streams[sids[i]]
+            raw = b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes()
+            assert raw[4] == 4
+            assert raw == refs[i][r][0], (i, r)
+            assert torch.equal(b["frames_out"].cpu(), refs[i][r][1]), (i, r)
+    assert srv.stats()["graphs"] >= 2
+    srv.close()
