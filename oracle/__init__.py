@@ -453,12 +453,12 @@ def encode_chunk_t(arch: int, frames: np.ndarray, qp: int, K: int, weights: np.n
     cap = 64 + d["Cz"] + 4 * (K + min(K, nz)) + 2 * (ny + nz + 4 * K) + 16
     out = np.empty(cap, np.uint8)
     nbytes = C.c_size_t()
-    tw = np.ascontiguousarray(tw, np.float32)
+    tw = None if tw is None else np.ascontiguousarray(tw, np.float32)  # None for the DC-block model (arch 2)
     mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
     ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
     c_out = np.empty((H8, W8, Cc), np.float64)
-    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data, ci.ctypes.data if ci is not None else None,
-              c_out.ctypes.data)
+    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data if tw is not None else None,
+              ci.ctypes.data if ci is not None else None, c_out.ctypes.data)
     arrs, dbg = {}, None
     if debug:
         arrs = dict(y=np.empty((d["Hy"], d["Wy"], d["Cy"])), z=np.empty((d["Hz"], d["Wz"], d["Cz"])),
@@ -483,16 +483,72 @@ def decode_chunk_t(arch: int, N: int, bits: bytes, H: int, W: int, weights: np.n
     a = np.frombuffer(bits, np.uint8).copy()
     yhat = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
     frames = np.empty((N, H, W, 3), np.float64)
-    tw = np.ascontiguousarray(tw, np.float32)
+    tw = None if tw is None else np.ascontiguousarray(tw, np.float32)
     mw = None if mean_weights is None else np.ascontiguousarray(mean_weights, np.float32)
     ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
     c_out = np.empty((H8, W8, Cc), np.float64)
-    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data, ci.ctypes.data if ci is not None else None,
-              c_out.ctypes.data)
+    o = _Opts(mw.ctypes.data if mw is not None else None, tw.ctypes.data if tw is not None else None,
+              ci.ctypes.data if ci is not None else None, c_out.ctypes.data)
     rc = lib().orc_decode_chunk_opts(arch, N, _p(a), C.c_size_t(len(bits)), H, W, _p(weights), C.byref(o),
                                      _p(frames), _p(yhat))
     _check(rc, "decode_chunk_opts")
     return frames, yhat, c_out
+
+
+# ---------------------------------------------------------------- DC-block model (arch 2)
+DC_C, DC_CF, DC_CC = 512, 256, 128
+
+
+def dc_weight_count(N: int) -> int:
+    lib().orc_dc_weight_count.restype = C.c_size_t
+    return int(lib().orc_dc_weight_count(N))
+
+
+def dw_conv(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Depth-wise 3x3, zero padding 1: x [H][W][C], w [C][3][3][1], b [C]."""
+    x = np.ascontiguousarray(x, np.float64)
+    H, W, Cc = x.shape
+    out = np.empty_like(x)
+    lib().orc_dw_conv(_p(x), H, W, Cc, _p(np.ascontiguousarray(w, np.float32)), _p(np.ascontiguousarray(b, np.float32)),
+                      _p(out))
+    return out
+
+
+def dc_analysis(N: int, x: np.ndarray, weights: np.ndarray, c_in: np.ndarray | None) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64)
+    _, H, W, _ = x.shape
+    d = latent_dims(2, H, W)
+    y = np.empty((d["Hy"], d["Wy"], d["Cy"]), np.float64)
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    _check(lib().orc_dc_analysis(N, _p(x), H, W, _p(weights), _p(ci) if ci is not None else None, _p(y)), "dc_analysis")
+    return y
+
+
+def dc_prior_term(N: int, c_in: np.ndarray | None, H8: int, W8: int, weights: np.ndarray) -> np.ndarray:
+    pc = np.empty((H8 // 2, W8 // 2, 128), np.float64)
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    _check(lib().orc_dc_prior_term(N, _p(ci) if ci is not None else None, H8, W8, _p(weights), _p(pc)), "dc_prior_term")
+    return pc
+
+
+def dc_trunk(N: int, yhat: np.ndarray, weights: np.ndarray, c_in: np.ndarray | None, want_c_out: bool = True):
+    """Chunk decoder (-> F [2Hy][2Wy][512]) and context generation (-> C_{i+1} [2Hy][2Wy][128])."""
+    yhat = np.ascontiguousarray(yhat, np.float64)
+    Hy, Wy, _ = yhat.shape
+    F = np.empty((2 * Hy, 2 * Wy, DC_C), np.float64)
+    c_out = np.empty((2 * Hy, 2 * Wy, DC_CC), np.float64) if want_c_out else None
+    ci = None if c_in is None else np.ascontiguousarray(c_in, np.float64)
+    _check(lib().orc_dc_trunk(N, _p(yhat), Hy, Wy, _p(weights), _p(ci) if ci is not None else None, _p(F),
+                              _p(c_out) if c_out is not None else None), "dc_trunk")
+    return F, c_out
+
+
+def dc_frames(N: int, F: np.ndarray, H: int, W: int, weights: np.ndarray) -> np.ndarray:
+    F = np.ascontiguousarray(F, np.float64)
+    H8, W8, _ = F.shape
+    out = np.empty((N, H, W, 3), np.float64)
+    _check(lib().orc_dc_frames(N, _p(F), H8, W8, H, W, _p(weights), _p(out)), "dc_frames")
+    return out
 
 
 def num_threads() -> int:

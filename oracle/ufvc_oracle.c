@@ -48,6 +48,12 @@
 #define RANS_L (1u << 16) /* lower bound of the 32-bit rANS state */
 #define ORC_CF 64         /* temporal chunk feature channels */
 #define ORC_CC 64         /* temporal context channels */
+/* DC-block model widths: chunk modules, frame decoders, context, latent, hyper-latent */
+#define DC_C 512
+#define DC_CF 256
+#define DC_CC 128
+#define DC_CY 256
+#define DC_CZ 128
 
 /* ------------------------------------------------------------------------------------------------ */
 /* Architecture (plain reading of Fig. 3; widths per workload)                                      */
@@ -57,13 +63,18 @@ typedef struct { int e0, e1, e2, cy, cz, cd1, cd2; } arch_t;
 static int get_arch(int arch, arch_t* a) {
     if (arch == 0) { arch_t t = {64, 96, 128, 128, 64, 128, 64}; *a = t; return ORC_OK; }
     if (arch == 1) { arch_t t = {64, 128, 192, 256, 128, 128, 64}; *a = t; return ORC_OK; }
+    if (arch == 2) { arch_t t = {0, 0, 0, 256, 128, 0, 0}; *a = t; return ORC_OK; }  /* DC-block model */
     return ORC_ERR_ARG;
 }
+
+static int dc_hyper_layer(int l);  /* DC-block model: blob index of hyperprior layer l = 6..10 */
+static void dc_layer_ptr(int N, const float* blob, int l, const float** w, const float** b);
+size_t orc_dc_weight_count(int N);
 
 /* Layer l of the blob: (cout, k, cin).  Encoder/hyper layers 0..10, then 8 per frame. */
 int orc_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
     arch_t a;
-    if (get_arch(arch, &a) || N < 1 || l < 0 || l >= 11 + 8 * N) return ORC_ERR_ARG;
+    if (arch == 2 || get_arch(arch, &a) || N < 1 || l < 0 || l >= 11 + 8 * N) return ORC_ERR_ARG;
     int t[11][3] = {{a.e0, 3, 3 * N}, {a.e1, 3, a.e0}, {a.e2, 3, a.e1}, {a.e2, 3, a.e2}, {a.e2, 1, a.e2},
                     {a.cy, 3, a.e2},  {a.cz, 3, a.cy}, {a.cz, 3, a.cz}, {4 * a.cz, 3, a.cz},
                     {4 * a.cz, 3, a.cz}, {2 * a.cy, 1, a.cz}};
@@ -75,6 +86,7 @@ int orc_layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
 }
 
 size_t orc_weight_count(int arch, int N) {
+    if (arch == 2) return orc_dc_weight_count(N);
     size_t n = 0;
     int co, k, ci;
     for (int l = 0; l < 11 + 8 * N; l++) {
@@ -86,6 +98,7 @@ size_t orc_weight_count(int arch, int N) {
 
 /* Pointers to layer l's kernel [Cout][k][k][Cin] and bias [Cout] inside the blob. */
 static void layer_ptr(int arch, int N, const float* blob, int l, const float** w, const float** b) {
+    if (arch == 2) { dc_layer_ptr(N, blob, dc_hyper_layer(l), w, b); return; }  /* hyperprior layers only */
     size_t off = 0;
     int co, k, ci;
     for (int i = 0; i < l; i++) {
@@ -893,7 +906,7 @@ int orc_context_dims(int arch, int H, int W, int* H8, int* W8, int* Cc) {
     if (get_arch(arch, &a) || H < 1 || W < 1) return ORC_ERR_ARG;
     *H8 = (H + 15) / 16 * 2;
     *W8 = (W + 15) / 16 * 2;
-    *Cc = ORC_CC;
+    *Cc = arch == 2 ? DC_CC : ORC_CC;
     return ORC_OK;
 }
 
@@ -951,6 +964,225 @@ int orc_synthesis_f(int arch, int N, const double* yhat, int Hy, int Wy, int H, 
                     const double* F, const float* tw, double* frames) {
     if (!F || !tw) return ORC_ERR_ARG;
     return synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, F, tw, frames);
+}
+
+/* ------------------------------------------------------------------------------------------------ */
+/* DC-block model (Appendix: all modules built from depth-wise convolution blocks; HT-S block counts) */
+/* ------------------------------------------------------------------------------------------------ */
+/* Reading of the appendix figure and counts (widths are not given; they are chosen so that the model
+ * costs about the paper's 211 G MACs per 1080p frame for N = 8):
+ *   DC block of width C:  y = x + PWb(GELU(DW(PWa(x)))),  out = y + PWd(GELU(PWc(y)))
+ *     PWa, PWb 1x1 C -> C; DW 3x3 depth-wise (one 3x3 filter per channel); PWc 1x1 C -> 2C; PWd 2C -> C
+ *   at 1/8 of the padded frame size (H8 x W8):
+ *   patch embedding  x = PE(s2d8(frames))          s2d8: channel (3n + c) 64 + 8 dy + dx, PE 1x1 -> C
+ *   chunk encoder    x += EC(C_i); 6 DC blocks; y = ED(x)   (ED 3x3 stride 2, C -> Cy)
+ *   hyperprior       as the plain model's (H1, H2, S1, S2, S3), with PC(C_i) (3x3 stride 2, Cc -> Cz)
+ *                    added to the S2 features before S3
+ *   chunk decoder    x = GELU(PS(DU(y^))) + FC(C_i)  (DU 1x1 Cy -> 4C), 7 DC blocks -> F_i
+ *   context          11 DC blocks on F_i, C_{i+1} = GO(.)  (GO 1x1 C -> Cc)
+ *   frame decoder f  FP_f (1x1 C -> Cf), 3 DC blocks at Cf, FO_f (1x1 Cf -> 192), pixel shuffle x8,
+ *                    x^ = clamp(0.5 + o, 0, 1), cropped
+ * C = 512, Cf = 256, Cc = 128, Cy = 256, Cz = 128; C_0 = 0.  Blob order: PE, EC, 6 x [PWa DW PWb PWc PWd],
+ * ED, H1, H2, S1, S2, S3, PC, DU, FC, 7 x [...], 11 x [...], GO, then per frame FP_f, 3 x [...] at Cf,
+ * FO_f; a depth-wise layer is stored as kernel [C][3][3][1] + bias [C]. */
+#define DC_SHARED 132  /* layers before the frame decoders */
+#define DC_PER_FRAME 17
+
+/* block layer j (0..4) of width c: (cout, k, cin) */
+static void dc_block_shape(int c, int j, int* co, int* k, int* ci) {
+    const int t[5][3] = {{c, 1, c}, {c, 3, 1}, {c, 1, c}, {2 * c, 1, c}, {c, 1, 2 * c}};
+    *co = t[j][0]; *k = t[j][1]; *ci = t[j][2];
+}
+
+int orc_dc_layer_shape(int N, int l, int* cout, int* k, int* cin) {
+    if (N < 1 || l < 0 || l >= DC_SHARED + DC_PER_FRAME * N) return ORC_ERR_ARG;
+    if (l >= DC_SHARED) {
+        int j = (l - DC_SHARED) % DC_PER_FRAME;
+        if (j == 0) { *cout = DC_CF; *k = 1; *cin = DC_C; }
+        else if (j == 16) { *cout = 192; *k = 1; *cin = DC_CF; }
+        else dc_block_shape(DC_CF, (j - 1) % 5, cout, k, cin);
+        return ORC_OK;
+    }
+    if (l == 0) { *cout = DC_C; *k = 1; *cin = 3 * N * 64; }
+    else if (l == 1) { *cout = DC_C; *k = 1; *cin = DC_CC; }
+    else if (l < 32) dc_block_shape(DC_C, (l - 2) % 5, cout, k, cin);
+    else if (l == 32) { *cout = DC_CY; *k = 3; *cin = DC_C; }
+    else if (l == 33) { *cout = DC_CZ; *k = 3; *cin = DC_CY; }
+    else if (l == 34) { *cout = DC_CZ; *k = 3; *cin = DC_CZ; }
+    else if (l == 35 || l == 36) { *cout = 4 * DC_CZ; *k = 3; *cin = DC_CZ; }
+    else if (l == 37) { *cout = 2 * DC_CY; *k = 1; *cin = DC_CZ; }
+    else if (l == 38) { *cout = DC_CZ; *k = 3; *cin = DC_CC; }
+    else if (l == 39) { *cout = 4 * DC_C; *k = 1; *cin = DC_CY; }
+    else if (l == 40) { *cout = DC_C; *k = 1; *cin = DC_CC; }
+    else if (l < 131) dc_block_shape(DC_C, (l - 41) % 5, cout, k, cin);
+    else { *cout = DC_CC; *k = 1; *cin = DC_C; }
+    return ORC_OK;
+}
+
+size_t orc_dc_weight_count(int N) {
+    size_t n = 0;
+    int co, k, ci;
+    for (int l = 0; l < DC_SHARED + DC_PER_FRAME * N; l++) {
+        if (orc_dc_layer_shape(N, l, &co, &k, &ci)) return 0;
+        n += (size_t)co * k * k * ci + co;
+    }
+    return n;
+}
+
+static int dc_hyper_layer(int l) { return 33 + (l - 6); }  /* H1 H2 S1 S2 S3 */
+
+static void dc_layer_ptr(int N, const float* blob, int l, const float** w, const float** b) {
+    size_t off = 0;
+    int co, k, ci;
+    for (int i = 0; i < l; i++) {
+        orc_dc_layer_shape(N, i, &co, &k, &ci);
+        off += (size_t)co * k * k * ci + co;
+    }
+    orc_dc_layer_shape(N, l, &co, &k, &ci);
+    *w = blob + off;
+    *b = blob + off + (size_t)co * k * k * ci;
+}
+
+/* Depth-wise 3x3 convolution, zero padding 1: out[h][w][c] = b[c] + sum w[c][ky][kx] x[h+ky-1][w+kx-1][c]. */
+void orc_dw_conv(const double* x, int H, int W, int C, const float* w, const float* b, double* out) {
+    #pragma omp parallel for
+    for (int h = 0; h < H; h++)
+        for (int ww = 0; ww < W; ww++)
+            for (int c = 0; c < C; c++) {
+                double acc = b[c];
+                for (int ky = 0; ky < 3; ky++)
+                    for (int kx = 0; kx < 3; kx++) {
+                        int ih = h + ky - 1, iw = ww + kx - 1;
+                        if (ih < 0 || ih >= H || iw < 0 || iw >= W) continue;
+                        acc += (double)w[(size_t)c * 9 + ky * 3 + kx] * x[((size_t)ih * W + iw) * C + c];
+                    }
+                out[((size_t)h * W + ww) * C + c] = acc;
+            }
+}
+
+/* One DC block of width c on x [H][W][c] in place; its five layers start at blob layer l0. */
+static void dc_block(int N, const float* wts, int l0, double* x, int H, int W, int c) {
+    const size_t n = (size_t)H * W;
+    const float *wk, *bk;
+    double* t = dalloc(n * c);
+    double* u = dalloc(n * c);
+    double* v = dalloc(n * 2 * c);
+    dc_layer_ptr(N, wts, l0, &wk, &bk);
+    orc_conv2d(x, H, W, c, wk, bk, c, 1, 1, t);
+    dc_layer_ptr(N, wts, l0 + 1, &wk, &bk);
+    orc_dw_conv(t, H, W, c, wk, bk, u);
+    gelu_inplace(u, n * c);
+    dc_layer_ptr(N, wts, l0 + 2, &wk, &bk);
+    orc_conv2d(u, H, W, c, wk, bk, c, 1, 1, t);
+    for (size_t i = 0; i < n * c; i++) x[i] += t[i];
+    dc_layer_ptr(N, wts, l0 + 3, &wk, &bk);
+    orc_conv2d(x, H, W, c, wk, bk, 2 * c, 1, 1, v);
+    gelu_inplace(v, n * 2 * c);
+    dc_layer_ptr(N, wts, l0 + 4, &wk, &bk);
+    orc_conv2d(v, H, W, 2 * c, wk, bk, c, 1, 1, t);
+    for (size_t i = 0; i < n * c; i++) x[i] += t[i];
+    free(t); free(u); free(v);
+}
+
+/* c_in NULL stands for the all-zero first context: a 1x1 / stride-2 3x3 layer of it is its bias. */
+static void dc_context_layer(int N, const float* wts, int l, const double* c_in, int H8, int W8, int stride,
+                             double* out) {
+    const float *wk, *bk;
+    int co, k, ci;
+    orc_dc_layer_shape(N, l, &co, &k, &ci);
+    dc_layer_ptr(N, wts, l, &wk, &bk);
+    if (c_in) {
+        orc_conv2d(c_in, H8, W8, ci, wk, bk, co, k, stride, out);
+    } else {
+        int Ho = conv_out(H8, k, stride), Wo = conv_out(W8, k, stride);
+        for (size_t i = 0; i < (size_t)Ho * Wo; i++)
+            for (int c = 0; c < co; c++) out[i * co + c] = bk[c];
+    }
+}
+
+/* Chunk encoder: frames (network channels x [N][H][W][3] in [0, 1]) -> y [H8/2][W8/2][Cy]. */
+int orc_dc_analysis(int N, const double* xin, int H, int W, const float* wts, const double* c_in, double* y) {
+    const int Hp = (H + 15) / 16 * 16, Wp = (W + 15) / 16 * 16, H8 = Hp / 8, W8 = Wp / 8, C0 = 3 * N * 64;
+    const size_t n8 = (size_t)H8 * W8;
+    double* p = dalloc(n8 * C0);
+    for (int h = 0; h < Hp; h++)
+        for (int w = 0; w < Wp; w++) {
+            const int sh = h < H ? h : H - 1, sw = w < W ? w : W - 1;
+            for (int n = 0; n < N; n++)
+                for (int c = 0; c < 3; c++)
+                    p[((size_t)(h / 8) * W8 + w / 8) * C0 + (3 * n + c) * 64 + 8 * (h % 8) + (w % 8)] =
+                        xin[(((size_t)n * H + sh) * W + sw) * 3 + c];
+        }
+    const float *wk, *bk;
+    double* x = dalloc(n8 * DC_C);
+    double* e = dalloc(n8 * DC_C);
+    dc_layer_ptr(N, wts, 0, &wk, &bk);
+    orc_conv2d(p, H8, W8, C0, wk, bk, DC_C, 1, 1, x);
+    dc_context_layer(N, wts, 1, c_in, H8, W8, 1, e);
+    for (size_t i = 0; i < n8 * DC_C; i++) x[i] += e[i];
+    for (int b = 0; b < 6; b++) dc_block(N, wts, 2 + 5 * b, x, H8, W8, DC_C);
+    dc_layer_ptr(N, wts, 32, &wk, &bk);
+    orc_conv2d(x, H8, W8, DC_C, wk, bk, DC_CY, 3, 2, y);
+    free(p); free(x); free(e);
+    return ORC_OK;
+}
+
+/* The prior's context term PC(C_i) [H8/2][W8/2][Cz]. */
+int orc_dc_prior_term(int N, const double* c_in, int H8, int W8, const float* wts, double* pc) {
+    dc_context_layer(N, wts, 38, c_in, H8, W8, 2, pc);
+    return ORC_OK;
+}
+
+/* Chunk decoder and context generation: y^ [Hy][Wy][Cy] -> F [2Hy][2Wy][C] and (c_out) C_{i+1} [.][.][Cc]. */
+int orc_dc_trunk(int N, const double* yhat, int Hy, int Wy, const float* wts, const double* c_in, double* F,
+                 double* c_out) {
+    const int H8 = 2 * Hy, W8 = 2 * Wy;
+    const size_t n8 = (size_t)H8 * W8;
+    const float *wk, *bk;
+    double* t = dalloc((size_t)Hy * Wy * 4 * DC_C);
+    double* e = dalloc(n8 * DC_C);
+    dc_layer_ptr(N, wts, 39, &wk, &bk);
+    orc_conv2d(yhat, Hy, Wy, DC_CY, wk, bk, 4 * DC_C, 1, 1, t);
+    orc_pixel_shuffle(t, Hy, Wy, DC_C, F);
+    gelu_inplace(F, n8 * DC_C);
+    dc_context_layer(N, wts, 40, c_in, H8, W8, 1, e);
+    for (size_t i = 0; i < n8 * DC_C; i++) F[i] += e[i];
+    for (int b = 0; b < 7; b++) dc_block(N, wts, 41 + 5 * b, F, H8, W8, DC_C);
+    if (c_out) {
+        double* g = dalloc(n8 * DC_C);
+        memcpy(g, F, sizeof(double) * n8 * DC_C);
+        for (int b = 0; b < 11; b++) dc_block(N, wts, 76 + 5 * b, g, H8, W8, DC_C);
+        dc_layer_ptr(N, wts, 131, &wk, &bk);
+        orc_conv2d(g, H8, W8, DC_C, wk, bk, DC_CC, 1, 1, c_out);
+        free(g);
+    }
+    free(t); free(e);
+    return ORC_OK;
+}
+
+/* Frame decoders: F [H8][W8][C] -> frames [N][H][W][3] in [0, 1]. */
+int orc_dc_frames(int N, const double* F, int H8, int W8, int H, int W, const float* wts, double* frames) {
+    const size_t n8 = (size_t)H8 * W8;
+    for (int f = 0; f < N; f++) {
+        const int l0 = DC_SHARED + DC_PER_FRAME * f;
+        const float *wk, *bk;
+        double* h = dalloc(n8 * DC_CF);
+        double* o = dalloc(n8 * 192);
+        dc_layer_ptr(N, wts, l0, &wk, &bk);
+        orc_conv2d(F, H8, W8, DC_C, wk, bk, DC_CF, 1, 1, h);
+        for (int b = 0; b < 3; b++) dc_block(N, wts, l0 + 1 + 5 * b, h, H8, W8, DC_CF);
+        dc_layer_ptr(N, wts, l0 + 16, &wk, &bk);
+        orc_conv2d(h, H8, W8, DC_CF, wk, bk, 192, 1, 1, o);
+        /* pixel shuffle x8: out[8h + dy][8w + dx][c] = o[h][w][64 c + 8 dy + dx] */
+        for (int yy = 0; yy < H; yy++)
+            for (int xx = 0; xx < W; xx++)
+                for (int c = 0; c < 3; c++)
+                    frames[(((size_t)f * H + yy) * W + xx) * 3 + c] =
+                        clampd(0.5 + o[((size_t)(yy / 8) * W8 + xx / 8) * 192 + 64 * c + 8 * (yy % 8) + (xx % 8)],
+                               0.0, 1.0);
+        free(h); free(o);
+    }
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------------------------------ */
@@ -1036,12 +1268,18 @@ int orc_encode_chunk_opts(int arch, int N, const uint8_t* frames, int H, int W, 
     int e2 = 0, k_, c_;
     orc_layer_shape(arch, N, 2, &e2, &k_, &c_);  /* A3's width: the encoder features at 1/8 */
     double* ec = tw ? dalloc((size_t)4 * Hy * Wy * e2) : NULL;
-    double* pc = tw ? dalloc((size_t)Hy * Wy * Cz) : NULL;
+    const int dcm = arch == 2;  /* the DC-block model carries its temporal context itself */
+    double* pc = (tw || dcm) ? dalloc((size_t)Hy * Wy * Cz) : NULL;
     int rc = ORC_OK;
     orc_build_tables(freq, cum);
     orc_color_in(0, frames, N, H, W, xin);
-    if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, ec, pc);
-    analysis_core(arch, N, xin, H, W, wts, ec, y);
+    if (dcm) {
+        orc_dc_prior_term(N, o->c_in, 2 * Hy, 2 * Wy, wts, pc);
+        orc_dc_analysis(N, xin, H, W, wts, o->c_in, y);
+    } else {
+        if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, ec, pc);
+        analysis_core(arch, N, xin, H, W, wts, ec, y);
+    }
     orc_hyper_analysis(arch, N, y, Hy, Wy, wts, z);
     orc_quantize_z(z, Hz * Wz, Cz, zhat, iz);
     hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, pc, mu, ls, sp);
@@ -1056,7 +1294,11 @@ int orc_encode_chunk_opts(int arch, int N, const uint8_t* frames, int H, int W, 
         double q = orc_qstep(qp);
         for (size_t i = 0; i < ny; i++) yh[i] = rhat[i] * q + mu[i];
     }
-    if (tw && o->c_out) {  /* the encoder tracks the decoder's context: F and C_{i+1} from its own y^ */
+    if (dcm && o->c_out) {  /* the encoder runs the decoder's trunk to track the context */
+        double* F = dalloc((size_t)4 * Hy * Wy * DC_C);
+        orc_dc_trunk(N, yh, Hy, Wy, wts, o->c_in, F, o->c_out);
+        free(F);
+    } else if (tw && o->c_out) {  /* the encoder tracks the decoder's context: F and C_{i+1} from its own y^ */
         double* F = dalloc((size_t)4 * Hy * Wy * ORC_CF);
         orc_chunk_feature(arch, N, yh, Hy, Wy, tw, o->c_in, F);
         orc_context_next(arch, N, F, 2 * Hy, 2 * Wy, tw, o->c_out);
@@ -1068,7 +1310,7 @@ int orc_encode_chunk_opts(int arch, int N, const uint8_t* frames, int H, int W, 
     if (cap < hdr) { rc = ORC_ERR_CAPACITY; goto done; }
     memset(out, 0, hdr);
     memcpy(out, "UFVC", 4);
-    out[4] = (uint8_t)(1 + (pm ? 1 : 0) + (tw ? 2 : 0)); out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
+    out[4] = (uint8_t)(1 + (pm ? 1 : 0) + ((tw || dcm) ? 2 : 0)); out[5] = (uint8_t)arch; out[6] = (uint8_t)N; out[7] = (uint8_t)qp;
     put16(out + 8, (uint32_t)W); put16(out + 10, (uint32_t)H);
     put32(out + 12, (uint32_t)K); put32(out + 16, (uint32_t)Kz);
     memcpy(out + 20, iz, Cz);
@@ -1118,8 +1360,8 @@ int orc_decode_chunk_opts(int arch, int N, const uint8_t* bits, size_t nbytes, i
     if (orc_latent_dims(arch, H, W, &Hy, &Wy, &Hz, &Wz, &Cy, &Cz)) return ORC_ERR_ARG;
     size_t hdr = (20 + (size_t)Cz + 3) / 4 * 4;
     if (nbytes < hdr || memcmp(bits, "UFVC", 4) || bits[4] < 1 || bits[4] > 4) return ORC_ERR_CORRUPT;
-    const int v_pm = bits[4] == 2 || bits[4] == 4, v_tc = bits[4] >= 3;
-    if ((v_pm && !pm) || (v_tc != (tw != NULL))) return ORC_ERR_ARG;
+    const int v_pm = bits[4] == 2 || bits[4] == 4, v_tc = bits[4] >= 3, dcm = arch == 2;
+    if ((v_pm && !pm) || (v_tc != (tw != NULL || dcm))) return ORC_ERR_ARG;
     if (bits[5] != arch || bits[6] != N || get16(bits + 8) != (uint32_t)W || get16(bits + 10) != (uint32_t)H)
         return ORC_ERR_ARG;
     int qp = bits[7];
@@ -1140,12 +1382,13 @@ int orc_decode_chunk_opts(int arch, int N, const uint8_t* bits, size_t nbytes, i
     int16_t* rhat = (int16_t*)malloc(2 * ny);
     double* yhat = dalloc(ny);
     double* sp = dalloc((size_t)Hy * Wy * Cz);
-    double* pc = tw ? dalloc((size_t)Hy * Wy * Cz) : NULL;
-    double* F = tw ? dalloc((size_t)4 * Hy * Wy * ORC_CF) : NULL;
+    double* pc = (tw || dcm) ? dalloc((size_t)Hy * Wy * Cz) : NULL;
+    double* F = (tw || dcm) ? dalloc((size_t)4 * Hy * Wy * (dcm ? DC_C : ORC_CF)) : NULL;
     size_t used1 = 0, used2 = 0;
     int rc = orc_rans_decode(bits + hdr, nbytes - hdr, zidx, nz, Kz, freq, cum, NSYM, RMAX, zhat, &used1);
     if (rc) goto done;
-    if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, NULL, pc);
+    if (dcm) orc_dc_prior_term(N, o->c_in, 2 * Hy, 2 * Wy, wts, pc);
+    else if (tw) orc_context_terms(arch, N, o->c_in, 2 * Hy, 2 * Wy, tw, NULL, pc);
     hyper_synthesis_core(arch, N, zhat, Hz, Wz, Hy, Wy, wts, pc, mu, ls, sp);
     orc_scale_index(ls, ny, qp, idx);
     rc = orc_rans_decode(bits + hdr + used1, nbytes - hdr - used1, idx, ny, K, freq, cum, NSYM, RMAX, rhat, &used2);
@@ -1161,11 +1404,16 @@ int orc_decode_chunk_opts(int arch, int N, const uint8_t* bits, size_t nbytes, i
         for (size_t i = 0; i < ny; i++) yhat[i] = rhat[i] * q + mu[i];
     }
     if (yhat_out) memcpy(yhat_out, yhat, sizeof(double) * ny);
-    if (tw) {
-        orc_chunk_feature(arch, N, yhat, Hy, Wy, tw, o->c_in, F);
-        if (o->c_out) orc_context_next(arch, N, F, 2 * Hy, 2 * Wy, tw, o->c_out);
+    if (dcm) {
+        orc_dc_trunk(N, yhat, Hy, Wy, wts, o->c_in, F, o->c_out);
+        if (frames_out) orc_dc_frames(N, F, 2 * Hy, 2 * Wy, H, W, wts, frames_out);
+    } else {
+        if (tw) {
+            orc_chunk_feature(arch, N, yhat, Hy, Wy, tw, o->c_in, F);
+            if (o->c_out) orc_context_next(arch, N, F, 2 * Hy, 2 * Wy, tw, o->c_out);
+        }
+        if (frames_out) synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, F, tw, frames_out);
     }
-    if (frames_out) synthesis_core(arch, N, yhat, Hy, Wy, H, W, wts, F, tw, frames_out);
 done:
     free(freq); free(cum); free(zhat); free(zidx); free(mu); free(ls); free(idx); free(rhat); free(yhat); free(sp);
     free(pc); free(F);

@@ -11,5 +11,6 @@ This package draws random numbers and lays them out; it holds none of the codec'
 """
 from .video import moving_texture, chunk_frames  # noqa: F401
 from .weights import layer_table, draw_weights, ARCHS, mean_layer_table, draw_mean_weights, \
-    temporal_layer_table, draw_temporal_weights  # noqa: F401
+    temporal_layer_table, draw_temporal_weights, \
+    dc_layer_table, draw_dc_weights  # noqa: F401
 from .symbols import laplace_symbols  # noqa: F401

@@ -135,3 +135,59 @@ def split_temporal_weights(blob: np.ndarray, arch: int, n_frames: int) -> dict[s
         off += n + co
     assert off == blob.size
     return out
+
+
+# DC-block model (arch 2): chunk width 512, frame-decoder width 256, context 128, latent 256, hyper-latent 128
+DC = dict(c=512, cf=256, cc=128, cy=256, cz=128)
+
+
+def dc_layer_table(n_frames: int) -> list[tuple[str, int, int, int]]:
+    """[(name, Cout, k, Cin)] of the DC-block model's blob; a depth-wise layer ("*.dw") has Cin = 1."""
+    c, cf, cc, cy, cz = DC["c"], DC["cf"], DC["cc"], DC["cy"], DC["cz"]
+
+    def block(prefix, w):
+        return [(f"{prefix}.a", w, 1, w), (f"{prefix}.dw", w, 3, 1), (f"{prefix}.b", w, 1, w),
+                (f"{prefix}.c", 2 * w, 1, w), (f"{prefix}.d", w, 1, 2 * w)]
+    t = [("PE", c, 1, 3 * n_frames * 64), ("EC", c, 1, cc)]
+    for b in range(6):
+        t += block(f"E{b}", c)
+    t += [("ED", cy, 3, c), ("H1", cz, 3, cy), ("H2", cz, 3, cz), ("S1", 4 * cz, 3, cz), ("S2", 4 * cz, 3, cz),
+          ("S3", 2 * cy, 1, cz), ("PC", cz, 3, cc), ("DU", 4 * c, 1, cy), ("FC", c, 1, cc)]
+    for b in range(7):
+        t += block(f"D{b}", c)
+    for b in range(11):
+        t += block(f"G{b}", c)
+    t += [("GO", cc, 1, c)]
+    for f in range(n_frames):
+        t += [(f"FP.{f}", cf, 1, c)]
+        for b in range(3):
+            t += block(f"F{f}.{b}", cf)
+        t += [(f"FO.{f}", 192, 1, cf)]
+    return t
+
+
+def draw_dc_weights(n_frames: int, seed: int = 0, bias_std: float = 0.01, branch_gain: float = 0.2,
+                    loop_gain: float = 0.1) -> np.ndarray:
+    """Flat float32 blob of the DC-block model, N(0, 2/fan_in) kernels, except: the last layer of each residual
+    branch (".b", ".d") at branch_gain times that standard deviation, so that 24 chunk-level and 3 frame-level
+    blocks of residual additions keep the activations' scale; and EC, FC (the context's way into the next
+    chunk) and GO (the context generator's output) at loop_gain, so that the untrained context recursion
+    contracts (with GO at full gain the context's scale grows about 1.3x per chunk)."""
+    rng = np.random.default_rng([seed, 11])
+    parts = []
+    for name, co, k, ci in dc_layer_table(n_frames):
+        g = loop_gain if name in ("EC", "FC", "GO") else branch_gain if name.endswith((".b", ".d")) else 1.0
+        fan_in = k * k * ci
+        parts.append(rng.normal(0.0, g * np.sqrt(2.0 / fan_in), size=co * k * k * ci).astype(np.float32))
+        parts.append(rng.normal(0.0, bias_std, size=co).astype(np.float32))
+    return np.ascontiguousarray(np.concatenate(parts))
+
+
+def split_dc_weights(blob: np.ndarray, n_frames: int) -> dict[str, tuple[np.ndarray, np.ndarray]]:
+    out, off = {}, 0
+    for name, co, k, ci in dc_layer_table(n_frames):
+        n = co * k * k * ci
+        out[name] = (blob[off:off + n].reshape(co, k, k, ci), blob[off + n:off + n + co])
+        off += n + co
+    assert off == blob.size
+    return out
