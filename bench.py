@@ -5,7 +5,7 @@ scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
                     [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
-                    [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--no-temporal]
+                    [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--no-temporal] [--no-dc]
                     [--serving-window S]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
@@ -135,6 +135,31 @@ def run_reference(args) -> None:
             "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "frames/s"},
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def dc_flops(Hy: int, Wy: int) -> dict:
+    """Tensor-core FLOPs (2 x MACs) of one encode and one decode of the DC-block model (arch 2, N frames) at
+    latent size Hy x Wy, from its layer table: the encoder runs patch embedding, encoder blocks, ED, H1, H2,
+    PC and, to track the context, the chunk decoder and the context generation; the decoder runs PC, the
+    chunk decoder, the frame decoders and the context generation.  (S1..S3 are the FP32 path.)"""
+    from synthetic.weights import dc_layer_table
+    P8, P16 = 4 * Hy * Wy, Hy * Wy
+    Hz, Wz = -(-Hy // 4), -(-Wy // 4)
+    pos = {"ED": P16, "PC": P16, "DU": P16, "H1": (-(-Hy // 2)) * (-(-Wy // 2)), "H2": Hz * Wz}
+    enc = dec = 0
+    for name, co, k, ci in dc_layer_table(N):
+        if name in ("S1", "S2", "S3"):
+            continue
+        f = 2 * pos.get(name, P8) * co * k * k * ci
+        head = name.split(".")[0]
+        if name in ("PE", "EC", "ED", "H1", "H2") or (head.startswith("E") and head[1:].isdigit()):
+            enc += f
+        elif name.startswith(("FP", "FO")) or (head.startswith("F") and head[1:].isdigit()):
+            dec += f
+        elif name == "FC" or name in ("DU", "PC", "GO") or head[0] in "DG":
+            enc += f
+            dec += f
+    return {"enc": enc, "dec": dec}
 
 
 def conv_flops(Hy: int, Wy: int) -> dict:
@@ -384,6 +409,7 @@ def main() -> None:
     ap.add_argument("--no-pm", action="store_true", help="skip the progressive-means variant")
     ap.add_argument("--no-color", action="store_true", help="skip the colour-format variants")
     ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-context variant")
+    ap.add_argument("--no-dc", action="store_true", help="skip the DC-block model (HT-S counts)")
     ap.add_argument("--serving-window", type=float, default=4.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -528,6 +554,25 @@ def main() -> None:
                "stage_ms_per_step": st_t}
         ct.close()
 
+    # ---- the DC-block model at the paper's HT-S block counts (arch 2), BF16, context carried between steps
+    dcx = None
+    if args.precision == "bf16" and not args.no_dc:
+        cdc = U.Codec(2, N, K, synthetic.draw_dc_weights(N, seed=0), "bf16", device=local)
+        sdc = max(3, args.steps // 2)
+        rd = time_codec(cdc, fr, frames_np, W_, H_, sdc, 3, True, flush, temporal=True)
+        t_enc, t_dec = statistics.mean(rd["t_enc"]), statistics.mean(rd["t_dec"])
+        fl = dc_flops(-(-H_ // 16), -(-W_ // 16))
+        st_d = {k: round(sum(m for m, _ in v) / sdc, 4) for k, v in
+                sorted(rd["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}
+        pk_dc = peaks()["bf16_tflops_sustained"]
+        tf = (fl["enc"] + fl["dec"]) / ((t_enc + t_dec) / 1000.0) / 1e12
+        dcx = {"value": N * sdc / (sum(a + b for a, b in zip(rd["t_enc"], rd["t_dec"])) / 1000.0),
+               "enc_fps": N / (t_enc / 1000.0), "dec_fps": N / (t_dec / 1000.0), "psnr_db": rd["psnr"],
+               "bytes_per_chunk": rd["nbytes"], "steps": sdc, "macs_per_frame_g": 205.3,
+               "tensor_tflop_per_step": (fl["enc"] + fl["dec"]) / 1e12, "tensor_tflops": tf,
+               "tensor_frac_of_sustained": tf / pk_dc, "stage_ms_per_step": st_d}
+        cdc.close()
+
     # ---- colour interface (YUV444 model interface): BT.709 RGB and YUV420 chunks of the same content
     color = None
     if args.precision == "bf16" and not args.no_color and (W_, H_) == (W, H):
@@ -619,6 +664,8 @@ def main() -> None:
             line["color_formats"] = color
         if tcx is not None:
             line["temporal_context_path"] = tcx
+        if dcx is not None:
+            line["dc_model_path"] = dcx
         if pm is not None:
             if fp32 is not None:
                 pm["dbitrate_vs_fp32"] = (pm["bytes_per_chunk"] - fp32["bytes_per_chunk"]) / fp32["bytes_per_chunk"]

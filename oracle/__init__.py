@@ -216,7 +216,7 @@ def analysis(arch: int, frames: np.ndarray, weights: np.ndarray) -> np.ndarray:
 def hyper_analysis(arch: int, N: int, y: np.ndarray, weights: np.ndarray) -> np.ndarray:
     y = np.ascontiguousarray(y, np.float64)
     Hy, Wy, _ = y.shape
-    cz = {0: 64, 1: 128}[arch]
+    cz = {0: 64, 1: 128, 2: 128}[arch]
     z = np.empty(((Hy + 3) // 4, (Wy + 3) // 4, cz), np.float64)
     _check(lib().orc_hyper_analysis(arch, N, _p(y), Hy, Wy, _p(weights), _p(z)), "hyper_analysis")
     return z
@@ -237,7 +237,7 @@ def hyper_synthesis(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, weigh
     prior of the progressive mean steps."""
     zhat = np.ascontiguousarray(zhat, np.int16)
     Hz, Wz, _ = zhat.shape
-    cy, cz = {0: (128, 64), 1: (256, 128)}[arch]
+    cy, cz = {0: (128, 64), 1: (256, 128), 2: (256, 128)}[arch]
     mu = np.empty((Hy, Wy, cy), np.float64)
     ls = np.empty((Hy, Wy, cy), np.float64)
     sp = np.empty((Hy, Wy, cz), np.float64)
@@ -419,7 +419,7 @@ def hyper_synthesis_add(arch: int, N: int, zhat: np.ndarray, Hy: int, Wy: int, w
     """Hyper-synthesis with add_s [Hy][Wy][Cz] added to the features before S3 -> (mu, log sigma, s)."""
     zhat = np.ascontiguousarray(zhat, np.int16)
     Hz, Wz, _ = zhat.shape
-    cy, cz = {0: (128, 64), 1: (256, 128)}[arch]
+    cy, cz = {0: (128, 64), 1: (256, 128), 2: (256, 128)}[arch]
     mu = np.empty((Hy, Wy, cy), np.float64)
     ls = np.empty((Hy, Wy, cy), np.float64)
     sp = np.empty((Hy, Wy, cz), np.float64)

@@ -99,6 +99,11 @@ struct Plan {
     float *t_zero = nullptr, *t_F_e = nullptr, *t_pc_e = nullptr, *t_yh_e = nullptr, *t_F_d = nullptr,
           *t_pc_d = nullptr;
     bool t_enc_ready = false, t_dec_ready = false;
+    // DC-block model activations (activation type; o float): encoder s2d input, trunk and block scratch;
+    // decoder trunk, block scratch and the frame decoders' [N][H8][W8][.] tensors
+    float *dc_x0 = nullptr, *dc_h = nullptr, *dc_t1e = nullptr, *dc_t2e = nullptr, *dc_t3e = nullptr;
+    float *dc_F = nullptr, *dc_t1d = nullptr, *dc_t2d = nullptr, *dc_t3d = nullptr, *dc_hf = nullptr,
+          *dc_f1 = nullptr, *dc_f2 = nullptr, *dc_f3 = nullptr, *dc_o = nullptr;
     bool enc_ready = false, dec_ready = false;
     std::vector<void*> allocs;
     Workspace ws_enc, ws_dec;
@@ -136,6 +141,12 @@ struct ufvc_ctx {
     LayerW tl[TL_N];
     LayerW tdf;
     bool tc_on = false;
+    int cc = kCc;  // temporal context channels
+    // DC-block model (arch 2): its shared layers by blob index (depth-wise layers: w = [9][C] float) and
+    // the frame-decoder layers grouped over the frame positions; it always carries the temporal context
+    bool dcm = false;
+    std::vector<LayerW> dcl;
+    LayerW dcf[kDcPerFrame];
     const void* cur_cin = nullptr;
     void* cur_cout = nullptr;
     std::map<long long, Plan*> plans;
@@ -306,6 +317,14 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
         AL(p->cnt_y, (size_t)K);
         AL(p->off_ws, (size_t)p->Kz + K);
         AL(p->zthr, (size_t)kBins - 1);
+        if (ctx->dcm) {
+            const size_t P = (size_t)p->h3 * p->w3;
+            AL(p->dc_x0, (P * 3 * N * 64 + act - 1) / act);
+            AL(p->dc_h, (P * kDcC + act - 1) / act);
+            AL(p->dc_t1e, (P * kDcC + act - 1) / act);
+            AL(p->dc_t2e, (P * kDcC + act - 1) / act);
+            AL(p->dc_t3e, (P * 2 * kDcC + act - 1) / act);
+        }
     }
     if (dec) {
         AL(p->dzhat, p->nz);
@@ -335,6 +354,18 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
         AL(p->bufB, (n2 + act - 1) / act);
         AL(p->bufT2, (n2 + act - 1) / act);
         AL(p->bufC, (n3 + act - 1) / act);
+        if (ctx->dcm) {
+            const size_t P = (size_t)p->h3 * p->w3;
+            AL(p->dc_F, (P * kDcC + act - 1) / act);
+            AL(p->dc_t1d, (P * kDcC + act - 1) / act);
+            AL(p->dc_t2d, (P * kDcC + act - 1) / act);
+            AL(p->dc_t3d, (P * 2 * kDcC + act - 1) / act);
+            AL(p->dc_hf, (N * P * kDcCf + act - 1) / act);
+            AL(p->dc_f1, (N * P * kDcCf + act - 1) / act);
+            AL(p->dc_f2, (N * P * kDcCf + act - 1) / act);
+            AL(p->dc_f3, (N * P * 2 * kDcCf + act - 1) / act);
+            AL(p->dc_o, N * P * 192);
+        }
     }
 #undef AL
     return UFVC_OK;
@@ -364,7 +395,7 @@ static ufvc_status tc_buffers(ufvc_ctx* ctx, Plan* p, bool enc, size_t* dry_byte
         {enc ? &p->t_F_e : &p->t_F_d, (n8 * kCf + act - 1) / act},
         {enc ? &p->t_pc_e : &p->t_pc_d, (size_t)p->Hy * p->Wy * ctx->arch.cz},
         {enc ? &p->t_yh_e : nullptr, (ny + act - 1) / act},
-        {enc ? &p->t_zero : nullptr, (n8 * kCc + act - 1) / act}};
+        {enc ? &p->t_zero : nullptr, (n8 * ctx->cc + act - 1) / act}};
     for (auto& e : bufs) {
         if (!e.b) continue;
         if (dry_bytes) *dry_bytes += (e.n * sizeof(float) + 255) & ~(size_t)255;
@@ -404,7 +435,7 @@ static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan**
         return st;
     if (ctx->tc_on && !p->t_enc_ready) {  // the zero context lives with the encoder half: allocate it first
         if ((st = tc_buffers(ctx, p, true, nullptr)) != UFVC_OK) return st;
-        CK(cudaMemset(p->t_zero, 0, (size_t)4 * p->Hy * p->Wy * kCc * (ctx->cfg.precision == UFVC_FP32 ? 4 : 2)));
+        CK(cudaMemset(p->t_zero, 0, (size_t)4 * p->Hy * p->Wy * ctx->cc * (ctx->cfg.precision == UFVC_FP32 ? 4 : 2)));
         p->t_enc_ready = true;
     }
     if (ctx->tc_on && for_decode && !p->t_dec_ready) {
@@ -562,6 +593,71 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
     return UFVC_OK;
 }
 
+// A depth-wise 3x3 layer (blob kernel [C][3][3][1] + bias [C], per group) as float [g][9][C] taps and [g][C]
+// biases for the depth-wise kernel (every precision).
+static ufvc_status upload_dw(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
+                             int gstride, int C) {
+    L.cout = C; L.k = 3; L.cin = 1; L.groups = groups;
+    std::vector<float> w((size_t)groups * 9 * C), b((size_t)groups * C);
+    for (int g = 0; g < groups; ++g) {
+        const float* src = blob + offs[first + g * gstride];
+        for (int c = 0; c < C; ++c) {
+            for (int t = 0; t < 9; ++t) w[((size_t)g * 9 + t) * C + c] = src[(size_t)c * 9 + t];
+            b[(size_t)g * C + c] = src[(size_t)C * 9 + c];
+        }
+    }
+    ufvc_status st;
+    if ((st = dalloc(ctx, nullptr, &L.w, w.size())) != UFVC_OK) return st;
+    if ((st = dalloc(ctx, nullptr, &L.b, b.size())) != UFVC_OK) return st;
+    CK(cudaMemcpy(L.w, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.b, b.data(), b.size() * 4, cudaMemcpyHostToDevice));
+    return UFVC_OK;
+}
+
+// The DC-block model's layers: shared ones into ctx->dcl (and the hyperprior into ctx->enc[L_H1..L_S3], the
+// prior's context layer into ctx->tl[TL_PC], so that the hyperprior code serves both models), frame ones
+// grouped into ctx->dcf.
+static ufvc_status upload_dc(ufvc_ctx* ctx, const float* weights) {
+    const int N = ctx->N, nl = kDcShared + kDcPerFrame * N;
+    std::vector<size_t> offs(nl);
+    size_t off = 0;
+    for (int l = 0; l < nl; ++l) {
+        int co, k, ci;
+        dc_layer_shape(N, l, &co, &k, &ci);
+        offs[l] = off;
+        off += (size_t)co * k * k * ci + co;
+    }
+    ufvc_status st;
+    ctx->dcl.assign(kDcShared, LayerW());
+    for (int l = 0; l < kDcShared; ++l) {
+        int sh[3];
+        dc_layer_shape(N, l, &sh[0], &sh[1], &sh[2]);
+        if (sh[2] == 1) {
+            st = upload_dw(ctx, ctx->dcl[l], weights, offs.data(), l, 1, 1, sh[0]);
+        } else if (l >= DC_H1 && l <= DC_S3) {  // S1..S3: the deterministic FP32 path, as in the plain model
+            st = upload_layer(ctx, ctx->enc[L_H1 + (l - DC_H1)], weights, offs.data(), l, 1, l <= DC_H2, false, false,
+                              sh, true, 1);
+        } else if (l == DC_PC) {
+            st = upload_layer(ctx, ctx->tl[TL_PC], weights, offs.data(), l, 1, true, false, false, sh, true, 1);
+        } else {
+            st = upload_layer(ctx, ctx->dcl[l], weights, offs.data(), l, 1, true, l == DC_DU, false, sh, true, 1);
+        }
+        if (st != UFVC_OK) return st;
+    }
+    for (int j = 0; j < kDcPerFrame; ++j) {
+        int sh[3];
+        dc_layer_shape(N, kDcShared + j, &sh[0], &sh[1], &sh[2]);
+        st = sh[2] == 1 ? upload_dw(ctx, ctx->dcf[j], weights, offs.data(), kDcShared + j, N, kDcPerFrame, sh[0])
+                        : upload_layer(ctx, ctx->dcf[j], weights, offs.data(), kDcShared + j, N, true, false, false, sh,
+                                       true, kDcPerFrame);
+        if (st != UFVC_OK) return st;
+    }
+    ctx->dcm = true;
+    ctx->tc_on = true;
+    ctx->cc = kDcCc;
+    return UFVC_OK;
+}
+
 // A1 (3x3, stride 2, 3N -> e0) regrouped for space-to-depth input: super-pixel (Y, X) holds input pixels
 // (2Y + dy, 2X + dx) as channels [2 dy + dx][32].  Output pixel (oh, ow) reads input rows 2 oh - 1 .. 2 oh + 1,
 // i.e. sub-row 1 of super-row oh - 1 and both sub-rows of super-row oh: tap (sy, sx) of the 2x2 form at
@@ -613,6 +709,8 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
         for (LayerW* L : {&ctx->tl[0], &ctx->tl[1], &ctx->tl[2], &ctx->tl[3], &ctx->tl[4], &ctx->tdf}) {
             cudaFree(L->w); cudaFree(L->b); cudaFree(L->wtc); cudaFree(L->btc);
         }
+        for (LayerW& L : ctx->dcl) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
+        for (LayerW& L : ctx->dcf) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
         cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
@@ -634,7 +732,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
     if (n_weights != weight_count(cfg->arch, cfg->chunk_len)) return UFVC_ERR_ARG;
     // the tensor-core path stages K in 64-channel chunks: every activation width must be a multiple of
     // 64, which holds for the 1080p-family widths only (the tiny widths include 96)
-    if (cfg->precision != UFVC_FP32 && cfg->arch != 1) return UFVC_ERR_UNSUPPORTED;
+    if (cfg->precision != UFVC_FP32 && cfg->arch == 0) return UFVC_ERR_UNSUPPORTED;
+    if (cfg->precision == UFVC_FP8 && cfg->arch == 2) return UFVC_ERR_UNSUPPORTED;
     ufvc_ctx* ctx = new ufvc_ctx();
     ctx->cfg = *cfg;
     ctx->arch = a;
@@ -657,6 +756,11 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         cudaMemcpy(ctx->d_qinv, ctx->tabs.qinv.data(), 64 * 4, cudaMemcpyHostToDevice) ||
         cudaMemset(ctx->d_status, 0, 4))
         return bail(UFVC_ERR_CUDA);
+    if (cfg->arch == 2) {
+        if ((st = upload_dc(ctx, weights)) != UFVC_OK) return bail(st);
+        *out = ctx;
+        return UFVC_OK;
+    }
     // weight blob offsets
     const int nl = L_NENC + D_NDEC * ctx->N;
     std::vector<size_t> offs(nl);
@@ -704,6 +808,10 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     for (int l = 0; l < TL_N; ++l) c->tl[l] = base->tl[l];
     c->tdf = base->tdf;
     c->tc_on = base->tc_on;
+    c->cc = base->cc;
+    c->dcm = base->dcm;
+    c->dcl = base->dcl;
+    for (int j = 0; j < kDcPerFrame; ++j) c->dcf[j] = base->dcf[j];
     c->borrowed = true;
     if (cudaMalloc(&c->d_status, 4) != cudaSuccess || cudaMemset(c->d_status, 0, 4) != cudaSuccess) {
         cudaFree(c->d_status);
@@ -852,16 +960,91 @@ static ufvc_status run_progressive(ufvc_ctx* ctx, int Hy, int Wy, const float* y
     return UFVC_OK;
 }
 
+// One DC block (PWa, DW, PWb, PWc, PWd) on x in place: y = x + PWb(GELU(DW(PWa(x)))), x = y + PWd(GELU(PWc(y))).
+// groups > 1: one block per frame position (own weights), x / t1 / t2 with gs elements per group, t3 gs3.
+static ufvc_status run_dc_block(ufvc_ctx* ctx, const LayerW* L, void* x, int H, int W, int groups, long long gs,
+                                long long gs3, void* t1, void* t2, void* t3, cudaStream_t s) {
+    const bool f32 = ctx->cfg.precision == UFVC_FP32;
+    const long long ig = groups > 1 ? gs : 0, ig3 = groups > 1 ? gs3 : 0;
+    RUN(conv(ctx, L[0], x, H, W, 1, 0, OUT_NHWC, t1, H, W, s, nullptr, nullptr, 0, ig, ig, 0, groups));
+    launch_dw_conv(t1, groups, H, W, L[1].cout, ig, L[1].w, L[1].b, t2, f32, s);
+    RUN(conv(ctx, L[2], t2, H, W, 1, 0, OUT_NHWC, x, H, W, s, x, nullptr, 0, ig, ig, ig, groups));
+    RUN(conv(ctx, L[3], x, H, W, 1, 1, OUT_NHWC, t3, H, W, s, nullptr, nullptr, 0, ig, ig3, 0, groups));
+    RUN(conv(ctx, L[4], t3, H, W, 1, 0, OUT_NHWC, x, H, W, s, x, nullptr, 0, ig3, ig, ig, groups));
+    return UFVC_OK;
+}
+
+// DC-block model, chunk decoder: F = GELU(PS(DU(y^))) + FC(C_i), then 7 blocks (t1..t3: block scratch).
+static ufvc_status run_dc_trunk(ufvc_ctx* ctx, Plan* p, const void* yhat, const void* cin, void* F, void* t1, void* t2,
+                                void* t3, cudaStream_t s) {
+    const int H8 = p->h3, W8 = p->w3;
+    prof_begin(ctx, "dc.chunk_decoder", s);
+    RUN(conv(ctx, ctx->dcl[DC_DU], yhat, p->Hy, p->Wy, 1, 1, OUT_PS, F, H8, W8, s));
+    RUN(conv(ctx, ctx->dcl[DC_FC], cin, H8, W8, 1, 0, OUT_NHWC, F, H8, W8, s, F));
+    for (int b = 0; b < 7; ++b) RUN(run_dc_block(ctx, &ctx->dcl[DC_D0 + 5 * b], F, H8, W8, 1, 0, 0, t1, t2, t3, s));
+    prof_end(ctx, s, 2 + 7 * 5);
+    return UFVC_OK;
+}
+
+// DC-block model, context generation in place on F: 11 blocks, C_{i+1} = GO(.).
+static ufvc_status run_dc_context(ufvc_ctx* ctx, Plan* p, void* F, void* cout, void* t1, void* t2, void* t3,
+                                  cudaStream_t s) {
+    const int H8 = p->h3, W8 = p->w3;
+    prof_begin(ctx, "dc.context", s);
+    for (int b = 0; b < 11; ++b) RUN(run_dc_block(ctx, &ctx->dcl[DC_G0 + 5 * b], F, H8, W8, 1, 0, 0, t1, t2, t3, s));
+    RUN(conv(ctx, ctx->dcl[DC_GO], F, H8, W8, 1, 0, OUT_NHWC, cout, H8, W8, s));
+    prof_end(ctx, s, 11 * 5 + 1);
+    return UFVC_OK;
+}
+
+// DC-block model, frame decoders (grouped over the frame positions) from F to frames in final_mode.
+static ufvc_status run_dc_frames(ufvc_ctx* ctx, Plan* p, const void* F, void* frames_out, int final_mode,
+                                 cudaStream_t s) {
+    const int H8 = p->h3, W8 = p->w3, N = ctx->N;
+    const long long P = (long long)H8 * W8, gsf = P * kDcCf, gs3 = P * 2 * kDcCf, gso = P * 192;
+    prof_begin(ctx, "dc.frame_decoders", s);
+    RUN(conv(ctx, ctx->dcf[0], F, H8, W8, 1, 0, OUT_NHWC, p->dc_hf, H8, W8, s, nullptr, nullptr, 0, 0, gsf, 0, N));
+    for (int b = 0; b < 3; ++b)
+        RUN(run_dc_block(ctx, &ctx->dcf[1 + 5 * b], p->dc_hf, H8, W8, N, gsf, gs3, p->dc_f1, p->dc_f2, p->dc_f3, s));
+    RUN(conv(ctx, ctx->dcf[kDcPerFrame - 1], p->dc_hf, H8, W8, 1, 0, OUT_NHWC, p->dc_o, H8, W8, s, nullptr, nullptr, 0,
+             gsf, gso, 0, N, true));
+    const bool conv_out = ctx->color != UFVC_COLOR_RGB;
+    launch_ps8_out(p->dc_o, N, H8, W8, p->H, p->W, conv_out ? (void*)p->fstage : frames_out,
+                   !conv_out && final_mode == OUT_PS_FINAL_U8, s);
+    if (conv_out) launch_color_out(ctx->color, final_mode == OUT_PS_FINAL_F32, p->fstage, N, p->H, p->W, frames_out, s);
+    prof_end(ctx, s, 2 + 3 * 5 + 1 + (conv_out ? 1 : 0));
+    return UFVC_OK;
+}
+
+// DC-block model, patch embedding and chunk encoder: frames -> y (float).
+static ufvc_status run_dc_encoder(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, const void* cin, cudaStream_t s) {
+    const int H8 = p->h3, W8 = p->w3;
+    const bool f32 = ctx->cfg.precision == UFVC_FP32;
+    prof_begin(ctx, "pack", s);
+    launch_pack_s2d8(frames, ctx->N, p->H, p->W, H8, W8, p->dc_x0, f32, ctx->color, s);
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "analysis", s);
+    RUN(conv(ctx, ctx->dcl[DC_PE], p->dc_x0, H8, W8, 1, 0, OUT_NHWC, p->dc_h, H8, W8, s));
+    RUN(conv(ctx, ctx->dcl[DC_EC], cin, H8, W8, 1, 0, OUT_NHWC, p->dc_h, H8, W8, s, p->dc_h));
+    for (int b = 0; b < 6; ++b)
+        RUN(run_dc_block(ctx, &ctx->dcl[DC_E0 + 5 * b], p->dc_h, H8, W8, 1, 0, 0, p->dc_t1e, p->dc_t2e, p->dc_t3e, s));
+    RUN(conv(ctx, ctx->dcl[DC_ED], p->dc_h, H8, W8, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s, nullptr, nullptr, 0, 0, 0, 0,
+             1, true));
+    prof_end(ctx, s, 2 + 6 * 5 + 1);
+    return UFVC_OK;
+}
+
 // FP8 calibration run (FP32 path): record max |x| of activation tensor t
 static void probe(ufvc_ctx* ctx, int t, const float* x, size_t n, cudaStream_t s) {
     if (ctx->amax) launch_absmax(x, n, ctx->amax + t, s);
 }
 
-static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
+// The plain model's analysis: pack, A1..A3, EC(C_i) with the temporal context, the cross-frame interaction,
+// A4 -> y (float in every precision: it feeds the quantiser).
+static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, const void* cin, cudaStream_t s) {
     const Arch& a = ctx->arch;
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     const bool s2d = ctx->a1s2d.wtc != nullptr && p->C0p == 32;
-    ctx->cur_ws = &p->ws_enc;
     prof_begin(ctx, "pack", s);
     if (ctx->cfg.precision == UFVC_FP32)
         launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s, ctx->color);
@@ -881,7 +1064,6 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);
     RUN(conv(ctx, ctx->enc[L_A3], p->a2, p->h2, p->w2, 2, 1, OUT_NHWC, p->a3, p->h3, p->w3, s));
     probe(ctx, T_A3, p->a3, (size_t)p->h3 * p->w3 * a.e2, s);
-    const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
     if (cin)  // temporal context: the patch-embedded features + EC(C_i), in place
         RUN(conv(ctx, ctx->tl[TL_EC], cin, p->h3, p->w3, 1, 0, OUT_NHWC, p->a3, p->h3, p->w3, s, p->a3));
     RUN(conv(ctx, ctx->enc[L_XA], p->a3, p->h3, p->w3, 1, 1, OUT_NHWC, p->xt, p->h3, p->w3, s));
@@ -894,6 +1076,16 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
              0, 1, true));
     probe(ctx, T_Y, p->y, p->ny, s);
     prof_end(ctx, s, 6);
+    return UFVC_OK;
+}
+
+static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, int qp, cudaStream_t s) {
+    const Arch& a = ctx->arch;
+    const bool fp8 = ctx->cfg.precision == UFVC_FP8;
+    ctx->cur_ws = &p->ws_enc;
+    const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
+    if (ctx->dcm) RUN(run_dc_encoder(ctx, p, frames, cin, s));
+    else RUN(run_plain_analysis(ctx, p, frames, cin, s));
     prof_begin(ctx, "hyper_analysis", s);
     if (use_tc(ctx, ctx->enc[L_H1])) {
         // tensor cores: only the encoder computes z (z^ travels in the bit-stream), so the hyper-analysis
@@ -926,7 +1118,12 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
         const bool f32 = ctx->cfg.precision == UFVC_FP32;
         launch_dequant(p->rhat, p->mu, p->ny, ctx->d_qstep, nullptr, f32 ? p->t_yh_e : nullptr,
                        f32 ? nullptr : reinterpret_cast<__nv_bfloat16*>(p->t_yh_e), s, nullptr, 0.f, qp);
-        RUN(run_chunk_feature(ctx, p, p->t_yh_e, cin, p->t_F_e, ctx->cur_cout, s));
+        if (ctx->dcm) {  // the encoder runs the decoder's trunk and context generation on its own scratch
+            RUN(run_dc_trunk(ctx, p, p->t_yh_e, cin, p->dc_h, p->dc_t1e, p->dc_t2e, p->dc_t3e, s));
+            RUN(run_dc_context(ctx, p, p->dc_h, ctx->cur_cout, p->dc_t1e, p->dc_t2e, p->dc_t3e, s));
+        } else {
+            RUN(run_chunk_feature(ctx, p, p->t_yh_e, cin, p->t_F_e, ctx->cur_cout, s));
+        }
     }
     return UFVC_OK;
 }
@@ -1062,6 +1259,13 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
     prof_end(ctx, s, ctx->pm_on ? 1 : 2);
     const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
+    if (ctx->dcm) {  // chunk decoder, frame decoders, then the context generation in place on F
+        RUN(run_dc_trunk(ctx, p, yh, cin, p->dc_F, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
+        RUN(run_dc_frames(ctx, p, p->dc_F, d_frames, final_mode, s));
+        if (ctx->cur_cout) RUN(run_dc_context(ctx, p, p->dc_F, ctx->cur_cout, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
+        CK(cudaGetLastError());
+        return UFVC_OK;
+    }
     if (cin) RUN(run_chunk_feature(ctx, p, yh, cin, p->t_F_d, ctx->cur_cout, s));
     RUN(run_decoders(ctx, p, yh, d_frames, final_mode, s, cin ? (const void*)p->t_F_d : nullptr));
     CK(cudaGetLastError());
@@ -1211,7 +1415,7 @@ extern "C" size_t ufvc_temporal_weight_count(int arch, int chunk_len) { return t
 extern "C" ufvc_status ufvc_set_temporal_context(ufvc_ctx* ctx, const float* weights, size_t n_weights) {
     if (!ctx || !weights) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: bad argument");
     if (ctx->borrowed) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: context shares another's weights");
-    if (ctx->tc_on) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: already set");
+    if (ctx->tc_on) return fail(ctx, UFVC_ERR_ARG, "set_temporal_context: already set (the DC-block model has its own)");
     if (ctx->cfg.precision == UFVC_FP8)
         return fail(ctx, UFVC_ERR_UNSUPPORTED, "set_temporal_context: not available in FP8 contexts");
     if (n_weights != temporal_weight_count(ctx->cfg.arch, ctx->N))
@@ -1241,7 +1445,7 @@ extern "C" ufvc_status ufvc_set_temporal_context(ufvc_ctx* ctx, const float* wei
 extern "C" size_t ufvc_context_bytes(const ufvc_ctx* ctx, int width, int height) {
     if (!ctx || width < 1 || height < 1) return 0;
     const size_t es = ctx->cfg.precision == UFVC_FP32 ? 4 : 2;
-    return (size_t)((height + 15) / 16 * 2) * ((width + 15) / 16 * 2) * kCc * es;
+    return (size_t)((height + 15) / 16 * 2) * ((width + 15) / 16 * 2) * ctx->cc * es;
 }
 
 // runs fn with the call's context buffers installed (temporal-context contexts only)

@@ -1278,7 +1278,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
     a.cin_chunks = c32 ? 1 : d.Cin / 64;
     a.ksteps = d.k * d.k * a.cin_chunks;
-    if (a.ksteps > 64) return cudaErrorInvalidValue;
+    if (d.kmask && a.ksteps > 64) return cudaErrorInvalidValue;  // the skip mask has one bit per K step
     // steps skipped by kmask have all-zero weights, so a kernel that runs every step computes the same
     // result: only the staged BF16 N = 64 kernel (the space-to-depth first layer) reads the mask
     a.kmask = d.kmask ? d.kmask : ~0ull;

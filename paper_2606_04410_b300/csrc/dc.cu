@@ -1,0 +1,222 @@
+// DC-block model (Appendix: every module built from depth-wise convolution blocks, HT-S block counts):
+// the three elementwise / depth-wise kernels it needs besides the library's 1x1 and 3x3 convolutions.
+//
+//   pack_s2d8   frames -> patch-embedding input [H8][W8][3N 64]: channel (3n + c) 64 + 8 dy + dx holds
+//               frame n's channel c at pixel (8 h8 + dy, 8 w8 + dx) (replicate padding to multiples of 16);
+//   dw_conv     depth-wise 3x3 (zero padding 1) + bias + GELU (exact erf form), NHWC, grouped (each group
+//               its own filters), float or bf16 activations, float weights [g][9][C];
+//   ps8_out     the frame decoders' last 1x1 output o [N][H8][W8][192] -> x^ = clamp(0.5 + o, 0, 1) at
+//               pixel (8 h8 + dy, 8 w8 + dx), channel c = o[.][.][64 c + 8 dy + dx], cropped, as uint8
+//               rint(255 x^) or float.
+// All three are bandwidth-bound; each thread moves 8 channels (16 or 32 bytes) at a time.
+#include "ufvc_internal.h"
+
+#include <cuda_bf16.h>
+
+namespace ufvc {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void ld8(const T* p, float* v);
+template <>
+__device__ __forceinline__ void ld8<float>(const float* p, float* v) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void ld8<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[2 * j] = __uint_as_float(w[j] << 16);
+        v[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void st8(T* p, const float* v);
+template <>
+__device__ __forceinline__ void st8<float>(float* p, const float* v) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <>
+__device__ __forceinline__ void st8<__nv_bfloat16>(__nv_bfloat16* p, const float* v) {
+    uint4 u;
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+        w[j] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    u.x = w[0]; u.y = w[1]; u.z = w[2]; u.w = w[3];
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
+// the caller's frame formats (see the pack kernels of the plain model): frame n's three channels
+template <int FMT>
+__device__ __forceinline__ void px3(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W, float* v) {
+    uint32_t b[3];
+    if (FMT <= 1) {
+        const uint8_t* p = fr + ((size_t)n * H * W + (size_t)sh * W + sw) * 3;
+        b[0] = p[0]; b[1] = p[1]; b[2] = p[2];
+    } else if (FMT == 2) {
+        const size_t pl = (size_t)H * W;
+        const uint8_t* p = fr + (size_t)n * 3 * pl + (size_t)sh * W + sw;
+        b[0] = p[0]; b[1] = p[pl]; b[2] = p[2 * pl];
+    } else {
+        const int Wc = (W + 1) >> 1, Hc = (H + 1) >> 1;
+        const size_t pl = (size_t)H * W, cpl = (size_t)Hc * Wc;
+        const uint8_t* f = fr + (size_t)n * (pl + 2 * cpl);
+        const size_t ci = (size_t)(sh >> 1) * Wc + (sw >> 1);
+        b[0] = f[(size_t)sh * W + sw]; b[1] = f[pl + ci]; b[2] = f[pl + cpl + ci];
+    }
+    const float r = b[0] / 255.0f, g = b[1] / 255.0f, bl = b[2] / 255.0f;
+    if (FMT == 1) {  // BT.709 (full range, chroma centred at 0.5)
+        const float y = fmaf(0.0722f, bl, fmaf(0.7152f, g, 0.2126f * r));
+        v[0] = y;
+        v[1] = fmaf(bl - y, 1.0f / 1.8556f, 0.5f);
+        v[2] = fmaf(r - y, 1.0f / 1.5748f, 0.5f);
+    } else {
+        v[0] = r; v[1] = g; v[2] = bl;
+    }
+}
+
+// one thread per (position, frame n, sub-row dy): the 8 pixels of that sub-row, all three channels
+template <int FMT, typename T>
+__global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int H8, int W8,
+                                 T* __restrict__ x) {
+    pdl_trigger();
+    pdl_wait();
+    const int C0 = 3 * N * 64;
+    const long long total = (long long)H8 * W8 * N * 8;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int dy = (int)(t & 7);
+        long long r = t >> 3;
+        const int n = (int)(r % N);
+        r /= N;
+        const int pos = (int)r, h8 = pos / W8, w8 = pos - h8 * W8;
+        const int h = 8 * h8 + dy, sh = h < H ? h : H - 1;
+        float v[3][8];
+#pragma unroll
+        for (int dx = 0; dx < 8; ++dx) {
+            const int w = 8 * w8 + dx, sw = w < W ? w : W - 1;
+            float p[3];
+            px3<FMT>(frames, n, sh, sw, H, W, p);
+            v[0][dx] = p[0]; v[1][dx] = p[1]; v[2][dx] = p[2];
+        }
+        T* o = x + (size_t)pos * C0 + (size_t)(3 * n) * 64 + 8 * dy;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st8<T>(o + c * 64, v[c]);
+    }
+}
+
+__device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+// one thread per (group, pixel, run of 8 channels)
+template <typename T>
+__global__ void dw_conv_kernel(const T* __restrict__ x, int G, int H, int W, int C, long long gs,
+                               const float* __restrict__ w, const float* __restrict__ b, T* __restrict__ out) {
+    pdl_trigger();
+    pdl_wait();
+    const int c8 = C >> 3;
+    const long long total = (long long)G * H * W * c8;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int cr = (int)(t % c8);
+        long long r = t / c8;
+        const int pix = (int)(r % ((long long)H * W));
+        const int g = (int)(r / ((long long)H * W));
+        const int h = pix / W, ww = pix - h * W, c0 = 8 * cr;
+        const T* xg = x + g * gs;
+        const float* wg = w + (size_t)g * 9 * C;
+        float acc[8];
+        ld8<float>(b + (size_t)g * C + c0, acc);
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+            const int ih = h + ky - 1;
+            if (ih < 0 || ih >= H) continue;
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const int iw = ww + kx - 1;
+                if (iw < 0 || iw >= W) continue;
+                float v[8], k[8];
+                ld8<T>(xg + ((size_t)ih * W + iw) * C + c0, v);
+                ld8<float>(wg + (size_t)(3 * ky + kx) * C + c0, k);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[j] = fmaf(k[j], v[j], acc[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = gelu_erf(acc[j]);
+        st8<T>(out + g * gs + (size_t)pix * C + c0, acc);
+    }
+}
+
+// one thread per output pixel (n, y, x)
+template <bool U8>
+__global__ void ps8_out_kernel(const float* __restrict__ o, int N, int H8, int W8, int H, int W,
+                               void* __restrict__ frames) {
+    pdl_trigger();
+    pdl_wait();
+    const long long total = (long long)N * H * W;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % W);
+        long long r = t / W;
+        const int y = (int)(r % H);
+        const int n = (int)(r / H);
+        const float* src = o + (((size_t)n * H8 + (y >> 3)) * W8 + (x >> 3)) * 192 + 8 * (y & 7) + (x & 7);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float v = fminf(fmaxf(0.5f + src[64 * c], 0.0f), 1.0f);
+            if (U8) static_cast<uint8_t*>(frames)[3 * t + c] = (uint8_t)rintf(255.0f * v);
+            else static_cast<float*>(frames)[3 * t + c] = v;
+        }
+    }
+}
+
+unsigned grid_of(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 148 * 16) g = 148 * 16;
+    return (unsigned)(g ? g : 1);
+}
+
+}  // namespace
+
+void launch_pack_s2d8(const uint8_t* frames, int N, int H, int W, int H8, int W8, void* x, bool f32, int fmt,
+                      cudaStream_t s) {
+    const dim3 g(grid_of((long long)H8 * W8 * N * 8));
+#define PACK8(F)                                                                                              \
+    (f32 ? launch_pdl(pack_s2d8_kernel<F, float>, g, dim3(256), 0, s, frames, N, H, W, H8, W8, (float*)x)     \
+         : launch_pdl(pack_s2d8_kernel<F, __nv_bfloat16>, g, dim3(256), 0, s, frames, N, H, W, H8, W8,          \
+                      (__nv_bfloat16*)x))
+    switch (fmt) {
+        case 1: (void)PACK8(1); break;
+        case 2: (void)PACK8(2); break;
+        case 3: (void)PACK8(3); break;
+        default: (void)PACK8(0); break;
+    }
+#undef PACK8
+}
+
+void launch_dw_conv(const void* x, int G, int H, int W, int C, long long gs, const float* w, const float* b, void* out,
+                    bool f32, cudaStream_t s) {
+    const dim3 g(grid_of((long long)G * H * W * (C >> 3)));
+    if (f32)
+        (void)launch_pdl(dw_conv_kernel<float>, g, dim3(256), 0, s, (const float*)x, G, H, W, C, gs, w, b, (float*)out);
+    else
+        (void)launch_pdl(dw_conv_kernel<__nv_bfloat16>, g, dim3(256), 0, s, (const __nv_bfloat16*)x, G, H, W, C, gs, w,
+                         b, (__nv_bfloat16*)out);
+}
+
+void launch_ps8_out(const float* o, int N, int H8, int W8, int H, int W, void* frames, bool u8, cudaStream_t s) {
+    const dim3 g(grid_of((long long)N * H * W));
+    if (u8) (void)launch_pdl(ps8_out_kernel<true>, g, dim3(256), 0, s, o, N, H8, W8, H, W, frames);
+    else (void)launch_pdl(ps8_out_kernel<false>, g, dim3(256), 0, s, o, N, H8, W8, H, W, frames);
+}
+
+}  // namespace ufvc

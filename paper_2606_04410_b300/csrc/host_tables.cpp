@@ -89,10 +89,44 @@ void build_host_tables(HostTables& t) {
 bool get_arch(int arch, Arch* a) {
     if (arch == 0) { *a = Arch{64, 96, 128, 128, 64, 128, 64}; return true; }
     if (arch == 1) { *a = Arch{64, 128, 192, 256, 128, 128, 64}; return true; }
+    if (arch == 2) { *a = Arch{0, 0, 0, kDcCy, kDcCz, 0, 0}; return true; }  // DC-block model
     return false;
 }
 
+// DC-block model (arch 2): blob layer l -> (cout, k, cin); depth-wise layers have cin = 1.  Shared layers:
+// PE, EC, 6 encoder blocks, ED, H1, H2, S1, S2, S3, PC, DU, FC, 7 decoder blocks, 11 context blocks, GO;
+// then per frame FP, 3 blocks at the frame width, FO.  A block is PWa, DW, PWb, PWc, PWd.
+static void dc_block_shape(int c, int j, int* co, int* k, int* ci) {
+    const int t[5][3] = {{c, 1, c}, {c, 3, 1}, {c, 1, c}, {2 * c, 1, c}, {c, 1, 2 * c}};
+    *co = t[j][0]; *k = t[j][1]; *ci = t[j][2];
+}
+
+bool dc_layer_shape(int N, int l, int* cout, int* k, int* cin) {
+    if (N < 1 || l < 0 || l >= kDcShared + kDcPerFrame * N) return false;
+    if (l >= kDcShared) {
+        const int j = (l - kDcShared) % kDcPerFrame;
+        if (j == 0) { *cout = kDcCf; *k = 1; *cin = kDcC; }
+        else if (j == kDcPerFrame - 1) { *cout = 192; *k = 1; *cin = kDcCf; }
+        else dc_block_shape(kDcCf, (j - 1) % 5, cout, k, cin);
+        return true;
+    }
+    if (l == DC_PE) { *cout = kDcC; *k = 1; *cin = 3 * N * 64; }
+    else if (l == DC_EC || l == DC_FC) { *cout = kDcC; *k = 1; *cin = kDcCc; }
+    else if (l < DC_ED) dc_block_shape(kDcC, (l - DC_E0) % 5, cout, k, cin);
+    else if (l == DC_ED) { *cout = kDcCy; *k = 3; *cin = kDcC; }
+    else if (l == DC_H1) { *cout = kDcCz; *k = 3; *cin = kDcCy; }
+    else if (l == DC_H2) { *cout = kDcCz; *k = 3; *cin = kDcCz; }
+    else if (l == DC_S1 || l == DC_S2) { *cout = 4 * kDcCz; *k = 3; *cin = kDcCz; }
+    else if (l == DC_S3) { *cout = 2 * kDcCy; *k = 1; *cin = kDcCz; }
+    else if (l == DC_PC) { *cout = kDcCz; *k = 3; *cin = kDcCc; }
+    else if (l == DC_DU) { *cout = 4 * kDcC; *k = 1; *cin = kDcCy; }
+    else if (l < DC_GO) dc_block_shape(kDcC, (l - DC_D0) % 5, cout, k, cin);
+    else { *cout = kDcCc; *k = 1; *cin = kDcC; }
+    return true;
+}
+
 bool layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
+    if (arch == 2) return dc_layer_shape(N, l, cout, k, cin);
     Arch a;
     if (!get_arch(arch, &a) || N < 1 || l < 0 || l >= L_NENC + D_NDEC * N) return false;
     if (l < L_NENC) {
@@ -114,6 +148,13 @@ bool layer_shape(int arch, int N, int l, int* cout, int* k, int* cin) {
 size_t weight_count(int arch, int N) {
     size_t n = 0;
     int co, k, ci;
+    if (arch == 2) {
+        for (int l = 0; l < kDcShared + kDcPerFrame * N; ++l) {
+            if (!dc_layer_shape(N, l, &co, &k, &ci)) return 0;
+            n += (size_t)co * k * k * ci + co;
+        }
+        return n;
+    }
     for (int l = 0; l < L_NENC + D_NDEC * N; ++l) {
         if (!layer_shape(arch, N, l, &co, &k, &ci)) return 0;
         n += (size_t)co * k * k * ci + co;

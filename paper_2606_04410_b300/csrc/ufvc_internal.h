@@ -75,6 +75,21 @@ size_t weight_count(int arch, int N);
 bool mean_layer_shape(int arch, int l, int* cout, int* k, int* cin);
 size_t mean_weight_count(int arch);
 constexpr int kMeanLayers = 6;
+// DC-block model (arch 2): widths and the blob indices of its shared layers (encoder blocks from DC_E0,
+// decoder blocks from DC_D0, context blocks from DC_G0, five layers each); frame layers from kDcShared,
+// kDcPerFrame per frame position (FP, 3 blocks, FO)
+constexpr int kDcC = 512, kDcCf = 256, kDcCc = 128, kDcCy = 256, kDcCz = 128;
+enum DcLayer { DC_PE = 0, DC_EC = 1, DC_E0 = 2, DC_ED = 32, DC_H1 = 33, DC_H2, DC_S1, DC_S2, DC_S3, DC_PC, DC_DU,
+               DC_FC, DC_D0 = 41, DC_G0 = 76, DC_GO = 131 };
+constexpr int kDcShared = 132, kDcPerFrame = 17;
+bool dc_layer_shape(int N, int l, int* cout, int* k, int* cin);
+// DC-block kernels (dc.cu): patch-embedding pack, depth-wise 3x3 + GELU (weights [g][9][C] float), x8 output
+void launch_pack_s2d8(const uint8_t* frames, int N, int H, int W, int H8, int W8, void* x, bool f32, int fmt,
+                      cudaStream_t s);
+void launch_dw_conv(const void* x, int G, int H, int W, int C, long long gs, const float* w, const float* b, void* out,
+                    bool f32, cudaStream_t s);
+void launch_ps8_out(const float* o, int N, int H8, int W8, int H, int W, void* frames, bool u8, cudaStream_t s);
+
 // temporal chunk context: feature and context channels, and the shared layers (then DF per frame)
 constexpr int kCf = 64, kCc = 64;
 enum TemporalLayer { TL_EC = 0, TL_FD, TL_FC, TL_CG, TL_PC, TL_N };

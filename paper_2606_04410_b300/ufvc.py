@@ -199,10 +199,12 @@ class Codec:
         return int(lib.ufvc_context_bytes(self.h, width, height))
 
     def new_context(self, width: int, height: int, device=None) -> torch.Tensor:
-        """A context buffer [2 ceil(H/16)][2 ceil(W/16)][64] (bf16, or float32 in FP32 contexts)."""
+        """A context buffer [2 ceil(H/16)][2 ceil(W/16)][Cc] (Cc = 64, 128 for the DC-block model; bf16, or
+        float32 in FP32 contexts)."""
         dt = torch.float32 if self.precision == "fp32" else torch.bfloat16
-        return torch.empty((2 * (-(-height // 16)), 2 * (-(-width // 16)), 64), dtype=dt,
-                           device=device or torch.device(f"cuda:{self.device}"))
+        h8, w8 = 2 * (-(-height // 16)), 2 * (-(-width // 16))
+        cc = self.context_bytes(width, height) // (h8 * w8 * (4 if self.precision == "fp32" else 2))
+        return torch.empty((h8, w8, cc), dtype=dt, device=device or torch.device(f"cuda:{self.device}"))
 
     def encode_chunk_tc(self, frames: torch.Tensor, ctx_in, ctx_out, qp: int = 32, bits=None, nbytes=None,
                         stream=None, width=None, height=None):
