@@ -76,22 +76,6 @@ __device__ __forceinline__ const float* stage_bias(const TcArgs& p, float* sbias
     return sbias;  // visible after the block barrier that follows the set-up
 }
 
-// GELU x * Phi(x) with the normal CDF written as a logistic of an odd polynomial:
-// Phi(x) ~= 1 / (1 + exp(-x P(min(x^2, 100)))), P(t) = 1.59501577 + 7.40112920e-2 t - 7.03033577e-4 t^2.
-// P was fitted for this kernel by minimising max |x (Phi(x) - approximation)| over [-14, 14]: the GELU
-// error is below 2.6e-5 everywhere (P > 0 on the clamped range, so the logistic saturates the right way
-// for large |x|), against the 2^-9 relative rounding of the bf16 activation it feeds.  Cost: six FP32
-// operations and two MUFU operations (ex2, rcp) with -log2(e) folded into the coefficients.
-__device__ __forceinline__ float gelu_tc(float x) {
-    const float t = fminf(x * x, 100.0f);
-    float p = fmaf(t, 7.03033577e-4f * 1.44269504088896341f, -7.40112920e-2f * 1.44269504088896341f);
-    p = fmaf(p, t, -1.59501577f * 1.44269504088896341f);
-    float e, r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(p * x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
-    return x * r;
-}
-
 // The same GELU for two values at once, the logistic taken as 0.5 + 0.5 tanh(z / 2) and z / 2 =
 // x P(t) / 2 evaluated in packed half precision with one tanh.approx.f16x2 for both values; the final
 // product x (0.5 + 0.5 tanh) is FP32.  Half precision adds about 1e-3 absolute to the logistic, so the

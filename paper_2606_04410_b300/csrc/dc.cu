@@ -3,8 +3,9 @@
 //
 //   pack_s2d8   frames -> patch-embedding input [H8][W8][3N 64]: channel (3n + c) 64 + 8 dy + dx holds
 //               frame n's channel c at pixel (8 h8 + dy, 8 w8 + dx) (replicate padding to multiples of 16);
-//   dw_conv     depth-wise 3x3 (zero padding 1) + bias + GELU (exact erf form), NHWC, grouped (each group
-//               its own filters), float or bf16 activations, float weights [g][9][C];
+//   dw_conv     depth-wise 3x3 (zero padding 1) + bias + GELU, NHWC, grouped (each group its own filters),
+//               float activations (exact erf GELU) or bf16 (the tensor-core epilogues' GELU), float weights
+//               [g][9][C];
 //   ps8_out     the frame decoders' last 1x1 output o [N][H8][W8][192] -> x^ = clamp(0.5 + o, 0, 1) at
 //               pixel (8 h8 + dy, 8 w8 + dx), channel c = o[.][.][64 c + 8 dy + dx], cropped, as uint8
 //               rint(255 x^) or float.
@@ -84,31 +85,31 @@ __device__ __forceinline__ void px3(const uint8_t* __restrict__ fr, int n, int s
     }
 }
 
-// one thread per (position, frame n, sub-row dy): the 8 pixels of that sub-row, all three channels
+// one thread per (super-row h8, frame n, sub-row dy, position w8), w8 fastest: a warp reads 32 consecutive
+// 8-pixel runs of one frame row; each thread writes its three 8-channel runs
 template <int FMT, typename T>
 __global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int H8, int W8,
                                  T* __restrict__ x) {
     pdl_trigger();
     pdl_wait();
     const int C0 = 3 * N * 64;
-    const long long total = (long long)H8 * W8 * N * 8;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int dy = (int)(t & 7);
-        long long r = t >> 3;
-        const int n = (int)(r % N);
-        r /= N;
-        const int pos = (int)r, h8 = pos / W8, w8 = pos - h8 * W8;
+    const unsigned total = (unsigned)H8 * W8 * N * 8;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const unsigned w8 = t % W8;
+        unsigned r = t / W8;
+        const int dy = (int)(r & 7);
+        r >>= 3;
+        const int n = (int)(r % N), h8 = (int)(r / N);
         const int h = 8 * h8 + dy, sh = h < H ? h : H - 1;
         float v[3][8];
 #pragma unroll
         for (int dx = 0; dx < 8; ++dx) {
-            const int w = 8 * w8 + dx, sw = w < W ? w : W - 1;
+            const int w = 8 * (int)w8 + dx, sw = w < W ? w : W - 1;
             float p[3];
             px3<FMT>(frames, n, sh, sw, H, W, p);
             v[0][dx] = p[0]; v[1][dx] = p[1]; v[2][dx] = p[2];
         }
-        T* o = x + (size_t)pos * C0 + (size_t)(3 * n) * 64 + 8 * dy;
+        T* o = x + ((size_t)h8 * W8 + w8) * C0 + (size_t)(3 * n) * 64 + 8 * dy;
 #pragma unroll
         for (int c = 0; c < 3; ++c) st8<T>(o + c * 64, v[c]);
     }
@@ -116,43 +117,65 @@ __global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int 
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// one thread per (group, pixel, run of 8 channels)
+// one thread per (group, row, strip of kDwPix output pixels, run of 8 channels), channel run fastest: a warp
+// reads 32 consecutive runs (512 bytes of bf16) per load; the strip's 3 x (kDwPix + 2) input runs and the
+// run's nine filter taps are loaded once for its kDwPix outputs
+constexpr int kDwPix = 4;
+
 template <typename T>
 __global__ void dw_conv_kernel(const T* __restrict__ x, int G, int H, int W, int C, long long gs,
                                const float* __restrict__ w, const float* __restrict__ b, T* __restrict__ out) {
     pdl_trigger();
     pdl_wait();
-    const int c8 = C >> 3;
-    const long long total = (long long)G * H * W * c8;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
+    const int c8 = C >> 3, ws = (W + kDwPix - 1) / kDwPix;
+    const unsigned total = (unsigned)G * H * ws * c8;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int cr = (int)(t % c8);
-        long long r = t / c8;
-        const int pix = (int)(r % ((long long)H * W));
-        const int g = (int)(r / ((long long)H * W));
-        const int h = pix / W, ww = pix - h * W, c0 = 8 * cr;
+        unsigned r = t / c8;
+        const int s0 = (int)(r % ws) * kDwPix;
+        r /= ws;
+        const int h = (int)(r % H), g = (int)(r / H);
+        const int c0 = 8 * cr;
         const T* xg = x + g * gs;
-        const float* wg = w + (size_t)g * 9 * C;
-        float acc[8];
-        ld8<float>(b + (size_t)g * C + c0, acc);
+        const float* wg = w + (size_t)g * 9 * C + c0;
+        float k[9][8], acc[kDwPix][8], bias[8];
+#pragma unroll
+        for (int tp = 0; tp < 9; ++tp) ld8<float>(wg + (size_t)tp * C, k[tp]);
+        ld8<float>(b + (size_t)g * C + c0, bias);
+#pragma unroll
+        for (int q = 0; q < kDwPix; ++q)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[q][j] = bias[j];
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
             const int ih = h + ky - 1;
             if (ih < 0 || ih >= H) continue;
+            const T* row = xg + (size_t)ih * W * C + c0;
 #pragma unroll
-            for (int kx = 0; kx < 3; ++kx) {
-                const int iw = ww + kx - 1;
+            for (int u = 0; u < kDwPix + 2; ++u) {  // input column s0 - 1 + u
+                const int iw = s0 - 1 + u;
                 if (iw < 0 || iw >= W) continue;
-                float v[8], k[8];
-                ld8<T>(xg + ((size_t)ih * W + iw) * C + c0, v);
-                ld8<float>(wg + (size_t)(3 * ky + kx) * C + c0, k);
+                float v[8];
+                ld8<T>(row + (size_t)iw * C, v);
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[j] = fmaf(k[j], v[j], acc[j]);
+                for (int q = 0; q < kDwPix; ++q) {  // output column s0 + q uses tap kx = u - q
+                    const int kx = u - q;
+                    if (kx < 0 || kx > 2) continue;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[q][j] = fmaf(k[3 * ky + kx][j], v[j], acc[q][j]);
+                }
             }
         }
+        T* o = out + g * gs + ((size_t)h * W + s0) * C + c0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = gelu_erf(acc[j]);
-        st8<T>(out + g * gs + (size_t)pix * C + c0, acc);
+        for (int q = 0; q < kDwPix; ++q) {
+            if (s0 + q >= W) break;
+            // bf16 activations: the tensor-core epilogues' GELU (|error| < 2.6e-5, far below the bf16 rounding
+            // of the result); float activations: the exact erf form
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[q][j] = sizeof(T) == 2 ? gelu_tc(acc[q][j]) : gelu_erf(acc[q][j]);
+            st8<T>(o + (size_t)q * C, acc[q]);
+        }
     }
 }
 
@@ -205,7 +228,7 @@ void launch_pack_s2d8(const uint8_t* frames, int N, int H, int W, int H8, int W8
 
 void launch_dw_conv(const void* x, int G, int H, int W, int C, long long gs, const float* w, const float* b, void* out,
                     bool f32, cudaStream_t s) {
-    const dim3 g(grid_of((long long)G * H * W * (C >> 3)));
+    const dim3 g(grid_of((long long)G * H * ((W + kDwPix - 1) / kDwPix) * (C >> 3)));
     if (f32)
         (void)launch_pdl(dw_conv_kernel<float>, g, dim3(256), 0, s, (const float*)x, G, H, W, C, gs, w, b, (float*)out);
     else
