@@ -117,56 +117,75 @@ __global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int 
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
-// one thread per (group, row, strip of kDwPix output pixels, run of 8 channels), channel run fastest: a warp
-// reads 32 consecutive runs (512 bytes of bf16) per load; the strip's 3 x (kDwPix + 2) input runs and the
-// run's nine filter taps are loaded once for its kDwPix outputs
+// one thread per (row, strip of kDwPix output pixels, run of 8 channels) of group blockIdx.y, channel run
+// fastest: a warp reads 32 consecutive runs (512 bytes of bf16) per load; the strip's 3 x (kDwPix + 2) input
+// runs are loaded once for its kDwPix outputs; the group's 9 x C filter taps and C biases are staged in
+// shared memory once per block (C <= kDwMaxC)
 constexpr int kDwPix = 4;
+constexpr int kDwMaxC = 512;
 
 template <typename T>
-__global__ void dw_conv_kernel(const T* __restrict__ x, int G, int H, int W, int C, long long gs,
-                               const float* __restrict__ w, const float* __restrict__ b, T* __restrict__ out) {
+__global__ void __launch_bounds__(256, 2) dw_conv_kernel(const T* __restrict__ x, int H, int W, int C, long long gs,
+                                                      const float* __restrict__ w, const float* __restrict__ b,
+                                                      T* __restrict__ out) {
+    __shared__ __align__(16) float sw[10 * kDwMaxC];  // 9 taps x C, then the biases
+    const int g = blockIdx.y;
+    for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) sw[i] = w[(size_t)g * 9 * C + i];
+    for (int i = threadIdx.x; i < C; i += blockDim.x) sw[9 * C + i] = b[(size_t)g * C + i];
+    __syncthreads();
     pdl_trigger();
     pdl_wait();
     const int c8 = C >> 3, ws = (W + kDwPix - 1) / kDwPix;
-    const unsigned total = (unsigned)G * H * ws * c8;
+    const unsigned total = (unsigned)H * ws * c8;
+    const T* xg = x + g * gs;
+    T* og = out + g * gs;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int cr = (int)(t % c8);
-        unsigned r = t / c8;
-        const int s0 = (int)(r % ws) * kDwPix;
-        r /= ws;
-        const int h = (int)(r % H), g = (int)(r / H);
+        const unsigned r = t / c8;
+        const int s0 = (int)(r % ws) * kDwPix, h = (int)(r / ws);
         const int c0 = 8 * cr;
-        const T* xg = x + g * gs;
-        const float* wg = w + (size_t)g * 9 * C + c0;
-        float k[9][8], acc[kDwPix][8], bias[8];
-#pragma unroll
-        for (int tp = 0; tp < 9; ++tp) ld8<float>(wg + (size_t)tp * C, k[tp]);
-        ld8<float>(b + (size_t)g * C + c0, bias);
+        float acc[kDwPix][8], bias[8];
+        ld8<float>(sw + 9 * C + c0, bias);
 #pragma unroll
         for (int q = 0; q < kDwPix; ++q)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[q][j] = bias[j];
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky) {
+            // the row's kDwPix + 2 input runs are all loaded before any arithmetic (clamped addresses, zeroed
+            // outside the image), so their latencies overlap instead of forming load -> use chains
             const int ih = h + ky - 1;
-            if (ih < 0 || ih >= H) continue;
-            const T* row = xg + (size_t)ih * W * C + c0;
+            const bool rv = ih >= 0 && ih < H;
+            const T* row = xg + (size_t)(ih < 0 ? 0 : (ih >= H ? H - 1 : ih)) * W * C + c0;
+            uint4 raw[kDwPix + 2][sizeof(T) / 2];  // 8 channels: one 16-byte vector (bf16) or two (float)
+            bool cv[kDwPix + 2];
 #pragma unroll
             for (int u = 0; u < kDwPix + 2; ++u) {  // input column s0 - 1 + u
                 const int iw = s0 - 1 + u;
-                if (iw < 0 || iw >= W) continue;
+                cv[u] = rv && iw >= 0 && iw < W;
+                const uint4* src = reinterpret_cast<const uint4*>(row + (size_t)(iw < 0 ? 0 : (iw >= W ? W - 1 : iw)) * C);
+#pragma unroll
+                for (int e = 0; e < (int)(sizeof(T) / 2); ++e) raw[u][e] = src[e];
+            }
+            float k[3][8];  // this kernel row's three taps, read from shared memory once per row
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) ld8<float>(sw + (3 * ky + kx) * C + c0, k[kx]);
+#pragma unroll
+            for (int u = 0; u < kDwPix + 2; ++u) {
                 float v[8];
-                ld8<T>(row + (size_t)iw * C, v);
+                ld8<T>(reinterpret_cast<const T*>(raw[u]), v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = cv[u] ? v[j] : 0.0f;
 #pragma unroll
                 for (int q = 0; q < kDwPix; ++q) {  // output column s0 + q uses tap kx = u - q
                     const int kx = u - q;
                     if (kx < 0 || kx > 2) continue;
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[q][j] = fmaf(k[3 * ky + kx][j], v[j], acc[q][j]);
+                    for (int j = 0; j < 8; ++j) acc[q][j] = fmaf(k[kx][j], v[j], acc[q][j]);
                 }
             }
         }
-        T* o = out + g * gs + ((size_t)h * W + s0) * C + c0;
+        T* o = og + ((size_t)h * W + s0) * C + c0;
 #pragma unroll
         for (int q = 0; q < kDwPix; ++q) {
             if (s0 + q >= W) break;
@@ -226,14 +245,20 @@ void launch_pack_s2d8(const uint8_t* frames, int N, int H, int W, int H8, int W8
 #undef PACK8
 }
 
+// C <= kDwMaxC, a multiple of 8; blocks spread over the groups (gridDim.y = G) so each stages one group's taps
 void launch_dw_conv(const void* x, int G, int H, int W, int C, long long gs, const float* w, const float* b, void* out,
                     bool f32, cudaStream_t s) {
-    const dim3 g(grid_of((long long)G * H * ((W + kDwPix - 1) / kDwPix) * (C >> 3)));
+    if (C > kDwMaxC || (C & 7) || G < 1) return;
+    long long per = (long long)H * ((W + kDwPix - 1) / kDwPix) * (C >> 3);
+    unsigned gx = grid_of(per);
+    const unsigned cap = (148u * 16u + G - 1) / G;  // about sixteen blocks per SM in all
+    if (gx > cap) gx = cap ? cap : 1;
+    const dim3 g(gx, (unsigned)G);
     if (f32)
-        (void)launch_pdl(dw_conv_kernel<float>, g, dim3(256), 0, s, (const float*)x, G, H, W, C, gs, w, b, (float*)out);
+        (void)launch_pdl(dw_conv_kernel<float>, g, dim3(256), 0, s, (const float*)x, H, W, C, gs, w, b, (float*)out);
     else
-        (void)launch_pdl(dw_conv_kernel<__nv_bfloat16>, g, dim3(256), 0, s, (const __nv_bfloat16*)x, G, H, W, C, gs, w,
-                         b, (__nv_bfloat16*)out);
+        (void)launch_pdl(dw_conv_kernel<__nv_bfloat16>, g, dim3(256), 0, s, (const __nv_bfloat16*)x, H, W, C, gs, w, b,
+                         (__nv_bfloat16*)out);
 }
 
 void launch_ps8_out(const float* o, int N, int H8, int W8, int H, int W, void* frames, bool u8, cudaStream_t s) {
