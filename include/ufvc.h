@@ -56,17 +56,21 @@ typedef enum {
     UFVC_FP32 = 0,  /* every convolution in FP32 on CUDA cores (deterministic) */
     UFVC_BF16 = 1,  /* analysis, hyper-analysis and decoder convolutions: BF16 operands on tcgen05
                        tensor cores, FP32 accumulation in TMEM; the entropy-parameter path (hyper-
-                       synthesis) stays deterministic FP32.  arch 1 only (all activation widths
+                       synthesis) stays deterministic FP32.  arch 1 and 2 (all activation widths
                        multiples of 64); arch 0 gives UFVC_ERR_UNSUPPORTED */
     UFVC_FP8 = 2    /* as BF16 but the tensor-core layers (all except the final frame layer, which
                        stays BF16) take E4M3 operands: weights with one scale per output channel
                        (absmax / 448), activations with one scale per tensor from
-                       ufvc_calibrate_fp8; FP32 accumulation.  Needs calibration before use */
+                       ufvc_calibrate_fp8; FP32 accumulation.  Needs calibration before use.
+                       arch 1 only */
 } ufvc_precision;
 
 typedef struct {
     int arch;        /* 0: tiny widths (analysis 64/96/128, Cy=128, Cz=64);
-                        1: 1080p-family widths (analysis 64/128/192, Cy=256, Cz=128) */
+                        1: 1080p-family widths (analysis 64/128/192, Cy=256, Cz=128);
+                        2: the DC-block model at the paper's HT-S block counts (Appendix): every
+                           module built from depth-wise convolution blocks, Cy=256, Cz=128, with the
+                           temporal chunk context built in (see "DC-block model" below) */
     int chunk_len;   /* N, frames per chunk (1..16); N frame-specific decoders */
     int lanes;       /* K, interleaved rANS lanes of the latent section (1..65536) */
     int precision;   /* ufvc_precision */
@@ -81,7 +85,20 @@ size_t ufvc_weight_count(int arch, int chunk_len);
  * host in FP64 and uploads them.  `weights` is a host float32 blob: for each layer in the order
  *   A1 A2 A3 Xa Xb A4 H1 H2 S1 S2 S3, then for f = 0..N-1: D0 R1a R1b U1 R2a R2b U2 U3,
  * the kernel [Cout][k][k][Cin] followed by the bias [Cout] (shapes: see ufvc_layer_shape).
- * Returns UFVC_ERR_ARG if n_weights != ufvc_weight_count(arch, chunk_len). */
+ * Returns UFVC_ERR_ARG if n_weights != ufvc_weight_count(arch, chunk_len).
+ *
+ * DC-block model (arch 2).  A DC block of width C is y = x + PWb(GELU(DW(PWa(x)))), then
+ * y + PWd(GELU(PWc(y))) with PWa, PWb 1x1 C -> C, DW a 3x3 depth-wise layer (one filter per channel,
+ * stored as kernel [C][3][3][1]), PWc 1x1 C -> 2C, PWd 1x1 2C -> C (a reading of the paper's block
+ * figure).  At 1/8 of the padded frame size: patch embedding PE (1x1 over the 8x8 space-to-depth of the
+ * N stacked frames, channel (3n + c) 64 + 8 dy + dx), EC(C_i), 6 blocks at 512, ED (3x3 stride 2) -> y;
+ * the plain hyperprior with PC(C_i) added before S3; chunk decoder GELU(PS(DU(y^))) + FC(C_i), 7 blocks
+ * -> F; context generation: 11 blocks on F, GO (1x1) -> C_{i+1} (128 channels); frame decoder f: FP_f
+ * (1x1 512 -> 256), 3 blocks at 256, FO_f (1x1 -> 192), pixel shuffle x8, x^ = clamp(0.5 + o, 0, 1).
+ * Blob order: PE, EC, 6 x [PWa DW PWb PWc PWd], ED, H1, H2, S1, S2, S3, PC, DU, FC, 7 x [...],
+ * 11 x [...], GO, then per frame FP, 3 x [...], FO.  The context is always carried: the plain chunk
+ * calls code a stream's first chunk, the _tc calls carry C_i (ufvc_context_bytes: 128 channels).
+ * BF16 and FP32 only. */
 ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights, size_t n_weights, ufvc_ctx** out);
 void ufvc_destroy(ufvc_ctx* ctx);
 

@@ -1735,6 +1735,7 @@ extern "C" ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, i
 // ------------------------------------------------------------------------------------------------
 namespace ufvc {
 const uint32_t* ctx_packed_tables(const ufvc_ctx* c) { return c->d_packed; }
+bool ctx_temporal(const ufvc_ctx* c) { return c->tc_on; }
 int* ctx_status_word(ufvc_ctx* c) { return c->d_status; }
 int ctx_device(const ufvc_ctx* c) { return c->cfg.device; }
 void ctx_set_error(ufvc_ctx* c, const char* msg) { c->err = msg; }

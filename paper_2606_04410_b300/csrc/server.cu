@@ -13,7 +13,8 @@
 // Every slot computes with the same kernels as a single context, and none of them depends on what
 // runs beside it, so a request's bit-stream and frames are the same alone and in a mix.
 //
-// With the temporal chunk context (ufvc_server_set_temporal_context) each stream also owns its coding
+// With the temporal chunk context (ufvc_server_set_temporal_context, or the DC-block model, which always
+// has it) each stream also owns its coding
 // state on the device: the encoder's and the decoder's context C_i.  A request copies the stream's
 // context into the slot's input buffer (zeros for the stream's first chunk, which equals C_0 = 0),
 // runs, and copies the slot's output context back, so the slot's graphs keep fixed pointers and a
@@ -389,6 +390,7 @@ extern "C" ufvc_status ufvc_server_create(const ufvc_config* cfg, const float* w
         delete S;
         return st;
     }
+    S->temporal = ctx_temporal(S->base);  // the DC-block model carries its context from the start
     S->worker = std::thread(worker_main, S);
     *out = S;
     return UFVC_OK;

@@ -204,3 +204,45 @@ def test_server_streams_carry_temporal_context():
             assert torch.equal(b["frames_out"].cpu(), refs[i][r][1]), (i, r)
     assert srv.stats()["graphs"] >= 2
     srv.close()
+
+
+def test_server_dc_model_streams_carry_context():
+    """A server on the DC-block model (whose temporal context is built in) keeps every stream's context
+    chain on the device: bit-streams and frames equal a single context coding the same chunks in order."""
+    u = U()
+    n = 2
+    blob = synthetic.draw_dc_weights(n, seed=5)
+    sizes = [(64, 64), (96, 64)]
+    rounds = 3
+    chunks = {i: [torch.from_numpy(synthetic.moving_texture(120 + 10 * i + r, n, H, W, max_step=3, period=64)).cuda()
+                  for r in range(rounds)] for i, (W, H) in enumerate(sizes)}
+    refs = {}
+    for i, (W, H) in enumerate(sizes):
+        c = u.Codec(2, n, 64, blob, "bf16")
+        ce = [c.new_context(W, H), c.new_context(W, H)]
+        cd = [c.new_context(W, H), c.new_context(W, H)]
+        out = []
+        for r in range(rounds):
+            bits, nb = c.encode_chunk_tc(chunks[i][r], ce[r % 2] if r else None, ce[(r + 1) % 2], QP)
+            m = int(nb.item())
+            fr = c.decode_chunk_tc(bits, m, W, H, cd[r % 2] if r else None, cd[(r + 1) % 2])
+            assert c.sync_status() == 0
+            out.append((bits[:m].cpu().numpy().tobytes(), fr.cpu().clone()))
+        refs[i] = out
+        c.close()
+    srv = u.Server(2, n, 64, blob, "bf16", max_slots=2)
+    sids = {i: srv.open_stream(W, H, QP) for i, (W, H) in enumerate(sizes)}
+    for r in range(rounds):
+        for i in sids:
+            srv.streams[sids[i]]["frames_in"].copy_(chunks[i][r])
+        torch.cuda.synchronize()
+        tickets = [(i, srv.submit(sids[i], op)) for i in sids for op in (u.UFVC_OP_ENCODE, u.UFVC_OP_DECODE)]
+        for i, t in tickets:
+            assert srv.wait(t, 120000.0)["status"] == 0
+        for i in sids:
+            b = srv.streams[sids[i]]
+            raw = b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes()
+            assert raw[4] == 3 and raw[5] == 2
+            assert raw == refs[i][r][0], (i, r)
+            assert torch.equal(b["frames_out"].cpu(), refs[i][r][1]), (i, r)
+    srv.close()
