@@ -681,9 +681,9 @@ static ufvc_status upload_a1_s2d(ufvc_ctx* ctx, const float* src) {
                     for (int dx = 0; dx < 2; ++dx) {
                         const int ky = 2 * sy + dy - 1, kx = 2 * sx + dx - 1;
                         if (ky < 0 || kx < 0) continue;
-                        for (int c = 0; c < ci; ++c)
+                        for (int c = 0; c < ci; ++c)  // the input carries kS2dInScale
                             wt[(size_t)o * K + (sy * 2 + sx) * 128 + (dy * 2 + dx) * 32 + c] =
-                                __float2bfloat16(src[((size_t)o * 9 + ky * 3 + kx) * ci + c]);
+                                __float2bfloat16(src[((size_t)o * 9 + ky * 3 + kx) * ci + c] / kS2dInScale);
                     }
     ufvc_status st;
     if ((st = dalloc(ctx, nullptr, &L.wtc, wt.size())) != UFVC_OK) return st;

@@ -102,18 +102,20 @@ void launch_pack(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int
     }
 }
 
-// bf16 bits of frame n's three channels: bytes through the v / 255 table, BT.709 in float
+// bf16 bits of frame n's three channels times in_scale: bytes through the table (v / 255, or v / 256 for
+// in_scale = 255 / 256), BT.709 in float
 template <int FMT>
 __device__ __forceinline__ void px_bf16(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W,
-                                        const uint16_t* lut, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
+                                        const uint16_t* lut, float in_scale, uint32_t& b0, uint32_t& b1,
+                                        uint32_t& b2) {
     uint32_t b[3];
     px_bytes<FMT>(fr, n, sh, sw, H, W, b);
     if (FMT == 1) {
         float v[3];
         bt709_from_bytes(b, v);
-        b0 = __bfloat16_as_ushort(__float2bfloat16_rn(v[0]));
-        b1 = __bfloat16_as_ushort(__float2bfloat16_rn(v[1]));
-        b2 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2]));
+        b0 = __bfloat16_as_ushort(__float2bfloat16_rn(v[0] * in_scale));
+        b1 = __bfloat16_as_ushort(__float2bfloat16_rn(v[1] * in_scale));
+        b2 = __bfloat16_as_ushort(__float2bfloat16_rn(v[2] * in_scale));
     } else {
         b0 = lut[b[0]]; b1 = lut[b[1]]; b2 = lut[b[2]];
     }
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
         for (int n = 0; n < 16; ++n) {
             // channels 3n, 3n+1, 3n+2 -> bf16 halves 3n .. 3n+2 of the packed row
             uint32_t b0 = 0, b1 = 0, b2 = 0;
-            if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, b0, b1, b2);
+            if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, 1.0f, b0, b1, b2);
             // halves 3n, 3n+1, 3n+2 land in words (3n)/2 .. (3n+2)/2 (n even: w, w, w+1 low; n odd: w high, w+1)
             if ((n & 1) == 0) {
                 pk[3 * n / 2] = b0 | (b1 << 16);
@@ -180,7 +182,8 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_kernel(const uint8_t* __re
 // Space-to-depth variant (3N <= 32) for the first layer's 2x2 form: pixel (h, w) becomes sub-pixel
 // (h & 1, w & 1) of super-pixel (h / 2, w / 2), whose 128 channels are [2 (h & 1) + (w & 1)][32].  A block
 // packs a 128-pixel segment of both rows of a super-row, so its 64 super-pixels (16 KB) are written as one
-// contiguous run; shared-memory chunk c (16 bytes) of the segment is kept at c ^ ((c >> 4) & 7).
+// contiguous run; shared-memory chunk c (16 bytes) of the segment is kept at c ^ ((c >> 4) & 7).  Values
+// are x * kS2dInScale: a byte v becomes v / 256, exact in bf16 (the 2x2 weights carry the inverse factor).
 template <int FMT>
 __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* __restrict__ frames, int N, int H,
                                                                  int W, int Hp, int Wp, __nv_bfloat16* __restrict__ x) {
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* 
     pdl_wait();
     __shared__ uint4 tile[kPackPix * 8];
     __shared__ uint16_t lut[256];
-    for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 255.0f));
+    for (int v = threadIdx.x; v < 256; v += blockDim.x) lut[v] = __bfloat16_as_ushort(__float2bfloat16_rn(v / 256.0f));
     __syncthreads();
     const int p = threadIdx.x, w0 = blockIdx.x * kPackPix, w = w0 + p;
     const int sw = w < W ? w : W - 1;  // replicate the last column
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(kPackPix) pack_bf16_s2d_kernel(const uint8_t* 
 #pragma unroll
             for (int n = 0; n < 16; ++n) {
                 uint32_t b0 = 0, b1 = 0, b2 = 0;
-                if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, b0, b1, b2);
+                if (n < N) px_bf16<FMT>(frames, n, sh, sw, H, W, lut, kS2dInScale, b0, b1, b2);
                 if ((n & 1) == 0) {
                     pk[3 * n / 2] = b0 | (b1 << 16);
                     pk[3 * n / 2 + 1] = b2;

@@ -63,6 +63,10 @@ constexpr uint32_t kProbM = 1u << 16;
 constexpr uint32_t kRansL = 1u << 16;
 constexpr int kCoarseShift = 7;                    // decoder slot -> symbol index: 128-slot buckets
 constexpr int kCoarse = 1 << (16 - kCoarseShift);  // 512 buckets per table
+// The BF16 space-to-depth input holds x * 255/256: a byte v is stored as v / 256, which bf16 represents
+// exactly (eight significant bits), and the first layer's 2x2 weights are multiplied by 256/255, so the
+// input planes add no rounding of their own to the analysis.
+constexpr float kS2dInScale = 255.0f / 256.0f;
 
 // ---------------------------------------------------------------------------------------------
 // Host-side tables (FP64 construction, built once per context)
