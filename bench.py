@@ -572,6 +572,13 @@ def main() -> None:
                "tensor_tflop_per_step": (fl["enc"] + fl["dec"]) / 1e12, "tensor_tflops": tf,
                "tensor_frac_of_sustained": tf / pk_dc, "stage_ms_per_step": st_d}
         cdc.close()
+        if not args.no_fp32_path:  # the FP32 DC model on the same chunk sequence (3 context steps), one timed step
+            c32 = U.Codec(2, N, K, synthetic.draw_dc_weights(N, seed=0), "fp32", device=local)
+            r32 = time_codec(c32, fr, frames_np, W_, H_, 1, 3, False, flush, temporal=True)
+            c32.close()
+            dcx["fp32_fps"] = N / ((r32["t_enc"][0] + r32["t_dec"][0]) / 1000.0)
+            dcx["dpsnr_db_vs_fp32"] = rd["psnr"] - r32["psnr"]
+            dcx["dbitrate_vs_fp32"] = (rd["nbytes"] - r32["nbytes"]) / r32["nbytes"]
 
     # ---- colour interface (YUV444 model interface): BT.709 RGB and YUV420 chunks of the same content
     color = None

@@ -506,7 +506,8 @@ extern "C" ufvc_status ufvc_latent_dims(int arch, int width, int height, int* Hy
 // no_fp8 keeps an FP8 context's layer on bf16 operands
 static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, const size_t* offs, int first, int groups,
                                 bool tc, bool pixel_shuffle = false, bool final_layer = false,
-                                const int* shape = nullptr, bool no_fp8 = false, int gstride = D_NDEC) {
+                                const int* shape = nullptr, bool no_fp8 = false, int gstride = D_NDEC,
+                                float tc_scale = 1.0f) {
     int co, k, ci;
     if (shape) { co = shape[0]; k = shape[1]; ci = shape[2]; }
     else layer_shape(ctx->cfg.arch, ctx->N, first, &co, &k, &ci);
@@ -545,7 +546,7 @@ static ufvc_status upload_layer(ufvc_ctx* ctx, LayerW& L, const float* blob, con
                 for (int t = 0; t < k * k; ++t)
                     for (int i = 0; i < ci; ++i)
                         wt[((size_t)g * L.cout_pad + row(o)) * K + (size_t)t * L.cin_tc + i] =
-                            __float2bfloat16(src[((size_t)o * k * k + t) * ci + i]);
+                            __float2bfloat16(tc_scale * src[((size_t)o * k * k + t) * ci + i]);
                 bt[(size_t)g * co + row(o)] = b[(size_t)g * co + o];
             }
         }
@@ -639,8 +640,9 @@ static ufvc_status upload_dc(ufvc_ctx* ctx, const float* weights) {
                               sh, true, 1);
         } else if (l == DC_PC) {
             st = upload_layer(ctx, ctx->tl[TL_PC], weights, offs.data(), l, 1, true, false, false, sh, true, 1);
-        } else {
-            st = upload_layer(ctx, ctx->dcl[l], weights, offs.data(), l, 1, true, l == DC_DU, false, sh, true, 1);
+        } else {  // the patch embedding's bf16 input carries kS2dInScale
+            st = upload_layer(ctx, ctx->dcl[l], weights, offs.data(), l, 1, true, l == DC_DU, false, sh, true, 1,
+                              l == DC_PE ? 1.0f / kS2dInScale : 1.0f);
         }
         if (st != UFVC_OK) return st;
     }

@@ -86,7 +86,8 @@ __device__ __forceinline__ void px3(const uint8_t* __restrict__ fr, int n, int s
 }
 
 // one thread per (super-row h8, frame n, sub-row dy, position w8), w8 fastest: a warp reads 32 consecutive
-// 8-pixel runs of one frame row; each thread writes its three 8-channel runs
+// 8-pixel runs of one frame row; each thread writes its three 8-channel runs.  bf16 runs hold x * kS2dInScale
+// (a byte v becomes v / 256, exact in bf16; the patch embedding's bf16 weights carry the inverse factor).
 template <int FMT, typename T>
 __global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int H8, int W8,
                                  T* __restrict__ x) {
@@ -107,7 +108,8 @@ __global__ void pack_s2d8_kernel(const uint8_t* __restrict__ frames, int N, int 
             const int w = 8 * (int)w8 + dx, sw = w < W ? w : W - 1;
             float p[3];
             px3<FMT>(frames, n, sh, sw, H, W, p);
-            v[0][dx] = p[0]; v[1][dx] = p[1]; v[2][dx] = p[2];
+            const float k = sizeof(T) == 2 ? kS2dInScale : 1.0f;
+            v[0][dx] = p[0] * k; v[1][dx] = p[1] * k; v[2][dx] = p[2] * k;
         }
         T* o = x + ((size_t)h8 * W8 + w8) * C0 + (size_t)(3 * n) * 64 + 8 * dy;
 #pragma unroll
