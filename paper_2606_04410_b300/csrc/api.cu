@@ -131,6 +131,7 @@ struct ufvc_ctx {
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
     // taps regrouped by 2x2 super-pixel; weight rows [64][tap][sub-pixel][32]; bias shared with enc[L_A1])
     LayerW a1s2d;
+    void* first_w = nullptr;  // A1's weight image for the kernel that reads frame bytes (BF16)
     // progressive means (ufvc_set_progressive_means): P1a P1b P2a P2b P3a P3b; pm_on selects version-2
     // streams (partitions 1..3 coded with the progressive means)
     LayerW pm[kMeanLayers];
@@ -714,6 +715,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
         for (LayerW& L : ctx->dcl) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
         for (LayerW& L : ctx->dcf) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
         cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
+        cudaFree(ctx->first_w);
         cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
     }
@@ -781,6 +783,16 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
             return bail(st);
     if (cfg->precision == UFVC_BF16 && 3 * ctx->N <= 32 && (st = upload_a1_s2d(ctx, weights + offs[L_A1])) != UFVC_OK)
         return bail(st);
+    if (cfg->precision == UFVC_BF16 && first_layer_ct(ctx->N) && ctx->enc[L_A1].cout == 64 && ctx->enc[L_A1].k == 3) {
+        // the frame-byte kernel's input is x * kS2dInScale, like the space-to-depth pack's
+        const int ct = first_layer_ct(ctx->N);
+        std::vector<uint16_t> img(first_layer_weight_bytes(ct) / 2);
+        first_layer_weights(weights + offs[L_A1], ctx->N, 1.0f / kS2dInScale, img.data());
+        uint16_t* dimg = nullptr;
+        if ((st = dalloc(ctx, nullptr, &dimg, img.size())) != UFVC_OK) return bail(st);
+        ctx->first_w = dimg;
+        if (cudaMemcpy(dimg, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return bail(UFVC_ERR_CUDA);
+    }
     *out = ctx;
     return UFVC_OK;
 }
@@ -804,6 +816,7 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     for (int l = 0; l < L_NENC; ++l) c->enc[l] = base->enc[l];
     for (int l = 0; l < D_NDEC; ++l) c->dec[l] = base->dec[l];
     c->a1s2d = base->a1s2d;
+    c->first_w = base->first_w;
     for (int l = 0; l < kMeanLayers; ++l) c->pm[l] = base->pm[l];
     c->pm_on = base->pm_on;
     c->color = base->color;
@@ -1047,20 +1060,28 @@ static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* fra
     const Arch& a = ctx->arch;
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     const bool s2d = ctx->a1s2d.wtc != nullptr && p->C0p == 32;
-    prof_begin(ctx, "pack", s);
-    if (ctx->cfg.precision == UFVC_FP32)
-        launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s, ctx->color);
-    else if (fp8)
-        launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s, ctx->color);
-    else
-        launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s,
-                         s2d, ctx->color);
-    prof_end(ctx, s, 1);
-    prof_begin(ctx, "analysis", s);
-    if (s2d)  // the same layer as a 2x2 stride-1 convolution over the space-to-depth input
-        RUN(conv(ctx, ctx->a1s2d, p->x, p->Hp / 2, p->Wp / 2, 1, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
-    else
-        RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    // BF16 frames in RGB, YUV444 or YUV420 with even N <= 8: A1 reads the frame bytes itself (no pack pass)
+    const bool first = ctx->first_w != nullptr && ctx->color != UFVC_COLOR_RGB_BT709;
+    if (first) {
+        prof_begin(ctx, "analysis", s);
+        CK(launch_first_layer(frames, ctx->color, ctx->N, p->H, p->W, p->h1, p->w1, ctx->first_w, ctx->enc[L_A1].b,
+                              reinterpret_cast<__nv_bfloat16*>(p->a1), ctx->d_status, s));
+    } else {
+        prof_begin(ctx, "pack", s);
+        if (ctx->cfg.precision == UFVC_FP32)
+            launch_pack(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, p->x, s, ctx->color);
+        else if (fp8)
+            launch_pack_fp8(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, reinterpret_cast<uint8_t*>(p->x), s, ctx->color);
+        else
+            launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s,
+                             s2d, ctx->color);
+        prof_end(ctx, s, 1);
+        prof_begin(ctx, "analysis", s);
+        if (s2d)  // the same layer as a 2x2 stride-1 convolution over the space-to-depth input
+            RUN(conv(ctx, ctx->a1s2d, p->x, p->Hp / 2, p->Wp / 2, 1, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+        else
+            RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
+    }
     probe(ctx, T_A1, p->a1, (size_t)p->h1 * p->w1 * a.e0, s);
     RUN(conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s));
     probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);

@@ -76,25 +76,6 @@ __device__ __forceinline__ const float* stage_bias(const TcArgs& p, float* sbias
     return sbias;  // visible after the block barrier that follows the set-up
 }
 
-// The same GELU for two values at once, the logistic taken as 0.5 + 0.5 tanh(z / 2) and z / 2 =
-// x P(t) / 2 evaluated in packed half precision with one tanh.approx.f16x2 for both values; the final
-// product x (0.5 + 0.5 tanh) is FP32.  Half precision adds about 1e-3 absolute to the logistic, so the
-// GELU's relative error stays at or below the 2^-9 rounding of the bf16 activation it is stored as.
-// (|x| > 255 squares to +inf in half precision and is clamped to t = 100; |x| beyond the half range
-// gives tanh = +-1, the exact limits.)
-__device__ __forceinline__ void gelu_tc2(float& a, float& b) {
-    const __half2 x = __floats2half2_rn(a, b);
-    const __half2 t = __hmin2(__hmul2(x, x), __float2half2_rn(100.0f));
-    __half2 q = __hfma2(t, __float2half2_rn(-7.03033577e-4f * 0.5f), __float2half2_rn(7.40112920e-2f * 0.5f));
-    q = __hfma2(q, t, __float2half2_rn(1.59501577f * 0.5f));
-    const __half2 z = __hmul2(q, x);
-    uint32_t ti;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(ti) : "r"(*reinterpret_cast<const uint32_t*>(&z)));
-    const float2 th = __half22float2(*reinterpret_cast<const __half2*>(&ti));
-    a *= fmaf(0.5f, th.x, 0.5f);
-    b *= fmaf(0.5f, th.y, 0.5f);
-}
-
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          bool honour_abort = true) {
     if (ptx::mbar_try_wait(bar, parity)) return true;

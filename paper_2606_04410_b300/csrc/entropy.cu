@@ -24,29 +24,6 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // ------------------------------------------------------------------------------------------------
 // pack
 // ------------------------------------------------------------------------------------------------
-// Colour interface (the model's input is YUV444; callers give RGB or YUV): the three bytes of frame n's
-// pixel (sh, sw) in the caller's format.  0, 1: RGB interleaved [N][H][W][3] (1 is converted with
-// BT.709); 2: YUV444 planar [N][3][H][W]; 3: YUV420 planar per frame, Y [H][W] then U and V
-// [ceil(H/2)][ceil(W/2)], each chroma sample serving its 2x2 block.
-template <int FMT>
-__device__ __forceinline__ void px_bytes(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W,
-                                         uint32_t* b) {
-    if (FMT <= 1) {
-        const uint8_t* p = fr + ((size_t)n * H * W + (size_t)sh * W + sw) * 3;
-        b[0] = __ldg(p); b[1] = __ldg(p + 1); b[2] = __ldg(p + 2);
-    } else if (FMT == 2) {
-        const size_t pl = (size_t)H * W;
-        const uint8_t* p = fr + (size_t)n * 3 * pl + (size_t)sh * W + sw;
-        b[0] = __ldg(p); b[1] = __ldg(p + pl); b[2] = __ldg(p + 2 * pl);
-    } else {
-        const int Wc = (W + 1) >> 1, Hc = (H + 1) >> 1;
-        const size_t pl = (size_t)H * W, cpl = (size_t)Hc * Wc;
-        const uint8_t* f = fr + (size_t)n * (pl + 2 * cpl);
-        const size_t ci = (size_t)(sh >> 1) * Wc + (sw >> 1);
-        b[0] = __ldg(f + (size_t)sh * W + sw); b[1] = __ldg(f + pl + ci); b[2] = __ldg(f + pl + cpl + ci);
-    }
-}
-
 // BT.709, full range, chroma centred at 0.5: Y = 0.2126 R + 0.7152 G + 0.0722 B, U = (B - Y) / 1.8556 + 0.5,
 // V = (R - Y) / 1.5748 + 0.5, on RGB bytes / 255
 __device__ __forceinline__ void bt709_from_bytes(const uint32_t* b, float* v) {

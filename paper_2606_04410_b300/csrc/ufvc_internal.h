@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -37,6 +38,48 @@ __device__ __forceinline__ float gelu_tc(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(p * x));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
     return x * r;
+}
+
+// The same GELU for two values at once, the logistic taken as 0.5 + 0.5 tanh(z / 2) and z / 2 =
+// x P(t) / 2 evaluated in packed half precision with one tanh.approx.f16x2 for both values; the final
+// product x (0.5 + 0.5 tanh) is FP32.  Half precision adds about 1e-3 absolute to the logistic, so the
+// GELU's relative error stays at or below the 2^-9 rounding of the bf16 activation it is stored as.
+// (|x| > 255 squares to +inf in half precision and is clamped to t = 100; |x| beyond the half range
+// gives tanh = +-1, the exact limits.)
+__device__ __forceinline__ void gelu_tc2(float& a, float& b) {
+    const __half2 x = __floats2half2_rn(a, b);
+    const __half2 t = __hmin2(__hmul2(x, x), __float2half2_rn(100.0f));
+    __half2 q = __hfma2(t, __float2half2_rn(-7.03033577e-4f * 0.5f), __float2half2_rn(7.40112920e-2f * 0.5f));
+    q = __hfma2(q, t, __float2half2_rn(1.59501577f * 0.5f));
+    const __half2 z = __hmul2(q, x);
+    uint32_t ti;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(ti) : "r"(*reinterpret_cast<const uint32_t*>(&z)));
+    const float2 th = __half22float2(*reinterpret_cast<const __half2*>(&ti));
+    a *= fmaf(0.5f, th.x, 0.5f);
+    b *= fmaf(0.5f, th.y, 0.5f);
+}
+
+// Colour interface (the model's input is YUV444; callers give RGB or YUV): the three bytes of frame n's
+// pixel (sh, sw) in the caller's format.  0, 1: RGB interleaved [N][H][W][3] (1 is converted with
+// BT.709); 2: YUV444 planar [N][3][H][W]; 3: YUV420 planar per frame, Y [H][W] then U and V
+// [ceil(H/2)][ceil(W/2)], each chroma sample serving its 2x2 block.
+template <int FMT>
+__device__ __forceinline__ void px_bytes(const uint8_t* __restrict__ fr, int n, int sh, int sw, int H, int W,
+                                         uint32_t* b) {
+    if (FMT <= 1) {
+        const uint8_t* p = fr + ((size_t)n * H * W + (size_t)sh * W + sw) * 3;
+        b[0] = __ldg(p); b[1] = __ldg(p + 1); b[2] = __ldg(p + 2);
+    } else if (FMT == 2) {
+        const size_t pl = (size_t)H * W;
+        const uint8_t* p = fr + (size_t)n * 3 * pl + (size_t)sh * W + sw;
+        b[0] = __ldg(p); b[1] = __ldg(p + pl); b[2] = __ldg(p + 2 * pl);
+    } else {
+        const int Wc = (W + 1) >> 1, Hc = (H + 1) >> 1;
+        const size_t pl = (size_t)H * W, cpl = (size_t)Hc * Wc;
+        const uint8_t* f = fr + (size_t)n * (pl + 2 * cpl);
+        const size_t ci = (size_t)(sh >> 1) * Wc + (sw >> 1);
+        b[0] = __ldg(f + (size_t)sh * W + sw); b[1] = __ldg(f + pl + ci); b[2] = __ldg(f + pl + cpl + ci);
+    }
 }
 
 template <typename... KArgs, typename... Args>
@@ -179,6 +222,15 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
 // fmt: the caller's colour format (ufvc_color); the network reads its three channels per frame
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s, bool s2d, int fmt);
+// First analysis layer straight from the frame bytes (conv_first.cu), BF16, colour formats 0, 2, 3 and
+// even N, 2 <= N <= 8: first_layer_ct(N) = 3N rounded up to 8 (0 where not supported);
+// first_layer_weights writes the swizzled bf16 weight image (first_layer_weight_bytes(ct) bytes) of the [64][3][3][3N] weights
+// times scale; out = GELU(A1(frames)) bf16 NHWC [Ho][Wo][64].
+int first_layer_ct(int n_frames);
+size_t first_layer_weight_bytes(int ct);
+void first_layer_weights(const float* w, int n_frames, float scale, uint16_t* img);
+cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
+                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s);
 // colour interface, output side (color.cu): x^ float [N][H][W][3] -> the caller's format (fmt 1..3), float
 // or uint8; frame_bytes = bytes of one frame in format fmt
 size_t frame_bytes(int fmt, int W, int H);
