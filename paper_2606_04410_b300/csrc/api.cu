@@ -131,7 +131,7 @@ struct ufvc_ctx {
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
     // taps regrouped by 2x2 super-pixel; weight rows [64][tap][sub-pixel][32]; bias shared with enc[L_A1])
     LayerW a1s2d;
-    void* first_w = nullptr;  // A1's weight image for the kernel that reads frame bytes (BF16)
+    void* first_w = nullptr;  // A1's weight image for the kernels that read frame bytes (BF16)
     // progressive means (ufvc_set_progressive_means): P1a P1b P2a P2b P3a P3b; pm_on selects version-2
     // streams (partitions 1..3 coded with the progressive means)
     LayerW pm[kMeanLayers];
@@ -785,13 +785,14 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
         return bail(st);
     if (cfg->precision == UFVC_BF16 && first_layer_ct(ctx->N) && ctx->enc[L_A1].cout == 64 && ctx->enc[L_A1].k == 3) {
         // the frame-byte kernel's input is x * kS2dInScale, like the space-to-depth pack's
-        const int ct = first_layer_ct(ctx->N);
-        std::vector<uint16_t> img(first_layer_weight_bytes(ct) / 2);
-        first_layer_weights(weights + offs[L_A1], ctx->N, 1.0f / kS2dInScale, img.data());
+        const int pitch = first_layer_pitch(ctx->N);
+        std::vector<uint16_t> img(first_layer_weight_bytes(pitch) / 2);
+        first_layer_weights(weights + offs[L_A1], ctx->N, 1.0f / kS2dInScale, pitch, img.data());
         uint16_t* dimg = nullptr;
         if ((st = dalloc(ctx, nullptr, &dimg, img.size())) != UFVC_OK) return bail(st);
         ctx->first_w = dimg;
-        if (cudaMemcpy(dimg, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess) return bail(UFVC_ERR_CUDA);
+        if (cudaMemcpy(dimg, img.data(), img.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(UFVC_ERR_CUDA);
     }
     *out = ctx;
     return UFVC_OK;

@@ -1065,6 +1065,16 @@ static bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint6
     return r == CUDA_SUCCESS;
 }
 
+// Frames [N][H][row_bytes] uint8 as a 3D tensor map (bytes, rows, frames) with box (box_x, box_y, N), no
+// swizzle; map points at a 64-byte aligned CUtensorMap.
+bool encode_frames_map(void* map, const void* frames, int N, int H, int row_bytes, int box_x, int box_y) {
+    const cuuint64_t dims[3] = {(cuuint64_t)row_bytes, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)H * row_bytes};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)N};
+    return encode_map(static_cast<CUtensorMap*>(map), frames, 3, dims, strides, box, CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                      CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
 // Output tile TW x TH = 128 pixels with the least padding; with th_divides, TH must divide Ho.
 static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false) {
     long long best = -1;

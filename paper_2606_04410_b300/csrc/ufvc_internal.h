@@ -223,12 +223,15 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s, bool s2d, int fmt);
 // First analysis layer straight from the frame bytes (conv_first.cu), BF16, colour formats 0, 2, 3 and
-// even N, 2 <= N <= 8: first_layer_ct(N) = 3N rounded up to 8 (0 where not supported);
-// first_layer_weights writes the swizzled bf16 weight image (first_layer_weight_bytes(ct) bytes) of the [64][3][3][3N] weights
-// times scale; out = GELU(A1(frames)) bf16 NHWC [Ho][Wo][64].
+// even N, 2 <= N <= 8 (first_layer_ct(N) = 0 otherwise).  first_layer_weights writes the swizzled bf16
+// image (first_layer_weight_bytes(pitch) bytes) of the [64][3][3][3N] weights times scale with
+// K = tap x pitch + channel, pitch = first_layer_pitch(N) (3N rounded up to 16).
+// out = GELU(A1(frames)) bf16 NHWC [Ho][Wo][64].
 int first_layer_ct(int n_frames);
-size_t first_layer_weight_bytes(int ct);
-void first_layer_weights(const float* w, int n_frames, float scale, uint16_t* img);
+int first_layer_pitch(int n_frames);
+size_t first_layer_weight_bytes(int pitch);
+void first_layer_weights(const float* w, int n_frames, float scale, int pitch, uint16_t* img);
+bool encode_frames_map(void* map, const void* frames, int N, int H, int row_bytes, int box_x, int box_y);
 cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
                                const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s);
 // colour interface, output side (color.cu): x^ float [N][H][W][3] -> the caller's format (fmt 1..3), float
