@@ -154,9 +154,9 @@ __device__ __forceinline__ uint32_t chan_byte(const uint8_t* __restrict__ fr, in
     if (FMT == 2) return __ldg(fr + ((size_t)(3 * n + colour) * H + sh) * W + sw);
     const int Wc = (W + 1) >> 1, Hc = (H + 1) >> 1;
     const size_t pl = (size_t)H * W, cpl = (size_t)Hc * Wc;
-    const uint8_t* f = fr + (size_t)n * (pl + 2 * cpl);
-    if (colour == 0) return __ldg(f + (size_t)sh * W + sw);
-    return __ldg(f + pl + (colour - 1) * cpl + (size_t)(sh >> 1) * Wc + (sw >> 1));
+    // one load at a selected offset (no branch, so the loads of a tile stay in flight together)
+    const size_t o = colour == 0 ? (size_t)sh * W + sw : pl + (colour - 1) * cpl + (size_t)(sh >> 1) * Wc + (sw >> 1);
+    return __ldg(fr + (size_t)n * (pl + 2 * cpl) + o);
 }
 
 template <int FMT, int CT>
