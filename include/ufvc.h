@@ -154,6 +154,26 @@ ufvc_status ufvc_encode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_frames, int n
 ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bits, size_t nbytes, uint8_t* h_frames,
                                    int n_frames, int width, int height, void* stream);
 
+/* ---- pipelined host-buffer round trips (streaming callers) ----
+ * A pipeline of `depth` slots (1..16), each a context sharing ctx's weights and tables (own plans,
+ * device buffers and non-blocking CUDA stream); ctx must outlive it and stay unchanged meanwhile.
+ * ufvc_pipe_submit enqueues one chunk's round trip on slot ticket % depth and returns at once:
+ * h_frames (ctx's colour format) to the device, ufvc_encode_chunk, the whole bit-stream buffer
+ * (`capacity` bytes, at least ufvc_max_bitstream_bytes) to h_bits, that host copy back to the device,
+ * ufvc_decode_chunk_dev of it, and the decoded frames to h_out (skipped when h_out is NULL).  One
+ * slot's copies overlap the others' kernels.  Host buffers must stay valid and unchanged until the
+ * ticket has been waited for; page-locked host memory makes the copies asynchronous.  *ticket gets
+ * consecutive numbers from 0.  UFVC_ERR_ARG if ticket t - depth has not been waited for yet,
+ * UFVC_ERR_CAPACITY if capacity is too small.  ufvc_pipe_wait blocks until the ticket's round trip has
+ * completed and returns its device status; *nbytes gets the stream size (the first *nbytes bytes of
+ * h_bits are the bit-stream).  Each ticket is waited for once. */
+typedef struct ufvc_pipe ufvc_pipe;
+ufvc_status ufvc_pipe_create(ufvc_ctx* ctx, int depth, ufvc_pipe** out);
+ufvc_status ufvc_pipe_submit(ufvc_pipe* pipe, const uint8_t* h_frames, int n_frames, int width, int height, int qp,
+                             uint8_t* h_bits, size_t capacity, uint8_t* h_out, long long* ticket);
+ufvc_status ufvc_pipe_wait(ufvc_pipe* pipe, long long ticket, size_t* nbytes);
+void ufvc_pipe_destroy(ufvc_pipe* pipe);
+
 /* Synchronise `stream`, then return and clear the device status word (UFVC_OK if no device-side
  * error was recorded since the last call). */
 ufvc_status ufvc_sync_status(ufvc_ctx* ctx, void* stream);

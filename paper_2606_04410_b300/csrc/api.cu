@@ -801,6 +801,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
 // A context that shares base's weights and tables (read-only on the device) but has its own plans,
 // workspaces, staging and status word, so that it can run concurrently with base on another stream.
 // base must outlive it.
+int ufvc::ctx_color(const ufvc_ctx* ctx) { return ctx->color; }
+
 ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     if (!base || base->borrowed) return nullptr;
     if (cudaSetDevice(base->cfg.device) != cudaSuccess) return nullptr;

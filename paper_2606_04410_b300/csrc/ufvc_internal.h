@@ -212,6 +212,7 @@ struct ConvDesc {
 
 // api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
 ufvc_ctx* ctx_clone_shared(const ufvc_ctx* base);
+int ctx_color(const ufvc_ctx* ctx);   // the context's colour format (ufvc_color)
 bool ctx_temporal(const ufvc_ctx* ctx);  // the context carries a temporal chunk context (C_i)
 size_t ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H);
 

@@ -37,7 +37,8 @@ EXPORTS = [
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
     "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
     "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
-    "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means",
+    "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means", "ufvc_pipe_create",
+    "ufvc_pipe_submit", "ufvc_pipe_wait", "ufvc_pipe_destroy",
 ]
 COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
@@ -105,6 +106,10 @@ _sigs = {
     "ufvc_set_temporal_context": (_i, [_vp, _vp, _sz]),
     "ufvc_server_set_temporal_context": (_i, [_vp, _vp, _sz]),
     "ufvc_server_set_progressive_means": (_i, [_vp, _vp, _sz]),
+    "ufvc_pipe_create": (_i, [_vp, _i, C.POINTER(_vp)]),
+    "ufvc_pipe_submit": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, C.POINTER(C.c_longlong)]),
+    "ufvc_pipe_wait": (_i, [_vp, C.c_longlong, C.POINTER(_sz)]),
+    "ufvc_pipe_destroy": (None, [_vp]),
     "ufvc_context_bytes": (_sz, [_vp, _i, _i]),
     "ufvc_encode_chunk_tc": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp, _vp, _vp]),
     "ufvc_decode_chunk_tc": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -425,6 +430,48 @@ class Codec:
         raw = names.raw
         return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), float(ms[i]), int(launches[i]))
                 for i in range(cnt.value)]
+
+
+class Pipe:
+    """Pipelined host-buffer round trips (ufvc_pipe_*): `depth` slots sharing codec's weights; submit()
+    enqueues frames -> encode -> bit-stream to host -> back -> decode -> frames to host and returns a
+    ticket; wait(ticket) returns the stream size.  Host buffers (page-locked for asynchronous copies) must
+    stay alive until their ticket has been waited for."""
+
+    def __init__(self, codec: "Codec", depth: int = 2):
+        h = C.c_void_p()
+        rc = lib.ufvc_pipe_create(codec.h, depth, C.byref(h))
+        if rc:
+            raise UfvcError(rc, "ufvc_pipe_create")
+        self.h, self.codec, self.depth = h, codec, depth
+
+    def submit(self, h_frames, width: int, height: int, h_bits, h_out=None, qp: int = 32) -> int:
+        t = C.c_longlong()
+        n = h_frames.shape[0]
+        cap = h_bits.numel() if isinstance(h_bits, torch.Tensor) else h_bits.size
+        rc = lib.ufvc_pipe_submit(self.h, _ptr(h_frames), n, width, height, qp, _ptr(h_bits), cap, _ptr(h_out),
+                                  C.byref(t))
+        if rc:
+            raise UfvcError(rc, "ufvc_pipe_submit")
+        return t.value
+
+    def wait(self, ticket: int) -> int:
+        nb = C.c_size_t()
+        rc = lib.ufvc_pipe_wait(self.h, ticket, C.byref(nb))
+        if rc:
+            raise UfvcError(rc, "ufvc_pipe_wait")
+        return nb.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ufvc_pipe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
