@@ -271,7 +271,10 @@ __device__ __forceinline__ void store_cols(const TcArgs& p, const float* bias_al
 enum { OP_BF16 = 0, OP_E4M3 = 1, OP_BF16_32 = 2 };
 
 // KM: some K steps are skipped (TcArgs::kmask); otherwise every step runs and the loops carry no test.
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false>
+// MT = 2: a tile is two 128-pixel sub-tiles stacked vertically (2 TH x TW pixels, one TMA box of 256 rows),
+// which share each stage's weight tile: two MMAs per K slice into two accumulators, 25 % fewer operand
+// bytes landing in shared memory per MMA; one epilogue group drains and stores the sub-tiles in turn.
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
@@ -279,15 +282,17 @@ __global__ void __launch_bounds__(kThreads, 1)
     static_assert(!(F8 && STAGED), "FP8 outputs use the per-thread epilogue");
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
-    constexpr int A_BYTES = 128 * ROWB;
+    static_assert(MT == 1 || (MT == 2 && !F8 && OP == OP_BF16), "two sub-tiles: BF16 operands");
+    constexpr int A_BYTES = 128 * MT * ROWB;
     constexpr int B_BYTES = BN * ROWB;
-    constexpr int EG = epi_groups(BN);  // epilogue groups (tiles drained concurrently)
+    constexpr int EG = MT == 2 ? 1 : epi_groups(BN);  // epilogue groups (tiles drained concurrently)
     constexpr int WPQ = 4 / EG;         // warps per TMEM lane quarter in a group
     constexpr int NACC = 2 * EG;        // TMEM accumulators
     constexpr int C_BYTES = STAGED ? 128 * BN * 2 * EG : 0;
-    constexpr uint32_t TMEM_COLS = (NACC * BN <= 32) ? 32 : (NACC * BN <= 64) ? 64 : (NACC * BN <= 128) ? 128
-                                   : (NACC * BN <= 256) ? 256 : 512;
-    static_assert(NACC * BN <= 512, "TMEM columns");
+    constexpr int ACOLS = MT * BN;      // TMEM columns of one tile's accumulator(s)
+    constexpr uint32_t TMEM_COLS = (NACC * ACOLS <= 32) ? 32 : (NACC * ACOLS <= 64) ? 64 : (NACC * ACOLS <= 128) ? 128
+                                   : (NACC * ACOLS <= 256) ? 256 : 512;
+    static_assert(NACC * ACOLS <= 512, "TMEM columns");
     // each of the WPQ warps of a lane quarter in a group drains PER of the BN columns
     constexpr int PER = BN / WPQ < 16 ? 16 : BN / WPQ;
     constexpr int CHUNK = PER % 32 == 0 ? 32 : 16;  // accumulator columns per tcgen05.ld round
@@ -356,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
                 const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
-                const int h0 = (mt / p.tiles_w) * p.TH, w0 = (mt % p.tiles_w) * p.TW;
+                const int h0 = (mt / p.tiles_w) * p.TH * MT, w0 = (mt % p.tiles_w) * p.TW;
                 const int ag = p.a_grouped ? g : 0;
                 for (int ks = 0; ks < p.ksteps; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;  // all-zero weights: no stage
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int acc = tl % NACC, use = tl / NACC;
                 if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 ptx::tc_fence_after();
-                const uint32_t d = tmem_base + acc * BN;
+                const uint32_t d = tmem_base + acc * ACOLS;
                 bool first = true;  // the tile's first executed step overwrites the accumulator
                 for (int ks = 0; ks < p.ksteps; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;
@@ -419,8 +424,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
-                            ptx::mma_f16(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32),
-                                         idesc, !first || kk != 0);
+#pragma unroll
+                            for (int h = 0; h < MT; ++h)  // sub-tile h: rows 128 h .. of the A box
+                                ptx::mma_f16(d + h * BN, ptx::sdesc_sw128(a0 + h * 16384 + kk * 32),
+                                             ptx::sdesc_sw128(b0 + kk * 32), idesc, !first || kk != 0);
                     }
                     ptx::mma_commit(&empty[s]);
                     first = false;
@@ -442,71 +449,78 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int lead = 2 + 4 * (egrp * WPQ + (cpart / GQ) * GQ);  // first warp of the slab group
         const bool elected = STAGED && warp == lead && lane == 0;
         uint8_t* sCg = sC + egrp * (BN / 64) * (128 * 128);      // this group's staging slabs
-        int tl = egrp, k = 0;
-        for (int t = blockIdx.x + egrp * gridDim.x; t < p.total_tiles; t += EG * gridDim.x, tl += EG, ++k) {
+        int tl = egrp, k = 0;  // k counts sub-tiles (the staging barriers' phases)
+        bool run = true;
+        for (int t = blockIdx.x + egrp * gridDim.x; run && t < p.total_tiles; t += EG * gridDim.x, tl += EG) {
             const int acc = tl % NACC, use = tl / NACC;
             if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
             const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
-            const int h0 = (mt / p.tiles_w) * p.TH, w0 = (mt % p.tiles_w) * p.TW;
-            const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
-            const bool valid = oh < p.Ho && ow < p.Wo;
-            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * BN;
-            const int c_begin = cpart * PER;
-            bool ok = true;
+            const int w0 = (mt % p.tiles_w) * p.TW;
 #pragma unroll 1
-            for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
-                float v[CHUNK];
-                if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
-                if constexpr (STAGED) {
-                    if (valid) finish_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
-                    if (c == c_begin && k > 0) {
-                        // the group's previous TMA stores must have read its staging slabs
-                        if (elected) {
-                            ptx::bulk_wait_read0();
-                            ptx::mbar_arrive(&cfree[grp]);
+            for (int hs = 0; hs < MT; ++hs, ++k) {
+                const int h0 = (mt / p.tiles_w) * p.TH * MT + hs * p.TH;
+                const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
+                const bool valid = oh < p.Ho && ow < p.Wo;
+                const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * ACOLS + hs * BN;
+                const int c_begin = cpart * PER;
+                bool ok = true;
+#pragma unroll 1
+                for (int c = c_begin; c < c_begin + PER && c < BN; c += CHUNK) {
+                    float v[CHUNK];
+                    if constexpr (CHUNK == 32) tmem_ld32(taddr + c, v); else ptx::tmem_ld16(taddr + c, v);
+                    if constexpr (STAGED) {
+                        if (valid) finish_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                        if (c == c_begin && k > 0) {
+                            // the group's previous TMA stores must have read its staging slabs
+                            if (elected) {
+                                ptx::bulk_wait_read0();
+                                ptx::mbar_arrive(&cfree[grp]);
+                            }
+                            ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err));
+                            if (!ok) break;  // warp-uniform: the next tcgen05.ld needs the whole warp
                         }
-                        ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err));
-                        if (!ok) break;  // warp-uniform: the next tcgen05.ld needs the whole warp
-                    }
-                    // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
-                    const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * (128 * 128) + row * 128;
+                        // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
+                        const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * (128 * 128) + row * 128;
 #pragma unroll
-                    for (int i = 0; i < CHUNK / 8; ++i) {
-                        const int j = ((c & 63) >> 3) + i;
-                        ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
-                                          pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
-                                          pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                        for (int i = 0; i < CHUNK / 8; ++i) {
+                            const int j = ((c & 63) >> 3) + i;
+                            ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                              pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                              pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                        }
+                    } else {
+                        if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
                     }
-                } else {
-                    if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
                 }
-            }
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(&tempty[acc]);
-            if (!ok) break;
-            if constexpr (STAGED) {
-                ptx::fence_proxy_async();  // this thread's staging writes -> visible to the TMA (async proxy)
-                ptx::mbar_arrive(&cwritten[grp]);
-                if (warp == lead) {  // the elected thread's warp (warp-uniform)
-                    bool w_ok = true;
-                    if (lane == 0) w_ok = wait_bar(&cwritten[grp], k & 1, abort_flag, p.err);
-                    if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
+                if (hs == MT - 1) {  // every sub-tile's columns are in registers or staged: free the accumulator
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(&tempty[acc]);
                 }
-                if (elected) {
-                    const int lo = (cpart / GQ) * GQ * PER;
-                    const int hi = lo + GQ * PER < BN ? lo + GQ * PER : BN;
-                    for (int sl = lo >> 6; sl < (hi + 63) >> 6; ++sl) {
-                        const int col0 = nt * BN + sl * 64;
-                        const uint8_t* src = sCg + sl * (128 * 128);
-                        if (p.c_rank == 4) {
-                            ptx::tma_store_4d(&tmC, src, col0, w0, h0, g);
-                        } else {
-                            const int sub = col0 / p.out_c, c0 = col0 - sub * p.out_c;
-                            ptx::tma_store_5d(&tmC, src, c0, sub & 1, w0, sub >> 1, g * p.Ho + h0);
+                if (!ok) { run = false; break; }
+                if constexpr (STAGED) {
+                    ptx::fence_proxy_async();  // this thread's staging writes -> visible to the TMA (async proxy)
+                    ptx::mbar_arrive(&cwritten[grp]);
+                    if (warp == lead) {  // the elected thread's warp (warp-uniform)
+                        bool w_ok = true;
+                        if (lane == 0) w_ok = wait_bar(&cwritten[grp], k & 1, abort_flag, p.err);
+                        if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) { run = false; break; }
+                    }
+                    if (elected && h0 < p.Ho) {  // a sub-tile wholly below the output stores nothing
+                        const int lo = (cpart / GQ) * GQ * PER;
+                        const int hi = lo + GQ * PER < BN ? lo + GQ * PER : BN;
+                        for (int sl = lo >> 6; sl < (hi + 63) >> 6; ++sl) {
+                            const int col0 = nt * BN + sl * 64;
+                            const uint8_t* src = sCg + sl * (128 * 128);
+                            if (p.c_rank == 4) {
+                                ptx::tma_store_4d(&tmC, src, col0, w0, h0, g);
+                            } else {
+                                const int sub = col0 / p.out_c, c0 = col0 - sub * p.out_c;
+                                ptx::tma_store_5d(&tmC, src, c0, sub & 1, w0, sub >> 1, g * p.Ho + h0);
+                            }
                         }
                     }
-                    ptx::bulk_commit();
+                    if (elected) ptx::bulk_commit();
                 }
             }
         }
@@ -1086,16 +1100,17 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false>
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
-    constexpr int kSmem = STAGES * (128 * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 * epi_groups(BN) : 0) + kSmemExtra;
+    constexpr int EG = MT == 2 ? 1 : epi_groups(BN);
+    constexpr int kSmem = STAGES * (128 * MT * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 * EG : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
     static int configured_smem = 0;
     if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP, KM>,
+        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured_smem = smem;
@@ -1107,7 +1122,8 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
+    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>, dim3(grid), dim3(kThreads), smem, s, a, b, c,
+                      args);
 }
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
@@ -1245,9 +1261,13 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
     if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
+    // two stacked 128-pixel sub-tiles per tile (sharing each stage's weights): the decoders' stride-1
+    // 128 -> 128 layers with NHWC bf16 outputs
+    const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.stride == 1 && d.groups > 1 &&
+                    d.kmask == 0) ? 2 : 1;
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
-    a.tiles_h = (Ho + a.TH - 1) / a.TH;
+    a.tiles_h = (Ho + a.TH * MT - 1) / (a.TH * MT);
     a.n_tiles = d.cout_pad / BN;
     a.groups = d.groups;
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
@@ -1290,7 +1310,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t dims[4] = {(cuuint64_t)d.Cin, (cuuint64_t)d.W, (cuuint64_t)d.H, (cuuint64_t)G};
         cuuint64_t str[3] = {d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz, (cuuint64_t)d.H * d.W * d.Cin * esz};
         if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
-        cuuint32_t box[4] = {boxc, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+        cuuint32_t box[4] = {boxc, (cuuint32_t)a.TW, (cuuint32_t)(a.TH * MT), 1};
         if (halo) { box[1] = 130; box[2] = 1; }
         ok = encode_map(&ma, d.in, 4, dims, str, box, dt, swz);
     } else {
@@ -1356,7 +1376,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         switch (BN) {
             case 64: return a.kmask != ~0ull ? launch_bn<64, 6, true, OP_BF16, true>(ma, mb, mc, a, s)
                                              : launch_bn<64, 6, true>(ma, mb, mc, a, s);
-            case 128: return launch_bn<128, 4, true>(ma, mb, mc, a, s);
+            case 128: return MT == 2 ? launch_bn<128, 3, true, OP_BF16, false, 2>(ma, mb, mc, a, s)
+                                     : launch_bn<128, 4, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
             default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);
         }
