@@ -1,5 +1,6 @@
 """Benchmark: 1080p 8-frame chunk encode + decode through libufvc (one step = one chunk encoded and
-decoded: pack, analysis + cross-frame interaction, hyper-analysis, z^, hyper-synthesis, quantise +
+decoded: frame bytes -> first analysis layer (read by its own kernel in BF16), analysis + cross-frame
+interaction, hyper-analysis, z^, hyper-synthesis, quantise +
 scale index, both rANS sections, bit-stream layout; header/lane parse, z^ decode, hyper-synthesis,
 scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 frames).
 
