@@ -1261,10 +1261,12 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
     if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
-    // two stacked 128-pixel sub-tiles per tile (sharing each stage's weights): the decoders' stride-1
-    // 128 -> 128 layers with NHWC bf16 outputs
-    const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.stride == 1 && d.groups > 1 &&
-                    d.kmask == 0) ? 2 : 1;
+    // two stacked 128-pixel sub-tiles per tile (sharing each stage's weights): the 128-output layers with
+    // NHWC bf16 outputs that keep at least two such tiles per SM (decoder R1, encoder A2 at video sizes;
+    // small layers such as H1 or the mean network would leave SMs idle)
+    const long long pairs = (long long)((Wo + a.TW - 1) / a.TW) * ((Ho + 2 * a.TH - 1) / (2 * a.TH)) *
+                            (d.cout_pad / 128) * d.groups;
+    const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.kmask == 0 && pairs >= 2 * 148) ? 2 : 1;
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
     a.tiles_h = (Ho + a.TH * MT - 1) / (a.TH * MT);
@@ -1317,7 +1319,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
         cuuint64_t str[4] = {d.Cin * esz, 2 * d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz,
                              2ull * d.W * d.Cin * esz};
-        cuuint32_t box[5] = {boxc, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
+        cuuint32_t box[5] = {boxc, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)(a.TH * MT)};
         ok = encode_map(&ma, d.in, 5, dims, str, box, dt, swz);
     }
     if (!ok) return cudaErrorInvalidValue;
