@@ -514,6 +514,12 @@ static int simt_plan(const ConvDesc& d, int* KS) {
         // thread, K split into as many ranges as one wave of three CTAs per SM holds
         const long long ctas = ((M + 63) / 64) * (d.Cout / 128) * d.groups;
         long long ks = 3 * 148 / ctas;
+        if (ks == 0 && nsteps16 >= 2) {
+            // more than one wave (S3 at 1080p: 512 CTAs on 444 slots): halve K when the half-work CTAs pack
+            // the waves tighter (3 waves of half the work against 2 of the whole)
+            const long long slots = 3 * 148, w1 = (ctas + slots - 1) / slots, w2 = (2 * ctas + slots - 1) / slots;
+            if (w2 < 2 * w1) ks = 2;
+        }
         if (ks > 16) ks = 16;
         if (ks > nsteps16) ks = nsteps16;
         *KS = (int)(ks < 1 ? 1 : ks);
