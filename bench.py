@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -57,9 +58,8 @@ class ClockSampler:
 
     def __init__(self, device: int):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ufvc_bench_clocks_{os.getpid()}_{device}.csv")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(device), "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
@@ -93,47 +93,81 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline() -> dict:
-    """The FP64 oracle, as it stands, on a bounded sample: the same 8-frame chunk cropped to a window of
-    the 1080p frames, encoded and decoded; frames/s scaled to the full 1080p area (the oracle's cost is
-    proportional to the pixel count)."""
+CROP_H, CROP_W = 256, 384
+CROP_WORKLOAD = f"{CROP_W}x{CROP_H} crop (top-left) of the 1080p 8-frame chunk, arch 1, K=4096 rANS lanes, qp=32"
+
+
+def oracle_crop_step() -> tuple[float, float]:
+    """One encode + decode of the crop by the FP64 oracle; returns (encode s, decode s)."""
     import oracle
     import synthetic
     frames = synthetic.chunk_frames("1080p", seed=0)
     blob = synthetic.draw_weights(1, N, seed=0)
-    oracle.build()
-    h, w = 256, 384
-    crop = np.ascontiguousarray(frames[:, :h, :w])
+    crop = np.ascontiguousarray(frames[:, :CROP_H, :CROP_W])
     t0 = time.perf_counter()
     bits = oracle.encode_chunk(1, crop, QP, K, blob)
     t1 = time.perf_counter()
-    oracle.decode_chunk(1, N, bits, h, w, blob)
+    oracle.decode_chunk(1, N, bits, CROP_H, CROP_W, blob)
+    return t1 - t0, time.perf_counter() - t1
+
+
+def cpu_baseline() -> dict:
+    """The FP64 oracle, as it stands, on the host cores: one whole 1080p 8-frame chunk encoded and
+    decoded with every OpenMP thread (measured, not scaled), plus the crop on one thread (scaled by area
+    to the full chunk, labelled as such) in a child process so the thread count can be set."""
+    import oracle
+    import synthetic
+    oracle.build()
+    frames = synthetic.chunk_frames("1080p", seed=0)
+    blob = synthetic.draw_weights(1, N, seed=0)
+    t0 = time.perf_counter()
+    bits = oracle.encode_chunk(1, frames, QP, K, blob)
+    t1 = time.perf_counter()
+    oracle.decode_chunk(1, N, bits, H, W, blob)
     t2 = time.perf_counter()
-    scale = (1088 * 1920) / (h * w)
-    t_chunk = (t2 - t0) * scale
-    return {"value": N / t_chunk, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one 8-frame chunk cropped to {w}x{h} (1/{scale:.1f} of the padded 1080p area), encode "
-                      f"{t1 - t0:.2f}s + decode {t2 - t1:.2f}s, scaled by area to a full 1080p chunk",
-            "enc_fps": N / ((t1 - t0) * scale), "dec_fps": N / ((t2 - t1) * scale)}
+    out = {"value": N / (t2 - t0), "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"one whole 1080p 8-frame chunk (1920x1080), encode {t1 - t0:.1f} s + decode {t2 - t1:.1f} s, "
+                     f"{oracle.num_threads()} OpenMP threads, measured",
+           "enc_fps": N / (t1 - t0), "dec_fps": N / (t2 - t1)}
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    code = "import bench, json; print(json.dumps(bench.oracle_crop_step()))"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=600)
+        te, td = json.loads(r.stdout.strip().splitlines()[-1])
+        area = (1088 * 1920) / (CROP_H * CROP_W)
+        out["single_core"] = {"value": N / ((te + td) * area), "unit": "frames/s", "cores": 1,
+                              "sample": f"{CROP_WORKLOAD}: encode {te:.2f} s + decode {td:.2f} s on one thread, "
+                                        f"scaled by the area ratio {area:.1f} to a full chunk"}
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError) as e:
+        out["single_core"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def run_reference(args) -> None:
+    """The reference arm: the FP64 oracle on the host cores, each step one encode + decode of the crop
+    (about 2 s on 16 threads, so K + W steps stay within minutes).  ms_per_step is the measured time of
+    a crop step; value converts it to full-chunk frames/s by the area ratio (the oracle's cost is
+    proportional to the pixel count: direct convolutions per output pixel, one rANS step per symbol)."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    vals = []
+    import oracle
+    oracle.build()
     for _ in range(args.warmup):
-        cpu_baseline()
-    cb = None
-    for _ in range(args.steps):
-        cb = cpu_baseline()
-        vals.append(cb["value"])
-    v = statistics.mean(vals)
+        oracle_crop_step()
+    steps = [sum(oracle_crop_step()) for _ in range(args.steps)]
+    t = statistics.mean(steps)
+    area = (1088 * 1920) / (CROP_H * CROP_W)
+    v = N / (t * area)
+    sample = f"{CROP_WORKLOAD}, encode + decode per step, {oracle.num_threads()} OpenMP threads"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * N / v, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64 oracle (CPU)"},
-            "cpu_baseline": {k: cb[k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "frames/s"},
+            "config": {"workload": sample, "precision": "fp64 oracle (CPU)",
+                       "value_basis": f"full 1080p chunk frames/s = 8 / (crop step time x area ratio {area:.1f})"},
+            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(), "sample": sample, "value": v,
+                             "unit": "frames/s"},
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -178,6 +212,94 @@ def conv_bytes(Hy: int, Wy: int, H_: int, W_: int) -> dict:
     a1, a2, a3 = N * 4 * Hy * Wy * 128 * 2, N * 16 * Hy * Wy * 64 * 2, N * 64 * Hy * Wy * 64 * 2
     return {"dec.D0": a0 + a1, "dec.R1": 2 * a1 + 3 * a1, "dec.U1": a1 + a2, "dec.R2": 2 * a2 + 3 * a2,
             "dec.U2": a2 + a3, "dec.U3": a3 + N * H_ * W_ * 3}
+
+
+def compute_peaks(pk: dict, precision: str) -> dict:
+    """Peaks each stage is measured against: tensor (burst bf16, x2 for E4M3 by the nominal ratio), FP32
+    ALU (148 SMs x 128 FMA/clk x 2 at the maximum SM clock, derived) and HBM (measured copy)."""
+    mhz = pk.get("sm_max_mhz", 2032.0)
+    src = pk["source"]
+    tens = pk["bf16_tflops"] * (2 if precision == "fp8" else 1)
+    return {"tensor": {"peak": tens, "unit": "TFLOP/s",
+                       "source": f"{src} bf16 burst" + (" x2 (fp8 nominal ratio)" if precision == "fp8" else "")},
+            "alu": {"peak": 148 * 128 * 2 * mhz * 1e6 / 1e12, "unit": "TFLOP/s",
+                    "source": f"derived: 148 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz"},
+            "hbm": {"peak": pk["hbm_gbs"], "unit": "GB/s", "source": f"{src} HBM copy"}}
+
+
+def stage_work(hy: int, wy: int, H_: int, W_: int, nbytes: int, lanes: int, precision: str) -> dict:
+    """Algorithmic work of one occurrence of every profiled stage of the plain model's step (arch 1, N
+    frames, latent hy x wy): {stage: {"flops": F, "flop_kind": "tensor"|"alu", "bytes": B, "lane_steps": S}}.
+    Bytes count every tensor a stage reads or writes once (activations bf16 on the tensor-core path, f32
+    on the FP32 path; y, mu, log sigma f32; r^ int16; indices u8; bit-stream words), FLOPs = 2 x MACs;
+    lane_steps = the longest lane's symbol count for the rANS stages."""
+    from synthetic.weights import layer_table
+    tab = {name: (co, k, ci) for name, co, k, ci in layer_table(1, N)}
+    Hp, Wp = -(-H_ // 16) * 16, -(-W_ // 16) * 16
+    h1, w1 = Hp // 2, Wp // 2
+    h2, w2, h3, w3 = h1 // 2, w1 // 2, h1 // 4, w1 // 4
+    hh, wh = -(-hy // 2), -(-wy // 2)
+    hz, wz = -(-hh // 2), -(-wh // 2)
+
+    def fl(name, h, w):
+        co, k, ci = tab[name]
+        return 2 * h * w * co * k * k * ci
+
+    a = 4 if precision == "fp32" else (1 if precision == "fp8" else 2)
+    kind = "alu" if precision == "fp32" else "tensor"
+    n, nz = hy * wy * 256, hz * wz * 128
+    e0, e1, e2 = 64, 128, 192
+    out = {
+        "A1": {"flops": fl("A1", h1, w1), "flop_kind": kind, "bytes": N * H_ * W_ * 3 + h1 * w1 * e0 * a},
+        "analysis": {"flops": fl("A2", h2, w2) + fl("A3", h3, w3) + fl("Xa", h3, w3) + fl("Xb", h3, w3)
+                     + fl("A4", hy, wy), "flop_kind": kind,
+                     "bytes": (h1 * w1 * e0 + h2 * w2 * e1 * 2 + h3 * w3 * e2 * 7) * a + n * 4},
+        "hyper_analysis": {"flops": fl("H1", hh, wh) + fl("H2", hz, wz), "flop_kind": kind,
+                           "bytes": n * 4 + n * a * 2 + hh * wh * 128 * a * 2 + nz * 4 + nz * 2},
+        "hyper_synthesis": {"flops": fl("S1", hz, wz) + fl("S2", 2 * hz, 2 * wz) + fl("S3", hy, wy),
+                            "flop_kind": "alu",
+                            "bytes": nz * 2 + 4 * hz * wz * 128 * 4 * 2 + 16 * hz * wz * 128 * 4 * 2 + n * 8},
+        "quantize": {"bytes": n * (4 + 4 + 4 + 2 + 1)},
+        "rans_encode": {"bytes": (n + nz) * 3 + nbytes, "lane_steps": -(-n // lanes)},
+        "bitstream": {"bytes": 2 * nbytes + 8 * lanes},
+        "parse": {"bytes": 4 * lanes + 4 * min(lanes, nz)},
+        "rans_decode_z": {"bytes": nz * 2 + 4096, "lane_steps": -(-nz // min(lanes, nz))},
+        "scale_index": {"bytes": n * (4 + 1)},
+        "rans_decode_y": {"bytes": nbytes + n * (1 + 2), "lane_steps": -(-n // lanes)},
+        "dequant": {"bytes": n * (2 + 4 + (4 if precision == "fp32" else a))},
+    }
+    cb = conv_bytes(hy, wy, H_, W_)
+    for k, f in conv_flops(hy, wy).items():
+        out[k] = {"flops": f, "flop_kind": kind, "bytes": cb[k] * (2 if precision == "fp32" else 1)}
+    return out
+
+
+def stage_roofline(stage_ms: dict, work: dict, pk: dict) -> dict:
+    """Each stage against its own bound: the compute peak of its kind or HBM, whichever its work takes
+    longer at.  ms = mean time of one occurrence (the hyper-synthesis runs once in each direction)."""
+    out = {}
+    for k, ms in stage_ms.items():
+        w = work.get(k)
+        if w is None:
+            continue
+        t = ms / 1000.0
+        tc = w.get("flops", 0) / (pk[w.get("flop_kind", "tensor")]["peak"] * 1e12)
+        tm = w["bytes"] / (pk["hbm"]["peak"] * 1e9)
+        if tc >= tm:
+            kind = w["flop_kind"]
+            ach = w["flops"] / t / 1e12
+            e = {"bound": kind, "achieved": ach, "peak": pk[kind]["peak"], "unit": "TFLOP/s",
+                 "frac": ach / pk[kind]["peak"], "algorithmic": w["flops"], "peak_source": pk[kind]["source"]}
+        else:
+            ach = w["bytes"] / t / 1e9
+            e = {"bound": "hbm", "achieved": ach, "peak": pk["hbm"]["peak"], "unit": "GB/s",
+                 "frac": ach / pk["hbm"]["peak"], "algorithmic": w["bytes"], "peak_source": pk["hbm"]["source"]}
+        e["ms"] = ms
+        e["floor_ms"] = 1000.0 * max(tc, tm)
+        if "lane_steps" in w:
+            e["lane_chain_ns_per_step"] = 1e6 * ms / w["lane_steps"]
+        out[k] = {kk: (round(vv, 5) if isinstance(vv, float) else vv) for kk, vv in e.items()}
+    return out
 
 
 def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, reps=5) -> dict:
@@ -228,8 +350,8 @@ def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, r
 
 
 # DRAM bytes per 1080p launch from one ncu capture of the SAME kernel build (dram__bytes_read.sum +
-# dram__bytes_write.sum on the 960x544 chunk, scaled by the 4x pixel count): profiles/<kernel>_<layer>_960x544.md.
-# An entry must be removed when its kernel changes.
+# dram__bytes_write.sum on the 960x544 chunk, scaled by the 4x pixel count).  An entry must be removed
+# when its kernel changes.
 NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.873536e6 + 73.990400e6), "dec.U3": 4 * (138.866688e6 + 6.584832e6)}
 
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
@@ -449,50 +571,40 @@ def main() -> None:
     frames_all, total_ms = shard.aggregate(N * args.steps, sum(t_step), dist if world > 1 else None, dev)
     value = frames_all / (total_ms / 1000.0)
 
-    # ---- dominant kernel roofline (per-stage events recorded inside the same timed steps)
+    # ---- roofline of every stage (per-stage events recorded inside the same timed steps) and of the
+    #      dominant kernel.  The step runs 2 ms at the maximum SM clock (sampled below), so the tensor
+    #      peak is the burst figure; the sustained one (a seconds-long GEMM loop at a power-capped clock) is
+    #      reported beside it.
     prof_acc = r["prof"]
     stage_ms = {k: statistics.mean(m for m, _ in v) for k, v in prof_acc.items()}
     stage_total_ms = {k: sum(m for m, _ in v) / args.steps for k, v in prof_acc.items()}
     launches_per_step = sum(sum(n for _, n in v) for v in prof_acc.values()) / args.steps
     hy, wy = -(-H_ // 16), -(-W_ // 16)
     flops = conv_flops(hy, wy)
-    cbytes = conv_bytes(hy, wy, H_, W_)
     conv_stages = {k: v for k, v in stage_ms.items() if k in flops}
     top = max(conv_stages, key=conv_stages.get)
     pk = peaks()
-    hbm = pk["hbm_gbs"]
-    if args.precision == "fp32":
-        peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        cbound, peak_src = "alu", f"derived: 148 SMs x 128 FP32 FMA/clk x 2 x {pk.get('sm_max_mhz', 2032.0):.0f} MHz"
-    else:
-        peak = pk["bf16_tflops_sustained"] if args.precision == "bf16" else 2 * pk["bf16_tflops_sustained"]
-        cbound = "tensor"
-        peak_src = f"{pk['source']} bf16 sustained" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")
-
-    def stage_roof(k: str) -> dict:
-        """A decoder conv stage against its own bound: compute or HBM, whichever takes longer at peak."""
-        t = conv_stages[k] / 1000.0
-        if flops[k] / (peak * 1e12) >= cbytes[k] / (hbm * 1e9):
-            return {"bound": cbound, "achieved": flops[k] / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": flops[k] / t / 1e12 / peak, "algorithmic": flops[k], "ms": conv_stages[k]}
-        return {"bound": "hbm", "achieved": cbytes[k] / t / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": cbytes[k] / t / 1e9 / hbm, "algorithmic": cbytes[k], "ms": conv_stages[k]}
-
-    stages = {k: stage_roof(k) for k in conv_stages}
+    peaks_used = compute_peaks(pk, args.precision)
+    stages = stage_roofline(stage_ms, stage_work(hy, wy, H_, W_, r["nbytes"], K, args.precision), peaks_used)
     kern = {"dec.U3": "conv_tc_final_kernel<1>", "dec.R2": "conv_tc_halo_kernel<64,2,1>"}
     tr = stages[top]
     dec_conv_ms = sum(v for k, v in stage_total_ms.items() if k in flops)
+    cpeak = peaks_used["tensor" if args.precision != "fp32" else "alu"]
     roofline = {"bound": tr["bound"], "kernel": (kern.get(top, "conv_tc_kernel") if args.precision != "fp32"
                                                  else "conv_simt") + f" ({top})",
                 "achieved": tr["achieved"], "peak": tr["peak"], "unit": tr["unit"], "frac": tr["frac"],
                 "traffic": NCU_TRAFFIC_1080P.get(top) if (W_, H_) == (W, H) and args.precision == "bf16" else None,
-                "traffic_unit": "bytes per launch", "peak_source": peak_src if tr["bound"] != "hbm" else f"{pk['source']} HBM copy",
-                "decoder_conv_stages": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv)
-                                            for kk, vv in v.items()} for k, v in stages.items()},
+                "traffic_unit": "bytes per launch", "peak_source": tr["peak_source"],
+                "per_launch": {"algorithmic": tr["algorithmic"], "ms": tr["ms"]},
+                "stage_roofline": stages,
                 "decoder_convs": {"tflops": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12,
-                                  "frac": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12 / peak},
+                                  "frac": sum(flops.values()) / (dec_conv_ms / 1000.0) / 1e12 / cpeak["peak"]},
                 "stage_ms_per_step": {k: round(v, 4) for k, v in
                                       sorted(stage_total_ms.items(), key=lambda kv: -kv[1])}}
+    if args.precision != "fp32":
+        sus = pk["bf16_tflops_sustained"] * (2 if args.precision == "fp8" else 1)
+        roofline["frac_of_sustained"] = tr["achieved"] / sus if tr["unit"] == "TFLOP/s" else None
+        roofline["sustained_peak"] = sus
 
     # ---- the FP32 path under the same methodology (the baseline the BF16 path must beat)
     fp32 = None
@@ -565,13 +677,14 @@ def main() -> None:
         fl = dc_flops(-(-H_ // 16), -(-W_ // 16))
         st_d = {k: round(sum(m for m, _ in v) / sdc, 4) for k, v in
                 sorted(rd["prof"].items(), key=lambda kv: -sum(m for m, _ in kv[1]))}
-        pk_dc = peaks()["bf16_tflops_sustained"]
+        pk_dc, pk_dc_sus = peaks()["bf16_tflops"], peaks()["bf16_tflops_sustained"]
         tf = (fl["enc"] + fl["dec"]) / ((t_enc + t_dec) / 1000.0) / 1e12
         dcx = {"value": N * sdc / (sum(a + b for a, b in zip(rd["t_enc"], rd["t_dec"])) / 1000.0),
                "enc_fps": N / (t_enc / 1000.0), "dec_fps": N / (t_dec / 1000.0), "psnr_db": rd["psnr"],
                "bytes_per_chunk": rd["nbytes"], "steps": sdc, "macs_per_frame_g": 205.3,
                "tensor_tflop_per_step": (fl["enc"] + fl["dec"]) / 1e12, "tensor_tflops": tf,
-               "tensor_frac_of_sustained": tf / pk_dc, "stage_ms_per_step": st_d}
+               "tensor_frac_of_burst": tf / pk_dc, "tensor_frac_of_sustained": tf / pk_dc_sus,
+               "stage_ms_per_step": st_d}
         cdc.close()
         if not args.no_fp32_path:  # the FP32 DC model on the same chunk sequence (3 context steps), one timed step
             c32 = U.Codec(2, N, K, synthetic.draw_dc_weights(N, seed=0), "fp32", device=local)

@@ -329,6 +329,28 @@ ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, 
 ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, int W, int stride, int act, int mode,
                             void* d_out, int out_h, int out_w, void* stream);
 
+/* Test hook for the timeout path of the entropy kernels (the paper has no counterpart: a library
+ * facility).  Every rANS encode and decode launch first copies the coding tables into shared memory and
+ * waits for the copy for a bounded time; `cycles` sets that bound in SM clocks (0 restores the default,
+ * about 2 s).  A wait that runs out records UFVC_ERR_TIMEOUT in the status word (ufvc_sync_status),
+ * the kernel returns without coding, an encoder's lanes are laid out empty, and the context stays usable.
+ * Synchronous, no device work. */
+ufvc_status ufvc_set_table_wait_limit(ufvc_ctx* ctx, long long cycles);
+
+/* The first analysis layer read straight from the frame bytes (the patch embedding of the stacked chunk,
+ * Sec. 3.1: frame n's three channels become channels 3n .. 3n+2 of one input, replicate-padded to a
+ * multiple of 16, then A1 = 3x3 stride-2 convolution + GELU), as the BF16 chunk encoder runs it: d_frames
+ * holds N frames in the context's colour format (RGB, YUV444P or YUV420P; YUV420 chroma repeated over
+ * its 2x2 block), d_out receives bf16 NHWC [ceil16(H)/2][ceil16(W)/2][64].  The bytes enter as v / 256
+ * (exact in bf16) and the bf16 weights carry 256 / 255, so the operands are bf16(w * 256 / 255) and
+ * v / 256.  kernel: 0 = the kernel the chunk encoder picks, 1 = the register-staged kernel (every
+ * format and width), 2 = the TMA-window kernel (interleaved RGB whose rows are a multiple of 16 bytes
+ * and start 16-byte aligned; UFVC_ERR_ARG otherwise).  UFVC_ERR_UNSUPPORTED for contexts whose first
+ * layer does not read the frame bytes (not BF16, an odd chunk length or one above 8, or BT.709 RGB
+ * input).  Asynchronous on `stream`; device-side errors go to the status word. */
+ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int kernel, void* d_out,
+                             void* stream);
+
 /* Allocation-free variant of ufvc_rans_encode (the paper has no counterpart: this is a library
  * facility).  Same arguments, same output bytes, same error reporting, but it never allocates:
  * ufvc_rans_encode may call cudaMalloc for its staging buffer, which callers capturing a stream, callers

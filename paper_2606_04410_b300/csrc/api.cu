@@ -126,6 +126,7 @@ struct ufvc_ctx {
     uint16_t* d_coarse = nullptr;
     float *d_thr = nullptr, *d_qstep = nullptr, *d_qinv = nullptr;
     int* d_status = nullptr;
+    long long table_spin = 0;  // bound on the entropy kernels' table-copy wait (clocks; 0: about 2 s)
     LayerW enc[L_NENC];
     LayerW dec[D_NDEC];
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
@@ -1066,7 +1067,7 @@ static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* fra
     // BF16 frames in RGB, YUV444 or YUV420 with even N <= 8: A1 reads the frame bytes itself (no pack pass)
     const bool first = ctx->first_w != nullptr && ctx->color != UFVC_COLOR_RGB_BT709;
     if (first) {
-        prof_begin(ctx, "analysis", s);
+        prof_begin(ctx, "A1", s);
         CK(launch_first_layer(frames, ctx->color, ctx->N, p->H, p->W, p->h1, p->w1, ctx->first_w, ctx->enc[L_A1].b,
                               reinterpret_cast<__nv_bfloat16*>(p->a1), ctx->d_status, s));
     } else {
@@ -1079,12 +1080,14 @@ static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* fra
             launch_pack_bf16(frames, ctx->N, p->H, p->W, p->Hp, p->Wp, p->C0p, reinterpret_cast<__nv_bfloat16*>(p->x), s,
                              s2d, ctx->color);
         prof_end(ctx, s, 1);
-        prof_begin(ctx, "analysis", s);
+        prof_begin(ctx, "A1", s);
         if (s2d)  // the same layer as a 2x2 stride-1 convolution over the space-to-depth input
             RUN(conv(ctx, ctx->a1s2d, p->x, p->Hp / 2, p->Wp / 2, 1, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
         else
             RUN(conv(ctx, ctx->enc[L_A1], p->x, p->Hp, p->Wp, 2, 1, OUT_NHWC, p->a1, p->h1, p->w1, s));
     }
+    prof_end(ctx, s, 1);
+    prof_begin(ctx, "analysis", s);
     probe(ctx, T_A1, p->a1, (size_t)p->h1 * p->w1 * a.e0, s);
     RUN(conv(ctx, ctx->enc[L_A2], p->a1, p->h1, p->w1, 2, 1, OUT_NHWC, p->a2, p->h2, p->w2, s));
     probe(ctx, T_A2, p->a2, (size_t)p->h2 * p->w2 * a.e1, s);
@@ -1101,7 +1104,7 @@ static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* fra
     RUN(conv(ctx, ctx->enc[L_A4], p->a3, p->h3, p->w3, 2, 0, OUT_NHWC, p->y, p->Hy, p->Wy, s, nullptr, nullptr, 0, 0, 0,
              0, 1, true));
     probe(ctx, T_Y, p->y, p->ny, s);
-    prof_end(ctx, s, 6);
+    prof_end(ctx, s, cin ? 6 : 5);
     return UFVC_OK;
 }
 
@@ -1226,7 +1229,7 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     RansSection secs[2];
     secs[0] = RansSection{p->zhat, p->iz, ctx->arch.cz, p->nz, p->Kz, p->scr_z, p->cap_z, p->cnt_z, ctx->d_status};
     secs[1] = RansSection{p->rhat, p->idx, 0, p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, p->cnt_y, ctx->d_status};
-    launch_rans_encode(secs, 2, ctx->d_packed, s);
+    launch_rans_encode(secs, 2, ctx->d_packed, s, ctx->table_spin);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "bitstream", s);
     launch_write_header(d_bits, 1 + (ctx->pm_on ? 1 : 0) + (ctx->tc_on ? 2 : 0), ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz,
@@ -1262,7 +1265,7 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     launch_rans_parse_expect(jy, nbytes, d_nbytes, ctx->d_status, s);
     prof_end(ctx, s, 3);
     prof_begin(ctx, "rans_decode_z", s);
-    launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
+    launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
     prof_end(ctx, s, 1);
     ctx->cur_ws = &p->ws_dec;
     const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
@@ -1271,19 +1274,18 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode_y", s);
-    launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
-    if (ctx->pm_on) {  // a version-1 stream leaves the means of the single pass (the steps check the version)
-        prof_end(ctx, s, 1);
+    launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
+    prof_end(ctx, s, 1);
+    if (ctx->pm_on)  // a version-1 stream leaves the means of the single pass (the steps check the version)
         RUN(run_progressive(ctx, p->Hy, p->Wy, nullptr, p->drhat, p->dmu, p->ds2, p->qp_dev, 0, p->ver_dev, p->pm_in_d,
                             p->pm_h_d, p->pm_mu_d, s));
-        prof_begin(ctx, "dequant", s);
-    }
+    prof_begin(ctx, "dequant", s);
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
                    fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
                    fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
     if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
-    prof_end(ctx, s, ctx->pm_on ? 1 : 2);
+    prof_end(ctx, s, 1);
     const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
     if (ctx->dcm) {  // chunk decoder, frame decoders, then the context generation in place on F
         RUN(run_dc_trunk(ctx, p, yh, cin, p->dc_F, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
@@ -1656,6 +1658,33 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
     return UFVC_OK;
 }
 
+extern "C" ufvc_status ufvc_set_table_wait_limit(ufvc_ctx* ctx, long long cycles) {
+    if (!ctx || cycles < 0) return fail(ctx, UFVC_ERR_ARG, "set_table_wait_limit: bad argument");
+    ctx->table_spin = cycles;
+    return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int kernel,
+                                        void* d_out, void* stream) {
+    if (!ctx || !d_frames || !d_out || width < 1 || height < 1 || width > 65535 || height > 65535 || kernel < 0 ||
+        kernel > 2)
+        return fail(ctx, UFVC_ERR_ARG, "first_layer: bad argument");
+    if (!ctx->first_w || ctx->color == UFVC_COLOR_RGB_BT709)
+        return fail(ctx, UFVC_ERR_UNSUPPORTED,
+                    "first_layer: this context's first layer does not read frame bytes (needs BF16, an even chunk "
+                    "length of at most 8 and colour format RGB, YUV444P or YUV420P)");
+    if (kernel == 2 && !first_layer_tma_ok(ctx->color, width, d_frames))
+        return fail(ctx, UFVC_ERR_ARG,
+                    "first_layer: the TMA kernel needs interleaved RGB frames with rows of a multiple of 16 bytes "
+                    "at a 16-byte aligned address");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int Ho = conv_out(ceil_div(height, 16) * 16, 3, 2), Wo = conv_out(ceil_div(width, 16) * 16, 3, 2);
+    CK(launch_first_layer(d_frames, ctx->color, ctx->N, height, width, Ho, Wo, ctx->first_w, ctx->enc[L_A1].b,
+                          static_cast<__nv_bfloat16*>(d_out), ctx->d_status, (cudaStream_t)stream, kernel));
+    CK(cudaGetLastError());
+    return UFVC_OK;
+}
+
 static ufvc_status ensure_rans_scratch(ufvc_ctx* ctx, size_t words, size_t lanes) {
     if (words > ctx->r_scr_words) {
         cudaFree(ctx->r_scr);
@@ -1690,7 +1719,7 @@ extern "C" ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, con
     RansSection sec{d_sym, d_idx, 0, n, lanes, ctx->r_scr, cap_lane, ctx->r_cnt, ctx->d_status};
 
     prof_begin(ctx, "rans_encode", s);
-    launch_rans_encode(&sec, 1, ctx->d_packed, s);
+    launch_rans_encode(&sec, 1, ctx->d_packed, s, ctx->table_spin);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_finalize", s);
     launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, ctx->r_off, ctx->d_status, s);
@@ -1715,7 +1744,7 @@ extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size
     launch_rans_parse(j, ctx->d_status, s);
     prof_end(ctx, s, 1);
     prof_begin(ctx, "rans_decode", s);
-    launch_rans_decode(j, ctx->d_packed, ctx->d_coarse, ctx->d_status, s);
+    launch_rans_decode(j, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
     prof_end(ctx, s, 1);
     CK(cudaGetLastError());
     return UFVC_OK;
@@ -1761,6 +1790,7 @@ extern "C" ufvc_status ufvc_get_profile(ufvc_ctx* ctx, char* names, float* ms, i
 // ------------------------------------------------------------------------------------------------
 namespace ufvc {
 const uint32_t* ctx_packed_tables(const ufvc_ctx* c) { return c->d_packed; }
+long long ctx_table_spin(const ufvc_ctx* c) { return c->table_spin; }
 bool ctx_temporal(const ufvc_ctx* c) { return c->tc_on; }
 int* ctx_status_word(ufvc_ctx* c) { return c->d_status; }
 int ctx_device(const ufvc_ctx* c) { return c->cfg.device; }

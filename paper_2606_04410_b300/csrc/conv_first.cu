@@ -544,16 +544,9 @@ static cudaError_t launch_first_tma_t(const uint8_t* frames, int N, int H, int W
                                       const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s) {
     alignas(64) CUtensorMap map;
     if (!encode_frames_map(&map, frames, N, H, 3 * W, kRawBX, kW4H)) return cudaErrorInvalidValue;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(conv_first_tma_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)first_tma_smem(CT, 8));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = smem_optin((const void*)conv_first_tma_kernel<CT>, (int)first_tma_smem(CT, 8));
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const int tiles = ((Wo + kT4W - 1) / kT4W) * ((Ho + kT4H - 1) / kT4H);
     const int grid = tiles < sms ? tiles : sms;
     return launch_pdl(conv_first_tma_kernel<CT>, dim3(grid), dim3(kTmaThreads), first_tma_smem(CT, N), s, map, N, H,
@@ -564,16 +557,9 @@ template <int FMT, int CT>
 static cudaError_t launch_first_t(const uint8_t* frames, int N, int H, int W, int Ho, int Wo, const void* wimg,
                                   const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s) {
     const size_t smem = first_reg_smem(CT);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(conv_first_kernel<FMT, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = smem_optin((const void*)conv_first_kernel<FMT, CT>, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const int tiles = ((Wo + kT4W - 1) / kT4W) * ((Ho + kT4H - 1) / kT4H);
     const int grid = tiles < sms ? tiles : sms;
     return launch_pdl(conv_first_kernel<FMT, CT>, dim3(grid), dim3(kRegThreads), smem, s, frames, N, H, W, Ho, Wo,
@@ -601,10 +587,16 @@ void first_layer_weights(const float* w, int n_frames, float scale, int pitch, u
             }
 }
 
+bool first_layer_tma_ok(int fmt, int W, const void* frames) {
+    return fmt == 0 && (3 * W) % 16 == 0 && (reinterpret_cast<uintptr_t>(frames) & 15) == 0;
+}
+
 cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s) {
+                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s, int sel) {
     const int ct = first_layer_ct(N);
-    if (fmt == 0 && (3 * W) % 16 == 0 && (reinterpret_cast<uintptr_t>(frames) & 15) == 0) {
+    const bool tma = first_layer_tma_ok(fmt, W, frames);
+    if (sel == 2 && !tma) return cudaErrorInvalidValue;
+    if (tma && sel != 1) {
         switch (ct) {  // whole 16-byte rows: the window comes by TMA
             case 8: return launch_first_tma_t<8>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);
             case 16: return launch_first_tma_t<16>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);

@@ -1108,19 +1108,9 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
     constexpr int kSmem = STAGES * (128 * MT * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 * EG : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
-    static int configured_smem = 0;
-    if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured_smem = smem;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    cudaError_t e = smem_optin((const void*)conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>, smem);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
     return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>, dim3(grid), dim3(kThreads), smem, s, a, b, c,
                       args);
@@ -1135,19 +1125,9 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
     constexpr int kSmem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + C_BYTES + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
-    static int configured_smem = 0;
-    if (configured_smem != smem) {
-        cudaError_t e = cudaFuncSetAttribute(conv_tc_halo_kernel<BN, STAGES, OUTK>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured_smem = smem;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    cudaError_t e = smem_optin((const void*)conv_tc_halo_kernel<BN, STAGES, OUTK>, smem);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
     return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
@@ -1157,19 +1137,9 @@ static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, cons
                                 cudaStream_t s) {
     constexpr int kSmem = 128 * 128 + 8 * 128 * 128 + (OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-    static int configured_smem = 0;
-    if (configured_smem != kSmem) {
-        cudaError_t e =
-            cudaFuncSetAttribute(conv_tc_final_kernel<OUTK>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess) return e;
-        configured_smem = kSmem;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    cudaError_t e = smem_optin((const void*)conv_tc_final_kernel<OUTK>, kSmem);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
     return launch_pdl(conv_tc_final_kernel<OUTK>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, args);
 }

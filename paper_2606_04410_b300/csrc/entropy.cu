@@ -464,7 +464,7 @@ void launch_f32_to_bf16_rows(const float* a, int H, int W, int C, __nv_bfloat16*
 // elements backwards (last first) and writes its words backwards into its scratch row, so that the
 // row's tail [cap_lane - words, cap_lane) is the lane stream in decoding order.
 // ------------------------------------------------------------------------------------------------
-struct RansSecPair { RansSection s[2]; int nsec; };
+struct RansSecPair { RansSection s[2]; int nsec; long long spin; };
 
 // Lanes per block: small blocks spread the lanes over the SMs (each block holds its own copy of the
 // tables), so that the lanes' dependent chains do not queue behind each other on one SM's shared
@@ -495,10 +495,13 @@ constexpr int kPF = 16;                            // per-lane prefetch depth (s
 constexpr long long kLoadSpin = 4000000000LL;      // ~2 s bounded wait for the table copy
 
 // The packed tables (and optionally the coarse decoding index) land in shared memory by TMA bulk copies
-// issued by one thread; every thread waits on the copy's mbarrier, bounded in time.  Returns false (and
-// records UFVC_ERR_TIMEOUT) if the copy did not complete.
+// issued by one thread; every thread waits on the copy's mbarrier for at most `spin` clocks (0: about
+// 2 s).  Returns false (and records UFVC_ERR_TIMEOUT) if the copy did not complete in time; the issuing
+// thread then waits once more, for at most about 2 s, for its copies in flight before the block exits.
 __device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __restrict__ tables, uint16_t* coarse,
-                                            const uint16_t* __restrict__ coarse_g, uint64_t* bar, int* status) {
+                                            const uint16_t* __restrict__ coarse_g, uint64_t* bar, int* status,
+                                            long long spin) {
+    if (spin <= 0) spin = kLoadSpin;
     if (threadIdx.x == 0) {
         ptx::mbar_init(bar, 1);
         ptx::fence_mbar_init();
@@ -519,7 +522,7 @@ __device__ __forceinline__ bool load_tables(uint32_t* tab, const uint32_t* __res
     }
     const long long t0 = clock64();
     while (!ptx::mbar_try_wait(bar, 0)) {
-        if (clock64() - t0 > kLoadSpin) {
+        if (clock64() - t0 > spin) {
             set_status(status, UFVC_ERR_TIMEOUT);
             if (threadIdx.x == 0) {  // the issuing thread waits once more, bounded, for its copies in flight
                 const long long t1 = clock64();
@@ -541,15 +544,22 @@ __global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const Rans
                                                                    const uint32_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum
     __shared__ uint64_t bar;
-    if (!load_tables(tab, tables, nullptr, nullptr, &bar, P.s[0].status)) return;
-    pdl_trigger();  // the tables above are constants: loaded while the previous kernel finishes
-    pdl_wait();
     int lane = blockIdx.x * blockDim.x + threadIdx.x;
     int si = 0;
     if (lane >= P.s[0].K) { lane -= P.s[0].K; si = 1; }
-    if (si >= P.nsec) return;
+    const bool mine = si < P.nsec && lane < P.s[si].K;
+    if (!load_tables(tab, tables, nullptr, nullptr, &bar, P.s[0].status, P.spin)) {
+        // no words for this lane: a zero count, which the layout kernels refuse to copy
+        if (mine) {
+            pdl_wait();
+            P.s[si].counts[lane] = 0;
+        }
+        return;
+    }
+    pdl_trigger();  // the tables above are constants: loaded while the previous kernel finishes
+    pdl_wait();
+    if (!mine) return;
     const RansSection& S = P.s[si];
-    if (lane >= S.K) return;
     const size_t n = S.n;
     const int K = S.K, per = S.idx_period;
     const int cnt = (size_t)lane < n ? (int)((n - lane + K - 1) / K) : 0;
@@ -617,16 +627,14 @@ __global__ void __launch_bounds__(kRansThreadsEnc) rans_encode_kernel(const Rans
     S.counts[lane] = (uint32_t)(S.cap_lane - wp);
 }
 
-void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s) {
+void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s,
+                        long long spin) {
     RansSecPair P{};
     P.nsec = nsec;
+    P.spin = spin;
     int total = 0;
     for (int i = 0; i < nsec; ++i) { P.s[i] = secs[i]; total += secs[i].K; }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(rans_encode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTabBytes);
-        attr = true;
-    }
+    (void)smem_optin((const void*)rans_encode_kernel, kTabBytes);
     (void)launch_pdl(rans_encode_kernel, dim3((total + kRansThreadsEnc - 1) / kRansThreadsEnc), dim3(kRansThreadsEnc), (size_t)(kTabBytes), s, P, packed_tables);
 }
 
@@ -654,14 +662,26 @@ __global__ void __launch_bounds__(kScanThreads) rans_finalize_kernel(const RansS
         const int K = S.K;
         const int per = (K + kScanThreads - 1) / kScanThreads;
         const int j0 = threadIdx.x * per;
+        // a lane holds 2 .. cap_lane words; any other count comes from a lane whose encoder stopped early
+        // (its table copy timed out): it is laid out as empty and reported
+        auto count = [&](int j) -> uint32_t {
+            const uint32_t c = S.counts[j];
+            return c >= 2 && c <= (uint32_t)S.cap_lane ? c : 0u;
+        };
         unsigned long long local = 0;
-        for (int j = j0; j < j0 + per && j < K; ++j) local += S.counts[j];
+        bool bad = false;
+        for (int j = j0; j < j0 + per && j < K; ++j) {
+            const uint32_t c = count(j);
+            bad |= c == 0;
+            local += c;
+        }
+        if (bad) set_status(status, UFVC_ERR_TIMEOUT);
         unsigned long long excl, total;
         BlockScanU64(tmp).ExclusiveSum(local, excl, total);
         const unsigned long long base = base_sh;
         const unsigned long long words_at = base + 4ull * K;
         for (int j = j0; j < j0 + per && j < K; ++j) {
-            const uint32_t c = S.counts[j];
+            const uint32_t c = count(j);
             off_ws[ws_base + j] = words_at + 2ull * excl;
             excl += c;
             const size_t cp = base + 4ull * j;
@@ -696,6 +716,7 @@ __global__ void rans_copy_kernel(const RansSecPair P, uint8_t* out, size_t capac
     if (si >= P.nsec || lane >= P.s[si].K) return;
     const RansSection& S = P.s[si];
     const uint32_t words = S.counts[lane];
+    if (words < 2 || words > (uint32_t)S.cap_lane) return;  // reported by the finaliser
     const uint16_t* src = S.scratch + (size_t)lane * S.cap_lane + (S.cap_lane - words);
     const uint64_t dst = off_ws[ws + lane];
     if (dst + 2ull * words > capacity) return;  // status already records the capacity error
@@ -787,12 +808,13 @@ void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const u
 template <int LPT, bool PER>
 __global__ void __launch_bounds__(kRansThreadsDec) rans_decode_kernel(const RansDecodeJob J,
                                                                    const uint32_t* __restrict__ tables,
-                                                                   const uint16_t* __restrict__ coarse_g, int* status) {
+                                                                   const uint16_t* __restrict__ coarse_g, int* status,
+                                                                   long long spin) {
     extern __shared__ __align__(16) uint32_t tab[];                      // [64][511] (freq << 16) | cum
     uint16_t* coarse = reinterpret_cast<uint16_t*>(tab + kBins * kNsym);  // [64][kCoarse], then [64] end runs
     const uint32_t* runs = reinterpret_cast<const uint32_t*>(coarse + kBins * kCoarse);  // A | B << 16
     __shared__ uint64_t bar;
-    if (!load_tables(tab, tables, coarse, coarse_g, &bar, status)) return;
+    if (!load_tables(tab, tables, coarse, coarse_g, &bar, status, spin)) return;
     pdl_trigger();  // the tables above are constants: loaded while the previous kernel finishes
     pdl_wait();
     if (*(volatile int*)status != 0) return;
@@ -939,19 +961,15 @@ __global__ void __launch_bounds__(kRansThreadsDec) rans_decode_kernel(const Rans
 constexpr int kRansDecLPT = UFVC_RANS_DEC_LPT;  // lanes per decoding thread
 
 void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
-                        cudaStream_t s) {
+                        cudaStream_t s, long long spin) {
     const int smem = kTabBytes + kCoarseBytes;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(rans_decode_kernel<kRansDecLPT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(rans_decode_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    (void)smem_optin((const void*)rans_decode_kernel<kRansDecLPT, false>, smem);
+    (void)smem_optin((const void*)rans_decode_kernel<1, true>, smem);
     if (j.idx_period) {
-        (void)launch_pdl(rans_decode_kernel<1, true>, dim3((j.K + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status);
+        (void)launch_pdl(rans_decode_kernel<1, true>, dim3((j.K + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status, spin);
     } else {
         const int G = (j.K + kRansDecLPT - 1) / kRansDecLPT;
-        (void)launch_pdl(rans_decode_kernel<kRansDecLPT, false>, dim3((G + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status);
+        (void)launch_pdl(rans_decode_kernel<kRansDecLPT, false>, dim3((G + kRansThreadsDec - 1) / kRansThreadsDec), dim3(kRansThreadsDec), (size_t)(smem), s, j, packed_tables, coarse, status, spin);
     }
 }
 

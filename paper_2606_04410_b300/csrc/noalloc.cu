@@ -37,6 +37,13 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
         ufvc::ctx_set_error(ctx, "rans_encode_noalloc: bad argument");
         return UFVC_ERR_ARG;
     }
+    // n above half the array can never fit (two bytes per symbol); refusing it first also keeps the
+    // size arithmetic below from wrapping and the per-lane row length within an int
+    if (n > kScratchBytes / 2) {
+        ufvc::ctx_set_error(ctx, "rans_encode_noalloc: n exceeds the 24 MiB static scratch (at most about 12.5 "
+                                 "million symbols); use ufvc_rans_encode");
+        return UFVC_ERR_ARG;
+    }
     const size_t cap_lane = n / (size_t)lanes + 3;
     const size_t off_bytes = align256((size_t)lanes * 8), cnt_bytes = align256((size_t)lanes * 4);
     const size_t need = off_bytes + cnt_bytes + (size_t)lanes * cap_lane * 2;
@@ -71,8 +78,9 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
         }
         base = g_scratch_addr[dev];
     }
-    // Nothing in the scratch is read before this call writes it (each lane writes its count and the
-    // words it later copies; the finaliser writes every offset), so no part needs clearing.
+    // Nothing in the scratch is read before this call writes it (each lane writes its count -- zero if
+    // its table copy timed out, which the layout kernels refuse -- and the words it later copies; the
+    // finaliser writes every offset), so no part needs clearing.
     unsigned char* b = static_cast<unsigned char*>(base);
     uint64_t* offsets = reinterpret_cast<uint64_t*>(b);
     uint32_t* counts = reinterpret_cast<uint32_t*>(b + off_bytes);
@@ -80,7 +88,7 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int* status = ufvc::ctx_status_word(ctx);
     ufvc::RansSection sec{d_sym, d_idx, 0, n, lanes, rows, (int)cap_lane, counts, status};
-    ufvc::launch_rans_encode(&sec, 1, ufvc::ctx_packed_tables(ctx), s);
+    ufvc::launch_rans_encode(&sec, 1, ufvc::ctx_packed_tables(ctx), s, ufvc::ctx_table_spin(ctx));
     ufvc::launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, offsets, status, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) {

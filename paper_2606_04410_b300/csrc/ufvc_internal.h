@@ -82,6 +82,12 @@ __device__ __forceinline__ void px_bytes(const uint8_t* __restrict__ fr, int n, 
     }
 }
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) applies to the current device only.  smem_optin sets it
+// for `func` on the current device the first time a size at least `bytes` is needed there (thread-safe;
+// one record per kernel and device).  sm_count caches the SM count of the current device.
+cudaError_t smem_optin(const void* func, int bytes);
+int sm_count();
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args&&... args) {
@@ -233,8 +239,11 @@ int first_layer_pitch(int n_frames);
 size_t first_layer_weight_bytes(int pitch);
 void first_layer_weights(const float* w, int n_frames, float scale, int pitch, uint16_t* img);
 bool encode_frames_map(void* map, const void* frames, int N, int H, int row_bytes, int box_x, int box_y);
+// sel: 0 = the kernel the chunk path picks (TMA windows where first_layer_tma_ok), 1 = the register-staged
+// kernel, 2 = the TMA kernel (cudaErrorInvalidValue where first_layer_tma_ok is false)
+bool first_layer_tma_ok(int fmt, int W, const void* frames);
 cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s);
+                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s, int sel = 0);
 // colour interface, output side (color.cu): x^ float [N][H][W][3] -> the caller's format (fmt 1..3), float
 // or uint8; frame_bytes = bytes of one frame in format fmt
 size_t frame_bytes(int fmt, int W, int H);
@@ -273,7 +282,9 @@ struct RansSection {
     uint32_t* counts;         // [K] word counts
     int* status;              // device status word (caller errors: symbol / index out of range)
 };
-void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s);
+// spin: bound on the wait for the table copy in SM clocks (0: about 2 s); see ufvc_set_table_wait_limit
+void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s,
+                        long long spin = 0);
 
 // Lay out one or two encoded sections after `hdr_bytes` of header in `out`: write lane counts, copy the
 // words, write the total size to *nbytes.  Capacity violations set *status = UFVC_ERR_CAPACITY.
@@ -302,7 +313,7 @@ void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s);
 void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const uint64_t* expect_end_dev, int* status,
                               cudaStream_t s);
 void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
-                        cudaStream_t s);
+                        cudaStream_t s, long long spin = 0);
 // y^ = r^ q + mu with q = qstep_all[*qp_dev] (qp_dev null: qstep_all[qp_host]); yf and / or yb may be null
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
                     float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f,
@@ -337,6 +348,7 @@ void launch_pm_step(int k, const float* y, int16_t* rhat, float* mu, const float
 // context internals for other translation units (defined in api.cu)
 namespace ufvc {
 const uint32_t* ctx_packed_tables(const ufvc_ctx* c);
+long long ctx_table_spin(const ufvc_ctx* c);
 int* ctx_status_word(ufvc_ctx* c);
 int ctx_device(const ufvc_ctx* c);
 void ctx_set_error(ufvc_ctx* c, const char* msg);

@@ -38,7 +38,8 @@ EXPORTS = [
     "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
     "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
     "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means", "ufvc_pipe_create",
-    "ufvc_pipe_submit", "ufvc_pipe_wait", "ufvc_pipe_destroy",
+    "ufvc_pipe_submit", "ufvc_pipe_wait", "ufvc_pipe_destroy", "ufvc_first_layer",
+    "ufvc_set_table_wait_limit",
 ]
 COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
@@ -86,6 +87,8 @@ _sigs = {
     "ufvc_get_profile": (_i, [_vp, _vp, _vp, _vp, _i, C.POINTER(_i)]),
     "ufvc_last_error": (C.c_char_p, [_vp]),
     "ufvc_conv_layer": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp]),
+    "ufvc_first_layer": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp]),
+    "ufvc_set_table_wait_limit": (_i, [_vp, C.c_longlong]),
     "ufvc_decode_chunk_dev": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _vp]),
     "ufvc_server_create": (_i, [C.POINTER(ufvc_config), _vp, _sz, _sz, _i, C.POINTER(_vp)]),
     "ufvc_server_destroy": (None, [_vp]),
@@ -409,6 +412,17 @@ class Codec:
         self._check(lib.ufvc_conv_layer(self.h, layer, _ptr(x), H, W, stride, act, mode, _ptr(out), oh, ow,
                                         _stream(stream)), "conv_layer")
         return out
+
+    def first_layer(self, frames: torch.Tensor, width: int, height: int, kernel: int = 0, stream=None) -> torch.Tensor:
+        """A1 from the frame bytes: bf16 [ceil16(H)/2][ceil16(W)/2][64] (kernel 0 auto, 1 register, 2 TMA)."""
+        out = torch.empty(((height + 15) // 16 * 8, (width + 15) // 16 * 8, 64), dtype=torch.bfloat16,
+                          device=frames.device)
+        self._check(lib.ufvc_first_layer(self.h, _ptr(frames), width, height, kernel, _ptr(out), _stream(stream)),
+                    "first_layer")
+        return out
+
+    def set_table_wait_limit(self, cycles: int):
+        self._check(lib.ufvc_set_table_wait_limit(self.h, int(cycles)), "set_table_wait_limit")
 
     def get_tables(self, qp: int = 32):
         freq = np.empty((64, 511), np.uint32)

@@ -178,7 +178,7 @@ def test_bf16_chunk(arch, N, H, W, K):
     # 0.0053 measured at 200x328); these bounds only guard against regressions.  The targets are the
     # PSNR and bitrate deltas.
     assert err_oracle < 0.15
-    assert report["y_err_vs_oracle"] < 0.1  # latent after the bf16 analysis (0.012-0.022 measured)
+    assert report["y_err_vs_oracle"] < 0.045  # latent after the bf16 analysis (0.012-0.022 measured)
     assert report["recon_rms_vs_oracle"] < 1.5e-2
     assert abs(report["dpsnr"]) < 0.05
     assert abs(report["dbitrate"]) < 0.005 + 64.0 / n32

@@ -59,3 +59,35 @@ def test_noalloc_rejects_oversize_request():
                                         u._ptr(nb), u._stream(None))
     assert rc == u.UFVC_ERR_ARG
     assert b"static scratch" in u.lib.ufvc_last_error(codec.h)
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """After one warm-up call on a fresh context (the first call on a device looks up the array's
+    address), further calls change the device's free memory by nothing: no cudaMalloc behind them."""
+    from paper_2606_04410_b300 import ufvc as u
+    codec = u.Codec(0, 1, 32, synthetic.draw_weights(0, 1), "fp32")
+    n, K = 2_088_960, 4096
+    r, b = synthetic.laplace_symbols(n, seed=21)
+    idx = np.clip(np.rint((np.log(b) - np.log(0.11)) / ((np.log(64.0) - np.log(0.11)) / 63)), 0, 63)
+    sym = torch.from_numpy(r).cuda()
+    it = torch.from_numpy(idx.astype(np.uint8)).cuda()
+    cap = 4 * K + 2 * (n + 2 * K) + 4
+    outs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    nbs = [torch.zeros(1, dtype=torch.int64, device="cuda") for _ in range(3)]
+
+    def call(i):
+        rc = u.lib.ufvc_rans_encode_noalloc(codec.h, u._ptr(sym), u._ptr(it), n, K, u._ptr(outs[i]), cap,
+                                            u._ptr(nbs[i]), u._stream(None))
+        assert rc == u.UFVC_OK, u.lib.ufvc_last_error(codec.h)
+
+    call(0)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    call(1)
+    call(2)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert codec.sync_status() == 0
+    assert free1 == free0
+    n0 = int(nbs[0].item())
+    assert int(nbs[2].item()) == n0 and torch.equal(outs[2][:n0], outs[0][:n0])
