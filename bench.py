@@ -260,12 +260,14 @@ def stage_work(hy: int, wy: int, H_: int, W_: int, nbytes: int, lanes: int, prec
                             "flop_kind": "alu",
                             "bytes": nz * 2 + 4 * hz * wz * 128 * 4 * 2 + 16 * hz * wz * 128 * 4 * 2 + n * 8},
         "quantize": {"bytes": n * (4 + 4 + 4 + 2 + 1)},
+        # both sections coded, laid out and the header written: symbols + indices in, the stream out
         "rans_encode": {"bytes": (n + nz) * 3 + nbytes, "lane_steps": -(-n // lanes)},
-        "bitstream": {"bytes": 2 * nbytes + 8 * lanes},
-        "parse": {"bytes": 4 * lanes + 4 * min(lanes, nz)},
-        "rans_decode_z": {"bytes": nz * 2 + 4096, "lane_steps": -(-nz // min(lanes, nz))},
+        # header + lane counts checked, z^ decoded
+        "rans_decode_z": {"bytes": nz * 2 + 4 * min(lanes, nz) + 4096, "lane_steps": -(-nz // min(lanes, nz))},
         "scale_index": {"bytes": n * (4 + 1)},
-        "rans_decode_y": {"bytes": nbytes + n * (1 + 2), "lane_steps": -(-n // lanes)},
+        # stream + indices + mu in, y^ = r^ q + mu out (activation type)
+        "rans_decode_y": {"bytes": nbytes + n * (1 + 4 + (4 if precision == "fp32" else a)),
+                          "lane_steps": -(-n // lanes)},
         "dequant": {"bytes": n * (2 + 4 + (4 if precision == "fp32" else a))},
     }
     cb = conv_bytes(hy, wy, H_, W_)

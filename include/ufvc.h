@@ -353,16 +353,17 @@ ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, int width, 
 
 /* Allocation-free variant of ufvc_rans_encode (the paper has no counterpart: this is a library
  * facility).  Same arguments, same output bytes, same error reporting, but it never allocates:
- * ufvc_rans_encode may call cudaMalloc for its staging buffer, which callers capturing a stream, callers
- * in real-time loops that cannot absorb the implicit device synchronisation, and callers whose device
- * memory belongs to their own pool allocator cannot accept.  The staging space is one fixed 24 MiB
- * array per device, held by every GPU that loads this library until the process exits; a call needs
- * 8 * lanes + 4 * lanes + 2 * lanes * (n / lanes + 3) bytes of it (each part rounded up to 256), which
- * allows roughly 12.5 million symbols, and returns UFVC_ERR_ARG (message in ufvc_last_error) beyond
- * that.  The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.  All calls on a device share
- * the array and it keeps the last call's contents (nothing in it needs to start at zero): calls whose
- * work can overlap on the GPU (different streams, or the same stream without ordering) race. */
+ * ufvc_rans_encode may call cudaMalloc for its staging rows, which callers in real-time loops that cannot
+ * absorb cudaMalloc's implicit device synchronisation, and callers whose device memory belongs to their
+ * own pool allocator, cannot accept.  The staging space is one fixed 24 MiB array per device, held by
+ * every GPU that loads this library until the process exits; a call needs 2304 bytes for its layout
+ * control block plus 2 * lanes * (n / lanes + 3) bytes of staging rows (rounded up to 256), which allows
+ * roughly 12.5 million symbols, and returns UFVC_ERR_ARG (message in ufvc_last_error) beyond that.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents; each call clears the control block on `stream` before its launch (a
+ * memset, not an allocation), and the rows need no clearing.  Calls whose work can overlap on the GPU
+ * (different streams, or the same stream without ordering) race. */
 ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t* d_idx, size_t n, int lanes,
                                      uint8_t* d_out, size_t capacity, uint64_t* d_nbytes, void* stream);
 

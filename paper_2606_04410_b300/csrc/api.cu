@@ -70,15 +70,14 @@ struct Plan {
           *z = nullptr, *zf = nullptr, *s1 = nullptr, *s2 = nullptr, *mu = nullptr, *ls = nullptr;
     int16_t *zhat = nullptr, *rhat = nullptr;
     uint8_t *iz = nullptr, *idx = nullptr;
-    uint16_t *scr_z = nullptr, *scr_y = nullptr;
-    uint32_t *cnt_z = nullptr, *cnt_y = nullptr;
-    uint64_t *off_ws = nullptr, *zthr = nullptr;
+    uint16_t *scr_z = nullptr, *scr_y = nullptr;  // rANS staging rows of the two sections
+    RansCtl* ctl = nullptr;                       // rANS layout control block (zero between launches)
+    uint64_t* zthr = nullptr;
     // decoder buffers
     int16_t *dzhat = nullptr, *drhat = nullptr;
-    uint8_t *diz = nullptr, *didx = nullptr;
+    uint8_t* didx = nullptr;
     int* qp_dev = nullptr;
-    uint64_t *lo_z = nullptr, *lo_y = nullptr, *next_z = nullptr, *next_y = nullptr;
-    uint32_t *lw_z = nullptr, *lw_y = nullptr;
+    uint64_t* next_z = nullptr;  // the byte after the z^ section
     float *dzf = nullptr, *ds1 = nullptr, *ds2 = nullptr, *dmu = nullptr, *dls = nullptr, *yhat = nullptr;
     __nv_bfloat16* yhat_bf = nullptr;
     // BF16 hyper-analysis inputs, rows and columns rounded up to even sizes (zero) for the stride-2 view
@@ -123,7 +122,7 @@ struct ufvc_ctx {
     int N = 0;
     HostTables tabs;
     uint32_t* d_packed = nullptr;
-    uint16_t* d_coarse = nullptr;
+    uint8_t* d_dec = nullptr;  // rANS decoding tables (build_decode_tables)
     float *d_thr = nullptr, *d_qstep = nullptr, *d_qinv = nullptr;
     int* d_status = nullptr;
     long long table_spin = 0;  // bound on the entropy kernels' table-copy wait (clocks; 0: about 2 s)
@@ -154,10 +153,9 @@ struct ufvc_ctx {
     std::map<long long, Plan*> plans;
     std::string err;
     // standalone rANS scratch
-    uint16_t* r_scr = nullptr;
-    uint32_t* r_cnt = nullptr;
-    uint64_t* r_off = nullptr;
-    size_t r_scr_words = 0, r_lanes = 0;
+    uint16_t* r_scr = nullptr;  // ufvc_rans_encode: staging rows and layout control block
+    RansCtl* r_ctl = nullptr;
+    size_t r_scr_words = 0;
     // host-API staging
     uint8_t *st_frames = nullptr, *st_bits = nullptr;
     uint64_t* st_nbytes = nullptr;
@@ -315,9 +313,8 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
         AL(p->idx, p->ny);
         AL(p->scr_z, (size_t)p->Kz * p->cap_z);
         AL(p->scr_y, (size_t)K * p->cap_y);
-        AL(p->cnt_z, (size_t)p->Kz);
-        AL(p->cnt_y, (size_t)K);
-        AL(p->off_ws, (size_t)p->Kz + K);
+        AL(p->ctl, 1);
+        if (!dry_bytes && cudaMemset(p->ctl, 0, sizeof(RansCtl)) != cudaSuccess) return UFVC_ERR_CUDA;
         AL(p->zthr, (size_t)kBins - 1);
         if (ctx->dcm) {
             const size_t P = (size_t)p->h3 * p->w3;
@@ -330,16 +327,10 @@ static ufvc_status plan_buffers(ufvc_ctx* ctx, Plan* p, bool enc, bool dec, size
     }
     if (dec) {
         AL(p->dzhat, p->nz);
-        AL(p->diz, (size_t)a.cz);
         AL(p->didx, p->ny);
         AL(p->qp_dev, 1);
         AL(p->ver_dev, 1);
-        AL(p->lo_z, (size_t)p->Kz);
-        AL(p->lo_y, (size_t)K);
-        AL(p->lw_z, (size_t)p->Kz);
-        AL(p->lw_y, (size_t)K);
         AL(p->next_z, 1);
-        AL(p->next_y, 1);
         AL(p->dzf, p->nz);
         AL(p->ds1, (size_t)4 * p->Hz * p->Wz * a.cz);
         AL(p->ds2, (size_t)p->Hy * p->Wy * a.cz);
@@ -717,11 +708,11 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
         for (LayerW& L : ctx->dcf) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); }
         cudaFree(ctx->a1s2d.wtc);  // (its bias is enc[L_A1]'s)
         cudaFree(ctx->first_w);
-        cudaFree(ctx->d_packed); cudaFree(ctx->d_coarse); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
+        cudaFree(ctx->d_packed); cudaFree(ctx->d_dec); cudaFree(ctx->d_thr); cudaFree(ctx->d_qstep);
         cudaFree(ctx->d_qinv);
     }
     cudaFree(ctx->d_status);
-    cudaFree(ctx->r_scr); cudaFree(ctx->r_cnt); cudaFree(ctx->r_off);
+    cudaFree(ctx->r_scr); cudaFree(ctx->r_ctl);
     cudaFree(ctx->st_frames); cudaFree(ctx->st_bits); cudaFree(ctx->st_nbytes);
     cudaFree(ctx->ws_stage.p);
     for (auto& e : ctx->prof) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -748,8 +739,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
     build_host_tables(ctx->tabs);
     ufvc_status st;
     if ((st = dalloc(ctx, nullptr, &ctx->d_packed, ctx->tabs.packed.size())) != UFVC_OK) return bail(st);
-    if ((st = dalloc(ctx, nullptr, &ctx->d_coarse, ctx->tabs.coarse.size())) != UFVC_OK) return bail(st);
-    if (cudaMemcpy(ctx->d_coarse, ctx->tabs.coarse.data(), ctx->tabs.coarse.size() * 2, cudaMemcpyHostToDevice))
+    if ((st = dalloc(ctx, nullptr, &ctx->d_dec, ctx->tabs.dec.size())) != UFVC_OK) return bail(st);
+    if (cudaMemcpy(ctx->d_dec, ctx->tabs.dec.data(), ctx->tabs.dec.size(), cudaMemcpyHostToDevice))
         return bail(UFVC_ERR_CUDA);
     if ((st = dalloc(ctx, nullptr, &ctx->d_thr, ctx->tabs.thr.size())) != UFVC_OK) return bail(st);
     if ((st = dalloc(ctx, nullptr, &ctx->d_qstep, 64)) != UFVC_OK) return bail(st);
@@ -813,7 +804,8 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     c->N = base->N;
     c->tabs = base->tabs;
     c->d_packed = base->d_packed;
-    c->d_coarse = base->d_coarse;
+    c->d_dec = base->d_dec;
+    c->table_spin = base->table_spin;
     c->d_thr = base->d_thr;
     c->d_qstep = base->d_qstep;
     c->d_qinv = base->d_qinv;
@@ -1225,17 +1217,36 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     if (st) return st;
 
     RUN(run_encoder_front(ctx, p, d_frames, qp, s));
+    // both sections coded, laid out and the header written in one launch
     prof_begin(ctx, "rans_encode", s);
-    RansSection secs[2];
-    secs[0] = RansSection{p->zhat, p->iz, ctx->arch.cz, p->nz, p->Kz, p->scr_z, p->cap_z, p->cnt_z, ctx->d_status};
-    secs[1] = RansSection{p->rhat, p->idx, 0, p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, p->cnt_y, ctx->d_status};
-    launch_rans_encode(secs, 2, ctx->d_packed, s, ctx->table_spin);
+    RansEncJob j{};
+    j.s[0] = RansEncSec{p->zhat, p->iz, ctx->arch.cz, (uint32_t)p->nz, p->Kz, p->scr_z, p->cap_z, 0};
+    j.s[1] = RansEncSec{p->rhat, p->idx, 0, (uint32_t)p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, 0};
+    j.nsec = 2;
+    j.out = d_bits;
+    j.capacity = capacity;
+    j.nbytes = d_nbytes;
+    j.base = p->hdr;
+    j.hdr_len = (int)p->hdr;
+    const int version = 1 + (ctx->pm_on ? 1 : 0) + (ctx->tc_on ? 2 : 0);
+    const uint32_t fields[] = {'U', 'F', 'V', 'C', (uint32_t)version, (uint32_t)ctx->cfg.arch, (uint32_t)ctx->N,
+                               (uint32_t)qp};
+    for (int i = 0; i < 8; ++i) j.hdr20[i] = (uint8_t)fields[i];
+    for (int i = 0; i < 2; ++i) {
+        j.hdr20[8 + i] = (uint8_t)(width >> (8 * i));
+        j.hdr20[10 + i] = (uint8_t)(height >> (8 * i));
+    }
+    for (int i = 0; i < 4; ++i) {
+        j.hdr20[12 + i] = (uint8_t)((uint32_t)ctx->cfg.lanes >> (8 * i));
+        j.hdr20[16 + i] = (uint8_t)((uint32_t)p->Kz >> (8 * i));
+    }
+    j.iz = p->iz;
+    j.cz = ctx->arch.cz;
+    j.ctl = p->ctl;
+    j.status = ctx->d_status;
+    j.spin = ctx->table_spin;
+    CK(launch_rans_encode(j, ctx->d_packed, s));
     prof_end(ctx, s, 1);
-    prof_begin(ctx, "bitstream", s);
-    launch_write_header(d_bits, 1 + (ctx->pm_on ? 1 : 0) + (ctx->tc_on ? 2 : 0), ctx->cfg.arch, ctx->N, qp, width, height, ctx->cfg.lanes, p->Kz,
-                        p->iz, ctx->arch.cz, capacity, ctx->d_status, s);
-    launch_rans_finalize(secs, 2, d_bits, p->hdr, capacity, d_nbytes, p->off_ws, ctx->d_status, s);
-    prof_end(ctx, s, 3);
     CK(cudaGetLastError());
     return UFVC_OK;
 }
@@ -1253,19 +1264,33 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     if (st) return st;
 
     const Arch& a = ctx->arch;
-    prof_begin(ctx, "parse", s);
-    launch_parse_header(d_bits, nbytes, ctx->cfg.arch, ctx->N, width, height, ctx->cfg.lanes, p->Kz, a.cz, ctx->pm_on,
-                        ctx->tc_on, p->qp_dev, p->ver_dev, p->diz, ctx->d_status, s);
-    const bool fp32 = ctx->cfg.precision == UFVC_FP32;
-    RansDecodeJob jz{d_bits, nbytes, p->hdr, nullptr, p->diz, a.cz, p->nz, p->Kz, p->lo_z, p->lw_z, p->next_z,
-                     p->dzhat};
-    RansDecodeJob jy{d_bits, nbytes, 0, p->next_z, p->didx, 0, p->ny, ctx->cfg.lanes, p->lo_y, p->lw_y, p->next_y,
-                     p->drhat};
-    launch_rans_parse(jz, ctx->d_status, s);
-    launch_rans_parse_expect(jy, nbytes, d_nbytes, ctx->d_status, s);
-    prof_end(ctx, s, 3);
+    const bool fp32 = ctx->cfg.precision == UFVC_FP32, fp8 = ctx->cfg.precision == UFVC_FP8;
+    // z^ section: the header is checked in the same launch (its scale indices are the section's tables)
     prof_begin(ctx, "rans_decode_z", s);
-    launch_rans_decode(jz, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
+    RansDecJob jz{};
+    jz.bits = d_bits;
+    jz.nbytes = nbytes;
+    jz.sec_off = p->hdr;
+    jz.idx = d_bits + 20;
+    jz.idx_period = a.cz;
+    jz.n = (uint32_t)p->nz;
+    jz.K = p->Kz;
+    jz.next_off = p->next_z;
+    jz.out = kDecSym;
+    jz.sym = p->dzhat;
+    jz.hdr_cz = a.cz;
+    jz.arch = ctx->cfg.arch;
+    jz.N = ctx->N;
+    jz.W = width;
+    jz.H = height;
+    jz.Ky = ctx->cfg.lanes;
+    jz.allow_pm = ctx->pm_on;
+    jz.temporal = ctx->tc_on;
+    jz.qp_out = p->qp_dev;
+    jz.ver_out = p->ver_dev;
+    jz.status = ctx->d_status;
+    jz.spin = ctx->table_spin;
+    CK(launch_rans_decode(jz, ctx->d_dec, s));
     prof_end(ctx, s, 1);
     ctx->cur_ws = &p->ws_dec;
     const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
@@ -1273,19 +1298,39 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_begin(ctx, "scale_index", s);
     launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
     prof_end(ctx, s, 1);
+    // y^ section, ending exactly at the stream's end; with the single-pass means the decoder writes
+    // y^ = r^ q + mu itself, the progressive means need r^ first
     prof_begin(ctx, "rans_decode_y", s);
-    launch_rans_decode(jy, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
+    RansDecJob jy{};
+    jy.bits = d_bits;
+    jy.nbytes = nbytes;
+    jy.sec_off_dev = p->next_z;
+    jy.expect_end = d_nbytes ? 0 : nbytes;
+    jy.expect_end_dev = d_nbytes;
+    jy.idx = p->didx;
+    jy.n = (uint32_t)p->ny;
+    jy.K = ctx->cfg.lanes;
+    jy.out = ctx->pm_on ? kDecSym : fp32 ? kDecF32 : fp8 ? kDecE4M3 : kDecBf16;
+    jy.sym = p->drhat;
+    jy.yout = fp32 ? (void*)p->yhat : (void*)p->yhat_bf;
+    jy.mu = p->dmu;
+    jy.qstep_all = ctx->d_qstep;
+    jy.qp_dev = p->qp_dev;
+    jy.inv8 = fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f;
+    jy.status = ctx->d_status;
+    jy.spin = ctx->table_spin;
+    CK(launch_rans_decode(jy, ctx->d_dec, s));
     prof_end(ctx, s, 1);
-    if (ctx->pm_on)  // a version-1 stream leaves the means of the single pass (the steps check the version)
+    if (ctx->pm_on) {  // a version-1 stream leaves the means of the single pass (the steps check the version)
         RUN(run_progressive(ctx, p->Hy, p->Wy, nullptr, p->drhat, p->dmu, p->ds2, p->qp_dev, 0, p->ver_dev, p->pm_in_d,
                             p->pm_h_d, p->pm_mu_d, s));
-    prof_begin(ctx, "dequant", s);
-    const bool fp8 = ctx->cfg.precision == UFVC_FP8;
-    launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
-                   fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
-                   fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
+        prof_begin(ctx, "dequant", s);
+        launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
+                       fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
+                       fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
+        prof_end(ctx, s, 1);
+    }
     if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
-    prof_end(ctx, s, 1);
     const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
     if (ctx->dcm) {  // chunk decoder, frame decoders, then the context generation in place on F
         RUN(run_dc_trunk(ctx, p, yh, cin, p->dc_F, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
@@ -1685,7 +1730,7 @@ extern "C" ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, 
     return UFVC_OK;
 }
 
-static ufvc_status ensure_rans_scratch(ufvc_ctx* ctx, size_t words, size_t lanes) {
+static ufvc_status ensure_rans_scratch(ufvc_ctx* ctx, size_t words) {
     if (words > ctx->r_scr_words) {
         cudaFree(ctx->r_scr);
         ctx->r_scr = nullptr;
@@ -1693,58 +1738,58 @@ static ufvc_status ensure_rans_scratch(ufvc_ctx* ctx, size_t words, size_t lanes
         if (st) return st;
         ctx->r_scr_words = words;
     }
-    if (lanes > ctx->r_lanes) {
-        cudaFree(ctx->r_cnt);
-        cudaFree(ctx->r_off);
-        ctx->r_cnt = nullptr;
-        ctx->r_off = nullptr;
-        ufvc_status st = dalloc(ctx, nullptr, &ctx->r_cnt, lanes);
+    if (!ctx->r_ctl) {
+        ufvc_status st = dalloc(ctx, nullptr, &ctx->r_ctl, 1);
         if (st) return st;
-        st = dalloc(ctx, nullptr, &ctx->r_off, lanes);
-        if (st) return st;
-        ctx->r_lanes = lanes;
+        if (cudaMemset(ctx->r_ctl, 0, sizeof(RansCtl)) != cudaSuccess) return UFVC_ERR_CUDA;
     }
     return UFVC_OK;
 }
 
 extern "C" ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, const uint8_t* d_idx, size_t n, int lanes,
                                         uint8_t* d_out, size_t capacity, uint64_t* d_nbytes, void* stream) {
-    if (!ctx || (!d_sym && n) || (!d_idx && n) || !d_out || !d_nbytes || lanes < 1 || lanes > 65536)
+    if (!ctx || (!d_sym && n) || (!d_idx && n) || !d_out || !d_nbytes || lanes < 1 || lanes > 65536 ||
+        n > 0x7FFFFFFFull)
         return fail(ctx, UFVC_ERR_ARG, "rans_encode: bad argument");
     CK(cudaSetDevice(ctx->cfg.device));
     const int cap_lane = (int)(n / lanes + 3);
-    ufvc_status st = ensure_rans_scratch(ctx, (size_t)lanes * cap_lane, lanes);
+    ufvc_status st = ensure_rans_scratch(ctx, (size_t)lanes * cap_lane);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    RansSection sec{d_sym, d_idx, 0, n, lanes, ctx->r_scr, cap_lane, ctx->r_cnt, ctx->d_status};
-
+    RansEncJob j{};
+    j.s[0] = RansEncSec{d_sym, d_idx, 0, (uint32_t)n, lanes, ctx->r_scr, cap_lane, 0};
+    j.nsec = 1;
+    j.out = d_out;
+    j.capacity = capacity;
+    j.nbytes = d_nbytes;
+    j.ctl = ctx->r_ctl;
+    j.status = ctx->d_status;
+    j.spin = ctx->table_spin;
     prof_begin(ctx, "rans_encode", s);
-    launch_rans_encode(&sec, 1, ctx->d_packed, s, ctx->table_spin);
+    CK(launch_rans_encode(j, ctx->d_packed, s));
     prof_end(ctx, s, 1);
-    prof_begin(ctx, "rans_finalize", s);
-    launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, ctx->r_off, ctx->d_status, s);
-    prof_end(ctx, s, 2);
     CK(cudaGetLastError());
     return UFVC_OK;
 }
 
 extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, const uint8_t* d_idx,
                                         size_t n, int lanes, int16_t* d_sym, void* stream) {
-    if (!ctx || !d_in || (!d_idx && n) || (!d_sym && n) || lanes < 1 || lanes > 65536)
+    if (!ctx || !d_in || (!d_idx && n) || (!d_sym && n) || lanes < 1 || lanes > 65536 || n > 0x7FFFFFFFull)
         return fail(ctx, UFVC_ERR_ARG, "rans_decode: bad argument");
     CK(cudaSetDevice(ctx->cfg.device));
-    ufvc_status st = ensure_rans_scratch(ctx, 16, lanes);
-    if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    // lane offsets (u64) in r_off, lane word counts (u32) in r_cnt
-    RansDecodeJob j{d_in, nbytes, 0, nullptr, d_idx, 0, n, lanes, ctx->r_off, ctx->r_cnt, nullptr,
-                    d_sym};
-
-    prof_begin(ctx, "rans_parse", s);
-    launch_rans_parse(j, ctx->d_status, s);
-    prof_end(ctx, s, 1);
+    RansDecJob j{};
+    j.bits = d_in;
+    j.nbytes = nbytes;
+    j.idx = d_idx;
+    j.n = (uint32_t)n;
+    j.K = lanes;
+    j.out = kDecSym;
+    j.sym = d_sym;
+    j.status = ctx->d_status;
+    j.spin = ctx->table_spin;
     prof_begin(ctx, "rans_decode", s);
-    launch_rans_decode(j, ctx->d_packed, ctx->d_coarse, ctx->d_status, s, ctx->table_spin);
+    CK(launch_rans_decode(j, ctx->d_dec, s));
     prof_end(ctx, s, 1);
     CK(cudaGetLastError());
     return UFVC_OK;

@@ -6,6 +6,7 @@
 // tables turn a scale index into integer frequencies for the rANS coder.
 #include "ufvc_internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace ufvc {
@@ -62,25 +63,7 @@ void build_host_tables(HostTables& t) {
         for (int i = 0; i < kNsym; ++i) c[i + 1] = c[i] + f[i];
         for (int i = 0; i < kNsym; ++i) t.packed[k * kNsym + i] = (f[i] << 16) | c[i];
     }
-    // decoder index: for bucket b, the symbol whose interval [cum_s, cum_s + f_s) holds slot b << shift;
-    // then per table the lengths of its unit-frequency end runs (A: symbols 0..A-1, B: symbols 511-B..510
-    // have frequency 1, so there slot -> symbol is slot, resp. slot - 65025)
-    t.coarse.assign(kBins * kCoarse + 2 * kBins, 0);
-    for (int k = 0; k < kBins; ++k) {
-        const uint32_t* c = &t.cum[k * (kNsym + 1)];
-        int s = 0;
-        for (int b = 0; b < kCoarse; ++b) {
-            const uint32_t slot = (uint32_t)b << kCoarseShift;
-            while (c[s + 1] <= slot) ++s;
-            t.coarse[k * kCoarse + b] = (uint16_t)s;
-        }
-        const uint32_t* f = &t.packed[k * kNsym];
-        int a = 0, z = 0;
-        while (a < kNsym && (f[a] >> 16) == 1) ++a;
-        while (z < kNsym && (f[kNsym - 1 - z] >> 16) == 1) ++z;
-        t.coarse[kBins * kCoarse + 2 * k] = (uint16_t)a;
-        t.coarse[kBins * kCoarse + 2 * k + 1] = (uint16_t)z;
-    }
+    build_decode_tables(t.cum, t.dec);
 }
 
 // ---------------------------------------------------------------------------------------------

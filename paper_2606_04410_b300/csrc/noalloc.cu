@@ -1,14 +1,13 @@
 // Allocation-free variant of the rANS section encoder (ufvc_rans_encode_noalloc).
 //
 // ufvc_rans_encode needs scratch memory beyond its inputs and outputs: every lane writes its words into a
-// row of a staging buffer before they are laid out, and the lane word counts and destination offsets
-// live in device memory too.  That entry point allocates the staging buffer with cudaMalloc the first
-// time a size is seen.  Some callers cannot let a library allocate: code that runs while a stream is
-// being captured (allocation is not allowed there), real-time loops where cudaMalloc's implicit device
-// synchronisation would stall other work, and hosts whose device memory is wholly owned by their own
-// pool allocator.  For them this file keeps the scratch in one file-scope __device__ array of fixed
-// size, which every GPU that loads the library holds until the process exits, and the entry point below
-// performs no allocation of any kind.
+// row of a staging buffer before they are laid out, and the blocks publish their word totals in a small
+// control block.  That entry point allocates them with cudaMalloc the first time a size is seen.  Some
+// callers cannot let a library allocate: real-time loops where cudaMalloc's implicit device
+// synchronisation would stall other work, and hosts whose device memory is wholly owned by their own pool
+// allocator.  For them this file keeps the scratch in one file-scope __device__ array of fixed size, which
+// every GPU that loads the library holds until the process exits, and the entry point below performs no
+// allocation of any kind.
 #include "ufvc_internal.h"
 
 #include <mutex>
@@ -18,8 +17,8 @@ namespace {
 constexpr size_t kScratchBytes = 24ull << 20;  // 24 MiB per device
 constexpr int kMaxDevices = 64;
 
-// Layout of one call: lane destination offsets (u64 x lanes), lane word counts (u32 x lanes), then the
-// lane rows (u16 x lanes x (n / lanes + 3)), each part 256-byte aligned.
+// Layout of one call: the layout control block (tickets and published block totals, cleared before every
+// launch), then the lane rows (u16 x lanes x (n / lanes + 3)), each part 256-byte aligned.
 static __device__ __align__(256) unsigned char g_rans_scratch[kScratchBytes];
 
 std::mutex g_mu;
@@ -45,8 +44,8 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
         return UFVC_ERR_ARG;
     }
     const size_t cap_lane = n / (size_t)lanes + 3;
-    const size_t off_bytes = align256((size_t)lanes * 8), cnt_bytes = align256((size_t)lanes * 4);
-    const size_t need = off_bytes + cnt_bytes + (size_t)lanes * cap_lane * 2;
+    const size_t ctl_bytes = align256(ufvc::rans_ctl_bytes());
+    const size_t need = ctl_bytes + (size_t)lanes * cap_lane * 2;
     if (need > kScratchBytes) {
         ufvc::ctx_set_error(ctx, "rans_encode_noalloc: n + 3 * lanes exceeds the 24 MiB static scratch "
                                  "(at most about 12.5 million symbols); use ufvc_rans_encode");
@@ -78,19 +77,28 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
         }
         base = g_scratch_addr[dev];
     }
-    // Nothing in the scratch is read before this call writes it (each lane writes its count -- zero if
-    // its table copy timed out, which the layout kernels refuse -- and the words it later copies; the
-    // finaliser writes every offset), so no part needs clearing.
+    // The control block must start at zero: it is cleared on the stream before the launch (a memset, no
+    // allocation).  The rows hold nothing the call reads before writing it.
     unsigned char* b = static_cast<unsigned char*>(base);
-    uint64_t* offsets = reinterpret_cast<uint64_t*>(b);
-    uint32_t* counts = reinterpret_cast<uint32_t*>(b + off_bytes);
-    uint16_t* rows = reinterpret_cast<uint16_t*>(b + off_bytes + cnt_bytes);
+    ufvc::RansCtl* ctl = reinterpret_cast<ufvc::RansCtl*>(b);
+    uint16_t* rows = reinterpret_cast<uint16_t*>(b + ctl_bytes);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int* status = ufvc::ctx_status_word(ctx);
-    ufvc::RansSection sec{d_sym, d_idx, 0, n, lanes, rows, (int)cap_lane, counts, status};
-    ufvc::launch_rans_encode(&sec, 1, ufvc::ctx_packed_tables(ctx), s, ufvc::ctx_table_spin(ctx));
-    ufvc::launch_rans_finalize(&sec, 1, d_out, 0, capacity, d_nbytes, offsets, status, s);
-    e = cudaGetLastError();
+    e = cudaMemsetAsync(ctl, 0, ufvc::rans_ctl_bytes(), s);
+    if (e != cudaSuccess) {
+        ufvc::ctx_set_error(ctx, cudaGetErrorString(e));
+        return UFVC_ERR_CUDA;
+    }
+    ufvc::RansEncJob j{};
+    j.s[0] = ufvc::RansEncSec{d_sym, d_idx, 0, (uint32_t)n, lanes, rows, (int)cap_lane, 0};
+    j.nsec = 1;
+    j.out = d_out;
+    j.capacity = capacity;
+    j.nbytes = d_nbytes;
+    j.ctl = ctl;
+    j.status = ufvc::ctx_status_word(ctx);
+    j.spin = ufvc::ctx_table_spin(ctx);
+    e = ufvc::launch_rans_encode(j, ufvc::ctx_packed_tables(ctx), s);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         ufvc::ctx_set_error(ctx, cudaGetErrorString(e));
         return UFVC_ERR_CUDA;

@@ -110,8 +110,6 @@ constexpr int kRmax = 255;         // |r^| <= 255
 constexpr int kNsym = 511;         // symbols -255..255
 constexpr uint32_t kProbM = 1u << 16;
 constexpr uint32_t kRansL = 1u << 16;
-constexpr int kCoarseShift = 7;                    // decoder slot -> symbol index: 128-slot buckets
-constexpr int kCoarse = 1 << (16 - kCoarseShift);  // 512 buckets per table
 // The BF16 space-to-depth input holds x * 255/256: a byte v is stored as v / 256, which bf16 represents
 // exactly (eight significant bits), and the first layer's 2x2 weights are multiplied by 256/255, so the
 // input planes add no rounding of their own to the analysis.
@@ -128,7 +126,7 @@ struct HostTables {
     std::vector<float> qstep;     // [64]  q(qp) as float
     std::vector<float> qinv;      // [64]  1/q(qp) as float
     std::vector<double> log_thr;  // [63]  t_k in FP64 (z^ RMS index)
-    std::vector<uint16_t> coarse; // [64][kCoarse] symbol owning slot b << kCoarseShift, then [64][2] end-run lengths
+    std::vector<uint8_t> dec;     // decoder table image (build_decode_tables)
 };
 void build_host_tables(HostTables& t);
 double qstep_fp64(int qp);
@@ -269,65 +267,85 @@ void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp,
 void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s);
 void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s);
 
-// rANS: a "section job" describes one section of one stream
-struct RansSection {
-    const int16_t* sym;       // encode input
-    const uint8_t* idx;       // table index per element, or per channel if idx_period > 0
-    int idx_period;
-    size_t n;
-    int K;
-    // encode scratch
-    uint16_t* scratch;        // [K][cap_lane]
-    int cap_lane;
-    uint32_t* counts;         // [K] word counts
-    int* status;              // device status word (caller errors: symbol / index out of range)
+// rANS (rans.cu).  Encoding: one launch codes one or two sections and lays them out (lane counts, words,
+// padding) after `base` header bytes, writing the header itself when hdr_len > 0.  The control block
+// (tickets and published block totals) must be zero before the first launch; every launch leaves it
+// zero.  Staging rows: [K][cap_lane] u16 per section, cap_lane >= n / K + 3.
+constexpr int kRansMaxBlocks = 256;
+struct RansCtl {
+    unsigned int ticket, done;
+    uint64_t flag[kRansMaxBlocks];
 };
-// spin: bound on the wait for the table copy in SM clocks (0: about 2 s); see ufvc_set_table_wait_limit
-void launch_rans_encode(const RansSection* secs, int nsec, const uint32_t* packed_tables, cudaStream_t s,
-                        long long spin = 0);
+struct RansEncSec {
+    const int16_t* sym;       // symbols r^ in [-255, 255]
+    const uint8_t* idx;       // table index per element, or per channel when idx_period > 0
+    int idx_period;
+    uint32_t n;
+    int K;
+    uint16_t* rows;
+    int cap_lane;
+    int nblk;                 // set by the launcher
+};
+struct RansEncJob {
+    RansEncSec s[2];
+    int nsec, grid, lpb;      // grid and lanes per block: set by the launcher
+    uint8_t* out;
+    uint64_t capacity;
+    uint64_t* nbytes;         // device: size of the stream written
+    uint64_t base;            // first section's byte offset (the header length)
+    int hdr_len;              // 0: no header
+    uint8_t hdr20[20];        // the header's fixed fields, then cz scale indices from iz, then zeros
+    const uint8_t* iz;
+    int cz;
+    RansCtl* ctl;
+    int* status;
+    long long spin;           // bound on the table-copy wait in clocks (0: about 2 s)
+};
+cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cudaStream_t s);
+size_t rans_ctl_bytes();
 
-// Lay out one or two encoded sections after `hdr_bytes` of header in `out`: write lane counts, copy the
-// words, write the total size to *nbytes.  Capacity violations set *status = UFVC_ERR_CAPACITY.
-void launch_rans_finalize(const RansSection* secs, int nsec, uint8_t* out, size_t hdr_bytes, size_t capacity,
-                          uint64_t* nbytes, uint64_t* offsets_ws, int* status, cudaStream_t s);
-
-// Decoding: parse the lane counts of a section starting at byte `sec_off` (device value or host
-// constant), validate and produce word offsets.
-struct RansDecodeJob {
-    const uint8_t* bits;      // stream base
-    size_t nbytes;            // bytes available from the stream base
-    size_t sec_off_host;      // section offset if known on the host ...
-    const uint64_t* sec_off_dev; // ... or read from the device (then sec_off_host is ignored)
+// Decoding one section (count checks and offsets inside the launch).  Output: r^ (int16) or, fused,
+// y^ = r^ q + mu as bf16, float or E4M3 codes (q = qstep_all[*qp_dev], or qstep_all[qp_host]).  With
+// hdr_cz > 0 the launch first checks the container header against the context (arch, N, W, H, Ky lanes of
+// the latent section, K = Kz lanes here, the progressive-means and temporal flags) and block 0 writes the
+// rate and the version (2 for progressive means, else 1) to qp_out / ver_out.
+enum { kDecSym = 0, kDecBf16 = 1, kDecF32 = 2, kDecE4M3 = 3 };
+struct RansDecJob {
+    const uint8_t* bits;
+    uint64_t nbytes;                 // readable bytes from bits
+    uint64_t sec_off;                // section offset, or read from sec_off_dev when that is not null
+    const uint64_t* sec_off_dev;
+    uint64_t expect_end;             // the section must end exactly here (0: anywhere up to nbytes) ...
+    const uint64_t* expect_end_dev;  // ... or at the device value
     const uint8_t* idx;
     int idx_period;
-    size_t n;
+    uint32_t n;
     int K;
-    uint64_t* lane_off;       // [K] byte offsets of each lane stream (from the stream base)
-    uint32_t* lane_words;     // [K]
-    uint64_t* next_off;       // device: byte offset just past this section
-    int16_t* sym;             // output symbols
+    uint64_t* next_off;              // device: the byte after the section (may be null)
+    int out;
+    int16_t* sym;
+    void* yout;
+    const float* mu;
+    const float* qstep_all;
+    const int* qp_dev;
+    int qp_host;
+    float inv8;
+    int hdr_cz, arch, N, W, H, Ky, allow_pm, temporal;
+    int* qp_out;
+    int* ver_out;
+    int* status;
+    long long spin;
 };
-void launch_rans_parse(const RansDecodeJob& j, int* status, cudaStream_t s);
-// as launch_rans_parse, and the section must end exactly at byte `expect_end` of the stream (read from
-// the device when expect_end_dev is not null)
-void launch_rans_parse_expect(const RansDecodeJob& j, size_t expect_end, const uint64_t* expect_end_dev, int* status,
-                              cudaStream_t s);
-void launch_rans_decode(const RansDecodeJob& j, const uint32_t* packed_tables, const uint16_t* coarse, int* status,
-                        cudaStream_t s, long long spin = 0);
+cudaError_t launch_rans_decode(const RansDecJob& j, const uint8_t* dec_tables, cudaStream_t s);
+// the decoder's table image (196864 bytes) from cum [64][512]
+void build_decode_tables(const std::vector<uint32_t>& cum_all, std::vector<uint8_t>& out);
+
 // y^ = r^ q + mu with q = qstep_all[*qp_dev] (qp_dev null: qstep_all[qp_host]); yf and / or yb may be null
 void launch_dequant(const int16_t* rhat, const float* mu, size_t n, const float* qstep_all, const int* qp_dev,
                     float* yf, __nv_bfloat16* yb, cudaStream_t s, uint8_t* y8 = nullptr, float inv8 = 0.f,
                     int qp_host = 0);
 
-// Container header (version 1 + (progressive means) + 2 (temporal context)).
-void launch_write_header(uint8_t* out, int version, int arch, int N, int qp, int W, int H, int K, int Kz,
-                         const uint8_t* iz, int Cz, size_t capacity, int* status, cudaStream_t s);
-// Versions: 1 + (progressive means) + 2 (temporal context).  The parser accepts progressive means when
-// allow_pm, requires the temporal flag to equal temporal, and writes *ver_dev = 2 for a progressive-means
-// stream, else 1.
-void launch_parse_header(const uint8_t* bits, size_t nbytes, int arch, int N, int W, int H, int K, int Kz, int Cz,
-                         bool allow_pm, bool temporal, int* qp_dev, int* ver_dev, uint8_t* iz, int* status,
-                         cudaStream_t s);
+
 
 // Progressive means (progressive.cu).  `in` is the mean network's input [Hy][Wy][Cy + Cz], float (f32)
 // or bf16.  init: y^ of partition 0 (the encoder, y != null, first quantises partition 0 with mu0 into
