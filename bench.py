@@ -256,9 +256,12 @@ def stage_work(hy: int, wy: int, H_: int, W_: int, nbytes: int, lanes: int, prec
                      "bytes": (h1 * w1 * e0 + h2 * w2 * e1 * 2 + h3 * w3 * e2 * 7) * a + n * 4},
         "hyper_analysis": {"flops": fl("H1", hh, wh) + fl("H2", hz, wz), "flop_kind": kind,
                            "bytes": n * 4 + n * a * 2 + hh * wh * 128 * a * 2 + nz * 4 + nz * 2},
+        # S1..S3 with the entropy parameters formed in S3's pass (encoder: y in; mu, log sigma, r^, idx out;
+        # decoder: mu, idx out), the mean of the two
         "hyper_synthesis": {"flops": fl("S1", hz, wz) + fl("S2", 2 * hz, 2 * wz) + fl("S3", hy, wy),
                             "flop_kind": "alu",
-                            "bytes": nz * 2 + 4 * hz * wz * 128 * 4 * 2 + 16 * hz * wz * 128 * 4 * 2 + n * 8},
+                            "bytes": nz * 2 + 4 * hz * wz * 128 * 4 * 2 + 16 * hz * wz * 128 * 4 * 2
+                                     + n * (4 + 4 + 4 + 2 + 1 + 4 + 1) // 2},
         "quantize": {"bytes": n * (4 + 4 + 4 + 2 + 1)},
         # both sections coded, laid out and the header written: symbols + indices in, the stream out
         "rans_encode": {"bytes": (n + nz) * 3 + nbytes, "lane_steps": -(-n // lanes)},

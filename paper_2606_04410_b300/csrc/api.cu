@@ -232,10 +232,21 @@ static int conv_out(int x, int k, int s) { return (x + 2 * (k / 2) - k) / s + 1;
 // One convolution launch.  Layers with a tensor-core weight copy run on tcgen05 in BF16 precision
 // (bf16 activations in and out, except out_f32); all others (and every layer in FP32 precision) run on
 // the deterministic FP32 SIMT kernel.
+// The entropy parameters formed with the last hyper-synthesis layer (ConvDesc::ent_*): scale indices, and
+// with y the quantised residuals
+struct EntParams {
+    uint8_t* idx;
+    const float* y;
+    int16_t* rhat;
+    const int* qp_dev;
+    int qp;
+    bool keep_ls;
+};
+
 static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, int W, int stride, int act, int mode,
                         void* out, int out_h, int out_w, cudaStream_t s, const void* res = nullptr,
                         float* out2 = nullptr, int split = 0, long long in_gs = 0, long long out_gs = 0,
-                        long long res_gs = 0, int groups = 1, bool out_f32 = false);
+                        long long res_gs = 0, int groups = 1, bool out_f32 = false, const EntParams* ent = nullptr);
 
 static bool use_tc(const ufvc_ctx* ctx, const LayerW& L);
 
@@ -838,8 +849,13 @@ static bool use_tc(const ufvc_ctx* ctx, const LayerW& L) { return ctx->cfg.preci
 
 static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, int W, int stride, int act, int mode,
                         void* out, int out_h, int out_w, cudaStream_t s, const void* res, float* out2, int split,
-                        long long in_gs, long long out_gs, long long res_gs, int groups, bool out_f32) {
+                        long long in_gs, long long out_gs, long long res_gs, int groups, bool out_f32,
+                        const EntParams* ent) {
     ConvDesc d;
+    if (ent) {
+        d.ent_idx = ent->idx; d.ent_y = ent->y; d.ent_rhat = ent->rhat; d.ent_qp_dev = ent->qp_dev;
+        d.ent_qp = ent->qp; d.ent_keep_ls = ent->keep_ls ? 1 : 0; d.ent_thr = ctx->d_thr; d.ent_qinv = ctx->d_qinv;
+    }
     d.in = in; d.in_gs = in_gs; d.H = H; d.W = W;
     d.w = L.w; d.w_gs = L.w_gs; d.b = L.b; d.b_gs = L.b_gs;
     d.Cout = L.cout; d.k = L.k; d.stride = stride; d.mode = mode; d.act = act;
@@ -918,7 +934,7 @@ static bool check_shape(ufvc_ctx* ctx, int n_frames, int width, int height) {
 // PC(C_i) added before S3 (both null without the temporal context)
 static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zhat, float* zf, float* s1, float* s2,
                                        float* mu, float* ls, cudaStream_t s, const void* cin = nullptr,
-                                       float* pc_tmp = nullptr) {
+                                       float* pc_tmp = nullptr, const EntParams* ent = nullptr) {
     const Arch& a = ctx->arch;
     prof_begin(ctx, "hyper_synthesis", s);
     launch_i16_to_f32(zhat, p->nz, zf, s);
@@ -929,7 +945,8 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
                  nullptr, 0, 0, 0, 0, 1, true));
         launch_add_f32(s2, pc_tmp, (size_t)p->Hy * p->Wy * a.cz, s);
     }
-    RUN(conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy));
+    RUN(conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy, 0, 0, 0, 1,
+             false, ent));
     prof_end(ctx, s, cin ? 6 : 4);
     return UFVC_OK;
 }
@@ -1128,10 +1145,9 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
         launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
         prof_end(ctx, s, 3);
     }
-    RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s, cin, p->t_pc_e));
-    prof_begin(ctx, "quantize", s);
-    launch_quantize(p->y, p->mu, p->ls, p->ny, ctx->d_thr, ctx->d_qinv, nullptr, qp, p->rhat, p->idx, s);
-    prof_end(ctx, s, 1);
+    // the last hyper-synthesis layer also quantises the latent and forms its scale indices
+    const EntParams ent{p->idx, p->y, p->rhat, nullptr, qp, true};
+    RUN(run_hyper_synthesis(ctx, p, p->zhat, p->zf, p->s1, p->s2, p->mu, p->ls, s, cin, p->t_pc_e, &ent));
     if (ctx->pm_on)
         RUN(run_progressive(ctx, p->Hy, p->Wy, p->y, p->rhat, p->mu, p->s2, nullptr, qp, nullptr, p->pm_in_e, p->pm_h_e,
                             p->pm_mu_e, s));
@@ -1294,10 +1310,9 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     prof_end(ctx, s, 1);
     ctx->cur_ws = &p->ws_dec;
     const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
-    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s, cin, p->t_pc_d));
-    prof_begin(ctx, "scale_index", s);
-    launch_scale_index(p->dls, p->ny, ctx->d_thr, p->qp_dev, p->didx, s);
-    prof_end(ctx, s, 1);
+    // the last hyper-synthesis layer also forms the scale indices (at the rate the header carries)
+    const EntParams ent{p->didx, nullptr, nullptr, p->qp_dev, 0, false};
+    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s, cin, p->t_pc_d, &ent));
     // y^ section, ending exactly at the stream's end; with the single-pass means the decoder writes
     // y^ = r^ q + mu itself, the progressive means need r^ first
     prof_begin(ctx, "rans_decode_y", s);

@@ -498,6 +498,53 @@ __global__ void conv_simt_reduce_kernel(const ConvDesc d, int Ho, int Wo, int KS
     }
 }
 
+// The last hyper-synthesis layer's reduction with the entropy parameters formed in the same pass: each
+// thread sums four mu columns and the four log sigma columns of the same channels (range sums in range
+// order, then the bias, as conv_simt_reduce_kernel), writes mu (and log sigma with ent_keep_ls), the four
+// scale indices and, with ent_y, the four quantised residuals -- the quantiser's arithmetic, term for term.
+__global__ void conv_simt_reduce_entropy_kernel(const ConvDesc d, int M, int KS, const float* ws) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ float thr[kBins - 1];
+    const int qp = d.ent_qp_dev ? *d.ent_qp_dev : d.ent_qp;
+    if (threadIdx.x < kBins - 1) thr[threadIdx.x] = d.ent_thr[qp * (kBins - 1) + threadIdx.x];
+    __syncthreads();
+    const float qinv = d.ent_qinv[qp];
+    const int C = d.split, C4 = C >> 2;
+    const size_t per = (size_t)M * d.Cout;
+    const int total = M * C4;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const int m = i / C4, c = (i - m * C4) * 4;
+        const float* sm = ws + (size_t)m * d.Cout + c;
+        const float* sl = sm + C;
+        float4 mu = *reinterpret_cast<const float4*>(sm), ls = *reinterpret_cast<const float4*>(sl);
+        for (int ks = 1; ks < KS; ++ks) {
+            const float4 a = *reinterpret_cast<const float4*>(sm + ks * per);
+            const float4 b = *reinterpret_cast<const float4*>(sl + ks * per);
+            mu.x += a.x; mu.y += a.y; mu.z += a.z; mu.w += a.w;
+            ls.x += b.x; ls.y += b.y; ls.z += b.z; ls.w += b.w;
+        }
+        mu.x += d.b[c]; mu.y += d.b[c + 1]; mu.z += d.b[c + 2]; mu.w += d.b[c + 3];
+        ls.x += d.b[C + c]; ls.y += d.b[C + c + 1]; ls.z += d.b[C + c + 2]; ls.w += d.b[C + c + 3];
+        const size_t o = (size_t)m * C + c;
+        *reinterpret_cast<float4*>(static_cast<float*>(d.out) + o) = mu;
+        if (d.ent_keep_ls) *reinterpret_cast<float4*>(d.out2 + o) = ls;
+        const uint32_t id = (uint32_t)count_below(thr, ls.x) | ((uint32_t)count_below(thr, ls.y) << 8) |
+                            ((uint32_t)count_below(thr, ls.z) << 16) | ((uint32_t)count_below(thr, ls.w) << 24);
+        *reinterpret_cast<uint32_t*>(d.ent_idx + o) = id;
+        if (d.ent_y) {
+            const float4 y = *reinterpret_cast<const float4*>(d.ent_y + o);
+            const float r0 = fminf(fmaxf(rintf(__fmul_rn(__fsub_rn(y.x, mu.x), qinv)), -255.0f), 255.0f);
+            const float r1 = fminf(fmaxf(rintf(__fmul_rn(__fsub_rn(y.y, mu.y), qinv)), -255.0f), 255.0f);
+            const float r2 = fminf(fmaxf(rintf(__fmul_rn(__fsub_rn(y.z, mu.z), qinv)), -255.0f), 255.0f);
+            const float r3 = fminf(fmaxf(rintf(__fmul_rn(__fsub_rn(y.w, mu.w), qinv)), -255.0f), 255.0f);
+            const uint32_t lo = (uint32_t)(uint16_t)(int16_t)r0 | ((uint32_t)(uint16_t)(int16_t)r1 << 16);
+            const uint32_t hi = (uint32_t)(uint16_t)(int16_t)r2 | ((uint32_t)(uint16_t)(int16_t)r3 << 16);
+            *reinterpret_cast<uint2*>(d.ent_rhat + o) = make_uint2(lo, hi);
+        }
+    }
+}
+
 // The launch rule, shared by the launcher and the workspace query.  Returns the tile kind
 // (0: 128 x 16, 1: 128 x 64, 2: 64 x 64) and, for kind 2, the number of K ranges.
 static int simt_plan(const ConvDesc& d, int* KS) {
@@ -562,6 +609,24 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
     const int M = Ho * Wo;
     int KS;
     const int kind = simt_plan(d, &KS);
+    // the entropy parameters of the last hyper-synthesis layer: in its split-K reduction when it has one
+    // and the tensors allow four channels per thread, else by the quantiser after the layer
+    const bool want_ent = d.ent_idx != nullptr;
+    const bool fuse_ent = want_ent && kind == 3 && KS > 1 && d.groups == 1 && d.mode == OUT_NHWC && d.act == 0 &&
+                          !d.res && d.split > 0 && d.split % 4 == 0 && d.Cout == 2 * d.split && aligned16(d.out) &&
+                          (!d.ent_keep_ls || aligned16(d.out2)) && aligned16(d.b) &&
+                          (reinterpret_cast<uintptr_t>(d.ent_idx) & 3) == 0 &&
+                          (!d.ent_y || (aligned16(d.ent_y) && (reinterpret_cast<uintptr_t>(d.ent_rhat) & 7) == 0));
+    if (want_ent && !fuse_ent) {  // the layer as usual (mu and log sigma written), then the quantiser
+        ConvDesc u = d_in;
+        u.ent_idx = nullptr;
+        u.ent_keep_ls = 1;
+        cudaError_t e = launch_conv_simt(u, st);
+        if (e != cudaSuccess) return e;
+        launch_quantize(d.ent_y, static_cast<const float*>(d.out), d.out2, (size_t)M * d.split, d.ent_thr, d.ent_qinv,
+                        d.ent_qp_dev, d.ent_qp, d.ent_y ? d.ent_rhat : nullptr, d.ent_idx, st);
+        return cudaGetLastError();
+    }
     if (kind == 0) {
         dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
         (void)launch_pdl(conv_simt_kernel<128, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
@@ -573,6 +638,13 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
         if (KS > 1) {
             if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;
             (void)launch_pdl(conv_simt88_kernel<true>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            if (fuse_ent) {
+                const int n4 = M * (d.split / 4);
+                const unsigned blocks = (unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);
+                (void)launch_pdl(conv_simt_reduce_entropy_kernel, dim3(blocks), dim3(256), (size_t)(0), st, d, M, KS,
+                                 d.ws);
+                return cudaGetLastError();
+            }
             (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
         } else {
             (void)launch_pdl(conv_simt88_kernel<false>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, 1, nullptr);

@@ -367,16 +367,6 @@ void launch_zquant(const float* z, int npos, int cz, const uint64_t* zthr, int16
 // ------------------------------------------------------------------------------------------------
 // quantize / scale index
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ int count_below(const float* thr, float v) {
-    // #{k : thr[k] < v} for the 63 ascending thresholds (binary search)
-    int lo = 0, hi = kBins - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (thr[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 __global__ void quantize_kernel(const float* __restrict__ y, const float* __restrict__ mu,
                                 const float* __restrict__ logsig, size_t n, const float* __restrict__ thr_all,
                                 const float* __restrict__ qinv_all, const int* qp_dev, int qp_host,

@@ -110,6 +110,19 @@ constexpr int kRmax = 255;         // |r^| <= 255
 constexpr int kNsym = 511;         // symbols -255..255
 constexpr uint32_t kProbM = 1u << 16;
 constexpr uint32_t kRansL = 1u << 16;
+
+#ifdef __CUDACC__
+// #{k : thr[k] < v} for the 63 ascending scale-index thresholds (the scale index of log sigma v)
+__device__ __forceinline__ int count_below(const float* thr, float v) {
+    int lo = 0, hi = kBins - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (thr[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+#endif
+
 // The BF16 space-to-depth input holds x * 255/256: a byte v is stored as v / 256, which bf16 represents
 // exactly (eight significant bits), and the first layer's 2x2 weights are multiplied by 256/255, so the
 // input planes add no rounding of their own to the analysis.
@@ -212,6 +225,19 @@ struct ConvDesc {
     // tensor-core path: K steps (tap x 64-channel chunk, tap-major) whose weights are all zero and are
     // skipped (bit ks set = step ks runs; 0 = every step runs)
     unsigned long long kmask = 0;
+    // The last hyper-synthesis layer (columns [0, split) = mu, [split, Cout) = log sigma) with the entropy
+    // parameters formed in its output pass: ent_idx = #{k : thr_qp[k] < log sigma} and, with ent_y,
+    // ent_rhat = clamp(rint((y - mu) / q)), qp = *ent_qp_dev (or ent_qp).  mu goes to out; log sigma to
+    // out2 only with ent_keep_ls.  Formed in the split-K reduction where there is one, else by the
+    // quantiser after the layer (the same arithmetic either way).
+    uint8_t* ent_idx = nullptr;
+    const float* ent_y = nullptr;
+    int16_t* ent_rhat = nullptr;
+    const float* ent_thr = nullptr;   // [64 qp][63]
+    const float* ent_qinv = nullptr;  // [64]
+    const int* ent_qp_dev = nullptr;
+    int ent_qp = 0;
+    int ent_keep_ls = 1;
 };
 
 // api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
