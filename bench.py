@@ -7,7 +7,7 @@ scale index, whole-latent decode + dequantise, 8 frame-specific decoders, uint8 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32] [--impl ours|reference]
                     [--width W --height H] [--no-cpu-baseline] [--no-fp32-path] [--no-entropy-sweep]
                     [--no-serving] [--no-fp8] [--no-pm] [--no-color] [--no-temporal] [--no-dc]
-                    [--serving-window S]
+                    [--serving-windows R:S,...] [--serving-windows-fp32 R:S,...]
 
 Prints ONE JSON line (rank 0).  The headline path is BF16 (tensor cores); the FP32 path is timed beside
 it under the same methodology and reported with the PSNR and bitrate deltas.  Extra keys: the decoder
@@ -362,16 +362,19 @@ NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.873536e6 + 73.990400e6), "dec.U3": 4 * (1
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
 
 
-def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n_streams: int = 64, temporal=None,
-                  seed: int = 0, drain_s: float = 90.0, dist=None, rank: int = 0, world: int = 1) -> dict:
+def serving_bench(U, dev, frames_1080p, blob, precision: str, windows: list, n_streams: int = 64, temporal=None,
+                  seed: int = 0, drain_s: float = 120.0, dist=None, rank: int = 0, world: int = 1) -> dict:
     """Serving mix: n_streams streams of the SERVING_MIX resolutions (assigned by seed), each with Poisson
-    chunk arrivals at 30 fps (one 8-frame chunk per Exp(mean 8/30 s)), requests alternating encode and
-    decode (a decode codes the stream's latest device-resident bit-stream), submitted in real time for
-    window_s seconds to the continuous-batching server (HBM cap 150 GB).  Latency = submit -> completion
-    on the server's clock; frames/s = frames of the completed requests / (last completion - first submit).
-    Content: the 1080p synthetic chunk, cropped for the smaller sizes and tiled 2 x 2 for 4K.  Under
-    torchrun every rank serves the streams s with s mod world == rank (same global trace); frames and
-    the span are aggregated over ranks (sum, slowest), latencies gathered."""
+    chunk arrivals (one 8-frame chunk per Exp(mean 8/30 s) at 30 fps, divided by the window's rate
+    multiplier), each stream's requests alternating encode and decode across all windows (a decode codes
+    the stream's latest device-resident bit-stream, so every chunk is decoded, in order), submitted in real time to the continuous-batching server (HBM cap
+    150 GB).  `windows` = [(rate multiplier, seconds), ...] run back to back on the same warm server,
+    each drained before the next.  Per window: latency = submit -> completion on the server's clock;
+    frames/s = frames of the completed requests / (last completion - first submit); the share of
+    requests that ran in same-shape batches.  Content: the 1080p synthetic chunk, cropped for the
+    smaller sizes and tiled 2 x 2 for 4K.  Under torchrun every rank serves the streams s with
+    s mod world == rank (same global trace); frames and the span are aggregated over ranks (sum,
+    slowest), latencies gathered."""
     import torch
     from paper_2606_04410_b300 import shard
     rng = np.random.default_rng(seed)
@@ -394,60 +397,78 @@ def serving_bench(U, dev, frames_1080p, blob, precision: str, window_s: float, n
         srv.streams[sid]["frames_in"].copy_(content[(W_, H_)])
         sids[j] = sid
     torch.cuda.synchronize()
-    # warm-up: every stream once (slots, plans, workspaces, graph capture), then drain
+    # warm-up (slots, plans, workspaces, graph capture): every stream alone once, then all streams queued
+    # at once twice (the batch sizes the windows meet: direct run, then capture), then drain
     warm = []
+    for sid in sids.values():
+        warm.append(srv.submit(sid, U.UFVC_OP_ENCODE))
+        warm.append(srv.submit(sid, U.UFVC_OP_DECODE))
     for _ in range(2):
-        for sid in sids.values():
-            warm.append(srv.submit(sid, U.UFVC_OP_ENCODE))
-            warm.append(srv.submit(sid, U.UFVC_OP_DECODE))
+        warm += srv.submit_many([(sid, op) for op in (U.UFVC_OP_ENCODE, U.UFVC_OP_DECODE) for sid in sids.values()])
     for t in warm:
         assert srv.wait(t, 600000.0)["status"] == 0
-    # arrival trace
-    events = []
-    for j in range(n_streams):  # the global trace (same on every rank), then this rank's share
-        t, op = rng.exponential(8 / 30), U.UFVC_OP_ENCODE
-        while t < window_s:
-            if j in sids:
-                events.append((t, sids[j], op))
-            op = U.UFVC_OP_DECODE if op == U.UFVC_OP_ENCODE else U.UFVC_OP_ENCODE
-            t += rng.exponential(8 / 30)
-    events.sort()
-    if dist is not None and world > 1:
-        dist.barrier()
-    tickets = []
-    t0 = time.perf_counter()
-    for t, sid, op in events:
-        d = t0 + t - time.perf_counter()
-        if d > 0:
-            time.sleep(d)
-        tickets.append((sid, op, srv.submit(sid, op)))
-    res = [(sid, op, srv.wait(tk, drain_s * 1000.0)) for sid, op, tk in tickets]
-    done = [(sid, op, r) for sid, op, r in res if r["status"] == 0]
-    pending = sum(1 for _, _, r in res if r["status"] == U.UFVC_PENDING)
-    st = srv.stats()
-    lats = [(op, r["done_ms"] - r["submit_ms"]) for _, op, r in done]
-    span_ms = (max(r["done_ms"] for _, _, r in done) - min(r["submit_ms"] for _, _, r in res)) if done else 1.0
-    n_req, n_pend = len(events), pending
-    if dist is not None and world > 1:
-        gathered = [None] * world
-        dist.all_gather_object(gathered, (lats, n_req, n_pend))
-        lats = [x for g in gathered for x in g[0]]
-        n_req, n_pend = sum(g[1] for g in gathered), sum(g[2] for g in gathered)
-    n_done, span_ms = shard.aggregate(len(done), span_ms, dist if world > 1 else None, dev)
-    lat = np.array([v for _, v in lats] or [0.0])
-    lat_e = np.array([v for op, v in lats if op == U.UFVC_OP_ENCODE] or [0.0])
-    lat_d = np.array([v for op, v in lats if op == U.UFVC_OP_DECODE] or [0.0])
     out = {"streams": n_streams, "mix": {f"{w}x{h}": int((which == i).sum()) for i, (w, h) in enumerate(sizes)},
-           "window_s": window_s, "requests": n_req, "completed": int(n_done), "pending_after_drain": n_pend,
-           "frames_per_s": N * n_done / (span_ms / 1000.0),
-           "offered_frames_per_s": N * n_req / window_s, "ranks": world,
-           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                          "enc_p50": float(np.percentile(lat_e, 50)), "enc_p99": float(np.percentile(lat_e, 99)),
-                          "dec_p50": float(np.percentile(lat_d, 50)), "dec_p99": float(np.percentile(lat_d, 99))},
-           "slots": st["slots"], "graphs": st["graphs"], "hbm_used_gb": st["hbm_used"] / 2**30,
-           "hbm_cap_gb": 150}
+           "ranks": world, "hbm_cap_gb": 150, "rates": {}}
+    next_op = [U.UFVC_OP_ENCODE] * n_streams  # a stream's requests alternate across windows too
+    for rate, window_s in windows:
+        events = []
+        for j in range(n_streams):  # the global trace (same on every rank), then this rank's share
+            t = rng.exponential(8 / 30 / rate)
+            while t < window_s:
+                if j in sids:
+                    events.append((t, sids[j], next_op[j]))
+                next_op[j] = U.UFVC_OP_DECODE if next_op[j] == U.UFVC_OP_ENCODE else U.UFVC_OP_ENCODE
+                t += rng.exponential(8 / 30 / rate)
+        events.sort()
+        st0 = srv.stats()
+        if dist is not None and world > 1:
+            dist.barrier()
+        tickets = []
+        t0 = time.perf_counter()
+        for t, sid, op in events:
+            d = t0 + t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append((sid, op, srv.submit(sid, op)))
+        deadline = time.perf_counter() + drain_s
+        res = [(sid, op, srv.wait(tk, max(1.0, (deadline - time.perf_counter()) * 1000.0)))
+               for sid, op, tk in tickets]
+        done = [(sid, op, r) for sid, op, r in res if r["status"] == 0]
+        pending = sum(1 for _, _, r in res if r["status"] == U.UFVC_PENDING)
+        for _, _, tk in tickets:  # drain whatever the deadline left before the next window
+            srv.wait(tk, 600000.0)
+        st = srv.stats()
+        lats = [(op, r["done_ms"] - r["submit_ms"]) for _, op, r in done]
+        span_ms = (max(r["done_ms"] for _, _, r in done) - min(r["submit_ms"] for _, _, r in res)) if done else 1.0
+        n_req, n_pend, n_batched = len(events), pending, st["batched"] - st0["batched"]
+        if dist is not None and world > 1:
+            gathered = [None] * world
+            dist.all_gather_object(gathered, (lats, n_req, n_pend, n_batched))
+            lats = [x for g in gathered for x in g[0]]
+            n_req, n_pend = sum(g[1] for g in gathered), sum(g[2] for g in gathered)
+            n_batched = sum(g[3] for g in gathered)
+        n_done, span_ms = shard.aggregate(len(done), span_ms, dist if world > 1 else None, dev)
+        lat = np.array([v for _, v in lats] or [0.0])
+        lat_e = np.array([v for op, v in lats if op == U.UFVC_OP_ENCODE] or [0.0])
+        lat_d = np.array([v for op, v in lats if op == U.UFVC_OP_DECODE] or [0.0])
+        pc = lambda a, q: round(float(np.percentile(a, q)), 3)
+        out["rates"][f"x{rate:g}"] = {
+            "window_s": window_s, "offered_frames_per_s": round(N * n_req / window_s, 1), "requests": n_req,
+            "completed": int(n_done), "pending_after_drain": n_pend,
+            "frames_per_s": round(N * n_done / (span_ms / 1000.0), 1),
+            "batched_share": round(n_batched / max(1, n_done), 3),
+            "latency_ms": {"p50": pc(lat, 50), "p99": pc(lat, 99), "enc_p50": pc(lat_e, 50),
+                           "enc_p99": pc(lat_e, 99), "dec_p50": pc(lat_d, 50), "dec_p99": pc(lat_d, 99)}}
+    st = srv.stats()
+    out.update({"slots": st["slots"], "graphs": st["graphs"], "batches": st["batches"],
+                "hbm_used_gb": round(st["hbm_used"] / 2**30, 2)})
     srv.close()
     return out
+
+
+def parse_windows(spec: str) -> list:
+    """'1:60,2:8' -> [(1.0, 60.0), (2.0, 8.0)] (rate multiplier : seconds)."""
+    return [(float(a), float(b)) for a, b in (w.split(":") for w in spec.split(",") if w)]
 
 
 def time_codec(codec, fr, frames_np, W_, H_, steps, warmup, profile, flush, dist=None, world=1, temporal=False):
@@ -538,7 +559,10 @@ def main() -> None:
     ap.add_argument("--no-color", action="store_true", help="skip the colour-format variants")
     ap.add_argument("--no-temporal", action="store_true", help="skip the temporal-context variant")
     ap.add_argument("--no-dc", action="store_true", help="skip the DC-block model (HT-S counts)")
-    ap.add_argument("--serving-window", type=float, default=4.0)
+    ap.add_argument("--serving-windows", default="1:60,2:8,4:8,8:5",
+                    help="BF16 serving windows, rate multiplier:seconds, comma-separated")
+    ap.add_argument("--serving-windows-fp32", default="0.25:8,1:4")
+    ap.add_argument("--serving-windows-temporal", default="1:8,4:5")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -774,13 +798,15 @@ def main() -> None:
     serving = None
     if not args.no_serving and (W_, H_) == (W, H):
         dd = dist if world > 1 else None
-        serving = {args.precision: serving_bench(U, dev, frames_np, blob, args.precision, args.serving_window,
+        wins = parse_windows(args.serving_windows_fp32 if args.precision == "fp32" else args.serving_windows)
+        serving = {args.precision: serving_bench(U, dev, frames_np, blob, args.precision, wins,
                                                  dist=dd, rank=rank, world=world)}
         if args.precision != "fp32" and not args.no_fp32_path:
-            serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", args.serving_window / 2, dist=dd,
-                                            rank=rank, world=world)
+            serving["fp32"] = serving_bench(U, dev, frames_np, blob, "fp32", parse_windows(args.serving_windows_fp32),
+                                            dist=dd, rank=rank, world=world)
         if args.precision == "bf16" and not args.no_temporal:  # every stream carries its context chain
-            serving["bf16_temporal"] = serving_bench(U, dev, frames_np, blob, "bf16", args.serving_window, dist=dd,
+            serving["bf16_temporal"] = serving_bench(U, dev, frames_np, blob, "bf16",
+                                                     parse_windows(args.serving_windows_temporal), dist=dd,
                                                      rank=rank, world=world,
                                                      temporal=synthetic.draw_temporal_weights(1, N, seed=0))
 

@@ -174,6 +174,23 @@ ufvc_status ufvc_pipe_submit(ufvc_pipe* pipe, const uint8_t* h_frames, int n_fra
 ufvc_status ufvc_pipe_wait(ufvc_pipe* pipe, long long ticket, size_t* nbytes);
 void ufvc_pipe_destroy(ufvc_pipe* pipe);
 
+/* Batched chunk calls for serving (the paper has no counterpart: it codes chunk after chunk).  `batch`
+ * (1..8) chunks of the same size, each with its own buffers (host arrays of `batch` device pointers; the
+ * encoder takes one rate per chunk in qps, the decoder reads each stream's size from d_nbytes[b] on the
+ * device, as ufvc_decode_chunk_dev does).  Every chunk runs its own analysis, hyperprior and synthesis
+ * launches; the entropy coding of all chunks is shared: one launch codes and lays out the 2 x batch
+ * sections, one launch decodes the batch's z^ sections and one its y^ sections, so the latency-bound lane
+ * chains of the chunks run side by side on the SMs instead of one after another.  The bit-streams and
+ * frames are byte for byte those of the single-chunk calls.  Each batch position has its own per-size
+ * buffers (allocated on first use).  UFVC_ERR_UNSUPPORTED for batch > 1 in a context with a temporal
+ * context (every stream carries its own). */
+ufvc_status ufvc_encode_chunks(ufvc_ctx* ctx, int batch, const uint8_t* const* d_frames, int n_frames, int width,
+                               int height, const int* qps, uint8_t* const* d_bits, size_t capacity,
+                               uint64_t* const* d_nbytes, void* stream);
+ufvc_status ufvc_decode_chunks(ufvc_ctx* ctx, int batch, const uint8_t* const* d_bits, size_t capacity,
+                               const uint64_t* const* d_nbytes, uint8_t* const* d_frames, int n_frames, int width,
+                               int height, void* stream);
+
 /* Synchronise `stream`, then return and clear the device status word (UFVC_OK if no device-side
  * error was recorded since the last call). */
 ufvc_status ufvc_sync_status(ufvc_ctx* ctx, void* stream);
@@ -337,6 +354,13 @@ ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, i
  * Synchronous, no device work. */
 ufvc_status ufvc_set_table_wait_limit(ufvc_ctx* ctx, long long cycles);
 
+/* Kernel selection for the decoders' pixel-shuffle layers (D0, U1, U2 at 256 accumulator columns, Sec. 3.2
+ * frame decoders) on the tensor cores: enable = 1 (the default) runs them on pairs of SMs that share one
+ * MMA of 256 pixels (each SM loads its 128 pixels and half of the weights), 0 on one SM per 128-pixel tile.
+ * Both compute every output from the same bf16 operands with FP32 accumulation; layer outputs agree to
+ * the accumulation order.  UFVC_ERR_ARG for other values.  Synchronous, no device work. */
+ufvc_status ufvc_set_conv_pairs(ufvc_ctx* ctx, int enable);
+
 /* The first analysis layer read straight from the frame bytes (the patch embedding of the stacked chunk,
  * Sec. 3.1: frame n's three channels become channels 3n .. 3n+2 of one input, replicate-padded to a
  * multiple of 16, then A1 = 3x3 stride-2 convolution + GELU), as the BF16 chunk encoder runs it: d_frames
@@ -356,7 +380,7 @@ ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, int width, 
  * ufvc_rans_encode may call cudaMalloc for its staging rows, which callers in real-time loops that cannot
  * absorb cudaMalloc's implicit device synchronisation, and callers whose device memory belongs to their
  * own pool allocator, cannot accept.  The staging space is one fixed 24 MiB array per device, held by
- * every GPU that loads this library until the process exits; a call needs 2304 bytes for its layout
+ * every GPU that loads this library until the process exits; a call needs 8448 bytes for its layout
  * control block plus 2 * lanes * (n / lanes + 3) bytes of staging rows (rounded up to 256), which allows
  * roughly 12.5 million symbols, and returns UFVC_ERR_ARG (message in ufvc_last_error) beyond that.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress, with that device
@@ -405,7 +429,11 @@ ufvc_status ufvc_get_fp8_scales(const ufvc_ctx* ctx, float* act_scales, int n);
  * slots free up: a request runs on an idle slot of its frame size, or on a new slot if the pool has
  * room and the HBM cap allows the slot's footprint (idle slots of other sizes are released to make
  * room); requests of one stream run in submission order; requests on different slots overlap on the
- * device.  Results are identical to the single-context calls (same kernels, same arithmetic).
+ * device.  Queued requests of the same frame size and operation (and rate, for encodes) that are
+ * admitted together run as one batch on one slot (ufvc_encode_chunks / ufvc_decode_chunks: their rANS
+ * sections share launches), up to the slot's batch size (4 chunks up to 1080p, 1 above; 1 with the
+ * temporal context, where every stream carries its own).  Results are identical to the single-context
+ * calls (same kernels, same arithmetic).
  *
  * All server calls are thread-safe.  Device pointers returned by ufvc_server_stream_buffers stay valid
  * until the server is destroyed; the input buffer must not be modified while an encode request of the
@@ -424,6 +452,7 @@ typedef struct {
     double start_ms;     /* launched on a slot */
     double done_ms;      /* completion observed by the scheduler */
     uint64_t nbytes;     /* encode: bit-stream size (read back at completion); decode: the size decoded */
+    int batch;           /* requests in the batch it ran in (1: alone) */
 } ufvc_result;
 
 typedef struct {
@@ -434,6 +463,8 @@ typedef struct {
     uint64_t completed;       /* requests finished */
     size_t hbm_used;          /* bytes held: streams' buffers + slots' footprints */
     size_t hbm_cap;
+    uint64_t batches;         /* launches of two or more requests at once */
+    uint64_t batched;         /* requests that ran in such batches */
 } ufvc_server_stats;
 
 /* cfg / weights as for ufvc_create.  hbm_cap_bytes bounds the device bytes the server holds besides
@@ -453,6 +484,11 @@ ufvc_status ufvc_server_stream_buffers(ufvc_server* srv, int stream_id, uint8_t*
 /* Queue a request; returns at once with its ticket.  ENCODE codes the stream's input buffer into its
  * bit-stream buffers; DECODE decodes the stream's latest bit-stream into its output buffer. */
 ufvc_status ufvc_server_submit(ufvc_server* srv, int stream_id, int op, uint64_t* ticket);
+/* Queue n requests at once (request i: stream_ids[i], ops[i]; its ticket in tickets[i]), all or none
+ * (UFVC_ERR_ARG if any is invalid).  The scheduler sees them together, so same-shape requests among them
+ * whose streams are free run as batches (ufvc_result.batch). */
+ufvc_status ufvc_server_submit_many(ufvc_server* srv, int n, const int* stream_ids, const int* ops,
+                                    uint64_t* tickets);
 /* The request's result; returns UFVC_PENDING while it is queued or running, else its status. */
 ufvc_status ufvc_server_poll(ufvc_server* srv, uint64_t ticket, ufvc_result* out);
 /* Blocks until the request completed (timeout_ms < 0: no limit; UFVC_PENDING on timeout). */
@@ -465,7 +501,10 @@ const char* ufvc_server_last_error(const ufvc_server* srv);
  * before the first stream is opened (UFVC_ERR_ARG afterwards).  With the temporal context every stream
  * carries its own coding state on the device: the encoder's and the decoder's context, advanced by each
  * of the stream's encode and decode requests in submission order (the first chunk uses C_0 = 0); the
- * stream's chunks therefore have to be encoded and decoded in order, as for a single context. */
+ * stream's chunks therefore have to be encoded and decoded in order, as for a single context.  A stream
+ * holds only its latest bit-stream, so each ENCODE has to be followed by its DECODE before the stream's
+ * next ENCODE when the server decodes the stream: a DECODE whose bit-stream is not the chunk after the
+ * last one the stream's decoder decoded finishes with UFVC_ERR_ARG (nothing runs, both contexts unchanged). */
 ufvc_status ufvc_server_set_temporal_context(ufvc_server* srv, const float* weights, size_t n_weights);
 ufvc_status ufvc_server_set_progressive_means(ufvc_server* srv, const float* weights, size_t n_weights);
 

@@ -126,6 +126,7 @@ struct ufvc_ctx {
     float *d_thr = nullptr, *d_qstep = nullptr, *d_qinv = nullptr;
     int* d_status = nullptr;
     long long table_spin = 0;  // bound on the entropy kernels' table-copy wait (clocks; 0: about 2 s)
+    int conv_pairs = 1;        // the staged BN = 256 tensor-core layers run on CTA pairs
     LayerW enc[L_NENC];
     LayerW dec[D_NDEC];
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
@@ -408,8 +409,9 @@ static ufvc_status tc_buffers(ufvc_ctx* ctx, Plan* p, bool enc, size_t* dry_byte
     return UFVC_OK;
 }
 
-static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out) {
-    const long long key = ((long long)W << 20) | H;
+// slot: a batched call's chunk position (every position of a batch has its own buffers)
+static ufvc_status get_plan(ufvc_ctx* ctx, int W, int H, bool for_decode, Plan** out, int slot = 0) {
+    const long long key = ((long long)slot << 40) | ((long long)W << 20) | H;
     Plan* p;
     auto it = ctx->plans.find(key);
     if (it == ctx->plans.end()) {
@@ -817,6 +819,7 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     c->d_packed = base->d_packed;
     c->d_dec = base->d_dec;
     c->table_spin = base->table_spin;
+    c->conv_pairs = base->conv_pairs;
     c->d_thr = base->d_thr;
     c->d_qstep = base->d_qstep;
     c->d_qinv = base->d_qinv;
@@ -863,7 +866,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
     d.res = res; d.res_gs = res_gs; d.out2 = out2; d.split = split; d.groups = groups;
     if (use_tc(ctx, L)) {
         d.Cin = L.cin_tc; d.wtc = L.wtc; d.cout_pad = L.cout_pad; d.out_f32 = out_f32; d.err = ctx->d_status;
-        d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc; d.kmask = L.kmask;
+        d.btc = L.btc; d.ps_major = L.ps_major; d.wsc = L.wsc; d.kmask = L.kmask; d.pairs = ctx->conv_pairs;
         if (ctx->cfg.precision == UFVC_FP8 && L.w8) {
             d.w8 = L.w8; d.cscale = L.cs8; d.out_inv = L.out_inv; d.res_s = L.res_s;
         }
@@ -1221,44 +1224,47 @@ static ufvc_status run_decoders(ufvc_ctx* ctx, Plan* p, const void* yhat, void* 
 // ------------------------------------------------------------------------------------------------
 // chunk encode / decode
 // ------------------------------------------------------------------------------------------------
-extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height,
-                                         int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, void* stream) {
-    if (!ctx || !d_frames || !d_bits || !d_nbytes || !check_shape(ctx, n_frames, width, height) || qp < 0 || qp > 63)
-        return fail(ctx, UFVC_ERR_ARG, "encode_chunk: bad argument");
-    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "encode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
-    cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaSetDevice(ctx->cfg.device));
-    Plan* p;
-    ufvc_status st = get_plan(ctx, width, height, false, &p);
-    if (st) return st;
-
-    RUN(run_encoder_front(ctx, p, d_frames, qp, s));
-    // both sections coded, laid out and the header written in one launch
+// A batch of B chunks of one size: each chunk's analysis, hyperprior and entropy parameters run in its own
+// plan (batch position b), then the rANS coding of all 2B sections is one launch.
+static ufvc_status encode_batch(ufvc_ctx* ctx, int B, const uint8_t* const* frames, int width, int height,
+                                const int* qps, uint8_t* const* bits, size_t capacity, uint64_t* const* nbytes,
+                                cudaStream_t s) {
+    Plan* plans[kRansMaxStreams];
+    for (int b = 0; b < B; ++b) {
+        RUN(get_plan(ctx, width, height, false, &plans[b], b));
+        RUN(run_encoder_front(ctx, plans[b], frames[b], qps[b], s));
+    }
+    // both sections of every chunk coded, laid out and the headers written in one launch
     prof_begin(ctx, "rans_encode", s);
     RansEncJob j{};
-    j.s[0] = RansEncSec{p->zhat, p->iz, ctx->arch.cz, (uint32_t)p->nz, p->Kz, p->scr_z, p->cap_z, 0};
-    j.s[1] = RansEncSec{p->rhat, p->idx, 0, (uint32_t)p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, 0};
-    j.nsec = 2;
-    j.out = d_bits;
-    j.capacity = capacity;
-    j.nbytes = d_nbytes;
-    j.base = p->hdr;
-    j.hdr_len = (int)p->hdr;
     const int version = 1 + (ctx->pm_on ? 1 : 0) + (ctx->tc_on ? 2 : 0);
-    const uint32_t fields[] = {'U', 'F', 'V', 'C', (uint32_t)version, (uint32_t)ctx->cfg.arch, (uint32_t)ctx->N,
-                               (uint32_t)qp};
-    for (int i = 0; i < 8; ++i) j.hdr20[i] = (uint8_t)fields[i];
-    for (int i = 0; i < 2; ++i) {
-        j.hdr20[8 + i] = (uint8_t)(width >> (8 * i));
-        j.hdr20[10 + i] = (uint8_t)(height >> (8 * i));
+    for (int b = 0; b < B; ++b) {
+        Plan* p = plans[b];
+        j.s[2 * b] = RansEncSec{p->zhat, p->iz, ctx->arch.cz, (uint32_t)p->nz, p->Kz, p->scr_z, p->cap_z, b};
+        j.s[2 * b + 1] = RansEncSec{p->rhat, p->idx, 0, (uint32_t)p->ny, ctx->cfg.lanes, p->scr_y, p->cap_y, b};
+        RansEncStream& o = j.st[b];
+        o.out = bits[b];
+        o.capacity = capacity;
+        o.nbytes = nbytes[b];
+        o.base = p->hdr;
+        o.hdr_len = (int)p->hdr;
+        const uint32_t fields[] = {'U', 'F', 'V', 'C', (uint32_t)version, (uint32_t)ctx->cfg.arch, (uint32_t)ctx->N,
+                                   (uint32_t)qps[b]};
+        for (int i = 0; i < 8; ++i) o.hdr20[i] = (uint8_t)fields[i];
+        for (int i = 0; i < 2; ++i) {
+            o.hdr20[8 + i] = (uint8_t)(width >> (8 * i));
+            o.hdr20[10 + i] = (uint8_t)(height >> (8 * i));
+        }
+        for (int i = 0; i < 4; ++i) {
+            o.hdr20[12 + i] = (uint8_t)((uint32_t)ctx->cfg.lanes >> (8 * i));
+            o.hdr20[16 + i] = (uint8_t)((uint32_t)p->Kz >> (8 * i));
+        }
+        o.iz = p->iz;
+        o.cz = ctx->arch.cz;
     }
-    for (int i = 0; i < 4; ++i) {
-        j.hdr20[12 + i] = (uint8_t)((uint32_t)ctx->cfg.lanes >> (8 * i));
-        j.hdr20[16 + i] = (uint8_t)((uint32_t)p->Kz >> (8 * i));
-    }
-    j.iz = p->iz;
-    j.cz = ctx->arch.cz;
-    j.ctl = p->ctl;
+    j.nsec = 2 * B;
+    j.nstreams = B;
+    j.ctl = plans[0]->ctl;
     j.status = ctx->d_status;
     j.spin = ctx->table_spin;
     CK(launch_rans_encode(j, ctx->d_packed, s));
@@ -1267,33 +1273,44 @@ extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames,
     return UFVC_OK;
 }
 
-// nbytes: the stream size, or (with d_nbytes) the readable capacity, the size then being read on the device
-static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, void* d_frames, int final_mode,
-                               int n_frames, int width, int height, void* stream, const uint64_t* d_nbytes = nullptr) {
-    if (!ctx || !d_bits || !d_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
-        return fail(ctx, UFVC_ERR_ARG, "decode_chunk: bad argument");
-    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "decode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
-    cudaStream_t s = (cudaStream_t)stream;
+extern "C" ufvc_status ufvc_encode_chunk(ufvc_ctx* ctx, const uint8_t* d_frames, int n_frames, int width, int height,
+                                         int qp, uint8_t* d_bits, size_t capacity, uint64_t* d_nbytes, void* stream) {
+    if (!ctx || !d_frames || !d_bits || !d_nbytes || !check_shape(ctx, n_frames, width, height) || qp < 0 || qp > 63)
+        return fail(ctx, UFVC_ERR_ARG, "encode_chunk: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "encode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
     CK(cudaSetDevice(ctx->cfg.device));
-    Plan* p;
-    ufvc_status st = get_plan(ctx, width, height, true, &p);
-    if (st) return st;
+    return encode_batch(ctx, 1, &d_frames, width, height, &qp, &d_bits, capacity, &d_nbytes, (cudaStream_t)stream);
+}
 
+// nbytes: the stream size, or (with d_nbytes) the readable capacity, the size then being read on the device
+static ufvc_status decode_batch(ufvc_ctx* ctx, int B, const uint8_t* const* bits, size_t nbytes, void* const* frames,
+                                int final_mode, int width, int height, cudaStream_t s,
+                                const uint64_t* const* d_nbytes = nullptr) {
+    Plan* plans[kRansMaxDecSec];
+    for (int b = 0; b < B; ++b) RUN(get_plan(ctx, width, height, true, &plans[b], b));
     const Arch& a = ctx->arch;
     const bool fp32 = ctx->cfg.precision == UFVC_FP32, fp8 = ctx->cfg.precision == UFVC_FP8;
-    // z^ section: the header is checked in the same launch (its scale indices are the section's tables)
+    // z^ sections: each chunk's header is checked in the same launch (its scale indices are the section's
+    // tables)
     prof_begin(ctx, "rans_decode_z", s);
     RansDecJob jz{};
-    jz.bits = d_bits;
-    jz.nbytes = nbytes;
-    jz.sec_off = p->hdr;
-    jz.idx = d_bits + 20;
+    for (int b = 0; b < B; ++b) {
+        Plan* p = plans[b];
+        RansDecSec& e = jz.s[b];
+        e.bits = bits[b];
+        e.nbytes = nbytes;
+        e.sec_off = p->hdr;
+        e.idx = bits[b] + 20;
+        e.next_off = p->next_z;
+        e.sym = p->dzhat;
+        e.qp_out = p->qp_dev;
+        e.ver_out = p->ver_dev;
+    }
+    jz.nsec = B;
     jz.idx_period = a.cz;
-    jz.n = (uint32_t)p->nz;
-    jz.K = p->Kz;
-    jz.next_off = p->next_z;
+    jz.n = (uint32_t)plans[0]->nz;
+    jz.K = plans[0]->Kz;
     jz.out = kDecSym;
-    jz.sym = p->dzhat;
     jz.hdr_cz = a.cz;
     jz.arch = ctx->cfg.arch;
     jz.N = ctx->N;
@@ -1302,62 +1319,121 @@ static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbyt
     jz.Ky = ctx->cfg.lanes;
     jz.allow_pm = ctx->pm_on;
     jz.temporal = ctx->tc_on;
-    jz.qp_out = p->qp_dev;
-    jz.ver_out = p->ver_dev;
     jz.status = ctx->d_status;
     jz.spin = ctx->table_spin;
     CK(launch_rans_decode(jz, ctx->d_dec, s));
     prof_end(ctx, s, 1);
-    ctx->cur_ws = &p->ws_dec;
-    const void* cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
-    // the last hyper-synthesis layer also forms the scale indices (at the rate the header carries)
-    const EntParams ent{p->didx, nullptr, nullptr, p->qp_dev, 0, false};
-    RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s, cin, p->t_pc_d, &ent));
-    // y^ section, ending exactly at the stream's end; with the single-pass means the decoder writes
+    const void* cin = nullptr;
+    for (int b = 0; b < B; ++b) {
+        Plan* p = plans[b];
+        ctx->cur_ws = &p->ws_dec;
+        cin = ctx->tc_on ? (ctx->cur_cin ? ctx->cur_cin : (const void*)p->t_zero) : nullptr;
+        // the last hyper-synthesis layer also forms the scale indices (at the rate the header carries)
+        const EntParams ent{p->didx, nullptr, nullptr, p->qp_dev, 0, false};
+        RUN(run_hyper_synthesis(ctx, p, p->dzhat, p->dzf, p->ds1, p->ds2, p->dmu, p->dls, s, cin, p->t_pc_d, &ent));
+    }
+    // y^ sections, each ending exactly at its stream's end; with the single-pass means the decoder writes
     // y^ = r^ q + mu itself, the progressive means need r^ first
     prof_begin(ctx, "rans_decode_y", s);
     RansDecJob jy{};
-    jy.bits = d_bits;
-    jy.nbytes = nbytes;
-    jy.sec_off_dev = p->next_z;
-    jy.expect_end = d_nbytes ? 0 : nbytes;
-    jy.expect_end_dev = d_nbytes;
-    jy.idx = p->didx;
-    jy.n = (uint32_t)p->ny;
+    for (int b = 0; b < B; ++b) {
+        Plan* p = plans[b];
+        RansDecSec& e = jy.s[b];
+        e.bits = bits[b];
+        e.nbytes = nbytes;
+        e.sec_off_dev = p->next_z;
+        e.expect_end = d_nbytes ? 0 : nbytes;
+        e.expect_end_dev = d_nbytes ? d_nbytes[b] : nullptr;
+        e.idx = p->didx;
+        e.sym = p->drhat;
+        e.yout = fp32 ? (void*)p->yhat : (void*)p->yhat_bf;
+        e.mu = p->dmu;
+        e.qp_dev = p->qp_dev;
+    }
+    jy.nsec = B;
+    jy.n = (uint32_t)plans[0]->ny;
     jy.K = ctx->cfg.lanes;
     jy.out = ctx->pm_on ? kDecSym : fp32 ? kDecF32 : fp8 ? kDecE4M3 : kDecBf16;
-    jy.sym = p->drhat;
-    jy.yout = fp32 ? (void*)p->yhat : (void*)p->yhat_bf;
-    jy.mu = p->dmu;
     jy.qstep_all = ctx->d_qstep;
-    jy.qp_dev = p->qp_dev;
     jy.inv8 = fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f;
     jy.status = ctx->d_status;
     jy.spin = ctx->table_spin;
     CK(launch_rans_decode(jy, ctx->d_dec, s));
     prof_end(ctx, s, 1);
-    if (ctx->pm_on) {  // a version-1 stream leaves the means of the single pass (the steps check the version)
-        RUN(run_progressive(ctx, p->Hy, p->Wy, nullptr, p->drhat, p->dmu, p->ds2, p->qp_dev, 0, p->ver_dev, p->pm_in_d,
-                            p->pm_h_d, p->pm_mu_d, s));
-        prof_begin(ctx, "dequant", s);
-        launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
-                       fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
-                       fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
-        prof_end(ctx, s, 1);
+    for (int b = 0; b < B; ++b) {
+        Plan* p = plans[b];
+        if (ctx->pm_on) {  // a version-1 stream leaves the means of the single pass (the steps check the version)
+            RUN(run_progressive(ctx, p->Hy, p->Wy, nullptr, p->drhat, p->dmu, p->ds2, p->qp_dev, 0, p->ver_dev,
+                                p->pm_in_d, p->pm_h_d, p->pm_mu_d, s));
+            prof_begin(ctx, "dequant", s);
+            launch_dequant(p->drhat, p->dmu, p->ny, ctx->d_qstep, p->qp_dev, fp32 ? p->yhat : nullptr,
+                           fp32 || fp8 ? nullptr : p->yhat_bf, s, fp8 ? reinterpret_cast<uint8_t*>(p->yhat_bf) : nullptr,
+                           fp8 ? 1.f / ctx->act_scale[T_YHAT] : 0.f);
+            prof_end(ctx, s, 1);
+        }
+        if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
+        const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
+        if (ctx->dcm) {  // chunk decoder, frame decoders, then the context generation in place on F
+            RUN(run_dc_trunk(ctx, p, yh, cin, p->dc_F, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
+            RUN(run_dc_frames(ctx, p, p->dc_F, frames[b], final_mode, s));
+            if (ctx->cur_cout) RUN(run_dc_context(ctx, p, p->dc_F, ctx->cur_cout, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
+            continue;
+        }
+        if (cin) RUN(run_chunk_feature(ctx, p, yh, cin, p->t_F_d, ctx->cur_cout, s));
+        RUN(run_decoders(ctx, p, yh, frames[b], final_mode, s, cin ? (const void*)p->t_F_d : nullptr));
     }
-    if (fp32) probe(ctx, T_YHAT, p->yhat, p->ny, s);
-    const void* yh = fp32 ? (const void*)p->yhat : (const void*)p->yhat_bf;
-    if (ctx->dcm) {  // chunk decoder, frame decoders, then the context generation in place on F
-        RUN(run_dc_trunk(ctx, p, yh, cin, p->dc_F, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
-        RUN(run_dc_frames(ctx, p, p->dc_F, d_frames, final_mode, s));
-        if (ctx->cur_cout) RUN(run_dc_context(ctx, p, p->dc_F, ctx->cur_cout, p->dc_t1d, p->dc_t2d, p->dc_t3d, s));
-        CK(cudaGetLastError());
-        return UFVC_OK;
-    }
-    if (cin) RUN(run_chunk_feature(ctx, p, yh, cin, p->t_F_d, ctx->cur_cout, s));
-    RUN(run_decoders(ctx, p, yh, d_frames, final_mode, s, cin ? (const void*)p->t_F_d : nullptr));
     CK(cudaGetLastError());
     return UFVC_OK;
+}
+
+static ufvc_status decode_impl(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, void* d_frames, int final_mode,
+                               int n_frames, int width, int height, void* stream, const uint64_t* d_nbytes = nullptr) {
+    if (!ctx || !d_bits || !d_frames || !check_shape(ctx, n_frames, width, height) || nbytes == 0)
+        return fail(ctx, UFVC_ERR_ARG, "decode_chunk: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "decode_chunk: FP8 context not calibrated (ufvc_calibrate_fp8)");
+    CK(cudaSetDevice(ctx->cfg.device));
+    return decode_batch(ctx, 1, &d_bits, nbytes, &d_frames, final_mode, width, height, (cudaStream_t)stream,
+                        d_nbytes ? &d_nbytes : nullptr);
+}
+
+// Batched calls (serving): B chunks of one size, each with its own buffers, their rANS sections coded in one
+// launch.  Not for contexts that carry a temporal context (each stream has its own).
+static bool batch_ok(ufvc_ctx* ctx, int batch) {
+    return batch >= 1 && batch <= kRansMaxDecSec && (batch == 1 || (!ctx->tc_on && !ctx->dcm));
+}
+
+extern "C" ufvc_status ufvc_encode_chunks(ufvc_ctx* ctx, int batch, const uint8_t* const* d_frames, int n_frames,
+                                          int width, int height, const int* qps, uint8_t* const* d_bits,
+                                          size_t capacity, uint64_t* const* d_nbytes, void* stream) {
+    if (!ctx || !d_frames || !d_bits || !d_nbytes || !qps || !check_shape(ctx, n_frames, width, height))
+        return fail(ctx, UFVC_ERR_ARG, "encode_chunks: bad argument");
+    if (!batch_ok(ctx, batch))
+        return fail(ctx, batch >= 1 && batch <= kRansMaxDecSec ? UFVC_ERR_UNSUPPORTED : UFVC_ERR_ARG,
+                    "encode_chunks: batch must be 1..8, and 1 for a context with a temporal context");
+    for (int b = 0; b < batch; ++b)
+        if (!d_frames[b] || !d_bits[b] || !d_nbytes[b] || qps[b] < 0 || qps[b] > 63)
+            return fail(ctx, UFVC_ERR_ARG, "encode_chunks: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "encode_chunks: FP8 context not calibrated (ufvc_calibrate_fp8)");
+    CK(cudaSetDevice(ctx->cfg.device));
+    return encode_batch(ctx, batch, d_frames, width, height, qps, d_bits, capacity, d_nbytes, (cudaStream_t)stream);
+}
+
+extern "C" ufvc_status ufvc_decode_chunks(ufvc_ctx* ctx, int batch, const uint8_t* const* d_bits, size_t capacity,
+                                          const uint64_t* const* d_nbytes, uint8_t* const* d_frames, int n_frames,
+                                          int width, int height, void* stream) {
+    if (!ctx || !d_frames || !d_bits || !d_nbytes || !check_shape(ctx, n_frames, width, height) || capacity == 0)
+        return fail(ctx, UFVC_ERR_ARG, "decode_chunks: bad argument");
+    if (!batch_ok(ctx, batch))
+        return fail(ctx, batch >= 1 && batch <= kRansMaxDecSec ? UFVC_ERR_UNSUPPORTED : UFVC_ERR_ARG,
+                    "decode_chunks: batch must be 1..8, and 1 for a context with a temporal context");
+    for (int b = 0; b < batch; ++b)
+        if (!d_frames[b] || !d_bits[b] || !d_nbytes[b]) return fail(ctx, UFVC_ERR_ARG, "decode_chunks: bad argument");
+    if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "decode_chunks: FP8 context not calibrated (ufvc_calibrate_fp8)");
+    CK(cudaSetDevice(ctx->cfg.device));
+    void* fr[kRansMaxDecSec];
+    for (int b = 0; b < batch; ++b) fr[b] = d_frames[b];
+    return decode_batch(ctx, batch, d_bits, capacity, fr, OUT_PS_FINAL_U8, width, height, (cudaStream_t)stream,
+                        d_nbytes);
 }
 
 extern "C" ufvc_status ufvc_decode_chunk(ufvc_ctx* ctx, const uint8_t* d_bits, size_t nbytes, uint8_t* d_frames,
@@ -1718,6 +1794,12 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
     return UFVC_OK;
 }
 
+extern "C" ufvc_status ufvc_set_conv_pairs(ufvc_ctx* ctx, int enable) {
+    if (!ctx || (enable != 0 && enable != 1)) return fail(ctx, UFVC_ERR_ARG, "set_conv_pairs: bad argument");
+    ctx->conv_pairs = enable;
+    return UFVC_OK;
+}
+
 extern "C" ufvc_status ufvc_set_table_wait_limit(ufvc_ctx* ctx, long long cycles) {
     if (!ctx || cycles < 0) return fail(ctx, UFVC_ERR_ARG, "set_table_wait_limit: bad argument");
     ctx->table_spin = cycles;
@@ -1774,9 +1856,10 @@ extern "C" ufvc_status ufvc_rans_encode(ufvc_ctx* ctx, const int16_t* d_sym, con
     RansEncJob j{};
     j.s[0] = RansEncSec{d_sym, d_idx, 0, (uint32_t)n, lanes, ctx->r_scr, cap_lane, 0};
     j.nsec = 1;
-    j.out = d_out;
-    j.capacity = capacity;
-    j.nbytes = d_nbytes;
+    j.st[0].out = d_out;
+    j.st[0].capacity = capacity;
+    j.st[0].nbytes = d_nbytes;
+    j.nstreams = 1;
     j.ctl = ctx->r_ctl;
     j.status = ctx->d_status;
     j.spin = ctx->table_spin;
@@ -1794,13 +1877,14 @@ extern "C" ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size
     CK(cudaSetDevice(ctx->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     RansDecJob j{};
-    j.bits = d_in;
-    j.nbytes = nbytes;
-    j.idx = d_idx;
+    j.s[0].bits = d_in;
+    j.s[0].nbytes = nbytes;
+    j.s[0].idx = d_idx;
+    j.s[0].sym = d_sym;
+    j.nsec = 1;
     j.n = (uint32_t)n;
     j.K = lanes;
     j.out = kDecSym;
-    j.sym = d_sym;
     j.status = ctx->d_status;
     j.spin = ctx->table_spin;
     prof_begin(ctx, "rans_decode", s);

@@ -76,12 +76,15 @@ __device__ __forceinline__ const float* stage_bias(const TcArgs& p, float* sbias
     return sbias;  // visible after the block barrier that follows the set-up
 }
 
+// CL: acquire at cluster scope (a barrier the other CTA of a pair arrives on)
+template <bool CL = false>
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          bool honour_abort = true) {
-    if (ptx::mbar_try_wait(bar, parity)) return true;
+    auto test = [&] { return CL ? ptx::mbar_try_wait_cluster(bar, parity) : ptx::mbar_try_wait(bar, parity); };
+    if (test()) return true;
     const long long t0 = clock64();
     while (true) {
-        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (test()) return true;
         if (honour_abort && *abort_flag) return false;
         if (clock64() - t0 > kSpinLimit) {
             *abort_flag = 1;
@@ -274,7 +277,14 @@ enum { OP_BF16 = 0, OP_E4M3 = 1, OP_BF16_32 = 2 };
 // MT = 2: a tile is two 128-pixel sub-tiles stacked vertically (2 TH x TW pixels, one TMA box of 256 rows),
 // which share each stage's weight tile: two MMAs per K slice into two accumulators, 25 % fewer operand
 // bytes landing in shared memory per MMA; one epilogue group drains and stores the sub-tiles in turn.
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1>
+// PAIR: the kernel runs as clusters of two CTAs on two SMs that share one MMA of M = 256
+// (tcgen05.mma.cta_group::2, issued by the even CTA): a tile is two stacked 128-pixel sub-tiles, one per
+// CTA; each CTA loads its own sub-tile's input rows and HALF of the stage's weight rows (BN / 2), and
+// each holds its sub-tile's 128 x BN accumulator in its own TMEM, so a third fewer operand bytes land in
+// each SM's shared memory per MMA at BN = 256.  Both CTAs' loads complete on the even CTA's stage
+// barrier (its producer expects the bytes of both); the MMA commits arrive on both CTAs' barriers; the
+// odd CTA's epilogue frees an accumulator by arriving on the even CTA's barrier.
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
@@ -283,8 +293,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     static_assert(MT == 1 || (MT == 2 && !F8 && OP == OP_BF16), "two sub-tiles: BF16 operands");
+    static_assert(!PAIR || (MT == 1 && OP == OP_BF16 && !KM && BN % 32 == 0), "CTA pairs: BF16, one sub-tile each");
     constexpr int A_BYTES = 128 * MT * ROWB;
-    constexpr int B_BYTES = BN * ROWB;
+    constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROWB;  // this CTA's weight rows of a stage
+    constexpr int SUBS = PAIR ? 2 : MT;  // 128-pixel sub-tiles of a tile
     constexpr int EG = MT == 2 ? 1 : epi_groups(BN);  // epilogue groups (tiles drained concurrently)
     constexpr int WPQ = 4 / EG;         // warps per TMEM lane quarter in a group
     constexpr int NACC = 2 * EG;        // TMEM accumulators
@@ -317,6 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float* bias_all = stage_bias(p, sbias);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = PAIR ? ptx::cluster_rank() : 0;  // this CTA's place in its pair
+    const int cid = PAIR ? blockIdx.x >> 1 : blockIdx.x, ncl = PAIR ? gridDim.x >> 1 : gridDim.x;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             ptx::mbar_init(&full[s], 1);
@@ -324,7 +338,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < NACC; ++a) {
             ptx::mbar_init(&tfull[a], 1);
-            ptx::mbar_init(&tempty[a], 128 * WPQ);
+            // pairs: one arrival per epilogue warp of the group, in both CTAs (on the even CTA's barrier)
+            ptx::mbar_init(&tempty[a], PAIR ? 2 * 4 * WPQ : 128 * WPQ);
         }
         ptx::mbar_init(drain, 1);
         for (int gq = 0; gq < 4; ++gq) {
@@ -334,14 +349,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
-    if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 1) {
+        if constexpr (PAIR) ptx::tmem_alloc_pair(tmem_slot, TMEM_COLS);
+        else ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    }
     if (warp == 0 && lane == 0) {
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
         if (STAGED) ptx::prefetch_tmap(&tmC);
     }
     ptx::tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) ptx::cluster_sync();  // both CTAs' barriers exist before either signals the other's
+    else __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     // the set-up above (barriers, TMEM, biases, descriptor prefetch) may overlap the previous kernel's
@@ -359,9 +378,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
             bool ok = true;
-            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x) {
+            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
                 const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
-                const int h0 = (mt / p.tiles_w) * p.TH * MT, w0 = (mt % p.tiles_w) * p.TW;
+                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (int)crank * p.TH, w0 = (mt % p.tiles_w) * p.TW;
                 const int ag = p.a_grouped ? g : 0;
                 for (int ks = 0; ks < p.ksteps; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;  // all-zero weights: no stage
@@ -369,37 +388,59 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t ph = (it / STAGES) & 1;
                     ++it;
                     if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) { ok = false; break; }
-                    ptx::mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
                     const int tap = ks / p.cin_chunks, c0 = (ks - tap * p.cin_chunks) * CH;
                     const int ky = tap / p.k, kx = tap - ky * p.k;
-                    if (p.stride == 1) {
-                        ptx::tma_load_4d(sA + s * A_BYTES, &tmA, &full[s], c0, w0 + kx - p.pad, h0 + ky - p.pad, ag);
+                    if constexpr (PAIR) {
+                        // both CTAs' copies complete on the even CTA's barrier, which expects all of them
+                        const uint32_t fb = ptx::mapa(ptx::smem_u32(&full[s]), 0);
+                        if (crank == 0) ptx::mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+                        if (p.stride == 1) {
+                            ptx::tma_load_4d_pair(sA + s * A_BYTES, &tmA, fb, c0, w0 + kx - p.pad, h0 + ky - p.pad, ag);
+                        } else {
+                            const int tx = kx - p.pad, ty = ky - p.pad;
+                            const int wp = tx & 1, hp = ty & 1;
+                            ptx::tma_load_5d_pair(sA + s * A_BYTES, &tmA, fb, c0, wp, w0 + ((tx - wp) >> 1), hp,
+                                                  h0 + ((ty - hp) >> 1));
+                        }
+                        ptx::tma_load_3d_pair(sB + s * B_BYTES, &tmB, fb, ks * CH, nt * BN + (int)crank * (BN / 2), g);
                     } else {
-                        const int tx = kx - p.pad, ty = ky - p.pad;
-                        const int wp = tx & 1, hp = ty & 1;
-                        ptx::tma_load_5d(sA + s * A_BYTES, &tmA, &full[s], c0, wp, w0 + ((tx - wp) >> 1), hp,
-                                         h0 + ((ty - hp) >> 1));
+                        ptx::mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                        if (p.stride == 1) {
+                            ptx::tma_load_4d(sA + s * A_BYTES, &tmA, &full[s], c0, w0 + kx - p.pad, h0 + ky - p.pad, ag);
+                        } else {
+                            const int tx = kx - p.pad, ty = ky - p.pad;
+                            const int wp = tx & 1, hp = ty & 1;
+                            ptx::tma_load_5d(sA + s * A_BYTES, &tmA, &full[s], c0, wp, w0 + ((tx - wp) >> 1), hp,
+                                             h0 + ((ty - hp) >> 1));
+                        }
+                        ptx::tma_load_3d(sB + s * B_BYTES, &tmB, &full[s], ks * CH, nt * BN, g);
                     }
-                    ptx::tma_load_3d(sB + s * B_BYTES, &tmB, &full[s], ks * CH, nt * BN, g);
                     used[s] = true;
                     last_par[s] = ph;
                 }
             }
-            // make sure no copy is still writing shared memory when the CTA exits
+            // make sure no copy is still writing shared memory when the CTA exits (pairs: the even CTA's
+            // barriers count the odd CTA's copies too, and the odd CTA stays until the closing cluster
+            // barrier, which the even CTA reaches after these waits)
+            if (!PAIR || crank == 0) {
 #pragma unroll
-            for (int s = 0; s < STAGES; ++s)
-                if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+                for (int s = 0; s < STAGES; ++s)
+                    if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+            }
         }
         __syncwarp();
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(BN) : ptx::idesc_bf16(BN);
+        // ------------------------------------------------------------ MMA issuer (pairs: the even CTA's)
+        if (PAIR && crank != 0) {
+            // the odd CTA issues nothing; its accumulators are complete when the even CTA's last commit lands
+            if (lane == 0) wait_bar(drain, 0, abort_flag, p.err, false);
+        } else if (lane == 0) {
+            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(BN) : PAIR ? ptx::idesc_bf16_m256(BN) : ptx::idesc_bf16(BN);
             int it = 0, tl = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < p.total_tiles && ok; t += gridDim.x, ++tl) {
+            for (int t = cid; t < p.total_tiles && ok; t += ncl, ++tl) {
                 const int acc = tl % NACC, use = tl / NACC;
-                if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
+                if (!wait_bar<PAIR>(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem_base + acc * ACOLS;
                 bool first = true;  // the tile's first executed step overwrites the accumulator
@@ -421,6 +462,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=16 BF16 per 64-byte row
                             ptx::mma_f16(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
                                          !first || kk != 0);
+                    } else if constexpr (PAIR) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // M = 256: rows 0..127 from this CTA, 128..255 from the odd one
+                            ptx::mma_f16_pair(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32), idesc,
+                                              !first || kk != 0);
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
@@ -429,13 +475,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 ptx::mma_f16(d + h * BN, ptx::sdesc_sw128(a0 + h * 16384 + kk * 32),
                                              ptx::sdesc_sw128(b0 + kk * 32), idesc, !first || kk != 0);
                     }
-                    ptx::mma_commit(&empty[s]);
+                    if constexpr (PAIR) ptx::mma_commit_pair(&empty[s], 3);  // both CTAs' stage s is free
+                    else ptx::mma_commit(&empty[s]);
                     first = false;
                 }
-                if (ok) ptx::mma_commit(&tfull[acc]);
+                if (ok) {
+                    if constexpr (PAIR) ptx::mma_commit_pair(&tfull[acc], 3);
+                    else ptx::mma_commit(&tfull[acc]);
+                }
             }
             // all issued MMAs complete before TMEM is released
-            ptx::mma_commit(drain);
+            if constexpr (PAIR) ptx::mma_commit_pair(drain, 3);
+            else ptx::mma_commit(drain);
             wait_bar(drain, 0, abort_flag, p.err, false);
         }
         __syncwarp();
@@ -451,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* sCg = sC + egrp * (BN / 64) * (128 * 128);      // this group's staging slabs
         int tl = egrp, k = 0;  // k counts sub-tiles (the staging barriers' phases)
         bool run = true;
-        for (int t = blockIdx.x + egrp * gridDim.x; run && t < p.total_tiles; t += EG * gridDim.x, tl += EG) {
+        for (int t = cid + egrp * ncl; run && t < p.total_tiles; t += EG * ncl, tl += EG) {
             const int acc = tl % NACC, use = tl / NACC;
             if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
@@ -459,7 +510,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int w0 = (mt % p.tiles_w) * p.TW;
 #pragma unroll 1
             for (int hs = 0; hs < MT; ++hs, ++k) {
-                const int h0 = (mt / p.tiles_w) * p.TH * MT + hs * p.TH;
+                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (PAIR ? (int)crank : hs) * p.TH;
                 const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
                 const bool valid = oh < p.Ho && ow < p.Wo;
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * ACOLS + hs * BN;
@@ -495,7 +546,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (hs == MT - 1) {  // every sub-tile's columns are in registers or staged: free the accumulator
                     ptx::tc_fence_before();
-                    ptx::mbar_arrive(&tempty[acc]);
+                    if constexpr (PAIR) {  // one arrival per warp, on the even CTA's barrier
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive_remote(ptx::mapa(ptx::smem_u32(&tempty[acc]), 0));
+                    } else {
+                        ptx::mbar_arrive(&tempty[acc]);
+                    }
                 }
                 if (!ok) { run = false; break; }
                 if constexpr (STAGED) {
@@ -527,10 +583,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (elected) ptx::bulk_wait0();  // stores complete before the CTA (and its shared memory) ends
     }
     ptx::tc_fence_before();
-    __syncthreads();
+    // pairs: neither CTA leaves (freeing the shared memory and barriers the other signals) before both
+    // are done
+    if constexpr (PAIR) ptx::cluster_sync();
+    else __syncthreads();
     if (warp == 1) {
         ptx::tc_fence_after();
-        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
+        if constexpr (PAIR) ptx::tmem_dealloc_pair(tmem_base, TMEM_COLS);
+        else ptx::tmem_dealloc(tmem_base, TMEM_COLS);
     }
 }
 
@@ -1100,20 +1160,30 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1>
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
     constexpr int EG = MT == 2 ? 1 : epi_groups(BN);
-    constexpr int kSmem = STAGES * (128 * MT * ROWB + BN * ROWB) + (STAGED ? 128 * BN * 2 * EG : 0) + kSmemExtra;
+    constexpr int kSmem = STAGES * (128 * MT * ROWB + (PAIR ? BN / 2 : BN) * ROWB) +
+                          (STAGED ? 128 * BN * 2 * EG : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
-    cudaError_t e = smem_optin((const void*)conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>, smem);
+    const void* fn = (const void*)conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>;
+    cudaError_t e = smem_optin(fn, smem);
     if (e != cudaSuccess) return e;
+    if constexpr (PAIR) {
+        // one cluster of two CTAs per pair of SMs that can hold them at once, each cluster a tile at a time
+        const int pairs = max_pairs(fn, smem, kThreads);
+        if (pairs < 1) return cudaErrorInvalidConfiguration;
+        const int grid = 2 * (args.total_tiles < pairs ? args.total_tiles : pairs);
+        return launch_pdl_pair(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>, dim3(grid), dim3(kThreads), smem,
+                               s, a, b, c, args);
+    }
     const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT>, dim3(grid), dim3(kThreads), smem, s, a, b, c,
-                      args);
+    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>, dim3(grid), dim3(kThreads), smem, s, a, b,
+                      c, args);
 }
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
@@ -1237,9 +1307,13 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const long long pairs = (long long)((Wo + a.TW - 1) / a.TW) * ((Ho + 2 * a.TH - 1) / (2 * a.TH)) *
                             (d.cout_pad / 128) * d.groups;
     const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.kmask == 0 && pairs >= 2 * 148) ? 2 : 1;
+    // CTA pairs (one M = 256 MMA over two SMs, each loading half of the weights): the staged BN = 256
+    // layers (the decoders' pixel-shuffle layers D0, U1, U2)
+    const bool pair = d.pairs && !f8 && !c32 && !halo && staged && BN == 256 && d.kmask == 0;
+    const int SUB = (MT == 2 || pair) ? 2 : 1;  // 128-pixel sub-tiles per tile
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
-    a.tiles_h = (Ho + a.TH * MT - 1) / (a.TH * MT);
+    a.tiles_h = (Ho + a.TH * SUB - 1) / (a.TH * SUB);
     a.n_tiles = d.cout_pad / BN;
     a.groups = d.groups;
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
@@ -1297,7 +1371,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         const cuuint64_t K = (cuuint64_t)d.k * d.k * d.Cin;
         cuuint64_t dims[3] = {K, (cuuint64_t)d.cout_pad, (cuuint64_t)d.groups};
         cuuint64_t str[2] = {K * esz, K * d.cout_pad * esz};
-        cuuint32_t box[3] = {boxc, (cuuint32_t)BN, 1};
+        cuuint32_t box[3] = {boxc, (cuuint32_t)(pair ? BN / 2 : BN), 1};  // a pair's CTA loads half the rows
         if (!encode_map(&mb, f8 ? d.w8 : d.wtc, 3, dims, str, box, dt, swz)) return cudaErrorInvalidValue;
     }
     CUtensorMap mc = mb;  // unused by the unstaged kernels
@@ -1351,7 +1425,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             case 128: return MT == 2 ? launch_bn<128, 3, true, OP_BF16, false, 2>(ma, mb, mc, a, s)
                                      : launch_bn<128, 4, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
-            default: return launch_bn<256, 3, true>(ma, mb, mc, a, s);
+            default: return pair ? launch_bn<256, 4, true, OP_BF16, false, 1, true>(ma, mb, mc, a, s)
+                                 : launch_bn<256, 3, true>(ma, mb, mc, a, s);
         }
     }
     if (c32) return BN == 64 ? launch_bn<64, 12, false, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;

@@ -91,9 +91,10 @@ extern "C" ufvc_status ufvc_rans_encode_noalloc(ufvc_ctx* ctx, const int16_t* d_
     ufvc::RansEncJob j{};
     j.s[0] = ufvc::RansEncSec{d_sym, d_idx, 0, (uint32_t)n, lanes, rows, (int)cap_lane, 0};
     j.nsec = 1;
-    j.out = d_out;
-    j.capacity = capacity;
-    j.nbytes = d_nbytes;
+    j.st[0].out = d_out;
+    j.st[0].capacity = capacity;
+    j.st[0].nbytes = d_nbytes;
+    j.nstreams = 1;
     j.ctl = ctl;
     j.status = ufvc::ctx_status_word(ctx);
     j.spin = ufvc::ctx_table_spin(ctx);

@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
     }
     __syncthreads();
     const int t = ticket_sh;
-    const int total_blocks = J.s[0].nblk + (J.nsec > 1 ? J.s[1].nblk : 0);
-    if (!loaded || t < 0 || t >= total_blocks) goto done;
+    if (!loaded || t < 0 || t >= J.grid) goto done;
     {
-        const int si = t < J.s[0].nblk ? 0 : 1;
+        int si = 0;  // the section of this ticket (sections take consecutive ticket ranges)
+        while (si + 1 < J.nsec && t >= J.s[si + 1].first) ++si;
         const RansEncSec& S = J.s[si];
-        const int bs = t - (si ? J.s[0].nblk : 0);  // block within the section
+        const RansEncStream& O = J.st[S.stream];
+        const int bs = t - S.first;  // block within the section
         const int lane = bs * T + threadIdx.x;
         const bool live = (int)threadIdx.x < T && lane < S.K;
         const uint32_t cnt = live ? lane_elems(S.n, S.K, lane) : 0u;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
         const uint32_t excl = block_excl_scan(words, &agg, scan_sh);
         if (threadIdx.x < 32) {
             const int l = threadIdx.x;
-            const int first = si ? J.s[0].nblk : 0;  // the section's first ticket
+            const int first = S.first;  // the section's first ticket
             uint64_t pre = 0;
             bool ok = true;
             if (l == 0) ptx::st_release_u64(&ctl->flag[t], (t == first ? kFlagIncl : kFlagAgg) | agg);
@@ -338,13 +339,14 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
             }
             if (l == 0) {
                 if (ok && t != first) ptx::st_release_u64(&ctl->flag[t], kFlagIncl | (pre + agg));
-                uint64_t base = J.base;
-                if (ok && si == 1) {  // the y^ section follows the z^ section: its total is the last z^ block's
-                    const int lz = J.s[0].nblk - 1;
+                uint64_t base = O.base;
+                if (ok && S.prev >= 0) {  // the y^ section follows the z^ section: its total is the last z^ block's
+                    const RansEncSec& P = J.s[S.prev];
+                    const int lz = P.first + P.nblk - 1;
                     uint64_t f;
                     while (!((f = ptx::ld_acquire_u64(&ctl->flag[lz])) & kFlagIncl))
                         if (clock64() - t0 > kSpinDefault) { ok = false; break; }
-                    if (ok) base = (J.base + 4ull * J.s[0].K + 2ull * (f & kFlagMask) + 3ull) & ~3ull;
+                    if (ok) base = (O.base + 4ull * P.K + 2ull * (f & kFlagMask) + 3ull) & ~3ull;
                 }
                 if (!ok) {
                     set_status(J.status, UFVC_ERR_TIMEOUT);
@@ -359,8 +361,8 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
         {
             const uint64_t base = base_sh, words_at = base + 4ull * S.K;
             const uint64_t off = words_at + 2ull * (pre_sh + excl);
-            uint8_t* out = J.out;
-            const uint64_t cap = J.capacity;
+            uint8_t* out = O.out;
+            const uint64_t cap = O.capacity;
             if (live && base + 4ull * lane + 4 <= cap) {
                 uint8_t* c = out + base + 4ull * lane;
                 c[0] = words & 0xFF; c[1] = (words >> 8) & 0xFF; c[2] = (words >> 16) & 0xFF; c[3] = words >> 24;
@@ -396,17 +398,17 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
                 const uint64_t end = words_at + 2ull * (pre_sh + agg), end4 = (end + 3) & ~3ull;
                 for (uint64_t b = end; b < end4; ++b)
                     if (b < cap) out[b] = 0;
-                if (si == J.nsec - 1) {
-                    *J.nbytes = end4;
+                if (S.last) {
+                    *O.nbytes = end4;
                     if (end4 > cap) set_status(J.status, UFVC_ERR_CAPACITY);
                 }
             }
-            if (t == 0 && J.hdr_len > 0) {  // the container header
-                if ((uint64_t)J.hdr_len > cap) {
+            if (bs == 0 && S.prev < 0 && O.hdr_len > 0) {  // the stream's container header
+                if ((uint64_t)O.hdr_len > cap) {
                     if (threadIdx.x == 0) set_status(J.status, UFVC_ERR_CAPACITY);
                 } else {
-                    for (int i = threadIdx.x; i < J.hdr_len; i += BT)
-                        out[i] = i < 20 ? J.hdr20[i] : i < 20 + J.cz ? J.iz[i - 20] : 0;
+                    for (int i = threadIdx.x; i < O.hdr_len; i += BT)
+                        out[i] = i < 20 ? O.hdr20[i] : i < 20 + O.cz ? O.iz[i - 20] : 0;
                 }
             }
         }
@@ -429,28 +431,40 @@ done:
     }
 }
 
-// Threads per block for sections of K0 and K1 lanes: the smallest multiple of 32 for which the sections'
-// blocks fit in one wave of one block per SM, at most 512 (two sections of 65536 lanes then take 256
-// blocks, in more than one wave: a block only ever waits on blocks that started before it).
-static int enc_threads(int K0, int K1, int sms) {
+// Threads per block (lanes per block) for the job's sections: the smallest multiple of 32 for which their
+// blocks fit in one wave of one block per SM, at most 512 (more sections or lanes then take more than one
+// wave: a block only ever waits on blocks that started before it).
+static int enc_threads(const RansEncJob& j, int sms) {
     for (int T = 32; T < 512; T += 32) {
-        const int b = (K0 + T - 1) / T + (K1 + T - 1) / T;
+        int b = 0;
+        for (int i = 0; i < j.nsec; ++i) b += (j.s[i].K + T - 1) / T;
         if (b <= sms) return T;
     }
     return 512;
 }
 
 cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cudaStream_t s) {
-    const int sms = sm_count();
-    const int T = enc_threads(j.s[0].K, j.nsec > 1 ? j.s[1].K : 0, sms);
+    if (j.nsec < 1 || j.nsec > kRansMaxEncSec || j.nstreams < 1 || j.nstreams > kRansMaxStreams)
+        return cudaErrorInvalidValue;
+    const int T = enc_threads(j, sm_count());
     j.lpb = T;
-    j.s[0].nblk = (j.s[0].K + T - 1) / T;
-    if (j.nsec > 1) j.s[1].nblk = (j.s[1].K + T - 1) / T;
-    j.grid = j.s[0].nblk + (j.nsec > 1 ? j.s[1].nblk : 0);
+    j.grid = 0;
+    int cap = 0;
+    for (int i = 0; i < j.nsec; ++i) {
+        RansEncSec& e = j.s[i];
+        if (e.K < 1 || e.stream < 0 || e.stream >= j.nstreams) return cudaErrorInvalidValue;
+        e.nblk = (e.K + T - 1) / T;
+        e.first = j.grid;
+        j.grid += e.nblk;
+        // a stream's sections are consecutive: the one before it in the same stream, and whether it ends it
+        e.prev = i > 0 && j.s[i - 1].stream == e.stream ? i - 1 : -1;
+        e.last = i + 1 == j.nsec || j.s[i + 1].stream != e.stream;
+        if (e.prev >= 0 && j.s[e.prev].prev >= 0) return cudaErrorInvalidValue;  // at most two per stream
+        cap = e.cap_lane > cap ? e.cap_lane : cap;
+    }
     if (j.grid > kRansMaxBlocks) return cudaErrorInvalidValue;
     // the words go through shared memory when every lane's row fits there beside the tables; then the
     // block needs few threads to copy them, else 512 copy from the global rows
-    const int cap = j.nsec > 1 && j.s[1].cap_lane > j.s[0].cap_lane ? j.s[1].cap_lane : j.s[0].cap_lane;
     const size_t stage = ((size_t)T * cap * 2 + 15) & ~(size_t)15;
     const bool staged = kEncTabBytes + stage <= (size_t)kEncSmemMax;
     const int BT = staged ? (T < 128 ? 128 : T) : 512;
@@ -495,19 +509,21 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     __shared__ uint32_t scan_sh[32];
     __shared__ uint64_t red_sh[32];
     __shared__ int bad_sh;
+    const int si = blockIdx.x / J.bps, blk = blockIdx.x - si * J.bps;  // section, block within it
+    const RansDecSec& S = J.s[si];
     const bool loaded = __syncthreads_and(load_table(dsm, tables, kDecTabBytes, &bar, J.status, J.spin));
     if (loaded) pdl_trigger();
     pdl_wait();
     // the rate and version the later kernels read are always written (defaults unless the header is good)
-    if (J.hdr_cz > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-        *J.qp_out = 32;
-        *J.ver_out = 1;
+    if (J.hdr_cz > 0 && blk == 0 && threadIdx.x == 0) {
+        *S.qp_out = 32;
+        *S.ver_out = 1;
     }
     if (threadIdx.x == 0) bad_sh = *(volatile int*)J.status != 0;  // an earlier stage failed: nothing to do
     __syncthreads();
     if (!loaded || bad_sh) return;
-    const uint8_t* bits = J.bits;
-    const uint64_t nbytes = J.nbytes;
+    const uint8_t* bits = S.bits;
+    const uint64_t nbytes = S.nbytes;
     const int K = J.K, T = blockDim.x;
     // ---- container header (the z^ section's launch): every block checks it; block 0 publishes the rate
     //      and the version for the later kernels
@@ -539,21 +555,21 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
                 set_status(J.status, st);
                 bad_sh = 1;
             }
-            if (blockIdx.x == 0) {
-                *J.qp_out = qp;
-                *J.ver_out = ver;
+            if (blk == 0) {
+                *S.qp_out = qp;
+                *S.ver_out = ver;
             }
         }
         __syncthreads();
         if (bad_sh) return;
     }
     // ---- the section's lane counts: prefix before this block's first lane, and the total
-    const uint64_t sec = J.sec_off_dev ? *J.sec_off_dev : J.sec_off;
+    const uint64_t sec = S.sec_off_dev ? *S.sec_off_dev : S.sec_off;
     if (sec + 4ull * K > nbytes) {
         if (threadIdx.x == 0) set_status(J.status, UFVC_ERR_CORRUPT);
         return;
     }
-    const int first = blockIdx.x * T;
+    const int first = blk * T;
     const uint8_t* cb = bits + sec;
     // the counts' 16-byte aligned superset, when it fits in shared memory and lies inside the stream
     const uintptr_t lo = reinterpret_cast<uintptr_t>(cb) & ~(uintptr_t)15;
@@ -602,12 +618,12 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     tot = block_sum_u64(tot, red_sh);
     const uint64_t words_at = sec + 4ull * K;
     const uint64_t end4 = (words_at + 2ull * tot + 3ull) & ~3ull;
-    const uint64_t expect = J.expect_end_dev ? *J.expect_end_dev : J.expect_end;
+    const uint64_t expect = S.expect_end_dev ? *S.expect_end_dev : S.expect_end;
     if (end4 > nbytes || (expect != 0 && end4 != expect)) {
         if (threadIdx.x == 0) set_status(J.status, UFVC_ERR_CORRUPT);
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0 && J.next_off) *J.next_off = end4;
+    if (blk == 0 && threadIdx.x == 0 && S.next_off) *S.next_off = end4;
     const int lane = first + threadIdx.x;
     const bool inl = lane < K;
     const uint32_t words = inl ? count_at(lane) : 0u;
@@ -623,14 +639,14 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     const uint32_t cmax = __reduce_max_sync(0xffffffffu, mine);
     const uint32_t nw = okc ? words : 2u;
     const uint16_t* wp = reinterpret_cast<const uint16_t*>(bits + words_at + 2ull * (pre + excl));
-    if (!okc) wp = reinterpret_cast<const uint16_t*>(J.bits);  // not read (every step of this lane is idle)
+    if (!okc) wp = reinterpret_cast<const uint16_t*>(S.bits);  // not read (every step of this lane is idle)
     // the lane's words in decoding order: the state, then one word per renormalisation
     uint32_t x = okc ? (ld_u16(wp) << 16) | ld_u16(wp + 1) : kRansL;
     uint32_t r = 2;                                                        // next word to read
     uint32_t w0 = okc ? ld_u16(wp + (2 < nw ? 2 : nw - 1)) : 0u;          // words r and r + 1, fetched ahead
     unsigned short w1 = okc ? (unsigned short)ld_u16(wp + (3 < nw ? 3 : nw - 1)) : (unsigned short)0;
     float q = 0.f;
-    if (OUT != kDecSym) q = J.qstep_all[J.qp_dev ? *J.qp_dev : J.qp_host];
+    if (OUT != kDecSym) q = J.qstep_all[S.qp_dev ? *S.qp_dev : J.qp_host];
     const int per = J.idx_period;
     const int kmod = PER ? K % per : 0;
     int ip = PER && okc ? lane % per : 0;
@@ -645,8 +661,8 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
             const bool ok = m0 + (uint32_t)u < mine;
             td[u] = 0;
             md[u] = 0.f;
-            ld_if_u8(td[u], PER ? J.idx + ip : J.idx + fi, ok);
-            if (OUT != kDecSym && !tile_mode) ld_if_f32(md[u], J.mu + fi, ok);
+            ld_if_u8(td[u], PER ? S.idx + ip : S.idx + fi, ok);
+            if (OUT != kDecSym && !tile_mode) ld_if_f32(md[u], S.mu + fi, ok);
             if (PER) {
                 const int nip = ip + kmod;
                 ip = ok ? (nip >= per ? nip - per : nip) : ip;
@@ -705,12 +721,12 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     auto put = [&](uint32_t s, float mu) {
         const int v = (int)s - kRmax;
         if (OUT == kDecSym) {
-            J.sym[i] = (int16_t)v;
+            S.sym[i] = (int16_t)v;
         } else {
             const float yv = yval(v, mu);
-            if (OUT == kDecBf16) reinterpret_cast<__nv_bfloat16*>(J.yout)[i] = __float2bfloat16_rn(yv);
-            else if (OUT == kDecF32) reinterpret_cast<float*>(J.yout)[i] = yv;
-            else reinterpret_cast<uint8_t*>(J.yout)[i] =
+            if (OUT == kDecBf16) reinterpret_cast<__nv_bfloat16*>(S.yout)[i] = __float2bfloat16_rn(yv);
+            else if (OUT == kDecF32) reinterpret_cast<float*>(S.yout)[i] = yv;
+            else reinterpret_cast<uint8_t*>(S.yout)[i] =
                 (uint8_t)__nv_cvt_float_to_fp8(yv * J.inv8, __NV_SATFINITE, __NV_E4M3);
         }
         i += (uint32_t)K;
@@ -727,9 +743,9 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     // the warp writes the group's 16 rows of 32 consecutive elements as 16-byte vectors, y^ = r^ q + mu
     // computed there from mu read a group ahead.  Lane l writes elements 16 (l & 1) .. + 15 of row l / 2.
     const uint32_t j0 = (uint32_t)(lane & ~31);
-    const uintptr_t outp = OUT == kDecSym ? reinterpret_cast<uintptr_t>(J.sym) : reinterpret_cast<uintptr_t>(J.yout);
+    const uintptr_t outp = OUT == kDecSym ? reinterpret_cast<uintptr_t>(S.sym) : reinterpret_cast<uintptr_t>(S.yout);
     const bool fast = !PER && (K & 15) == 0 && (outp & 15) == 0 &&
-                      (OUT == kDecSym || (reinterpret_cast<uintptr_t>(J.mu) & 15) == 0) &&
+                      (OUT == kDecSym || (reinterpret_cast<uintptr_t>(S.mu) & 15) == 0) &&
                       __all_sync(0xffffffffu, okc && cmin >= (uint32_t)kPF);
     if (fast) {
         int16_t* tile = reinterpret_cast<int16_t*>(dsm + kDecTileOff) + (threadIdx.x >> 5) * (kPF * 32);
@@ -738,7 +754,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         auto load_mu = [&](uint32_t g0) {  // mu of the lane's 16 flush elements of group g0 (if it is whole)
             if (OUT == kDecSym) return;
             const bool ok = g0 + kPF <= cmin;
-            const float4* p = reinterpret_cast<const float4*>(J.mu + j0 + 16u * lh + (size_t)(g0 + lr) * K);
+            const float4* p = reinterpret_cast<const float4*>(S.mu + j0 + 16u * lh + (size_t)(g0 + lr) * K);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -753,7 +769,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
             const size_t e0 = j0 + 16u * lh + (size_t)(g0 + lr) * K;
             const uint32_t wv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
             if (OUT == kDecSym) {
-                uint4* dst = reinterpret_cast<uint4*>(J.sym + e0);
+                uint4* dst = reinterpret_cast<uint4*>(S.sym + e0);
                 dst[0] = a;
                 dst[1] = b;
             } else {
@@ -770,11 +786,11 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
                         const __nv_bfloat162 hv = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
                         pk[k] = *reinterpret_cast<const uint32_t*>(&hv);
                     }
-                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(J.yout) + e0);
+                    uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(S.yout) + e0);
                     dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                     dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 } else if (OUT == kDecF32) {
-                    float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(J.yout) + e0);
+                    float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(S.yout) + e0);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) dst[k] = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
                 } else {
@@ -788,7 +804,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
                                  << (8 * b2);
                         pk[k] = w;
                     }
-                    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(J.yout) + e0) =
+                    *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(S.yout) + e0) =
                         make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
             }
@@ -855,13 +871,16 @@ template <int OUT, bool PER>
 static cudaError_t launch_dec_t(const RansDecJob& j, const uint8_t* tables, cudaStream_t s) {
     cudaError_t e = smem_optin((const void*)rans_decode_kernel<OUT, PER>, kDecSmemBytes);
     if (e != cudaSuccess) return e;
-    const int T = dec_threads(j.K, sm_count());
-    return launch_pdl(rans_decode_kernel<OUT, PER>, dim3((j.K + T - 1) / T), dim3(T), (size_t)kDecSmemBytes, s, j,
-                      tables);
+    return launch_pdl(rans_decode_kernel<OUT, PER>, dim3(j.bps * j.nsec), dim3(j.threads), (size_t)kDecSmemBytes, s,
+                      j, tables);
 }
 
-cudaError_t launch_rans_decode(const RansDecJob& j, const uint8_t* dec_tables, cudaStream_t s) {
-    if (j.K < 1 || j.K > 65536) return cudaErrorInvalidValue;
+cudaError_t launch_rans_decode(RansDecJob& j, const uint8_t* dec_tables, cudaStream_t s) {
+    if (j.K < 1 || j.K > 65536 || j.nsec < 1 || j.nsec > kRansMaxDecSec) return cudaErrorInvalidValue;
+    // the lanes of all sections spread over one wave of one block per SM
+    j.threads = dec_threads(j.K * j.nsec, sm_count());
+    if (j.threads > j.K) j.threads = (j.K + 31) / 32 * 32;
+    j.bps = (j.K + j.threads - 1) / j.threads;
     if (j.idx_period) {
         if (j.out != kDecSym) return cudaErrorInvalidValue;
         return launch_dec_t<kDecSym, true>(j, dec_tables, s);

@@ -11,6 +11,7 @@ namespace {
 std::mutex g_mu;
 std::map<std::pair<const void*, int>, int> g_optin;  // (kernel, device) -> largest opt-in set there
 std::map<int, int> g_sms;                            // device -> SM count
+std::map<std::pair<const void*, int>, int> g_pairs;  // (kernel, device) -> co-resident CTA pairs
 }  // namespace
 
 cudaError_t smem_optin(const void* func, int bytes) {
@@ -35,6 +36,35 @@ int sm_count() {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 148;
     g_sms[dev] = sms;
     return sms;
+}
+
+int max_pairs(const void* func, int smem, int threads) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_pairs.find({func, dev});
+        if (it != g_pairs.end()) return it->second;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * sm_count());
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, func, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pairs[{func, dev}] = n;
+    return n;
 }
 
 }  // namespace ufvc

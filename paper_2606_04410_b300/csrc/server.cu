@@ -10,8 +10,12 @@
 // least recently used first, to make room).  Work on different slots overlaps on the device; the
 // scheduler notices completions through per-slot events and reads each slot context's status word.
 //
+// Same-shape work is batched: requests of one frame size and operation (and rate, for encodes) that are
+// admitted together run on one slot as one batched call (ufvc_encode_chunks / ufvc_decode_chunks), whose
+// entropy-coding launches carry every chunk of the batch; the slot keeps one graph per batch size.
+//
 // Every slot computes with the same kernels as a single context, and none of them depends on what
-// runs beside it, so a request's bit-stream and frames are the same alone and in a mix.
+// runs beside it or in its batch, so a request's bit-stream and frames are the same alone and in a mix.
 //
 // With the temporal chunk context (ufvc_server_set_temporal_context, or the DC-block model, which always
 // has it) each stream also owns its coding
@@ -73,25 +77,32 @@ struct Req {
     ufvc_result res{};
 };
 
+constexpr int kMaxBatch = 4;
+
 struct Slot {
-    int id = 0, W = 0, H = 0;
+    int id = 0, W = 0, H = 0, bmax = 1;  // bmax: the slot's batch size
     ufvc_ctx* ctx = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    uint8_t *frames = nullptr, *bits = nullptr, *out = nullptr;
-    uint64_t* nbytes = nullptr;
+    uint8_t *frames[kMaxBatch] = {}, *bits[kMaxBatch] = {}, *out[kMaxBatch] = {};
+    uint64_t* nbytes = nullptr;  // [kMaxBatch]
     void *cin = nullptr, *cout = nullptr;  // temporal context in / out of the slot's calls
     size_t cap = 0, footprint = 0;
     bool busy = false;
-    uint64_t ticket = 0;
+    std::vector<uint64_t> tickets;  // the batch running on the slot
     int launch_status = UFVC_OK;
     double last_used = 0;
-    // graphs: encode per qp, decode; ran[] = the call ran directly once (its buffers exist)
-    std::map<int, cudaGraphExec_t> g_enc;
-    cudaGraphExec_t g_dec = nullptr;
-    std::unordered_set<int> enc_ran, enc_nograph;
-    bool dec_ran = false, dec_nograph = false;
+    // graphs: encode per (batch, qp), decode per batch; ran = the call ran directly once (its buffers exist)
+    std::map<int, cudaGraphExec_t> g_enc, g_dec;
+    std::unordered_set<int> enc_ran, enc_nograph, dec_ran, dec_nograph;
 };
+
+// frame sizes up to 1080p batch four chunks, larger ones run alone; the temporal context runs alone
+int batch_size(bool temporal, int W, int H) {
+    if (temporal) return 1;
+    const long long b = 4ll * 1920 * 1088 / ((long long)W * H);
+    return b < 1 ? 1 : b > kMaxBatch ? kMaxBatch : (int)b;
+}
 
 }  // namespace
 
@@ -102,7 +113,7 @@ struct ufvc_server {
     size_t cap = 0, used = 0;
     int max_slots = 1, next_slot_id = 0;
     std::atomic<int> graphs{0};
-    uint64_t completed = 0, next_ticket = 1;
+    uint64_t completed = 0, next_ticket = 1, batches = 0, batched = 0;
     bool temporal = false;  // streams carry the temporal chunk context
     std::vector<Slot*> slots;
     std::vector<std::unique_ptr<StreamBuf>> streams;
@@ -123,13 +134,15 @@ namespace {
 void destroy_slot(ufvc_server* S, Slot* sl) {
     cudaStreamSynchronize(sl->st);
     for (auto& kv : sl->g_enc) cudaGraphExecDestroy(kv.second);
-    if (sl->g_dec) cudaGraphExecDestroy(sl->g_dec);
+    for (auto& kv : sl->g_dec) cudaGraphExecDestroy(kv.second);
     ufvc_destroy(sl->ctx);
     cudaFree(sl->cin);
     cudaFree(sl->cout);
-    cudaFree(sl->frames);
-    cudaFree(sl->bits);
-    cudaFree(sl->out);
+    for (int b = 0; b < kMaxBatch; ++b) {
+        cudaFree(sl->frames[b]);
+        cudaFree(sl->bits[b]);
+        cudaFree(sl->out[b]);
+    }
     cudaFree(sl->nbytes);
     cudaEventDestroy(sl->ev);
     cudaStreamDestroy(sl->st);
@@ -154,8 +167,10 @@ Slot* make_slot(ufvc_server* S, int W, int H) {
     const size_t frame_bytes = (size_t)S->N * W * H * 3;
     const size_t cap = ufvc_max_bitstream_bytes(S->base, W, H);
     const size_t cb = S->temporal ? ufvc_context_bytes(S->base, W, H) : 0;
-    // plan buffers + workspaces + staging + a margin for the rANS scratch, graphs and allocator rounding
-    const size_t fp = ctx_plan_bytes(S->base, W, H) + 2 * frame_bytes + cap + 2 * cb + (64ull << 20);
+    const int bmax = batch_size(S->temporal, W, H);
+    // per batch position: plan buffers + workspaces + staging; a margin for the rANS scratch, graphs and
+    // allocator rounding
+    const size_t fp = bmax * (ctx_plan_bytes(S->base, W, H) + 2 * frame_bytes + cap) + 2 * cb + (64ull << 20);
     if ((int)S->slots.size() >= S->max_slots && !evict_one(S, W, H, false)) return nullptr;
     while (S->cap && S->used + fp > S->cap)
         if (!evict_one(S, W, H, false)) return nullptr;
@@ -163,14 +178,17 @@ Slot* make_slot(ufvc_server* S, int W, int H) {
     sl->id = S->next_slot_id++;
     sl->W = W;
     sl->H = H;
+    sl->bmax = bmax;
     sl->cap = cap;
     sl->footprint = fp;
     sl->ctx = ctx_clone_shared(S->base);
     bool ok = sl->ctx && cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&sl->ev, cudaEventDisableTiming) == cudaSuccess &&
-              cudaMalloc(&sl->frames, frame_bytes) == cudaSuccess && cudaMalloc(&sl->bits, cap) == cudaSuccess &&
-              cudaMalloc(&sl->out, frame_bytes) == cudaSuccess && cudaMalloc(&sl->nbytes, 8) == cudaSuccess &&
+              cudaMalloc(&sl->nbytes, 8 * kMaxBatch) == cudaSuccess &&
               (!cb || (cudaMalloc(&sl->cin, cb) == cudaSuccess && cudaMalloc(&sl->cout, cb) == cudaSuccess));
+    for (int b = 0; ok && b < bmax; ++b)
+        ok = cudaMalloc(&sl->frames[b], frame_bytes) == cudaSuccess && cudaMalloc(&sl->bits[b], cap) == cudaSuccess &&
+             cudaMalloc(&sl->out[b], frame_bytes) == cudaSuccess;
     if (!ok) {
         S->err = "server: slot creation failed";
         cudaGetLastError();
@@ -179,9 +197,11 @@ Slot* make_slot(ufvc_server* S, int W, int H) {
         if (sl->ev) cudaEventDestroy(sl->ev);
         cudaFree(sl->cin);
         cudaFree(sl->cout);
-        cudaFree(sl->frames);
-        cudaFree(sl->bits);
-        cudaFree(sl->out);
+        for (int b = 0; b < kMaxBatch; ++b) {
+            cudaFree(sl->frames[b]);
+            cudaFree(sl->bits[b]);
+            cudaFree(sl->out[b]);
+        }
         cudaFree(sl->nbytes);
         delete sl;
         return nullptr;
@@ -223,51 +243,83 @@ ufvc_status run_call(ufvc_server* S, Slot* sl, cudaGraphExec_t* g, bool* ran, bo
     return fn();
 }
 
-// Launch request r of stream sb on slot sl (called without the lock; only the worker touches slots).
-void launch(ufvc_server* S, Slot* sl, StreamBuf* sb, int op) {
+// Launch the batch of requests (streams sbs, one operation) on slot sl (called without the lock; only the
+// worker touches slots).  A batch of one with the temporal context runs the context calls; every other
+// batch runs the batched calls, whose results equal the single-chunk calls'.
+void launch(ufvc_server* S, Slot* sl, const std::vector<StreamBuf*>& sbs, int op) {
     ufvc_status st = UFVC_OK;
-    const int N = S->N, W = sb->W, H = sb->H;
+    const int N = S->N, B = (int)sbs.size(), W = sbs[0]->W, H = sbs[0]->H, qp = sbs[0]->qp;
+    StreamBuf* sb = sbs[0];
     // the stream's context into the slot (zeros before its first chunk: C_0 = 0)
     auto ctx_in = [&](const void* c, uint64_t chunks) {
         if (!S->temporal) return;
         if (chunks) cudaMemcpyAsync(sl->cin, c, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
         else cudaMemsetAsync(sl->cin, 0, sb->ctx_bytes, sl->st);
     };
+    const uint8_t* frames[kMaxBatch];
+    const uint8_t* bits_in[kMaxBatch];
+    uint8_t* bits[kMaxBatch];
+    uint8_t* outs[kMaxBatch];
+    uint64_t* nbs[kMaxBatch];
+    const uint64_t* nbs_in[kMaxBatch];
+    int qps[kMaxBatch];
+    for (int b = 0; b < B; ++b) {
+        frames[b] = sl->frames[b];
+        bits[b] = sl->bits[b];
+        bits_in[b] = sl->bits[b];
+        outs[b] = sl->out[b];
+        nbs[b] = sl->nbytes + b;
+        nbs_in[b] = sl->nbytes + b;
+        qps[b] = qp;
+    }
     if (op == UFVC_OP_ENCODE) {
-        cudaMemcpyAsync(sl->frames, sb->in, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
+        for (int b = 0; b < B; ++b)
+            cudaMemcpyAsync(sl->frames[b], sbs[b]->in, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
         ctx_in(sb->ctx_enc, sb->enc_chunks);
-        auto it = sl->g_enc.find(sb->qp);
+        const int key = B * 64 + qp;
+        auto it = sl->g_enc.find(key);
         cudaGraphExec_t g = it == sl->g_enc.end() ? nullptr : it->second;
-        bool ran = sl->enc_ran.count(sb->qp) != 0, nograph = sl->enc_nograph.count(sb->qp) != 0;
+        bool ran = sl->enc_ran.count(key) != 0, nograph = sl->enc_nograph.count(key) != 0;
         st = run_call(S, sl, &g, &ran, &nograph, [&] {
             if (S->temporal)
-                return ufvc_encode_chunk_tc(sl->ctx, sl->frames, N, W, H, sb->qp, sl->bits, sl->cap, sl->nbytes,
+                return ufvc_encode_chunk_tc(sl->ctx, sl->frames[0], N, W, H, qp, sl->bits[0], sl->cap, sl->nbytes,
                                             sl->cin, sl->cout, sl->st);
-            return ufvc_encode_chunk(sl->ctx, sl->frames, N, W, H, sb->qp, sl->bits, sl->cap, sl->nbytes, sl->st);
+            return ufvc_encode_chunks(sl->ctx, B, frames, N, W, H, qps, bits, sl->cap, nbs, sl->st);
         });
-        if (g) sl->g_enc[sb->qp] = g;
-        if (ran) sl->enc_ran.insert(sb->qp);
-        if (nograph) sl->enc_nograph.insert(sb->qp);
+        if (g) sl->g_enc[key] = g;
+        if (ran) sl->enc_ran.insert(key);
+        if (nograph) sl->enc_nograph.insert(key);
         if (st == UFVC_OK) {
-            copy_sized(sb->bits, sl->bits, sl->nbytes, sb->cap, sl->st);
-            cudaMemcpyAsync(sb->nbytes, sl->nbytes, 8, cudaMemcpyDeviceToDevice, sl->st);
+            for (int b = 0; b < B; ++b) {
+                copy_sized(sbs[b]->bits, sl->bits[b], sl->nbytes + b, sbs[b]->cap, sl->st);
+                cudaMemcpyAsync(sbs[b]->nbytes, sl->nbytes + b, 8, cudaMemcpyDeviceToDevice, sl->st);
+            }
             if (S->temporal) {
                 cudaMemcpyAsync(sb->ctx_enc, sl->cout, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
                 ++sb->enc_chunks;
             }
         }
     } else {
-        copy_sized(sl->bits, sb->bits, sb->nbytes, sl->cap, sl->st);
-        cudaMemcpyAsync(sl->nbytes, sb->nbytes, 8, cudaMemcpyDeviceToDevice, sl->st);
+        for (int b = 0; b < B; ++b) {
+            copy_sized(sl->bits[b], sbs[b]->bits, sbs[b]->nbytes, sl->cap, sl->st);
+            cudaMemcpyAsync(sl->nbytes + b, sbs[b]->nbytes, 8, cudaMemcpyDeviceToDevice, sl->st);
+        }
         ctx_in(sb->ctx_dec, sb->dec_chunks);
-        st = run_call(S, sl, &sl->g_dec, &sl->dec_ran, &sl->dec_nograph, [&] {
+        auto it = sl->g_dec.find(B);
+        cudaGraphExec_t g = it == sl->g_dec.end() ? nullptr : it->second;
+        bool ran = sl->dec_ran.count(B) != 0, nograph = sl->dec_nograph.count(B) != 0;
+        st = run_call(S, sl, &g, &ran, &nograph, [&] {
             if (S->temporal)
-                return ufvc_decode_chunk_tc(sl->ctx, sl->bits, sl->cap, sl->nbytes, sl->out, 0, N, W, H, sl->cin,
-                                            sl->cout, sl->st);
-            return ufvc_decode_chunk_dev(sl->ctx, sl->bits, sl->cap, sl->nbytes, sl->out, N, W, H, sl->st);
+                return ufvc_decode_chunk_tc(sl->ctx, sl->bits[0], sl->cap, sl->nbytes, sl->out[0], 0, N, W, H,
+                                            sl->cin, sl->cout, sl->st);
+            return ufvc_decode_chunks(sl->ctx, B, bits_in, sl->cap, nbs_in, outs, N, W, H, sl->st);
         });
+        if (g) sl->g_dec[B] = g;
+        if (ran) sl->dec_ran.insert(B);
+        if (nograph) sl->dec_nograph.insert(B);
         if (st == UFVC_OK) {
-            cudaMemcpyAsync(sb->out, sl->out, sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
+            for (int b = 0; b < B; ++b)
+                cudaMemcpyAsync(sbs[b]->out, sl->out[b], sb->frame_bytes, cudaMemcpyDeviceToDevice, sl->st);
             if (S->temporal) {
                 cudaMemcpyAsync(sb->ctx_dec, sl->cout, sb->ctx_bytes, cudaMemcpyDeviceToDevice, sl->st);
                 ++sb->dec_chunks;
@@ -280,32 +332,61 @@ void launch(ufvc_server* S, Slot* sl, StreamBuf* sb, int op) {
 }
 
 void finish(ufvc_server* S, Slot* sl) {
-    Req& r = S->reqs[sl->ticket];
-    StreamBuf* sb = S->streams[r.res.stream_id].get();
     ufvc_status st = (ufvc_status)sl->launch_status;
     const ufvc_status dev = ufvc_sync_status(sl->ctx, sl->st);  // the slot's work is complete: no wait
     if (st == UFVC_OK) st = dev;
-    if (st == UFVC_OK) {
-        uint64_t nb = 0;
-        if (cudaMemcpy(&nb, r.res.op == UFVC_OP_ENCODE ? sb->nbytes : sl->nbytes, 8, cudaMemcpyDeviceToHost) ==
-            cudaSuccess)
-            r.res.nbytes = nb;
-        if (r.res.op == UFVC_OP_ENCODE) sb->has_bits = true;
+    const double done = S->now_ms();
+    const int B = (int)sl->tickets.size();
+    uint64_t nb[kMaxBatch] = {};
+    if (st == UFVC_OK && cudaMemcpy(nb, sl->nbytes, 8 * B, cudaMemcpyDeviceToHost) != cudaSuccess) st = UFVC_ERR_CUDA;
+    for (int b = 0; b < B; ++b) {
+        Req& r = S->reqs[sl->tickets[b]];
+        StreamBuf* sb = S->streams[r.res.stream_id].get();
+        if (st == UFVC_OK) {
+            r.res.nbytes = nb[b];
+            if (r.res.op == UFVC_OP_ENCODE) sb->has_bits = true;
+        }
+        r.res.status = st;
+        r.res.done_ms = done;
+        sb->running = false;
+        ++S->completed;
     }
-    r.res.status = st;
-    r.res.done_ms = S->now_ms();
+    if (B > 1) {
+        ++S->batches;
+        S->batched += B;
+    }
+    sl->tickets.clear();
     sl->busy = false;
-    sl->last_used = r.res.done_ms;
-    sb->running = false;
-    ++S->completed;
+    sl->last_used = done;
     S->cv_done.notify_all();
 }
 
-// Admit queued requests in arrival order; a stream's later requests wait behind its earlier ones.
-// Returns the launches to make (the caller launches them without holding the lock).
-std::vector<std::pair<Slot*, uint64_t>> admit(ufvc_server* S) {
-    std::vector<std::pair<Slot*, uint64_t>> todo;
+// Admit queued requests in arrival order; a stream's later requests wait behind its earlier ones.  A slot
+// takes the first admissible request and, up to its batch size, the later queued ones of the same frame
+// size and operation (and rate, for encodes) whose streams are free.  Returns the launches to make (the
+// caller launches them without holding the lock).
+struct Launch {
+    Slot* sl;
+    std::vector<StreamBuf*> sbs;
+    int op;
+};
+
+std::vector<Launch> admit(ufvc_server* S) {
+    std::vector<Launch> todo;
     std::unordered_set<int> blocked;
+    double t_adm = 0;  // a batch's requests start together
+    auto take = [&](Req& r, StreamBuf* sb, Slot* sl) {
+        sl->tickets.push_back(r.ticket);
+        sb->running = true;
+        r.res.slot = sl->id;
+        r.res.start_ms = t_adm;
+    };
+    auto fail_no_bits = [&](Req& r) {  // a decode with no bit-stream it can decode
+        r.res.status = UFVC_ERR_ARG;
+        r.res.done_ms = S->now_ms();
+        ++S->completed;
+        S->cv_done.notify_all();
+    };
     for (auto it = S->queue.begin(); it != S->queue.end();) {
         Req& r = S->reqs[*it];
         StreamBuf* sb = S->streams[r.res.stream_id].get();
@@ -314,11 +395,12 @@ std::vector<std::pair<Slot*, uint64_t>> admit(ufvc_server* S) {
             ++it;
             continue;
         }
-        if (r.res.op == UFVC_OP_DECODE && !sb->has_bits) {  // nothing encoded yet on this stream
-            r.res.status = UFVC_ERR_ARG;
-            r.res.done_ms = S->now_ms();
-            ++S->completed;
-            S->cv_done.notify_all();
+        // a decode needs a bit-stream; with the temporal context it must be the chunk that follows the
+        // last one this stream's decoder decoded (the stream holds only its latest bit-stream, so a chunk
+        // encoded over an undecoded one has lost its predecessor for the decoder's context chain)
+        if (r.res.op == UFVC_OP_DECODE &&
+            (!sb->has_bits || (S->temporal && sb->dec_chunks + 1 != sb->enc_chunks))) {
+            fail_no_bits(r);
             it = S->queue.erase(it);
             continue;
         }
@@ -332,12 +414,28 @@ std::vector<std::pair<Slot*, uint64_t>> admit(ufvc_server* S) {
             continue;
         }
         sl->busy = true;
-        sl->ticket = r.ticket;
-        sb->running = true;
-        r.res.slot = sl->id;
-        r.res.start_ms = S->now_ms();
-        todo.emplace_back(sl, r.ticket);
+        Launch l{sl, {sb}, r.res.op};
+        t_adm = S->now_ms();
+        take(r, sb, sl);
         it = S->queue.erase(it);
+        // the batch's other members: later queued requests of the same shape and operation
+        std::unordered_set<int> seen(blocked);
+        for (auto jt = it; jt != S->queue.end() && (int)l.sbs.size() < sl->bmax;) {
+            Req& q = S->reqs[*jt];
+            StreamBuf* qb = S->streams[q.res.stream_id].get();
+            const bool free = !qb->running && !seen.count(q.res.stream_id);
+            seen.insert(q.res.stream_id);  // a stream's later requests stay behind this one
+            if (free && q.res.op == l.op && qb->W == sb->W && qb->H == sb->H &&
+                (q.res.op == UFVC_OP_DECODE ? qb->has_bits : qb->qp == sb->qp)) {
+                take(q, qb, sl);
+                l.sbs.push_back(qb);
+                jt = S->queue.erase(jt);
+                continue;
+            }
+            ++jt;
+        }
+        for (size_t b = 0; b < l.sbs.size(); ++b) S->reqs[sl->tickets[b]].res.batch = (int)l.sbs.size();
+        todo.push_back(std::move(l));
     }
     return todo;
 }
@@ -356,13 +454,8 @@ void worker_main(ufvc_server* S) {
         }
         auto todo = admit(S);
         if (!todo.empty()) {
-            std::vector<std::pair<Slot*, std::pair<StreamBuf*, int>>> work;
-            for (auto& t : todo) {
-                const Req& r = S->reqs[t.second];
-                work.push_back({t.first, {S->streams[r.res.stream_id].get(), r.res.op}});
-            }
             lk.unlock();
-            for (auto& w : work) launch(S, w.first, w.second.first, w.second.second);
+            for (auto& l : todo) launch(S, l.sl, l.sbs, l.op);
             lk.lock();
             continue;
         }
@@ -470,24 +563,35 @@ extern "C" ufvc_status ufvc_server_stream_buffers(ufvc_server* S, int stream_id,
     return UFVC_OK;
 }
 
-extern "C" ufvc_status ufvc_server_submit(ufvc_server* S, int stream_id, int op, uint64_t* ticket) {
-    if (!S || !ticket || (op != UFVC_OP_ENCODE && op != UFVC_OP_DECODE)) return UFVC_ERR_ARG;
+extern "C" ufvc_status ufvc_server_submit_many(ufvc_server* S, int n, const int* stream_ids, const int* ops,
+                                               uint64_t* tickets) {
+    if (!S || n < 0 || (n && (!stream_ids || !ops || !tickets))) return UFVC_ERR_ARG;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (stream_id < 0 || stream_id >= (int)S->streams.size() || S->stop) return UFVC_ERR_ARG;
-        Req r;
-        r.ticket = S->next_ticket++;
-        r.res.status = UFVC_PENDING;
-        r.res.op = op;
-        r.res.stream_id = stream_id;
-        r.res.slot = -1;
-        r.res.submit_ms = S->now_ms();
-        S->reqs[r.ticket] = r;
-        S->queue.push_back(r.ticket);
-        *ticket = r.ticket;
+        if (S->stop) return UFVC_ERR_ARG;
+        for (int i = 0; i < n; ++i)  // all or nothing
+            if (stream_ids[i] < 0 || stream_ids[i] >= (int)S->streams.size() ||
+                (ops[i] != UFVC_OP_ENCODE && ops[i] != UFVC_OP_DECODE))
+                return UFVC_ERR_ARG;
+        for (int i = 0; i < n; ++i) {
+            Req r;
+            r.ticket = S->next_ticket++;
+            r.res.status = UFVC_PENDING;
+            r.res.op = ops[i];
+            r.res.stream_id = stream_ids[i];
+            r.res.slot = -1;
+            r.res.submit_ms = S->now_ms();
+            S->reqs[r.ticket] = r;
+            S->queue.push_back(r.ticket);
+            tickets[i] = r.ticket;
+        }
     }
     S->cv_work.notify_one();
     return UFVC_OK;
+}
+
+extern "C" ufvc_status ufvc_server_submit(ufvc_server* S, int stream_id, int op, uint64_t* ticket) {
+    return ufvc_server_submit_many(S, 1, &stream_id, &op, ticket);
 }
 
 extern "C" ufvc_status ufvc_server_poll(ufvc_server* S, uint64_t ticket, ufvc_result* out) {
@@ -522,6 +626,8 @@ extern "C" ufvc_status ufvc_server_stats_get(ufvc_server* S, ufvc_server_stats* 
     out->completed = S->completed;
     out->hbm_used = S->used;
     out->hbm_cap = S->cap;
+    out->batches = S->batches;
+    out->batched = S->batched;
     return UFVC_OK;
 }
 

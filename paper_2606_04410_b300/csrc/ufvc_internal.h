@@ -87,6 +87,9 @@ __device__ __forceinline__ void px_bytes(const uint8_t* __restrict__ fr, int n, 
 // one record per kernel and device).  sm_count caches the SM count of the current device.
 cudaError_t smem_optin(const void* func, int bytes);
 int sm_count();
+// clusters of two CTAs of `func` (smem bytes of dynamic shared memory, `threads` per CTA) that the current
+// device holds at once (0 if none or unknown); cached per kernel and device, after smem_optin
+int max_pairs(const void* func, int smem, int threads);
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
@@ -101,6 +104,27 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// launch_pdl for clusters of two CTAs (a CTA pair sharing tcgen05.mma.cta_group::2); grid.x even
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_pair(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                   Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 2;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 #endif
@@ -225,6 +249,8 @@ struct ConvDesc {
     // tensor-core path: K steps (tap x 64-channel chunk, tap-major) whose weights are all zero and are
     // skipped (bit ks set = step ks runs; 0 = every step runs)
     unsigned long long kmask = 0;
+    // tensor-core path: the staged BN = 256 layers may run on CTA pairs (tcgen05.mma.cta_group::2)
+    int pairs = 1;
     // The last hyper-synthesis layer (columns [0, split) = mu, [split, Cout) = log sigma) with the entropy
     // parameters formed in its output pass: ent_idx = #{k : thr_qp[k] < log sigma} and, with ent_y,
     // ent_rhat = clamp(rint((y - mu) / q)), qp = *ent_qp_dev (or ent_qp).  mu goes to out; log sigma to
@@ -293,11 +319,14 @@ void launch_pack_fp8(const uint8_t* frames, int N, int H, int W, int Hp, int Wp,
 void launch_f32_to_e4m3_rows(const float* a, int H, int W, int C, float inv, uint8_t* out, int Wd, cudaStream_t s);
 void launch_absmax(const float* x, size_t n, float* slot, cudaStream_t s);
 
-// rANS (rans.cu).  Encoding: one launch codes one or two sections and lays them out (lane counts, words,
-// padding) after `base` header bytes, writing the header itself when hdr_len > 0.  The control block
-// (tickets and published block totals) must be zero before the first launch; every launch leaves it
+// rANS (rans.cu).  Encoding: one launch codes the sections of up to kRansMaxStreams streams (a chunk's
+// stream: its z^ section, then its y^ section; or one bare section) and lays each stream out (lane counts,
+// words, padding) after `base` header bytes, writing the header itself when hdr_len > 0.  The control
+// block (tickets and published block totals) must be zero before the first launch; every launch leaves it
 // zero.  Staging rows: [K][cap_lane] u16 per section, cap_lane >= n / K + 3.
-constexpr int kRansMaxBlocks = 256;
+constexpr int kRansMaxBlocks = 1024;
+constexpr int kRansMaxStreams = 8;
+constexpr int kRansMaxEncSec = 2 * kRansMaxStreams;
 struct RansCtl {
     unsigned int ticket, done;
     uint64_t flag[kRansMaxBlocks];
@@ -310,11 +339,10 @@ struct RansEncSec {
     int K;
     uint16_t* rows;
     int cap_lane;
-    int nblk;                 // set by the launcher
+    int stream;               // the stream (output) it belongs to; a stream's sections are consecutive
+    int nblk, first, prev, last;  // set by the launcher
 };
-struct RansEncJob {
-    RansEncSec s[2];
-    int nsec, grid, lpb;      // grid and lanes per block: set by the launcher
+struct RansEncStream {
     uint8_t* out;
     uint64_t capacity;
     uint64_t* nbytes;         // device: size of the stream written
@@ -323,6 +351,13 @@ struct RansEncJob {
     uint8_t hdr20[20];        // the header's fixed fields, then cz scale indices from iz, then zeros
     const uint8_t* iz;
     int cz;
+};
+struct RansEncJob {
+    RansEncSec s[kRansMaxEncSec];
+    int nsec;
+    RansEncStream st[kRansMaxStreams];
+    int nstreams;
+    int grid, lpb;            // set by the launcher: blocks, lanes per block
     RansCtl* ctl;
     int* status;
     long long spin;           // bound on the table-copy wait in clocks (0: about 2 s)
@@ -330,39 +365,46 @@ struct RansEncJob {
 cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cudaStream_t s);
 size_t rans_ctl_bytes();
 
-// Decoding one section (count checks and offsets inside the launch).  Output: r^ (int16) or, fused,
-// y^ = r^ q + mu as bf16, float or E4M3 codes (q = qstep_all[*qp_dev], or qstep_all[qp_host]).  With
-// hdr_cz > 0 the launch first checks the container header against the context (arch, N, W, H, Ky lanes of
-// the latent section, K = Kz lanes here, the progressive-means and temporal flags) and block 0 writes the
-// rate and the version (2 for progressive means, else 1) to qp_out / ver_out.
+// Decoding sections of the same shape (K lanes, n elements, one per chunk) in one launch; the lane-count
+// checks and offsets are inside the launch.  Output: r^ (int16) or, fused, y^ = r^ q + mu as bf16, float
+// or E4M3 codes (q = qstep_all[*qp_dev], or qstep_all[qp_host]).  With hdr_cz > 0 every section's launch
+// blocks first check its container header against the context (arch, N, W, H, Ky lanes of the latent
+// section, K = Kz lanes here, the progressive-means and temporal flags) and the section's first block
+// writes the rate and the version (2 for progressive means, else 1) to qp_out / ver_out.
 enum { kDecSym = 0, kDecBf16 = 1, kDecF32 = 2, kDecE4M3 = 3 };
-struct RansDecJob {
+constexpr int kRansMaxDecSec = 8;
+struct RansDecSec {
     const uint8_t* bits;
     uint64_t nbytes;                 // readable bytes from bits
     uint64_t sec_off;                // section offset, or read from sec_off_dev when that is not null
     const uint64_t* sec_off_dev;
     uint64_t expect_end;             // the section must end exactly here (0: anywhere up to nbytes) ...
     const uint64_t* expect_end_dev;  // ... or at the device value
-    const uint8_t* idx;
-    int idx_period;
-    uint32_t n;
-    int K;
+    const uint8_t* idx;              // per element, or per channel (idx_period)
     uint64_t* next_off;              // device: the byte after the section (may be null)
-    int out;
     int16_t* sym;
     void* yout;
     const float* mu;
-    const float* qstep_all;
     const int* qp_dev;
+    int* qp_out;
+    int* ver_out;
+};
+struct RansDecJob {
+    RansDecSec s[kRansMaxDecSec];
+    int nsec;
+    int idx_period;
+    uint32_t n;
+    int K;
+    int out;
+    const float* qstep_all;
     int qp_host;
     float inv8;
     int hdr_cz, arch, N, W, H, Ky, allow_pm, temporal;
-    int* qp_out;
-    int* ver_out;
     int* status;
     long long spin;
+    int threads, bps;                // set by the launcher: threads per block, blocks per section
 };
-cudaError_t launch_rans_decode(const RansDecJob& j, const uint8_t* dec_tables, cudaStream_t s);
+cudaError_t launch_rans_decode(RansDecJob& j, const uint8_t* dec_tables, cudaStream_t s);
 // the decoder's table image (196864 bytes) from cum [64][512]
 void build_decode_tables(const std::vector<uint32_t>& cum_all, std::vector<uint8_t>& out);
 

@@ -32,14 +32,14 @@ EXPORTS = [
     "ufvc_hyper_synthesis", "ufvc_quantize", "ufvc_synthesize", "ufvc_rans_encode", "ufvc_rans_decode",
     "ufvc_get_tables", "ufvc_set_profiling", "ufvc_get_profile", "ufvc_last_error", "ufvc_conv_layer",
     "ufvc_rans_encode_noalloc", "ufvc_decode_chunk_dev", "ufvc_server_create", "ufvc_server_destroy",
-    "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_poll",
+    "ufvc_server_open_stream", "ufvc_server_stream_buffers", "ufvc_server_submit", "ufvc_server_submit_many", "ufvc_server_poll",
     "ufvc_server_wait", "ufvc_server_stats_get", "ufvc_server_last_error", "ufvc_calibrate_fp8",
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
     "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
     "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
     "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means", "ufvc_pipe_create",
     "ufvc_pipe_submit", "ufvc_pipe_wait", "ufvc_pipe_destroy", "ufvc_first_layer",
-    "ufvc_set_table_wait_limit",
+    "ufvc_set_table_wait_limit", "ufvc_set_conv_pairs", "ufvc_encode_chunks", "ufvc_decode_chunks",
 ]
 COLOR_RGB, COLOR_RGB_BT709, COLOR_YUV444P, COLOR_YUV420P = range(4)
 UFVC_OP_ENCODE, UFVC_OP_DECODE = 0, 1
@@ -53,12 +53,13 @@ class ufvc_config(C.Structure):
 class ufvc_result(C.Structure):
     _fields_ = [("status", C.c_int), ("op", C.c_int), ("stream_id", C.c_int), ("slot", C.c_int),
                 ("submit_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double),
-                ("nbytes", C.c_uint64)]
+                ("nbytes", C.c_uint64), ("batch", C.c_int)]
 
 
 class ufvc_server_stats(C.Structure):
     _fields_ = [("slots", C.c_int), ("busy_slots", C.c_int), ("queued", C.c_int), ("graphs", C.c_int),
-                ("completed", C.c_uint64), ("hbm_used", C.c_size_t), ("hbm_cap", C.c_size_t)]
+                ("completed", C.c_uint64), ("hbm_used", C.c_size_t), ("hbm_cap", C.c_size_t),
+                ("batches", C.c_uint64), ("batched", C.c_uint64)]
 
 
 _vp, _sz, _i = C.c_void_p, C.c_size_t, C.c_int
@@ -89,6 +90,9 @@ _sigs = {
     "ufvc_conv_layer": (_i, [_vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _i, _i, _vp]),
     "ufvc_first_layer": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp]),
     "ufvc_set_table_wait_limit": (_i, [_vp, C.c_longlong]),
+    "ufvc_set_conv_pairs": (_i, [_vp, _i]),
+    "ufvc_encode_chunks": (_i, [_vp, _i, _vp, _i, _i, _i, _vp, _vp, _sz, _vp, _vp]),
+    "ufvc_decode_chunks": (_i, [_vp, _i, _vp, _sz, _vp, _vp, _i, _i, _i, _vp]),
     "ufvc_decode_chunk_dev": (_i, [_vp, _vp, _sz, _vp, _vp, _i, _i, _i, _vp]),
     "ufvc_server_create": (_i, [C.POINTER(ufvc_config), _vp, _sz, _sz, _i, C.POINTER(_vp)]),
     "ufvc_server_destroy": (None, [_vp]),
@@ -96,6 +100,7 @@ _sigs = {
     "ufvc_server_stream_buffers": (_i, [_vp, _i, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_sz),
                                         C.POINTER(_vp)]),
     "ufvc_server_submit": (_i, [_vp, _i, _i, C.POINTER(C.c_uint64)]),
+    "ufvc_server_submit_many": (_i, [_vp, _i, _vp, _vp, _vp]),
     "ufvc_server_poll": (_i, [_vp, C.c_uint64, C.POINTER(ufvc_result)]),
     "ufvc_server_wait": (_i, [_vp, C.c_uint64, C.c_double, C.POINTER(ufvc_result)]),
     "ufvc_server_stats_get": (_i, [_vp, C.POINTER(ufvc_server_stats)]),
@@ -421,6 +426,29 @@ class Codec:
                     "first_layer")
         return out
 
+    def encode_chunks(self, frames: list, qps: list, bits: list, nbytes: list, width: int | None = None,
+                      height: int | None = None, stream=None):
+        """Batched encode: frames[b] (device tensors of one size) into bits[b], sizes into nbytes[b]."""
+        B = len(frames)
+        H = height if height is not None else frames[0].shape[1]
+        W = width if width is not None else frames[0].shape[2]
+        P = C.c_void_p * B
+        self._check(lib.ufvc_encode_chunks(self.h, B, P(*[_ptr(f) for f in frames]), self.N, W, H,
+                                           (C.c_int * B)(*qps), P(*[_ptr(b) for b in bits]), bits[0].numel(),
+                                           P(*[_ptr(n) for n in nbytes]), _stream(stream)), "encode_chunks")
+
+    def decode_chunks(self, bits: list, nbytes: list, width: int, height: int, outs: list, stream=None):
+        """Batched decode: bits[b] (sizes on the device in nbytes[b]) into uint8 frames outs[b]."""
+        B = len(bits)
+        P = C.c_void_p * B
+        self._check(lib.ufvc_decode_chunks(self.h, B, P(*[_ptr(b) for b in bits]), bits[0].numel(),
+                                           P(*[_ptr(n) for n in nbytes]), P(*[_ptr(o) for o in outs]), self.N, width,
+                                           height, _stream(stream)), "decode_chunks")
+
+    def set_conv_pairs(self, enable: bool):
+        """Decoder pixel-shuffle layers on SM pairs (True, the default) or one SM per tile."""
+        self._check(lib.ufvc_set_conv_pairs(self.h, int(bool(enable))), "set_conv_pairs")
+
     def set_table_wait_limit(self, cycles: int):
         self._check(lib.ufvc_set_table_wait_limit(self.h, int(cycles)), "set_table_wait_limit")
 
@@ -546,6 +574,15 @@ class Server:
         t = C.c_uint64()
         self._check(lib.ufvc_server_submit(self.h, stream_id, op, C.byref(t)), "submit")
         return t.value
+
+    def submit_many(self, requests: list[tuple[int, int]]) -> list[int]:
+        """Queue [(stream_id, op), ...] at once (all or none); returns their tickets."""
+        n = len(requests)
+        sids = (C.c_int * max(n, 1))(*[r[0] for r in requests])
+        ops = (C.c_int * max(n, 1))(*[r[1] for r in requests])
+        t = (C.c_uint64 * max(n, 1))()
+        self._check(lib.ufvc_server_submit_many(self.h, n, sids, ops, t), "submit_many")
+        return [int(t[i]) for i in range(n)]
 
     def poll(self, ticket: int) -> dict:
         r = ufvc_result()

@@ -1,8 +1,9 @@
 """GPU tests of the continuous-batching server (ufvc_server_*): every request's bit-stream and decoded
-frames are identical to the single-context calls on the same chunk whether it runs alone or in a mix of
-streams of different sizes on several slots (same kernels, no cross-request arithmetic); graphs are
-captured and replayed; a stream's requests keep their order; the HBM cap bounds the slots (idle slots
-of other sizes are released) and the stream buffers; a decode with nothing encoded is refused."""
+frames are identical to the single-context calls on the same chunk whether it runs alone, in a batch of
+same-shape requests, or in a mix of streams of different sizes on several slots (same kernels, no
+cross-request arithmetic); graphs are captured and replayed; a stream's requests keep their order; the
+HBM cap bounds the slots (idle slots of other sizes are released) and the stream buffers; a decode with
+nothing encoded is refused."""
 import numpy as np
 import pytest
 import torch
@@ -69,10 +70,12 @@ def test_server_alone_and_mix_match_single_context():
         srv.streams[sids[i]]["frames_in"].copy_(frames[i])
     torch.cuda.synchronize()
     for rnd in range(3):
-        tickets = []
-        for i, _, _ in specs:
-            tickets.append((i, u.UFVC_OP_ENCODE, srv.submit(sids[i], u.UFVC_OP_ENCODE)))
-            tickets.append((i, u.UFVC_OP_DECODE, srv.submit(sids[i], u.UFVC_OP_DECODE)))
+        reqs = [(i, op) for i, _, _ in specs for op in (u.UFVC_OP_ENCODE, u.UFVC_OP_DECODE)]
+        if rnd == 0:  # one by one: the scheduler may start some before the rest are queued
+            tickets = [(i, op, srv.submit(sids[i], op)) for i, op in reqs]
+        else:  # all at once: each size's two encodes (then decodes) run as one batch
+            ts = srv.submit_many([(sids[i], op) for i, op in reqs])
+            tickets = [(i, op, t) for (i, op), t in zip(reqs, ts)]
         results = [(i, op, srv.wait(t, 120000.0)) for i, op, t in tickets]
         for i, op, r in results:
             assert r["status"] == 0, (rnd, i, op, r)
@@ -84,6 +87,12 @@ def test_server_alone_and_mix_match_single_context():
             enc = [r for j, op, r in results if j == i and op == u.UFVC_OP_ENCODE][0]
             dec = [r for j, op, r in results if j == i and op == u.UFVC_OP_DECODE][0]
             assert dec["start_ms"] >= enc["done_ms"]
+        if rnd:
+            assert all(r["batch"] == 2 for _, _, r in results), [r["batch"] for _, _, r in results]
+            # the three sizes' encode batches ran on three slots at the same time
+            enc = {r["slot"]: r for _, op, r in results if op == u.UFVC_OP_ENCODE}
+            assert len(enc) == 3
+            assert max(r["start_ms"] for r in enc.values()) < min(r["done_ms"] for r in enc.values())
         for i, _, _ in specs:
             b = srv.streams[sids[i]]
             assert b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes() == refs[i][0]
@@ -91,7 +100,40 @@ def test_server_alone_and_mix_match_single_context():
     st = srv.stats()
     assert st["completed"] == 3 * 2 * len(specs) and st["queued"] == 0
     assert 1 <= st["slots"] <= 4 and st["graphs"] >= 2
-    # requests of different slots overlapped in time at least once
+    assert st["batches"] >= 2 * 6 and st["batched"] >= 2 * 12
+    srv.close()
+
+
+def test_server_batches_same_shape_requests():
+    """Four streams of one size queued at once run as one encode batch and one decode batch on one slot
+    (the slot's batch size is 4 at this size); each stream's bit-stream and frames equal the
+    single-context calls'.  A fifth stream of the size waits for the next batch; streams at another rate
+    are not batched with them."""
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=5)
+    W, H = SIZES[2]
+    qps = [QP, QP, QP, QP, QP, QP + 4]
+    frames = [_frames(90 + i, W, H) for i in range(len(qps))]
+    refs = [_reference(blob, frames[i], W, H, qps[i]) for i in range(len(qps))]
+    srv = u.Server(1, N, K, blob, "bf16", max_slots=1)
+    sids = [srv.open_stream(W, H, q) for q in qps]
+    for sid, fr in zip(sids, frames):
+        srv.streams[sid]["frames_in"].copy_(fr)
+    torch.cuda.synchronize()
+    for rnd in range(3):  # direct runs, captures, replays
+        reqs = [(sid, op) for op in (u.UFVC_OP_ENCODE, u.UFVC_OP_DECODE) for sid in sids]
+        res = [srv.wait(t, 120000.0) for t in srv.submit_many(reqs)]
+        assert all(r["status"] == 0 for r in res)
+        enc, dec = res[:len(sids)], res[len(sids):]
+        assert [r["batch"] for r in enc[:4]] == [4] * 4 and len({r["start_ms"] for r in enc[:4]}) == 1
+        assert enc[4]["batch"] == 1 and enc[5]["batch"] == 1  # the fifth stream and the other rate
+        assert [r["batch"] for r in dec[:4]] == [4] * 4
+        for i, sid in enumerate(sids):
+            b = srv.streams[sid]
+            assert b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes() == refs[i][0], (rnd, i)
+            assert torch.equal(b["frames_out"].cpu(), refs[i][1]), (rnd, i)
+    st = srv.stats()
+    assert st["slots"] == 1 and st["batches"] >= 6 and st["graphs"] >= 2
     srv.close()
 
 
@@ -203,6 +245,11 @@ def test_server_streams_carry_temporal_context():
             assert raw == refs[i][r][0], (i, r)
             assert torch.equal(b["frames_out"].cpu(), refs[i][r][1]), (i, r)
     assert srv.stats()["graphs"] >= 2
+    # a chunk encoded over an undecoded one: its decode is refused (the decoder's chain lost a chunk)
+    sid = sids[0]
+    t = srv.submit_many([(sid, u.UFVC_OP_ENCODE), (sid, u.UFVC_OP_ENCODE), (sid, u.UFVC_OP_DECODE)])
+    res = [srv.wait(x, 120000.0) for x in t]
+    assert [r["status"] for r in res] == [0, 0, u.UFVC_ERR_ARG]
     srv.close()
 
 

@@ -91,10 +91,25 @@ def test_tc_pixel_shuffle_cropped(layer, H, W, crop):
     _check_layer(1, 2, layer, H, W, 1, 1, 1, 256 if layer == 11 else (128 if layer == 14 else 64), crop)
 
 
-def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0)):
+@pytest.mark.parametrize("layer,H,W,cin_pad", [
+    (17, 136, 240, 64),   # U2 at the 1080p decoder's quarter size: 255 pairs of 128-pixel tiles
+    (11, 68, 120, 256),   # D0 on the 1080p latent, two N tiles of 256
+    (14, 25, 37, 128),    # U1, ragged: the last pair's second tile lies below the output
+    (17, 9, 260, 64),     # U2, one tile row: every pair's second tile lies below the output
+])
+def test_pixel_shuffle_pairs_equal_single(layer, H, W, cin_pad):
+    """The decoders' pixel-shuffle layers (256 accumulator columns) on SM pairs (one M = 256 MMA over two
+    SMs, each with half of the weights) and on one SM per tile: both within the float64 bound, and equal
+    bit for bit (the same products summed in the same order per output)."""
+    got = {p: _check_layer(1, 2, layer, H, W, 1, 1, 1, cin_pad, pairs=p) for p in (True, False)}
+    assert torch.equal(got[True], got[False])
+
+
+def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0), pairs=True):
     u = U()
     blob = synthetic.draw_weights(arch, N, seed=3, bias_std=0.1)
     codec = u.Codec(arch, N, 64, blob, "bf16")
+    codec.set_conv_pairs(pairs)
     _, co, k, ci = layer_table(arch, N)[layer]
     rng = np.random.default_rng(layer + H)
     x = np.zeros((H, W, cin_pad), np.float32)
@@ -118,6 +133,7 @@ def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0)):
     scale = float(ref.abs().max())
     bound = 8e-3 * ref.abs() + 2e-3 * scale
     assert bool((err <= bound).all()), f"max err {float(err.max()):.4g} scale {scale:.3g}"
+    return got
 
 
 def _run_chunk(codec, fr, qp):
@@ -154,6 +170,10 @@ def test_bf16_chunk(arch, N, H, W, K):
     # the decoder's own (deterministic FP32) hyper-synthesis reproduces the encoder's mu exactly
     rec = bf.decode_chunk(bits, n, W, H, f32=True)
     assert bf.sync_status() == 0
+    # the frame decoders' pixel-shuffle layers on one SM per tile instead of SM pairs: the same frames
+    bf.set_conv_pairs(False)
+    assert torch.equal(bf.decode_chunk(bits, n, W, H, f32=True), rec)
+    bf.set_conv_pairs(True)
     yhat = torch.from_numpy(st["rhat"]).cuda().float() + torch.from_numpy(st["mu"]).cuda()
     rec2 = bf.synthesize(yhat, W, H)
     torch.cuda.synchronize()
