@@ -499,7 +499,11 @@ constexpr int kDecTileOff = kDecTabBytes + kDecCntBytes;
 constexpr int kDecMaxWarps = 16;
 constexpr int kDecSmemBytes = kDecTileOff + kDecMaxWarps * 16 * 32 * 2;
 
-template <int OUT, bool PER>
+// HELP (one warp of lanes per block, the latency-bound case): two more warps serve the decoding warp
+// through shared-memory rings of four groups of 16 steps: warp 1 stages the lanes' scale indices ahead
+// of it, warp 2 takes its symbols and writes y^ = r^ q + mu (or r^) as 16-byte vectors, so the decoding
+// warp issues little besides the state chain.  The rings hand over through mbarriers (bounded waits).
+template <int OUT, bool PER, bool HELP = false>
 __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, const uint8_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint8_t dsm[];
     const uint2* ent = reinterpret_cast<const uint2*>(dsm);
@@ -524,14 +528,15 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     if (!loaded || bad_sh) return;
     const uint8_t* bits = S.bits;
     const uint64_t nbytes = S.nbytes;
-    const int K = J.K, T = blockDim.x;
+    // T: lanes per block (its first T threads); NT: all threads (HELP: the two serving warps besides)
+    const int K = J.K, T = HELP ? 32 : (int)blockDim.x, NT = blockDim.x;
     // ---- container header (the z^ section's launch): every block checks it; block 0 publishes the rate
     //      and the version for the later kernels
     if (J.hdr_cz > 0) {
         const uint64_t hdr = (20ull + J.hdr_cz + 3) & ~3ull;
         const bool whole = nbytes >= hdr;
         bool iz_bad = false;  // the scale indices, checked by all threads
-        for (int c = threadIdx.x; whole && c < J.hdr_cz; c += T) iz_bad |= bits[20 + c] >= kBins;
+        for (int c = threadIdx.x; whole && c < J.hdr_cz; c += NT) iz_bad |= bits[20 + c] >= kBins;
         iz_bad = __syncthreads_or(iz_bad);
         if (threadIdx.x == 0) {
             int st = 0, qp = 32, ver = 1;
@@ -604,14 +609,14 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
     };
     uint64_t pre = 0, tot = 0;
-    for (int j0 = threadIdx.x; j0 < K; j0 += 16 * T) {  // sixteen loads in flight per thread
+    for (int j0 = threadIdx.x; j0 < K; j0 += 16 * NT) {  // sixteen loads in flight per thread
         uint32_t c[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) c[k] = j0 + k * T < K ? count_at(j0 + k * T) : 0u;
+        for (int k = 0; k < 16; ++k) c[k] = j0 + k * NT < K ? count_at(j0 + k * NT) : 0u;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
             tot += c[k];
-            pre += j0 + k * T < first ? c[k] : 0u;
+            pre += j0 + k * NT < first ? c[k] : 0u;
         }
     }
     pre = block_sum_u64(pre, red_sh);
@@ -625,13 +630,13 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     }
     if (blk == 0 && threadIdx.x == 0 && S.next_off) *S.next_off = end4;
     const int lane = first + threadIdx.x;
-    const bool inl = lane < K;
+    const bool inl = (int)threadIdx.x < T && lane < K;
     const uint32_t words = inl ? count_at(lane) : 0u;
     uint32_t btot;
     const uint32_t excl = block_excl_scan(words, &btot, scan_sh);
     // From here on a warp steps in lock-step (the rare bisection below is a warp vote): lanes past K, and
     // lanes with a bad count, take part without coding; a warp with no lane left returns.
-    if (__all_sync(0xffffffffu, !inl)) return;
+    if (!HELP && __all_sync(0xffffffffu, !inl)) return;  // (HELP: the block's lanes are its warp 0, all < K)
     const uint32_t n = J.n, cnt = inl ? lane_elems(n, K, lane) : 0u;
     const bool okc = inl && words >= 2 && words <= cnt + 2;  // every read below stays inside the lane's words
     if (inl && !okc) set_status(J.status, UFVC_ERR_CORRUPT);
@@ -738,13 +743,157 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     std::true_type every;
     std::false_type some;
     uint32_t m0 = 0;
+    const uintptr_t outp = OUT == kDecSym ? reinterpret_cast<uintptr_t>(S.sym) : reinterpret_cast<uintptr_t>(S.yout);
+    if constexpr (HELP) {
+        // rings of four groups: indices [4][16 steps][32 lanes] u8, symbols [4][16][32] int16; barriers
+        // t_full, t_empty, s_full, s_empty (four each), one arrival per phase
+        uint8_t* ring_t = dsm + kDecTileOff;
+        int16_t* ring_s = reinterpret_cast<int16_t*>(dsm + kDecTileOff + 2048);
+        uint64_t* hb = reinterpret_cast<uint64_t*>(dsm + kDecTileOff + 6144);
+        __shared__ uint32_t ngr_sh;
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 16; ++k) ptx::mbar_init(&hb[k], 1);
+            ptx::fence_mbar_init();
+        }
+        if (w == 0) {  // whole groups of 16 steps that every lane of the warp codes, with aligned rows
+            const bool f = !PER && (K & 15) == 0 && (outp & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(S.idx) & 15) == 0 &&
+                           (OUT == kDecSym || (reinterpret_cast<uintptr_t>(S.mu) & 15) == 0) &&
+                           __all_sync(0xffffffffu, okc && cmin >= (uint32_t)kPF);
+            if (l == 0) ngr_sh = f ? cmin / kPF : 0u;
+        }
+        __syncthreads();
+        const uint32_t ngr = ngr_sh;
+        auto hwait = [&](uint64_t* b, uint32_t par) {
+            const long long t0 = clock64();
+            while (!ptx::mbar_try_wait(b, par))
+                if (clock64() - t0 > kSpinDefault) {
+                    set_status(J.status, UFVC_ERR_TIMEOUT);
+                    return false;
+                }
+            return true;
+        };
+        if (w == 1) {
+            // ---- index stage: lane l copies 16 indices of step 16 g + l / 2 (lanes 16 (l & 1) ..)
+            const int u = l >> 1, h = l & 1;
+            uint32_t badv = 0;
+            for (uint32_t g = 0; g < ngr; ++g) {
+                const int b = (int)(g & 3);
+                const uint32_t use = g >> 2;
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(S.idx + first + 16 * h + (size_t)(kPF * g + u) * K));
+                badv |= (v.x | v.y | v.z | v.w) & 0xC0C0C0C0u;  // an index of 64 or more
+                bool ok = true;
+                if (use > 0) ok = hwait(&hb[4 + b], (use - 1) & 1);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                *reinterpret_cast<uint4*>(ring_t + b * 512 + u * 32 + 16 * h) = v;
+                __syncwarp();
+                if (l == 0) ptx::mbar_arrive(&hb[b]);
+            }
+            if (badv) set_status(J.status, UFVC_ERR_ARG);
+            return;
+        }
+        if (w == 2) {
+            // ---- output: lane l writes elements 16 (l & 1) .. + 15 of step 16 g + l / 2, mu read a group ahead
+            const int lr = l >> 1, lh = l & 1;
+            float mv[16];
+            auto load_mu = [&](uint32_t g) {
+                if (OUT == kDecSym) return;
+                const bool ok = g < ngr;
+                const float4* pm = reinterpret_cast<const float4*>(S.mu + first + 16u * lh + (size_t)(kPF * g + lr) * K);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ok) v = __ldg(pm + k);
+                    mv[4 * k] = v.x; mv[4 * k + 1] = v.y; mv[4 * k + 2] = v.z; mv[4 * k + 3] = v.w;
+                }
+            };
+            load_mu(0);
+            for (uint32_t g = 0; g < ngr; ++g) {
+                const int b = (int)(g & 3);
+                const uint32_t use = g >> 2;
+                if (!__all_sync(0xffffffffu, hwait(&hb[8 + b], use & 1))) break;
+                const uint4* src = reinterpret_cast<const uint4*>(ring_s + b * 512 + lr * 32 + 16 * lh);
+                const uint4 a = src[0], c2 = src[1];
+                __syncwarp();
+                if (l == 0) ptx::mbar_arrive(&hb[12 + b]);  // the slot is free again
+                const size_t e0 = first + 16u * lh + (size_t)(kPF * g + lr) * K;
+                const uint32_t wv[8] = {a.x, a.y, a.z, a.w, c2.x, c2.y, c2.z, c2.w};
+                if (OUT == kDecSym) {
+                    uint4* dst = reinterpret_cast<uint4*>(S.sym + e0);
+                    dst[0] = a;
+                    dst[1] = c2;
+                } else {
+                    float y[16];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        y[2 * k] = yval((int)(int16_t)(wv[k] & 0xFFFFu), mv[2 * k]);
+                        y[2 * k + 1] = yval((int)(int16_t)(wv[k] >> 16), mv[2 * k + 1]);
+                    }
+                    if (OUT == kDecBf16) {
+                        uint32_t pk[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const __nv_bfloat162 hv = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
+                            pk[k] = *reinterpret_cast<const uint32_t*>(&hv);
+                        }
+                        uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(S.yout) + e0);
+                        dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else if (OUT == kDecF32) {
+                        float4* dst = reinterpret_cast<float4*>(reinterpret_cast<float*>(S.yout) + e0);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) dst[k] = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+                    } else {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            uint32_t wd = 0;
+#pragma unroll
+                            for (int b2 = 0; b2 < 4; ++b2)
+                                wd |= (uint32_t)__nv_cvt_float_to_fp8(y[4 * k + b2] * J.inv8, __NV_SATFINITE, __NV_E4M3)
+                                      << (8 * b2);
+                            pk[k] = wd;
+                        }
+                        *reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(S.yout) + e0) =
+                            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
+                load_mu(g + 1);
+            }
+            return;
+        }
+        // ---- warp 0: the state chains, 16 steps per group, indices from the ring, symbols into it
+        for (uint32_t g = 0; g < ngr; ++g) {
+            const int b = (int)(g & 3);
+            const uint32_t use = g >> 2;
+            ahead();
+            bool ok = hwait(&hb[b], use & 1);
+            if (use > 0 && ok) ok = hwait(&hb[12 + b], (use - 1) & 1);
+            if (!__all_sync(0xffffffffu, ok)) return;
+            const uint8_t* tr = ring_t + b * 512 + l;
+            int16_t* sr = ring_s + b * 512 + l;
+            uint32_t tv[kPF];
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) tv[u] = tr[u * 32];
+#pragma unroll
+            for (int u = 0; u < kPF; ++u) sr[u * 32] = (int16_t)((int)decode(tv[u], true, every) - kRmax);
+            __syncwarp();
+            if (l == 0) {
+                ptx::mbar_arrive(&hb[4 + b]);  // indices consumed
+                ptx::mbar_arrive(&hb[8 + b]);  // symbols ready
+            }
+        }
+        m0 = kPF * ngr;
+        fi = (uint32_t)lane + m0 * (uint32_t)K;
+        i = fi;
+    }
     // Fast path, for a warp of 32 lanes in range with good counts and 16-byte aligned rows: the symbols of
     // a group go to a shared-memory tile [16 steps][32 lanes] (one store each, off the state chain), then
     // the warp writes the group's 16 rows of 32 consecutive elements as 16-byte vectors, y^ = r^ q + mu
     // computed there from mu read a group ahead.  Lane l writes elements 16 (l & 1) .. + 15 of row l / 2.
     const uint32_t j0 = (uint32_t)(lane & ~31);
-    const uintptr_t outp = OUT == kDecSym ? reinterpret_cast<uintptr_t>(S.sym) : reinterpret_cast<uintptr_t>(S.yout);
-    const bool fast = !PER && (K & 15) == 0 && (outp & 15) == 0 &&
+    const bool fast = !HELP && !PER && (K & 15) == 0 && (outp & 15) == 0 &&
                       (OUT == kDecSym || (reinterpret_cast<uintptr_t>(S.mu) & 15) == 0) &&
                       __all_sync(0xffffffffu, okc && cmin >= (uint32_t)kPF);
     if (fast) {
@@ -869,6 +1018,12 @@ static int dec_threads(int K, int sms) {
 
 template <int OUT, bool PER>
 static cudaError_t launch_dec_t(const RansDecJob& j, const uint8_t* tables, cudaStream_t s) {
+    if (!PER && j.threads == 32) {  // one warp of lanes per block: two serving warps beside it
+        cudaError_t e = smem_optin((const void*)rans_decode_kernel<OUT, PER, true>, kDecSmemBytes);
+        if (e != cudaSuccess) return e;
+        return launch_pdl(rans_decode_kernel<OUT, PER, true>, dim3(j.bps * j.nsec), dim3(96), (size_t)kDecSmemBytes,
+                          s, j, tables);
+    }
     cudaError_t e = smem_optin((const void*)rans_decode_kernel<OUT, PER>, kDecSmemBytes);
     if (e != cudaSuccess) return e;
     return launch_pdl(rans_decode_kernel<OUT, PER>, dim3(j.bps * j.nsec), dim3(j.threads), (size_t)kDecSmemBytes, s,
