@@ -499,10 +499,12 @@ constexpr int kDecTileOff = kDecTabBytes + kDecCntBytes;
 constexpr int kDecMaxWarps = 16;
 constexpr int kDecSmemBytes = kDecTileOff + kDecMaxWarps * 16 * 32 * 2;
 
-// HELP (one warp of lanes per block, the latency-bound case): two more warps serve the decoding warp
-// through shared-memory rings of four groups of 16 steps: warp 1 stages the lanes' scale indices ahead
-// of it, warp 2 takes its symbols and writes y^ = r^ q + mu (or r^) as 16-byte vectors, so the decoding
-// warp issues little besides the state chain.  The rings hand over through mbarriers (bounded waits).
+// HELP (one warp of lanes per block, the latency-bound case): three more warps serve the decoding warp
+// through shared memory, in groups of 16 steps: warp 1 stages the lanes' scale indices in a ring four
+// groups ahead, warp 3 copies each lane's next stream words into a window one group ahead (so a
+// renormalisation reads its word from shared memory, off the global-load latency), and warp 2 takes the
+// symbols from a ring and writes y^ = r^ q + mu (or r^) as 16-byte vectors; the decoding warp issues
+// little besides the state chain.  The hand-overs are mbarriers with bounded waits.
 template <int OUT, bool PER, bool HELP = false>
 __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, const uint8_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint8_t dsm[];
@@ -677,8 +679,12 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     };
     uint32_t bad = 0;
     uint32_t i = (uint32_t)lane;  // element of the next output
-    // one symbol of this lane where act (ALL: known to hold for every lane of the warp); returns it
-    auto decode = [&](uint32_t t, bool act, auto all) -> uint32_t {
+    // the lane's words staged in shared memory (HELP groups): word r is win_cur[r + woff]
+    const uint16_t* win_cur = nullptr;
+    int woff = 0;
+    // one symbol of this lane where act (ALL: known to hold for every lane of the warp; SMW: the words come
+    // from the shared-memory window, else from the lane's global row through w0 / w1); returns it
+    auto decode = [&](uint32_t t, bool act, auto all, auto smw) -> uint32_t {
         if constexpr (decltype(all)::value) act = true;
         bad |= t;
         t &= (uint32_t)(kBins - 1);
@@ -716,8 +722,12 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
             const bool rn = xn < kRansL;
             x = rn ? (xn << 16) | w0 : xn;
             r += rn ? 1u : 0u;
-            w0 = rn ? (uint32_t)w1 : w0;
-            ld_if_u16(w1, wp + (r + 1 < nw ? r + 1 : nw - 1), rn);
+            if constexpr (decltype(smw)::value) {
+                w0 = win_cur[(int)r + woff];  // needed at the next renormalisation only
+            } else {
+                w0 = rn ? (uint32_t)w1 : w0;
+                ld_if_u16(w1, wp + (r + 1 < nw ? r + 1 : nw - 1), rn);
+            }
         }
         return s;
     };
@@ -746,22 +756,29 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     const uintptr_t outp = OUT == kDecSym ? reinterpret_cast<uintptr_t>(S.sym) : reinterpret_cast<uintptr_t>(S.yout);
     if constexpr (HELP) {
         // rings of four groups: indices [4][16 steps][32 lanes] u8, symbols [4][16][32] int16; barriers
-        // t_full, t_empty, s_full, s_empty (four each), one arrival per phase
+        // t_full, t_empty, s_full, s_empty (four each), then w_full, pub (two each), one arrival per phase;
+        // each lane's words for a group in a window [2][32 lanes][17] u32 (34 words), and the read positions
+        // the decoding warp publishes [2][32]
         uint8_t* ring_t = dsm + kDecTileOff;
         int16_t* ring_s = reinterpret_cast<int16_t*>(dsm + kDecTileOff + 2048);
         uint64_t* hb = reinterpret_cast<uint64_t*>(dsm + kDecTileOff + 6144);
+        uint32_t* rpos = reinterpret_cast<uint32_t*>(dsm + kDecTileOff + 6144 + 20 * 8);
+        uint32_t* win32 = reinterpret_cast<uint32_t*>(dsm + kDecTileOff + 6144 + 20 * 8 + 256);
         __shared__ uint32_t ngr_sh;
+        __shared__ uint64_t lstart[32];  // the lanes' first words, counted from the section's words
         const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
         if (threadIdx.x == 0) {
-            for (int k = 0; k < 16; ++k) ptx::mbar_init(&hb[k], 1);
+            for (int k = 0; k < 20; ++k) ptx::mbar_init(&hb[k], 1);
             ptx::fence_mbar_init();
         }
         if (w == 0) {  // whole groups of 16 steps that every lane of the warp codes, with aligned rows
             const bool f = !PER && (K & 15) == 0 && (outp & 15) == 0 &&
                            (reinterpret_cast<uintptr_t>(S.idx) & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(bits) & 3) == 0 &&
                            (OUT == kDecSym || (reinterpret_cast<uintptr_t>(S.mu) & 15) == 0) &&
                            __all_sync(0xffffffffu, okc && cmin >= (uint32_t)kPF);
             if (l == 0) ngr_sh = f ? cmin / kPF : 0u;
+            lstart[l] = pre + excl;
         }
         __syncthreads();
         const uint32_t ngr = ngr_sh;
@@ -863,21 +880,58 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
             }
             return;
         }
-        // ---- warp 0: the state chains, 16 steps per group, indices from the ring, symbols into it
+        if (w == 3) {
+            // ---- word stage: group g reads the lane's words R_g .. R_g + 15, R_g <= R_{g-1} + 16, so the
+            //      window of words R_{g-1} .. R_{g-1} + 31 (R_{-1} = 2, the first after the state) serves
+            //      it; R_{g-1} is published by the decoding warp when group g - 1 starts, which leaves the
+            //      whole of group g - 1 for the copy.  Whole u32 from the 4-byte boundary at or below.
+            const uint64_t wbase = words_at + 2ull * lstart[l];  // the lane's words, bytes from `bits`
+            for (uint32_t g = 0; g < ngr; ++g) {
+                uint32_t rp = 2;
+                if (g > 0) {
+                    if (!__all_sync(0xffffffffu, hwait(&hb[18 + ((g - 1) & 1)], ((g - 1) >> 1) & 1))) break;
+                    rp = rpos[((g - 1) & 1) * 32 + l];
+                }
+                const uint64_t b0 = (wbase + 2ull * rp) & ~3ull;
+                uint32_t* dst = win32 + ((g & 1) * 32 + l) * 17;
+#pragma unroll
+                for (int k = 0; k < 17; ++k) {
+                    const uint64_t o = b0 + 4ull * k;
+                    uint32_t v = 0;
+                    if (o + 4 <= nbytes) v = __ldg(reinterpret_cast<const uint32_t*>(bits + o));
+                    dst[k] = v;
+                }
+                __syncwarp();
+                if (l == 0) ptx::mbar_arrive(&hb[16 + (g & 1)]);
+            }
+            return;
+        }
+        // ---- warp 0: the state chains, 16 steps per group, indices and words from shared memory, symbols
+        //      into the ring
+        uint32_t rprev = 2;  // R_{g-1}: the window of group g starts there
         for (uint32_t g = 0; g < ngr; ++g) {
             const int b = (int)(g & 3);
             const uint32_t use = g >> 2;
-            ahead();
             bool ok = hwait(&hb[b], use & 1);
             if (use > 0 && ok) ok = hwait(&hb[12 + b], (use - 1) & 1);
+            if (ok) ok = hwait(&hb[16 + (g & 1)], (g >> 1) & 1);
             if (!__all_sync(0xffffffffu, ok)) return;
+            // this group's window; publish R_g for the next one
+            const uint64_t A = words_at / 2 + lstart[l] + rprev;  // (words_at is a multiple of 4)
+            woff = (int)(A & 1) - (int)rprev;
+            win_cur = reinterpret_cast<const uint16_t*>(win32 + ((g & 1) * 32 + l) * 17);
+            rpos[(g & 1) * 32 + l] = r;
+            __syncwarp();
+            if (l == 0) ptx::mbar_arrive(&hb[18 + (g & 1)]);
+            rprev = r;
             const uint8_t* tr = ring_t + b * 512 + l;
             int16_t* sr = ring_s + b * 512 + l;
             uint32_t tv[kPF];
 #pragma unroll
             for (int u = 0; u < kPF; ++u) tv[u] = tr[u * 32];
 #pragma unroll
-            for (int u = 0; u < kPF; ++u) sr[u * 32] = (int16_t)((int)decode(tv[u], true, every) - kRmax);
+            for (int u = 0; u < kPF; ++u)
+                sr[u * 32] = (int16_t)((int)decode(tv[u], true, every, every) - kRmax);
             __syncwarp();
             if (l == 0) {
                 ptx::mbar_arrive(&hb[4 + b]);  // indices consumed
@@ -887,6 +941,8 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         m0 = kPF * ngr;
         fi = (uint32_t)lane + m0 * (uint32_t)K;
         i = fi;
+        // the generic path reads the lane's words from its global row: w0 = word r (already held), w1 = r + 1
+        if (ngr > 0) w1 = (unsigned short)ld_u16(wp + (r + 1 < nw ? r + 1 : nw - 1));
     }
     // Fast path, for a warp of 32 lanes in range with good counts and 16-byte aligned rows: the symbols of
     // a group go to a shared-memory tile [16 steps][32 lanes] (one store each, off the state chain), then
@@ -966,7 +1022,8 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
             ahead();
             fetch(m0 + kPF, tn, mn);
 #pragma unroll
-            for (int u = 0; u < kPF; ++u) tile[u * 32 + (threadIdx.x & 31)] = (int16_t)((int)decode(tc[u], true, every) - kRmax);
+            for (int u = 0; u < kPF; ++u)
+                tile[u * 32 + (threadIdx.x & 31)] = (int16_t)((int)decode(tc[u], true, every, some) - kRmax);
             flush(m0);
             load_mu(m0 + kPF);
 #pragma unroll
@@ -985,7 +1042,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
 #pragma unroll
         for (int u = 0; u < kPF; ++u) {
             const bool act = okc;
-            const uint32_t sy = decode(tc[u], act, some);
+            const uint32_t sy = decode(tc[u], act, some, some);
             if (act) put(sy, mc[u]);
         }
 #pragma unroll
@@ -998,7 +1055,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         for (int u = 0; u < kPF; ++u)
             if (m0 + u < cmax) {
                 const bool act = m0 + u < mine;
-                const uint32_t sy = decode(tc[u], act, some);
+                const uint32_t sy = decode(tc[u], act, some, some);
                 if (act) put(sy, mc[u]);
             }
 #pragma unroll
@@ -1018,10 +1075,10 @@ static int dec_threads(int K, int sms) {
 
 template <int OUT, bool PER>
 static cudaError_t launch_dec_t(const RansDecJob& j, const uint8_t* tables, cudaStream_t s) {
-    if (!PER && j.threads == 32) {  // one warp of lanes per block: two serving warps beside it
+    if (!PER && j.threads == 32) {  // one warp of lanes per block: three serving warps beside it
         cudaError_t e = smem_optin((const void*)rans_decode_kernel<OUT, PER, true>, kDecSmemBytes);
         if (e != cudaSuccess) return e;
-        return launch_pdl(rans_decode_kernel<OUT, PER, true>, dim3(j.bps * j.nsec), dim3(96), (size_t)kDecSmemBytes,
+        return launch_pdl(rans_decode_kernel<OUT, PER, true>, dim3(j.bps * j.nsec), dim3(128), (size_t)kDecSmemBytes,
                           s, j, tables);
     }
     cudaError_t e = smem_optin((const void*)rans_decode_kernel<OUT, PER>, kDecSmemBytes);
