@@ -42,22 +42,6 @@ constexpr int kPF = 16;                                   // symbols fetched ahe
 constexpr long long kSpinDefault = 4000000000LL;          // about 2 s at 2 GHz
 constexpr uint64_t kFlagAgg = 1ull << 62, kFlagIncl = 2ull << 62, kFlagMask = (1ull << 62) - 1;
 
-// Loads issued where they stand (the per-lane prefetches must not sink down to their use).
-__device__ __forceinline__ uint32_t ld_early_u8(const uint8_t* p) {
-    unsigned short v;
-    asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ int ld_early_s16(const int16_t* p) {
-    short v;
-    asm volatile("ld.global.nc.s16 %0, [%1];" : "=h"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float ld_early_f32(const float* p) {
-    float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
 __device__ __forceinline__ uint32_t ld_u16(const uint16_t* p) {
     unsigned short v;
     asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(v) : "l"(p));
@@ -281,11 +265,12 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
                 x = enc_update(x, q);
             };
             auto flush = [&]() {  // the group's words, in emission order, backwards into the row
-                if (STAGE) return;
+                if constexpr (!STAGE) {
 #pragma unroll
-                for (int u = 0; u < kPF; ++u)
-                    if (emit & (1u << u)) row[--wp] = (uint16_t)wbuf[u];
-                emit = 0;
+                    for (int u = 0; u < kPF; ++u)
+                        if (emit & (1u << u)) row[--wp] = (uint16_t)wbuf[u];
+                    emit = 0;
+                }
             };
             const int top = (int)cnt - 1;
             fetch(top, tc, vc);
