@@ -363,14 +363,15 @@ ufvc_status ufvc_set_conv_pairs(ufvc_ctx* ctx, int enable);
 
 /* The first analysis layer read straight from the frame bytes (the patch embedding of the stacked chunk,
  * Sec. 3.1: frame n's three channels become channels 3n .. 3n+2 of one input, replicate-padded to a
- * multiple of 16, then A1 = 3x3 stride-2 convolution + GELU), as the BF16 chunk encoder runs it: d_frames
+ * multiple of 16, then A1 = 3x3 stride-2 convolution + GELU), as the BF16 and FP8 chunk encoders run it
+ * (the FP8 encoder with the same bf16 operands, writing E4M3 codes instead): d_frames
  * holds N frames in the context's colour format (RGB, YUV444P or YUV420P; YUV420 chroma repeated over
  * its 2x2 block), d_out receives bf16 NHWC [ceil16(H)/2][ceil16(W)/2][64].  The bytes enter as v / 256
  * (exact in bf16) and the bf16 weights carry 256 / 255, so the operands are bf16(w * 256 / 255) and
  * v / 256.  kernel: 0 = the kernel the chunk encoder picks, 1 = the register-staged kernel (every
  * format and width), 2 = the TMA-window kernel (interleaved RGB whose rows are a multiple of 16 bytes
  * and start 16-byte aligned; UFVC_ERR_ARG otherwise).  UFVC_ERR_UNSUPPORTED for contexts whose first
- * layer does not read the frame bytes (not BF16, an odd chunk length or one above 8, or BT.709 RGB
+ * layer does not read the frame bytes (FP32, an odd chunk length or one above 8, or BT.709 RGB
  * input).  Asynchronous on `stream`; device-side errors go to the status word. */
 ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, int width, int height, int kernel, void* d_out,
                              void* stream);

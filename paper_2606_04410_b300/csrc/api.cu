@@ -132,7 +132,7 @@ struct ufvc_ctx {
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
     // taps regrouped by 2x2 super-pixel; weight rows [64][tap][sub-pixel][32]; bias shared with enc[L_A1])
     LayerW a1s2d;
-    void* first_w = nullptr;  // A1's weight image for the kernels that read frame bytes (BF16)
+    void* first_w = nullptr;  // A1's weight image for the kernels that read frame bytes (BF16 and FP8)
     // progressive means (ufvc_set_progressive_means): P1a P1b P2a P2b P3a P3b; pm_on selects version-2
     // streams (partitions 1..3 coded with the progressive means)
     LayerW pm[kMeanLayers];
@@ -788,7 +788,8 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
             return bail(st);
     if (cfg->precision == UFVC_BF16 && 3 * ctx->N <= 32 && (st = upload_a1_s2d(ctx, weights + offs[L_A1])) != UFVC_OK)
         return bail(st);
-    if (cfg->precision == UFVC_BF16 && first_layer_ct(ctx->N) && ctx->enc[L_A1].cout == 64 && ctx->enc[L_A1].k == 3) {
+    if ((cfg->precision == UFVC_BF16 || cfg->precision == UFVC_FP8) && first_layer_ct(ctx->N) &&
+        ctx->enc[L_A1].cout == 64 && ctx->enc[L_A1].k == 3) {
         // the frame-byte kernel's input is x * kS2dInScale, like the space-to-depth pack's
         const int pitch = first_layer_pitch(ctx->N);
         std::vector<uint16_t> img(first_layer_weight_bytes(pitch) / 2);
@@ -1076,12 +1077,13 @@ static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* fra
     const Arch& a = ctx->arch;
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
     const bool s2d = ctx->a1s2d.wtc != nullptr && p->C0p == 32;
-    // BF16 frames in RGB, YUV444 or YUV420 with even N <= 8: A1 reads the frame bytes itself (no pack pass)
+    // BF16 / FP8 frames in RGB, YUV444 or YUV420 with even N <= 8: A1 reads the frame bytes itself (no pack)
     const bool first = ctx->first_w != nullptr && ctx->color != UFVC_COLOR_RGB_BT709;
     if (first) {
         prof_begin(ctx, "A1", s);
+        // (an FP8 context's A1 computes with bf16 operands and writes the E4M3 codes A2 reads)
         CK(launch_first_layer(frames, ctx->color, ctx->N, p->H, p->W, p->h1, p->w1, ctx->first_w, ctx->enc[L_A1].b,
-                              reinterpret_cast<__nv_bfloat16*>(p->a1), ctx->d_status, s));
+                              p->a1, fp8 ? 1.f / ctx->act_scale[T_A1] : 0.f, ctx->d_status, s));
     } else {
         prof_begin(ctx, "pack", s);
         if (ctx->cfg.precision == UFVC_FP32)
@@ -1813,16 +1815,16 @@ extern "C" ufvc_status ufvc_first_layer(ufvc_ctx* ctx, const uint8_t* d_frames, 
         return fail(ctx, UFVC_ERR_ARG, "first_layer: bad argument");
     if (!ctx->first_w || ctx->color == UFVC_COLOR_RGB_BT709)
         return fail(ctx, UFVC_ERR_UNSUPPORTED,
-                    "first_layer: this context's first layer does not read frame bytes (needs BF16, an even chunk "
-                    "length of at most 8 and colour format RGB, YUV444P or YUV420P)");
+                    "first_layer: this context's first layer does not read frame bytes (needs BF16 or FP8, an even "
+                    "chunk length of at most 8 and colour format RGB, YUV444P or YUV420P)");
     if (kernel == 2 && !first_layer_tma_ok(ctx->color, width, d_frames))
         return fail(ctx, UFVC_ERR_ARG,
                     "first_layer: the TMA kernel needs interleaved RGB frames with rows of a multiple of 16 bytes "
                     "at a 16-byte aligned address");
     CK(cudaSetDevice(ctx->cfg.device));
     const int Ho = conv_out(ceil_div(height, 16) * 16, 3, 2), Wo = conv_out(ceil_div(width, 16) * 16, 3, 2);
-    CK(launch_first_layer(d_frames, ctx->color, ctx->N, height, width, Ho, Wo, ctx->first_w, ctx->enc[L_A1].b,
-                          static_cast<__nv_bfloat16*>(d_out), ctx->d_status, (cudaStream_t)stream, kernel));
+    CK(launch_first_layer(d_frames, ctx->color, ctx->N, height, width, Ho, Wo, ctx->first_w, ctx->enc[L_A1].b, d_out,
+                          0.f, ctx->d_status, (cudaStream_t)stream, kernel));
     CK(cudaGetLastError());
     return UFVC_OK;
 }

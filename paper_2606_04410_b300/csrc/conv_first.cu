@@ -29,6 +29,7 @@
 #include "tc_ptx.h"
 
 #include <cuda.h>
+#include <cuda_fp8.h>
 
 namespace ufvc {
 
@@ -114,9 +115,27 @@ __device__ __forceinline__ void first_mma(uint32_t d, uint32_t xw, uint32_t sB_u
     }
 }
 
-// Epilogue of 32 accumulator columns (half) of output pixel (oh, ow): bias, GELU, bf16 NHWC store
-__device__ __forceinline__ void first_store(float* v, uint32_t bias_u, __nv_bfloat16* out, int oh, int ow, int Wo,
-                                            int half) {
+// NV consecutive output channels (NV a multiple of 16) as E4M3 codes of value x inv, 16 bytes at a time
+template <int NV>
+__device__ __forceinline__ void store_e4m3(const float* v, float inv, uint8_t* dst) {
+#pragma unroll
+    for (int i = 0; i < NV / 16; ++i) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float* f = v + 16 * i + 4 * k;
+            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[0] * inv, f[1] * inv), __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[2] * inv, f[3] * inv), __NV_SATFINITE, __NV_E4M3);
+            w[k] = lo | (hi << 16);
+        }
+        reinterpret_cast<uint4*>(dst)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// Epilogue of 32 accumulator columns (half) of output pixel (oh, ow): bias, GELU, NHWC store as bf16, or
+// as E4M3 codes of value x out_inv when out_inv != 0 (an FP8 context's A1)
+__device__ __forceinline__ void first_store(float* v, uint32_t bias_u, void* out, float out_inv, int oh, int ow,
+                                            int Wo, int half) {
 #pragma unroll
     for (int c = 0; c < 32; c += 4) {
         const float4 bb = lds_f4(bias_u + half * 128 + 4 * c);
@@ -124,7 +143,11 @@ __device__ __forceinline__ void first_store(float* v, uint32_t bias_u, __nv_bflo
         gelu_tc2(v[c], v[c + 1]);
         gelu_tc2(v[c + 2], v[c + 3]);
     }
-    uint4* d = reinterpret_cast<uint4*>(out + ((size_t)oh * Wo + ow) * 64 + half * 32);
+    if (out_inv != 0.f) {
+        store_e4m3<32>(v, out_inv, static_cast<uint8_t*>(out) + ((size_t)oh * Wo + ow) * 64 + half * 32);
+        return;
+    }
+    uint4* d = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + ((size_t)oh * Wo + ow) * 64 + half * 32);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         uint32_t u[4];
@@ -162,8 +185,8 @@ __device__ __forceinline__ uint32_t chan_byte(const uint8_t* __restrict__ fr, in
 template <int FMT, int CT>
 __global__ void __launch_bounds__(kRegThreads, 1)
     conv_first_kernel(const uint8_t* __restrict__ frames, int N, int H, int W, int Ho, int Wo,
-                      const uint4* __restrict__ wimg, const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
-                      int* err) {
+                      const uint4* __restrict__ wimg, const float* __restrict__ bias, void* __restrict__ out,
+                      float out_inv, int* err) {
     constexpr int CTP = first_ctp(CT);
     constexpr int KCB = first_kc(CTP);
     constexpr int PR = CT / 8;  // 8-channel groups holding real channels
@@ -267,16 +290,21 @@ __global__ void __launch_bounds__(kRegThreads, 1)
                 gelu_tc2(v[c], v[c + 1]);
                 gelu_tc2(v[c + 2], v[c + 3]);
             }
-            uint4* d = reinterpret_cast<uint4*>(out + ((size_t)oh * Wo + ow) * 64 + cq * 16);
+            if (out_inv != 0.f) {
+                store_e4m3<16>(v, out_inv, static_cast<uint8_t*>(out) + ((size_t)oh * Wo + ow) * 64 + cq * 16);
+            } else {
+                uint4* d = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + ((size_t)oh * Wo + ow) * 64 +
+                                                    cq * 16);
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                uint32_t u[4];
+                for (int i = 0; i < 2; ++i) {
+                    uint32_t u[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * i + 2 * e], v[8 * i + 2 * e + 1]);
-                    u[e] = *reinterpret_cast<uint32_t*>(&h);
+                    for (int e = 0; e < 4; ++e) {
+                        __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * i + 2 * e], v[8 * i + 2 * e + 1]);
+                        u[e] = *reinterpret_cast<uint32_t*>(&h);
+                    }
+                    d[i] = make_uint4(u[0], u[1], u[2], u[3]);
                 }
-                d[i] = make_uint4(u[0], u[1], u[2], u[3]);
             }
         }
         ptx::tc_fence_before();
@@ -376,7 +404,7 @@ template <int CT>
 __global__ void __launch_bounds__(kTmaThreads, 1)
     conv_first_tma_kernel(const __grid_constant__ CUtensorMap tmF, int N, int H, int Ho, int Wo,
                           const uint4* __restrict__ wimg, const float* __restrict__ bias,
-                          __nv_bfloat16* __restrict__ out, int* err) {
+                          void* __restrict__ out, float out_inv, int* err) {
     constexpr int CTP = first_ctp(CT);
     constexpr int KCB = first_kc(CTP);             // 64-element K chunks of the weights (K = 9 CTP)
     constexpr int PR = CT / 8;                     // 8-channel groups holding real channels
@@ -528,7 +556,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             ptx::mbar_arrive(&acc_empty[b]);
             const int h0 = (t / tiles_w) * kT4H, w0 = (t % tiles_w) * kT4W;
             const int oh = h0 + (row >> 3), ow = w0 + (row & 7);
-            if (oh < Ho && ow < Wo) first_store(v, ptx::smem_u32(sbias), out, oh, ow, Wo, half);
+            if (oh < Ho && ow < Wo) first_store(v, ptx::smem_u32(sbias), out, out_inv, oh, ow, Wo, half);
         }
     }
     ptx::tc_fence_before();
@@ -541,7 +569,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 
 template <int CT>
 static cudaError_t launch_first_tma_t(const uint8_t* frames, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                                      const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s) {
+                                      const float* bias, void* out, float out_inv, int* err, cudaStream_t s) {
     alignas(64) CUtensorMap map;
     if (!encode_frames_map(&map, frames, N, H, 3 * W, kRawBX, kW4H)) return cudaErrorInvalidValue;
     cudaError_t e = smem_optin((const void*)conv_first_tma_kernel<CT>, (int)first_tma_smem(CT, 8));
@@ -550,12 +578,12 @@ static cudaError_t launch_first_tma_t(const uint8_t* frames, int N, int H, int W
     const int tiles = ((Wo + kT4W - 1) / kT4W) * ((Ho + kT4H - 1) / kT4H);
     const int grid = tiles < sms ? tiles : sms;
     return launch_pdl(conv_first_tma_kernel<CT>, dim3(grid), dim3(kTmaThreads), first_tma_smem(CT, N), s, map, N, H,
-                      Ho, Wo, static_cast<const uint4*>(wimg), bias, out, err);
+                      Ho, Wo, static_cast<const uint4*>(wimg), bias, out, out_inv, err);
 }
 
 template <int FMT, int CT>
 static cudaError_t launch_first_t(const uint8_t* frames, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                                  const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s) {
+                                  const float* bias, void* out, float out_inv, int* err, cudaStream_t s) {
     const size_t smem = first_reg_smem(CT);
     cudaError_t e = smem_optin((const void*)conv_first_kernel<FMT, CT>, (int)smem);
     if (e != cudaSuccess) return e;
@@ -563,7 +591,7 @@ static cudaError_t launch_first_t(const uint8_t* frames, int N, int H, int W, in
     const int tiles = ((Wo + kT4W - 1) / kT4W) * ((Ho + kT4H - 1) / kT4H);
     const int grid = tiles < sms ? tiles : sms;
     return launch_pdl(conv_first_kernel<FMT, CT>, dim3(grid), dim3(kRegThreads), smem, s, frames, N, H, W, Ho, Wo,
-                      static_cast<const uint4*>(wimg), bias, out, err);
+                      static_cast<const uint4*>(wimg), bias, out, out_inv, err);
 }
 
 int first_layer_ct(int n_frames) {
@@ -592,23 +620,23 @@ bool first_layer_tma_ok(int fmt, int W, const void* frames) {
 }
 
 cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s, int sel) {
+                               const float* bias, void* out, float out_inv, int* err, cudaStream_t s, int sel) {
     const int ct = first_layer_ct(N);
     const bool tma = first_layer_tma_ok(fmt, W, frames);
     if (sel == 2 && !tma) return cudaErrorInvalidValue;
     if (tma && sel != 1) {
         switch (ct) {  // whole 16-byte rows: the window comes by TMA
-            case 8: return launch_first_tma_t<8>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);
-            case 16: return launch_first_tma_t<16>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);
-            case 24: return launch_first_tma_t<24>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);
+            case 8: return launch_first_tma_t<8>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);
+            case 16: return launch_first_tma_t<16>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);
+            case 24: return launch_first_tma_t<24>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);
             default: return cudaErrorInvalidValue;
         }
     }
 #define UFVC_FIRST(F)                                                                                          \
     switch (ct) {                                                                                              \
-        case 8: return launch_first_t<F, 8>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);                 \
-        case 16: return launch_first_t<F, 16>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);               \
-        case 24: return launch_first_t<F, 24>(frames, N, H, W, Ho, Wo, wimg, bias, out, err, s);               \
+        case 8: return launch_first_t<F, 8>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);                 \
+        case 16: return launch_first_t<F, 16>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);               \
+        case 24: return launch_first_t<F, 24>(frames, N, H, W, Ho, Wo, wimg, bias, out, out_inv, err, s);               \
         default: return cudaErrorInvalidValue;                                                                 \
     }
     switch (fmt) {

@@ -284,12 +284,17 @@ enum { OP_BF16 = 0, OP_E4M3 = 1, OP_BF16_32 = 2 };
 // each SM's shared memory per MMA at BN = 256.  Both CTAs' loads complete on the even CTA's stage
 // barrier (its producer expects the bytes of both); the MMA commits arrive on both CTAs' barriers; the
 // odd CTA's epilogue frees an accumulator by arriving on the even CTA's barrier.
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false>
+// O8 (with STAGED): the output is E4M3 codes (value x out_inv), staged as 64-byte rows per 64-channel slab
+// without swizzle; otherwise a staged output is bf16 (also for E4M3 operands, e.g. the layer feeding the
+// bf16 final layer).
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false,
+          bool O8 = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
     constexpr bool F8 = OP == OP_E4M3;
-    static_assert(!(F8 && STAGED), "FP8 outputs use the per-thread epilogue");
+    static_assert(!O8 || (STAGED && F8), "E4M3 staging: staged E4M3 layers");
+    constexpr int SLAB = 128 * (O8 ? 64 : 128);  // bytes of one 64-channel staging slab
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     static_assert(MT == 1 || (MT == 2 && !F8 && OP == OP_BF16), "two sub-tiles: BF16 operands");
@@ -300,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int EG = MT == 2 ? 1 : epi_groups(BN);  // epilogue groups (tiles drained concurrently)
     constexpr int WPQ = 4 / EG;         // warps per TMEM lane quarter in a group
     constexpr int NACC = 2 * EG;        // TMEM accumulators
-    constexpr int C_BYTES = STAGED ? 128 * BN * 2 * EG : 0;
+    constexpr int C_BYTES = STAGED ? (BN / 64) * SLAB * EG : 0;
     constexpr int ACOLS = MT * BN;      // TMEM columns of one tile's accumulator(s)
     constexpr uint32_t TMEM_COLS = (NACC * ACOLS <= 32) ? 32 : (NACC * ACOLS <= 64) ? 64 : (NACC * ACOLS <= 128) ? 128
                                    : (NACC * ACOLS <= 256) ? 256 : 512;
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int grp = egrp * SG + cpart / GQ;   // slab group (staged epilogue)
         const int lead = 2 + 4 * (egrp * WPQ + (cpart / GQ) * GQ);  // first warp of the slab group
         const bool elected = STAGED && warp == lead && lane == 0;
-        uint8_t* sCg = sC + egrp * (BN / 64) * (128 * 128);      // this group's staging slabs
+        uint8_t* sCg = sC + egrp * (BN / 64) * SLAB;             // this group's staging slabs
         int tl = egrp, k = 0;  // k counts sub-tiles (the staging barriers' phases)
         bool run = true;
         for (int t = cid + egrp * ncl; run && t < p.total_tiles; t += EG * ncl, tl += EG) {
@@ -531,14 +536,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                             ok = __all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err));
                             if (!ok) break;  // warp-uniform: the next tcgen05.ld needs the whole warp
                         }
-                        // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
-                        const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * (128 * 128) + row * 128;
+                        if constexpr (O8) {
+                            // row `row` of slab c/64: 64 E4M3 codes in order, 16 bytes at a time
+                            const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * SLAB + row * 64 + (c & 63);
 #pragma unroll
-                        for (int i = 0; i < CHUNK / 8; ++i) {
-                            const int j = ((c & 63) >> 3) + i;
-                            ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
-                                              pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
-                                              pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                            for (int i = 0; i < CHUNK / 16; ++i) {
+                                uint32_t wq[4];
+#pragma unroll
+                                for (int k4 = 0; k4 < 4; ++k4) {
+                                    const float* f = v + 16 * i + 4 * k4;
+                                    const uint32_t lo = __nv_cvt_float2_to_fp8x2(
+                                        make_float2(f[0] * p.out_inv, f[1] * p.out_inv), __NV_SATFINITE, __NV_E4M3);
+                                    const uint32_t hi = __nv_cvt_float2_to_fp8x2(
+                                        make_float2(f[2] * p.out_inv, f[3] * p.out_inv), __NV_SATFINITE, __NV_E4M3);
+                                    wq[k4] = lo | (hi << 16);
+                                }
+                                ptx::st_shared_v4(base + 16 * i, wq[0], wq[1], wq[2], wq[3]);
+                            }
+                        } else {
+                            // row `row` of slab c/64, 16-byte chunks XOR-swizzled by row & 7 (the TMA 128-byte swizzle)
+                            const uint32_t base = ptx::smem_u32(sCg) + (c >> 6) * SLAB + row * 128;
+#pragma unroll
+                            for (int i = 0; i < CHUNK / 8; ++i) {
+                                const int j = ((c & 63) >> 3) + i;
+                                ptx::st_shared_v4(base + ((j ^ (row & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                                  pack_bf16(v[8 * i + 2], v[8 * i + 3]),
+                                                  pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                                  pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                            }
                         }
                     } else {
                         if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
@@ -567,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int hi = lo + GQ * PER < BN ? lo + GQ * PER : BN;
                         for (int sl = lo >> 6; sl < (hi + 63) >> 6; ++sl) {
                             const int col0 = nt * BN + sl * 64;
-                            const uint8_t* src = sCg + sl * (128 * 128);
+                            const uint8_t* src = sCg + sl * SLAB;
                             if (p.c_rank == 4) {
                                 ptx::tma_store_4d(&tmC, src, col0, w0, h0, g);
                             } else {
@@ -610,26 +635,37 @@ __global__ void __launch_bounds__(kThreads, 1)
 constexpr int kHaloRowBytes = 17 * 1024;  // 130 rows x 128 B, rounded up to the 1024-B swizzle repeat
 __host__ __device__ constexpr int halo_groups(int BN) { return BN == 16 ? 4 : 2; }
 constexpr int kHaloBoxBytes = 130 * 128;
+// E4M3 operands (F8): 130 rows x 64 B with the 64-byte swizzle, rounded up to its 512-B repeat
+constexpr int kHaloRowBytes8 = 17 * 512;
+constexpr int kHaloBoxBytes8 = 130 * 64;
 
 // Epilogue of the resident-weight kernel.  The 16 epilogue warps form halo_groups(BN) groups that drain
 // different tiles at once, each from its own pair of TMEM accumulators: BN = 64 -> two groups of eight
 // warps (two column halves of 32 x four TMEM lane quarters), BN = 16 -> four groups of four warps.
 // OUTK: 0 = every thread stores its own pixel; 1 = bf16 NHWC (BN = 64) through a swizzled staging
-// tile per group and a TMA store.  (The final frame layer has its own kernel, conv_tc_final_kernel.)
-template <int BN, int STAGES, int OUTK>
+// tile per group and a TMA store; 2 = E4M3 NHWC codes (BN = 64) through a plain staging tile (128 pixel
+// rows of 64 bytes) per group and a TMA store.  (The final frame layer has its own kernel,
+// conv_tc_final_kernel.)
+// F8: E4M3 operands (kind::f8f6f4, K = 32 per MMA) in 64-byte rows with the 64-byte swizzle; a tap's
+// window is again its start address kx rows into the input row; the epilogue rescales each accumulator
+// column by the input scale times the output channel's weight scale (finish_cols).
+template <int BN, int STAGES, int OUTK, bool F8 = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_halo_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
-    constexpr int A_BYTES = 3 * kHaloRowBytes;
-    constexpr int B_BYTES = 9 * BN * 128;
+    constexpr int RB = F8 ? 64 : 128;  // bytes of one pixel's 64 input channels
+    constexpr int ROWB = F8 ? kHaloRowBytes8 : kHaloRowBytes;
+    constexpr int A_BYTES = 3 * ROWB;
+    constexpr int B_BYTES = 9 * BN * RB;
     constexpr int EG = halo_groups(BN);      // tiles drained concurrently (epilogue groups)
     constexpr int WPG = 16 / EG;             // warps per group: WPG / 4 column parts x 4 lane quarters
     constexpr int CPW = BN / (WPG / 4);      // accumulator columns per warp (16 or 32)
     constexpr int NACC = 2 * EG;             // TMEM accumulators
     constexpr uint32_t TMEM_COLS = NACC * BN <= 128 ? 128 : 256;
-    constexpr int C_BYTES = OUTK == 1 ? EG * 128 * BN * 2 : 0;  // one staging tile per group
+    constexpr int C_BYTES = OUTK == 1 ? EG * 128 * BN * 2 : OUTK == 2 ? EG * 128 * BN : 0;  // per group
     static_assert(BN == 16 || BN == 64, "resident-weight kernel: N tile of 16 or 64");
-    static_assert(OUTK == 0 || (OUTK == 1 && BN == 64), "staged stores: bf16 NHWC with N = 64");
+    static_assert(OUTK == 0 || BN == 64, "staged stores: N = 64");
+    static_assert(OUTK != 2 || F8, "E4M3 staging: FP8 layers");
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sB = smem;
@@ -703,17 +739,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bfree_par ^= 1;
                     }
                     ptx::mbar_arrive_expect_tx(bfull, B_BYTES);
-                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * BN * 128, &tmB, bfull, tap * 64, nt * BN, g);
+                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * BN * RB, &tmB, bfull, tap * 64, nt * BN, g);
                     cur_key = key;
                     ++nb;
                 }
                 const int s = it % STAGES;
                 const uint32_t ph = (it / STAGES) & 1;
                 if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) break;
-                ptx::mbar_arrive_expect_tx(&full[s], 3 * kHaloBoxBytes);
+                ptx::mbar_arrive_expect_tx(&full[s], 3 * (F8 ? kHaloBoxBytes8 : kHaloBoxBytes));
                 const int ag = p.a_grouped ? g : 0, w0 = strip * 128;
                 for (int ky = 0; ky < 3; ++ky)
-                    ptx::tma_load_4d(sA + s * A_BYTES + ky * kHaloRowBytes, &tmA, &full[s], 0, w0 - 1, oh + ky - 1, ag);
+                    ptx::tma_load_4d(sA + s * A_BYTES + ky * ROWB, &tmA, &full[s], 0, w0 - 1, oh + ky - 1, ag);
                 used[s] = true;
                 last_par[s] = ph;
             }
@@ -726,7 +762,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_bf16(BN);
+            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(BN) : ptx::idesc_bf16(BN);
             int it = 0, tl = 0, cur_key = -1;
             uint32_t bfull_par = 0;
             for (int t = t_begin; t < t_end; ++t, ++it, ++tl) {
@@ -749,10 +785,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap % 3;
+                    if constexpr (F8) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * kHaloRowBytes + kx * 128 + kk * 32),
-                                     ptx::sdesc_sw128(b0 + tap * BN * 128 + kk * 32), idesc, (tap | kk) != 0);
+                        for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
+                            ptx::mma_f8(d, ptx::sdesc_sw64(a0 + ky * ROWB + kx * 64 + kk * 32),
+                                        ptx::sdesc_sw64(b0 + tap * BN * 64 + kk * 32), idesc, (tap | kk) != 0);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * ROWB + kx * 128 + kk * 32),
+                                         ptx::sdesc_sw128(b0 + tap * BN * 128 + kk * 32), idesc, (tap | kk) != 0);
+                    }
                 }
                 ptx::mma_commit(&empty[s]);
                 ptx::mma_commit(&tfull[acc]);
@@ -767,7 +810,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int grp = colq / (WPG / 4), part = colq % (WPG / 4);
         const bool lead_warp = warp == 2 + grp * WPG;
         const bool elected = OUTK != 0 && lead_warp && lane == 0;
-        uint8_t* sCg = sC + grp * (128 * BN * 2);
+        uint8_t* sCg = sC + grp * (128 * BN * (OUTK == 2 ? 1 : 2));
         int tl = grp, k = 0;
         for (int t = t_begin + grp; t < t_end; t += EG, tl += EG, ++k) {
             const int acc = tl % NACC, use = tl / NACC;
@@ -794,7 +837,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
                 }
-                {
+                if constexpr (OUTK == 2) {
+                    // E4M3 codes, 64-byte pixel rows in order (no swizzle), 16 bytes at a time
+                    const uint32_t base = ptx::smem_u32(sCg) + row * 64 + part * CPW;
+#pragma unroll
+                    for (int i = 0; i < CPW / 16; ++i) {
+                        uint32_t wq[4];
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const float* f = v + 16 * i + 4 * k4;
+                            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[0] * p.out_inv, f[1] * p.out_inv),
+                                                                         __NV_SATFINITE, __NV_E4M3);
+                            const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[2] * p.out_inv, f[3] * p.out_inv),
+                                                                         __NV_SATFINITE, __NV_E4M3);
+                            wq[k4] = lo | (hi << 16);
+                        }
+                        ptx::st_shared_v4(base + 16 * i, wq[0], wq[1], wq[2], wq[3]);
+                    }
+                } else {
                     const uint32_t base = ptx::smem_u32(sCg) + row * 128;
 #pragma unroll
                     for (int i = 0; i < CPW / 8; ++i) {
@@ -1160,16 +1220,17 @@ static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false)
     }
 }
 
-template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false>
+template <int BN, int STAGES, bool STAGED, int OP = OP_BF16, bool KM = false, int MT = 1, bool PAIR = false,
+          bool O8 = false>
 static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                              cudaStream_t s) {
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;
     constexpr int EG = MT == 2 ? 1 : epi_groups(BN);
     constexpr int kSmem = STAGES * (128 * MT * ROWB + (PAIR ? BN / 2 : BN) * ROWB) +
-                          (STAGED ? 128 * BN * 2 * EG : 0) + kSmemExtra;
+                          (STAGED ? (BN / 64) * 128 * (O8 ? 64 : 128) * EG : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
-    const void* fn = (const void*)conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>;
+    const void* fn = (const void*)conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR, O8>;
     cudaError_t e = smem_optin(fn, smem);
     if (e != cudaSuccess) return e;
     if constexpr (PAIR) {
@@ -1177,29 +1238,30 @@ static cudaError_t launch_bn(const CUtensorMap& a, const CUtensorMap& b, const C
         const int pairs = max_pairs(fn, smem, kThreads);
         if (pairs < 1) return cudaErrorInvalidConfiguration;
         const int grid = 2 * (args.total_tiles < pairs ? args.total_tiles : pairs);
-        return launch_pdl_pair(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>, dim3(grid), dim3(kThreads), smem,
-                               s, a, b, c, args);
+        return launch_pdl_pair(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR, O8>, dim3(grid), dim3(kThreads),
+                               smem, s, a, b, c, args);
     }
     const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR>, dim3(grid), dim3(kThreads), smem, s, a, b,
-                      c, args);
+    return launch_pdl(conv_tc_kernel<BN, STAGES, STAGED, OP, KM, MT, PAIR, O8>, dim3(grid), dim3(kThreads), smem, s, a,
+                      b, c, args);
 }
 
 // d.in: bf16 NHWC [groups or 1][H][W][Cin] (Cin a multiple of 64); d.w: bf16 [groups][cout_pad][k*k*Cin];
 // returns a CUDA error or cudaSuccess; UFVC argument problems return cudaErrorInvalidValue.
-template <int BN, int STAGES, int OUTK>
+template <int BN, int STAGES, int OUTK, bool F8 = false>
 static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                                cudaStream_t s) {
-    constexpr int C_BYTES = OUTK == 1 ? halo_groups(BN) * 128 * BN * 2 : 0;
-    constexpr int kSmem = 9 * BN * 128 + STAGES * 3 * kHaloRowBytes + C_BYTES + kSmemExtra;
+    constexpr int C_BYTES = OUTK == 1 ? halo_groups(BN) * 128 * BN * 2 : OUTK == 2 ? halo_groups(BN) * 128 * BN : 0;
+    constexpr int kSmem = 9 * BN * (F8 ? 64 : 128) + STAGES * 3 * (F8 ? kHaloRowBytes8 : kHaloRowBytes) + C_BYTES +
+                          kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     const int smem = kSmem;
-    cudaError_t e = smem_optin((const void*)conv_tc_halo_kernel<BN, STAGES, OUTK>, smem);
+    cudaError_t e = smem_optin((const void*)conv_tc_halo_kernel<BN, STAGES, OUTK, F8>, smem);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
+    return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK, F8>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
 
 template <int OUTK>
@@ -1284,20 +1346,29 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // stride-1 3x3 layers with 64 input channels and at most 64 output channels: resident weights,
     // three input rows per 128-pixel strip (wider layers keep one N tile on the streaming kernel, which
     // re-reads the input less than several N tiles would)
-    const bool f8 = d.w8 != nullptr;  // E4M3 operands: streaming kernel, per-thread epilogue
-    const bool halo = !f8 && !c32 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64);
+    const bool f8 = d.w8 != nullptr;  // E4M3 operands
+    // E4M3 layers of this shape (the decoders' R2) take the resident-weight kernel with E4M3 NHWC outputs
+    // staged for TMA stores; other E4M3 layers the streaming kernel with the per-thread epilogue
+    const int out_c0 = (d.mode == OUT_NHWC && d.out_c_stride) ? d.out_c_stride : d.Cout;
+    const bool halo8 = f8 && d.stride == 1 && d.k == 3 && d.Cin == 64 && d.cout_pad == 64 && d.mode == OUT_NHWC &&
+                       !d.out_f32 && d.out_inv != 0.f && out_c0 % 16 == 0 && d.out_gs % 16 == 0;
+    const bool halo = (!f8 && !c32 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64)) ||
+                      halo8;
     if (halo) BN = d.cout_pad;
     // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
     // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
     // stored through one map whose row dimension spans all groups, so tiles must not cross a group's
     // last row (TH divides Ho)
     const int Cq = d.Cout / 4;
-    const bool ps_stage = !f8 && !halo && BN >= 64 && d.mode == OUT_PS && d.ps_major && Cq % 64 == 0 &&
+    // (E4M3 operands: E4M3 outputs are staged as codes, the pixel-shuffle layer feeding the final layer as
+    // bf16; both with 16-byte aligned rows)
+    const bool o8 = f8 && d.out_inv != 0.f;
+    const bool ps_stage = !halo && !c32 && BN >= 64 && d.mode == OUT_PS && d.ps_major && Cq % 64 == 0 &&
                           d.out_h == 2 * Ho && d.out_w == 2 * Wo &&
                           (d.groups == 1 || d.out_gs == 4LL * Ho * Wo * Cq);
     const int out_c = (d.mode == OUT_NHWC && d.out_c_stride) ? d.out_c_stride : d.Cout;
-    const bool nhwc_stage = !f8 && !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 && out_c % 8 == 0 &&
-                            d.out_gs % 8 == 0;
+    const bool nhwc_stage = !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 &&
+                            (f8 ? o8 && out_c % 16 == 0 && d.out_gs % 16 == 0 : out_c % 8 == 0 && d.out_gs % 8 == 0);
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
     if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
@@ -1375,6 +1446,45 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (!encode_map(&mb, f8 ? d.w8 : d.wtc, 3, dims, str, box, dt, swz)) return cudaErrorInvalidValue;
     }
     CUtensorMap mc = mb;  // unused by the unstaged kernels
+    if (halo8) {
+        // E4M3 codes [G][out_h][out_w][out_c], positions beyond Ho x Wo dropped; 64-byte boxes, no swizzle
+        const int Hd = d.out_h < Ho ? d.out_h : Ho, Wd = d.out_w < Wo ? d.out_w : Wo;
+        cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
+        cuuint64_t str[3] = {(cuuint64_t)out_c, (cuuint64_t)d.out_w * out_c,
+                             d.groups > 1 ? (cuuint64_t)d.out_gs : (cuuint64_t)d.out_h * d.out_w * out_c};
+        cuuint32_t box[4] = {64, 128, 1, 1};
+        if (!encode_map(&mc, d.out, 4, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return cudaErrorInvalidValue;
+        return launch_halo<64, 4, 2, true>(ma, mb, mc, a, s);
+    }
+    if (f8 && staged) {
+        // staged outputs of E4M3 layers: codes (64-byte boxes, no swizzle) or bf16 (128-byte swizzle)
+        const cuuint64_t oe = o8 ? 1 : 2;
+        const CUtensorMapDataType odt = o8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        const CUtensorMapSwizzle osw = o8 ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B;
+        bool okc;
+        if (ps_stage) {
+            cuuint64_t dims[5] = {(cuuint64_t)Cq, 2, (cuuint64_t)Wo, 2, (cuuint64_t)Ho * d.groups};
+            cuuint64_t str[4] = {Cq * oe, 2 * Cq * oe, 2ull * Wo * Cq * oe, 4ull * Wo * Cq * oe};
+            cuuint32_t box[5] = {64, 1, (cuuint32_t)a.TW, 1, (cuuint32_t)a.TH};
+            okc = encode_map(&mc, d.out, 5, dims, str, box, odt, osw);
+        } else {
+            const int Hd = d.out_h < Ho ? d.out_h : Ho, Wd = d.out_w < Wo ? d.out_w : Wo;
+            cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
+            cuuint64_t str[3] = {out_c * oe, (cuuint64_t)d.out_w * out_c * oe,
+                                 d.groups > 1 ? (cuuint64_t)d.out_gs * oe : (cuuint64_t)d.out_h * d.out_w * out_c * oe};
+            cuuint32_t box[4] = {64, (cuuint32_t)a.TW, (cuuint32_t)a.TH, 1};
+            okc = encode_map(&mc, d.out, 4, dims, str, box, odt, osw);
+        }
+        if (!okc) return cudaErrorInvalidValue;
+        if (!o8) return BN == 256 ? launch_bn<256, 5, true, OP_E4M3>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
+        switch (BN) {
+            case 64: return launch_bn<64, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
+            case 128: return launch_bn<128, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
+            case 192: return launch_bn<192, 7, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
+            default: return launch_bn<256, 6, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
+        }
+    }
     if (f8) {
         if (d.mode != OUT_NHWC && !(d.mode == OUT_PS && d.ps_major)) return cudaErrorInvalidValue;
         switch (BN) {

@@ -292,8 +292,9 @@ bool encode_frames_map(void* map, const void* frames, int N, int H, int row_byte
 // sel: 0 = the kernel the chunk path picks (TMA windows where first_layer_tma_ok), 1 = the register-staged
 // kernel, 2 = the TMA kernel (cudaErrorInvalidValue where first_layer_tma_ok is false)
 bool first_layer_tma_ok(int fmt, int W, const void* frames);
+// out: bf16 NHWC [Ho][Wo][64], or E4M3 codes of value x out_inv when out_inv != 0
 cudaError_t launch_first_layer(const uint8_t* frames, int fmt, int N, int H, int W, int Ho, int Wo, const void* wimg,
-                               const float* bias, __nv_bfloat16* out, int* err, cudaStream_t s, int sel = 0);
+                               const float* bias, void* out, float out_inv, int* err, cudaStream_t s, int sel = 0);
 // colour interface, output side (color.cu): x^ float [N][H][W][3] -> the caller's format (fmt 1..3), float
 // or uint8; frame_bytes = bytes of one frame in format fmt
 size_t frame_bytes(int fmt, int W, int H);
