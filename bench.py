@@ -357,7 +357,7 @@ def entropy_sweep(U, dev, lanes=(1024, 4096, 16384, 65536), n=240 * 135 * 256, r
 # DRAM bytes per 1080p launch from one ncu capture of the SAME kernel build (dram__bytes_read.sum +
 # dram__bytes_write.sum on the 960x544 chunk, scaled by the 4x pixel count).  An entry must be removed
 # when its kernel changes.
-NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.873536e6 + 73.990400e6), "dec.U3": 4 * (138.866688e6 + 6.584832e6)}
+NCU_TRAFFIC_1080P = {"dec.U2": 4 * (35.841536e6 + 74.318080e6), "dec.U3": 4 * (138.866688e6 + 6.584832e6)}
 
 SERVING_MIX = [((854, 480), 0.40), ((1280, 720), 0.30), ((1920, 1080), 0.25), ((3840, 2160), 0.05)]
 

@@ -507,6 +507,11 @@ const char* ufvc_server_last_error(const ufvc_server* srv);
  * next ENCODE when the server decodes the stream: a DECODE whose bit-stream is not the chunk after the
  * last one the stream's decoder decoded finishes with UFVC_ERR_ARG (nothing runs, both contexts unchanged). */
 ufvc_status ufvc_server_set_temporal_context(ufvc_server* srv, const float* weights, size_t n_weights);
+/* An FP8 server's activation scales (as ufvc_calibrate_fp8 on the server's own context, synchronous), set
+ * before the first stream is opened (UFVC_ERR_ARG afterwards); until then an FP8 server's requests finish
+ * with UFVC_ERR_ARG. */
+ufvc_status ufvc_server_calibrate_fp8(ufvc_server* srv, const uint8_t* d_frames, int n_frames, int width, int height,
+                                      int qp);
 ufvc_status ufvc_server_set_progressive_means(ufvc_server* srv, const float* weights, size_t n_weights);
 
 #ifdef __cplusplus

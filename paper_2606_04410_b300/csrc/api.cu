@@ -821,6 +821,8 @@ ufvc_ctx* ufvc::ctx_clone_shared(const ufvc_ctx* base) {
     c->d_dec = base->d_dec;
     c->table_spin = base->table_spin;
     c->conv_pairs = base->conv_pairs;
+    c->fp8_ready = base->fp8_ready;  // the calibration as it stands (the layers' scales are shared)
+    for (int t = 0; t < T_NT; ++t) c->act_scale[t] = base->act_scale[t];
     c->d_thr = base->d_thr;
     c->d_qstep = base->d_qstep;
     c->d_qinv = base->d_qinv;

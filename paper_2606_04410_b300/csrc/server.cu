@@ -655,6 +655,15 @@ extern "C" ufvc_status ufvc_server_set_temporal_context(ufvc_server* S, const fl
     });
 }
 
+extern "C" ufvc_status ufvc_server_calibrate_fp8(ufvc_server* S, const uint8_t* d_frames, int n_frames, int width,
+                                                 int height, int qp) {
+    return server_configure(S, "server_calibrate_fp8", [&] {
+        const ufvc_status st = ufvc_calibrate_fp8(S->base, d_frames, n_frames, width, height, qp, nullptr);
+        if (st == UFVC_OK) return ufvc_sync_status(S->base, nullptr);
+        return st;
+    });
+}
+
 extern "C" ufvc_status ufvc_server_set_progressive_means(ufvc_server* S, const float* weights, size_t n_weights) {
     return server_configure(S, "server_set_progressive_means",
                             [&] { return ufvc_set_progressive_means(S->base, weights, n_weights); });

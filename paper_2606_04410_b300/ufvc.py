@@ -37,7 +37,7 @@ EXPORTS = [
     "ufvc_get_fp8_scales", "ufvc_mean_weight_count", "ufvc_set_progressive_means", "ufvc_progressive_means",
     "ufvc_frame_bytes", "ufvc_set_color_format", "ufvc_temporal_weight_count", "ufvc_set_temporal_context",
     "ufvc_context_bytes", "ufvc_encode_chunk_tc", "ufvc_decode_chunk_tc", "ufvc_encode_stages_tc",
-    "ufvc_server_set_temporal_context", "ufvc_server_set_progressive_means", "ufvc_pipe_create",
+    "ufvc_server_set_temporal_context", "ufvc_server_calibrate_fp8", "ufvc_server_set_progressive_means", "ufvc_pipe_create",
     "ufvc_pipe_submit", "ufvc_pipe_wait", "ufvc_pipe_destroy", "ufvc_first_layer",
     "ufvc_set_table_wait_limit", "ufvc_set_conv_pairs", "ufvc_encode_chunks", "ufvc_decode_chunks",
 ]
@@ -113,6 +113,7 @@ _sigs = {
     "ufvc_temporal_weight_count": (_sz, [_i, _i]),
     "ufvc_set_temporal_context": (_i, [_vp, _vp, _sz]),
     "ufvc_server_set_temporal_context": (_i, [_vp, _vp, _sz]),
+    "ufvc_server_calibrate_fp8": (_i, [_vp, _vp, _i, _i, _i, _i]),
     "ufvc_server_set_progressive_means": (_i, [_vp, _vp, _sz]),
     "ufvc_pipe_create": (_i, [_vp, _i, C.POINTER(_vp)]),
     "ufvc_pipe_submit": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, C.POINTER(C.c_longlong)]),
@@ -539,6 +540,12 @@ class Server:
         if mean_weights is not None:
             mw = np.ascontiguousarray(mean_weights, np.float32)
             self._check(lib.ufvc_server_set_progressive_means(self.h, _ptr(mw), mw.size), "server_set_progressive_means")
+
+    def calibrate_fp8(self, frames: torch.Tensor, qp: int = 32, width: int | None = None, height: int | None = None):
+        """FP8 servers: activation scales from the FP32 path on this chunk (before the first stream)."""
+        H = height if height is not None else frames.shape[1]
+        W = width if width is not None else frames.shape[2]
+        self._check(lib.ufvc_server_calibrate_fp8(self.h, _ptr(frames), self.N, W, H, qp), "server_calibrate_fp8")
 
     def close(self):
         if self.h:

@@ -26,13 +26,18 @@ def _sync_round_trip(u, codec, frames, W, H):
     return bits, np.asarray(out).reshape(-1)
 
 
-@pytest.mark.parametrize("N,H,W,K,depth", [(8, 128, 160, 4096, 2), (2, 72, 120, 256, 3)])
-def test_pipe_equals_sync_calls(N, H, W, K, depth):
+@pytest.mark.parametrize("N,H,W,K,depth,prec", [(8, 128, 160, 4096, 2, "bf16"), (2, 72, 120, 256, 3, "bf16"),
+                                                  (8, 72, 160, 512, 2, "fp8")])
+def test_pipe_equals_sync_calls(N, H, W, K, depth, prec):
     u = U()
     blob = synthetic.draw_weights(1, N, seed=3)
-    codec = u.Codec(1, N, K, blob, "bf16")
-    ref = u.Codec(1, N, K, blob, "bf16")
+    codec = u.Codec(1, N, K, blob, prec)
+    ref = u.Codec(1, N, K, blob, prec)
     chunks = [synthetic.moving_texture(50 + i, N, H, W, max_step=16, refresh=0.1) for i in range(5)]
+    if prec == "fp8":  # the pipe's slots take the context's calibration as it stands when it is created
+        cal = torch.from_numpy(chunks[0]).cuda()
+        codec.calibrate_fp8(cal, 32)
+        ref.calibrate_fp8(cal, 32)
     pipe = u.Pipe(codec, depth)
     cap = codec.max_bitstream_bytes(W, H)
     h_in = [torch.from_numpy(c).pin_memory() for c in chunks]

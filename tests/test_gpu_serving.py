@@ -137,6 +137,43 @@ def test_server_batches_same_shape_requests():
     srv.close()
 
 
+def test_fp8_server_matches_single_context():
+    """An FP8 server calibrated on a chunk codes like a single FP8 context calibrated on the same chunk
+    (the slots share the server's scales): byte-identical bit-streams and frames; uncalibrated, its
+    requests are refused."""
+    u = U()
+    blob = synthetic.draw_weights(1, N, seed=6)
+    W, H = SIZES[2]
+    frames = [_frames(130 + i, W, H) for i in range(3)]
+    c = u.Codec(1, N, K, blob, "fp8")
+    c.calibrate_fp8(frames[0], QP)
+    refs = []
+    for fr in frames:
+        bits, nb = c.encode_chunk(fr, QP)
+        n = int(nb.item())
+        refs.append((bits[:n].cpu().numpy().tobytes(), c.decode_chunk(bits, n, W, H).cpu().clone()))
+    assert c.sync_status() == 0
+    raw = u.Server(1, N, K, blob, "fp8", max_slots=1)
+    sid = raw.open_stream(W, H, QP)
+    raw.streams[sid]["frames_in"].copy_(frames[0])
+    torch.cuda.synchronize()
+    assert raw.wait(raw.submit(sid, u.UFVC_OP_ENCODE), 120000.0)["status"] == u.UFVC_ERR_ARG
+    raw.close()
+    srv = u.Server(1, N, K, blob, "fp8", max_slots=2)
+    srv.calibrate_fp8(frames[0], QP)
+    sids = [srv.open_stream(W, H, QP) for _ in frames]
+    for sid, fr in zip(sids, frames):
+        srv.streams[sid]["frames_in"].copy_(fr)
+    torch.cuda.synchronize()
+    reqs = [(sid, op) for op in (u.UFVC_OP_ENCODE, u.UFVC_OP_DECODE) for sid in sids]
+    assert all(srv.wait(t, 120000.0)["status"] == 0 for t in srv.submit_many(reqs))
+    for sid, ref in zip(sids, refs):
+        b = srv.streams[sid]
+        assert b["bits"][:int(b["nbytes"].item())].cpu().numpy().tobytes() == ref[0]
+        assert torch.equal(b["frames_out"].cpu(), ref[1])
+    srv.close()
+
+
 def test_server_hbm_cap_releases_idle_slots_and_bounds_streams():
     u = U()
     blob = synthetic.draw_weights(1, N, seed=2)
