@@ -185,7 +185,13 @@ __device__ __forceinline__ uint32_t enc_update(uint32_t x, const EncSym& q) {
 // STAGE: the lanes' words are staged in shared memory (after the tables) instead of the global rows; the
 // block copies them to their place either way.  A block codes J.lpb lanes (its first J.lpb threads); all
 // its threads copy.
-template <bool STAGE>
+// HELP (one warp of lanes per block, staged, the latency-bound case): warp 1 serves the coding warp
+// through a shared-memory ring of four groups of 16 steps: it loads each element's symbol and scale index,
+// checks them and writes the table word ((freq << 16) | cum) and the reciprocal of the frequency, so the
+// coding warp's step is the state chain and the store of its renormalisation word.  Hand-over through
+// mbarriers with bounded waits.
+constexpr int kEncRingBytes = 4 * kPF * 32 * 8;
+template <bool STAGE, bool HELP = false>
 __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, const uint32_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum, then the staged words
     __shared__ uint64_t bar;
@@ -217,9 +223,114 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
         uint16_t* row = STAGE ? stage + (size_t)(live ? threadIdx.x : 0) * S.cap_lane
                               : S.rows + (size_t)(live ? lane : 0) * S.cap_lane;
         uint32_t words = 0;
+        // HELP: whole groups of 16 steps below the lanes' common element count, coded from the ring
+        uint32_t ngr = 0, cmin = 0;
+        int hx_wp = S.cap_lane;
+        uint32_t hx_x = kRansL, hx_bad = 0;
+        if constexpr (HELP) {
+            static_assert(STAGE, "serving warp: staged words");
+            __shared__ uint32_t ngr_sh, cmin_sh;
+            const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+            uint2* ring = reinterpret_cast<uint2*>(reinterpret_cast<uint8_t*>(stage) + J.stage_bytes);
+            uint64_t* hb = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(ring) + kEncRingBytes);
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < 8; ++k) ptx::mbar_init(&hb[k], 1);  // full[4], empty[4]
+                ptx::fence_mbar_init();
+            }
+            if (w == 0) {
+                const uint32_t cm = __reduce_min_sync(0xffffffffu, live ? cnt : 0u);
+                const bool f = S.idx_period == 0 && __all_sync(0xffffffffu, live);
+                if (l == 0) {
+                    cmin_sh = cm;
+                    ngr_sh = f ? cm / kPF : 0u;
+                }
+            }
+            __syncthreads();
+            ngr = ngr_sh;
+            cmin = cmin_sh;
+            auto hwait = [&](uint64_t* b, uint32_t par) {
+                const long long t0 = clock64();
+                while (!ptx::mbar_try_wait(b, par))
+                    if (clock64() - t0 > kSpinDefault) {
+                        set_status(J.status, UFVC_ERR_TIMEOUT);
+                        return false;
+                    }
+                return true;
+            };
+            const int K = S.K;
+            const size_t lane0 = (size_t)bs * T;
+            if (w == 1) {
+                // ---- producer: group g holds the elements m = cmin - 1 - 16 g - u of the warp's lanes
+                uint32_t bad = 0;
+                for (uint32_t g = 0; g < ngr; ++g) {
+                    const int b = (int)(g & 3);
+                    const uint32_t use = g >> 2;
+                    uint32_t tv[kPF];
+                    int sv[kPF];
+#pragma unroll
+                    for (int u = 0; u < kPF; ++u) {
+                        const size_t e = lane0 + l + (size_t)(cmin - 1 - kPF * g - u) * K;
+                        tv[u] = __ldg(S.idx + e);
+                        sv[u] = __ldg(S.sym + e);
+                    }
+                    if (use > 0 && !__all_sync(0xffffffffu, hwait(&hb[4 + b], (use - 1) & 1))) break;
+#pragma unroll
+                    for (int u = 0; u < kPF; ++u) {
+                        const uint32_t v = (uint32_t)(sv[u] + kRmax);
+                        const bool ok = tv[u] < (uint32_t)kBins && v < (uint32_t)kNsym;
+                        bad |= !ok;
+                        const uint32_t ent = tab[ok ? tv[u] * kNsym + v : kRmax];
+                        ring[(b * kPF + u) * 32 + l] = make_uint2(ent, __float_as_uint(__frcp_rn((float)(ent >> 16))));
+                    }
+                    __syncwarp();
+                    if (l == 0) ptx::mbar_arrive(&hb[b]);
+                }
+                if (bad) set_status(J.status, UFVC_ERR_ARG);
+            } else if (w == 0 && ngr > 0) {
+                // ---- coding warp: first the top element of the lanes that have one more, then the groups
+                uint16_t* hrow = stage + (size_t)threadIdx.x * S.cap_lane;
+                if (cnt > cmin) {
+                    const size_t e = lane0 + l + (size_t)cmin * K;
+                    const uint32_t tt = __ldg(S.idx + e), v = (uint32_t)(__ldg(S.sym + e) + kRmax);
+                    const bool ok = tt < (uint32_t)kBins && v < (uint32_t)kNsym;
+                    hx_bad |= !ok;
+                    const EncSym q = enc_sym(tab[ok ? tt * kNsym + v : kRmax]);
+                    const bool o = hx_x >= (q.f << 16);
+                    if (o) hrow[--hx_wp] = (uint16_t)hx_x;
+                    hx_x = o ? hx_x >> 16 : hx_x;
+                    hx_x = enc_update(hx_x, q);
+                }
+                for (uint32_t g = 0; g < ngr; ++g) {
+                    const int b = (int)(g & 3);
+                    const uint32_t use = g >> 2;
+                    if (!__all_sync(0xffffffffu, hwait(&hb[b], use & 1))) break;
+                    uint2 rv[kPF];
+#pragma unroll
+                    for (int u = 0; u < kPF; ++u) rv[u] = ring[(b * kPF + u) * 32 + l];
+#pragma unroll
+                    for (int u = 0; u < kPF; ++u) {
+                        EncSym q;
+                        q.f = rv[u].x >> 16;
+                        q.c = rv[u].x & 0xFFFFu;
+                        q.rcp = __uint_as_float(rv[u].y);
+                        const bool o = hx_x >= (q.f << 16);
+                        if (o) hrow[--hx_wp] = (uint16_t)hx_x;
+                        hx_x = o ? hx_x >> 16 : hx_x;
+                        hx_x = enc_update(hx_x, q);
+                    }
+                    __syncwarp();
+                    if (l == 0) ptx::mbar_arrive(&hb[4 + b]);
+                }
+            }
+        }
         if (live) {
             int wp = S.cap_lane;
             uint32_t x = kRansL, bad = 0;
+            if (HELP && ngr > 0) {  // continue below the ring's groups
+                wp = hx_wp;
+                x = hx_x;
+                bad = hx_bad;
+            }
             const int K = S.K, per = S.idx_period;
             // per-channel tables: index of element lane + m K is (lane + m K) mod per, stepped down by K mod per
             const int kmod = per ? K % per : 0;
@@ -272,7 +383,8 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
                     emit = 0;
                 }
             };
-            const int top = (int)cnt - 1;
+            const int top = (HELP && ngr > 0) ? (int)(cmin - kPF * ngr) - 1 : (int)cnt - 1;
+            if (HELP && ngr > 0) fe = (uint32_t)lane + (top > 0 ? (uint32_t)top * (uint32_t)K : 0u);
             fetch(top, tc, vc);
             int mtop = top;
             for (; mtop >= kPF - 1; mtop -= kPF) {  // whole groups of kPF symbols
@@ -431,7 +543,20 @@ static int enc_threads(const RansEncJob& j, int sms) {
 cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cudaStream_t s) {
     if (j.nsec < 1 || j.nsec > kRansMaxEncSec || j.nstreams < 1 || j.nstreams > kRansMaxStreams)
         return cudaErrorInvalidValue;
-    const int T = enc_threads(j, sm_count());
+    int T = enc_threads(j, sm_count());
+    // few lanes per SM (the latency-bound case): one warp of lanes per block with its serving warp, when
+    // the blocks stay within the control block and the words, the ring and the tables fit
+    bool help = false;
+    if (T <= 64) {
+        int b32 = 0, cap32 = 0;
+        for (int i = 0; i < j.nsec; ++i) {
+            b32 += (j.s[i].K + 31) / 32;
+            cap32 = j.s[i].cap_lane > cap32 ? j.s[i].cap_lane : cap32;
+        }
+        const size_t st32 = ((size_t)32 * cap32 * 2 + 15) & ~(size_t)15;
+        help = b32 <= kRansMaxBlocks && kEncTabBytes + st32 + kEncRingBytes + 64 <= (size_t)kEncSmemMax;
+        if (help) T = 32;
+    }
     j.lpb = T;
     j.grid = 0;
     int cap = 0;
@@ -453,11 +578,17 @@ cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cud
     const size_t stage = ((size_t)T * cap * 2 + 15) & ~(size_t)15;
     const bool staged = kEncTabBytes + stage <= (size_t)kEncSmemMax;
     const int BT = staged ? (T < 128 ? 128 : T) : 512;
+    j.stage_bytes = (int)stage;
     // the shared memory holds the tables (then the lanes' offsets and counts, 12 bytes each) and the stage
-    const int smem = (int)(kEncTabBytes + (staged ? stage : 0));
-    const void* kern = staged ? (const void*)rans_encode_kernel<true> : (const void*)rans_encode_kernel<false>;
+    // (HELP: then the ring and its eight barriers)
+    const int smem = (int)(kEncTabBytes + (staged ? stage : 0) + (help ? kEncRingBytes + 64 : 0));
+    const void* kern = help     ? (const void*)rans_encode_kernel<true, true>
+                       : staged ? (const void*)rans_encode_kernel<true>
+                                : (const void*)rans_encode_kernel<false>;
     cudaError_t e = smem_optin(kern, smem);
     if (e != cudaSuccess) return e;
+    if (help)
+        return launch_pdl(rans_encode_kernel<true, true>, dim3(j.grid), dim3(BT), (size_t)smem, s, j, packed_tables);
     if (staged) return launch_pdl(rans_encode_kernel<true>, dim3(j.grid), dim3(BT), (size_t)smem, s, j, packed_tables);
     return launch_pdl(rans_encode_kernel<false>, dim3(j.grid), dim3(BT), (size_t)smem, s, j, packed_tables);
 }

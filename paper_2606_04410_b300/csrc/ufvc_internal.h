@@ -359,6 +359,7 @@ struct RansEncJob {
     RansEncStream st[kRansMaxStreams];
     int nstreams;
     int grid, lpb;            // set by the launcher: blocks, lanes per block
+    int stage_bytes;          // set by the launcher: the staged words' bytes in shared memory (16-aligned)
     RansCtl* ctl;
     int* status;
     long long spin;           // bound on the table-copy wait in clocks (0: about 2 s)
