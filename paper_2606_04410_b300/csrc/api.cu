@@ -127,6 +127,7 @@ struct ufvc_ctx {
     int* d_status = nullptr;
     long long table_spin = 0;  // bound on the entropy kernels' table-copy wait (clocks; 0: about 2 s)
     int conv_pairs = 1;        // the staged BN = 256 tensor-core layers run on CTA pairs
+    int conv_launches = 0;     // kernels launched by conv() (the profiler's launch counts)
     LayerW enc[L_NENC];
     LayerW dec[D_NDEC];
     // BF16 with 3N <= 32: A1 as a 2x2 stride-1 layer on the space-to-depth input (the 3x3 stride-2
@@ -878,6 +879,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
             ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
             return UFVC_ERR_CUDA;
         }
+        ++ctx->conv_launches;
         return UFVC_OK;
     }
     d.Cin = L.cin_p;
@@ -894,7 +896,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
         d.ws = ws->p;
         d.ws_cap = ws->cap;
     }
-    CK(launch_conv_simt(d, s));
+    CK(launch_conv_simt(d, s, &ctx->conv_launches));
     return UFVC_OK;
 }
 
@@ -943,6 +945,7 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
                                        float* pc_tmp = nullptr, const EntParams* ent = nullptr) {
     const Arch& a = ctx->arch;
     prof_begin(ctx, "hyper_synthesis", s);
+    const int nl0 = ctx->conv_launches;
     launch_i16_to_f32(zhat, p->nz, zf, s);
     RUN(conv(ctx, ctx->enc[L_S1], zf, p->Hz, p->Wz, 1, 1, OUT_PS, s1, 2 * p->Hz, 2 * p->Wz, s));
     RUN(conv(ctx, ctx->enc[L_S2], s1, 2 * p->Hz, 2 * p->Wz, 1, 1, OUT_PS, s2, p->Hy, p->Wy, s));  // crop
@@ -953,7 +956,8 @@ static ufvc_status run_hyper_synthesis(ufvc_ctx* ctx, Plan* p, const int16_t* zh
     }
     RUN(conv(ctx, ctx->enc[L_S3], s2, p->Hy, p->Wy, 1, 0, OUT_NHWC, mu, p->Hy, p->Wy, s, nullptr, ls, a.cy, 0, 0, 0, 1,
              false, ent));
-    prof_end(ctx, s, cin ? 6 : 4);
+    // the conversion (+ the context addition) and every kernel of the layers, split-K reductions included
+    prof_end(ctx, s, 1 + (cin ? 1 : 0) + (ctx->conv_launches - nl0));
     return UFVC_OK;
 }
 

@@ -599,7 +599,9 @@ static unsigned reduce_blocks(const ConvDesc& d, int M) {  // one thread per fou
     return (unsigned)((total4 + 255) / 256 < 4096 ? (total4 + 255) / 256 : 4096);
 }
 
-cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
+cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st, int* nl) {
+    int nl_ = 0;
+    if (!nl) nl = &nl_;
     ConvDesc d = d_in;
     d.vec4 = d.mode == OUT_NHWC && d.Cout % 4 == 0 && d.split % 4 == 0 && d.out_gs % 4 == 0 && aligned16(d.out) &&
              (!d.split || (aligned16(d.out2) && (d.Cout - d.split) % 4 == 0)) &&
@@ -621,48 +623,49 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st) {
         ConvDesc u = d_in;
         u.ent_idx = nullptr;
         u.ent_keep_ls = 1;
-        cudaError_t e = launch_conv_simt(u, st);
+        cudaError_t e = launch_conv_simt(u, st, nl);
         if (e != cudaSuccess) return e;
+        ++*nl;
         launch_quantize(d.ent_y, static_cast<const float*>(d.out), d.out2, (size_t)M * d.split, d.ent_thr, d.ent_qinv,
                         d.ent_qp_dev, d.ent_qp, d.ent_y ? d.ent_rhat : nullptr, d.ent_idx, st);
         return cudaGetLastError();
     }
     if (kind == 0) {
         dim3 grid((M + 127) / 128, (d.Cout + 15) / 16, d.groups);
-        (void)launch_pdl(conv_simt_kernel<128, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
+        ++*nl, (void)launch_pdl(conv_simt_kernel<128, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
     } else if (kind == 1) {
         dim3 grid((M + 127) / 128, (d.Cout + 63) / 64, d.groups);
-        (void)launch_pdl(conv_simt_kernel<128, 64>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
+        ++*nl, (void)launch_pdl(conv_simt_kernel<128, 64>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo);
     } else if (kind == 3) {
         dim3 grid((M + 63) / 64, d.Cout / 128, d.groups * KS);
         if (KS > 1) {
             if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;
-            (void)launch_pdl(conv_simt88_kernel<true>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            ++*nl, (void)launch_pdl(conv_simt88_kernel<true>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
             if (fuse_ent) {
                 const int n4 = M * (d.split / 4);
                 const unsigned blocks = (unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);
-                (void)launch_pdl(conv_simt_reduce_entropy_kernel, dim3(blocks), dim3(256), (size_t)(0), st, d, M, KS,
+                ++*nl, (void)launch_pdl(conv_simt_reduce_entropy_kernel, dim3(blocks), dim3(256), (size_t)(0), st, d, M, KS,
                                  d.ws);
                 return cudaGetLastError();
             }
-            (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            ++*nl, (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
         } else {
-            (void)launch_pdl(conv_simt88_kernel<false>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
+            ++*nl, (void)launch_pdl(conv_simt88_kernel<false>, dim3(grid), dim3(128), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
         }
     } else if (KS > 1) {
         if (!d.ws || d.ws_cap < conv_simt_workspace(d)) return cudaErrorInvalidValue;  // caller's workspace
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups * KS);
         if (d.Cin % 32 == 0)
-            (void)launch_pdl(conv_simt64_kernel<true, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            ++*nl, (void)launch_pdl(conv_simt64_kernel<true, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
         else
-            (void)launch_pdl(conv_simt64_kernel<true, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
-        (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+            ++*nl, (void)launch_pdl(conv_simt64_kernel<true, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
+        ++*nl, (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho, Wo, KS, d.ws);
     } else {
         dim3 grid((M + 63) / 64, (d.Cout + 63) / 64, d.groups);
         if (d.Cin % 32 == 0)
-            (void)launch_pdl(conv_simt64_kernel<false, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
+            ++*nl, (void)launch_pdl(conv_simt64_kernel<false, 32>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
         else
-            (void)launch_pdl(conv_simt64_kernel<false, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
+            ++*nl, (void)launch_pdl(conv_simt64_kernel<false, 16>, dim3(grid), dim3(256), (size_t)(0), st, d, Ho, Wo, 1, nullptr);
     }
     return cudaGetLastError();
 }

@@ -272,7 +272,9 @@ int ctx_color(const ufvc_ctx* ctx);   // the context's colour format (ufvc_color
 bool ctx_temporal(const ufvc_ctx* ctx);  // the context carries a temporal chunk context (C_i)
 size_t ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H);
 
-cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s);
+// nl (optional): incremented by the number of kernels launched (the layer, its split-K reduction, the
+// quantiser where the entropy parameters are not formed in the reduction)
+cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s, int* nl = nullptr);
 // floats of split-K workspace the SIMT launch of d uses (0: none)
 size_t conv_simt_workspace(const ConvDesc& d);
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
