@@ -155,13 +155,15 @@ ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bits, size_t 
                                    int n_frames, int width, int height, void* stream);
 
 /* ---- pipelined host-buffer round trips (streaming callers) ----
- * A pipeline of `depth` slots (1..16), each a context sharing ctx's weights and tables (own plans,
- * device buffers and non-blocking CUDA stream); ctx must outlive it and stay unchanged meanwhile.
- * ufvc_pipe_submit enqueues one chunk's round trip on slot ticket % depth and returns at once:
- * h_frames (ctx's colour format) to the device, ufvc_encode_chunk, the whole bit-stream buffer
- * (`capacity` bytes, at least ufvc_max_bitstream_bytes) to h_bits, that host copy back to the device,
- * ufvc_decode_chunk_dev of it, and the decoded frames to h_out (skipped when h_out is NULL).  One
- * slot's copies overlap the others' kernels.  Host buffers must stay valid and unchanged until the
+ * A pipeline of `depth` slots (1..16) of device buffers, one context sharing ctx's weights and tables
+ * (own plans and status word), one compute stream and four copy streams; ctx must outlive it and stay
+ * unchanged meanwhile.  ufvc_pipe_submit enqueues one chunk's round trip on slot ticket % depth and
+ * returns at once: h_frames (ctx's colour format) to the device, ufvc_encode_chunk, the whole bit-stream
+ * buffer (`capacity` bytes, at least ufvc_max_bitstream_bytes) to h_bits, that host copy back to the
+ * device, ufvc_decode_chunk_dev of it, and the decoded frames to h_out (skipped when h_out is NULL).
+ * The kernels run one chunk at a time on the compute stream; a ticket's decode is enqueued after the
+ * next ticket's encode (or by its wait), so the copies of the other tickets and the bit-stream's trip
+ * through the host overlap the kernels.  Host buffers must stay valid and unchanged until the
  * ticket has been waited for; page-locked host memory makes the copies asynchronous.  *ticket gets
  * consecutive numbers from 0.  UFVC_ERR_ARG if ticket t - depth has not been waited for yet,
  * UFVC_ERR_CAPACITY if capacity is too small.  ufvc_pipe_wait blocks until the ticket's round trip has

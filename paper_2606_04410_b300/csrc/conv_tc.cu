@@ -298,10 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     static_assert(MT == 1 || (MT == 2 && !F8 && OP == OP_BF16), "two sub-tiles: BF16 operands");
-    static_assert(!PAIR || (MT == 1 && OP == OP_BF16 && !KM && BN % 32 == 0), "CTA pairs: BF16, one sub-tile each");
+    static_assert(!PAIR || (OP == OP_BF16 && !KM && BN % 32 == 0), "CTA pairs: BF16");
     constexpr int A_BYTES = 128 * MT * ROWB;
     constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROWB;  // this CTA's weight rows of a stage
-    constexpr int SUBS = PAIR ? 2 : MT;  // 128-pixel sub-tiles of a tile
+    // 128-pixel sub-tiles of a tile; a pair's CTA r holds sub-tiles r MT .. r MT + MT - 1, and the pair's
+    // MMA h joins sub-tile h of both CTAs (M = 256)
+    constexpr int SUBS = PAIR ? 2 * MT : MT;
     constexpr int EG = MT == 2 ? 1 : epi_groups(BN);  // epilogue groups (tiles drained concurrently)
     constexpr int WPQ = 4 / EG;         // warps per TMEM lane quarter in a group
     constexpr int NACC = 2 * EG;        // TMEM accumulators
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = cid; t < p.total_tiles && ok; t += ncl) {
                 const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
-                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (int)crank * p.TH, w0 = (mt % p.tiles_w) * p.TW;
+                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (int)crank * MT * p.TH, w0 = (mt % p.tiles_w) * p.TW;
                 const int ag = p.a_grouped ? g : 0;
                 for (int ks = 0; ks < p.ksteps; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;  // all-zero weights: no stage
@@ -470,8 +472,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else if constexpr (PAIR) {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // M = 256: rows 0..127 from this CTA, 128..255 from the odd one
-                            ptx::mma_f16_pair(d, ptx::sdesc_sw128(a0 + kk * 32), ptx::sdesc_sw128(b0 + kk * 32), idesc,
-                                              !first || kk != 0);
+#pragma unroll
+                            for (int h = 0; h < MT; ++h)  // sub-tile h of both CTAs
+                                ptx::mma_f16_pair(d + h * BN, ptx::sdesc_sw128(a0 + h * 16384 + kk * 32),
+                                                  ptx::sdesc_sw128(b0 + kk * 32), idesc, !first || kk != 0);
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk)  // 4 x K=16 BF16 per 128-byte row
@@ -515,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int w0 = (mt % p.tiles_w) * p.TW;
 #pragma unroll 1
             for (int hs = 0; hs < MT; ++hs, ++k) {
-                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (PAIR ? (int)crank : hs) * p.TH;
+                const int h0 = (mt / p.tiles_w) * p.TH * SUBS + ((PAIR ? (int)crank * MT : 0) + hs) * p.TH;
                 const int oh = h0 + row / p.TW, ow = w0 + row % p.TW;
                 const bool valid = oh < p.Ho && ow < p.Wo;
                 const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + acc * ACOLS + hs * BN;
@@ -1210,12 +1214,13 @@ bool encode_frames_map(void* map, const void* frames, int N, int H, int row_byte
 }
 
 // Output tile TW x TH = 128 pixels with the least padding; with th_divides, TH must divide Ho.
-static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false) {
+// rm: sub-tiles stacked vertically in a tile (two sub-tiles, SM pairs), so a tile covers rm * TH rows
+static void pick_tile(int Ho, int Wo, int* TW, int* TH, bool th_divides = false, int rm = 1) {
     long long best = -1;
     for (int tw = 128; tw >= 8; tw >>= 1) {
         const int th = 128 / tw;
         if (th_divides && Ho % th != 0) continue;
-        const long long cost = (long long)((Wo + tw - 1) / tw) * tw * ((Ho + th - 1) / th) * th;
+        const long long cost = (long long)((Wo + tw - 1) / tw) * tw * ((Ho + th * rm - 1) / (th * rm)) * th * rm;
         if (best < 0 || cost < best) { best = cost; *TW = tw; *TH = th; }
     }
 }
@@ -1380,8 +1385,12 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.kmask == 0 && pairs >= 2 * 148) ? 2 : 1;
     // CTA pairs (one M = 256 MMA over two SMs, each loading half of the weights): the staged BN = 256
     // layers (the decoders' pixel-shuffle layers D0, U1, U2)
-    const bool pair = d.pairs && !f8 && !c32 && !halo && staged && BN == 256 && d.kmask == 0;
-    const int SUB = (MT == 2 || pair) ? 2 : 1;  // 128-pixel sub-tiles per tile
+    // (and the two-sub-tile 128-output layers with at least four waves of pair tiles: each SM then lands its
+    // two 128-pixel A tiles and half of the weight rows per stage, 40 KB instead of 48 KB)
+    const bool pair = d.pairs && !f8 && !c32 && !halo && staged && d.kmask == 0 &&
+                      (BN == 256 || (BN == 128 && MT == 2 && pairs >= 4 * 148));
+    const int SUB = pair ? 2 * MT : MT;  // 128-pixel sub-tiles per tile
+    if (SUB > 1) pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1, SUB);  // the stack's rows fit Ho
     a.Ho = Ho; a.Wo = Wo;
     a.tiles_w = (Wo + a.TW - 1) / a.TW;
     a.tiles_h = (Ho + a.TH * SUB - 1) / (a.TH * SUB);
@@ -1532,7 +1541,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         switch (BN) {
             case 64: return a.kmask != ~0ull ? launch_bn<64, 6, true, OP_BF16, true>(ma, mb, mc, a, s)
                                              : launch_bn<64, 6, true>(ma, mb, mc, a, s);
-            case 128: return MT == 2 ? launch_bn<128, 3, true, OP_BF16, false, 2>(ma, mb, mc, a, s)
+            case 128: return MT == 2 ? (pair ? launch_bn<128, 4, true, OP_BF16, false, 2, true>(ma, mb, mc, a, s)
+                                             : launch_bn<128, 3, true, OP_BF16, false, 2>(ma, mb, mc, a, s))
                                      : launch_bn<128, 4, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 4, true>(ma, mb, mc, a, s);
             default: return pair ? launch_bn<256, 4, true, OP_BF16, false, 1, true>(ma, mb, mc, a, s)

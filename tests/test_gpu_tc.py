@@ -105,6 +105,36 @@ def test_pixel_shuffle_pairs_equal_single(layer, H, W, cin_pad):
     assert torch.equal(got[True], got[False])
 
 
+def test_r1_pairs_two_subtiles_equal_single():
+    """A 128-output layer large enough for SM pairs on top of two sub-tiles per CTA (each CTA of a pair holds
+    two stacked 128-pixel sub-tiles, each pair MMA joins sub-tile h of both CTAs): R1a at 544 x 480 (1020
+    two-sub-tile tiles).  Equal bit for bit to the one-SM two-sub-tile kernel, and within the float64 bound
+    on row bands at the top, middle and bottom."""
+    u = U()
+    blob = synthetic.draw_weights(1, 2, seed=3, bias_std=0.1)
+    H, W, layer = 544, 480, 12
+    _, co, k, ci = layer_table(1, 2)[layer]
+    rng = np.random.default_rng(7)
+    x = torch.from_numpy(rng.normal(size=(H, W, ci)).astype(np.float32)).to(torch.bfloat16).cuda()
+    got = {}
+    for pairs in (True, False):
+        codec = u.Codec(1, 2, 64, blob, "bf16")
+        codec.set_conv_pairs(pairs)
+        out = torch.zeros((H, W, co), dtype=torch.bfloat16, device="cuda")
+        codec.conv_layer(layer, x, 1, 1, 0, out)
+        assert codec.sync_status() == 0
+        got[pairs] = out.cpu()
+    assert torch.equal(got[True], got[False])
+    xd = x.double().cpu()
+    for r0, r1 in ((0, 6), (270, 276), (538, 544)):
+        # the band's input rows with one row of context on each side (or the image border): output rows
+        # r0 .. r1 - 1 of the slice's convolution are those of the whole layer
+        lo, hi = max(r0 - 1, 0), min(r1 + 1, H)
+        ref = ref_layer(blob, 1, 2, layer, xd[lo:hi], 1, 1, 0, hi - lo, W)[r0 - lo:r1 - lo]
+        err = (got[True][r0:r1].double() - ref).abs()
+        assert bool((err <= 8e-3 * ref.abs() + 2e-3 * float(ref.abs().max())).all()), (r0, float(err.max()))
+
+
 def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0), pairs=True):
     u = U()
     blob = synthetic.draw_weights(arch, N, seed=3, bias_std=0.1)
