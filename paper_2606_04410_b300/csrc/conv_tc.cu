@@ -892,6 +892,229 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ------------------------------------------------------------------------------------------------
+// Stride-1 3x3 layers with 64 bf16 inputs and 64 bf16 NHWC outputs (the decoders' R2) with the three
+// horizontal taps in the MMA's N dimension.  With A = input pixels and B = one tap's 64 x 64 weights
+// (the resident-weight kernel above) each MMA is M = 128, N = 64: 6 KB of operands read from shared
+// memory per 262 KFLOP, so the tensor cores wait on shared memory.  Here B for kernel row ky is the
+// 192 x 64 matrix of the three taps (kx, c) stacked, so one MMA of N = 192 per (ky, 16 channels)
+// computes, for every input pixel x of the strip,
+//     D[x][(kx, c)] = sum_ky sum_ci w[c][ky][kx][ci] in[oh + ky - 1][x][ci]
+// (12 MMAs per tile instead of 36, 10 KB of operands per 786 KFLOP), and the epilogue applies the
+// horizontal shift: out[oh][x][c] = D[x - 1][(0, c)] + D[x][(1, c)] + D[x + 1][(2, c)].  Accumulator
+// rows are pixels, i.e. TMEM lanes, so the neighbours are warp shuffles: warp quarter q holds input
+// pixels x0 + 30 q - 1 .. x0 + 30 q + 30 (one 32-pixel TMA box per quarter and input row, halos
+// overlapping) and its lanes 1..30 produce output pixels x0 + 30 q .. x0 + 30 q + 29, so a tile is a
+// strip of 120 output pixels of one row.  The resident weights keep the tap-major layout of the kernel
+// above (tap = 3 ky + kx, 64 rows each), so the three taps of one ky are 192 consecutive rows.
+// Two epilogue groups of eight warps (two column halves x four lane quarters) drain alternate tiles
+// from two accumulators of 192 columns; outputs go through a swizzled staging tile per group and a
+// TMA store of 120 pixels x 64 channels, which clips at the image edge.
+// ------------------------------------------------------------------------------------------------
+constexpr int kKxnStrip = 120;       // output pixels per tile
+constexpr int kKxnRowBytes = 16384;  // one input row of a tile: 4 boxes x 32 pixels x 128 B
+template <int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    conv_tc_kxn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
+    constexpr int A_BYTES = 3 * kKxnRowBytes;
+    constexpr int B_BYTES = 9 * 64 * 128;
+    constexpr int C_BYTES = 2 * 16384;  // two staging tiles of 120 x 128 B (16 KB slots)
+    constexpr uint32_t TMEM_COLS = 512;  // accumulators at columns 0 and 256, 192 columns each
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sB = smem;
+    uint8_t* sA = smem + B_BYTES;
+    uint8_t* sC = sA + STAGES * A_BYTES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sC + C_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* bfull = tempty + 2;
+    uint64_t* bfree = bfull + 1;
+    uint64_t* drain = bfree + 1;
+    uint64_t* cwritten = drain + 1;
+    uint64_t* cfree = cwritten + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
+    const float* bias_all = stage_bias(p, sbias);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            ptx::mbar_init(&tfull[a], 1);
+            ptx::mbar_init(&tempty[a], 32 * 8);
+            ptx::mbar_init(&cwritten[a], 32 * 8);
+            ptx::mbar_init(&cfree[a], 1);
+        }
+        ptx::mbar_init(bfull, 1);
+        ptx::mbar_init(bfree, 1);
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 1) ptx::tmem_alloc(tmem_slot, TMEM_COLS);
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmA);
+        ptx::prefetch_tmap(&tmB);
+        ptx::prefetch_tmap(&tmC);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    pdl_trigger();
+    pdl_wait();
+    // tile t = (g * Ho + oh) * tiles_w + strip; this CTA owns [t_begin, t_end)
+    const int t_begin = (int)((long long)p.total_tiles * blockIdx.x / gridDim.x);
+    const int t_end = (int)((long long)p.total_tiles * (blockIdx.x + 1) / gridDim.x);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0, cur_g = -1, nb = 0;
+            uint32_t bfree_par = 0, last_par[STAGES];
+            bool used[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
+            for (int t = t_begin; t < t_end; ++t, ++it) {
+                const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, g = r / p.Ho;
+                if (g != cur_g) {
+                    if (cur_g >= 0) {  // the MMAs that read the previous group's weights must be complete
+                        if (!wait_bar(bfree, bfree_par, abort_flag, p.err)) break;
+                        bfree_par ^= 1;
+                    }
+                    ptx::mbar_arrive_expect_tx(bfull, B_BYTES);
+                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * 64 * 128, &tmB, bfull, tap * 64, 0, g);
+                    cur_g = g;
+                    ++nb;
+                }
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!wait_bar(&empty[s], ph ^ 1, abort_flag, p.err)) break;
+                ptx::mbar_arrive_expect_tx(&full[s], A_BYTES);
+                const int ag = p.a_grouped ? g : 0, x0 = strip * kKxnStrip;
+                for (int ky = 0; ky < 3; ++ky)
+                    for (int q = 0; q < 4; ++q)
+                        ptx::tma_load_4d(sA + s * A_BYTES + ky * kKxnRowBytes + q * 4096, &tmA, &full[s], 0,
+                                         x0 + 30 * q - 1, oh + ky - 1, ag);
+                used[s] = true;
+                last_par[s] = ph;
+            }
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s)
+                if (used[s]) wait_bar(&full[s], last_par[s], abort_flag, p.err, false);
+            if (nb) wait_bar(bfull, (nb - 1) & 1, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = ptx::idesc_bf16(192);
+            int it = 0, cur_g = -1;
+            uint32_t bfull_par = 0;
+            for (int t = t_begin; t < t_end; ++t, ++it) {
+                const int g = t / p.tiles_w / p.Ho;
+                if (g != cur_g) {
+                    if (cur_g >= 0) ptx::mma_commit(bfree);  // old weights free once these MMAs finish
+                    if (!wait_bar(bfull, bfull_par, abort_flag, p.err)) break;
+                    bfull_par ^= 1;
+                    ptx::tc_fence_after();
+                    cur_g = g;
+                }
+                const int acc = it & 1, use = it >> 1;
+                if (!wait_bar(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
+                const int s = it % STAGES;
+                const uint32_t ph = (it / STAGES) & 1;
+                if (!wait_bar(&full[s], ph, abort_flag, p.err)) break;
+                ptx::tc_fence_after();
+                const uint32_t d = tmem_base + acc * 256;
+                const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB);
+#pragma unroll
+                for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * kKxnRowBytes + kk * 32),
+                                     ptx::sdesc_sw128(b0 + ky * 192 * 128 + kk * 32), idesc, (ky | kk) != 0);
+                ptx::mma_commit(&empty[s]);
+                ptx::mma_commit(&tfull[acc]);
+            }
+            ptx::mma_commit(drain);
+            wait_bar(drain, 0, abort_flag, p.err, false);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: warp 2 + 4 c + q reads TMEM lane quarter q; c = 2 grp + part (channels 32 part ..)
+        const int q = warp & 3, colq = (warp - 2) >> 2, grp = colq >> 1, part = colq & 1;
+        const bool lead_warp = warp == 2 + grp * 8;
+        const bool elected = lead_warp && lane == 0;
+        const bool inner = lane >= 1 && lane <= 30;  // lanes that produce an output pixel
+        const int srow = 30 * q + lane - 1;           // its row of the 120-pixel strip
+        uint8_t* sCg = sC + grp * 16384;
+        int k = 0;
+        for (int t = t_begin + grp, tl = grp; t < t_end; t += 2, tl += 2, ++k) {
+            const int use = tl >> 1;
+            if (!__all_sync(0xffffffffu, wait_bar(&tfull[grp], use & 1, abort_flag, p.err))) break;
+            ptx::tc_fence_after();
+            const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, g = r / p.Ho;
+            const int ow = strip * kKxnStrip + srow;
+            const bool valid = inner && ow < p.Wo;
+            const int co0 = part * 32;
+            const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + grp * 256 + co0;
+            float v[32], u[32];
+            ptx::tmem_ld32(taddr + 64, v);  // kx = 1: this pixel
+            ptx::tmem_ld32(taddr, u);       // kx = 0: the pixel to the left contributes
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += __shfl_up_sync(0xffffffffu, u[i], 1);
+            ptx::tmem_ld32(taddr + 128, u);  // kx = 2: the pixel to the right contributes
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += __shfl_down_sync(0xffffffffu, u[i], 1);
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(&tempty[grp]);  // the accumulator is in registers: TMEM free for the next tile
+            if (valid) finish_cols<32>(p, bias_all, g, oh, ow, co0, v);
+            if (k > 0) {  // the group's previous TMA store must have read its staging tile
+                if (elected) {
+                    ptx::bulk_wait_read0();
+                    ptx::mbar_arrive(&cfree[grp]);
+                }
+                if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
+            }
+            if (inner) {
+                const uint32_t base = ptx::smem_u32(sCg) + srow * 128;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = part * 4 + i;
+                    ptx::st_shared_v4(base + ((j ^ (srow & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                      pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                      pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                }
+            }
+            ptx::fence_proxy_async();
+            ptx::mbar_arrive(&cwritten[grp]);
+            if (lead_warp) {
+                bool w_ok = true;
+                if (lane == 0) w_ok = wait_bar(&cwritten[grp], k & 1, abort_flag, p.err);
+                if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) break;
+            }
+            if (elected) {  // (a tile lying wholly past a cropped output stores nothing)
+                if (strip * kKxnStrip < min(p.out_w, p.Wo) && oh < p.out_h)
+                    ptx::tma_store_4d(&tmC, sCg, 0, strip * kKxnStrip, oh, g);
+                ptx::bulk_commit();
+            }
+        }
+        if (elected) ptx::bulk_wait0();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // Final decoder layer (3x3, 64 -> 12 channels, pixel shuffle, x^ = clamp(0.5 + o, 0, 1)) in scatter
 // form.  With only 12 outputs, the gather form would stream every input pixel nine times through the
 // tensor cores (one K=64 slice per tap) for an N of 16.  Instead each input pixel is multiplied ONCE by
@@ -1269,6 +1492,18 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
     return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK, F8>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
 
+template <int STAGES>
+static cudaError_t launch_kxn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
+                              cudaStream_t s) {
+    constexpr int kSmem = 9 * 64 * 128 + STAGES * 3 * kKxnRowBytes + 2 * 16384 + kSmemExtra;
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+    cudaError_t e = smem_optin((const void*)conv_tc_kxn_kernel<STAGES>, kSmem);
+    if (e != cudaSuccess) return e;
+    const int sms = sm_count();
+    const int grid = args.total_tiles < sms ? args.total_tiles : sms;
+    return launch_pdl(conv_tc_kxn_kernel<STAGES>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, args);
+}
+
 template <int OUTK>
 static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                                 cudaStream_t s) {
@@ -1360,6 +1595,9 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const bool halo = (!f8 && !c32 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64)) ||
                       halo8;
     if (halo) BN = d.cout_pad;
+    // bf16 64 -> 64 layers with staged NHWC outputs: the three horizontal taps in N (conv_tc_kxn_kernel)
+    const bool kxn = halo && !f8 && d.Cout == 64 && d.cout_pad == 64 && d.mode == OUT_NHWC && !d.out_f32 &&
+                     out_c0 % 8 == 0 && d.out_gs % 8 == 0;
     // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
     // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
     // stored through one map whose row dimension spans all groups, so tiles must not cross a group's
@@ -1376,7 +1614,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
                             (f8 ? o8 && out_c % 16 == 0 && d.out_gs % 16 == 0 : out_c % 8 == 0 && d.out_gs % 8 == 0);
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
-    if (halo) { a.TW = 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
+    if (halo) { a.TW = kxn ? kKxnStrip : 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
     // two stacked 128-pixel sub-tiles per tile (sharing each stage's weights): the 128-output layers with
     // NHWC bf16 outputs that keep at least two such tiles per SM (decoder R1, encoder A2 at video sizes;
     // small layers such as H1 or the mean network would leave SMs idle)
@@ -1437,7 +1675,7 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t str[3] = {d.Cin * esz, (cuuint64_t)d.W * d.Cin * esz, (cuuint64_t)d.H * d.W * d.Cin * esz};
         if (a.a_grouped) str[2] = (cuuint64_t)d.in_gs * esz;
         cuuint32_t box[4] = {boxc, (cuuint32_t)a.TW, (cuuint32_t)(a.TH * MT), 1};
-        if (halo) { box[1] = 130; box[2] = 1; }
+        if (halo) { box[1] = kxn ? 32 : 130; box[2] = 1; }
         ok = encode_map(&ma, d.in, 4, dims, str, box, dt, swz);
     } else {
         cuuint64_t dims[5] = {(cuuint64_t)d.Cin, 2, (cuuint64_t)d.W / 2, 2, (cuuint64_t)d.H / 2};
@@ -1513,9 +1751,9 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
             cuuint64_t str[3] = {out_c * esz, (cuuint64_t)d.out_w * out_c * esz,
                                  d.groups > 1 ? (cuuint64_t)d.out_gs * esz : (cuuint64_t)d.out_h * d.out_w * out_c * esz};
-            cuuint32_t box[4] = {64, 128, 1, 1};
+            cuuint32_t box[4] = {64, (cuuint32_t)(kxn ? kKxnStrip : 128), 1, 1};
             if (!encode_map(&mc, d.out, 4, dims, str, box)) return cudaErrorInvalidValue;
-            return launch_halo<64, 2, 1>(ma, mb, mc, a, s);
+            return kxn ? launch_kxn<2>(ma, mb, mc, a, s) : launch_halo<64, 2, 1>(ma, mb, mc, a, s);
         }
         return BN == 16 ? launch_halo<16, 3, 0>(ma, mb, mc, a, s) : launch_halo<64, 2, 0>(ma, mb, mc, a, s);
     }

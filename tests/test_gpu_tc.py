@@ -67,14 +67,17 @@ LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
     (1, 2, 19, 9, 13, 1, 1, 1, 256),     # D0 frame 1 (grouped weights offset)
     (1, 2, 12, 136, 240, 1, 1, 0, 128),  # R1a at 1080p decoder resolution (255 tiles)
     (1, 2, 14, 23, 37, 1, 1, 1, 128),    # U1: 128 -> 256 PS, ragged
-    (1, 2, 15, 40, 56, 1, 1, 0, 64),     # R2a: 64 -> 64
+    (1, 2, 15, 40, 56, 1, 1, 0, 64),     # R2a: 64 -> 64 (horizontal taps in N, 120-pixel strips)
     (1, 2, 17, 24, 40, 1, 1, 1, 64),     # U2: 64 -> 256 PS
     (1, 2, 18, 24, 40, 1, 0, 2, 64),     # U3: 64 -> 12 PS, final mapping
     (1, 2, 26, 31, 29, 1, 0, 2, 64),     # U3 frame 1, ragged (crop)
-    (1, 2, 15, 17, 300, 1, 1, 0, 64),    # R2a over three 128-pixel strips (ragged last strip)
+    (1, 2, 15, 17, 300, 1, 1, 0, 64),    # R2a over three strips (ragged last strip)
     (1, 2, 17, 9, 260, 1, 1, 1, 64),     # U2 (four N tiles of 64) over three strips
     (1, 2, 26, 5, 390, 1, 0, 2, 64),     # U3 frame 1 over four strips, final mapping
-    (1, 2, 15, 272, 300, 1, 1, 0, 64),   # R2a: 816 tiles, runs of rows per CTA through the row FIFO
+    (1, 2, 15, 272, 300, 1, 1, 0, 64),   # R2a: 816 tiles of 120 pixels, several groups' rows per CTA
+    (1, 2, 15, 9, 480, 1, 1, 0, 64),     # R2a at the 1080p R2 width: four whole 120-pixel strips
+    (1, 2, 15, 13, 121, 1, 1, 0, 64),    # R2a: a second strip holding one pixel
+    (1, 2, 15, 6, 119, 1, 1, 0, 64),     # R2a: one strip, its last lane pair past the edge
     (1, 2, 18, 150, 260, 1, 0, 0, 64),   # U3 as a plain NHWC layer: the N = 16 resident-weight kernel
 ]
 
