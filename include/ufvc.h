@@ -338,7 +338,9 @@ ufvc_status ufvc_rans_decode(ufvc_ctx* ctx, const uint8_t* d_in, size_t nbytes, 
  * of frame f are 11 + 8 f + j) applied to d_in [H][W][Cin_s] with zero padding k/2 and `stride`;
  * act = 1 applies GELU; mode 0 writes NHWC [out_h][out_w][Cout], mode 1 pixel-shuffles x2 into
  * [out_h][out_w][Cout/4] (positions outside out_h x out_w are dropped), mode 2 writes
- * clamp(0.5 + o, 0, 1) pixel-shuffled as float.  In FP32 precision (and for the hyper-synthesis
+ * clamp(0.5 + o, 0, 1) pixel-shuffled as float, mode 3 writes NHWC like mode 0 plus the residual that
+ * d_out holds on entry, in place (as the decoders' second residual-block convolutions R1b and R2b run,
+ * Sec. 3.2; d_out in the tensor layout of d_out for mode 0).  In FP32 precision (and for the hyper-synthesis
  * layers S1 S2 S3) tensors are float with Cin_s = Cin rounded up to 16; otherwise they are bf16 with
  * Cin_s rounded up to 64 (32 for a layer with at most 32 input channels, i.e. the first layer for
  * N <= 10) and the layer runs on the tensor cores (stride 2 needs even H and W).  In FP8 precision the

@@ -1773,7 +1773,7 @@ extern "C" ufvc_status ufvc_synthesize(ufvc_ctx* ctx, const float* d_yhat, int w
 extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_in, int H, int W, int stride, int act,
                                        int mode, void* d_out, int out_h, int out_w, void* stream) {
     if (!ctx || !d_in || !d_out || layer < 0 || layer >= L_NENC + D_NDEC * ctx->N || H < 1 || W < 1 ||
-        (stride != 1 && stride != 2) || mode < 0 || mode > 2 || out_h < 1 || out_w < 1)
+        (stride != 1 && stride != 2) || mode < 0 || mode > 3 || out_h < 1 || out_w < 1)
         return fail(ctx, UFVC_ERR_ARG, "conv_layer: bad argument");
     if (fp8_unready(ctx)) return fail(ctx, UFVC_ERR_ARG, "conv_layer: FP8 context not calibrated (ufvc_calibrate_fp8)");
     CK(cudaSetDevice(ctx->cfg.device));
@@ -1793,11 +1793,12 @@ extern "C" ufvc_status ufvc_conv_layer(ufvc_ctx* ctx, int layer, const void* d_i
         if (L.cs8) L.cs8 += g * L.b_gs;
     }
     L.groups = 1;
-    const int m = mode == 0 ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
+    const int m = (mode == 0 || mode == 3) ? OUT_NHWC : mode == 1 ? OUT_PS : OUT_PS_FINAL_F32;
     if (use_tc(ctx, L) && L.ps_major && m != OUT_PS)
         return fail(ctx, UFVC_ERR_ARG, "conv_layer: this layer's tensor-core weights are laid out for pixel shuffle");
     ctx->cur_ws = &ctx->ws_stage;
-    RUN(conv(ctx, L, d_in, H, W, stride, act, m, d_out, out_h, out_w, (cudaStream_t)stream));
+    RUN(conv(ctx, L, d_in, H, W, stride, act, m, d_out, out_h, out_w, (cudaStream_t)stream,
+             mode == 3 ? d_out : nullptr));  // mode 3: the residual is d_out's content, updated in place
     CK(cudaGetLastError());
     return UFVC_OK;
 }

@@ -18,6 +18,19 @@ namespace ufvc {
 
 __device__ __forceinline__ float gelu_erf(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
+// (c0, c1) = (a * b0 + c0, a * b1 + c1), each one IEEE fused multiply-add rounded to nearest (the packed
+// FP32 instruction of sm_100+: the results of two fmaf calls in one issue slot)
+__device__ __forceinline__ void fma2_bcast(float& c0, float& c1, float a, float b0, float b1) {
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %2};\n\t"
+        "mov.b64 pb, {%3, %4};\n\t"
+        "mov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\t"
+        "mov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a), "f"(b0), "f"(b1));
+}
+
 __device__ __forceinline__ void store_out(const ConvDesc& d, int g, int oh, int ow, int co, float v) {
     if (d.mode == OUT_NHWC) {
         if (oh >= d.out_h || ow >= d.out_w) return;
@@ -379,9 +392,15 @@ __global__ void __launch_bounds__(128, 3) conv_simt88_kernel(const ConvDesc d, i
     const int nck = Cin / BK, nsteps = k * k * nck;
     const int s_begin = (int)((long long)ks * nsteps / KS), s_end = (int)((long long)(ks + 1) * nsteps / KS);
     float4 ra[2][2], rb[2][4];
-    auto load_regs = [&](int step, float4* qa, float4* qb) {
-        const int tap = step / nck, c0 = (step - tap * nck) * BK;
-        const int ky = tap / k, kx = tap - ky * k;
+    // the next step to load, as (tap, ky, kx, channel chunk): steps are loaded in order
+    int l_tap = s_begin / nck, l_ck = s_begin - l_tap * nck, l_ky = l_tap / k, l_kx = l_tap - l_ky * k;
+    auto load_regs = [&](int, float4* qa, float4* qb) {
+        const int tap = l_tap, c0 = l_ck * BK, ky = l_ky, kx = l_kx;
+        if (++l_ck == nck) {
+            l_ck = 0;
+            ++l_tap;
+            if (++l_kx == k) { l_kx = 0; ++l_ky; }
+        }
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int ih = a_oh[r] * s + ky - p, iw = a_ow[r] * s + kx - p;
@@ -430,7 +449,7 @@ __global__ void __launch_bounds__(128, 3) conv_simt88_kernel(const ConvDesc d, i
 #pragma unroll
             for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < 8; j += 2) fma2_bcast(acc[i][j], acc[i][j + 1], av[i], bv[j], bv[j + 1]);
         }
     };
     if (s_begin < s_end) load_regs(s_begin, ra[0], rb[0]);

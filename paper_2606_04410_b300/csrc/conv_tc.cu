@@ -101,11 +101,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) { ptx::tmem_ld32(taddr, v); }
 
-// Bias, activation and (bf16 NHWC output with a residual) the residual, in place, for NV (16 or 32)
-// consecutive accumulator columns of one output pixel.
+// Operand scales (FP8), bias and activation, in place, for NV (16 or 32) consecutive accumulator
+// columns of one output pixel.
 template <int NV>
-__device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
-                                            float* v) {
+__device__ __forceinline__ void bias_act_cols(const TcArgs& p, const float* bias_all, int g, int co0, float* v) {
     if (p.cscale) {  // FP8: undo the operand scales first
         const float* cs = p.cscale + (size_t)g * p.b_gs + co0;
 #pragma unroll
@@ -126,6 +125,13 @@ __device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_a
 #pragma unroll
         for (int i = 0; i < NV; i += 2) gelu_tc2(v[i], v[i + 1]);
     }
+}
+
+// bias_act_cols, then (NHWC outputs with a residual) the residual read from global memory.
+template <int NV>
+__device__ __forceinline__ void finish_cols(const TcArgs& p, const float* bias_all, int g, int oh, int ow, int co0,
+                                            float* v) {
+    bias_act_cols<NV>(p, bias_all, g, co0, v);
     if (p.mode == OUT_NHWC && p.res8 && co0 < p.Cout) {
         const uint4* r = reinterpret_cast<const uint4*>(p.res8 + (size_t)g * p.res_gs +
                                                         ((size_t)oh * p.out_w + ow) * p.out_c + co0);
@@ -908,14 +914,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 // above (tap = 3 ky + kx, 64 rows each), so the three taps of one ky are 192 consecutive rows.
 // Two epilogue groups of eight warps (two column halves x four lane quarters) drain alternate tiles
 // from two accumulators of 192 columns; outputs go through a swizzled staging tile per group and a
-// TMA store of 120 pixels x 64 channels, which clips at the image edge.
+// TMA store of 120 pixels x 64 channels, which clips at the image edge.  A residual (p.res) arrives
+// by TMA in the staging tile itself (the layout the output is stored from): the group's elected thread
+// loads the residual of the group's next tile as soon as the previous store has read the tile, so the
+// epilogue threads add it from shared memory instead of waiting on global loads.
 // ------------------------------------------------------------------------------------------------
 constexpr int kKxnStrip = 120;       // output pixels per tile
 constexpr int kKxnRowBytes = 16384;  // one input row of a tile: 4 boxes x 32 pixels x 128 B
 template <int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kxn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                       const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
+                       const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
+                       const TcArgs p) {
     constexpr int A_BYTES = 3 * kKxnRowBytes;
     constexpr int B_BYTES = 9 * 64 * 128;
     constexpr int C_BYTES = 2 * 16384;  // two staging tiles of 120 x 128 B (16 KB slots)
@@ -934,7 +944,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* drain = bfree + 1;
     uint64_t* cwritten = drain + 1;
     uint64_t* cfree = cwritten + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cfree + 2);
+    uint64_t* rfull = cfree + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rfull + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* sbias = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tmem_slot + 2) + 15) & ~uintptr_t(15));
     const float* bias_all = stage_bias(p, sbias);
@@ -950,6 +961,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_init(&tempty[a], 32 * 8);
             ptx::mbar_init(&cwritten[a], 32 * 8);
             ptx::mbar_init(&cfree[a], 1);
+            ptx::mbar_init(&rfull[a], 1);
         }
         ptx::mbar_init(bfull, 1);
         ptx::mbar_init(bfree, 1);
@@ -962,6 +974,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::prefetch_tmap(&tmA);
         ptx::prefetch_tmap(&tmB);
         ptx::prefetch_tmap(&tmC);
+        if (p.res) ptx::prefetch_tmap(&tmR);
     }
     ptx::tc_fence_before();
     __syncthreads();
@@ -1052,15 +1065,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool elected = lead_warp && lane == 0;
         const bool inner = lane >= 1 && lane <= 30;  // lanes that produce an output pixel
         const int srow = 30 * q + lane - 1;           // its row of the 120-pixel strip
+        const bool res = p.res != nullptr;
         uint8_t* sCg = sC + grp * 16384;
+        // the residual of tile t into the staging tile (elected thread)
+        auto load_res = [&](int t) {
+            const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, g = r / p.Ho;
+            ptx::mbar_arrive_expect_tx(&rfull[grp], kKxnStrip * 128);
+            ptx::tma_load_4d(sCg, &tmR, &rfull[grp], 0, strip * kKxnStrip, oh, g);
+        };
+        int n_res = 0;  // residual loads issued
+        if (res && elected && t_begin + grp < t_end) { load_res(t_begin + grp); ++n_res; }
         int k = 0;
         for (int t = t_begin + grp, tl = grp; t < t_end; t += 2, tl += 2, ++k) {
             const int use = tl >> 1;
             if (!__all_sync(0xffffffffu, wait_bar(&tfull[grp], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
             const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, g = r / p.Ho;
-            const int ow = strip * kKxnStrip + srow;
-            const bool valid = inner && ow < p.Wo;
             const int co0 = part * 32;
             const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + grp * 256 + co0;
             float v[32], u[32];
@@ -1073,8 +1093,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int i = 0; i < 32; ++i) v[i] += __shfl_down_sync(0xffffffffu, u[i], 1);
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[grp]);  // the accumulator is in registers: TMEM free for the next tile
-            if (valid) finish_cols<32>(p, bias_all, g, oh, ow, co0, v);
-            if (k > 0) {  // the group's previous TMA store must have read its staging tile
+            bias_act_cols<32>(p, bias_all, g, co0, v);
+            const uint32_t base = ptx::smem_u32(sCg) + srow * 128;
+            if (res) {  // the residual tile has landed in the staging tile
+                if (!__all_sync(0xffffffffu, wait_bar(&rfull[grp], k & 1, abort_flag, p.err))) break;
+                if (inner) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 w = ptx::ld_shared_v4(base + (((part * 4 + i) ^ (srow & 7)) << 4));
+                        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[8 * i + e] += __bfloat162float(h[e]);
+                    }
+                }
+            } else if (k > 0) {  // the group's previous TMA store must have read its staging tile
                 if (elected) {
                     ptx::bulk_wait_read0();
                     ptx::mbar_arrive(&cfree[grp]);
@@ -1082,7 +1114,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
             }
             if (inner) {
-                const uint32_t base = ptx::smem_u32(sCg) + srow * 128;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int j = part * 4 + i;
@@ -1102,8 +1133,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (strip * kKxnStrip < min(p.out_w, p.Wo) && oh < p.out_h)
                     ptx::tma_store_4d(&tmC, sCg, 0, strip * kKxnStrip, oh, g);
                 ptx::bulk_commit();
+                if (res && t + 2 < t_end) {  // the next residual once the store has read the tile
+                    ptx::bulk_wait_read0();
+                    load_res(t + 2);
+                    ++n_res;
+                }
             }
         }
+        if (elected && n_res > k)  // a residual load that no tile consumed (stopped early): let it land
+            wait_bar(&rfull[grp], (n_res - 1) & 1, abort_flag, p.err, false);
         if (elected) ptx::bulk_wait0();
     }
     ptx::tc_fence_before();
@@ -1493,15 +1531,15 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
 }
 
 template <int STAGES>
-static cudaError_t launch_kxn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
-                              cudaStream_t s) {
+static cudaError_t launch_kxn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const CUtensorMap& r,
+                              const TcArgs& args, cudaStream_t s) {
     constexpr int kSmem = 9 * 64 * 128 + STAGES * 3 * kKxnRowBytes + 2 * 16384 + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = smem_optin((const void*)conv_tc_kxn_kernel<STAGES>, kSmem);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_kxn_kernel<STAGES>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, args);
+    return launch_pdl(conv_tc_kxn_kernel<STAGES>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, r, args);
 }
 
 template <int OUTK>
@@ -1753,7 +1791,13 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
                                  d.groups > 1 ? (cuuint64_t)d.out_gs * esz : (cuuint64_t)d.out_h * d.out_w * out_c * esz};
             cuuint32_t box[4] = {64, (cuuint32_t)(kxn ? kKxnStrip : 128), 1, 1};
             if (!encode_map(&mc, d.out, 4, dims, str, box)) return cudaErrorInvalidValue;
-            return kxn ? launch_kxn<2>(ma, mb, mc, a, s) : launch_halo<64, 2, 1>(ma, mb, mc, a, s);
+            if (!kxn) return launch_halo<64, 2, 1>(ma, mb, mc, a, s);
+            CUtensorMap mr = mc;  // the residual, loaded into the staging tile: the output's layout and box
+            if (a.res) {
+                cuuint64_t rstr[3] = {str[0], str[1], d.groups > 1 ? (cuuint64_t)d.res_gs * esz : str[2]};
+                if (!encode_map(&mr, d.res, 4, dims, rstr, box)) return cudaErrorInvalidValue;
+            }
+            return launch_kxn<2>(ma, mb, mc, mr, a, s);
         }
         return BN == 16 ? launch_halo<16, 3, 0>(ma, mb, mc, a, s) : launch_halo<64, 2, 0>(ma, mb, mc, a, s);
     }

@@ -169,6 +169,38 @@ def _check_layer(arch, N, layer, H, W, stride, act, mode, cin_pad, crop=(0, 0), 
     return got
 
 
+@pytest.mark.parametrize("layer,H,W,cin_pad", [
+    (16, 9, 480, 64),     # R2b at the 1080p R2 width: four whole 120-pixel strips
+    (16, 13, 121, 64),    # R2b: a second strip holding one pixel
+    (16, 272, 300, 64),   # R2b: 816 tiles, several tiles per epilogue group (residual reloads)
+    (16, 40, 56, 64),     # R2b: one strip, narrower than the strip
+    (13, 136, 240, 128),  # R1b at the 1080p decoder resolution (two sub-tiles on SM pairs)
+    (13, 23, 37, 128),    # R1b, ragged
+])
+def test_tc_residual_layer_vs_float64(layer, H, W, cin_pad):
+    """Second convolution of a decoder residual block (mode 3): out = conv(x) + b + r with r the bf16
+    content of the output buffer, updated in place, against float64 on the same bf16 operands."""
+    u = U()
+    arch, N = 1, 2
+    blob = synthetic.draw_weights(arch, N, seed=3, bias_std=0.1)
+    codec = u.Codec(arch, N, 64, blob, "bf16")
+    _, co, k, ci = layer_table(arch, N)[layer]
+    rng = np.random.default_rng(layer + H + W)
+    x = np.zeros((H, W, cin_pad), np.float32)
+    x[..., :ci] = rng.normal(size=(H, W, ci))
+    xb = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    r = torch.from_numpy(rng.normal(size=(H, W, co)).astype(np.float32)).to(torch.bfloat16).cuda()
+    out = r.clone()
+    codec.conv_layer(layer, xb, 1, 0, 3, out)
+    assert codec.sync_status() == 0
+    got = out.double().cpu()
+    ref = ref_layer(blob, arch, N, layer, xb.double().cpu(), 1, 0, 0, H, W) + r.double().cpu()
+    err = (got - ref).abs()
+    scale = float(ref.abs().max())
+    bound = 8e-3 * ref.abs() + 2e-3 * scale
+    assert bool((err <= bound).all()), f"max err {float(err.max()):.4g} scale {scale:.3g}"
+
+
 def _run_chunk(codec, fr, qp):
     bits, nb = codec.encode_chunk(fr, qp)
     assert codec.sync_status() == 0
