@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int SLAB = 128 * (O8 ? 64 : 128);  // bytes of one 64-channel staging slab
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
-    static_assert(MT == 1 || (MT == 2 && !F8 && OP == OP_BF16), "two sub-tiles: BF16 operands");
+    static_assert(MT == 1 || (MT == 2 && (OP == OP_BF16 || OP == OP_E4M3)), "two sub-tiles: 64-channel rows");
     static_assert(!PAIR || (OP == OP_BF16 && !KM && BN % 32 == 0), "CTA pairs: BF16");
     constexpr int A_BYTES = 128 * MT * ROWB;
     constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROWB;  // this CTA's weight rows of a stage
@@ -468,8 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if constexpr (F8) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
-                            ptx::mma_f8(d, ptx::sdesc_sw64(a0 + kk * 32), ptx::sdesc_sw64(b0 + kk * 32), idesc,
-                                        !first || kk != 0);
+#pragma unroll
+                            for (int h = 0; h < MT; ++h)  // sub-tile h: rows 128 h .. of the A box
+                                ptx::mma_f8(d + h * BN, ptx::sdesc_sw64(a0 + h * 8192 + kk * 32),
+                                            ptx::sdesc_sw64(b0 + kk * 32), idesc, !first || kk != 0);
                     } else if constexpr (OP == OP_BF16_32) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=16 BF16 per 64-byte row
@@ -1658,7 +1660,8 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // small layers such as H1 or the mean network would leave SMs idle)
     const long long pairs = (long long)((Wo + a.TW - 1) / a.TW) * ((Ho + 2 * a.TH - 1) / (2 * a.TH)) *
                             (d.cout_pad / 128) * d.groups;
-    const int MT = (!f8 && !c32 && !halo && nhwc_stage && BN == 128 && d.kmask == 0 && pairs >= 2 * 148) ? 2 : 1;
+    // (E4M3 operands too, with E4M3 outputs: the FP8 decoders' R1)
+    const int MT = ((!f8 || o8) && !c32 && !halo && nhwc_stage && BN == 128 && d.kmask == 0 && pairs >= 2 * 148) ? 2 : 1;
     // CTA pairs (one M = 256 MMA over two SMs, each loading half of the weights): the staged BN = 256
     // layers (the decoders' pixel-shuffle layers D0, U1, U2)
     // (and the two-sub-tile 128-output layers with at least four waves of pair tiles: each SM then lands its
@@ -1765,7 +1768,9 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         if (!o8) return BN == 256 ? launch_bn<256, 5, true, OP_E4M3>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
         switch (BN) {
             case 64: return launch_bn<64, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
-            case 128: return launch_bn<128, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
+            case 128:
+                return MT == 2 ? launch_bn<128, 8, true, OP_E4M3, false, 2, false, true>(ma, mb, mc, a, s)
+                               : launch_bn<128, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
             case 192: return launch_bn<192, 7, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
             default: return launch_bn<256, 6, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
         }

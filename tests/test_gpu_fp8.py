@@ -70,6 +70,8 @@ FP8_LAYERS = [
     (4, 17, 41, 1, 0, 0, T_XT, T_A3R),     # Xb: 1x1, 192 -> 192
     (11, 9, 13, 1, 1, 1, T_YHAT, T_D0),    # D0 frame 0: 256 -> 512, sub-pixel-major pixel shuffle
     (20, 23, 37, 1, 1, 0, T_D0, T_R1A),    # R1a frame 1: 128 -> 128
+    (20, 272, 300, 1, 1, 0, T_D0, T_R1A),  # R1a: two stacked 128-pixel sub-tiles per tile
+    (1, 544, 600, 2, 1, 0, T_A1, T_A2),    # A2, stride 2, two sub-tiles per tile
     (14, 12, 21, 1, 1, 1, T_R1B, T_U1),    # U1 frame 0: 128 -> 256 PS
     (17, 24, 40, 1, 1, 1, T_R2B, None),    # U2 frame 0: 64 -> 256 PS, bf16 output (feeds the final layer)
     (15, 40, 56, 1, 1, 0, T_U1, T_R2A),    # R2a frame 0: 64 -> 64 3x3, resident-weight E4M3 kernel, staged
