@@ -921,16 +921,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 // loads the residual of the group's next tile as soon as the previous store has read the tile, so the
 // epilogue threads add it from shared memory instead of waiting on global loads.
 // ------------------------------------------------------------------------------------------------
+// F8: E4M3 operands (kind::f8f6f4, K = 32 per MMA) in 64-byte rows with the 64-byte swizzle, E4M3
+// outputs (value x out_inv) staged as plain 64-byte rows, and an E4M3 residual of scale res_s; the
+// accumulator columns are rescaled per output channel (input scale x weight scale) after the three
+// horizontal taps are summed, which share the channel's scale.
 constexpr int kKxnStrip = 120;       // output pixels per tile
-constexpr int kKxnRowBytes = 16384;  // one input row of a tile: 4 boxes x 32 pixels x 128 B
-template <int STAGES>
+template <int STAGES, bool F8 = false>
 __global__ void __launch_bounds__(kThreads, 1)
     conv_tc_kxn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                        const __grid_constant__ CUtensorMap tmC, const __grid_constant__ CUtensorMap tmR,
                        const TcArgs p) {
-    constexpr int A_BYTES = 3 * kKxnRowBytes;
-    constexpr int B_BYTES = 9 * 64 * 128;
-    constexpr int C_BYTES = 2 * 16384;  // two staging tiles of 120 x 128 B (16 KB slots)
+    constexpr int RB = F8 ? 64 : 128;         // bytes of one pixel's 64 channels
+    constexpr int BOXB = 32 * RB;             // one 32-pixel box
+    constexpr int ROWB = 4 * BOXB;            // one input row of a tile: four boxes
+    constexpr int A_BYTES = 3 * ROWB;
+    constexpr int B_BYTES = 9 * 64 * RB;
+    constexpr int CSLOT = F8 ? 8192 : 16384;  // one staging tile of 120 pixel rows
+    constexpr int C_BYTES = 2 * CSLOT;
     constexpr uint32_t TMEM_COLS = 512;  // accumulators at columns 0 and 256, 192 columns each
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1003,7 +1010,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bfree_par ^= 1;
                     }
                     ptx::mbar_arrive_expect_tx(bfull, B_BYTES);
-                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * 64 * 128, &tmB, bfull, tap * 64, 0, g);
+                    for (int tap = 0; tap < 9; ++tap) ptx::tma_load_3d(sB + tap * 64 * RB, &tmB, bfull, tap * 64, 0, g);
                     cur_g = g;
                     ++nb;
                 }
@@ -1014,7 +1021,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int ag = p.a_grouped ? g : 0, x0 = strip * kKxnStrip;
                 for (int ky = 0; ky < 3; ++ky)
                     for (int q = 0; q < 4; ++q)
-                        ptx::tma_load_4d(sA + s * A_BYTES + ky * kKxnRowBytes + q * 4096, &tmA, &full[s], 0,
+                        ptx::tma_load_4d(sA + s * A_BYTES + ky * ROWB + q * BOXB, &tmA, &full[s], 0,
                                          x0 + 30 * q - 1, oh + ky - 1, ag);
                 used[s] = true;
                 last_par[s] = ph;
@@ -1027,7 +1034,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = ptx::idesc_bf16(192);
+            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(192) : ptx::idesc_bf16(192);
             int it = 0, cur_g = -1;
             uint32_t bfull_par = 0;
             for (int t = t_begin; t < t_end; ++t, ++it) {
@@ -1048,11 +1055,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d = tmem_base + acc * 256;
                 const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB);
 #pragma unroll
-                for (int ky = 0; ky < 3; ++ky)
+                for (int ky = 0; ky < 3; ++ky) {
+                    if constexpr (F8) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * kKxnRowBytes + kk * 32),
-                                     ptx::sdesc_sw128(b0 + ky * 192 * 128 + kk * 32), idesc, (ky | kk) != 0);
+                        for (int kk = 0; kk < 2; ++kk)
+                            ptx::mma_f8(d, ptx::sdesc_sw64(a0 + ky * ROWB + kk * 32),
+                                        ptx::sdesc_sw64(b0 + ky * 192 * 64 + kk * 32), idesc, (ky | kk) != 0);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            ptx::mma_f16(d, ptx::sdesc_sw128(a0 + ky * ROWB + kk * 32),
+                                         ptx::sdesc_sw128(b0 + ky * 192 * 128 + kk * 32), idesc, (ky | kk) != 0);
+                    }
+                }
                 ptx::mma_commit(&empty[s]);
                 ptx::mma_commit(&tfull[acc]);
             }
@@ -1067,12 +1082,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool elected = lead_warp && lane == 0;
         const bool inner = lane >= 1 && lane <= 30;  // lanes that produce an output pixel
         const int srow = 30 * q + lane - 1;           // its row of the 120-pixel strip
-        const bool res = p.res != nullptr;
-        uint8_t* sCg = sC + grp * 16384;
+        const bool res = F8 ? p.res8 != nullptr : p.res != nullptr;
+        uint8_t* sCg = sC + grp * CSLOT;
         // the residual of tile t into the staging tile (elected thread)
         auto load_res = [&](int t) {
             const int strip = t % p.tiles_w, r = t / p.tiles_w, oh = r % p.Ho, g = r / p.Ho;
-            ptx::mbar_arrive_expect_tx(&rfull[grp], kKxnStrip * 128);
+            ptx::mbar_arrive_expect_tx(&rfull[grp], kKxnStrip * RB);
             ptx::tma_load_4d(sCg, &tmR, &rfull[grp], 0, strip * kKxnStrip, oh, g);
         };
         int n_res = 0;  // residual loads issued
@@ -1096,16 +1111,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::tc_fence_before();
             ptx::mbar_arrive(&tempty[grp]);  // the accumulator is in registers: TMEM free for the next tile
             bias_act_cols<32>(p, bias_all, g, co0, v);
-            const uint32_t base = ptx::smem_u32(sCg) + srow * 128;
+            // this pixel's row of the staging tile: bf16 128-byte rows with the 128-byte swizzle, or E4M3
+            // 64-byte rows in order (this thread's 32 channels: bytes 32 part ..)
+            const uint32_t base = ptx::smem_u32(sCg) + srow * RB;
             if (res) {  // the residual tile has landed in the staging tile
                 if (!__all_sync(0xffffffffu, wait_bar(&rfull[grp], k & 1, abort_flag, p.err))) break;
                 if (inner) {
+                    if constexpr (F8) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const uint4 w = ptx::ld_shared_v4(base + (((part * 4 + i) ^ (srow & 7)) << 4));
-                        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&w);
+                        for (int i = 0; i < 2; ++i) {
+                            const uint4 w = ptx::ld_shared_v4(base + part * 32 + 16 * i);
+                            const __nv_fp8x2_storage_t* h = reinterpret_cast<const __nv_fp8x2_storage_t*>(&w);
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) v[8 * i + e] += __bfloat162float(h[e]);
+                            for (int e = 0; e < 8; ++e) {
+                                const float2 f = __half22float2(__half2(__nv_cvt_fp8x2_to_halfraw2(h[e], __NV_E4M3)));
+                                v[16 * i + 2 * e] += f.x * p.res_s;
+                                v[16 * i + 2 * e + 1] += f.y * p.res_s;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint4 w = ptx::ld_shared_v4(base + (((part * 4 + i) ^ (srow & 7)) << 4));
+                            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&w);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) v[8 * i + e] += __bfloat162float(h[e]);
+                        }
                     }
                 }
             } else if (k > 0) {  // the group's previous TMA store must have read its staging tile
@@ -1116,12 +1147,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!__all_sync(0xffffffffu, wait_bar(&cfree[grp], (k - 1) & 1, abort_flag, p.err))) break;
             }
             if (inner) {
+                if constexpr (F8) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int j = part * 4 + i;
-                    ptx::st_shared_v4(base + ((j ^ (srow & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
-                                      pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
-                                      pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                    for (int i = 0; i < 2; ++i) {
+                        uint32_t wq[4];
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const float* f = v + 16 * i + 4 * k4;
+                            const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(f[0] * p.out_inv, f[1] * p.out_inv),
+                                                                         __NV_SATFINITE, __NV_E4M3);
+                            const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(f[2] * p.out_inv, f[3] * p.out_inv),
+                                                                         __NV_SATFINITE, __NV_E4M3);
+                            wq[k4] = lo | (hi << 16);
+                        }
+                        ptx::st_shared_v4(base + part * 32 + 16 * i, wq[0], wq[1], wq[2], wq[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = part * 4 + i;
+                        ptx::st_shared_v4(base + ((j ^ (srow & 7)) << 4), pack_bf16(v[8 * i], v[8 * i + 1]),
+                                          pack_bf16(v[8 * i + 2], v[8 * i + 3]), pack_bf16(v[8 * i + 4], v[8 * i + 5]),
+                                          pack_bf16(v[8 * i + 6], v[8 * i + 7]));
+                    }
                 }
             }
             ptx::fence_proxy_async();
@@ -1532,16 +1580,17 @@ static cudaError_t launch_halo(const CUtensorMap& a, const CUtensorMap& b, const
     return launch_pdl(conv_tc_halo_kernel<BN, STAGES, OUTK, F8>, dim3(grid), dim3(kThreads), smem, s, a, b, c, args);
 }
 
-template <int STAGES>
+template <int STAGES, bool F8 = false>
 static cudaError_t launch_kxn(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const CUtensorMap& r,
                               const TcArgs& args, cudaStream_t s) {
-    constexpr int kSmem = 9 * 64 * 128 + STAGES * 3 * kKxnRowBytes + 2 * 16384 + kSmemExtra;
+    constexpr int RB = F8 ? 64 : 128;
+    constexpr int kSmem = 9 * 64 * RB + STAGES * 3 * 4 * 32 * RB + 2 * (F8 ? 8192 : 16384) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-    cudaError_t e = smem_optin((const void*)conv_tc_kxn_kernel<STAGES>, kSmem);
+    cudaError_t e = smem_optin((const void*)conv_tc_kxn_kernel<STAGES, F8>, kSmem);
     if (e != cudaSuccess) return e;
     const int sms = sm_count();
     const int grid = args.total_tiles < sms ? args.total_tiles : sms;
-    return launch_pdl(conv_tc_kxn_kernel<STAGES>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, r, args);
+    return launch_pdl(conv_tc_kxn_kernel<STAGES, F8>, dim3(grid), dim3(kThreads), kSmem, s, a, b, c, r, args);
 }
 
 template <int OUTK>
@@ -1636,8 +1685,9 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
                       halo8;
     if (halo) BN = d.cout_pad;
     // bf16 64 -> 64 layers with staged NHWC outputs: the three horizontal taps in N (conv_tc_kxn_kernel)
-    const bool kxn = halo && !f8 && d.Cout == 64 && d.cout_pad == 64 && d.mode == OUT_NHWC && !d.out_f32 &&
-                     out_c0 % 8 == 0 && d.out_gs % 8 == 0;
+    // (E4M3: the layers the resident-weight E4M3 kernel takes, with 64 outputs)
+    const bool kxn = halo && d.Cout == 64 && d.cout_pad == 64 && d.mode == OUT_NHWC && !d.out_f32 &&
+                     (f8 ? halo8 : out_c0 % 8 == 0 && d.out_gs % 8 == 0);
     // staged epilogue (bf16 output through shared memory and TMA stores): NHWC, or a sub-pixel-major
     // pixel shuffle written whole (no crop) with 64-channel runs; grouped pixel-shuffle outputs are
     // stored through one map whose row dimension spans all groups, so tiles must not cross a group's
@@ -1740,10 +1790,17 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         cuuint64_t dims[4] = {(cuuint64_t)out_c, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)d.groups};
         cuuint64_t str[3] = {(cuuint64_t)out_c, (cuuint64_t)d.out_w * out_c,
                              d.groups > 1 ? (cuuint64_t)d.out_gs : (cuuint64_t)d.out_h * d.out_w * out_c};
-        cuuint32_t box[4] = {64, 128, 1, 1};
+        cuuint32_t box[4] = {64, (cuuint32_t)(kxn ? kKxnStrip : 128), 1, 1};
         if (!encode_map(&mc, d.out, 4, dims, str, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE))
             return cudaErrorInvalidValue;
-        return launch_halo<64, 4, 2, true>(ma, mb, mc, a, s);
+        if (!kxn) return launch_halo<64, 4, 2, true>(ma, mb, mc, a, s);
+        CUtensorMap mr = mc;  // the E4M3 residual, loaded into the staging tile
+        if (a.res8) {
+            cuuint64_t rstr[3] = {str[0], str[1], d.groups > 1 ? (cuuint64_t)d.res_gs : str[2]};
+            if (!encode_map(&mr, d.res, 4, dims, rstr, box, CU_TENSOR_MAP_DATA_TYPE_UINT8, CU_TENSOR_MAP_SWIZZLE_NONE))
+                return cudaErrorInvalidValue;
+        }
+        return launch_kxn<6, true>(ma, mb, mc, mr, a, s);
     }
     if (f8 && staged) {
         // staged outputs of E4M3 layers: codes (64-byte boxes, no swizzle) or bf16 (128-byte swizzle)

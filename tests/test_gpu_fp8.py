@@ -74,9 +74,9 @@ FP8_LAYERS = [
     (1, 544, 600, 2, 1, 0, T_A1, T_A2),    # A2, stride 2, two sub-tiles per tile
     (14, 12, 21, 1, 1, 1, T_R1B, T_U1),    # U1 frame 0: 128 -> 256 PS
     (17, 24, 40, 1, 1, 1, T_R2B, None),    # U2 frame 0: 64 -> 256 PS, bf16 output (feeds the final layer)
-    (15, 40, 56, 1, 1, 0, T_U1, T_R2A),    # R2a frame 0: 64 -> 64 3x3, resident-weight E4M3 kernel, staged
-    (23, 17, 300, 1, 1, 0, T_U1, T_R2A),   # R2a frame 1 over three 128-pixel strips (ragged last strip)
-    (16, 33, 129, 1, 0, 0, T_R2A, T_R2B),  # R2b frame 0 (no residual here), a one-pixel second strip
+    (15, 40, 56, 1, 1, 0, T_U1, T_R2A),    # R2a frame 0: 64 -> 64 3x3, horizontal taps in N, staged E4M3
+    (23, 17, 300, 1, 1, 0, T_U1, T_R2A),   # R2a frame 1 over three 120-pixel strips (ragged last strip)
+    (16, 33, 129, 1, 0, 0, T_R2A, T_R2B),  # R2b frame 0 (no residual here), a nine-pixel second strip
 ]
 
 
@@ -117,6 +117,41 @@ def test_fp8_layer_vs_float64(layer, H, W, stride, act, mode, tin, tout):
     if tout is not None:  # E4M3 outputs saturate at +-448 codes (outputs beyond the calibrated range)
         lim = 448.0 * float(scales[tout])
         ref = ref.clamp(-lim, lim)
+    err = (got - ref).abs()
+    bound = 0.07 * ref.abs() + 0.02 * float(ref.abs().max())
+    assert bool((err <= bound).all()), f"max err {float(err.max()):.4g} scale {float(ref.abs().max()):.3g}"
+
+
+@pytest.mark.parametrize("layer,H,W,tin,tout,tres", [
+    (16, 9, 480, T_R2A, T_R2B, T_U1),     # R2b at the 1080p R2 width (horizontal taps in N, 120-pixel strips)
+    (16, 13, 121, T_R2A, T_R2B, T_U1),    # R2b: a second strip holding one pixel
+    (16, 272, 300, T_R2A, T_R2B, T_U1),   # R2b: many tiles per epilogue group (residual reloads)
+    (13, 272, 300, T_R1A, T_R1B, T_D0),   # R1b: two stacked sub-tiles, residual read per thread
+])
+def test_fp8_residual_layer_vs_float64(layer, H, W, tin, tout, tres):
+    """Second convolution of a decoder residual block in FP8 (mode 3): the output buffer holds the
+    residual's E4M3 codes (scale of the block input) and receives the output's codes in place."""
+    N = 2
+    blob = synthetic.draw_weights(1, N, seed=5)
+    codec, _ = _calibrated(N, 64, 96, blob)
+    scales = codec.fp8_scales()
+    w, b, co, k, ci = _layer(blob, 1, N, layer)
+    wt = torch.from_numpy(w)
+    sw = wt.abs().amax(dim=(1, 2, 3), keepdim=True) / 448.0
+    wq = _e4m3(wt / sw) * sw
+    rng = np.random.default_rng(layer + W)
+    s_in, s_res, s_out = float(scales[tin]), float(scales[tres]), float(scales[tout])
+    codes = (torch.from_numpy(rng.normal(size=(H, W, ci)) * 60.0)).to(torch.float8_e4m3fn)
+    xq = codes.to(torch.float64) * s_in
+    rcodes = (torch.from_numpy(rng.normal(size=(H, W, co)) * 60.0)).to(torch.float8_e4m3fn)
+    rq = rcodes.to(torch.float64) * s_res
+    out = rcodes.view(torch.uint8).contiguous().cuda()
+    codec.conv_layer(layer, codes.view(torch.uint8).contiguous().cuda(), 1, 0, 3, out)
+    assert codec.sync_status() == 0
+    got = out.cpu().view(torch.float8_e4m3fn).to(torch.float64) * s_out
+    y = F.conv2d(xq.permute(2, 0, 1)[None], wq.permute(0, 3, 1, 2), torch.from_numpy(b), padding=k // 2)
+    lim = 448.0 * s_out
+    ref = (y[0].permute(1, 2, 0) + rq).clamp(-lim, lim)
     err = (got - ref).abs()
     bound = 0.07 * ref.abs() + 0.02 * float(ref.abs().max())
     assert bool((err <= bound).all()), f"max err {float(err.max()):.4g} scale {float(ref.abs().max()):.3g}"
