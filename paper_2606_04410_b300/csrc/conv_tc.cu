@@ -1684,6 +1684,10 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     const bool halo = (!f8 && !c32 && d.stride == 1 && d.k == 3 && d.Cin == 64 && (d.cout_pad == 16 || d.cout_pad == 64)) ||
                       halo8;
     if (halo) BN = d.cout_pad;
+    // NHWC layers with fewer 128-pixel tiles than SMs at N = 256 (the encoder's A4 on a 1080p latent: 64
+    // tiles) take N tiles of 128, so that twice as many SMs share the work
+    if (BN == 256 && d.mode == OUT_NHWC && ((long long)Ho * Wo + 127) / 128 * (d.cout_pad / 256) * d.groups < sm_count())
+        BN = 128;
     // bf16 64 -> 64 layers with staged NHWC outputs: the three horizontal taps in N (conv_tc_kxn_kernel)
     // (E4M3: the layers the resident-weight E4M3 kernel takes, with 64 outputs)
     const bool kxn = halo && d.Cout == 64 && d.cout_pad == 64 && d.mode == OUT_NHWC && !d.out_f32 &&
