@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int ROWB = OP == OP_BF16 ? 128 : 64;  // bytes of one K row of a stage
     constexpr int CH = OP == OP_BF16_32 ? 32 : 64;  // input channels per stage
     static_assert(MT == 1 || (MT == 2 && (OP == OP_BF16 || OP == OP_E4M3)), "two sub-tiles: 64-channel rows");
-    static_assert(!PAIR || (OP == OP_BF16 && !KM && BN % 32 == 0), "CTA pairs: BF16");
+    static_assert(!PAIR || ((OP == OP_BF16 || OP == OP_E4M3) && !KM && BN % 32 == 0), "CTA pairs: 64-channel rows");
     constexpr int A_BYTES = 128 * MT * ROWB;
     constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * ROWB;  // this CTA's weight rows of a stage
     // 128-pixel sub-tiles of a tile; a pair's CTA r holds sub-tiles r MT .. r MT + MT - 1, and the pair's
@@ -448,7 +448,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the odd CTA issues nothing; its accumulators are complete when the even CTA's last commit lands
             if (lane == 0) wait_bar(drain, 0, abort_flag, p.err, false);
         } else if (lane == 0) {
-            constexpr uint32_t idesc = F8 ? ptx::idesc_e4m3(BN) : PAIR ? ptx::idesc_bf16_m256(BN) : ptx::idesc_bf16(BN);
+            constexpr uint32_t idesc = F8 ? (PAIR ? ptx::idesc_e4m3_m256(BN) : ptx::idesc_e4m3(BN))
+                                          : PAIR ? ptx::idesc_bf16_m256(BN) : ptx::idesc_bf16(BN);
             int it = 0, tl = 0;
             bool ok = true;
             for (int t = cid; t < p.total_tiles && ok; t += ncl, ++tl) {
@@ -465,7 +466,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!wait_bar(&full[s], ph, abort_flag, p.err)) { ok = false; break; }
                     ptx::tc_fence_after();
                     const uint32_t a0 = ptx::smem_u32(sA + s * A_BYTES), b0 = ptx::smem_u32(sB + s * B_BYTES);
-                    if constexpr (F8) {
+                    if constexpr (F8 && PAIR) {
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk)  // M = 256 over the pair, 2 x K=32 E4M3 per 64-byte row
+#pragma unroll
+                            for (int h = 0; h < MT; ++h)
+                                ptx::mma_f8_pair(d + h * BN, ptx::sdesc_sw64(a0 + h * 8192 + kk * 32),
+                                                 ptx::sdesc_sw64(b0 + kk * 32), idesc, !first || kk != 0);
+                    } else if constexpr (F8) {
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk)  // 2 x K=32 E4M3 per 64-byte row
 #pragma unroll
@@ -1720,8 +1728,10 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     // layers (the decoders' pixel-shuffle layers D0, U1, U2)
     // (and the two-sub-tile 128-output layers with at least four waves of pair tiles: each SM then lands its
     // two 128-pixel A tiles and half of the weight rows per stage, 40 KB instead of 48 KB)
-    const bool pair = d.pairs && !f8 && !c32 && !halo && staged && d.kmask == 0 &&
-                      (BN == 256 || (BN == 128 && MT == 2 && pairs >= 4 * 148));
+    // (E4M3 operands: only the layer with bf16 outputs, U2; with E4M3 outputs D0 and U1 ran 2-6 % slower on
+    // pairs than on single SMs)
+    const bool pair = d.pairs && !c32 && !halo && staged && d.kmask == 0 &&
+                      ((BN == 256 && !o8) || (!f8 && BN == 128 && MT == 2 && pairs >= 4 * 148));
     const int SUB = pair ? 2 * MT : MT;  // 128-pixel sub-tiles per tile
     if (SUB > 1) pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1, SUB);  // the stack's rows fit Ho
     a.Ho = Ho; a.Wo = Wo;
@@ -1826,7 +1836,10 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
             okc = encode_map(&mc, d.out, 4, dims, str, box, odt, osw);
         }
         if (!okc) return cudaErrorInvalidValue;
-        if (!o8) return BN == 256 ? launch_bn<256, 5, true, OP_E4M3>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
+        if (!o8)
+            return BN != 256 ? cudaErrorInvalidValue
+                   : pair    ? launch_bn<256, 8, true, OP_E4M3, false, 1, true>(ma, mb, mc, a, s)
+                             : launch_bn<256, 5, true, OP_E4M3>(ma, mb, mc, a, s);
         switch (BN) {
             case 64: return launch_bn<64, 8, true, OP_E4M3, false, 1, false, true>(ma, mb, mc, a, s);
             case 128:

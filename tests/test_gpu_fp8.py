@@ -157,6 +157,33 @@ def test_fp8_residual_layer_vs_float64(layer, H, W, tin, tout, tres):
     assert bool((err <= bound).all()), f"max err {float(err.max()):.4g} scale {float(ref.abs().max()):.3g}"
 
 
+@pytest.mark.parametrize("layer,H,W,tin,tout", [
+    (17, 136, 240, T_R2B, None),   # U2 at the 1080p decoder's quarter size
+    (17, 9, 260, T_R2B, None),     # U2, one tile row: every pair's second tile lies below the output
+    (25, 25, 37, T_R2B, None),     # U2 frame 1, ragged
+])
+def test_fp8_pixel_shuffle_pairs_equal_single(layer, H, W, tin, tout):
+    """The E4M3 layer with bf16 outputs (U2) on SM pairs (one M = 256 MMA over two SMs) gives the same
+    bytes as on one SM per 128-pixel tile: the same products summed in the same order."""
+    N = 2
+    blob = synthetic.draw_weights(1, N, seed=5)
+    codec, _ = _calibrated(N, 64, 96, blob)
+    _, _, co, k, ci = _layer(blob, 1, N, layer)
+    rng = np.random.default_rng(layer + H)
+    codes = (torch.from_numpy(rng.normal(size=(H, W, ci)) * 60.0)).to(torch.float8_e4m3fn)
+    xin = codes.view(torch.uint8).contiguous().cuda()
+    outs = []
+    for pairs in (True, False):
+        codec.set_conv_pairs(pairs)
+        out = torch.zeros((2 * H, 2 * W, co // 4), dtype=torch.uint8 if tout is not None else torch.bfloat16,
+                          device="cuda")
+        codec.conv_layer(layer, xin, 1, 1, 1, out)
+        assert codec.sync_status() == 0
+        outs.append(out.cpu())
+    assert torch.equal(outs[0].view(torch.uint8), outs[1].view(torch.uint8))
+    assert int((outs[0].view(torch.uint8) != 0).sum()) > outs[0].numel() // 4  # not trivially equal
+
+
 @pytest.mark.parametrize("N,H,W", [(2, 200, 328), (8, 128, 160)])
 def test_fp8_chunk(N, H, W):
     u = U()
