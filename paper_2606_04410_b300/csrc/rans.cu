@@ -804,37 +804,37 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         if constexpr (decltype(all)::value) act = true;
         bad |= t;
         t &= (uint32_t)(kBins - 1);
-        const uint32_t slot = x & 0xFFFFu;
+        const uint32_t slot = x & 0xFFFFu, xh = x >> 16;
         const uint2 e = ent[t * 256 + (slot >> 8)];
         const uint32_t ab = runs[t];
-        uint32_t s = e.x & 511u, c = e.y & 0xFFFFu, f = (e.x >> 9) & 0xFFFFu;
-        const uint32_t f1 = e.y >> 16, b1 = c + f;
-        const bool h = slot >= b1;
-        s += h ? 1u : 0u;
-        c = h ? b1 : c;
-        f = h ? f1 : f;
         const bool tl = slot < (ab & 0xFFFFu), tr = slot >= kProbM - (ab >> 16);
+        const uint32_t s0 = e.x & 511u, c0 = e.y & 0xFFFFu, f0 = (e.x >> 9) & 0xFFFFu;
+        const uint32_t f1 = e.y >> 16, b1 = c0 + f0;
+        // the next state for both candidates, s0 and s0 + 1, computed before the choice (off the chain)
+        const uint32_t xn0 = f0 * xh + (slot - c0), xn1 = f1 * xh + (slot - b1);
+        const bool h = slot >= b1;
+        uint32_t xn = h ? xn1 : xn0;
+        uint32_t s = s0 + (h ? 1u : 0u);
+        xn = tl || tr ? xh : xn;  // the tails: f = 1, c = slot
+        s = tl ? slot : tr ? slot - (kProbM - kNsym) : s;
         const uint32_t d = e.x >> 25;
         const bool far = act && d >= 2u && slot >= b1 + f1 && !tl && !tr;
         if (__any_sync(0xffffffffu, far)) {
             if (far) {  // the slot lies past s0 + 1: bisection over the bucket's remaining symbols
                 const uint16_t* C = cum + t * 512;
-                uint32_t lo = s + 1, hi = (e.x & 511u) + (d < 127u ? d : 255u);
+                uint32_t lo = s0 + 2, hi = s0 + (d < 127u ? d : 255u);
                 hi = hi < (uint32_t)(kNsym - 1) ? hi : (uint32_t)(kNsym - 1);
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi + 1) >> 1;
                     if (C[mid] <= slot) lo = mid; else hi = mid - 1;
                 }
                 s = lo;
-                c = C[lo];
-                f = (lo + 1 < (uint32_t)kNsym ? (uint32_t)C[lo + 1] : kProbM) - c;
+                const uint32_t c = C[lo];
+                const uint32_t f = (lo + 1 < (uint32_t)kNsym ? (uint32_t)C[lo + 1] : kProbM) - c;
+                xn = f * xh + slot - c;
             }
         }
-        s = tl ? slot : tr ? slot - (kProbM - kNsym) : s;
-        c = tl || tr ? slot : c;
-        f = tl || tr ? 1u : f;
         if (act) {
-            const uint32_t xn = f * (x >> 16) + slot - c;
             const bool rn = xn < kRansL;
             x = rn ? (xn << 16) | w0 : xn;
             r += rn ? 1u : 0u;
