@@ -874,12 +874,26 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
         if (ctx->cfg.precision == UFVC_FP8 && L.w8) {
             d.w8 = L.w8; d.cscale = L.cs8; d.out_inv = L.out_inv; d.res_s = L.res_s;
         }
-        const cudaError_t e = launch_conv_tc(d, s);
+        const size_t tneed = conv_tc_workspace(d);  // split-K range sums (layers with few tiles)
+        if (tneed) {
+            Workspace* ws = ctx->cur_ws;
+            if (tneed > ws->cap) {  // first use of this shape: grow (cudaFree waits for the old buffer's users)
+                cudaFree(ws->p);
+                ws->p = nullptr;
+                ws->cap = 0;
+                CK(cudaMalloc(&ws->p, tneed * sizeof(float)));
+                ws->cap = tneed;
+            }
+            d.tc_ws = ws->p;
+            d.tc_ws_cap = ws->cap;
+        }
+        int extra = 0;
+        const cudaError_t e = launch_conv_tc(d, s, &extra);
         if (e != cudaSuccess) {
             ctx->err = std::string("tensor-core conv launch: ") + cudaGetErrorString(e);
             return UFVC_ERR_CUDA;
         }
-        ++ctx->conv_launches;
+        ctx->conv_launches += 1 + extra;
         return UFVC_OK;
     }
     d.Cin = L.cin_p;
@@ -1136,6 +1150,7 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
     if (ctx->dcm) RUN(run_dc_encoder(ctx, p, frames, cin, s));
     else RUN(run_plain_analysis(ctx, p, frames, cin, s));
     prof_begin(ctx, "hyper_analysis", s);
+    const int nl_ha = ctx->conv_launches;
     if (use_tc(ctx, ctx->enc[L_H1])) {
         // tensor cores: only the encoder computes z (z^ travels in the bit-stream), so the hyper-analysis
         // needs no bit-exact twin on the decoder side
@@ -1148,13 +1163,13 @@ static ufvc_status run_encoder_front(ufvc_ctx* ctx, Plan* p, const uint8_t* fram
         RUN(conv(ctx, ctx->enc[L_H2], p->hb_bf, p->hhe, p->whe, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s, nullptr,
                  nullptr, 0, 0, 0, 0, 1, true));
         launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
-        prof_end(ctx, s, 4);
+        prof_end(ctx, s, 2 + (ctx->conv_launches - nl_ha));  // the conversion, z^ and every conv kernel
     } else {
         RUN(conv(ctx, ctx->enc[L_H1], p->y, p->Hy, p->Wy, 2, 1, OUT_NHWC, p->hb, p->hh, p->wh, s));
         probe(ctx, T_HB, p->hb, (size_t)p->hh * p->wh * a.cz, s);
         RUN(conv(ctx, ctx->enc[L_H2], p->hb, p->hh, p->wh, 2, 0, OUT_NHWC, p->z, p->Hz, p->Wz, s));
         launch_zquant(p->z, p->Hz * p->Wz, a.cz, p->zthr, p->zhat, p->iz, s);
-        prof_end(ctx, s, 3);
+        prof_end(ctx, s, 1 + (ctx->conv_launches - nl_ha));
     }
     // the last hyper-synthesis layer also quantises the latent and forms its scale indices
     const EntParams ent{p->idx, p->y, p->rhat, nullptr, qp, true};

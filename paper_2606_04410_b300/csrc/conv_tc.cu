@@ -65,6 +65,11 @@ struct TcArgs {
     // so the epilogue may store NV consecutive channels as 16-byte vectors; else channel by channel
     int vec_out;
     unsigned long long kmask;  // K steps that run (bit ks); the others have all-zero weights
+    // split K (layers with few tiles): work unit u = tile u / ksplit, K range u % ksplit; each range's raw
+    // sums go to ws [ksplit][groups][Ho][Wo][ws_c] (float) and conv_tc_split_reduce_kernel finishes the layer
+    int ksplit;
+    float* ws;
+    int ws_c;
 };
 
 // All groups' biases (groups x Cout floats) copied once into shared memory when they fit; the epilogue
@@ -391,11 +396,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) { used[s] = false; last_par[s] = 0; }
             bool ok = true;
-            for (int t = cid; t < p.total_tiles && ok; t += ncl) {
+            for (int u = cid; u < p.total_tiles && ok; u += ncl) {
+                const int t = u / p.ksplit, kr = u - t * p.ksplit;
                 const int nt = t % p.n_tiles, r = t / p.n_tiles, mt = r % tiles_m, g = r / tiles_m;
                 const int h0 = (mt / p.tiles_w) * p.TH * SUBS + (int)crank * MT * p.TH, w0 = (mt % p.tiles_w) * p.TW;
                 const int ag = p.a_grouped ? g : 0;
-                for (int ks = 0; ks < p.ksteps; ++ks) {
+                const int ke = (kr + 1) * p.ksteps / p.ksplit;
+                for (int ks = kr * p.ksteps / p.ksplit; ks < ke; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;  // all-zero weights: no stage
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -452,13 +459,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                                           : PAIR ? ptx::idesc_bf16_m256(BN) : ptx::idesc_bf16(BN);
             int it = 0, tl = 0;
             bool ok = true;
-            for (int t = cid; t < p.total_tiles && ok; t += ncl, ++tl) {
+            for (int u = cid; u < p.total_tiles && ok; u += ncl, ++tl) {
+                const int kr = u % p.ksplit;
                 const int acc = tl % NACC, use = tl / NACC;
                 if (!wait_bar<PAIR>(&tempty[acc], (use & 1) ^ 1, abort_flag, p.err)) break;
                 ptx::tc_fence_after();
                 const uint32_t d = tmem_base + acc * ACOLS;
                 bool first = true;  // the tile's first executed step overwrites the accumulator
-                for (int ks = 0; ks < p.ksteps; ++ks) {
+                const int ke = (kr + 1) * p.ksteps / p.ksplit;
+                for (int ks = kr * p.ksteps / p.ksplit; ks < ke; ++ks) {
                     if (KM && !((p.kmask >> ks) & 1ull)) continue;
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -527,7 +536,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint8_t* sCg = sC + egrp * (BN / 64) * SLAB;             // this group's staging slabs
         int tl = egrp, k = 0;  // k counts sub-tiles (the staging barriers' phases)
         bool run = true;
-        for (int t = cid + egrp * ncl; run && t < p.total_tiles; t += EG * ncl, tl += EG) {
+        for (int u = cid + egrp * ncl; run && u < p.total_tiles; u += EG * ncl, tl += EG) {
+            const int t = u / p.ksplit, kr = u - t * p.ksplit;
             const int acc = tl % NACC, use = tl / NACC;
             if (!__all_sync(0xffffffffu, wait_bar(&tfull[acc], use & 1, abort_flag, p.err))) break;
             ptx::tc_fence_after();
@@ -586,7 +596,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                         }
                     } else {
-                        if (valid) store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                        if (valid) {
+                            if (p.ksplit > 1) {  // this K range's raw sums
+                                float4* dst = reinterpret_cast<float4*>(
+                                    p.ws + (((size_t)kr * p.groups + g) * p.Ho * p.Wo + (size_t)oh * p.Wo + ow) * p.ws_c +
+                                    nt * BN + c);
+#pragma unroll
+                                for (int i = 0; i < CHUNK / 4; ++i)
+                                    dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                            } else {
+                                store_cols<CHUNK>(p, bias_all, g, oh, ow, nt * BN + c, v);
+                            }
+                        }
                     }
                 }
                 if (hs == MT - 1) {  // every sub-tile's columns are in registers or staged: free the accumulator
@@ -1618,6 +1639,7 @@ static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, cons
 static cudaError_t launch_conv_final(const ConvDesc& d, cudaStream_t s) {
     const int Ho = d.H, Wo = d.W;
     TcArgs a{};
+    a.ksplit = 1;
     a.Ho = Ho; a.Wo = Wo;
     a.TW = kFinStrip; a.TH = 1;
     a.tiles_w = (Wo + kFinStrip - 1) / kFinStrip;
@@ -1664,7 +1686,67 @@ static cudaError_t launch_conv_final(const ConvDesc& d, cudaStream_t s) {
     return launch_final<0>(ma, mb, mc, a, s);
 }
 
-cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
+// Split K for bf16 NHWC layers with few 128-pixel tiles (the hyper-analysis H1, H2 on a 1080p latent: 16
+// and 4 tiles, each running 36 or 18 K steps one after another on a single SM): as many K ranges as fill
+// about one CTA per SM, each of at least four 64-channel steps.  1 = no split.
+int conv_tc_ksplit(const ConvDesc& d) {
+    if (d.w8 || d.kmask || d.mode != OUT_NHWC || d.res) return 1;
+    if (d.Cin % 64 != 0 || (d.stride != 1 && d.stride != 2) || d.k % 2 == 0 || d.Cout % 4 != 0) return 1;
+    if (d.stride == 1 && d.k == 3 && d.Cin == 64 && d.cout_pad <= 64) return 1;  // the resident-weight kernels
+    const int out_c = d.out_c_stride ? d.out_c_stride : d.Cout;
+    if (out_c % 4 != 0 || d.out_gs % 4 != 0 || (reinterpret_cast<uintptr_t>(d.out) & 15) != 0) return 1;
+    const int pad = d.k / 2;
+    const long long Ho = (d.H + 2 * pad - d.k) / d.stride + 1, Wo = (d.W + 2 * pad - d.k) / d.stride + 1;
+    const int sms = sm_count();
+    int BN = d.cout_pad >= 256 ? 256 : d.cout_pad;
+    long long tiles = (Ho * Wo + 127) / 128 * (d.cout_pad / BN) * d.groups;
+    if (BN == 256 && tiles < sms) tiles *= 2;  // (N tiles of 128, as launch_conv_tc picks them)
+    const int ksteps = d.k * d.k * (d.Cin / 64);
+    if (tiles * 4 > sms || ksteps < 8) return 1;
+    long long ks = sms / tiles;
+    if (ks > ksteps / 4) ks = ksteps / 4;
+    return ks >= 2 ? (int)ks : 1;
+}
+
+size_t conv_tc_workspace(const ConvDesc& d) {
+    const int ks = conv_tc_ksplit(d);
+    if (ks < 2) return 0;
+    const int pad = d.k / 2;
+    const size_t Ho = (d.H + 2 * pad - d.k) / d.stride + 1, Wo = (d.W + 2 * pad - d.k) / d.stride + 1;
+    return (size_t)ks * d.groups * Ho * Wo * d.cout_pad;
+}
+
+// The split layers' finish: out = act(bias + (((range 0) + range 1) + ...)), four channels per thread
+__global__ void conv_tc_split_reduce_kernel(const TcArgs p) {
+    pdl_trigger();
+    pdl_wait();
+    const int C4 = p.Cout >> 2;
+    const long long per_g = (long long)p.Ho * p.Wo * C4, total = per_g * p.groups;
+    const size_t slice = (size_t)p.groups * p.Ho * p.Wo * p.ws_c;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i / per_g);
+        const long long rem = i - (long long)g * per_g;
+        const int m = (int)(rem / C4), c = (int)(rem - (long long)m * C4) * 4;
+        const int oh = m / p.Wo, ow = m - oh * p.Wo;
+        if (oh >= p.out_h || ow >= p.out_w) continue;
+        const float* src = p.ws + ((size_t)g * p.Ho * p.Wo + m) * p.ws_c + c;
+        float4 v = *reinterpret_cast<const float4*>(src);
+        for (int kr = 1; kr < p.ksplit; ++kr) {
+            const float4 u = *reinterpret_cast<const float4*>(src + kr * slice);
+            v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+        }
+        const float* b = p.bias + (size_t)g * p.b_gs + c;
+        v.x += b[0]; v.y += b[1]; v.z += b[2]; v.w += b[3];
+        if (p.act) { gelu_tc2(v.x, v.y); gelu_tc2(v.z, v.w); }
+        const size_t o = (size_t)g * p.out_gs + ((size_t)oh * p.out_w + ow) * p.out_c + c;
+        if (p.out_f32) *reinterpret_cast<float4*>(static_cast<float*>(p.out) + o) = v;
+        else *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(p.out) + o) = make_uint2(pack_bf16(v.x, v.y), pack_bf16(v.z, v.w));
+    }
+}
+
+cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s, int* nl) {
+    int nl_ = 0;
+    if (!nl) nl = &nl_;
     if (d.wsc && (d.mode == OUT_PS_FINAL_U8 || d.mode == OUT_PS_FINAL_F32) && d.k == 3 && d.stride == 1 &&
         d.Cin == 64 && d.Cout == 12)
         return launch_conv_final(d, s);
@@ -1712,10 +1794,14 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
                           d.out_h == 2 * Ho && d.out_w == 2 * Wo &&
                           (d.groups == 1 || d.out_gs == 4LL * Ho * Wo * Cq);
     const int out_c = (d.mode == OUT_NHWC && d.out_c_stride) ? d.out_c_stride : d.Cout;
-    const bool nhwc_stage = !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 &&
+    // (split-K layers write raw range sums instead, finished by conv_tc_split_reduce_kernel)
+    int ksplit = conv_tc_ksplit(d);
+    if (ksplit > 1 && (!d.tc_ws || d.tc_ws_cap < conv_tc_workspace(d))) ksplit = 1;
+    const bool nhwc_stage = ksplit == 1 && !halo && BN >= 64 && d.mode == OUT_NHWC && !d.out_f32 &&
                             (f8 ? o8 && out_c % 16 == 0 && d.out_gs % 16 == 0 : out_c % 8 == 0 && d.out_gs % 8 == 0);
     const bool staged = ps_stage || nhwc_stage;
     TcArgs a{};
+    a.ksplit = 1;
     if (halo) { a.TW = kxn ? kKxnStrip : 128; a.TH = 1; } else pick_tile(Ho, Wo, &a.TW, &a.TH, ps_stage && d.groups > 1);
     // two stacked 128-pixel sub-tiles per tile (sharing each stage's weights): the 128-output layers with
     // NHWC bf16 outputs that keep at least two such tiles per SM (decoder R1, encoder A2 at video sizes;
@@ -1740,6 +1826,12 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
     a.n_tiles = d.cout_pad / BN;
     a.groups = d.groups;
     a.total_tiles = a.tiles_w * a.tiles_h * a.n_tiles * d.groups;
+    if (ksplit > 1) {  // work units: (tile, K range)
+        a.ksplit = ksplit;
+        a.ws = d.tc_ws;
+        a.ws_c = d.cout_pad;
+        a.total_tiles *= ksplit;
+    }
     a.cin_chunks = c32 ? 1 : d.Cin / 64;
     a.ksteps = d.k * d.k * a.cin_chunks;
     if (d.kmask && a.ksteps > 64) return cudaErrorInvalidValue;  // the skip mask has one bit per K step
@@ -1911,13 +2003,19 @@ cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s) {
         }
     }
     if (c32) return BN == 64 ? launch_bn<64, 12, false, OP_BF16_32>(ma, mb, mc, a, s) : cudaErrorInvalidValue;
+    cudaError_t e;
     switch (BN) {
-        case 16: return launch_bn<16, 8, false>(ma, mb, mc, a, s);
-        case 64: return launch_bn<64, 8, false>(ma, mb, mc, a, s);
-        case 128: return launch_bn<128, 6, false>(ma, mb, mc, a, s);
-        case 192: return launch_bn<192, 5, false>(ma, mb, mc, a, s);
-        default: return launch_bn<256, 4, false>(ma, mb, mc, a, s);
+        case 16: e = launch_bn<16, 8, false>(ma, mb, mc, a, s); break;
+        case 64: e = launch_bn<64, 8, false>(ma, mb, mc, a, s); break;
+        case 128: e = launch_bn<128, 6, false>(ma, mb, mc, a, s); break;
+        case 192: e = launch_bn<192, 5, false>(ma, mb, mc, a, s); break;
+        default: e = launch_bn<256, 4, false>(ma, mb, mc, a, s); break;
     }
+    if (e != cudaSuccess || ksplit == 1) return e;
+    const long long n4 = (long long)d.groups * Ho * Wo * (d.Cout / 4);
+    const unsigned blocks = (unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);
+    ++*nl;
+    return launch_pdl(conv_tc_split_reduce_kernel, dim3(blocks), dim3(256), (size_t)0, s, a);
 }
 
 }  // namespace ufvc

@@ -244,6 +244,8 @@ struct ConvDesc {
     float res_s = 0.f;
     float* ws = nullptr;        // SIMT split-K workspace (conv_simt_workspace(d) floats), or nullptr
     size_t ws_cap = 0;
+    float* tc_ws = nullptr;     // tensor-core split-K workspace (conv_tc_workspace(d) floats), or nullptr
+    size_t tc_ws_cap = 0;
     int* err = nullptr;         // device status word (bounded-wait timeouts)
     int vec4 = 0;               // SIMT: set by the launcher when NHWC outputs may be written 16 bytes at a time
     // tensor-core path: K steps (tap x 64-channel chunk, tap-major) whose weights are all zero and are
@@ -277,7 +279,9 @@ size_t ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H);
 cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s, int* nl = nullptr);
 // floats of split-K workspace the SIMT launch of d uses (0: none)
 size_t conv_simt_workspace(const ConvDesc& d);
-cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s);
+cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s, int* nl = nullptr);  // nl: launches beyond the conv
+int conv_tc_ksplit(const ConvDesc& d);         // K ranges of a split tensor-core layer (1: not split)
+size_t conv_tc_workspace(const ConvDesc& d);   // floats of its range-sum workspace (0: none)
 // fmt: the caller's colour format (ufvc_color); the network reads its three channels per frame
 void launch_pack_bf16(const uint8_t* frames, int N, int H, int W, int Hp, int Wp, int Cp, __nv_bfloat16* x,
                       cudaStream_t s, bool s2d, int fmt);

@@ -79,6 +79,9 @@ LAYERS = [  # (arch, N, layer, H, W, stride, act, mode, cin_pad)
     (1, 2, 15, 13, 121, 1, 1, 0, 64),    # R2a: a second strip holding one pixel
     (1, 2, 15, 6, 119, 1, 1, 0, 64),     # R2a: one strip, its last lane pair past the edge
     (1, 2, 18, 150, 260, 1, 0, 0, 64),   # U3 as a plain NHWC layer: the N = 16 resident-weight kernel
+    (1, 8, 6, 68, 120, 2, 1, 0, 256),    # H1 on the 1080p latent: 16 tiles, K split in ranges (GELU)
+    (1, 8, 7, 34, 60, 2, 0, 0, 128),     # H2 on the 1080p hyper-latent: 4 tiles, K split in ranges
+    (1, 8, 6, 18, 26, 2, 1, 0, 256),     # H1, ragged (9 x 13 outputs), one tile: the most ranges
 ]
 
 
