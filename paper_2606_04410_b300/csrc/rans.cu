@@ -191,6 +191,10 @@ __device__ __forceinline__ uint32_t enc_update(uint32_t x, const EncSym& q) {
 // coding warp's step is the state chain and the store of its renormalisation word.  Hand-over through
 // mbarriers with bounded waits.
 constexpr int kEncRingBytes = 4 * kPF * 32 * 8;
+// the producer's raw rows: per group, 16 rows of 32 indices (32 B) and 32 symbols (64 B), four groups
+constexpr int kEncRawGroups = 4;
+constexpr int kEncRawBytes = kEncRawGroups * kPF * 96;
+constexpr int kEncHelpExtra = kEncRingBytes + 128 + kEncRawBytes;  // ring, 8 barriers, raw rows
 template <bool STAGE, bool HELP = false>
 __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, const uint32_t* __restrict__ tables) {
     extern __shared__ __align__(16) uint32_t tab[];  // [64][511] (freq << 16) | cum, then the staged words
@@ -233,6 +237,8 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
             const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
             uint2* ring = reinterpret_cast<uint2*>(reinterpret_cast<uint8_t*>(stage) + J.stage_bytes);
             uint64_t* hb = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(ring) + kEncRingBytes);
+            // raw rows of group g in slot g % 4: indices [16][32] u8, then symbols [16][32] s16
+            uint8_t* raw = reinterpret_cast<uint8_t*>(hb) + 128;
             if (threadIdx.x == 0) {
                 for (int k = 0; k < 8; ++k) ptx::mbar_init(&hb[k], 1);  // full[4], empty[4]
                 ptx::fence_mbar_init();
@@ -260,18 +266,51 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
             const int K = S.K;
             const size_t lane0 = (size_t)bs * T;
             if (w == 1) {
-                // ---- producer: group g holds the elements m = cmin - 1 - 16 g - u of the warp's lanes
+                // ---- producer: group g holds the elements m = cmin - 1 - 16 g - u of the warp's lanes.  When
+                //      the rows are 16-byte aligned, each row of a group (32 indices, 32 symbols) arrives by a
+                //      bulk copy issued four groups ahead, so the loads' latency overlaps the coding; else
+                //      the lanes load their elements directly
+                const bool bulk = ((reinterpret_cast<uintptr_t>(S.idx) | reinterpret_cast<uintptr_t>(S.sym)) & 15) == 0 &&
+                                  (K & 15) == 0 && (lane0 & 15) == 0;
+                // lane l copies 16 bytes of the index rows (row l / 2, half l & 1) and 32 bytes of the symbol
+                // rows (row l / 2, quarters 2 (l & 1) and 2 (l & 1) + 1) of group g into raw slot g % 4
+                auto issue = [&](uint32_t g) {
+                    if (g < ngr) {
+                        uint8_t* dst = raw + (g % kEncRawGroups) * (kPF * 96);
+                        const int u = l >> 1, h = l & 1;
+                        const size_t e = lane0 + (size_t)(cmin - 1 - kPF * g - u) * K;
+                        ptx::cp_async16(dst + u * 32 + 16 * h, S.idx + e + 16 * h);
+                        ptx::cp_async16(dst + kPF * 32 + u * 64 + 32 * h, S.sym + e + 16 * h);
+                        ptx::cp_async16(dst + kPF * 32 + u * 64 + 32 * h + 16, S.sym + e + 16 * h + 8);
+                    }
+                    ptx::cp_async_commit();  // (an empty group past the last keeps the count)
+                };
+                if (bulk)
+                    for (uint32_t g = 0; g < (uint32_t)kEncRawGroups; ++g) issue(g);
                 uint32_t bad = 0;
                 for (uint32_t g = 0; g < ngr; ++g) {
                     const int b = (int)(g & 3);
                     const uint32_t use = g >> 2;
                     uint32_t tv[kPF];
                     int sv[kPF];
+                    if (bulk) {
+                        ptx::cp_async_wait<kEncRawGroups - 1>();  // this lane's copies of group g have landed
+                        __syncwarp();                              // and every lane's
+                        const uint8_t* src = raw + (g % kEncRawGroups) * (kPF * 96);
 #pragma unroll
-                    for (int u = 0; u < kPF; ++u) {
-                        const size_t e = lane0 + l + (size_t)(cmin - 1 - kPF * g - u) * K;
-                        tv[u] = __ldg(S.idx + e);
-                        sv[u] = __ldg(S.sym + e);
+                        for (int u = 0; u < kPF; ++u) {
+                            tv[u] = src[u * 32 + l];
+                            sv[u] = reinterpret_cast<const int16_t*>(src + kPF * 32)[u * 32 + l];
+                        }
+                        __syncwarp();  // the slot is read: group g + 4 may overwrite it
+                        issue(g + kEncRawGroups);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < kPF; ++u) {
+                            const size_t e = lane0 + l + (size_t)(cmin - 1 - kPF * g - u) * K;
+                            tv[u] = __ldg(S.idx + e);
+                            sv[u] = __ldg(S.sym + e);
+                        }
                     }
                     if (use > 0 && !__all_sync(0xffffffffu, hwait(&hb[4 + b], (use - 1) & 1))) break;
 #pragma unroll
@@ -285,6 +324,7 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
                     __syncwarp();
                     if (l == 0) ptx::mbar_arrive(&hb[b]);
                 }
+                if (bulk) ptx::cp_async_wait<0>();  // nothing in flight when the block's shared memory is freed
                 if (bad) set_status(J.status, UFVC_ERR_ARG);
             } else if (w == 0 && ngr > 0) {
                 // ---- coding warp: first the top element of the lanes that have one more, then the groups
@@ -554,7 +594,7 @@ cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cud
             cap32 = j.s[i].cap_lane > cap32 ? j.s[i].cap_lane : cap32;
         }
         const size_t st32 = ((size_t)32 * cap32 * 2 + 15) & ~(size_t)15;
-        help = b32 <= kRansMaxBlocks && kEncTabBytes + st32 + kEncRingBytes + 64 <= (size_t)kEncSmemMax;
+        help = b32 <= kRansMaxBlocks && kEncTabBytes + st32 + kEncHelpExtra <= (size_t)kEncSmemMax;
         if (help) T = 32;
     }
     j.lpb = T;
@@ -580,8 +620,8 @@ cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cud
     const int BT = staged ? (T < 128 ? 128 : T) : 512;
     j.stage_bytes = (int)stage;
     // the shared memory holds the tables (then the lanes' offsets and counts, 12 bytes each) and the stage
-    // (HELP: then the ring and its eight barriers)
-    const int smem = (int)(kEncTabBytes + (staged ? stage : 0) + (help ? kEncRingBytes + 64 : 0));
+    // (HELP: then the ring, its barriers and the producer's raw rows)
+    const int smem = (int)(kEncTabBytes + (staged ? stage : 0) + (help ? kEncHelpExtra : 0));
     const void* kern = help     ? (const void*)rans_encode_kernel<true, true>
                        : staged ? (const void*)rans_encode_kernel<true>
                                 : (const void*)rans_encode_kernel<false>;
