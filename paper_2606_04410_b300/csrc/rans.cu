@@ -804,7 +804,8 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
     const uint32_t words = inl ? count_at(lane) : 0u;
     uint32_t btot;
     const uint32_t excl = block_excl_scan(words, &btot, scan_sh);
-    // From here on a warp steps in lock-step (the rare bisection below is a warp vote): lanes past K, and
+    // From here on a warp steps in lock-step (the rare bisection below is a lane's own branch; the warp
+    // reconverges after it): lanes past K, and
     // lanes with a bad count, take part without coding; a warp with no lane left returns.
     if (!HELP && __all_sync(0xffffffffu, !inl)) return;  // (HELP: the block's lanes are its warp 0, all < K)
     const uint32_t n = J.n, cnt = inl ? lane_elems(n, K, lane) : 0u;
@@ -871,7 +872,7 @@ __global__ void __launch_bounds__(512) rans_decode_kernel(const RansDecJob J, co
         s = tl ? slot : tr ? slot - (kProbM - kNsym) : s;
         const uint32_t d = e.x >> 25;
         const bool far = act && d >= 2u && slot >= b1 + f1 && !tl && !tr;
-        if (__any_sync(0xffffffffu, far)) {
+        {  // (a lane's own branch: a warp vote before it cost more on the chain than the rare divergence)
             if (far) {  // the slot lies past s0 + 1: bisection over the bucket's remaining symbols
                 const uint16_t* C = cum + t * 512;
                 uint32_t lo = s0 + 2, hi = s0 + (d < 127u ? d : 255u);
