@@ -195,7 +195,7 @@ __device__ __forceinline__ uint32_t enc_update(uint32_t x, const EncSym& q) {
 }
 
 // STAGE: the lanes' words are staged in shared memory (after the tables) instead of the global rows; the
-// block copies them to their place either way.  A block codes J.lpb lanes (its first J.lpb threads); all
+// block copies them to their place either way.  A block codes S.lpb lanes (its first S.lpb threads); all
 // its threads copy.
 // HELP (one warp of lanes per block, staged, the latency-bound case): warp 1 serves the coding warp
 // through a shared-memory ring of four groups of 16 steps: it loads each element's symbol and scale index,
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
     __shared__ int ticket_sh, last_sh, abort_sh;
     __shared__ unsigned long long pre_sh, base_sh;
     RansCtl* ctl = J.ctl;
-    const int T = J.lpb, BT = blockDim.x;
+    const int BT = blockDim.x;
     uint16_t* stage = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(tab) + kEncTabBytes);
     const bool loaded = __syncthreads_and(load_table(tab, tables, kEncTabBytes, &bar, J.status, J.spin));
     if (loaded) pdl_trigger();  // the tables are constants: loaded while the previous kernel finishes
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(512) rans_encode_kernel(const RansEncJob J, co
         while (si + 1 < J.nsec && t >= J.s[si + 1].first) ++si;
         const RansEncSec& S = J.s[si];
         const RansEncStream& O = J.st[S.stream];
+        const int T = S.lpb;         // this section's lanes per block
         const int bs = t - S.first;  // block within the section
         const int lane = bs * T + threadIdx.x;
         const bool live = (int)threadIdx.x < T && lane < S.K;
@@ -599,6 +600,7 @@ cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cud
     // few lanes per SM (the latency-bound case): one warp of lanes per block with its serving warp, when
     // the blocks stay within the control block and the words, the ring and the tables fit
     bool help = false;
+    size_t st_help = 0;  // the staged words' bytes the serving-warp layout was checked with
     if (T <= 64) {
         int b32 = 0, cap32 = 0;
         for (int i = 0; i < j.nsec; ++i) {
@@ -607,29 +609,46 @@ cudaError_t launch_rans_encode(RansEncJob& j, const uint32_t* packed_tables, cud
         }
         const size_t st32 = ((size_t)32 * cap32 * 2 + 15) & ~(size_t)15;
         help = b32 <= kRansMaxBlocks && kEncTabBytes + st32 + kEncHelpExtra <= (size_t)kEncSmemMax;
-        if (help) T = 32;
+        if (help) {
+            T = 32;
+            st_help = st32;
+        }
     }
     j.lpb = T;
     j.grid = 0;
-    int cap = 0;
+    size_t stage_max = 0;  // the largest block's staged words
     for (int i = 0; i < j.nsec; ++i) {
         RansEncSec& e = j.s[i];
         if (e.K < 1 || e.stream < 0 || e.stream >= j.nstreams) return cudaErrorInvalidValue;
-        e.nblk = (e.K + T - 1) / T;
+        // with serving warps (one warp of lanes per block), a section with per-channel tables (the z^
+        // section: 16 steps per lane, no serving warp) takes up to 512 lanes per block, so that its few
+        // blocks leave the SMs to the long y^ blocks instead of holding 128 of them at the start
+        e.lpb = T;
+        if (help && e.idx_period > 0) {  // (its rows must fit in the staged words checked above)
+            int l = (e.K + 31) / 32 * 32;
+            l = l < 512 ? l : 512;
+            const long long fit = (long long)(st_help / (2ull * (e.cap_lane > 0 ? e.cap_lane : 1))) / 32 * 32;
+            l = l < fit ? l : (int)fit;
+            e.lpb = l > 32 ? l : 32;
+        }
+        j.lpb = e.lpb > j.lpb ? e.lpb : j.lpb;
+        e.nblk = (e.K + e.lpb - 1) / e.lpb;
         e.first = j.grid;
         j.grid += e.nblk;
         // a stream's sections are consecutive: the one before it in the same stream, and whether it ends it
         e.prev = i > 0 && j.s[i - 1].stream == e.stream ? i - 1 : -1;
         e.last = i + 1 == j.nsec || j.s[i + 1].stream != e.stream;
         if (e.prev >= 0 && j.s[e.prev].prev >= 0) return cudaErrorInvalidValue;  // at most two per stream
-        cap = e.cap_lane > cap ? e.cap_lane : cap;
+        const size_t st = (size_t)e.lpb * e.cap_lane * 2;
+        stage_max = st > stage_max ? st : stage_max;
     }
     if (j.grid > kRansMaxBlocks) return cudaErrorInvalidValue;
     // the words go through shared memory when every lane's row fits there beside the tables; then the
     // block needs few threads to copy them, else 512 copy from the global rows
-    const size_t stage = ((size_t)T * cap * 2 + 15) & ~(size_t)15;
+    const size_t stage = (stage_max + 15) & ~(size_t)15;
     const bool staged = kEncTabBytes + stage <= (size_t)kEncSmemMax;
-    const int BT = staged ? (T < 128 ? 128 : T) : 512;
+    if (!staged && help) return cudaErrorInvalidValue;  // (help was chosen with the rows fitting)
+    const int BT = staged ? (j.lpb < 128 ? 128 : j.lpb) : 512;
     j.stage_bytes = (int)stage;
     // the shared memory holds the tables (then the lanes' offsets and counts, 12 bytes each) and the stage
     // (HELP: then the ring, its barriers and the producer's raw rows)

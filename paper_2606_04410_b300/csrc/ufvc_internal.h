@@ -348,6 +348,7 @@ struct RansEncSec {
     int cap_lane;
     int stream;               // the stream (output) it belongs to; a stream's sections are consecutive
     int nblk, first, prev, last;  // set by the launcher
+    int lpb;                  // set by the launcher: lanes per block (its first lpb threads)
 };
 struct RansEncStream {
     uint8_t* out;
@@ -364,7 +365,7 @@ struct RansEncJob {
     int nsec;
     RansEncStream st[kRansMaxStreams];
     int nstreams;
-    int grid, lpb;            // set by the launcher: blocks, lanes per block
+    int grid, lpb;            // set by the launcher: blocks, the largest section's lanes per block
     int stage_bytes;          // set by the launcher: the staged words' bytes in shared memory (16-aligned)
     RansCtl* ctl;
     int* status;
