@@ -1279,6 +1279,10 @@ cudaError_t launch_rans_decode(RansDecJob& j, const uint8_t* dec_tables, cudaStr
     if (j.K < 1 || j.K > 65536 || j.nsec < 1 || j.nsec > kRansMaxDecSec) return cudaErrorInvalidValue;
     // the lanes of all sections spread over one wave of one block per SM
     j.threads = dec_threads(j.K * j.nsec, sm_count());
+    // per-channel tables (the z^ section: a few steps per lane) in blocks of up to 512 lanes: each block's
+    // fixed costs (the tables' copy, the header, the scan of the lane counts) then count a few times
+    // instead of once per warp of lanes
+    if (j.idx_period) j.threads = 512;
     if (j.threads > j.K) j.threads = (j.K + 31) / 32 * 32;
     j.bps = (j.K + j.threads - 1) / j.threads;
     if (j.idx_period) {
