@@ -136,14 +136,18 @@ constexpr uint32_t kProbM = 1u << 16;
 constexpr uint32_t kRansL = 1u << 16;
 
 #ifdef __CUDACC__
-// #{k : thr[k] < v} for the 63 ascending scale-index thresholds (the scale index of log sigma v)
+// #{k : thr[k] < v} for the 63 ascending scale-index thresholds (the scale index of log sigma v).  The
+// thresholds are the log-domain midpoints of log-spaced bins, so they are nearly equally spaced: a
+// linear guess from the first and last is within a step of the count, and the two loops move it to the
+// exact count (for any guess, NaN and infinities included: the result is the comparisons', not the
+// guess's).
 __device__ __forceinline__ int count_below(const float* thr, float v) {
-    int lo = 0, hi = kBins - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (thr[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
+    const float t0 = thr[0], tl = thr[kBins - 2];
+    const float gf = (v - t0) * (float)(kBins - 2) / (tl - t0) + 1.0f;
+    int c = gf <= 0.0f ? 0 : gf >= (float)(kBins - 1) ? kBins - 1 : (int)gf;
+    while (c > 0 && !(thr[c - 1] < v)) --c;
+    while (c < kBins - 1 && thr[c] < v) ++c;
+    return c;
 }
 #endif
 
