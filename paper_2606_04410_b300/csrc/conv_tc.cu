@@ -1256,7 +1256,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                          const __grid_constant__ CUtensorMap tmC, const TcArgs p) {
     constexpr int STAGES = 8, A_BYTES = 128 * 128, B_BYTES = 128 * 128, NACC = 4;
     constexpr uint32_t TMEM_COLS = 512;
-    constexpr int C_BYTES = OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0;
+    // staging: RG output rows (each three boxes of 240 elements) gathered before one barrier and their
+    // TMA stores, so the epilogue warps meet once per RG rows
+    constexpr int RG = OUTK == 1 ? 4 : 2;
+    constexpr int CSLOT = OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0, C_BYTES = RG * CSLOT;
     // staging box stride in elements: every box starts 128-byte aligned (a TMA requirement on the
     // shared-memory address): 512 B for uint8, 480 floats = 1920 B for float
     constexpr int BOXE = OUTK == 1 ? 512 : 480;
@@ -1406,7 +1409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3, k = (warp - 2) >> 2;
         const bool elected = OUTK != 0 && warp == 2 && lane == 0;
         const uint32_t lane_base = tmem_base + ((uint32_t)(q * 32) << 16) + 32 * k;
-        int pr = 0, waited = 0, o = 0;
+        int pr = 0, waited = 0, o = 0, pc = 0, y0 = 0;  // o: rows in the open group, pc: groups stored
         bool ok = true;
         for (int t = t_begin; t < t_end && ok;) {
             const int ya = t % Ho, r = t / Ho, strip = r % p.tiles_w, g = r / p.tiles_w;
@@ -1416,8 +1419,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float b0 = bias[0], b1 = bias[1], b2 = bias[2];
             const int xo = strip * kFinStrip + 30 * q + lane - 1;
             const bool xvalid = lane >= 1 && lane <= 30 && xo < p.Wo;
+            // this thread's three staging elements (the same for every row): element xb of the strip's
+            // 720-element output row pair lies in box xb / 240
+            int se[3];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const int c = 3 * k + cc, dy = (c >> 1) & 1;
+                const int xb = (2 * (30 * q + lane - 1) + (c & 1)) * 3 + (c >> 2);
+                se[cc] = (xb / 240) * BOXE + dy * 240 + xb % 240;
+            }
             // output row y from its nine tap sums S (kx-major within each channel's 9)
-            auto emit = [&](int y, const float* S) -> bool {
+            auto emit = [&](int y, const float* S, bool last) -> bool {
                 float outv[3];
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
@@ -1438,39 +1450,44 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 } else {
-                    if (o > 0) {  // the previous row's TMA stores must have read the staging block
-                        if (elected) {
-                            ptx::bulk_wait_read0();
-                            ptx::mbar_arrive(cfree);
+                    if (o == 0) {  // a new group: the previous group's TMA stores must have read the staging
+                        if (pc > 0) {
+                            if (elected) {
+                                ptx::bulk_wait_read0();
+                                ptx::mbar_arrive(cfree);
+                            }
+                            if (!__all_sync(0xffffffffu, wait_bar(cfree, (pc - 1) & 1, abort_flag, p.err))) return false;
                         }
-                        if (!__all_sync(0xffffffffu, wait_bar(cfree, (o - 1) & 1, abort_flag, p.err))) return false;
+                        y0 = y;  // (a group's rows are consecutive rows of one run)
                     }
+                    uint8_t* slot = sC + o * CSLOT;
                     if (xvalid) {
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) {
-                            // element xb of the strip's 720-element output row pair: box xb / 240
-                            const int c = 3 * k + cc, dy = (c >> 1) & 1;
-                            const int xb = (2 * (30 * q + lane - 1) + (c & 1)) * 3 + (c >> 2);
-                            const int e = (xb / 240) * BOXE + dy * 240 + xb % 240;
-                            if constexpr (OUTK == 1) sC[e] = (uint8_t)rintf(outv[cc] * 255.0f);
-                            else reinterpret_cast<float*>(sC)[e] = outv[cc];
+                            if constexpr (OUTK == 1) slot[se[cc]] = (uint8_t)rintf(outv[cc] * 255.0f);
+                            else reinterpret_cast<float*>(slot)[se[cc]] = outv[cc];
                         }
                     }
-                    ptx::fence_proxy_async();
-                    ptx::mbar_arrive(cwritten);
-                    if (warp == 2) {
-                        bool w_ok = true;
-                        if (lane == 0) w_ok = wait_bar(cwritten, o & 1, abort_flag, p.err);
-                        if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) return false;
-                    }
-                    if (elected) {
-#pragma unroll
-                        for (int b = 0; b < 3; ++b)
-                            ptx::tma_store_3d(&tmC, sC + b * BOXE * (OUTK == 1 ? 1 : 4),
-                                              strip * 2 * kFinStrip * 3 + b * 240, 2 * y, g);
-                        ptx::bulk_commit();
-                    }
                     ++o;
+                    if (o == RG || last) {  // the group is complete: one barrier, then its rows' stores
+                        ptx::fence_proxy_async();
+                        ptx::mbar_arrive(cwritten);
+                        if (warp == 2) {
+                            bool w_ok = true;
+                            if (lane == 0) w_ok = wait_bar(cwritten, pc & 1, abort_flag, p.err);
+                            if (!__shfl_sync(0xffffffffu, (int)w_ok, 0)) return false;
+                        }
+                        if (elected) {
+                            for (int h = 0; h < o; ++h)
+#pragma unroll
+                                for (int b = 0; b < 3; ++b)
+                                    ptx::tma_store_3d(&tmC, sC + h * CSLOT + b * BOXE * (OUTK == 1 ? 1 : 4),
+                                                      strip * 2 * kFinStrip * 3 + b * 240, 2 * (y0 + h), g);
+                            ptx::bulk_commit();
+                        }
+                        ++pc;
+                        o = 0;
+                    }
                 }
                 return true;
             };
@@ -1495,12 +1512,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     SB[i] += v[9 + i];
                     SC[i] = v[i];
                 }
-                if (j - 1 >= ya && !emit(j - 1, SA)) { ok = false; break; }
+                if (j - 1 >= ya && !emit(j - 1, SA, j - 1 == yb)) { ok = false; break; }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) { SA[i] = SB[i]; SB[i] = SC[i]; }
             }
             if (!ok) break;
-            if (r1 == yb && !emit(yb, SA)) { ok = false; break; }  // the image's last row has no row below
+            if (r1 == yb && !emit(yb, SA, true)) { ok = false; break; }  // the image's last row has no row below
             pr += r1 - r0 + 1;
             t = te;
         }
@@ -1625,7 +1642,7 @@ static cudaError_t launch_kxn(const CUtensorMap& a, const CUtensorMap& b, const 
 template <int OUTK>
 static cudaError_t launch_final(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& c, const TcArgs& args,
                                 cudaStream_t s) {
-    constexpr int kSmem = 128 * 128 + 8 * 128 * 128 + (OUTK == 1 ? 1536 : OUTK == 2 ? 6144 : 0) + kSmemExtra;
+    constexpr int kSmem = 128 * 128 + 8 * 128 * 128 + (OUTK == 1 ? 4 * 1536 : OUTK == 2 ? 2 * 6144 : 0) + kSmemExtra;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = smem_optin((const void*)conv_tc_final_kernel<OUTK>, kSmem);
     if (e != cudaSuccess) return e;
