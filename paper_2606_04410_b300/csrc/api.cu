@@ -1096,9 +1096,9 @@ static void probe(ufvc_ctx* ctx, int t, const float* x, size_t n, cudaStream_t s
 static ufvc_status run_plain_analysis(ufvc_ctx* ctx, Plan* p, const uint8_t* frames, const void* cin, cudaStream_t s) {
     const Arch& a = ctx->arch;
     const bool fp8 = ctx->cfg.precision == UFVC_FP8;
-    const bool s2d = ctx->a1s2d.wtc != nullptr && p->C0p == 32;
+    const bool s2d = ctx->cfg.precision == UFVC_BF16 && ctx->a1s2d.wtc != nullptr && p->C0p == 32;
     // BF16 / FP8 frames in RGB, YUV444 or YUV420 with even N <= 8: A1 reads the frame bytes itself (no pack)
-    const bool first = ctx->first_w != nullptr && ctx->color != UFVC_COLOR_RGB_BT709;
+    const bool first = ctx->cfg.precision != UFVC_FP32 && ctx->first_w != nullptr && ctx->color != UFVC_COLOR_RGB_BT709;
     if (first) {
         prof_begin(ctx, "A1", s);
         // (an FP8 context's A1 computes with bf16 operands and writes the E4M3 codes A2 reads)
@@ -1987,6 +1987,10 @@ extern "C" ufvc_status ufvc_calibrate_fp8(ufvc_ctx* ctx, const uint8_t* d_frames
     ufvc_ctx* c = ctx_clone_shared(ctx);
     if (!c) return fail(ctx, UFVC_ERR_OOM, "calibrate_fp8: context clone failed");
     c->cfg.precision = UFVC_FP32;
+    // the frame-byte A1 kernel and the space-to-depth A1 write bf16 / E4M3 activations: the FP32 run takes
+    // the packed input and A1's FP32 weights instead
+    c->first_w = nullptr;
+    c->a1s2d = LayerW{};
     const size_t cap = ufvc_max_bitstream_bytes(ctx, width, height);
     uint8_t *bits = nullptr, *out = nullptr;
     uint64_t* nb = nullptr;

@@ -64,6 +64,30 @@ def test_fp8_requires_calibration():
     assert e.value.code == u.UFVC_ERR_ARG
 
 
+T_Y = 6
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_fp8_calibration_is_the_fp32_analysis(N):
+    """The calibration run is the FP32 path: its y scale is max |y| of the FP64 oracle's analysis / 448
+    (N = 2 has the frame-byte A1 kernel in FP8, N = 3 does not), and contexts calibrated in a row agree."""
+    u = U()
+    H, W = 48, 80
+    blob = synthetic.draw_weights(1, N, seed=11)
+    chunk = synthetic.moving_texture(4, N, H, W, max_step=8, refresh=0.1)
+    y = oracle.analysis(1, chunk, blob)
+    want = float(np.abs(y).max()) / 448.0
+    fr = torch.from_numpy(chunk).cuda()
+    got = []
+    for _ in range(3):  # each calibration's clone frees its buffers for the next one's
+        c = u.Codec(1, N, 64, blob, "fp8")
+        c.calibrate_fp8(fr, 32)
+        got.append(np.array(c.fp8_scales()))
+    assert abs(got[0][T_Y] - want) <= 1e-4 * want, (got[0][T_Y], want)
+    for g in got[1:]:
+        np.testing.assert_array_equal(g, got[0])
+
+
 # (layer, H, W, stride, act, mode, input tensor, output tensor or None for bf16)
 FP8_LAYERS = [
     (1, 34, 50, 2, 1, 0, T_A1, T_A2),      # A2: 64 -> 128, stride 2
