@@ -46,6 +46,9 @@ struct LayerW {
     float* cs8 = nullptr;
     float out_inv = 0.f, res_s = 0.f;
     unsigned long long kmask = 0;  // tensor-core K steps that run (0: all); see ConvDesc::kmask
+    // hyper-synthesis layers of the plain model (every precision): [cout][k*k][3][cin] float, the TF32
+    // parts (hi, lo, hi) of each weight for the three-product tensor-core GEMM (conv_tf32.cu)
+    float* wtf = nullptr;
 };
 
 // Activation tensors of the FP8 path, each with one per-tensor scale (absmax / 448 on the FP32 path of a
@@ -667,6 +670,38 @@ static ufvc_status upload_dc(ufvc_ctx* ctx, const float* weights) {
     return UFVC_OK;
 }
 
+// The TF32 parts of a float: hi(x) = x with the 13 low mantissa bits cleared, lo(x) = hi(x - hi(x)).
+static float tf32_hi(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u &= 0xFFFFE000u;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+
+// A hyper-synthesis layer's weights for the three-product TF32 GEMM: K index (tap, part, c) holds
+// (hi, lo, hi)[part] of w[o][tap][c], against the input planes (hi, hi, lo) (conv_tf32.cu).  Layers the GEMM
+// does not take (Cin not a multiple of 32, Cout not a multiple of 256) keep only the SIMT weights.
+static ufvc_status upload_tf32(ufvc_ctx* ctx, LayerW& L, const float* src) {
+    const int co = L.cout, kk = L.k * L.k, ci = L.cin;
+    if (ci % 32 != 0 || ci != L.cin_p || co % 256 != 0 || L.groups != 1) return UFVC_OK;
+    std::vector<float> w((size_t)co * kk * 3 * ci);
+    for (int o = 0; o < co; ++o)
+        for (int t = 0; t < kk; ++t)
+            for (int c = 0; c < ci; ++c) {
+                const float v = src[((size_t)o * kk + t) * ci + c];
+                const float hi = tf32_hi(v), lo = tf32_hi(v - hi);
+                float* row = &w[((size_t)o * kk + t) * 3 * ci];
+                row[c] = hi;
+                row[ci + c] = lo;
+                row[2 * ci + c] = hi;
+            }
+    ufvc_status st;
+    if ((st = dalloc(ctx, nullptr, &L.wtf, w.size())) != UFVC_OK) return st;
+    CK(cudaMemcpy(L.wtf, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+    return UFVC_OK;
+}
+
 // A1 (3x3, stride 2, 3N -> e0) regrouped for space-to-depth input: super-pixel (Y, X) holds input pixels
 // (2Y + dy, 2X + dx) as channels [2 dy + dx][32].  Output pixel (oh, ow) reads input rows 2 oh - 1 .. 2 oh + 1,
 // i.e. sub-row 1 of super-row oh - 1 and both sub-rows of super-row oh: tap (sy, sx) of the 2x2 form at
@@ -711,7 +746,7 @@ extern "C" void ufvc_destroy(ufvc_ctx* ctx) {
             for (int l = 0; l < nl; ++l) {
                 LayerW& L = Ls[l];
                 cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); cudaFree(L.btc); cudaFree(L.wsc);
-                cudaFree(L.w8); cudaFree(L.cs8);
+                cudaFree(L.w8); cudaFree(L.cs8); cudaFree(L.wtf);
             }
         }
         for (LayerW& L : ctx->pm) { cudaFree(L.w); cudaFree(L.b); cudaFree(L.wtc); }
@@ -789,6 +824,9 @@ extern "C" ufvc_status ufvc_create(const ufvc_config* cfg, const float* weights,
             return bail(st);
     if (cfg->precision == UFVC_BF16 && 3 * ctx->N <= 32 && (st = upload_a1_s2d(ctx, weights + offs[L_A1])) != UFVC_OK)
         return bail(st);
+    if (cfg->arch == 1)  // the hyper-synthesis on the tensor cores (TF32, three products), every precision
+        for (int l : {L_S1, L_S2, L_S3})
+            if ((st = upload_tf32(ctx, ctx->enc[l], weights + offs[l])) != UFVC_OK) return bail(st);
     if ((cfg->precision == UFVC_BF16 || cfg->precision == UFVC_FP8) && first_layer_ct(ctx->N) &&
         ctx->enc[L_A1].cout == 64 && ctx->enc[L_A1].k == 3) {
         // the frame-byte kernel's input is x * kS2dInScale, like the space-to-depth pack's
@@ -897,6 +935,7 @@ static ufvc_status conv(ufvc_ctx* ctx, const LayerW& L, const void* in, int H, i
         return UFVC_OK;
     }
     d.Cin = L.cin_p;
+    d.wtf = L.wtf;
     const size_t need = conv_simt_workspace(d);
     if (need) {
         Workspace* ws = ctx->cur_ws;

@@ -603,6 +603,7 @@ static int simt_plan(const ConvDesc& d, int* KS) {
 }
 
 size_t conv_simt_workspace(const ConvDesc& d) {
+    if (conv_tf32x3_ok(d)) return conv_tf32x3_workspace(d);
     int KS;
     const int kind = simt_plan(d, &KS);
     if ((kind != 2 && kind != 3) || KS == 1) return 0;
@@ -633,9 +634,10 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st, int* nl) {
     // the entropy parameters of the last hyper-synthesis layer: in its split-K reduction when it has one
     // and the tensors allow four channels per thread, else by the quantiser after the layer
     const bool want_ent = d.ent_idx != nullptr;
-    const bool fuse_ent = want_ent && kind == 3 && KS > 1 && d.groups == 1 && d.mode == OUT_NHWC && d.act == 0 &&
-                          !d.res && d.split > 0 && d.split % 4 == 0 && d.Cout == 2 * d.split && aligned16(d.out) &&
-                          (!d.ent_keep_ls || aligned16(d.out2)) && aligned16(d.b) &&
+    const bool tf = conv_tf32x3_ok(d);  // the TF32 three-product GEMM, then the range-sum reduction below
+    const bool fuse_ent = want_ent && (tf || (kind == 3 && KS > 1)) && d.groups == 1 && d.mode == OUT_NHWC &&
+                          d.act == 0 && !d.res && d.split > 0 && d.split % 4 == 0 && d.Cout == 2 * d.split &&
+                          aligned16(d.out) && (!d.ent_keep_ls || aligned16(d.out2)) && aligned16(d.b) &&
                           (reinterpret_cast<uintptr_t>(d.ent_idx) & 3) == 0 &&
                           (!d.ent_y || (aligned16(d.ent_y) && (reinterpret_cast<uintptr_t>(d.ent_rhat) & 7) == 0));
     if (want_ent && !fuse_ent) {  // the layer as usual (mu and log sigma written), then the quantiser
@@ -647,6 +649,22 @@ cudaError_t launch_conv_simt(const ConvDesc& d_in, cudaStream_t st, int* nl) {
         ++*nl;
         launch_quantize(d.ent_y, static_cast<const float*>(d.out), d.out2, (size_t)M * d.split, d.ent_thr, d.ent_qinv,
                         d.ent_qp_dev, d.ent_qp, d.ent_y ? d.ent_rhat : nullptr, d.ent_idx, st);
+        return cudaGetLastError();
+    }
+    if (tf) {
+        const float* sums = nullptr;
+        cudaError_t e = launch_tf32x3_gemm(d, st, &KS, &sums);
+        if (e != cudaSuccess) return e;
+        *nl += 2;
+        if (fuse_ent) {
+            const int n4 = M * (d.split / 4);
+            const unsigned blocks = (unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096);
+            ++*nl, (void)launch_pdl(conv_simt_reduce_entropy_kernel, dim3(blocks), dim3(256), (size_t)(0), st, d, M, KS,
+                                    sums);
+        } else {
+            ++*nl, (void)launch_pdl(conv_simt_reduce_kernel, dim3(reduce_blocks(d, M)), dim3(256), (size_t)(0), st, d, Ho,
+                                    Wo, KS, sums);
+        }
         return cudaGetLastError();
     }
     if (kind == 0) {

@@ -1561,6 +1561,17 @@ static bool encode_map(CUtensorMap* m, const void* base, int rank, const cuuint6
     return r == CUDA_SUCCESS;
 }
 
+bool encode_f32_map_sw128(void* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                          const uint32_t* box) {
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5];
+    if (rank < 1 || rank > 5) return false;
+    for (int i = 0; i < rank; ++i) { d[i] = dims[i]; b[i] = box[i]; }
+    for (int i = 0; i + 1 < rank; ++i) st[i] = strides[i];
+    return encode_map(static_cast<CUtensorMap*>(map), base, rank, d, st, b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                      CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 // Frames [N][H][row_bytes] uint8 as a 3D tensor map (bytes, rows, frames) with box (box_x, box_y, N), no
 // swizzle; map points at a 64-byte aligned CUtensorMap.
 bool encode_frames_map(void* map, const void* frames, int N, int H, int row_bytes, int box_x, int box_y) {

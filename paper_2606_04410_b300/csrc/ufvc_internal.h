@@ -270,6 +270,10 @@ struct ConvDesc {
     const int* ent_qp_dev = nullptr;
     int ent_qp = 0;
     int ent_keep_ls = 1;
+    // hyper-synthesis layers on the tensor cores (conv_tf32.cu): weights [Cout][k*k][3][Cin] float, the
+    // TF32 parts (hi, lo, hi) of each weight; launched through launch_conv_simt, whose workspace then
+    // holds the input's TF32 planes and the K-range sums
+    const float* wtf = nullptr;
 };
 
 // api.cu internals used by the server: a context sharing another's weights, and a plan's device bytes
@@ -284,6 +288,16 @@ cudaError_t launch_conv_simt(const ConvDesc& d, cudaStream_t s, int* nl = nullpt
 // floats of split-K workspace the SIMT launch of d uses (0: none)
 size_t conv_simt_workspace(const ConvDesc& d);
 cudaError_t launch_conv_tc(const ConvDesc& d, cudaStream_t s, int* nl = nullptr);  // nl: launches beyond the conv
+// TF32 three-product GEMM of a hyper-synthesis layer (conv_tf32.cu): conv_tf32x3_ok(d) when d has wtf and
+// a shape it takes (stride 1, k = 1 or 3, Cin % 32 == 0, Cout % 256 == 0, one group); the workspace holds
+// the input's planes then the K-range sums; launch_tf32x3_gemm launches the planes and GEMM kernels and
+// returns the number of K ranges and where their sums start
+bool conv_tf32x3_ok(const ConvDesc& d);
+size_t conv_tf32x3_workspace(const ConvDesc& d);
+cudaError_t launch_tf32x3_gemm(const ConvDesc& d, cudaStream_t s, int* KS, const float** sums);
+// A float32 tensor map with the 128-byte swizzle (conv_tc.cu); map points at a 64-byte aligned CUtensorMap
+bool encode_f32_map_sw128(void* map, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                          const uint32_t* box);
 int conv_tc_ksplit(const ConvDesc& d);         // K ranges of a split tensor-core layer (1: not split)
 size_t conv_tc_workspace(const ConvDesc& d);   // floats of its range-sum workspace (0: none)
 // fmt: the caller's colour format (ufvc_color); the network reads its three channels per frame
