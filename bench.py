@@ -215,13 +215,16 @@ def conv_bytes(Hy: int, Wy: int, H_: int, W_: int) -> dict:
 
 
 def compute_peaks(pk: dict, precision: str) -> dict:
-    """Peaks each stage is measured against: tensor (burst bf16, x2 for E4M3 by the nominal ratio), FP32
-    ALU (148 SMs x 128 FMA/clk x 2 at the maximum SM clock, derived) and HBM (measured copy)."""
+    """Peaks each stage is measured against: tensor (burst bf16, x2 for E4M3 by the nominal ratio), TF32
+    tensor (burst bf16 x 0.5, the nominal ratio), FP32 ALU (148 SMs x 128 FMA/clk x 2 at the maximum SM
+    clock, derived) and HBM (measured copy)."""
     mhz = pk.get("sm_max_mhz", 2032.0)
     src = pk["source"]
     tens = pk["bf16_tflops"] * (2 if precision == "fp8" else 1)
     return {"tensor": {"peak": tens, "unit": "TFLOP/s",
                        "source": f"{src} bf16 burst" + (" x2 (fp8 nominal ratio)" if precision == "fp8" else "")},
+            "tf32": {"peak": pk["bf16_tflops"] * 0.5, "unit": "TFLOP/s",
+                     "source": f"{src} bf16 burst x0.5 (tf32 nominal ratio)"},
             "alu": {"peak": 148 * 128 * 2 * mhz * 1e6 / 1e12, "unit": "TFLOP/s",
                     "source": f"derived: 148 SMs x 128 FP32 FMA/clk x 2 x {mhz:.0f} MHz"},
             "hbm": {"peak": pk["hbm_gbs"], "unit": "GB/s", "source": f"{src} HBM copy"}}
@@ -229,7 +232,7 @@ def compute_peaks(pk: dict, precision: str) -> dict:
 
 def stage_work(hy: int, wy: int, H_: int, W_: int, nbytes: int, lanes: int, precision: str) -> dict:
     """Algorithmic work of one occurrence of every profiled stage of the plain model's step (arch 1, N
-    frames, latent hy x wy): {stage: {"flops": F, "flop_kind": "tensor"|"alu", "bytes": B, "lane_steps": S}}.
+    frames, latent hy x wy): {stage: {"flops": F, "flop_kind": "tensor"|"tf32"|"alu", "bytes": B, "lane_steps": S}}.
     Bytes count every tensor a stage reads or writes once (activations bf16 on the tensor-core path, f32
     on the FP32 path; y, mu, log sigma f32; r^ int16; indices u8; bit-stream words), FLOPs = 2 x MACs;
     lane_steps = the longest lane's symbol count for the rANS stages."""
@@ -257,9 +260,10 @@ def stage_work(hy: int, wy: int, H_: int, W_: int, nbytes: int, lanes: int, prec
         "hyper_analysis": {"flops": fl("H1", hh, wh) + fl("H2", hz, wz), "flop_kind": kind,
                            "bytes": n * 4 + n * a * 2 + hh * wh * 128 * a * 2 + nz * 4 + nz * 2},
         # S1..S3 with the entropy parameters formed in S3's pass (encoder: y in; mu, log sigma, r^, idx out;
-        # decoder: mu, idx out), the mean of the two
+        # decoder: mu, idx out), the mean of the two; TF32 tensor cores in every precision (the GEMM
+        # executes three products per multiply-add: the FLOPs here are the algorithmic ones)
         "hyper_synthesis": {"flops": fl("S1", hz, wz) + fl("S2", 2 * hz, 2 * wz) + fl("S3", hy, wy),
-                            "flop_kind": "alu",
+                            "flop_kind": "tf32",
                             "bytes": nz * 2 + 4 * hz * wz * 128 * 4 * 2 + 16 * hz * wz * 128 * 4 * 2
                                      + n * (4 + 4 + 4 + 2 + 1 + 4 + 1) // 2},
         "quantize": {"bytes": n * (4 + 4 + 4 + 2 + 1)},
