@@ -670,11 +670,12 @@ static ufvc_status upload_dc(ufvc_ctx* ctx, const float* weights) {
     return UFVC_OK;
 }
 
-// The TF32 parts of a float: hi(x) = x with the 13 low mantissa bits cleared, lo(x) = hi(x - hi(x)).
+// The TF32 parts of a float: hi(x) = x rounded to the nearest TF32 value (the 13 low fraction bits rounded
+// away, halves away from zero), lo(x) = hi(x - hi(x)).
 static float tf32_hi(float x) {
     uint32_t u;
     std::memcpy(&u, &x, 4);
-    u &= 0xFFFFE000u;
+    u = (u + 0x1000u) & 0xFFFFE000u;
     std::memcpy(&x, &u, 4);
     return x;
 }

@@ -1,8 +1,10 @@
 // Hyper-synthesis layers (S1, S2, S3) on the 5th-generation tensor cores at FP32-level accuracy.
 //
-// A float x is split into two TF32 parts: hi(x) = x with the 13 low mantissa bits cleared and
-// lo(x) = hi(x - hi(x)) (x - hi(x) is exact in FP32), so that |x - hi(x) - lo(x)| < 2^-20 |x|.  A product
-// a w is taken as hi(a) hi(w) + hi(a) lo(w) + lo(a) hi(w); the terms left out are of order 2^-20 |a w|.
+// A float x is split into two TF32 parts: hi(x) = x rounded to the nearest TF32 value (10 fraction bits;
+// the 13 low bits of the FP32 fraction rounded away, halves away from zero) and lo(x) = hi(x - hi(x))
+// (x - hi(x) is exact in FP32), so that |x - hi(x) - lo(x)| <= 2^-22 |x|.  A product a w is taken as
+// hi(a) hi(w) + hi(a) lo(w) + lo(a) hi(w); the terms left out are of order 2^-22 |a w| and, rounded to
+// nearest rather than truncated, of either sign, so they do not add up along K.
 // The three products run as one GEMM over a tripled K: for tap t and input channel c, K index
 // (t, part, c) pairs the input plane (hi, hi, lo)[part] with the weight plane (hi, lo, hi)[part].
 // tcgen05.mma kind::tf32 reads each operand from its 32-bit container; the parts carry no bits below
@@ -59,7 +61,10 @@ __device__ __forceinline__ bool tf_wait(uint64_t* bar, uint32_t parity, volatile
     }
 }
 
-__device__ __forceinline__ float tf_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (finite x; a carry out of the fraction steps the exponent, as it should)
+__device__ __forceinline__ float tf_hi(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 __global__ void __launch_bounds__(kTfThreads, 1)
     conv_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,

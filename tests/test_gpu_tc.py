@@ -297,3 +297,37 @@ def test_bf16_u8_frames_match_f32(N, H, W):
     b = bf.decode_chunk(bits, n, W, H)
     assert bf.sync_status() == 0
     assert torch.equal(b, torch.round(f * 255.0).to(torch.uint8))
+
+
+# measured: 2.05e-5 (mu, 1080p latent), 4-7e-6 (ragged shapes) -- the FP32 accumulation's error over
+# K = 1152 terms and three layers; bound about 2.5x the largest, below the chunk tests' 1e-4
+TF32X3_TOL = 5e-5
+
+
+@pytest.mark.parametrize("Hz,Wz,Hy,Wy", [(17, 30, 68, 120), (4, 6, 13, 21), (9, 13, 33, 50)])
+def test_tf32_hyper_synthesis_vs_float64(Hz, Wz, Hy, Wy):
+    """The hyper-synthesis on the TF32 tensor cores (three products per term) against the FP64 oracle, at
+    the 1080p latent (S1 in 14 K ranges over 5 tiles, S2 in 4 over 17, S3 in one over 68) and two ragged
+    cropped shapes; the FP32 and BF16 contexts run the same kernels and must agree bit for bit (a stream
+    coded in one precision decodes in the other)."""
+    u = U()
+    N = 2
+    blob = synthetic.draw_weights(1, N, seed=7)
+    rng = np.random.default_rng(Hz * 100 + Wz)
+    zhat = np.clip(np.rint(rng.laplace(0.0, 1.5, size=(Hz, Wz, 128))), -20, 20).astype(np.int16)
+    mu_o, ls_o = oracle.hyper_synthesis(1, N, zhat, Hy, Wy, blob)
+    zt = torch.from_numpy(zhat).cuda()
+    out = {}
+    for prec in ("fp32", "bf16"):
+        c = u.Codec(1, N, 64, blob, prec)
+        mu, ls = c.hyper_synthesis(zt, Hy, Wy)
+        assert c.sync_status() == 0
+        out[prec] = (mu.cpu().numpy().astype(np.float64), ls.cpu().numpy().astype(np.float64))
+    for what, g, ref in (("mu", out["fp32"][0], mu_o), ("log sigma", out["fp32"][1], ls_o)):
+        err = np.abs(g - ref) / np.maximum(1.0, np.abs(ref))
+        print(f"{what} {Hz}x{Wz}: max rel err {err.max():.3g}")
+        # the three-product split leaves terms of order 2^-22 |a w| per product (rounded to nearest, of
+        # either sign), FP32 accumulation adds its own rounding over K = 1152 terms and three layers
+        assert err.max() <= TF32X3_TOL, f"{what}: max rel err {err.max():.3g}"
+    np.testing.assert_array_equal(out["fp32"][0], out["bf16"][0])
+    np.testing.assert_array_equal(out["fp32"][1], out["bf16"][1])
