@@ -774,14 +774,14 @@ def main() -> None:
               "method": "ufvc_encode_chunk_host + ufvc_decode_chunk_host, one step at a time",
               "h2d_bytes_per_step": int(h_frames.numel() + nbh.value),
               "d2h_bytes_per_step": int(nbh.value + h_out.numel() + 8)}
-    # pipelined (ufvc_pipe_*, four slots: 1.86 ms per 1080p step in steady state against 1.91 with three,
-    # 1.88 with five and 1.89 with six): every step still copies its frames in, its bit-stream buffer out
-    # and back, and its decoded frames out; one slot's copies overlap the other slots' kernels.  A slot is
-    # reused only after its previous ticket's frames are back on the host, so with three slots the frame
-    # copies out and in of consecutive tickets left the compute stream too little slack.  The timed region
-    # runs from the first submit to the last wait (pipeline fill and drain included, over 48 steps or
-    # more, about 0.1 s at 1080p, so that they weigh as in a stream of chunks rather than a handful).
-    depth, n_pipe = 4, max(48, args.steps)
+    # pipelined (ufvc_pipe_*, five slots, with which the pipe enqueues a ticket's decode two encodes after
+    # its own: 1.76 ms per 1080p step in steady state against 1.86 with four slots and 1.91 with three,
+    # where the decode follows the next encode): every step still copies its frames in, its bit-stream
+    # buffer out and back, and its decoded frames out; one slot's copies overlap the other slots' kernels.
+    # The timed region runs from the first submit to the last wait (pipeline fill and drain included, over
+    # 48 steps or more, about 0.1 s at 1080p, so that they weigh as in a stream of chunks rather than a
+    # handful).
+    depth, n_pipe = 5, max(48, args.steps)
     pipe = U.Pipe(codec, depth)
     pb = [torch.empty(cap, dtype=torch.uint8).pin_memory() for _ in range(depth)]
     po = [torch.empty((N, H_, W_, 3), dtype=torch.uint8).pin_memory() for _ in range(depth)]

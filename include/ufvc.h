@@ -162,8 +162,8 @@ ufvc_status ufvc_decode_chunk_host(ufvc_ctx* ctx, const uint8_t* h_bits, size_t 
  * buffer (`capacity` bytes, at least ufvc_max_bitstream_bytes) to h_bits, that host copy back to the
  * device, ufvc_decode_chunk_dev of it, and the decoded frames to h_out (skipped when h_out is NULL).
  * The kernels run one chunk at a time on the compute stream; a ticket's decode is enqueued after the
- * next ticket's encode (or by its wait), so the copies of the other tickets and the bit-stream's trip
- * through the host overlap the kernels.  Host buffers must stay valid and unchanged until the
+ * next ticket's encode, or after the second next one's with depth >= 5 (or by its wait), so the copies of
+ * the other tickets and the bit-stream's trip through the host overlap the kernels.  Host buffers must stay valid and unchanged until the
  * ticket has been waited for; page-locked host memory makes the copies asynchronous.  *ticket gets
  * consecutive numbers from 0.  UFVC_ERR_ARG if ticket t - depth has not been waited for yet,
  * UFVC_ERR_CAPACITY if capacity is too small.  ufvc_pipe_wait blocks until the ticket's round trip has

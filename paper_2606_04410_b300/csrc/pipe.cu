@@ -8,14 +8,19 @@
 //   frames in (copy stream)  ->  encode (compute)  ->  bit-stream buffer and size out, then that host copy
 //   back in (copy streams)  ->  ufvc_decode_chunk_dev (compute, size read on the device)  ->  frames out.
 // All kernels run on the one compute stream, one chunk's kernels at a time, as on a single context: the
-// decode of ticket t is enqueued after the encode of ticket t + 1 (by the next submit, or by the wait of
+// decode of ticket t is enqueued after the encode of ticket t + lag (by that submit, or by the wait of
 // ticket t), so the compute stream never stands still while a bit-stream crosses the host link, and the
-// copies of the other tickets overlap it.  Each encode and each decode moves the status word into the
+// copies of the other tickets overlap it.  lag = 2 with five slots or more (the bit-stream's copies out
+// and back in queue on the copy engines behind 50 MB frame copies, and one encode of slack was not always
+// enough: 1.76 against 1.86 ms per 1080p step), else 1 (with fewer slots the host, which reuses a slot
+// only after its ticket's frames are back, would wait on decodes held back: four slots 1.93 ms, three
+// 3.37 ms with lag 2).  Each encode and each decode moves the status word into the
 // slot's mapped pinned status word and clears it, by a one-thread kernel (a copy there would queue on the
 // copy engine behind the frame copies and stall the compute stream), so every ticket reports its own
 // device status.
 #include "ufvc_internal.h"
 
+#include <deque>
 #include <vector>
 
 using namespace ufvc;
@@ -42,7 +47,8 @@ struct ufvc_pipe {
     cudaStream_t cs = nullptr, in_frames = nullptr, out_bits = nullptr, in_bits = nullptr, out_frames = nullptr;
     std::vector<PipeSlot> slots;
     long long next = 0;
-    long long pending = -1;  // a ticket whose decode is not enqueued yet
+    std::deque<long long> pending;  // tickets whose decodes are not enqueued yet, oldest first
+    size_t lag = 1;                 // encodes between a ticket's encode and its decode on the compute stream
 };
 
 static void free_slot(PipeSlot& s) {
@@ -70,6 +76,7 @@ extern "C" ufvc_status ufvc_pipe_create(ufvc_ctx* ctx, int depth, ufvc_pipe** ou
     ufvc_pipe* p = new ufvc_pipe();
     p->base = ctx;
     p->slots.resize(depth);
+    p->lag = depth >= 5 ? 2 : 1;
     bool ok = (p->ctx = ctx_clone_shared(ctx)) != nullptr;
     for (cudaStream_t* q : {&p->cs, &p->in_frames, &p->out_bits, &p->in_bits, &p->out_frames})
         ok = ok && cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) == cudaSuccess;
@@ -187,13 +194,13 @@ extern "C" ufvc_status ufvc_pipe_submit(ufvc_pipe* p, const uint8_t* h_frames, i
     }
     p->next = t + 1;
     *ticket = t;
-    // the previous ticket's decode goes after this encode on the compute stream
-    if (p->pending >= 0) {
-        const long long u = p->pending;
-        p->pending = -1;
+    // the decode of the ticket lag encodes back goes after this encode on the compute stream
+    if (h_out) p->pending.push_back(t);
+    while (p->pending.size() > p->lag) {
+        const long long u = p->pending.front();
+        p->pending.pop_front();
         if ((st = enqueue_decode(p, u))) return st;
     }
-    if (h_out) p->pending = t;
     return UFVC_OK;
 }
 
@@ -202,9 +209,10 @@ extern "C" ufvc_status ufvc_pipe_wait(ufvc_pipe* p, long long ticket, size_t* nb
     PipeSlot& s = p->slots[ticket % (long long)p->slots.size()];
     if (s.ticket != ticket || s.waited) return UFVC_ERR_ARG;
     if (cudaSetDevice(ctx_device(p->base)) != cudaSuccess) return UFVC_ERR_CUDA;
-    if (p->pending == ticket) {  // its decode waits for no later encode
-        p->pending = -1;
-        const ufvc_status st = enqueue_decode(p, ticket);
+    while (!p->pending.empty() && p->pending.front() <= ticket) {  // its decode waits for no later encode
+        const long long u = p->pending.front();
+        p->pending.pop_front();
+        const ufvc_status st = enqueue_decode(p, u);
         if (st) return st;
     }
     if (cudaEventSynchronize(s.done) != cudaSuccess) return UFVC_ERR_CUDA;
