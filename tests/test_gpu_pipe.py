@@ -27,13 +27,15 @@ def _sync_round_trip(u, codec, frames, W, H):
 
 
 @pytest.mark.parametrize("N,H,W,K,depth,prec", [(8, 128, 160, 4096, 2, "bf16"), (2, 72, 120, 256, 3, "bf16"),
-                                                  (8, 72, 160, 512, 2, "fp8")])
+                                                  (8, 72, 160, 512, 2, "fp8"),
+                                                  # five slots: each decode follows the second next encode
+                                                  (2, 72, 120, 256, 5, "bf16")])
 def test_pipe_equals_sync_calls(N, H, W, K, depth, prec):
     u = U()
     blob = synthetic.draw_weights(1, N, seed=3)
     codec = u.Codec(1, N, K, blob, prec)
     ref = u.Codec(1, N, K, blob, prec)
-    chunks = [synthetic.moving_texture(50 + i, N, H, W, max_step=16, refresh=0.1) for i in range(5)]
+    chunks = [synthetic.moving_texture(50 + i, N, H, W, max_step=16, refresh=0.1) for i in range(max(5, depth + 3))]
     if prec == "fp8":  # the pipe's slots take the context's calibration as it stands when it is created
         cal = torch.from_numpy(chunks[0]).cuda()
         codec.calibrate_fp8(cal, 32)
