@@ -468,13 +468,15 @@ size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
     size_t bytes = 0;
     plan_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, true, &bytes);
     const Arch& a = ctx->arch;
-    auto ws = [&](int h, int w, int k, int cout, int cin) {
+    auto ws = [&](int h, int w, int k, int cout, int cin, const LayerW& L) {
         ConvDesc d;
         d.H = h; d.W = w; d.k = k; d.stride = 1; d.Cout = cout; d.Cin = ceil_div(cin, 16) * 16; d.groups = 1;
+        d.wtf = L.wtf;  // the TF32 GEMM's planes and K-range sums where the layer has it
         return conv_simt_workspace(d) * sizeof(float);
     };
-    size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz), ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz),
-                          ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz)});
+    size_t hs = std::max({ws(tmp.Hz, tmp.Wz, 3, 4 * a.cz, a.cz, ctx->enc[L_S1]),
+                          ws(2 * tmp.Hz, 2 * tmp.Wz, 3, 4 * a.cz, a.cz, ctx->enc[L_S2]),
+                          ws(tmp.Hy, tmp.Wy, 1, 2 * a.cy, a.cz, ctx->enc[L_S3])});
     if (ctx->color != UFVC_COLOR_RGB) bytes += ((size_t)ctx->N * H * W * 3 * sizeof(float) + 255) & ~(size_t)255;
     if (ctx->tc_on) {
         tc_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
@@ -484,7 +486,7 @@ size_t ufvc::ctx_plan_bytes(const ufvc_ctx* ctx, int W, int H) {
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, true, &bytes);
         pm_buffers(const_cast<ufvc_ctx*>(ctx), &tmp, false, &bytes);
         if (ctx->cfg.precision == UFVC_FP32)
-            hs = std::max({hs, ws(tmp.Hy, tmp.Wy, 3, a.cz, a.cy + a.cz), ws(tmp.Hy, tmp.Wy, 1, a.cy, a.cz)});
+            hs = std::max({hs, ws(tmp.Hy, tmp.Wy, 3, a.cz, a.cy + a.cz, LayerW{}), ws(tmp.Hy, tmp.Wy, 1, a.cy, a.cz, LayerW{})});
     }
     return bytes + 2 * hs;
 }
